@@ -1,0 +1,337 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix (no GPU needed).
+
+Each test names the passage of arXiv:1411.0660 it checks, or the mathematical fact used.
+A plausible slip anywhere in the oracle (wrong sign of the field, a dropped bond, the
+periodic bond missing, an index off by one, a transposed operand in the eigensolver, a wrong
+log) makes at least one of these fail.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from spin_kron import hamiltonian_full, schmidt_entropy, sector_indices, total_spin_sq
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _gold(name):
+    with open(os.path.join(GOLD, name)) as f:
+        return json.load(f)
+
+
+# ---------------------------------------------------------------- disorder (Eq. 1) ----------
+def test_splitmix64_published_vector(orc):
+    g = _gold("splitmix64_seed1234567.json")
+    f = orc.fields(5, 1.0, g["seed"])
+    k = ((f + 1.0) * 2.0**52).astype(np.uint64)  # exact: u = (z >> 11) 2^-53
+    want = np.array([int(x) >> 11 for x in g["outputs"]], dtype=np.uint64)
+    assert np.array_equal(k, want)
+
+
+def test_fields_uniform_range_and_mean(orc):
+    f = np.concatenate([orc.fields(22, 3.0, s) for s in range(400)])
+    assert f.min() >= -3.0 and f.max() < 3.0
+    assert abs(f.mean()) < 0.1 and abs(f.var() - 3.0**2 / 3.0) < 0.15
+
+
+# ---------------------------------------------------------------- basis -----------------------
+@pytest.mark.parametrize("L", [2, 4, 6, 8, 10, 12, 14, 16, 18, 20])
+def test_basis_dimension_and_order(orc, L):
+    st = orc.basis(L)
+    assert len(st) == math.comb(L, L // 2)
+    assert np.all(np.diff(st.astype(np.int64)) > 0)
+    if L <= 16:
+        allst = np.arange(2**L, dtype=np.uint32)
+        pc = np.zeros_like(allst)
+        for b in range(L):
+            pc += (allst >> b) & 1
+        assert np.array_equal(st, allst[pc == L // 2])
+
+
+def test_basis_dimension_L22_printed_in_paper(orc):
+    assert len(orc.basis(22)) == _gold("paper_values.json")["dim_L22_Sz0"]["value"]
+
+
+# ---------------------------------------------------------------- Hamiltonian -----------------
+@pytest.mark.parametrize("L,J", [(2, 1.0), (4, 1.0), (6, 0.7), (8, 1.0), (10, 1.3)])
+def test_csr_matches_kronecker_construction(orc, L, J):
+    rng = np.random.default_rng(L)
+    hi = rng.uniform(-2, 2, L)
+    Hfull = hamiltonian_full(L, hi, J)
+    idx = sector_indices(L, L // 2)
+    want = Hfull[np.ix_(idx, idx)]
+    got = orc.csr(L, hi, J).dense()
+    assert np.abs(got - want).max() < 1e-13
+
+
+@pytest.mark.parametrize("L", [4, 6, 8, 10, 12, 14, 16])
+def test_csr_nnz_closed_form(orc, L):
+    H = orc.csr(L, np.zeros(L))
+    assert H.rowptr[-1] == math.comb(L, L // 2) + 2 * L * math.comb(L - 2, L // 2 - 1)
+
+
+@pytest.mark.parametrize("L", [4, 8, 12, 14])
+def test_csr_structure(orc, L):
+    hi = orc.fields(L, 2.5, 7)
+    H = orc.csr(L, hi)
+    A = H.dense()
+    assert np.array_equal(A, A.T)
+    for i in range(H.n):
+        cols = H.col[H.rowptr[i]:H.rowptr[i + 1]]
+        assert np.all(np.diff(cols) > 0) and i in cols
+    off = A - np.diag(np.diag(A))
+    assert set(np.unique(off[off != 0])) == {0.5}
+
+
+@pytest.mark.parametrize("L", [4, 6, 8, 10, 12, 14, 16])
+def test_trace_is_field_independent_closed_form(orc, L):
+    # every S^z_i is traceless in the S^z = 0 sector; each bond contributes
+    # (#aligned - #antiparallel) / 4 = (C(L-2, L/2-2) + C(L-2, L/2) - 2 C(L-2, L/2-1)) / 4
+    c = math.comb
+    want = L / 4 * (c(L - 2, L // 2 - 2) + c(L - 2, L // 2) - 2 * c(L - 2, L // 2 - 1))
+    for h, seed in [(0.0, 0), (3.0, 1), (5.0, 9)]:
+        H = orc.csr(L, orc.fields(L, h, seed))
+        diag = np.array([H.val[H.rowptr[i]:H.rowptr[i + 1]][H.col[H.rowptr[i]:H.rowptr[i + 1]] == i][0]
+                         for i in range(H.n)])
+        assert abs(diag.sum() - want) < 1e-9 * max(1.0, abs(want))
+    if L == 12:
+        assert want == -252
+    if L == 14:
+        assert want == -924
+
+
+# ---------------------------------------------------------------- dense eigensolver ----------
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 17, 64])
+def test_syev_random_symmetric_vs_library(orc, n):
+    rng = np.random.default_rng(n)
+    A = rng.standard_normal((n, n))
+    A = A + A.T
+    w, V = orc.syev(A)
+    assert np.abs(w - np.linalg.eigvalsh(A)).max() < 1e-12 * max(1, np.abs(w).max())
+    assert np.abs(V.T @ V - np.eye(n)).max() < 1e-13
+    assert np.abs(A @ V - V * w).max() < 1e-12 * max(1, np.abs(w).max())
+
+
+def test_syev_special_matrices(orc):
+    for A in [np.zeros((6, 6)), np.diag([3.0, -1.0, 2.0, 2.0, 0.0]), np.ones((7, 7)),
+              np.diag(np.ones(9)) * 2 + np.diag(np.ones(8), 1) + np.diag(np.ones(8), -1)]:
+        w, V = orc.syev(A)
+        assert np.abs(w - np.linalg.eigvalsh(A)).max() < 1e-13 * max(1, np.abs(w).max())
+        assert np.abs(A @ V - V * w).max() < 1e-13 * max(1, np.abs(w).max())
+    # tridiagonal path alone, with the last eigenvector row
+    d, e = np.array([1.0, -2.0, 0.5, 3.0]), np.array([0.3, 1.0, -0.7])
+    T = np.diag(d) + np.diag(e, 1) + np.diag(e, -1)
+    w, zl = orc.stev(d, e)
+    wl, Vl = np.linalg.eigh(T)
+    assert np.abs(w - wl).max() < 1e-14 * 4
+    assert np.abs(np.abs(zl) - np.abs(Vl[-1])).max() < 1e-13
+
+
+@pytest.mark.parametrize("hs", [(0.3, -0.7), (0.0, 0.0), (2.0, 1.0), (-4.0, 3.5)])
+@pytest.mark.parametrize("J", [1.0, 0.4])
+def test_L2_closed_form(orc, hs, J):
+    # literal periodic bonds (0,1) and (1,0): H = [[-J/2 + d, J], [J, -J/2 - d]], d = (h0-h1)/2
+    w = orc.syev(orc.csr(2, np.array(hs), J).dense(), vectors=False)
+    d = (hs[0] - hs[1]) / 2
+    want = sorted([-J / 2 - math.sqrt(J * J + d * d), -J / 2 + math.sqrt(J * J + d * d)])
+    assert np.allclose(w, want, atol=1e-14)
+
+
+def test_L4_zero_field_spectrum(orc):
+    # H = S_A . S_B with A = {0, 2}, B = {1, 3}: {-2, -1, 1} from S_A = S_B = 1 and three zeros
+    w = orc.syev(orc.csr(4, np.zeros(4)).dense(), vectors=False)
+    assert np.allclose(w, [-2, -1, 0, 0, 0, 1], atol=1e-14)
+
+
+@pytest.mark.parametrize("L", [6, 8, 10])
+def test_dense_spectrum_vs_library(orc, L):
+    hi = orc.fields(L, 1.5, 3)
+    A = orc.csr(L, hi).dense()
+    w = orc.syev(A, vectors=False)
+    assert np.abs(w - np.linalg.eigvalsh(A)).max() < 1e-12
+    assert abs(w.sum() - np.trace(A)) < 1e-11
+
+
+def test_su2_multiplets_at_zero_field(orc):
+    L = 8
+    A = orc.csr(L, np.zeros(L)).dense()
+    w, V = orc.syev(A)
+    # <S^2> on each eigenvector of a non-degenerate level is S(S+1)
+    S2 = total_spin_sq(L)
+    idx = sector_indices(L, L // 2)
+    S2s = S2[np.ix_(idx, idx)]
+    gaps = np.diff(w)
+    for j in range(len(w)):
+        isolated = (j == 0 or gaps[j - 1] > 1e-8) and (j == len(w) - 1 or gaps[j] > 1e-8)
+        if not isolated:
+            continue
+        s2 = V[:, j] @ S2s @ V[:, j]
+        S = (-1 + math.sqrt(1 + 4 * s2)) / 2
+        assert abs(S - round(S)) < 1e-8
+    # spec(S^z = 1) is contained in spec(S^z = 0)
+    idx1 = sector_indices(L, L // 2 + 1)
+    w1 = np.linalg.eigvalsh(hamiltonian_full(L, np.zeros(L))[np.ix_(idx1, idx1)])
+    for x in w1:
+        assert np.min(np.abs(w - x)) < 1e-10
+
+
+def test_uniform_field_leaves_sector_spectrum(orc):
+    L = 10
+    w0 = orc.syev(orc.csr(L, np.zeros(L)).dense(), vectors=False)
+    w1 = orc.syev(orc.csr(L, np.full(L, 1.7)).dense(), vectors=False)
+    assert np.abs(w0 - w1).max() < 1e-12
+
+
+def test_zero_coupling_is_diagonal(orc):
+    L = 10
+    hi = orc.fields(L, 2.0, 11)
+    H = orc.csr(L, hi, J=0.0)
+    A = H.dense()
+    e = orc.nearest_dense(H, 0.5, 12)
+    assert np.abs(np.sort(np.diag(A)) - orc.syev(A, vectors=False)).max() < 1e-14
+    for j in range(12):
+        assert orc.s1p(e.evecs[:, j]) < 1e-12
+        assert orc.entanglement(L, e.evecs[:, j]) < 1e-12
+
+
+# ---------------------------------------------------------------- window selection ------------
+def test_nearest_window_selection(orc):
+    L, eps, nev = 10, 0.37, 15
+    H = orc.csr(L, orc.fields(L, 2.0, 5))
+    e = orc.nearest_dense(H, eps, nev)
+    w = np.linalg.eigvalsh(H.dense())
+    sigma = w[0] + eps * (w[-1] - w[0])
+    assert abs(e.sigma - sigma) < 1e-12 and abs(e.emin - w[0]) < 1e-12 and abs(e.emax - w[-1]) < 1e-12
+    order = np.lexsort((w, np.abs(w - sigma)))
+    assert np.abs(e.evals - np.sort(w[order[:nev]])).max() < 1e-12
+    assert e.resid.max() < 1e-12
+
+
+@pytest.mark.parametrize("L", [8, 10, 12])
+def test_extremal_lanczos_vs_dense(orc, L):
+    H = orc.csr(L, orc.fields(L, 3.0, 2))
+    w = orc.syev(H.dense(), vectors=False)
+    emin, emax = orc.extremal_bounds(H)
+    assert abs(emin - w[0]) < 1e-12 * abs(w).max() and abs(emax - w[-1]) < 1e-12 * abs(w).max()
+
+
+# ---------------------------------------------------------------- sparse path ----------------
+@pytest.mark.parametrize("L", [8, 10, 12])
+def test_ldlt_inertia_and_solve(orc, L):
+    H = orc.csr(L, orc.fields(L, 2.0, 4))
+    A = H.dense()
+    w = np.linalg.eigvalsh(A)
+    f = orc.LDLT(H)
+    for sigma in [w[0] - 1, 0.5 * (w[3] + w[4]), 0.5 * (w[H.n // 2] + w[H.n // 2 + 1]), w[-1] + 1]:
+        f.factor(sigma)
+        assert f.negative == int(np.sum(w < sigma))
+        b = np.random.default_rng(0).standard_normal(H.n)
+        x = f.solve(b)
+        assert np.linalg.norm((A - sigma * np.eye(H.n)) @ x - b) < 1e-9 * np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("L,h,eps", [(10, 1.0, 0.5), (12, 2.0, 0.1), (12, 4.0, 0.9)])
+def test_shift_invert_matches_dense(orc, L, h, eps):
+    job = orc.Job(L, h, 3, eps, 20)
+    d = orc.solve_job(job, "dense")
+    s = orc.solve_job(job, "si")
+    hn = max(abs(d.emin), abs(d.emax))
+    assert abs(d.sigma - s.sigma) < 1e-12 * hn
+    assert np.abs(d.evals - s.evals).max() < 1e-12 * hn
+    assert s.resid.max() < 1e-12 * hn
+    assert np.abs(d.r - s.r).max() < 1e-9
+
+
+# ---------------------------------------------------------------- observables ----------------
+def test_gap_ratio_hand_example(orc):
+    r, rm = orc.gap_ratio(np.array([0.0, 1.0, 3.0, 4.0, 4.5]))
+    assert np.allclose(r, [0.5, 0.5, 0.5]) and abs(rm - 0.5) < 1e-15
+    r, rm = orc.gap_ratio(np.array([1.0, 1.0, 1.0, 2.0]))
+    assert math.isnan(r[0]) and r[1] == 0.0 and rm == 0.0
+
+
+def test_gap_ratio_goe_and_poisson_limits(orc):
+    """Characterization section (i): r_GOE = 0.5307(1), r_Poisson = 2 ln 2 - 1.  Weak disorder
+    sits near GOE and strong disorder near Poisson (L = 12, central 300 levels, 8 samples)."""
+    g = _gold("paper_values.json")
+    means = {}
+    for h in (1.0, 6.0):
+        rs = []
+        for seed in range(8):
+            H = orc.csr(12, orc.fields(12, h, seed))
+            w = orc.syev(H.dense(), vectors=False)
+            r, _ = orc.gap_ratio(w[312:612])
+            rs.append(r[~np.isnan(r)])
+        rs = np.concatenate(rs)
+        means[h] = (rs.mean(), rs.std() / math.sqrt(len(rs)))
+    goe, poi = g["r_goe"]["value"], g["r_poisson"]["value"]
+    assert abs(means[1.0][0] - goe) < 4 * means[1.0][1] + 0.01
+    assert abs(means[6.0][0] - poi) < 4 * means[6.0][1] + 0.01
+
+
+def test_s1p_limits(orc):
+    n = 924
+    y = np.zeros(n)
+    y[17] = -2.0
+    assert orc.s1p(y) == 0.0
+    assert abs(orc.s1p(np.ones(n)) - math.log(n)) < 1e-12
+    # a Gaussian random vector: ln n + psi(1/2) + ln 2 = ln n - 0.7296 (large n)
+    z = np.random.default_rng(1).standard_normal(200000)
+    assert abs(orc.s1p(z) - (math.log(200000) - 0.7296)) < 0.01
+
+
+def test_entanglement_L2_formula(orc):
+    a, b = 0.6, -0.8
+    want = -(a * a) * math.log(a * a) - (b * b) * math.log(b * b)
+    assert abs(orc.entanglement(2, np.array([a, b])) - want) < 1e-14
+
+
+@pytest.mark.parametrize("L", [4, 6, 8, 10])
+def test_entanglement_vs_library_svd(orc, L):
+    idx = sector_indices(L, L // 2)
+    rng = np.random.default_rng(L)
+    for _ in range(3):
+        y = rng.standard_normal(len(idx))
+        full = np.zeros(2**L)
+        full[idx] = y
+        assert abs(orc.entanglement(L, y) - schmidt_entropy(L, full)) < 1e-12
+        assert 0 <= orc.entanglement(L, y) <= (L // 2) * math.log(2) + 1e-12
+
+
+def _singlet_product(L, pairs):
+    """Full-space product of singlets (up down - down up)/sqrt2 on the given site pairs."""
+    full = np.zeros(2**L)
+    for s in range(2**L):
+        amp = 1.0
+        for (i, j) in pairs:
+            bi, bj = (s >> i) & 1, (s >> j) & 1
+            if bi == bj:
+                amp = 0.0
+                break
+            amp *= (1 if bi == 1 else -1) / math.sqrt(2)
+        full[s] = amp
+    return full
+
+
+@pytest.mark.parametrize("pairs,nbonds", [([(0, 1), (2, 3)], 0), ([(0, 2), (1, 3)], 2), ([(0, 3), (1, 2)], 2),
+                                          ([(0, 1), (2, 3), (4, 5)], 1), ([(0, 4), (1, 5), (2, 3)], 3),
+                                          ([(0, 5), (1, 2), (3, 4)], 1)])
+def test_entanglement_singlet_products(orc, pairs, nbonds):
+    L = 2 * len(pairs)
+    full = _singlet_product(L, pairs)
+    y = full[sector_indices(L, L // 2)]
+    assert abs(np.linalg.norm(y) - 1) < 1e-14
+    crossing = sum(1 for (i, j) in pairs if (i < L // 2) != (j < L // 2))
+    assert crossing == nbonds
+    assert abs(orc.entanglement(L, y) - nbonds * math.log(2)) < 1e-13
+
+
+def test_entanglement_product_state_zero(orc):
+    L = 8
+    st = orc.basis(L)
+    y = np.zeros(len(st))
+    y[5] = 1.0
+    assert orc.entanglement(L, y, st) == 0.0
