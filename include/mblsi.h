@@ -1,0 +1,176 @@
+/*
+ * mblsi.h -- C ABI of the GB300 (sm_103a) shift-invert exact-diagonalization library for the
+ * random-field Heisenberg chain of Luitz, Laflorencie and Alet (arXiv:1411.0660).
+ *
+ * Model (Eq. 1, field written as +h_i, periodic chain, J = 1 unless given):
+ *     H = J sum_{i=0}^{L-1} S_i . S_{(i+1) mod L} + sum_i h_i S^z_i ,   h_i uniform on [-h, h]
+ * restricted to the S^z_tot = 0 sector of even L (numerical-method section).  Site i is bit i
+ * of a uint32 state, a set bit is spin up; the basis is every state with L/2 set bits in
+ * ascending integer order (= the combinatorial number system, rank(s) = sum_t C(p_t, t+1) over
+ * the set-bit positions p_0 < p_1 < ...).
+ *
+ * Energy target (numerical-method section, read with E_min at eps = 0):
+ *     sigma = E_min + eps (E_max - E_min),   ||H|| := max(|E_min|, |E_max|)
+ * The method returns the nev eigenpairs nearest sigma through the shift-invert transformation
+ * (H - sigma)^-1 (numerical-method section).  Ties in |lambda - sigma| take the lower lambda.
+ *
+ * Conventions for every entry point
+ *   - Return value: MBL_OK or one of the MBL_ERR_* codes; mbl_last_error() gives detail.
+ *   - Handles (mbl_ctx, mbl_sector, mbl_factorization) are opaque, owned by the library and released
+ *     with the matching *_destroy.  A context is used by one host thread at a time; separate
+ *     contexts may run on separate threads.
+ *   - Host arrays are caller owned and must hold the stated number of elements.  Entry points
+ *     whose name ends in _dev take device pointers (caller owned, on the context's device)
+ *     and a cudaStream_t passed as void* (NULL = the context's own stream); they return once
+ *     the work is enqueued unless stated otherwise.
+ *   - Vectors of the sector are indexed by basis rank.  Blocks of eigenvectors are n x nev
+ *     column-major (column j is eigenvector j, unit 2-norm, arbitrary sign).
+ */
+#ifndef MBLSI_H
+#define MBLSI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MBL_OK 0
+#define MBL_ERR_INVALID 1       /* bad argument: L odd, L < 2, L > 22, nev outside [1, n] ... */
+#define MBL_ERR_OOM 2           /* the HBM budget of the context cannot hold the request */
+#define MBL_ERR_SINGULAR 3      /* factorization broke down even with FP64 fronts */
+#define MBL_ERR_NOT_CONVERGED 4 /* eigenpairs below tolerance not reached; partial results out */
+#define MBL_ERR_TIMEOUT 5       /* a bounded device wait expired */
+#define MBL_ERR_CUDA 6          /* a CUDA runtime error (text in mbl_last_error) */
+#define MBL_PENDING 7           /* serving: the request is not finished yet */
+
+/* Arithmetic of the frontal matrices (dense LDL^T of the multifrontal factorization). */
+#define MBL_PREC_FP64 0   /* FP64 fronts and FP64 triangular solves */
+#define MBL_PREC_FP32 1   /* FP32 fronts and solves, FP64 iterative refinement */
+
+typedef struct mbl_ctx mbl_ctx;
+typedef struct mbl_sector mbl_sector;
+typedef struct mbl_factorization mbl_factorization;
+
+/* Options of factor/solve_near.  mbl_opts_default fills the defaults given in brackets. */
+typedef struct mbl_opts {
+    int precision;        /* MBL_PREC_* of the fronts                               [FP32] */
+    int block;            /* block width p of the shift-invert Lanczos, 1..32       [8]    */
+    int ncv;              /* Krylov basis size before a restart, 0 = automatic      [0]    */
+    int max_restarts;     /* thick restarts before MBL_ERR_NOT_CONVERGED            [60]   */
+    double tol;           /* accept when ||H y - theta y|| <= tol ||H||              [1e-10]*/
+    double target_tol;    /* converge towards this (the FP64 floor)                  [1e-13]*/
+    double refine_tol;    /* refinement stop: ||b - A x|| <= refine_tol (|A||x| + |b|)[1e-15]*/
+    int max_refine;       /* refinement steps per application                       [20]   */
+    uint64_t start_seed;  /* seed of the random start block                         [12345]*/
+} mbl_opts;
+
+typedef struct mbl_factor_stats {
+    int64_t n;              /* sector dimension */
+    int64_t nnz_l;          /* stored entries of the unit lower factor (strictly lower) */
+    int64_t n_supernodes;   /* fronts of the assembly tree */
+    int64_t max_front;      /* largest front order */
+    int64_t tree_levels;    /* levels of the batched schedule */
+    int64_t perturbed;      /* pivots replaced by +-tiny (static pivoting) */
+    int64_t negative;       /* negative pivots = eigenvalues of H below sigma (if none perturbed) */
+    double flops;           /* algorithmic factorization flops (sum over fronts) */
+    double factor_bytes;    /* bytes of the stored factor */
+    double front_bytes;     /* bytes of the frontal arena (factor + contribution blocks) */
+    double ms_factor;       /* device time of the numeric factorization */
+} mbl_factor_stats;
+
+typedef struct mbl_solve_stats {
+    int restarts;           /* thick restarts done */
+    int op_applies;         /* block applications of (H - sigma)^-1 */
+    int solves;             /* block triangular solves (applications x refinement steps) */
+    int fp64_fallback;      /* 1 if refinement stalled and FP64 fronts were used */
+    int krylov_dim;         /* final basis size */
+    double max_resid;       /* max ||H y - theta y|| / ||H|| of the returned pairs */
+    double ms_total;        /* wall time of solve_near */
+    double ms_factor;       /* of which numeric factorization */
+} mbl_solve_stats;
+
+void mbl_opts_default(mbl_opts *opts);
+const char *mbl_version(void);
+const char *mbl_last_error(mbl_ctx *ctx);
+const char *mbl_status_string(int status);
+
+/* Context on CUDA device `device` with a memory budget (0 = no limit) used for admission. */
+int mbl_ctx_create(int device, size_t hbm_budget_bytes, mbl_ctx **out);
+void mbl_ctx_destroy(mbl_ctx *ctx);
+int mbl_ctx_synchronize(mbl_ctx *ctx);
+
+/* Sector of Eq. 1 for (L, h, seed): h_i = h (2 u_i - 1), u_i = (z_i >> 11) 2^-53 with z_i the
+ * i-th output of SplitMix64 started at `seed` (the paper names no generator).  Builds the basis
+ * (combinadic enumeration) and the CSR Hamiltonian on the device, bit-exactly:
+ *   row k: columns ascending, diagonal always stored, value
+ *          0.25 J (n_aligned - n_antiparallel) then + (+-0.5) h_i for i = 0..L-1 in order,
+ *          one off-diagonal J/2 per antiparallel bond (i, i+1 mod L), summed when two bonds reach
+ *          the same state (L = 2 only).
+ * L must be even, 2 <= L <= 22, h >= 0. */
+int mbl_build_sector(mbl_ctx *ctx, int L, double h, uint64_t seed, mbl_sector **out);
+/* Same with explicit fields h_i[L] (host) and coupling J. */
+int mbl_build_sector_fields(mbl_ctx *ctx, int L, const double *h_i, double J, mbl_sector **out);
+void mbl_sector_destroy(mbl_sector *sec);
+
+int mbl_sector_info(const mbl_sector *sec, int64_t *dim, int64_t *nnz);
+/* Device-to-host copies for inspection: states[dim]; rowptr[dim+1], col[nnz], val[nnz]; h_i[L]. */
+int mbl_sector_copy_basis(const mbl_sector *sec, uint32_t *states);
+int mbl_sector_copy_csr(const mbl_sector *sec, int64_t *rowptr, int32_t *col, double *val);
+int mbl_sector_copy_fields(const mbl_sector *sec, double *h_i);
+/* Combinadic rank of `count` states (host arrays) computed on the device; -1 if a state is not
+ * in the sector. */
+int mbl_sector_rank(const mbl_sector *sec, const uint32_t *states, int64_t count, int64_t *ranks);
+/* y = (H - shift) x for nrhs vectors, host arrays n x nrhs column-major (FP64 CSR SpMV). */
+int mbl_spmv(mbl_sector *sec, double shift, const double *x, double *y, int nrhs);
+
+/* E_min and E_max of the sector (numerical-method section): block Lanczos on H with full
+ * reorthogonalization, converged to 1e-13 ||H||.  Cached on the sector. */
+int mbl_extremal_bounds(mbl_sector *sec, double *e_min, double *e_max);
+
+/* Numeric factorization P (H - sigma I) P^T = L D L^T (supernodal multifrontal; ordering and
+ * symbolic analysis cached per L in the context).  Diagonal pivoting inside each panel of the
+ * fully-summed block; a pivot below tiny = 1e-7 ||H|| (FP32) or 1e-12 ||H|| (FP64) is replaced by
+ * +-tiny and counted.  opts may be NULL (defaults). */
+int mbl_factor(mbl_sector *sec, double sigma, const mbl_opts *opts, mbl_factorization **out);
+int mbl_factor_stats_get(const mbl_factorization *f, mbl_factor_stats *stats);
+/* x = (H - sigma)^-1 b for nrhs right-hand sides (host, n x nrhs column-major), with FP64
+ * iterative refinement when `refine` is nonzero. */
+int mbl_factor_solve(mbl_factorization *f, const double *b, double *x, int nrhs, int refine);
+void mbl_factor_destroy(mbl_factorization *f);
+
+/* The nev eigenpairs of the sector nearest sigma = E_min + eps (E_max - E_min): block
+ * shift-invert Lanczos with full reorthogonalization and thick restarts on (H - sigma)^-1,
+ * every application refined in FP64 against the CSR, then Rayleigh-Ritz on H.
+ * Outputs (host): evals[nev] ascending, evecs[n*nev] column-major, resid[nev] =
+ * ||H y - theta y||; *nconv = pairs with resid <= tol ||H||; *sigma_used.  stats may be NULL.
+ * Returns MBL_ERR_NOT_CONVERGED (with the partial results written) if nconv < nev. */
+int mbl_solve_near(mbl_sector *sec, double eps, int nev, const mbl_opts *opts, double *evals,
+                   double *evecs, double *resid, int *nconv, double *sigma_used,
+                   mbl_solve_stats *stats);
+/* Same with device outputs d_evals[nev], d_evecs[n*nev], d_resid[nev]; returns after the
+ * results are written (the host needs them to decide convergence). */
+int mbl_solve_near_dev(mbl_sector *sec, double eps, int nev, const mbl_opts *opts,
+                       double *d_evals, double *d_evecs, double *d_resid, int *nconv,
+                       double *sigma_used, mbl_solve_stats *stats, void *stream);
+
+/* Observables of nev eigenpairs of an L-site sector (characterization section):
+ *   r[nev-2]   gap ratios r_k = min(d_k, d_{k+1}) / max(d_k, d_{k+1}), d_k = E_k - E_{k-1},
+ *              of the ascending evals (NaN where both gaps are zero, excluded from r_mean);
+ *   s1p[nev]   participation entropy -sum_i p_i ln p_i, p_i = y_i^2 / ||y||^2;
+ *   se[nev]    half-chain entanglement entropy -Tr rho_A ln rho_A, A = sites 0..L/2-1,
+ *              from the eigenvalues of the Gram matrices M M^T of the reshaped vector
+ *              (Schmidt weights below 1e-15 count as zero).
+ * Host arrays; evecs n x nev column-major. */
+int mbl_observables(mbl_ctx *ctx, int L, int nev, const double *evals, const double *evecs,
+                    double *r, double *r_mean, double *s1p, double *se);
+/* Same on device arrays, enqueued on `stream` (NULL = context stream). */
+int mbl_observables_dev(mbl_ctx *ctx, int L, int nev, const double *d_evals,
+                        const double *d_evecs, double *d_r, double *d_r_mean, double *d_s1p,
+                        double *d_se, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MBLSI_H */

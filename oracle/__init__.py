@@ -21,6 +21,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import platform
 import subprocess
 from dataclasses import dataclass
 
@@ -39,6 +40,9 @@ _u32p = np.ctypeslib.ndpointer(dtype=np.uint32, flags="C_CONTIGUOUS")
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (no FMA contraction; portable flags only)."""
     os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+    stamp = os.path.join(os.path.dirname(_LIB), "ARCH")
+    if not (os.path.exists(stamp) and open(stamp).read().strip() == platform.machine()):
+        force = True
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(
         os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "mbl_oracle.h"))
     ):
@@ -47,6 +51,8 @@ def build(force: bool = False) -> str:
             ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-o", tmp, _SRC, "-lm"]
         )
         os.replace(tmp, _LIB)
+        with open(stamp, "w") as f:
+            f.write(platform.machine())
     return _LIB
 
 

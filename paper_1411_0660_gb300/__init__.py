@@ -1,0 +1,238 @@
+"""GB300 (sm_103a) shift-invert exact diagonalization of the random-field Heisenberg chain.
+
+Python face of libmblsi (include/mblsi.h): every step runs in the library's CUDA kernels; this
+module only marshals arguments.  Method: Luitz, Laflorencie, Alet, arXiv:1411.0660 (Eq. 1, the
+numerical-method section, and the observables of the characterization section).
+
+    ctx = Context(0)
+    sec = build_sector(ctx, L=16, h=3.0, seed=7)
+    emin, emax = extremal_bounds(sec)
+    res = solve_near(sec, eps=0.5, nev=50)
+    r, r_mean, s1p, se = observables(ctx, 16, res.evals, res.evecs)
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _capi
+from ._capi import MBL_PREC_FP32, MBL_PREC_FP64, FactorStats, Opts, SolveStats
+
+__all__ = ["Context", "Sector", "Factorization", "MblError", "build_sector", "build_sector_fields",
+           "extremal_bounds", "factor", "solve_near", "solve_near_dev", "observables", "observables_dev",
+           "default_opts", "MBL_PREC_FP32", "MBL_PREC_FP64"]
+
+
+class MblError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+def _lib():
+    return _capi.load()
+
+
+def _check(rc: int, ctx_handle=None):
+    if rc != _capi.MBL_OK:
+        msg = _lib().mbl_last_error(ctx_handle)
+        raise MblError(rc, msg.decode() if msg else "")
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def default_opts(**kw) -> Opts:
+    o = Opts()
+    _lib().mbl_opts_default(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+class Context:
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0):
+        h = ctypes.c_void_p()
+        _check(_lib().mbl_ctx_create(device, hbm_budget_bytes, ctypes.byref(h)))
+        self.handle = h
+
+    def synchronize(self):
+        _check(_lib().mbl_ctx_synchronize(self.handle), self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _lib().mbl_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Sector:
+    def __init__(self, ctx: Context, handle, L: int):
+        self.ctx, self.handle, self.L = ctx, handle, L
+        n, nnz = ctypes.c_int64(), ctypes.c_int64()
+        _check(_lib().mbl_sector_info(handle, ctypes.byref(n), ctypes.byref(nnz)), ctx.handle)
+        self.dim, self.nnz = n.value, nnz.value
+
+    def basis(self) -> np.ndarray:
+        out = np.zeros(self.dim, dtype=np.uint32)
+        _check(_lib().mbl_sector_copy_basis(self.handle, _ptr(out)), self.ctx.handle)
+        return out
+
+    def csr(self):
+        rp = np.zeros(self.dim + 1, dtype=np.int64)
+        col = np.zeros(self.nnz, dtype=np.int32)
+        val = np.zeros(self.nnz, dtype=np.float64)
+        _check(_lib().mbl_sector_copy_csr(self.handle, _ptr(rp), _ptr(col), _ptr(val)), self.ctx.handle)
+        return rp, col, val
+
+    def fields(self) -> np.ndarray:
+        out = np.zeros(self.L, dtype=np.float64)
+        _check(_lib().mbl_sector_copy_fields(self.handle, _ptr(out)), self.ctx.handle)
+        return out
+
+    def rank(self, states) -> np.ndarray:
+        st = np.ascontiguousarray(states, dtype=np.uint32)
+        out = np.zeros(len(st), dtype=np.int64)
+        _check(_lib().mbl_sector_rank(self.handle, _ptr(st), len(st), _ptr(out)), self.ctx.handle)
+        return out
+
+    def spmv(self, x: np.ndarray, shift: float = 0.0) -> np.ndarray:
+        X = np.asfortranarray(x, dtype=np.float64)
+        if X.ndim == 1:
+            X = X[:, None]
+        Y = np.zeros_like(X, order="F")
+        _check(_lib().mbl_spmv(self.handle, float(shift), _ptr(X), _ptr(Y), X.shape[1]), self.ctx.handle)
+        return Y[:, 0] if np.ndim(x) == 1 else Y
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _lib().mbl_sector_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def build_sector(ctx: Context, L: int, h: float, seed: int) -> Sector:
+    h_ = ctypes.c_void_p()
+    _check(_lib().mbl_build_sector(ctx.handle, L, float(h), ctypes.c_uint64(seed & (2**64 - 1)), ctypes.byref(h_)),
+           ctx.handle)
+    return Sector(ctx, h_, L)
+
+
+def build_sector_fields(ctx: Context, L: int, h_i, J: float = 1.0) -> Sector:
+    hi = np.ascontiguousarray(h_i, dtype=np.float64)
+    h_ = ctypes.c_void_p()
+    _check(_lib().mbl_build_sector_fields(ctx.handle, L, _ptr(hi), float(J), ctypes.byref(h_)), ctx.handle)
+    return Sector(ctx, h_, L)
+
+
+def extremal_bounds(sec: Sector):
+    lo, hi = ctypes.c_double(), ctypes.c_double()
+    _check(_lib().mbl_extremal_bounds(sec.handle, ctypes.byref(lo), ctypes.byref(hi)), sec.ctx.handle)
+    return lo.value, hi.value
+
+
+class Factorization:
+    def __init__(self, sec: Sector, handle):
+        self.sec, self.handle = sec, handle
+
+    def stats(self) -> dict:
+        s = FactorStats()
+        _check(_lib().mbl_factor_stats_get(self.handle, ctypes.byref(s)), self.sec.ctx.handle)
+        return {f: getattr(s, f) for f, _ in FactorStats._fields_}
+
+    def solve(self, b: np.ndarray, refine: bool = True) -> np.ndarray:
+        B = np.asfortranarray(b, dtype=np.float64)
+        if B.ndim == 1:
+            B = B[:, None]
+        X = np.zeros_like(B, order="F")
+        _check(_lib().mbl_factor_solve(self.handle, _ptr(B), _ptr(X), B.shape[1], 1 if refine else 0),
+               self.sec.ctx.handle)
+        return X[:, 0] if np.ndim(b) == 1 else X
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _lib().mbl_factor_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def factor(sec: Sector, sigma: float, opts: Opts | None = None, **kw) -> Factorization:
+    o = opts if opts is not None else default_opts(**kw)
+    h = ctypes.c_void_p()
+    _check(_lib().mbl_factor(sec.handle, float(sigma), ctypes.byref(o), ctypes.byref(h)), sec.ctx.handle)
+    return Factorization(sec, h)
+
+
+@dataclass
+class NearResult:
+    evals: np.ndarray
+    evecs: np.ndarray  # dim x nev (column j = eigenvector j)
+    resid: np.ndarray
+    nconv: int
+    sigma: float
+    stats: dict
+
+
+def solve_near(sec: Sector, eps: float, nev: int, opts: Opts | None = None, allow_partial: bool = False,
+               **kw) -> NearResult:
+    o = opts if opts is not None else default_opts(**kw)
+    ev = np.zeros(nev)
+    vec = np.zeros((sec.dim, nev), order="F")
+    res = np.zeros(nev)
+    nc, sg, st = ctypes.c_int(), ctypes.c_double(), SolveStats()
+    rc = _lib().mbl_solve_near(sec.handle, float(eps), nev, ctypes.byref(o), _ptr(ev), _ptr(vec), _ptr(res),
+                               ctypes.byref(nc), ctypes.byref(sg), ctypes.byref(st))
+    if not (allow_partial and rc == _capi.MBL_ERR_NOT_CONVERGED):
+        _check(rc, sec.ctx.handle)
+    return NearResult(ev, vec, res, nc.value, sg.value, {f: getattr(st, f) for f, _ in SolveStats._fields_})
+
+
+def solve_near_dev(sec: Sector, eps: float, nev: int, d_evals, d_evecs, d_resid, stream=None,
+                   opts: Opts | None = None, **kw):
+    """Device variant: d_* are torch CUDA tensors (float64) of sizes nev, dim*nev, nev."""
+    o = opts if opts is not None else default_opts(**kw)
+    nc, sg, st = ctypes.c_int(), ctypes.c_double(), SolveStats()
+    s = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
+    _check(_lib().mbl_solve_near_dev(sec.handle, float(eps), nev, ctypes.byref(o), ctypes.c_void_p(d_evals.data_ptr()),
+                                     ctypes.c_void_p(d_evecs.data_ptr()), ctypes.c_void_p(d_resid.data_ptr()),
+                                     ctypes.byref(nc), ctypes.byref(sg), ctypes.byref(st), s), sec.ctx.handle)
+    return nc.value, sg.value, {f: getattr(st, f) for f, _ in SolveStats._fields_}
+
+
+def observables(ctx: Context, L: int, evals: np.ndarray, evecs: np.ndarray):
+    ev = np.ascontiguousarray(evals, dtype=np.float64)
+    V = np.asfortranarray(evecs, dtype=np.float64)
+    nev = len(ev)
+    r = np.zeros(max(nev - 2, 1))
+    rm = np.zeros(1)
+    s1p = np.zeros(nev)
+    se = np.zeros(nev)
+    _check(_lib().mbl_observables(ctx.handle, L, nev, _ptr(ev), _ptr(V), _ptr(r), _ptr(rm), _ptr(s1p), _ptr(se)),
+           ctx.handle)
+    return r[: max(nev - 2, 0)], float(rm[0]), s1p, se
+
+
+def observables_dev(ctx: Context, L: int, nev: int, d_evals, d_evecs, d_r, d_rmean, d_s1p, d_se, stream=None):
+    s = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
+    _check(_lib().mbl_observables_dev(ctx.handle, L, nev, ctypes.c_void_p(d_evals.data_ptr()),
+                                      ctypes.c_void_p(d_evecs.data_ptr()), ctypes.c_void_p(d_r.data_ptr()),
+                                      ctypes.c_void_p(d_rmean.data_ptr()), ctypes.c_void_p(d_s1p.data_ptr()),
+                                      ctypes.c_void_p(d_se.data_ptr()), s), ctx.handle)

@@ -1,0 +1,98 @@
+"""ctypes declarations of libmblsi (include/mblsi.h).  Argument marshalling only."""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+c_int, c_int64, c_double, c_void_p, c_size_t, c_uint64 = (
+    ctypes.c_int, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_uint64)
+P = ctypes.POINTER
+
+MBL_OK = 0
+MBL_ERR_INVALID = 1
+MBL_ERR_OOM = 2
+MBL_ERR_SINGULAR = 3
+MBL_ERR_NOT_CONVERGED = 4
+MBL_ERR_TIMEOUT = 5
+MBL_ERR_CUDA = 6
+MBL_PENDING = 7
+MBL_PREC_FP64 = 0
+MBL_PREC_FP32 = 1
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("precision", c_int), ("block", c_int), ("ncv", c_int), ("max_restarts", c_int),
+                ("tol", c_double), ("target_tol", c_double), ("refine_tol", c_double), ("max_refine", c_int),
+                ("start_seed", c_uint64)]
+
+
+class FactorStats(ctypes.Structure):
+    _fields_ = [("n", c_int64), ("nnz_l", c_int64), ("n_supernodes", c_int64), ("max_front", c_int64),
+                ("tree_levels", c_int64), ("perturbed", c_int64), ("negative", c_int64), ("flops", c_double),
+                ("factor_bytes", c_double), ("front_bytes", c_double), ("ms_factor", c_double)]
+
+
+class SolveStats(ctypes.Structure):
+    _fields_ = [("restarts", c_int), ("op_applies", c_int), ("solves", c_int), ("fp64_fallback", c_int),
+                ("krylov_dim", c_int), ("max_resid", c_double), ("ms_total", c_double), ("ms_factor", c_double)]
+
+
+# (name, restype, argtypes); every entry point of include/mblsi.h
+SIGNATURES = [
+    ("mbl_opts_default", None, [P(Opts)]),
+    ("mbl_version", ctypes.c_char_p, []),
+    ("mbl_last_error", ctypes.c_char_p, [c_void_p]),
+    ("mbl_status_string", ctypes.c_char_p, [c_int]),
+    ("mbl_ctx_create", c_int, [c_int, c_size_t, P(c_void_p)]),
+    ("mbl_ctx_destroy", None, [c_void_p]),
+    ("mbl_ctx_synchronize", c_int, [c_void_p]),
+    ("mbl_build_sector", c_int, [c_void_p, c_int, c_double, c_uint64, P(c_void_p)]),
+    ("mbl_build_sector_fields", c_int, [c_void_p, c_int, c_void_p, c_double, P(c_void_p)]),
+    ("mbl_sector_destroy", None, [c_void_p]),
+    ("mbl_sector_info", c_int, [c_void_p, P(c_int64), P(c_int64)]),
+    ("mbl_sector_copy_basis", c_int, [c_void_p, c_void_p]),
+    ("mbl_sector_copy_csr", c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    ("mbl_sector_copy_fields", c_int, [c_void_p, c_void_p]),
+    ("mbl_sector_rank", c_int, [c_void_p, c_void_p, c_int64, c_void_p]),
+    ("mbl_spmv", c_int, [c_void_p, c_double, c_void_p, c_void_p, c_int]),
+    ("mbl_extremal_bounds", c_int, [c_void_p, P(c_double), P(c_double)]),
+    ("mbl_factor", c_int, [c_void_p, c_double, P(Opts), P(c_void_p)]),
+    ("mbl_factor_stats_get", c_int, [c_void_p, P(FactorStats)]),
+    ("mbl_factor_solve", c_int, [c_void_p, c_void_p, c_void_p, c_int, c_int]),
+    ("mbl_factor_destroy", None, [c_void_p]),
+    ("mbl_solve_near", c_int, [c_void_p, c_double, c_int, P(Opts), c_void_p, c_void_p, c_void_p, P(c_int),
+                               P(c_double), P(SolveStats)]),
+    ("mbl_solve_near_dev", c_int, [c_void_p, c_double, c_int, P(Opts), c_void_p, c_void_p, c_void_p, P(c_int),
+                                   P(c_double), P(SolveStats), c_void_p]),
+    ("mbl_observables", c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                c_void_p]),
+    ("mbl_observables_dev", c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                    c_void_p, c_void_p]),
+]
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load the CUDA library.  There is no CPU fallback: a missing or unbuildable library raises."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = lib_path()
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise ImportError(f"libmblsi.so not built ({path}); run paper_1411_0660_gb300.build.build()")
+        _build.build()
+    L = ctypes.CDLL(path)
+    for name, res, args in SIGNATURES:
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L

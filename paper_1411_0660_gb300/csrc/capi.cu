@@ -1,0 +1,473 @@
+// capi.cu -- the extern "C" boundary of libmblsi (see include/mblsi.h for the contract).
+#include <chrono>
+#include <cmath>
+#include <cstring>
+
+#include "krylov.h"
+#include "observables.h"
+
+namespace mbl {
+
+DevMem &DevMem::operator=(DevMem &&o) noexcept {
+    if (this != &o) {
+        release();
+        p = o.p;
+        bytes = o.bytes;
+        ctx = o.ctx;
+        o.p = nullptr;
+        o.bytes = 0;
+        o.ctx = nullptr;
+    }
+    return *this;
+}
+
+void DevMem::alloc(Ctx *c, size_t nbytes) {
+    release();
+    if (nbytes == 0) nbytes = 16;
+    if (c->budget && c->in_use + nbytes > c->budget)
+        fail(MBL_ERR_OOM, "allocation of " + std::to_string(nbytes) + " bytes exceeds the context budget");
+    cudaError_t e = cudaMalloc(&p, nbytes);
+    if (e == cudaErrorMemoryAllocation) {
+        (void)cudaGetLastError();
+        p = nullptr;
+        fail(MBL_ERR_OOM, "cudaMalloc of " + std::to_string(nbytes) + " bytes failed");
+    }
+    MBL_CUDA(e);
+    bytes = nbytes;
+    ctx = c;
+    c->in_use += nbytes;
+    if (c->in_use > c->peak) c->peak = c->in_use;
+}
+
+void DevMem::release() {
+    if (p) {
+        cudaFree(p);
+        if (ctx) ctx->in_use -= bytes;
+    }
+    p = nullptr;
+    bytes = 0;
+}
+
+std::shared_ptr<Plan> get_plan(mbl_sector *sec) {
+    Ctx *ctx = sec->ctx;
+    auto it = ctx->plans.find(sec->L);
+    if (it != ctx->plans.end()) return it->second;
+    int64_t n = sec->n;
+    std::vector<uint32_t> st(n);
+    std::vector<int64_t> rp(n + 1);
+    std::vector<int32_t> col(sec->nnz);
+    MBL_CUDA(cudaMemcpy(st.data(), sec->states.data(), n * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+    MBL_CUDA(cudaMemcpy(rp.data(), sec->rowptr.data(), (n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost));
+    MBL_CUDA(cudaMemcpy(col.data(), sec->col.data(), sec->nnz * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    auto P = build_plan(sec->L, st, rp, col);
+    upload_plan(ctx, *P);
+    ctx->plans[sec->L] = P;
+    return P;
+}
+
+std::unique_ptr<Factorization> make_factorization(mbl_sector *sec, double sigma, int prec, double hnorm) {
+    if (prec != MBL_PREC_FP64 && prec != MBL_PREC_FP32) fail(MBL_ERR_INVALID, "unknown precision");
+    auto F = std::make_unique<Factorization>();
+    F->ctx = sec->ctx;
+    F->sec = sec;
+    F->plan = get_plan(sec);
+    F->sigma = sigma;
+    F->prec = prec;
+    F->tiny = (prec == MBL_PREC_FP64 ? 1e-12 : 1e-7) * hnorm;
+    F->allocate();
+    cudaStream_t st = sec->ctx->stream;
+    cudaEvent_t e0, e1;
+    MBL_CUDA(cudaEventCreate(&e0));
+    MBL_CUDA(cudaEventCreate(&e1));
+    MBL_CUDA(cudaEventRecord(e0, st));
+    numeric_factor(*F, st);
+    MBL_CUDA(cudaEventRecord(e1, st));
+    MBL_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    MBL_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    F->ms_factor = ms;
+    unsigned long long cnt[2];
+    MBL_CUDA(cudaMemcpy(cnt, F->counters.data(), sizeof(cnt), cudaMemcpyDeviceToHost));
+    F->perturbed = (int64_t)cnt[0];
+    F->negative = (int64_t)cnt[1];
+    F->release_scratch();
+    return F;
+}
+
+}  // namespace mbl
+
+using namespace mbl;
+
+static thread_local std::string g_last_error;
+
+static int report(Ctx *ctx, int code, const std::string &msg) {
+    g_last_error = msg;
+    if (ctx) ctx->last_error = msg;
+    return code;
+}
+
+#define API_TRY try {
+#define API_CATCH(CTX)                                                               \
+    }                                                                                \
+    catch (const mbl::Error &e) {                                                    \
+        return report((CTX), e.code, e.msg);                                         \
+    }                                                                                \
+    catch (const std::bad_alloc &) {                                                 \
+        return report((CTX), MBL_ERR_OOM, "host allocation failed");                 \
+    }                                                                                \
+    catch (const std::exception &e) {                                                \
+        return report((CTX), MBL_ERR_INVALID, e.what());                             \
+    }                                                                                \
+    return MBL_OK;
+
+extern "C" {
+
+void mbl_opts_default(mbl_opts *o) {
+    if (!o) return;
+    o->precision = MBL_PREC_FP32;
+    o->block = 8;
+    o->ncv = 0;
+    o->max_restarts = 60;
+    o->tol = 1e-10;
+    o->target_tol = 1e-13;
+    o->refine_tol = 1e-15;
+    o->max_refine = 20;
+    o->start_seed = 12345;
+}
+
+const char *mbl_version(void) { return "mblsi 0.1 (sm_103a)"; }
+
+const char *mbl_last_error(mbl_ctx *ctx) { return ctx ? ctx->last_error.c_str() : g_last_error.c_str(); }
+
+const char *mbl_status_string(int s) {
+    switch (s) {
+        case MBL_OK: return "ok";
+        case MBL_ERR_INVALID: return "invalid argument";
+        case MBL_ERR_OOM: return "out of memory budget";
+        case MBL_ERR_SINGULAR: return "singular factorization";
+        case MBL_ERR_NOT_CONVERGED: return "not converged";
+        case MBL_ERR_TIMEOUT: return "device wait timed out";
+        case MBL_ERR_CUDA: return "CUDA error";
+        case MBL_PENDING: return "pending";
+        default: return "unknown status";
+    }
+}
+
+int mbl_ctx_create(int device, size_t budget, mbl_ctx **out) {
+    if (!out) return report(nullptr, MBL_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    mbl_ctx *c = nullptr;
+    API_TRY
+    int ndev = 0;
+    MBL_CUDA(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) fail(MBL_ERR_INVALID, "no such CUDA device");
+    MBL_CUDA(cudaSetDevice(device));
+    c = new mbl_ctx();
+    c->device = device;
+    c->budget = budget;
+    MBL_CUDA(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+    MBL_CUDA(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device));
+    upload_binomials();
+    *out = c;
+    c = nullptr;
+    }
+    catch (const mbl::Error &e) {
+        delete c;
+        return report(nullptr, e.code, e.msg);
+    }
+    return MBL_OK;
+}
+
+void mbl_ctx_destroy(mbl_ctx *ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    ctx->plans.clear();
+    ctx->ent.clear();
+    cudaStreamDestroy(ctx->stream);
+    delete ctx;
+}
+
+int mbl_ctx_synchronize(mbl_ctx *ctx) {
+    API_TRY
+    MBL_CUDA(cudaStreamSynchronize(ctx->stream));
+    API_CATCH(ctx)
+}
+
+static int build_common(mbl_ctx *ctx, int L, const double *h_host, double J, bool from_seed, double h, uint64_t seed,
+                        mbl_sector **out) {
+    if (!ctx || !out) return report(ctx, MBL_ERR_INVALID, "NULL argument");
+    *out = nullptr;
+    if (L < 2 || L > 22 || (L & 1)) return report(ctx, MBL_ERR_INVALID, "L must be even with 2 <= L <= 22");
+    if (from_seed && !(h >= 0.0)) return report(ctx, MBL_ERR_INVALID, "h must be >= 0");
+    mbl_sector *s = new mbl_sector();
+    API_TRY
+    MBL_CUDA(cudaSetDevice(ctx->device));
+    s->ctx = ctx;
+    s->L = L;
+    s->J = J;
+    int64_t n = 1;
+    for (int i = 1; i <= L / 2; ++i) n = n * (L / 2 + i) / i;
+    s->n = n;
+    s->d_hfield.alloc(ctx, 32);
+    if (from_seed) {
+        launch_fields(L, h, seed, s->d_hfield.data(), ctx->stream);
+        MBL_CUDA(cudaMemcpyAsync(s->hfield, s->d_hfield.data(), L * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    } else {
+        std::memcpy(s->hfield, h_host, L * sizeof(double));
+        MBL_CUDA(cudaMemcpyAsync(s->d_hfield.data(), s->hfield, L * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    }
+    build_sector_device(s, ctx->stream);
+    *out = s;
+    s = nullptr;
+    }
+    catch (const mbl::Error &e) {
+        delete s;
+        return report(ctx, e.code, e.msg);
+    }
+    return MBL_OK;
+}
+
+int mbl_build_sector(mbl_ctx *ctx, int L, double h, uint64_t seed, mbl_sector **out) {
+    return build_common(ctx, L, nullptr, 1.0, true, h, seed, out);
+}
+
+int mbl_build_sector_fields(mbl_ctx *ctx, int L, const double *h_i, double J, mbl_sector **out) {
+    if (!h_i) return report(ctx, MBL_ERR_INVALID, "h_i is NULL");
+    return build_common(ctx, L, h_i, J, false, 0.0, 0, out);
+}
+
+void mbl_sector_destroy(mbl_sector *sec) {
+    if (!sec) return;
+    cudaStreamSynchronize(sec->ctx->stream);
+    delete sec;
+}
+
+int mbl_sector_info(const mbl_sector *sec, int64_t *dim, int64_t *nnz) {
+    if (!sec) return report(nullptr, MBL_ERR_INVALID, "sector is NULL");
+    if (dim) *dim = sec->n;
+    if (nnz) *nnz = sec->nnz;
+    return MBL_OK;
+}
+
+int mbl_sector_copy_basis(const mbl_sector *sec, uint32_t *states) {
+    if (!sec || !states) return report(nullptr, MBL_ERR_INVALID, "NULL argument");
+    API_TRY
+    MBL_CUDA(cudaStreamSynchronize(sec->ctx->stream));
+    MBL_CUDA(cudaMemcpy(states, sec->states.data(), sec->n * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+    API_CATCH(sec->ctx)
+}
+
+int mbl_sector_copy_csr(const mbl_sector *sec, int64_t *rowptr, int32_t *col, double *val) {
+    if (!sec) return report(nullptr, MBL_ERR_INVALID, "sector is NULL");
+    API_TRY
+    MBL_CUDA(cudaStreamSynchronize(sec->ctx->stream));
+    if (rowptr) MBL_CUDA(cudaMemcpy(rowptr, sec->rowptr.data(), (sec->n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost));
+    if (col) MBL_CUDA(cudaMemcpy(col, sec->col.data(), sec->nnz * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    if (val) MBL_CUDA(cudaMemcpy(val, sec->val.data(), sec->nnz * sizeof(double), cudaMemcpyDeviceToHost));
+    API_CATCH(sec->ctx)
+}
+
+int mbl_sector_copy_fields(const mbl_sector *sec, double *h_i) {
+    if (!sec || !h_i) return report(nullptr, MBL_ERR_INVALID, "NULL argument");
+    API_TRY
+    MBL_CUDA(cudaStreamSynchronize(sec->ctx->stream));
+    std::memcpy(h_i, sec->hfield, sec->L * sizeof(double));
+    API_CATCH(sec->ctx)
+}
+
+int mbl_sector_rank(const mbl_sector *sec, const uint32_t *states, int64_t count, int64_t *ranks) {
+    if (!sec || (count > 0 && (!states || !ranks))) return report(nullptr, MBL_ERR_INVALID, "NULL argument");
+    API_TRY
+    if (count <= 0) return MBL_OK;
+    DVec<uint32_t> ds;
+    DVec<int64_t> dr;
+    ds.alloc(sec->ctx, count);
+    dr.alloc(sec->ctx, count);
+    MBL_CUDA(cudaMemcpy(ds.data(), states, count * sizeof(uint32_t), cudaMemcpyHostToDevice));
+    launch_rank(sec->L, ds.data(), count, dr.data(), sec->ctx->stream);
+    MBL_CUDA(cudaStreamSynchronize(sec->ctx->stream));
+    MBL_CUDA(cudaMemcpy(ranks, dr.data(), count * sizeof(int64_t), cudaMemcpyDeviceToHost));
+    API_CATCH(sec->ctx)
+}
+
+int mbl_spmv(mbl_sector *sec, double shift, const double *x, double *y, int nrhs) {
+    if (!sec || !x || !y || nrhs < 1) return report(nullptr, MBL_ERR_INVALID, "bad argument");
+    API_TRY
+    int64_t n = sec->n;
+    DVec<double> dx, dy;
+    dx.alloc(sec->ctx, (size_t)n * nrhs);
+    dy.alloc(sec->ctx, (size_t)n * nrhs);
+    MBL_CUDA(cudaMemcpy(dx.data(), x, (size_t)n * nrhs * sizeof(double), cudaMemcpyHostToDevice));
+    launch_spmv(sec, shift, dx.data(), 1, n, dy.data(), 1, n, nrhs, sec->ctx->stream);
+    MBL_CUDA(cudaStreamSynchronize(sec->ctx->stream));
+    MBL_CUDA(cudaMemcpy(y, dy.data(), (size_t)n * nrhs * sizeof(double), cudaMemcpyDeviceToHost));
+    API_CATCH(sec->ctx)
+}
+
+int mbl_extremal_bounds(mbl_sector *sec, double *e_min, double *e_max) {
+    if (!sec || !e_min || !e_max) return report(nullptr, MBL_ERR_INVALID, "NULL argument");
+    API_TRY
+    MBL_CUDA(cudaSetDevice(sec->ctx->device));
+    extremal_bounds(sec, e_min, e_max);
+    API_CATCH(sec->ctx)
+}
+
+int mbl_factor(mbl_sector *sec, double sigma, const mbl_opts *opts, mbl_factorization **out) {
+    if (!sec || !out) return report(nullptr, MBL_ERR_INVALID, "NULL argument");
+    *out = nullptr;
+    mbl_opts o;
+    mbl_opts_default(&o);
+    if (opts) o = *opts;
+    API_TRY
+    MBL_CUDA(cudaSetDevice(sec->ctx->device));
+    double emin, emax;
+    extremal_bounds(sec, &emin, &emax);
+    double hn = std::max(std::fabs(emin), std::fabs(emax));
+    auto F = make_factorization(sec, sigma, o.precision, hn);
+    mbl_factorization *h = new mbl_factorization();
+    h->f = std::move(F);
+    *out = h;
+    API_CATCH(sec->ctx)
+}
+
+int mbl_factor_stats_get(const mbl_factorization *fh, mbl_factor_stats *s) {
+    if (!fh || !s) return report(nullptr, MBL_ERR_INVALID, "NULL argument");
+    const Factorization &f = *fh->f;
+    const Plan &p = *f.plan;
+    s->n = p.n;
+    s->nnz_l = p.nnz_l;
+    s->n_supernodes = p.ns;
+    s->max_front = p.max_front;
+    s->tree_levels = p.nlevels;
+    s->perturbed = f.perturbed;
+    s->negative = f.negative;
+    s->flops = p.flops;
+    s->factor_bytes = (double)(p.nnz_l + p.n) * f.elem_size();
+    s->front_bytes = (double)p.arena_elems * f.elem_size();
+    s->ms_factor = f.ms_factor;
+    return MBL_OK;
+}
+
+int mbl_factor_solve(mbl_factorization *fh, const double *b, double *x, int nrhs, int refine) {
+    if (!fh || !b || !x || nrhs < 1) return report(nullptr, MBL_ERR_INVALID, "bad argument");
+    Factorization &f = *fh->f;
+    Ctx *ctx = f.ctx;
+    API_TRY
+    cudaStream_t st = ctx->stream;
+    int64_t n = f.plan->n;
+    DVec<double> cm, B, X;
+    cm.alloc(ctx, (size_t)n * nrhs);
+    MBL_CUDA(cudaMemcpy(cm.data(), b, (size_t)n * nrhs * sizeof(double), cudaMemcpyHostToDevice));
+    double emin, emax;
+    extremal_bounds(f.sec, &emin, &emax);
+    double hn = std::max(std::fabs(emin), std::fabs(emax));
+    RefinedSolve rs{f.sec, &f, hn + std::fabs(f.sigma), 1e-15, 20};
+    for (int c0 = 0; c0 < nrhs; c0 += 32) {
+        int p = std::min(32, nrhs - c0);
+        B.alloc(ctx, (size_t)n * p);
+        X.alloc(ctx, (size_t)n * p);
+        // column-major host block -> row-major device block (copy_cols on the transposed view)
+        for (int q = 0; q < p; ++q) copy_cols(n, cm.data() + (size_t)(c0 + q) * n, 1, 0, B.data(), p, q, 1, st);
+        if (refine) rs.apply(B.data(), p, X.data(), p, st);
+        else factor_solve_raw(f, B.data(), p, X.data(), p, p, false, st);
+        for (int q = 0; q < p; ++q) copy_cols(n, X.data(), p, q, cm.data() + (size_t)(c0 + q) * n, 1, 0, 1, st);
+    }
+    MBL_CUDA(cudaStreamSynchronize(st));
+    MBL_CUDA(cudaMemcpy(x, cm.data(), (size_t)n * nrhs * sizeof(double), cudaMemcpyDeviceToHost));
+    API_CATCH(ctx)
+}
+
+void mbl_factor_destroy(mbl_factorization *f) {
+    if (!f) return;
+    if (f->f) cudaStreamSynchronize(f->f->ctx->stream);
+    delete f;
+}
+
+int mbl_solve_near_dev(mbl_sector *sec, double eps, int nev, const mbl_opts *opts, double *d_evals, double *d_evecs,
+                       double *d_resid, int *nconv, double *sigma_used, mbl_solve_stats *stats, void *stream) {
+    if (!sec || !d_evals || !d_evecs || !d_resid || !nconv || !sigma_used)
+        return report(nullptr, MBL_ERR_INVALID, "NULL argument");
+    mbl_opts o;
+    mbl_opts_default(&o);
+    if (opts) o = *opts;
+    API_TRY
+    MBL_CUDA(cudaSetDevice(sec->ctx->device));
+    cudaStream_t st = sec->ctx->stream;
+    if (stream) {
+        // order after the caller's stream, run on the context stream, then make the caller wait
+        cudaEvent_t ev;
+        MBL_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        MBL_CUDA(cudaEventRecord(ev, (cudaStream_t)stream));
+        MBL_CUDA(cudaStreamWaitEvent(st, ev, 0));
+        cudaEventDestroy(ev);
+    }
+    solve_near(sec, eps, nev, o, d_evals, d_evecs, d_resid, nconv, sigma_used, stats, st);
+    if (*nconv < nev) fail(MBL_ERR_NOT_CONVERGED, "only " + std::to_string(*nconv) + " of " + std::to_string(nev) +
+                                                      " eigenpairs reached the tolerance");
+    API_CATCH(sec->ctx)
+}
+
+int mbl_solve_near(mbl_sector *sec, double eps, int nev, const mbl_opts *opts, double *evals, double *evecs,
+                   double *resid, int *nconv, double *sigma_used, mbl_solve_stats *stats) {
+    if (!sec || !evals || !evecs || !resid || !nconv || !sigma_used)
+        return report(nullptr, MBL_ERR_INVALID, "NULL argument");
+    if (nev < 1 || nev > sec->n) return report(sec->ctx, MBL_ERR_INVALID, "nev must be in [1, dim]");
+    int rc = MBL_OK;
+    API_TRY
+    Ctx *ctx = sec->ctx;
+    int64_t n = sec->n;
+    DVec<double> de, dv, dr;
+    de.alloc(ctx, nev);
+    dv.alloc(ctx, (size_t)n * nev);
+    dr.alloc(ctx, nev);
+    rc = mbl_solve_near_dev(sec, eps, nev, opts, de.data(), dv.data(), dr.data(), nconv, sigma_used, stats, nullptr);
+    if (rc != MBL_OK && rc != MBL_ERR_NOT_CONVERGED) return rc;
+    std::string keep = ctx->last_error;
+    MBL_CUDA(cudaMemcpy(evals, de.data(), nev * sizeof(double), cudaMemcpyDeviceToHost));
+    MBL_CUDA(cudaMemcpy(evecs, dv.data(), (size_t)n * nev * sizeof(double), cudaMemcpyDeviceToHost));
+    MBL_CUDA(cudaMemcpy(resid, dr.data(), nev * sizeof(double), cudaMemcpyDeviceToHost));
+    if (rc != MBL_OK) return report(ctx, rc, keep);
+    API_CATCH(sec->ctx)
+}
+
+int mbl_observables_dev(mbl_ctx *ctx, int L, int nev, const double *d_evals, const double *d_evecs, double *d_r,
+                        double *d_r_mean, double *d_s1p, double *d_se, void *stream) {
+    if (!ctx || !d_evals || !d_evecs || !d_s1p || !d_se || (nev > 2 && !d_r))
+        return report(ctx, MBL_ERR_INVALID, "NULL argument");
+    if (L < 2 || L > 22 || (L & 1)) return report(ctx, MBL_ERR_INVALID, "L must be even with 2 <= L <= 22");
+    API_TRY
+    MBL_CUDA(cudaSetDevice(ctx->device));
+    cudaStream_t st = stream ? (cudaStream_t)stream : ctx->stream;
+    observables_dev(ctx, L, nev, d_evals, d_evecs, d_r, d_r_mean, d_s1p, d_se, st);
+    API_CATCH(ctx)
+}
+
+int mbl_observables(mbl_ctx *ctx, int L, int nev, const double *evals, const double *evecs, double *r, double *r_mean,
+                    double *s1p, double *se) {
+    if (!ctx || !evals || !evecs || !s1p || !se || (nev > 2 && !r)) return report(ctx, MBL_ERR_INVALID, "NULL argument");
+    if (L < 2 || L > 22 || (L & 1)) return report(ctx, MBL_ERR_INVALID, "L must be even with 2 <= L <= 22");
+    API_TRY
+    int64_t n = 1;
+    for (int i = 1; i <= L / 2; ++i) n = n * (L / 2 + i) / i;
+    if (nev < 1 || nev > n) fail(MBL_ERR_INVALID, "nev must be in [1, dim]");
+    DVec<double> de, dv, dr, drm, ds, dse;
+    de.alloc(ctx, nev);
+    dv.alloc(ctx, (size_t)n * nev);
+    dr.alloc(ctx, std::max(nev - 2, 1));
+    drm.alloc(ctx, 1);
+    ds.alloc(ctx, nev);
+    dse.alloc(ctx, nev);
+    MBL_CUDA(cudaMemcpy(de.data(), evals, nev * sizeof(double), cudaMemcpyHostToDevice));
+    MBL_CUDA(cudaMemcpy(dv.data(), evecs, (size_t)n * nev * sizeof(double), cudaMemcpyHostToDevice));
+    observables_dev(ctx, L, nev, de.data(), dv.data(), dr.data(), drm.data(), ds.data(), dse.data(), ctx->stream);
+    if (nev > 2 && r) MBL_CUDA(cudaMemcpy(r, dr.data(), (nev - 2) * sizeof(double), cudaMemcpyDeviceToHost));
+    if (r_mean) MBL_CUDA(cudaMemcpy(r_mean, drm.data(), sizeof(double), cudaMemcpyDeviceToHost));
+    MBL_CUDA(cudaMemcpy(s1p, ds.data(), nev * sizeof(double), cudaMemcpyDeviceToHost));
+    MBL_CUDA(cudaMemcpy(se, dse.data(), nev * sizeof(double), cudaMemcpyDeviceToHost));
+    API_CATCH(ctx)
+}
+
+}  // extern "C"

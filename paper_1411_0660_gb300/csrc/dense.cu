@@ -1,0 +1,483 @@
+// dense.cu -- FP64 block kernels of the Krylov solvers and a batched small symmetric
+// eigensolver.
+//
+// The eigensolver serves the Rayleigh-Ritz steps (projected matrices of the shift-invert
+// Lanczos, numerical-method section) and the Schmidt spectra of the half-chain entanglement
+// entropy (characterization section (ii)).  One CTA per matrix:
+//   1. Householder reduction to tridiagonal form (matrix in shared memory up to order 160);
+//   2a. eigenvalues only: every eigenvalue by bisection on Sturm counts, one thread each;
+//   2b. with eigenvectors: implicit QL with Wilkinson shifts; one thread generates the rotations
+//       of a sweep (the scalar chain) and every thread applies the whole sweep to its rows of Z,
+//       so the O(m^3) accumulation runs in parallel without a barrier per rotation;
+//   3. back-transformation by the stored reflectors, one warp per vector.
+#include <cfloat>
+
+#include "mbl_internal.h"
+
+namespace mbl {
+
+// ------------------------------------------------------------------------------------------
+// Block kernels on row-major n x ld blocks of vectors.
+// ------------------------------------------------------------------------------------------
+constexpr int TN_ROWS = 16;   // rows staged per step
+constexpr int TN_CHUNKS = 304; // partial-sum chunks (2 x 152 SMs)
+constexpr int TN_MAXKP = 8192;  // PER (8) outputs x 1024 threads
+
+size_t dense_tn_work(int64_t n, int k, int p) { return (size_t)TN_CHUNKS * (size_t)k * (size_t)p; }
+
+__global__ void k_tn_partial(int64_t n, const double *__restrict__ V, int ldv, int c0, int k,
+                             const double *__restrict__ X, int ldx, int x0, int p, double *__restrict__ work,
+                             int64_t rows_per) {
+    extern __shared__ double sm[];
+    double *sv = sm;                 // TN_ROWS x k
+    double *sx = sm + TN_ROWS * k;   // TN_ROWS x p
+    int64_t r0 = (int64_t)blockIdx.x * rows_per, r1 = min(n, r0 + rows_per);
+    int kp = k * p;
+    constexpr int PER = 8;
+    double acc[PER];
+#pragma unroll
+    for (int u = 0; u < PER; ++u) acc[u] = 0.0;
+    for (int64_t rb = r0; rb < r1; rb += TN_ROWS) {
+        int nr = (int)min((int64_t)TN_ROWS, r1 - rb);
+        for (int t = threadIdx.x; t < nr * k; t += blockDim.x) {
+            int r = t / k, a = t - r * k;
+            sv[r * k + a] = V[(rb + r) * ldv + c0 + a];
+        }
+        for (int t = threadIdx.x; t < nr * p; t += blockDim.x) {
+            int r = t / p, q = t - r * p;
+            sx[r * p + q] = X[(rb + r) * ldx + x0 + q];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            int o = threadIdx.x + u * blockDim.x;
+            if (o < kp) {
+                int a = o / p, q = o - a * p;
+                double s = acc[u];
+                for (int r = 0; r < nr; ++r) s = fma(sv[r * k + a], sx[r * p + q], s);
+                acc[u] = s;
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+        int o = threadIdx.x + u * blockDim.x;
+        if (o < kp) work[(size_t)blockIdx.x * kp + o] = acc[u];
+    }
+}
+
+__global__ void k_tn_reduce(int nch, int kp, const double *__restrict__ work, double *__restrict__ C) {
+    int o = blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= kp) return;
+    double s = 0.0;
+    for (int c = 0; c < nch; ++c) s += work[(size_t)c * kp + o];
+    C[o] = s;
+}
+
+void dense_tn(int64_t n, const double *V, int ldv, int c0, int k, const double *X, int ldx, int x0, int p,
+              double *C, double *work, cudaStream_t st) {
+    if (k <= 0 || p <= 0) return;
+    if (k * p > TN_MAXKP) fail(MBL_ERR_INVALID, "dense_tn: block too wide");
+    int threads = 1024;
+    while (threads > 128 && threads * 8 / 2 >= k * p) threads /= 2;
+    int64_t rows_per = (n + TN_CHUNKS - 1) / TN_CHUNKS;
+    if (rows_per < 1) rows_per = 1;
+    int nch = (int)((n + rows_per - 1) / rows_per);
+    size_t smem = (size_t)TN_ROWS * (k + p) * sizeof(double);
+    static bool attr = false;
+    if (!attr) {
+        MBL_CUDA(cudaFuncSetAttribute(k_tn_partial, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        attr = true;
+    }
+    k_tn_partial<<<nch, threads, smem, st>>>(n, V, ldv, c0, k, X, ldx, x0, p, work, rows_per);
+    MBL_LAUNCH_CHECK();
+    k_tn_reduce<<<(k * p + 255) / 256, 256, 0, st>>>(nch, k * p, work, C);
+    MBL_LAUNCH_CHECK();
+}
+
+__global__ void k_nn_sub(int64_t n, const double *__restrict__ V, int ldv, int c0, int k,
+                         const double *__restrict__ C, int p, double *__restrict__ X) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t i = t / p;
+    int q = (int)(t - i * p);
+    if (i >= n) return;
+    const double *v = V + i * ldv + c0;
+    double s = 0.0;
+    for (int a = 0; a < k; ++a) s = fma(v[a], C[a * p + q], s);
+    X[i * p + q] -= s;
+}
+
+void dense_nn_sub(int64_t n, const double *V, int ldv, int c0, int k, const double *C, int p, double *X,
+                  cudaStream_t st) {
+    if (k <= 0) return;
+    int64_t tot = n * p;
+    k_nn_sub<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(n, V, ldv, c0, k, C, p, X);
+    MBL_LAUNCH_CHECK();
+}
+
+__global__ void k_nn(int64_t n, const double *__restrict__ V, int ldv, int k, const double *__restrict__ S, int m,
+                     double *__restrict__ Y, int ldy, int y0) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t i = t / m;
+    int j = (int)(t - i * m);
+    if (i >= n) return;
+    const double *v = V + i * ldv;
+    double s = 0.0;
+    for (int a = 0; a < k; ++a) s = fma(v[a], S[a * m + j], s);
+    Y[i * ldy + y0 + j] = s;
+}
+
+void dense_nn(int64_t n, const double *V, int ldv, int k, const double *S, int m, double *Y, int ldy, int y0,
+              cudaStream_t st) {
+    if (m <= 0) return;
+    int64_t tot = n * m;
+    k_nn<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(n, V, ldv, k, S, m, Y, ldy, y0);
+    MBL_LAUNCH_CHECK();
+}
+
+__global__ void k_copy_cols(int64_t n, const double *src, int lds, int s0, double *dst, int ldd, int d0, int m) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t i = t / m;
+    int j = (int)(t - i * m);
+    if (i >= n) return;
+    dst[i * ldd + d0 + j] = src[i * lds + s0 + j];
+}
+
+void copy_cols(int64_t n, const double *src, int lds, int s0, double *dst, int ldd, int d0, int m,
+               cudaStream_t st) {
+    if (m <= 0) return;
+    int64_t tot = n * m;
+    k_copy_cols<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(n, src, lds, s0, dst, ldd, d0, m);
+    MBL_LAUNCH_CHECK();
+}
+
+// Cholesky of the p x p Gram matrix G = R^T R (R upper, row-major); flag = 0 if not positive.
+__global__ void k_chol(int p, const double *G, double *R, int *flag) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double maxd = 0.0;
+    for (int j = 0; j < p; ++j) maxd = fmax(maxd, G[j * p + j]);
+    for (int i = 0; i < p * p; ++i) R[i] = 0.0;
+    for (int j = 0; j < p; ++j) {
+        double s = G[j * p + j];
+        for (int l = 0; l < j; ++l) s -= R[l * p + j] * R[l * p + j];
+        if (!(s > 1e-28 * maxd) || !(maxd > 0.0)) {
+            *flag = 0;
+            s = fmax(maxd, 1e-300);  // keep going with a harmless value
+        }
+        double rjj = sqrt(s);
+        R[j * p + j] = rjj;
+        for (int c = j + 1; c < p; ++c) {
+            double t = G[j * p + c];
+            for (int l = 0; l < j; ++l) t -= R[l * p + j] * R[l * p + c];
+            R[j * p + c] = t / rjj;
+        }
+    }
+}
+
+// x_row <- x_row R^{-1} for every row
+__global__ void k_trsm_rows(int64_t n, double *X, int p, const double *R) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double x[32];
+    for (int j = 0; j < p; ++j) x[j] = X[i * p + j];
+    for (int j = 0; j < p; ++j) {
+        double s = x[j];
+        for (int l = 0; l < j; ++l) s -= x[l] * R[l * p + j];
+        x[j] = s / R[j * p + j];
+    }
+    for (int j = 0; j < p; ++j) X[i * p + j] = x[j];
+}
+
+void chol_qr(int64_t n, double *X, int p, double *R, double *G, double *work, int *d_flag, cudaStream_t st) {
+    dense_tn(n, X, p, 0, p, X, p, 0, p, G, work, st);
+    k_chol<<<1, 32, 0, st>>>(p, G, R, d_flag);
+    MBL_LAUNCH_CHECK();
+    k_trsm_rows<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(n, X, p, R);
+    MBL_LAUNCH_CHECK();
+}
+
+// ------------------------------------------------------------------------------------------
+// Batched small symmetric eigensolver.
+// ------------------------------------------------------------------------------------------
+constexpr int EIG_THREADS = 512;
+constexpr int EIG_SMEM_MAX_M = 160;
+
+size_t syev_work_doubles(int mmax, bool vecs) {
+    // d, e, beta, v, p, e^2 (8m with slack) [+ Z (m*m) + sort scratch (m*m) with eigenvectors]
+    size_t m = (size_t)mmax;
+    return 8 * m + (vecs ? 2 * m * m : 0) + 64;
+}
+
+__device__ double block_sum(double v, double *red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    double s = 0.0;
+    int nw = (blockDim.x + 31) >> 5;
+    for (int i = 0; i < nw; ++i) s += red[i];
+    __syncthreads();
+    return s;
+}
+
+// Sturm count: number of eigenvalues of T(d, e2) below x.
+__device__ int sturm_count(int m, const double *d, const double *e2, double x, double pivmin) {
+    int c = 0;
+    double q = d[0] - x;
+    if (fabs(q) < pivmin) q = -pivmin;
+    c += q < 0.0;
+    for (int i = 1; i < m; ++i) {
+        q = (d[i] - x) - e2[i - 1] / q;
+        if (fabs(q) < pivmin) q = -pivmin;
+        c += q < 0.0;
+    }
+    return c;
+}
+
+// One implicit QL sweep on the unreduced block lo..hi of (d, e), recording the rotations:
+// T <- J^T T J with J = [[c, s], [-s, c]] in planes (hi-1, hi), ..., (lo, lo+1); the first rotation
+// zeroes the upper entry of the last column of T - mu I, the others chase the bulge upward.
+__device__ int ql_sweep_record(int lo, int hi, double *d, double *e, double *cs, double *sn) {
+    double delta = 0.5 * (d[lo + 1] - d[lo]);
+    double b = e[lo];
+    double mu = d[lo] - b * b / (delta + copysign(hypot(delta, b), delta));
+    double x = d[hi] - mu, z = e[hi - 1];
+    for (int k = hi - 1; k >= lo; --k) {
+        double r = hypot(x, z);
+        double c = 1.0, s = 0.0;
+        if (r != 0.0) { c = x / r; s = z / r; }
+        if (k < hi - 1) e[k + 1] = r;
+        double a = d[k], bb = e[k], dd = d[k + 1];
+        d[k] = a * c * c - 2.0 * bb * c * s + dd * s * s;
+        d[k + 1] = a * s * s + 2.0 * bb * c * s + dd * c * c;
+        e[k] = (a - dd) * c * s + bb * (c * c - s * s);
+        if (k > lo) {
+            double bulge = s * e[k - 1];
+            e[k - 1] = c * e[k - 1];
+            x = e[k];
+            z = bulge;
+        }
+        cs[k] = c;
+        sn[k] = s;
+    }
+    return hi - lo;
+}
+
+// A: m x m column-major (lda = m) at A + aoff[b]; W: eigenvalues at W + woff[b];
+// vecs: eigenvectors into A (columns ascending); info[b] = 1 if QL did not converge.
+__global__ void __launch_bounds__(EIG_THREADS) k_syev(const int *mv, const int64_t *aoff, const int64_t *woff,
+                                                      double *Aall, double *Wall, int vecs, const int *selall,
+                                                      double *workall, size_t wstride, int *info) {
+    extern __shared__ double sm[];
+    __shared__ double red[EIG_THREADS / 32];
+    __shared__ double s_gl, s_gu, s_pivmin;
+    int b = blockIdx.x;
+    int m = mv[b];
+    double *Ag = Aall + aoff[b];
+    double *W = Wall + woff[b];
+    double *work = workall + (size_t)b * wstride;
+    double *d = work, *e = work + m, *beta = work + 2 * m, *vv = work + 3 * m, *pp = work + 4 * m;
+    double *e2 = work + 5 * m;
+    double *Z = work + 8 * m;                 // m x m
+    double *scr = Z + (size_t)m * m;          // m x m scratch
+    if (m <= 0) return;
+    if (m == 1) {
+        if (threadIdx.x == 0) {
+            W[0] = Ag[0];
+            if (vecs) Ag[0] = 1.0;
+        }
+        return;
+    }
+    bool in_smem = m <= EIG_SMEM_MAX_M;
+    double *a = in_smem ? sm : Ag;
+    int lda = m;
+    if (in_smem) {
+        for (int t = threadIdx.x; t < m * m; t += blockDim.x) a[t] = Ag[t];
+        __syncthreads();
+    }
+    // ---- 1. Householder tridiagonalization ----
+    for (int k = 0; k + 2 < m; ++k) {
+        int len = m - k - 1;
+        double *x = a + (size_t)k * lda + (k + 1);
+        double loc = 0.0;
+        for (int i = threadIdx.x; i < len; i += blockDim.x) loc += x[i] * x[i];
+        double alpha2 = block_sum(loc, red);
+        if (alpha2 == 0.0) {
+            if (threadIdx.x == 0) beta[k] = 0.0;
+            __syncthreads();
+            continue;
+        }
+        double x0 = x[0];
+        double sgn = x0 >= 0.0 ? 1.0 : -1.0;
+        double alpha = sqrt(alpha2);
+        double v0 = x0 + sgn * alpha;
+        loc = 0.0;
+        for (int i = threadIdx.x; i < len; i += blockDim.x) {
+            double v = (i == 0) ? 1.0 : x[i] / v0;
+            vv[i] = v;
+            if (i > 0) loc += v * v;
+        }
+        double vtv = 1.0 + block_sum(loc, red);
+        double bk = 2.0 / vtv;
+        // p = bk * A22 v (full symmetric storage)
+        double *A22 = a + (size_t)(k + 1) * lda + (k + 1);
+        for (int i = threadIdx.x; i < len; i += blockDim.x) {
+            double s = 0.0;
+            for (int j = 0; j < len; ++j) s = fma(A22[(size_t)j * lda + i], vv[j], s);
+            pp[i] = bk * s;
+        }
+        __syncthreads();
+        loc = 0.0;
+        for (int i = threadIdx.x; i < len; i += blockDim.x) loc += pp[i] * vv[i];
+        double K = 0.5 * bk * block_sum(loc, red);
+        for (int i = threadIdx.x; i < len; i += blockDim.x) pp[i] -= K * vv[i];
+        __syncthreads();
+        for (int t = threadIdx.x; t < len * len; t += blockDim.x) {
+            int i = t % len, j = t / len;
+            A22[(size_t)j * lda + i] -= vv[i] * pp[j] + pp[i] * vv[j];
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < len; i += blockDim.x) x[i] = (i == 0) ? -sgn * alpha : vv[i];
+        if (threadIdx.x == 0) beta[k] = bk;
+        __syncthreads();
+    }
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        d[i] = a[(size_t)i * lda + i];
+        if (i + 1 < m) {
+            e[i] = a[(size_t)i * lda + i + 1];
+            e2[i] = e[i] * e[i];
+        }
+    }
+    __syncthreads();
+    // ---- 2. eigenvalues only: bisection ----
+    if (!vecs) {
+    if (threadIdx.x == 0) {
+        double gl = d[0], gu = d[0], emax2 = 0.0;
+        for (int i = 0; i < m; ++i) {
+            double r = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i + 1 < m ? fabs(e[i]) : 0.0);
+            gl = fmin(gl, d[i] - r);
+            gu = fmax(gu, d[i] + r);
+            if (i + 1 < m) emax2 = fmax(emax2, e2[i]);
+        }
+        double tn = fmax(fabs(gl), fabs(gu));
+        gl -= 2.0 * DBL_EPSILON * tn * m + 1e-300;
+        gu += 2.0 * DBL_EPSILON * tn * m + 1e-300;
+        s_gl = gl;
+        s_gu = gu;
+        s_pivmin = DBL_MIN * fmax(1.0, emax2);
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < m; j += blockDim.x) {
+        double lo = s_gl, hi = s_gu;
+        for (int it = 0; it < 200; ++it) {
+            double mid = 0.5 * (lo + hi);
+            if (hi - lo <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + 4.0 * s_pivmin || mid == lo || mid == hi)
+                break;
+            if (sturm_count(m, d, e2, mid, s_pivmin) > j) hi = mid; else lo = mid;
+        }
+        W[j] = 0.5 * (lo + hi);
+    }
+    return;
+    }
+    // ---- 3. implicit QL on (d, e) accumulating Z (row-major m x m, starts as identity) ----
+    {
+        double *cs = pp, *sn = vv;  // reuse the Householder scratch for the sweep's rotations
+        for (int t = threadIdx.x; t < m * m; t += blockDim.x) Z[t] = ((t / m) == (t % m)) ? 1.0 : 0.0;
+        __shared__ int s_lo, s_hi, s_done, s_fail;
+        if (threadIdx.x == 0) { s_lo = 0; s_done = 0; s_fail = 0; }
+        __syncthreads();
+        int iter = 0;
+        while (true) {
+            if (threadIdx.x == 0) {
+                int lo = s_lo;
+                s_hi = -1;
+                while (lo < m - 1) {
+                    if (fabs(e[lo]) <= DBL_EPSILON * (fabs(d[lo]) + fabs(d[lo + 1]))) { e[lo] = 0.0; ++lo; iter = 0; continue; }
+                    int hi = lo + 1;
+                    while (hi < m - 1 && !(fabs(e[hi]) <= DBL_EPSILON * (fabs(d[hi]) + fabs(d[hi + 1])))) ++hi;
+                    if (hi < m - 1) e[hi] = 0.0;
+                    if (++iter > 100) { s_fail = 1; lo = m; break; }
+                    ql_sweep_record(lo, hi, d, e, cs, sn);
+                    s_hi = hi;
+                    break;
+                }
+                s_lo = lo;
+                if (lo >= m - 1) s_done = 1;
+            }
+            __syncthreads();
+            if (s_hi >= 0) {
+                int lo = s_lo, hi = s_hi;
+                for (int r = threadIdx.x; r < m; r += blockDim.x) {
+                    double *zr = Z + (size_t)r * m;
+                    for (int k = hi - 1; k >= lo; --k) {
+                        double c = cs[k], sv = sn[k];
+                        double a0 = zr[k], a1 = zr[k + 1];
+                        zr[k] = c * a0 - sv * a1;
+                        zr[k + 1] = sv * a0 + c * a1;
+                    }
+                }
+            }
+            __syncthreads();
+            if (s_done) break;
+        }
+        if (threadIdx.x == 0) {
+            // selection sort of the eigenvalues; record the permutation in cs (as doubles)
+            for (int i = 0; i < m; ++i) cs[i] = (double)i;
+            for (int i = 0; i < m - 1; ++i) {
+                int mi = i;
+                for (int j = i + 1; j < m; ++j) if (d[j] < d[mi]) mi = j;
+                double t = d[i]; d[i] = d[mi]; d[mi] = t;
+                t = cs[i]; cs[i] = cs[mi]; cs[mi] = t;
+            }
+            if (info) info[b] = s_fail;
+        }
+        __syncthreads();
+        for (int j = threadIdx.x; j < m; j += blockDim.x) W[j] = d[j];
+        // gather sorted columns of Z (row-major) into column-major scratch e2.. -> use scr
+        for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
+            int c = t / m, r = t % m;
+            scr[t] = Z[(size_t)r * m + (int)cs[c]];
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < m * m; t += blockDim.x) Z[t] = scr[t];
+        __syncthreads();
+    }
+    // ---- 4. back-transformation y = H_0 ... H_{m-3} z, one warp per vector ----
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int c = warp; c < m; c += nw) {
+        double *z = Z + (size_t)c * m;
+        for (int k = m - 3; k >= 0; --k) {
+            double bk = beta[k];
+            if (bk == 0.0) continue;
+            const double *vk = a + (size_t)k * lda + (k + 1);
+            int len = m - k - 1;
+            double s = 0.0;
+            for (int i = lane; i < len; i += 32) s += (i == 0 ? 1.0 : vk[i]) * z[k + 1 + i];
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            s *= bk;
+            for (int i = lane; i < len; i += 32) z[k + 1 + i] -= s * (i == 0 ? 1.0 : vk[i]);
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < m * m; t += blockDim.x) Ag[t] = Z[t];
+}
+
+void syev_batched(int batch, const int *d_m, const int64_t *d_aoff, const int64_t *d_woff, double *d_A,
+                  double *d_w, int vecs, const int *d_sel, int mmax, double *d_work, int *d_info, cudaStream_t st) {
+    if (batch <= 0) return;
+    size_t smem = mmax <= EIG_SMEM_MAX_M ? (size_t)mmax * mmax * sizeof(double) : 0;
+    static bool attr = false;
+    if (!attr) {
+        MBL_CUDA(cudaFuncSetAttribute(k_syev, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      EIG_SMEM_MAX_M * EIG_SMEM_MAX_M * sizeof(double)));
+        attr = true;
+    }
+    k_syev<<<batch, EIG_THREADS, smem, st>>>(d_m, d_aoff, d_woff, d_A, d_w, vecs, d_sel, d_work,
+                                             syev_work_doubles(mmax, vecs != 0), d_info);
+    MBL_LAUNCH_CHECK();
+}
+
+}  // namespace mbl

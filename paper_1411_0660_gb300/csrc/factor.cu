@@ -1,0 +1,669 @@
+// factor.cu -- batched multifrontal LDL^T of H - sigma I and the supernodal triangular solves.
+//
+// The shift-invert transformation of arXiv:1411.0660 (numerical-method section) needs
+// (H - sigma)^-1 applied many times; the paper factors H - sigma with a parallel sparse direct
+// solver.  Here the factorization is a supernodal multifrontal LDL^T driven by the static plan
+// (plan.h): fronts of one tree level are processed together, panel by panel:
+//   assemble   zero the front, scatter the CSR entries (minus sigma on the diagonal) and
+//              extend-add the children's contribution blocks (deterministic, no atomics);
+//   diag       one CTA factors the NB x NB diagonal block with diagonal pivoting inside it
+//              (a pivot below `tiny` is replaced by +-tiny), and inverts its unit-lower factor;
+//   trsm       W21 = A21 L11^-T (= L21 D), L21 = W21 D^-1, row blocks in parallel;
+//   update     A22 -= L21 W21^T on the lower triangle, 64 x 64 tiles in parallel.
+// Pivoting permutes only the variables of the current panel; the rows of earlier panel
+// columns keep their order and the solves apply each panel's permutation when they reach it.
+#include <cfloat>
+
+#include "factor.h"
+
+namespace mbl {
+
+template <class T>
+__device__ __forceinline__ T tabs(T x) { return x < T(0) ? -x : x; }
+
+__device__ __forceinline__ int lower_bound_i32(const int32_t *a, int n, int x) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (a[mid] < x) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// descriptor whose [off, off + count) range holds `b` (descs of one step are ordered by off)
+__device__ __forceinline__ int find_desc2(const PanelDesc *d, int nd, int64_t b) {
+    int lo = 0, hi = nd - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (d[mid].off2 <= b) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+__device__ __forceinline__ int find_desc3(const PanelDesc *d, int nd, int64_t b) {
+    int lo = 0, hi = nd - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (d[mid].off3 <= b) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// ------------------------------------------------------------------------------------------
+// Numeric factorization kernels
+// ------------------------------------------------------------------------------------------
+template <class T>
+__global__ void __launch_bounds__(256) k_assemble(const AsmItem *items, const int64_t *fo, const int32_t *fsz,
+                                                  const int32_t *nc, const int32_t *sn_start, const int32_t *ch_ptr,
+                                                  const int32_t *ch_list, const int64_t *rel_off,
+                                                  const int32_t *relind, const int64_t *amap_ptr,
+                                                  const int64_t *amap_src, const int32_t *amap_row,
+                                                  const double *val, double sigma, T *arena) {
+    AsmItem it = items[blockIdx.x];
+    int s = it.front, f = fsz[s], c0 = it.c0, c1 = min(f, c0 + ACOLS);
+    T *F = arena + fo[s];
+    for (int c = c0; c < c1; ++c)
+        for (int r = c + threadIdx.x; r < f; r += blockDim.x) F[(int64_t)c * f + r] = T(0);
+    __syncthreads();
+    int ncs = nc[s];
+    for (int c = c0; c < min(c1, ncs); ++c) {
+        int64_t j = sn_start[s] + c;
+        for (int64_t e = amap_ptr[j] + threadIdx.x; e < amap_ptr[j + 1]; e += blockDim.x) {
+            int r = amap_row[e];
+            double v = val[amap_src[e]];
+            if (r == c) v -= sigma;
+            F[(int64_t)c * f + r] = (T)v;
+        }
+    }
+    __syncthreads();
+    for (int q = ch_ptr[s]; q < ch_ptr[s + 1]; ++q) {
+        int ch = ch_list[q];
+        int fc = fsz[ch], ncc = nc[ch], uc = fc - ncc;
+        const int32_t *rel = relind + rel_off[ch];
+        const T *C = arena + fo[ch];
+        int blo = lower_bound_i32(rel, uc, c0), bhi = lower_bound_i32(rel, uc, c1);
+        for (int b = blo; b < bhi; ++b) {
+            T *Pcol = F + (int64_t)rel[b] * f;
+            const T *Ccol = C + (int64_t)(ncc + b) * fc + ncc;
+            for (int a = b + threadIdx.x; a < uc; a += blockDim.x) Pcol[rel[a]] += Ccol[a];
+        }
+        __syncthreads();
+    }
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_panel_diag(const PanelDesc *descs, const int64_t *fo, const int32_t *fsz,
+                                                    const int32_t *sn_start, T *arena, T *Dg, int32_t *piv, T *linv,
+                                                    double tiny, unsigned long long *counters) {
+    __shared__ T B[NB][NB + 1];
+    __shared__ int perm[NB];
+    __shared__ int s_j;
+    __shared__ T s_d;
+    const PanelDesc d = descs[blockIdx.x];
+    const int s = d.front, f = fsz[s], k0 = d.k0, w = d.w;
+    T *F = arena + fo[s];
+    const int tid = threadIdx.x, bd = blockDim.x;
+    for (int idx = tid; idx < w * w; idx += bd) {
+        int r = idx % w, c = idx / w;
+        B[r][c] = (r >= c) ? F[(int64_t)(k0 + c) * f + k0 + r] : T(0);
+    }
+    if (tid < w) perm[tid] = tid;
+    __syncthreads();
+    for (int t = 0; t < w; ++t) {
+        if (tid < 32) {
+            T best = T(-1);
+            int bj = t;
+            for (int i = t + tid; i < w; i += 32) {
+                T v = tabs(B[i][i]);
+                if (v > best) { best = v; bj = i; }
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                T ov = __shfl_down_sync(0xffffffffu, best, o);
+                int oj = __shfl_down_sync(0xffffffffu, bj, o);
+                if (ov > best || (ov == best && oj < bj)) { best = ov; bj = oj; }
+            }
+            if (tid == 0) s_j = bj;
+        }
+        __syncthreads();
+        const int j = s_j;
+        if (j != t) {
+            for (int c = tid; c < t; c += bd) { T x = B[t][c]; B[t][c] = B[j][c]; B[j][c] = x; }
+            for (int c = t + 1 + tid; c < j; c += bd) { T x = B[c][t]; B[c][t] = B[j][c]; B[j][c] = x; }
+            for (int r = j + 1 + tid; r < w; r += bd) { T x = B[r][t]; B[r][t] = B[r][j]; B[r][j] = x; }
+            if (tid == 0) {
+                T x = B[t][t]; B[t][t] = B[j][j]; B[j][j] = x;
+                int pp = perm[t]; perm[t] = perm[j]; perm[j] = pp;
+            }
+        }
+        __syncthreads();
+        if (tid == 0) {
+            T dv = B[t][t];
+            if (!(tabs(dv) >= (T)tiny)) {
+                dv = (dv >= T(0)) ? (T)tiny : (T)(-tiny);
+                atomicAdd(&counters[0], 1ull);
+            }
+            if (dv < T(0)) atomicAdd(&counters[1], 1ull);
+            B[t][t] = dv;
+            s_d = dv;
+        }
+        __syncthreads();
+        const T dv = s_d;
+        const int m = w - t - 1;
+        for (int idx = tid; idx < m * m; idx += bd) {
+            int r = t + 1 + idx % m, c = t + 1 + idx / m;
+            if (r >= c) B[r][c] -= B[r][t] * (B[c][t] / dv);
+        }
+        __syncthreads();
+        for (int r = t + 1 + tid; r < w; r += bd) B[r][t] /= dv;
+        __syncthreads();
+    }
+    // write L11 (strictly lower), D on the diagonal, pivots
+    for (int idx = tid; idx < w * w; idx += bd) {
+        int r = idx % w, c = idx / w;
+        if (r >= c) F[(int64_t)(k0 + c) * f + k0 + r] = B[r][c];
+    }
+    const int64_t g0 = (int64_t)sn_start[s] + k0;
+    if (tid < w) {
+        Dg[g0 + tid] = B[tid][tid];
+        piv[g0 + tid] = k0 + perm[tid];
+    }
+    // Linv = L11^-1 (unit lower), row-major NB x NB: Linv[t][k] for k <= t; one thread per column
+    T *Li = linv + (int64_t)blockIdx.x * NB * NB;
+    if (tid < w) {
+        const int c = tid;
+        T x[NB];
+        for (int r = 0; r < w; ++r) x[r] = T(0);
+        x[c] = T(1);
+        for (int r = c + 1; r < w; ++r) {
+            T acc = T(0);
+            for (int k = c; k < r; ++k) acc += B[r][k] * x[k];
+            x[r] = -acc;
+        }
+        for (int r = 0; r < w; ++r) Li[r * NB + c] = x[r];
+    }
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_panel_trsm(const PanelDesc *descs, int nd, const int64_t *fo,
+                                                    const int32_t *fsz, const int32_t *sn_start, T *arena,
+                                                    const T *Dg, const int32_t *piv, const T *linv, T *wscr) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T *Ls = reinterpret_cast<T *>(smraw);      // NB x (NB+1): Ls[t][k]
+    T *As = Ls + NB * (NB + 1);                // RB x (NB+1): As[i][k]
+    __shared__ T Dinv[NB];
+    __shared__ int pv[NB];
+    const int di = find_desc2(descs, nd, blockIdx.x);
+    const PanelDesc d = descs[di];
+    const int s = d.front, f = fsz[s], k0 = d.k0, w = d.w, m2 = d.m2;
+    const int rb = (int)(blockIdx.x - d.off2);
+    const int r0 = k0 + w + rb * RB;
+    const int nr = min(RB, f - r0);
+    T *F = arena + fo[s];
+    const T *Li = linv + (int64_t)di * NB * NB;
+    const int tid = threadIdx.x, bd = blockDim.x;
+    const int64_t g0 = (int64_t)sn_start[s] + k0;
+    for (int idx = tid; idx < w * w; idx += bd) {
+        int t = idx / w, k = idx % w;
+        Ls[t * (NB + 1) + k] = Li[t * NB + k];
+    }
+    if (tid < w) {
+        Dinv[tid] = T(1) / Dg[g0 + tid];
+        pv[tid] = piv[g0 + tid];
+    }
+    __syncthreads();
+    for (int idx = tid; idx < nr * w; idx += bd) {
+        int i = idx % nr, k = idx / nr;
+        As[i * (NB + 1) + k] = F[(int64_t)pv[k] * f + r0 + i];
+    }
+    __syncthreads();
+    T *W = wscr + d.woff;
+    for (int idx = tid; idx < nr * w; idx += bd) {
+        int i = idx % nr, t = idx / nr;
+        T acc = T(0);
+        for (int k = 0; k <= t; ++k) acc += As[i * (NB + 1) + k] * Ls[t * (NB + 1) + k];
+        F[(int64_t)(k0 + t) * f + r0 + i] = acc * Dinv[t];
+        W[(int64_t)(r0 - k0 - w + i) + (int64_t)t * m2] = acc;
+    }
+}
+
+// Trailing update of one 64 x 64 lower tile: C[i][j] -= sum_t L21[i][t] W21[j][t]
+template <class T>
+__global__ void __launch_bounds__(256) k_panel_update(const PanelDesc *descs, int nd, const int64_t *fo,
+                                                      const int32_t *fsz, T *arena, const T *wscr) {
+    constexpr int KC = 16;
+    static_assert(RB == NB, "solve kernels share one shared-memory size");
+    __shared__ T As[KC][TB + 4];
+    __shared__ T Bs[KC][TB + 4];
+    const int di = find_desc3(descs, nd, blockIdx.x);
+    const PanelDesc d = descs[di];
+    const int s = d.front, f = fsz[s], k0 = d.k0, w = d.w, m2 = d.m2;
+    int64_t t = (int64_t)blockIdx.x - d.off3;
+    int bi = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+    while ((int64_t)(bi + 1) * (bi + 2) / 2 <= t) ++bi;
+    while ((int64_t)bi * (bi + 1) / 2 > t) --bi;
+    const int bj = (int)(t - (int64_t)bi * (bi + 1) / 2);
+    const int base = k0 + w;
+    const int i0 = base + bi * TB, j0 = base + bj * TB;
+    T *F = arena + fo[s];
+    const T *W = wscr + d.woff;
+    const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+    T acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
+    for (int kt = 0; kt < w; kt += KC) {
+        for (int idx = tid; idx < KC * TB; idx += 256) {
+            int k = idx / TB, i = idx % TB;
+            int kk = kt + k;
+            int gi = i0 + i, gj = j0 + i;
+            As[k][i] = (kk < w && gi < f) ? F[(int64_t)(k0 + kk) * f + gi] : T(0);
+            Bs[k][i] = (kk < w && gj < f) ? W[(int64_t)(gj - base) + (int64_t)kk * m2] : T(0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < KC; ++k) {
+            T a[4], b[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                a[u] = As[k][ty * 4 + u];
+                b[u] = Bs[k][tx * 4 + u];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u][v] += a[u] * b[v];
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        int gj = j0 + tx * 4 + v;
+        if (gj >= f) continue;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            int gi = i0 + ty * 4 + u;
+            if (gi >= f || gi < gj) continue;
+            F[(int64_t)gj * f + gi] -= acc[u][v];
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Triangular solves (row-major n x p blocks, p <= 32), multifrontal order.
+// ------------------------------------------------------------------------------------------
+template <class T>
+__global__ void k_perm_in(int64_t n, int p, const int32_t *perm, const double *B, int64_t ldb, T *y) {
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n * p) return;
+    int64_t k = idx / p;
+    int q = (int)(idx - k * p);
+    y[idx] = (T)B[(int64_t)perm[k] * ldb + q];
+}
+
+template <class T>
+__global__ void k_perm_out(int64_t n, int p, const int32_t *perm, const T *x, double *X, int64_t ldx, int accumulate) {
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n * p) return;
+    int64_t k = idx / p;
+    int q = (int)(idx - k * p);
+    double v = (double)x[idx];
+    double *dst = X + (int64_t)perm[k] * ldx + q;
+    *dst = accumulate ? *dst + v : v;
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_fwd_gather(const AsmItem *items, const int64_t *zo, const int32_t *fsz,
+                                                    const int32_t *nc, const int32_t *sn_start, const int32_t *ch_ptr,
+                                                    const int32_t *ch_list, const int64_t *rel_off,
+                                                    const int32_t *relind, const T *y, T *Z, int p) {
+    AsmItem it = items[blockIdx.x];
+    const int s = it.front, f = fsz[s], r0 = it.c0, r1 = min(f, r0 + ACOLS), ncs = nc[s];
+    T *z = Z + zo[s] * p;
+    for (int idx = threadIdx.x; idx < (r1 - r0) * p; idx += blockDim.x) {
+        int r = r0 + idx / p, q = idx % p;
+        z[(int64_t)r * p + q] = (r < ncs) ? y[((int64_t)sn_start[s] + r) * p + q] : T(0);
+    }
+    __syncthreads();
+    for (int qq = ch_ptr[s]; qq < ch_ptr[s + 1]; ++qq) {
+        int ch = ch_list[qq];
+        int ncc = nc[ch], uc = fsz[ch] - ncc;
+        const int32_t *rel = relind + rel_off[ch];
+        int alo = lower_bound_i32(rel, uc, r0), ahi = lower_bound_i32(rel, uc, r1);
+        const T *zc = Z + zo[ch] * p;
+        for (int idx = threadIdx.x; idx < (ahi - alo) * p; idx += blockDim.x) {
+            int a = alo + idx / p, q = idx % p;
+            z[(int64_t)rel[a] * p + q] += zc[(int64_t)(ncc + a) * p + q];
+        }
+        __syncthreads();
+    }
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_fwd_diag(const PanelDesc *descs, const int64_t *fo, const int64_t *zo,
+                                                  const int32_t *fsz, const int32_t *sn_start, const T *arena,
+                                                  const int32_t *piv, T *Z, int p) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T(*Lb)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(smraw);
+    T(*zs)[33] = reinterpret_cast<T(*)[33]>(smraw + sizeof(T) * NB * (NB + 1));
+    const PanelDesc d = descs[blockIdx.x];
+    const int s = d.front, f = fsz[s], k0 = d.k0, w = d.w;
+    const T *F = arena + fo[s];
+    T *z = Z + zo[s] * p;
+    const int64_t g0 = (int64_t)sn_start[s] + k0;
+    for (int idx = threadIdx.x; idx < w * w; idx += blockDim.x) {
+        int r = idx % w, c = idx / w;
+        Lb[r][c] = (r > c) ? F[(int64_t)(k0 + c) * f + k0 + r] : T(0);
+    }
+    for (int idx = threadIdx.x; idx < w * p; idx += blockDim.x) {
+        int t = idx / p, q = idx % p;
+        zs[t][q] = z[(int64_t)piv[g0 + t] * p + q];
+    }
+    __syncthreads();
+    for (int t = 0; t < w; ++t) {
+        for (int idx = threadIdx.x; idx < (w - t - 1) * p; idx += blockDim.x) {
+            int r = t + 1 + idx / p, q = idx % p;
+            zs[r][q] -= Lb[r][t] * zs[t][q];
+        }
+        __syncthreads();
+    }
+    for (int idx = threadIdx.x; idx < w * p; idx += blockDim.x) {
+        int t = idx / p, q = idx % p;
+        z[(int64_t)(k0 + t) * p + q] = zs[t][q];
+    }
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_fwd_update(const PanelDesc *descs, int nd, const int64_t *fo,
+                                                    const int64_t *zo, const int32_t *fsz, const T *arena, T *Z,
+                                                    int p) {
+    __shared__ T zp[NB][33];
+    const int di = find_desc2(descs, nd, blockIdx.x);
+    const PanelDesc d = descs[di];
+    const int s = d.front, f = fsz[s], k0 = d.k0, w = d.w;
+    const int r0 = k0 + w + (int)(blockIdx.x - d.off2) * RB;
+    const int nr = min(RB, f - r0);
+    const T *F = arena + fo[s];
+    T *z = Z + zo[s] * p;
+    for (int idx = threadIdx.x; idx < w * p; idx += blockDim.x) {
+        int t = idx / p, q = idx % p;
+        zp[t][q] = z[(int64_t)(k0 + t) * p + q];
+    }
+    __syncthreads();
+    const int i = threadIdx.x % RB;
+    if (i >= nr) return;
+    for (int q = threadIdx.x / RB; q < p; q += blockDim.x / RB) {
+        T acc = T(0);
+        for (int t = 0; t < w; ++t) acc += F[(int64_t)(k0 + t) * f + r0 + i] * zp[t][q];
+        z[(int64_t)(r0 + i) * p + q] -= acc;
+    }
+}
+
+template <class T>
+__global__ void k_fwd_finish(const AsmItem *items, const int64_t *zo, const int32_t *nc, const int32_t *sn_start,
+                             const T *Dg, const T *Z, T *yfw, int p) {
+    AsmItem it = items[blockIdx.x];
+    const int s = it.front, r0 = it.c0, r1 = min(nc[s], r0 + ACOLS);
+    const T *z = Z + zo[s] * p;
+    for (int idx = threadIdx.x; idx < (r1 - r0) * p; idx += blockDim.x) {
+        int r = r0 + idx / p, q = idx % p;
+        int64_t g = (int64_t)sn_start[s] + r;
+        yfw[g * p + q] = z[(int64_t)r * p + q] / Dg[g];
+    }
+}
+
+template <class T>
+__global__ void k_bwd_gather(const AsmItem *items, const int64_t *zo, const int32_t *fsz, const int32_t *nc,
+                             const int32_t *sn_start, const int64_t *rows_off, const int32_t *rows, const T *yfw,
+                             const T *x, T *Z, int p) {
+    AsmItem it = items[blockIdx.x];
+    const int s = it.front, f = fsz[s], r0 = it.c0, r1 = min(f, r0 + ACOLS), ncs = nc[s];
+    T *z = Z + zo[s] * p;
+    const int32_t *rw = rows + rows_off[s];
+    for (int idx = threadIdx.x; idx < (r1 - r0) * p; idx += blockDim.x) {
+        int r = r0 + idx / p, q = idx % p;
+        z[(int64_t)r * p + q] = (r < ncs) ? yfw[((int64_t)sn_start[s] + r) * p + q] : x[(int64_t)rw[r] * p + q];
+    }
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_bwd_partial(const PanelDesc *descs, int nd, const int64_t *fo,
+                                                     const int64_t *zo, const int32_t *fsz, const T *arena,
+                                                     const T *Z, int p, T *P) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T(*Fs)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(smraw);
+    T(*zsh)[33] = reinterpret_cast<T(*)[33]>(smraw + sizeof(T) * RB * (NB + 1));
+    const int di = find_desc2(descs, nd, blockIdx.x);
+    const PanelDesc d = descs[di];
+    const int s = d.front, f = fsz[s], k0 = d.k0, w = d.w;
+    const int r0 = k0 + w + (int)(blockIdx.x - d.off2) * RB;
+    const int nr = min(RB, f - r0);
+    const T *F = arena + fo[s];
+    const T *z = Z + zo[s] * p;
+    for (int idx = threadIdx.x; idx < nr * w; idx += blockDim.x) {
+        int i = idx % nr, t = idx / nr;
+        Fs[i][t] = F[(int64_t)(k0 + t) * f + r0 + i];
+    }
+    for (int idx = threadIdx.x; idx < nr * p; idx += blockDim.x) {
+        int i = idx / p, q = idx % p;
+        zsh[i][q] = z[(int64_t)(r0 + i) * p + q];
+    }
+    __syncthreads();
+    T *out = P + (int64_t)blockIdx.x * NB * 32;
+    for (int o = threadIdx.x; o < w * p; o += blockDim.x) {
+        int t = o / p, q = o % p;
+        T acc = T(0);
+        for (int i = 0; i < nr; ++i) acc += Fs[i][t] * zsh[i][q];
+        out[t * 32 + q] = acc;
+    }
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_bwd_diag(const PanelDesc *descs, const int64_t *fo, const int64_t *zo,
+                                                  const int32_t *fsz, const int32_t *sn_start, const T *arena,
+                                                  const int32_t *piv, const T *P, T *Z, int p) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T(*Lb)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(smraw);
+    T(*zs)[33] = reinterpret_cast<T(*)[33]>(smraw + sizeof(T) * NB * (NB + 1));
+    const PanelDesc d = descs[blockIdx.x];
+    const int s = d.front, f = fsz[s], k0 = d.k0, w = d.w;
+    const T *F = arena + fo[s];
+    T *z = Z + zo[s] * p;
+    const int64_t g0 = (int64_t)sn_start[s] + k0;
+    const int64_t nblk = (d.m2 + RB - 1) / RB;
+    for (int idx = threadIdx.x; idx < w * w; idx += blockDim.x) {
+        int r = idx % w, c = idx / w;
+        Lb[r][c] = (r > c) ? F[(int64_t)(k0 + c) * f + k0 + r] : T(0);
+    }
+    for (int idx = threadIdx.x; idx < w * p; idx += blockDim.x) {
+        int t = idx / p, q = idx % p;
+        T v = z[(int64_t)(k0 + t) * p + q];
+        for (int64_t b = 0; b < nblk; ++b) v -= P[(d.off2 + b) * NB * 32 + t * 32 + q];
+        zs[t][q] = v;
+    }
+    __syncthreads();
+    for (int r = w - 1; r > 0; --r) {
+        for (int idx = threadIdx.x; idx < r * p; idx += blockDim.x) {
+            int t = idx / p, q = idx % p;
+            zs[t][q] -= Lb[r][t] * zs[r][q];
+        }
+        __syncthreads();
+    }
+    for (int idx = threadIdx.x; idx < w * p; idx += blockDim.x) {
+        int t = idx / p, q = idx % p;
+        z[(int64_t)piv[g0 + t] * p + q] = zs[t][q];
+    }
+}
+
+template <class T>
+__global__ void k_bwd_finish(const AsmItem *items, const int64_t *zo, const int32_t *nc, const int32_t *sn_start,
+                             const T *Z, T *x, int p) {
+    AsmItem it = items[blockIdx.x];
+    const int s = it.front, r0 = it.c0, r1 = min(nc[s], r0 + ACOLS);
+    const T *z = Z + zo[s] * p;
+    for (int idx = threadIdx.x; idx < (r1 - r0) * p; idx += blockDim.x) {
+        int r = r0 + idx / p, q = idx % p;
+        x[((int64_t)sn_start[s] + r) * p + q] = z[(int64_t)r * p + q];
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Host drivers
+// ------------------------------------------------------------------------------------------
+template <class T>
+static void factor_impl(Factorization &fz, cudaStream_t st) {
+    Plan &p = *fz.plan;
+    mbl_sector *sec = fz.sec;
+    T *arena = static_cast<T *>(fz.arena.m.p);
+    T *Dg = static_cast<T *>(fz.D.m.p);
+    T *wscr = static_cast<T *>(fz.wscr.m.p);
+    T *linv = static_cast<T *>(fz.linv.m.p);
+    static bool attr = false;
+    if (!attr) {
+        MBL_CUDA(cudaFuncSetAttribute(k_panel_trsm<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
+        MBL_CUDA(cudaFuncSetAttribute(k_panel_trsm<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
+        attr = true;
+    }
+    size_t trsm_smem = (size_t)(NB + RB) * (NB + 1) * sizeof(T);
+    MBL_CUDA(cudaMemsetAsync(fz.counters.data(), 0, 2 * sizeof(unsigned long long), st));
+    for (int l = 0; l < p.nlevels; ++l) {
+        int na = p.asm_ptr[l + 1] - p.asm_ptr[l];
+        k_assemble<T><<<na, 256, 0, st>>>(p.d_asm_items.data() + p.asm_ptr[l], p.d_sn_fo.data(), p.d_sn_f.data(),
+                                          p.d_sn_nc.data(), p.d_sn_start.data(), p.d_ch_ptr.data(),
+                                          p.d_ch_list.data(), p.d_sn_rel_off.data(), p.d_relind.data(),
+                                          p.d_amap_ptr.data(), p.d_amap_src.data(), p.d_amap_row.data(),
+                                          sec->val.data(), fz.sigma, arena);
+        MBL_LAUNCH_CHECK();
+        for (int si = p.lvl_step_ptr[l]; si < p.lvl_step_ptr[l + 1]; ++si) {
+            const PanelStep &stp = p.steps[si];
+            const PanelDesc *dd = p.d_descs.data() + stp.d0;
+            k_panel_diag<T><<<stp.nd, 256, 0, st>>>(dd, p.d_sn_fo.data(), p.d_sn_f.data(), p.d_sn_start.data(), arena,
+                                                    Dg, fz.piv.data(), linv, fz.tiny, fz.counters.data());
+            MBL_LAUNCH_CHECK();
+            if (stp.n2 > 0) {
+                k_panel_trsm<T><<<(unsigned)stp.n2, 256, trsm_smem, st>>>(dd, stp.nd, p.d_sn_fo.data(), p.d_sn_f.data(),
+                                                                         p.d_sn_start.data(), arena, Dg, fz.piv.data(),
+                                                                         linv, wscr);
+                MBL_LAUNCH_CHECK();
+            }
+            if (stp.n3 > 0) {
+                k_panel_update<T><<<(unsigned)stp.n3, 256, 0, st>>>(dd, stp.nd, p.d_sn_fo.data(), p.d_sn_f.data(), arena,
+                                                                    wscr);
+                MBL_LAUNCH_CHECK();
+            }
+        }
+    }
+}
+
+void numeric_factor(Factorization &fz, cudaStream_t st) {
+    if (fz.prec == MBL_PREC_FP64) factor_impl<double>(fz, st);
+    else factor_impl<float>(fz, st);
+}
+
+template <class T>
+static void solve_impl(Factorization &fz, const double *B, int64_t ldb, double *X, int64_t ldx, int p, bool accumulate,
+                       cudaStream_t st) {
+    Plan &pl = *fz.plan;
+    int64_t n = pl.n;
+    T *arena = static_cast<T *>(fz.arena.m.p);
+    T *Dg = static_cast<T *>(fz.D.m.p);
+    fz.ensure_solve_work(p);
+    T *Z = static_cast<T *>(fz.zwork.m.p);
+    T *y = static_cast<T *>(fz.ywork.m.p);
+    T *yfw = static_cast<T *>(fz.yfw.m.p);
+    T *P = static_cast<T *>(fz.pwork.m.p);
+    int64_t tot = n * p;
+    unsigned g = (unsigned)((tot + 255) / 256);
+    const size_t dsm = sizeof(T) * (size_t)(NB * (NB + 1) + NB * 33);  // Lb + zs (and Fs + zsh, RB == NB)
+    static bool attr = false;
+    if (!attr) {
+        MBL_CUDA(cudaFuncSetAttribute(k_fwd_diag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024));
+        MBL_CUDA(cudaFuncSetAttribute(k_bwd_diag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024));
+        MBL_CUDA(cudaFuncSetAttribute(k_bwd_partial<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024));
+        attr = true;
+    }
+    k_perm_in<T><<<g, 256, 0, st>>>(n, p, pl.d_perm.data(), B, ldb, y);
+    MBL_LAUNCH_CHECK();
+    for (int l = 0; l < pl.nlevels; ++l) {
+        int na = pl.asm_ptr[l + 1] - pl.asm_ptr[l];
+        const AsmItem *items = pl.d_asm_items.data() + pl.asm_ptr[l];
+        k_fwd_gather<T><<<na, 256, 0, st>>>(items, pl.d_sn_zo.data(), pl.d_sn_f.data(), pl.d_sn_nc.data(),
+                                            pl.d_sn_start.data(), pl.d_ch_ptr.data(), pl.d_ch_list.data(),
+                                            pl.d_sn_rel_off.data(), pl.d_relind.data(), y, Z, p);
+        MBL_LAUNCH_CHECK();
+        for (int si = pl.lvl_step_ptr[l]; si < pl.lvl_step_ptr[l + 1]; ++si) {
+            const PanelStep &stp = pl.steps[si];
+            const PanelDesc *dd = pl.d_descs.data() + stp.d0;
+            k_fwd_diag<T><<<stp.nd, 256, dsm, st>>>(dd, pl.d_sn_fo.data(), pl.d_sn_zo.data(), pl.d_sn_f.data(),
+                                                  pl.d_sn_start.data(), arena, fz.piv.data(), Z, p);
+            MBL_LAUNCH_CHECK();
+            if (stp.n2 > 0) {
+                k_fwd_update<T><<<(unsigned)stp.n2, 256, 0, st>>>(dd, stp.nd, pl.d_sn_fo.data(), pl.d_sn_zo.data(),
+                                                                  pl.d_sn_f.data(), arena, Z, p);
+                MBL_LAUNCH_CHECK();
+            }
+        }
+        k_fwd_finish<T><<<na, 256, 0, st>>>(items, pl.d_sn_zo.data(), pl.d_sn_nc.data(), pl.d_sn_start.data(), Dg, Z,
+                                            yfw, p);
+        MBL_LAUNCH_CHECK();
+    }
+    for (int l = pl.nlevels - 1; l >= 0; --l) {
+        int na = pl.asm_ptr[l + 1] - pl.asm_ptr[l];
+        const AsmItem *items = pl.d_asm_items.data() + pl.asm_ptr[l];
+        k_bwd_gather<T><<<na, 256, 0, st>>>(items, pl.d_sn_zo.data(), pl.d_sn_f.data(), pl.d_sn_nc.data(),
+                                            pl.d_sn_start.data(), pl.d_sn_rows_off.data(), pl.d_rows.data(), yfw, y, Z,
+                                            p);
+        MBL_LAUNCH_CHECK();
+        for (int si = pl.lvl_step_ptr[l + 1] - 1; si >= pl.lvl_step_ptr[l]; --si) {
+            const PanelStep &stp = pl.steps[si];
+            const PanelDesc *dd = pl.d_descs.data() + stp.d0;
+            if (stp.n2 > 0) {
+                k_bwd_partial<T><<<(unsigned)stp.n2, 256, dsm, st>>>(dd, stp.nd, pl.d_sn_fo.data(), pl.d_sn_zo.data(),
+                                                                   pl.d_sn_f.data(), arena, Z, p, P);
+                MBL_LAUNCH_CHECK();
+            }
+            k_bwd_diag<T><<<stp.nd, 256, dsm, st>>>(dd, pl.d_sn_fo.data(), pl.d_sn_zo.data(), pl.d_sn_f.data(),
+                                                  pl.d_sn_start.data(), arena, fz.piv.data(), P, Z, p);
+            MBL_LAUNCH_CHECK();
+        }
+        k_bwd_finish<T><<<na, 256, 0, st>>>(items, pl.d_sn_zo.data(), pl.d_sn_nc.data(), pl.d_sn_start.data(), Z, y, p);
+        MBL_LAUNCH_CHECK();
+    }
+    k_perm_out<T><<<g, 256, 0, st>>>(n, p, pl.d_perm.data(), y, X, ldx, accumulate ? 1 : 0);
+    MBL_LAUNCH_CHECK();
+}
+
+void factor_solve_raw(Factorization &fz, const double *B, int64_t ldb, double *X, int64_t ldx, int p, bool accumulate,
+                      cudaStream_t st) {
+    if (p < 1 || p > 32) fail(MBL_ERR_INVALID, "solve: 1 <= nrhs <= 32 per block");
+    if (fz.prec == MBL_PREC_FP64) solve_impl<double>(fz, B, ldb, X, ldx, p, accumulate, st);
+    else solve_impl<float>(fz, B, ldb, X, ldx, p, accumulate, st);
+}
+
+void Factorization::ensure_solve_work(int p) {
+    if (p <= work_p) return;
+    size_t es = elem_size();
+    Plan &pl = *plan;
+    zwork.alloc(ctx, (size_t)pl.zwork_elems * p * es);
+    ywork.alloc(ctx, (size_t)pl.n * p * es);
+    yfw.alloc(ctx, (size_t)pl.n * p * es);
+    pwork.alloc(ctx, (size_t)std::max<int64_t>(pl.max_step_n2, 1) * NB * 32 * es);
+    work_p = p;
+}
+
+void Factorization::allocate() {
+    Plan &pl = *plan;
+    size_t es = elem_size();
+    arena.alloc(ctx, (size_t)pl.arena_elems * es);
+    D.alloc(ctx, (size_t)pl.n * es);
+    piv.alloc(ctx, pl.n);
+    counters.alloc(ctx, 2);
+    wscr.alloc(ctx, (size_t)std::max<int64_t>(pl.wscratch_elems, 1) * es);
+    linv.alloc(ctx, (size_t)std::max<int64_t>(pl.max_desc_per_step, 1) * NB * NB * es);
+}
+
+void Factorization::release_scratch() {
+    wscr.release();
+    linv.release();
+}
+
+}  // namespace mbl

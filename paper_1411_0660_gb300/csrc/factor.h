@@ -1,0 +1,43 @@
+// factor.h -- numeric factorization object and the raw triangular solve.
+#pragma once
+
+#include "plan.h"
+
+namespace mbl {
+
+struct Factorization {
+    Ctx *ctx = nullptr;
+    mbl_sector *sec = nullptr;
+    std::shared_ptr<Plan> plan;
+    double sigma = 0.0;
+    int prec = MBL_PREC_FP32;
+    double tiny = 0.0;
+    DVec<char> arena, D, wscr, linv, zwork, ywork, yfw, pwork;
+    DVec<int32_t> piv;
+    DVec<unsigned long long> counters;  // [0] perturbed pivots, [1] negative pivots
+    int work_p = 0;
+    int64_t perturbed = 0, negative = 0;
+    double ms_factor = 0.0;
+
+    size_t elem_size() const { return prec == MBL_PREC_FP64 ? sizeof(double) : sizeof(float); }
+    void allocate();
+    void release_scratch();
+    void ensure_solve_work(int p);
+};
+
+// Enqueue the numeric factorization of H - sigma I (allocate() first).
+void numeric_factor(Factorization &fz, cudaStream_t st);
+// X (n x p row-major FP64, row stride ldx) (+)= (L D L^T)^-1 B, B row stride ldb; 1 <= p <= 32.
+void factor_solve_raw(Factorization &fz, const double *B, int64_t ldb, double *X, int64_t ldx, int p, bool accumulate,
+                      cudaStream_t st);
+
+// Plan of the sector's L (built from the device CSR on first use and cached in the context).
+std::shared_ptr<Plan> get_plan(mbl_sector *sec);
+// Create, allocate and run a factorization (synchronous; fills stats).
+std::unique_ptr<Factorization> make_factorization(mbl_sector *sec, double sigma, int prec, double hnorm);
+
+}  // namespace mbl
+
+struct mbl_factorization {
+    std::unique_ptr<mbl::Factorization> f;
+};

@@ -1,0 +1,55 @@
+// krylov.h -- block Krylov-Schur engine, refined shift-invert operator, eigen drivers.
+#pragma once
+
+#include <functional>
+
+#include "factor.h"
+
+namespace mbl {
+
+constexpr int64_t DENSE_MAX_N = 400;  // sectors up to this size are diagonalized densely on the device
+
+// Op: Y (n x p, ld p) = Op X (X row stride ldx)
+using OpFn = std::function<void(const double *X, int ldx, double *Y, cudaStream_t st)>;
+
+struct KrylovSchur {
+    Ctx *ctx;
+    int64_t n;
+    int p, ncv, ldv;
+    int m = 0;  // basis columns; the first m - p have been expanded
+    DVec<double> V, V2, W, T, C1, C2, R1, R2, Rm, G, work, eigA, eigW, eigWork, res, SK, Bk;
+    DVec<int> flag, eigInfo, eigM, keep;
+    DVec<int64_t> eigOff;
+
+    KrylovSchur(Ctx *c, int64_t n_, int p_, int ncv_);
+    bool full() const { return m + p > ldv; }  // no room for another block
+    void start(uint64_t seed, cudaStream_t st);
+    void expand(const OpFn &op, cudaStream_t st);
+    // Ritz values (ascending) of the expanded part and their Krylov-Schur residual norms
+    void ritz(cudaStream_t st, std::vector<double> &theta, std::vector<double> &rnorm);
+    // keep the listed Ritz pairs (indices into the last ritz() result) plus the residual block
+    void restart(const std::vector<int> &keep_idx, cudaStream_t st);
+
+  private:
+    void orthonormalize_new_block(int m, cudaStream_t st, bool *deflated);
+};
+
+// (H - sigma)^-1 through the factor with FP64 iterative refinement against the CSR.
+struct RefinedSolve {
+    mbl_sector *sec;
+    Factorization *fz;
+    double anorm;      // ||H - sigma|| bound
+    double rtol;       // stop when ||b - A x|| <= rtol (anorm ||x|| + ||b||) per column
+    int max_refine;
+    int solves = 0, applies = 0;
+    bool stalled = false;
+    double last_rel = 0.0;
+    DVec<double> R, part, norms;
+    void apply(const double *X, int ldx, double *Y, int p, cudaStream_t st);
+};
+
+void extremal_bounds(mbl_sector *sec, double *emin, double *emax);
+void solve_near(mbl_sector *sec, double eps, int nev, const mbl_opts &o, double *d_evals, double *d_evecs,
+                double *d_resid, int *nconv, double *sigma_used, mbl_solve_stats *stats, cudaStream_t st);
+
+}  // namespace mbl

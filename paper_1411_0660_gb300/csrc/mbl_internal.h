@@ -1,0 +1,139 @@
+// mbl_internal.h -- shared declarations of the mblsi library (host C++ and CUDA).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "mblsi.h"
+
+namespace mbl {
+
+struct Error {
+    int code;
+    std::string msg;
+};
+
+[[noreturn]] inline void fail(int code, const std::string &m) { throw Error{code, m}; }
+
+#define MBL_CUDA(x)                                                                            \
+    do {                                                                                       \
+        cudaError_t e_ = (x);                                                                  \
+        if (e_ != cudaSuccess)                                                                 \
+            ::mbl::fail(MBL_ERR_CUDA, std::string(#x) + " -> " + cudaGetErrorString(e_) +      \
+                                          " at " + __FILE__ + ":" + std::to_string(__LINE__)); \
+    } while (0)
+
+#define MBL_LAUNCH_CHECK() MBL_CUDA(cudaGetLastError())
+
+struct Ctx;
+
+// Device allocation accounted against the context budget (admission control).
+struct DevMem {
+    void *p = nullptr;
+    size_t bytes = 0;
+    Ctx *ctx = nullptr;
+    DevMem() = default;
+    DevMem(const DevMem &) = delete;
+    DevMem &operator=(const DevMem &) = delete;
+    DevMem(DevMem &&o) noexcept { *this = std::move(o); }
+    DevMem &operator=(DevMem &&o) noexcept;
+    ~DevMem() { release(); }
+    void alloc(Ctx *c, size_t nbytes);
+    void release();
+};
+
+template <class T>
+struct DVec {
+    DevMem m;
+    size_t n = 0;
+    T *data() const { return static_cast<T *>(m.p); }
+    void alloc(Ctx *c, size_t count) {
+        m.alloc(c, count * sizeof(T));
+        n = count;
+    }
+    void release() {
+        m.release();
+        n = 0;
+    }
+    size_t size() const { return n; }
+};
+
+struct Plan;       // symbolic analysis, symbolic.cpp
+struct EntTables;  // entanglement block tables, observables.cu
+
+struct Ctx {
+    int device = 0;
+    size_t budget = 0;  // 0 = unlimited
+    size_t in_use = 0;
+    size_t peak = 0;
+    cudaStream_t stream = nullptr;
+    std::string last_error;
+    std::map<int, std::shared_ptr<Plan>> plans;     // per L
+    std::map<int, std::shared_ptr<EntTables>> ent;  // per L
+    int sm_count = 0;
+};
+
+}  // namespace mbl
+
+struct mbl_ctx : public mbl::Ctx {};
+
+struct mbl_sector {
+    mbl::Ctx *ctx = nullptr;
+    int L = 0;
+    int64_t n = 0, nnz = 0;
+    double J = 1.0;
+    double hfield[32] = {0};
+    mbl::DVec<uint32_t> states;
+    mbl::DVec<int64_t> rowptr;
+    mbl::DVec<int32_t> col;
+    mbl::DVec<double> val;
+    mbl::DVec<double> d_hfield;
+    bool have_bounds = false;
+    double emin = 0, emax = 0;
+    std::shared_ptr<mbl::Plan> plan;  // lazily attached
+};
+
+namespace mbl {
+
+// ---------------- sector.cu ----------------
+void upload_binomials();
+void launch_fields(int L, double h, uint64_t seed, double *d_out, cudaStream_t st);
+void build_sector_device(mbl_sector *sec, cudaStream_t st);
+void launch_rank(int L, const uint32_t *d_states, int64_t count, int64_t *d_ranks, cudaStream_t st);
+// y[i*ys_r + q*ys_c] = sum_j A_ij x[j*xs_r + q*xs_c] - shift x[i*xs_r + q*xs_c]   (FP64)
+void launch_spmv(const mbl_sector *sec, double shift, const double *x, int64_t xs_r, int64_t xs_c,
+                 double *y, int64_t ys_r, int64_t ys_c, int p, cudaStream_t st);
+
+// ---------------- dense.cu (FP64 block kernels, small symmetric eigensolver) ----------------
+// C[k x p] (row-major, ldc = p) = V[:, c0:c0+k]^T X[:, x0:x0+p], V n x ldv and X n x ldx row-major.
+// Uses `work` (>= dense_tn_work doubles) for deterministic partial sums; k * p <= 10240.
+size_t dense_tn_work(int64_t n, int k, int p);
+void dense_tn(int64_t n, const double *V, int ldv, int c0, int k, const double *X, int ldx, int x0, int p,
+              double *C, double *work, cudaStream_t st);
+// X -= V[:, c0:c0+k] C  (C k x p row-major)
+void dense_nn_sub(int64_t n, const double *V, int ldv, int c0, int k, const double *C, int p, double *X,
+                  cudaStream_t st);
+// Y[:, 0:m] = V[:, 0:k] S  (S k x m row-major, Y n x ldy row-major starting at column y0)
+void dense_nn(int64_t n, const double *V, int ldv, int k, const double *S, int m, double *Y, int ldy,
+              int y0, cudaStream_t st);
+// Copy columns: dst[:, d0:d0+m] = src[:, s0:s0+m] (row-major, given leading dims)
+void copy_cols(int64_t n, const double *src, int lds, int s0, double *dst, int ldd, int d0, int m,
+               cudaStream_t st);
+// Cholesky-QR of X (n x p row-major) in place; R (p x p row-major, upper) returned on device.
+// rank_ok[0] on device set to 0 if the Gram matrix is not numerically positive definite.
+void chol_qr(int64_t n, double *X, int p, double *R, double *G, double *work, int *d_flag,
+             cudaStream_t st);
+// Batched symmetric eigensolver on device: for b in [0, batch): A_b (m_b x m_b, column-major,
+// lda_b) -> eigenvalues ascending w_b, eigenvectors (if vecs) overwrite A_b.
+size_t syev_work_doubles(int mmax, bool vecs = true);
+// sel (optional, indexed like w): eigenvectors are computed only where sel != 0 (others zero).
+void syev_batched(int batch, const int *d_m, const int64_t *d_aoff, const int64_t *d_woff, double *d_A,
+                  double *d_w, int vecs, const int *d_sel, int mmax, double *d_work, int *d_info,
+                  cudaStream_t st);
+
+}  // namespace mbl

@@ -1,0 +1,210 @@
+// observables.cu -- eigenvector observables of arXiv:1411.0660, characterization section:
+//   (i)   gap ratio r^(n) = min(d_n, d_{n+1}) / max(d_n, d_{n+1}), d_n = E_n - E_{n-1};
+//   (iii) participation entropy S_1^P = -sum_i p_i ln p_i, p_i = |<i|n>|^2 in the S^z basis;
+//   (ii)  half-chain entanglement entropy S^E = -Tr rho_A ln rho_A for A = sites 0..L/2-1.
+// For S^E the vector is split by the magnetization n_A of the half chain: the block
+// M_{n_A}[a][b] = psi(a + b 2^{L/2}) (a with n_A up spins, b with L/2 - n_A) has Gram matrix
+// M M^T whose eigenvalues are the Schmidt weights of that block; all blocks of all vectors go to
+// one batched eigenvalue launch.
+#include <algorithm>
+#include <cmath>
+
+#include "observables.h"
+
+namespace mbl {
+
+__global__ void k_gap_ratio(int nev, const double *ev, double *r, double *rmean) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double s = 0.0;
+    int cnt = 0;
+    for (int k = 1; k + 1 < nev; ++k) {
+        double d0 = ev[k] - ev[k - 1], d1 = ev[k + 1] - ev[k];
+        double mx = d0 > d1 ? d0 : d1, mn = d0 > d1 ? d1 : d0;
+        if (mx == 0.0) {
+            r[k - 1] = NAN;
+            continue;
+        }
+        r[k - 1] = mn / mx;
+        s += r[k - 1];
+        ++cnt;
+    }
+    if (rmean) *rmean = cnt > 0 ? s / cnt : NAN;
+}
+
+// One CTA per vector: A = sum y^2, B = sum y^2 ln y^2; S = ln A - B / A.
+__global__ void k_s1p(int64_t n, const double *Y, double *s1p, double *nrm2) {
+    __shared__ double ra[32], rb[32];
+    const double *y = Y + (int64_t)blockIdx.x * n;
+    double a = 0.0, b = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        double v = y[i] * y[i];
+        a += v;
+        if (v > 0.0) b += v * log(v);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) { ra[w] = a; rb[w] = b; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double A = 0.0, B = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) { A += ra[i]; B += rb[i]; }
+        s1p[blockIdx.x] = log(A) - B / A;
+        nrm2[blockIdx.x] = A;
+    }
+}
+
+// Gram matrices: CTA (vector j, block q) writes G_q (dA x dA, column-major) normalized by |y|^2.
+__global__ void k_gram(int64_t n, int nblk, const double *Y, const double *nrm2, const int32_t *idx,
+                       const int64_t *boff, const int32_t *dA, const int32_t *dB, const int64_t *goff, double *G) {
+    extern __shared__ double Ms[];
+    const int j = blockIdx.x / nblk, q = blockIdx.x % nblk;
+    const int da = dA[q], db = dB[q];
+    const double *y = Y + (int64_t)j * n;
+    const int32_t *ix = idx + boff[q];
+    const double inv = 1.0 / nrm2[j];
+    double *g = G + goff[(int64_t)j * nblk + q];
+    const bool in_smem = (int64_t)da * db <= 12288;
+    if (in_smem) {
+        for (int t = threadIdx.x; t < da * db; t += blockDim.x) Ms[t] = y[ix[t]];
+        __syncthreads();
+    }
+    for (int t = threadIdx.x; t < da * da; t += blockDim.x) {
+        int r = t % da, c = t / da;
+        if (r < c) continue;
+        double s = 0.0;
+        if (in_smem)
+            for (int b = 0; b < db; ++b) s += Ms[r * db + b] * Ms[c * db + b];
+        else
+            for (int b = 0; b < db; ++b) s += y[ix[r * db + b]] * y[ix[c * db + b]];
+        s *= inv;
+        g[(int64_t)c * da + r] = s;
+        g[(int64_t)r * da + c] = s;
+    }
+}
+
+__global__ void k_entropy_sum(int nev, int nblk, const int32_t *dA, const int64_t *woff, const double *lam, double *se) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= nev) return;
+    double S = 0.0;
+    for (int q = 0; q < nblk; ++q) {
+        const double *l = lam + woff[(int64_t)j * nblk + q];
+        for (int i = 0; i < dA[q]; ++i)
+            if (l[i] > 1e-15) S -= l[i] * log(l[i]);
+    }
+    se[j] = S;
+}
+
+static int64_t host_binom(int n, int k) {
+    if (k < 0 || k > n) return 0;
+    int64_t r = 1;
+    for (int i = 1; i <= k; ++i) r = r * (n - k + i) / i;
+    return r;
+}
+
+static int64_t host_rank(uint32_t s) {
+    int64_t r = 0;
+    int t = 0;
+    while (s) {
+        int p = __builtin_ctz(s);
+        ++t;
+        r += host_binom(p, t);
+        s &= s - 1;
+    }
+    return r;
+}
+
+EntTables &ent_tables(Ctx *ctx, int L) {
+    auto it = ctx->ent.find(L);
+    if (it != ctx->ent.end()) return *it->second;
+    auto T = std::make_shared<EntTables>();
+    int LA = L / 2, LB = L - L / 2;
+    std::vector<int32_t> idx, da, db;
+    std::vector<int64_t> boff;
+    for (int nA = 0; nA <= LA; ++nA) {
+        int nB = L / 2 - nA;
+        if (nB < 0 || nB > LB) continue;
+        std::vector<uint32_t> as, bs;
+        for (uint32_t a = 0; a < (1u << LA); ++a) if (__builtin_popcount(a) == nA) as.push_back(a);
+        for (uint32_t b = 0; b < (1u << LB); ++b) if (__builtin_popcount(b) == nB) bs.push_back(b);
+        boff.push_back((int64_t)idx.size());
+        da.push_back((int32_t)as.size());
+        db.push_back((int32_t)bs.size());
+        for (uint32_t a : as)
+            for (uint32_t b : bs) idx.push_back((int32_t)host_rank(a | (b << LA)));
+    }
+    T->nblk = (int)da.size();
+    T->dA = da;
+    T->dAmax = *std::max_element(da.begin(), da.end());
+    T->d_idx.alloc(ctx, idx.size());
+    T->d_boff.alloc(ctx, boff.size());
+    T->d_dA.alloc(ctx, da.size());
+    T->d_dB.alloc(ctx, db.size());
+    MBL_CUDA(cudaMemcpy(T->d_idx.data(), idx.data(), idx.size() * 4, cudaMemcpyHostToDevice));
+    MBL_CUDA(cudaMemcpy(T->d_boff.data(), boff.data(), boff.size() * 8, cudaMemcpyHostToDevice));
+    MBL_CUDA(cudaMemcpy(T->d_dA.data(), da.data(), da.size() * 4, cudaMemcpyHostToDevice));
+    MBL_CUDA(cudaMemcpy(T->d_dB.data(), db.data(), db.size() * 4, cudaMemcpyHostToDevice));
+    EntTables &ref = *T;
+    ctx->ent[L] = T;
+    return ref;
+}
+
+void observables_dev(Ctx *ctx, int L, int nev, const double *d_evals, const double *d_evecs, double *d_r,
+                     double *d_rmean, double *d_s1p, double *d_se, cudaStream_t st) {
+    int64_t n = host_binom(L, L / 2);
+    if (nev < 1 || nev > n) fail(MBL_ERR_INVALID, "observables: nev must be in [1, dim]");
+    if (nev > 2 || d_rmean) {
+        k_gap_ratio<<<1, 32, 0, st>>>(nev, d_evals, d_r, d_rmean);
+        MBL_LAUNCH_CHECK();
+    }
+    DVec<double> nrm2;
+    nrm2.alloc(ctx, nev);
+    k_s1p<<<nev, 256, 0, st>>>(n, d_evecs, d_s1p, nrm2.data());
+    MBL_LAUNCH_CHECK();
+    EntTables &E = ent_tables(ctx, L);
+    int nb = E.nblk;
+    int64_t batch = (int64_t)nev * nb;
+    std::vector<int> hm(batch);
+    std::vector<int64_t> hg(batch), hw(batch);
+    int64_t g = 0, w = 0;
+    for (int j = 0; j < nev; ++j)
+        for (int q = 0; q < nb; ++q) {
+            int64_t b = (int64_t)j * nb + q;
+            hm[b] = E.dA[q];
+            hg[b] = g;
+            hw[b] = w;
+            g += (int64_t)E.dA[q] * E.dA[q];
+            w += E.dA[q];
+        }
+    DVec<int> dm, info;
+    DVec<int64_t> dgo, dwo;
+    DVec<double> G, lam, work;
+    dm.alloc(ctx, batch);
+    info.alloc(ctx, batch);
+    dgo.alloc(ctx, batch);
+    dwo.alloc(ctx, batch);
+    G.alloc(ctx, g);
+    lam.alloc(ctx, w);
+    size_t ws = syev_work_doubles(E.dAmax, false);
+    work.alloc(ctx, ws * batch);
+    MBL_CUDA(cudaMemcpyAsync(dm.data(), hm.data(), batch * sizeof(int), cudaMemcpyHostToDevice, st));
+    MBL_CUDA(cudaMemcpyAsync(dgo.data(), hg.data(), batch * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    MBL_CUDA(cudaMemcpyAsync(dwo.data(), hw.data(), batch * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    static bool attr = false;
+    if (!attr) {
+        MBL_CUDA(cudaFuncSetAttribute(k_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, 12288 * 8));
+        attr = true;
+    }
+    k_gram<<<(unsigned)batch, 256, 12288 * 8, st>>>(n, nb, d_evecs, nrm2.data(), E.d_idx.data(), E.d_boff.data(),
+                                                    E.d_dA.data(), E.d_dB.data(), dgo.data(), G.data());
+    MBL_LAUNCH_CHECK();
+    syev_batched((int)batch, dm.data(), dgo.data(), dwo.data(), G.data(), lam.data(), 0, nullptr, E.dAmax,
+                 work.data(), info.data(), st);
+    k_entropy_sum<<<(nev + 63) / 64, 64, 0, st>>>(nev, nb, E.d_dA.data(), dwo.data(), lam.data(), d_se);
+    MBL_LAUNCH_CHECK();
+    MBL_CUDA(cudaStreamSynchronize(st));
+}
+
+}  // namespace mbl

@@ -1,0 +1,80 @@
+// plan.h -- symbolic analysis of the sector pattern (host, once per L) and its device mirror.
+//
+// The pattern of H - sigma I does not depend on the fields, the seed or sigma, so one plan
+// serves every factorization at a given L.  It holds the fill-reducing order, the supernodal
+// assembly tree, the front row lists, the maps that scatter the CSR entries and the children's
+// contribution blocks into the fronts, and the static launch schedule (levels x panels) that the
+// batched numeric factorization and the triangular solves replay.
+#pragma once
+
+#include "mbl_internal.h"
+
+namespace mbl {
+
+constexpr int NB = 64;  // panel width of the blocked frontal LDL^T (pivot window)
+constexpr int RB = 64;  // rows per row block (stage 2 / solve updates)
+constexpr int TB = 64;  // tile edge of the trailing (Schur) update
+constexpr int ACOLS = 32;  // columns per assembly work item
+
+// One active front in one (level, panel) step.
+struct PanelDesc {
+    int32_t front;   // supernode id
+    int32_t k0;      // first column of the panel inside the front
+    int32_t w;       // panel width (<= NB)
+    int32_t m2;      // rows below the diagonal block: f - k0 - w
+    int64_t off2;    // prefix count of row blocks (stage 2) before this descriptor in its step
+    int64_t off3;    // prefix count of trailing tiles (stage 3) before this descriptor in its step
+    int64_t woff;    // offset (elements) of this front's W21 scratch (m2 x NB column-major, ld m2)
+};
+
+struct PanelStep {
+    int32_t level, kk;
+    int32_t d0, nd;  // descriptor range
+    int64_t n2, n3;  // row blocks and trailing tiles in this step
+    int64_t wsize;   // W21 scratch elements used by this step
+};
+
+struct AsmItem {     // assembly work item: columns [c0, c0 + ACOLS) of a front
+    int32_t front, c0;
+};
+
+struct Plan {
+    int L = 0;
+    int64_t n = 0, nnzA = 0;
+    std::vector<int32_t> perm, iperm;  // new -> old, old -> new
+    int32_t ns = 0;
+    std::vector<int32_t> sn_start, sn_nc, sn_f, sn_parent, sn_level;
+    std::vector<int64_t> sn_rows_off, sn_fo, sn_zo, sn_rel_off;
+    std::vector<int32_t> rows, relind;
+    std::vector<int32_t> ch_ptr, ch_list;
+    std::vector<int32_t> col_snode;           // new column -> supernode
+    std::vector<int64_t> amap_ptr;            // new column -> entries (n + 1)
+    std::vector<int64_t> amap_src;            // CSR position
+    std::vector<int32_t> amap_row;            // local row in the front
+    std::vector<int32_t> lvl_ptr, lvl_fronts;  // fronts by level
+    std::vector<int32_t> asm_ptr;             // assembly items by level
+    std::vector<AsmItem> asm_items;
+    std::vector<PanelStep> steps;
+    std::vector<int32_t> lvl_step_ptr;        // steps by level
+    std::vector<PanelDesc> descs;
+    int64_t arena_elems = 0, zwork_elems = 0, wscratch_elems = 0, max_desc_per_step = 0;
+    int64_t max_step_n2 = 0;
+    int64_t nnz_l = 0;
+    double flops = 0.0;
+    int32_t max_front = 0, nlevels = 0;
+    double ms_analyse = 0.0;
+
+    // device mirror
+    DVec<int32_t> d_perm, d_iperm, d_sn_start, d_sn_nc, d_sn_f, d_rows, d_relind, d_ch_ptr, d_ch_list, d_amap_row;
+    DVec<int64_t> d_sn_rows_off, d_sn_fo, d_sn_zo, d_sn_rel_off, d_amap_ptr, d_amap_src;
+    DVec<AsmItem> d_asm_items;
+    DVec<PanelDesc> d_descs;
+    bool on_device = false;
+};
+
+// Build the plan for the pattern of a sector (host arrays: states, rowptr, col of the CSR).
+std::shared_ptr<Plan> build_plan(int L, const std::vector<uint32_t> &states, const std::vector<int64_t> &rowptr,
+                                 const std::vector<int32_t> &col);
+void upload_plan(Ctx *ctx, Plan &p);
+
+}  // namespace mbl

@@ -1,0 +1,561 @@
+// symbolic.cpp -- host symbolic analysis: ordering, assembly tree, fronts, maps, schedule.
+//
+// Ordering.  The Hilbert-space graph of Eq. 1 (vertices = basis states, edges = the spin
+// exchanges of antiparallel neighbours) is expander-like, with coordination ~ L (the
+// Hilbert-space-graph paragraph of arXiv:1411.0660).  Generic minimum degree leaves a root front
+// of about a third of the sector.  This build instead uses nested dissection with separators
+// taken from the physics: the weighted magnetization
+//     f_k(s) = sum_i w_k(i) n_i(s),   w_k(i) = cos(2 pi k i / L) or sin(2 pi k i / L)
+// changes by at most D_k = 2 sin(pi k / L) under one exchange across a bond, so the states with
+// f_k in a band [m, m + D_k) separate {f_k < m} from {f_k >= m + D_k}.  The band is chosen near
+// the median to balance the halves, the separator is then thinned (a separator vertex with no
+// neighbour on one side moves to the other side), and the two halves are dissected recursively
+// with the next Fourier mode.  Subgraphs of at most LEAF vertices are ordered by minimum degree.
+//
+// Symbolic factorization.  Elimination tree (Liu), postorder, column counts from row subtrees,
+// fundamental supernodes, relaxed amalgamation, and supernodal row structures by merging the
+// children's update rows.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <numeric>
+
+#include "plan.h"
+
+namespace mbl {
+
+namespace {
+
+constexpr int LEAF = 64;
+
+struct Graph {
+    int64_t n;
+    const std::vector<int64_t> *rowptr;
+    const std::vector<int32_t> *col;
+};
+
+// Minimum degree on a small induced subgraph (<= 64 vertices, bitset elimination graph).
+void md_leaf(const Graph &g, const std::vector<int32_t> &V, std::vector<int32_t> &pos_in, std::vector<int32_t> &out) {
+    int k = (int)V.size();
+    for (int a = 0; a < k; ++a) pos_in[V[a]] = a;
+    std::vector<uint64_t> adj(k, 0);
+    for (int a = 0; a < k; ++a) {
+        int32_t v = V[a];
+        for (int64_t e = (*g.rowptr)[v]; e < (*g.rowptr)[v + 1]; ++e) {
+            int32_t u = (*g.col)[e];
+            int b = pos_in[u];
+            if (b >= 0 && b != a) adj[a] |= 1ull << b;
+        }
+    }
+    uint64_t alive = (k == 64) ? ~0ull : ((1ull << k) - 1);
+    for (int t = 0; t < k; ++t) {
+        int best = -1, bd = 1 << 30;
+        for (int a = 0; a < k; ++a)
+            if ((alive >> a) & 1) {
+                int d = __builtin_popcountll(adj[a] & alive);
+                if (d < bd) { bd = d; best = a; }
+            }
+        uint64_t N = adj[best] & alive & ~(1ull << best);
+        for (int a = 0; a < k; ++a)
+            if ((N >> a) & 1) adj[a] |= N & ~(1ull << a);
+        alive &= ~(1ull << best);
+        out.push_back(V[best]);
+    }
+    for (int a = 0; a < k; ++a) pos_in[V[a]] = -1;
+}
+
+struct ND {
+    const Graph &g;
+    int L;
+    const std::vector<uint32_t> &states;
+    std::vector<std::vector<double>> w;  // modes
+    std::vector<double> D;
+    std::vector<int8_t> part;            // scratch membership: 0 none, 1 V1, 2 V2, 3 S
+    std::vector<int32_t> pos_in;
+    std::vector<int32_t> order;
+
+    ND(const Graph &g_, int L_, const std::vector<uint32_t> &st) : g(g_), L(L_), states(st) {
+        for (int k = 1; k <= L; ++k) {
+            std::vector<double> c(L), s(L);
+            for (int i = 0; i < L; ++i) {
+                c[i] = std::cos(2.0 * M_PI * k * i / L);
+                s[i] = std::sin(2.0 * M_PI * k * i / L);
+            }
+            double d = 2.0 * std::sin(M_PI * k / L);
+            w.push_back(c); D.push_back(d);
+            w.push_back(s); D.push_back(d);
+        }
+        part.assign(g.n, 0);
+        pos_in.assign(g.n, -1);
+    }
+
+    double fval(int mode, uint32_t s) const {
+        double f = 0.0;
+        const std::vector<double> &wm = w[mode];
+        for (int i = 0; i < L; ++i)
+            if ((s >> i) & 1u) f += wm[i];
+        return f;
+    }
+
+    void run(std::vector<int32_t> V, int depth) {
+        if ((int)V.size() <= LEAF) {
+            md_leaf(g, V, pos_in, order);
+            return;
+        }
+        int N = (int)V.size();
+        // pick the mode and band of least cost |S| + 0.3 ||V1| - |V2||
+        double best_cost = 1e300, best_m = 0.0;
+        int best_mode = -1;
+        std::vector<double> f(N), fs(N);
+        for (int cand = 0; cand < 2; ++cand) {
+            int mode = std::min<int>(depth + cand, (int)w.size() - 1);
+            for (int a = 0; a < N; ++a) f[a] = fval(mode, states[V[a]]);
+            fs = f;
+            std::sort(fs.begin(), fs.end());
+            double Dm = D[mode];
+            for (int qi = 0; qi <= 40; ++qi) {
+                double q = 0.3 + 0.01 * qi;
+                double m = fs[(size_t)(q * (N - 1))] - 0.5 * Dm;
+                int64_t n1 = std::lower_bound(fs.begin(), fs.end(), m - 1e-12) - fs.begin();
+                int64_t nS = (std::lower_bound(fs.begin(), fs.end(), m + Dm - 1e-12) - fs.begin()) - n1;
+                int64_t n2 = N - n1 - nS;
+                double cost = (double)nS + 0.3 * (double)std::llabs(n1 - n2);
+                if (n1 == 0 || n2 == 0) cost = 1e300;
+                if (cost < best_cost) { best_cost = cost; best_m = m; best_mode = mode; }
+            }
+        }
+        if (best_mode < 0) {  // cannot split (degenerate values): fall back to minimum degree in chunks
+            std::vector<int32_t> chunk;
+            for (int a = 0; a < N; ++a) {
+                chunk.push_back(V[a]);
+                if ((int)chunk.size() == LEAF) { md_leaf(g, chunk, pos_in, order); chunk.clear(); }
+            }
+            if (!chunk.empty()) md_leaf(g, chunk, pos_in, order);
+            return;
+        }
+        double Dm = D[best_mode];
+        for (int a = 0; a < N; ++a) {
+            double fv = fval(best_mode, states[V[a]]);
+            part[V[a]] = fv < best_m - 1e-12 ? 1 : (fv < best_m + Dm - 1e-12 ? 3 : 2);
+        }
+        // thin the separator
+        for (int a = 0; a < N; ++a) {
+            int32_t v = V[a];
+            if (part[v] != 3) continue;
+            bool n1 = false, n2 = false;
+            for (int64_t e = (*g.rowptr)[v]; e < (*g.rowptr)[v + 1]; ++e) {
+                int8_t pu = part[(*g.col)[e]];
+                n1 |= pu == 1;
+                n2 |= pu == 2;
+            }
+            if (!n1) part[v] = 2;
+            else if (!n2) part[v] = 1;
+        }
+        std::vector<int32_t> V1, V2, S;
+        for (int a = 0; a < N; ++a) {
+            int8_t pv = part[V[a]];
+            (pv == 1 ? V1 : pv == 2 ? V2 : S).push_back(V[a]);
+        }
+        for (int a = 0; a < N; ++a) part[V[a]] = 0;
+        std::vector<int32_t>().swap(V);
+        run(std::move(V1), depth + 1);
+        run(std::move(V2), depth + 1);
+        for (int32_t v : S) order.push_back(v);
+    }
+};
+
+}  // namespace
+
+std::shared_ptr<Plan> build_plan(int L, const std::vector<uint32_t> &states, const std::vector<int64_t> &rowptr,
+                                 const std::vector<int32_t> &col) {
+    auto t0 = std::chrono::steady_clock::now();
+    auto P = std::make_shared<Plan>();
+    Plan &p = *P;
+    int64_t n = (int64_t)states.size();
+    p.L = L;
+    p.n = n;
+    p.nnzA = rowptr[n];
+    Graph g{n, &rowptr, &col};
+
+    // ---- 1. nested-dissection order ----
+    {
+        ND nd(g, L, states);
+        std::vector<int32_t> all(n);
+        std::iota(all.begin(), all.end(), 0);
+        nd.run(std::move(all), 0);
+        p.perm = std::move(nd.order);
+    }
+    if ((int64_t)p.perm.size() != n) fail(MBL_ERR_INVALID, "ordering lost vertices");
+
+    auto lower_lists = [&](const std::vector<int32_t> &perm, std::vector<int32_t> &iperm, std::vector<int64_t> &lp,
+                           std::vector<int32_t> &li) {
+        // li[lp[i]..lp[i+1]) = new neighbours k < i of new vertex i (ascending)
+        iperm.assign(n, -1);
+        for (int64_t k = 0; k < n; ++k) iperm[perm[k]] = (int32_t)k;
+        lp.assign(n + 1, 0);
+        for (int64_t r = 0; r < n; ++r) {
+            int32_t a = iperm[r];
+            for (int64_t e = rowptr[r]; e < rowptr[r + 1]; ++e) {
+                int32_t b = iperm[col[e]];
+                if (b < a) lp[a + 1]++;
+            }
+        }
+        for (int64_t i = 0; i < n; ++i) lp[i + 1] += lp[i];
+        li.assign(lp[n], 0);
+        std::vector<int64_t> fill(lp.begin(), lp.end() - 1);
+        for (int64_t r = 0; r < n; ++r) {
+            int32_t a = iperm[r];
+            for (int64_t e = rowptr[r]; e < rowptr[r + 1]; ++e) {
+                int32_t b = iperm[col[e]];
+                if (b < a) li[fill[a]++] = b;
+            }
+        }
+        for (int64_t i = 0; i < n; ++i) std::sort(li.begin() + lp[i], li.begin() + lp[i + 1]);
+    };
+    auto etree = [&](const std::vector<int64_t> &lp, const std::vector<int32_t> &li, std::vector<int32_t> &parent) {
+        parent.assign(n, -1);
+        std::vector<int32_t> anc(n, -1);
+        for (int64_t i = 0; i < n; ++i)
+            for (int64_t e = lp[i]; e < lp[i + 1]; ++e) {
+                int32_t r = li[e];
+                while (anc[r] != -1 && anc[r] != i) {
+                    int32_t t = anc[r];
+                    anc[r] = (int32_t)i;
+                    r = t;
+                }
+                if (anc[r] == -1) {
+                    anc[r] = (int32_t)i;
+                    parent[r] = (int32_t)i;
+                }
+            }
+    };
+
+    std::vector<int64_t> lp;
+    std::vector<int32_t> li, parent;
+    lower_lists(p.perm, p.iperm, lp, li);
+    etree(lp, li, parent);
+
+    // ---- 2. postorder (children visited in ascending order), compose with the ND order ----
+    {
+        std::vector<int32_t> head(n, -1), next(n, -1);
+        for (int64_t j = n - 1; j >= 0; --j)
+            if (parent[j] >= 0) {
+                next[j] = head[parent[j]];
+                head[parent[j]] = (int32_t)j;
+            }
+        std::vector<int32_t> post;
+        post.reserve(n);
+        std::vector<int32_t> stack;
+        for (int64_t r = 0; r < n; ++r) {
+            if (parent[r] != -1) continue;
+            stack.push_back((int32_t)r);
+            while (!stack.empty()) {
+                int32_t v = stack.back();
+                if (head[v] != -1) {
+                    int32_t c = head[v];
+                    head[v] = next[c];
+                    stack.push_back(c);
+                } else {
+                    stack.pop_back();
+                    post.push_back(v);
+                }
+            }
+        }
+        std::vector<int32_t> perm2(n);
+        for (int64_t k = 0; k < n; ++k) perm2[k] = p.perm[post[k]];
+        p.perm = std::move(perm2);
+    }
+    lower_lists(p.perm, p.iperm, lp, li);
+    etree(lp, li, parent);
+
+    // ---- 3. column counts (strictly lower) by row subtrees ----
+    std::vector<int64_t> cc(n, 0);
+    {
+        std::vector<int32_t> mark(n, -1);
+        for (int64_t i = 0; i < n; ++i) {
+            mark[i] = (int32_t)i;
+            for (int64_t e = lp[i]; e < lp[i + 1]; ++e) {
+                int32_t r = li[e];
+                while (mark[r] != i) {
+                    cc[r]++;
+                    mark[r] = (int32_t)i;
+                    r = parent[r];
+                }
+            }
+        }
+    }
+    std::vector<int32_t> nchild(n, 0);
+    for (int64_t j = 0; j < n; ++j)
+        if (parent[j] >= 0) nchild[parent[j]]++;
+
+    // ---- 4. fundamental supernodes ----
+    std::vector<int32_t> fs_start;
+    for (int64_t j = 0; j < n; ++j) {
+        bool cont = j > 0 && parent[j - 1] == j && cc[j - 1] == cc[j] + 1 && nchild[j] == 1;
+        if (!cont) fs_start.push_back((int32_t)j);
+    }
+    fs_start.push_back((int32_t)n);
+    int32_t nfs = (int32_t)fs_start.size() - 1;
+    std::vector<int32_t> col2fs(n);
+    for (int32_t s = 0; s < nfs; ++s)
+        for (int32_t j = fs_start[s]; j < fs_start[s + 1]; ++j) col2fs[j] = s;
+
+    // ---- 5. relaxed amalgamation on the supernode tree (postorder = column order) ----
+    // A supernode is [first, last] with front size f = nc + |update rows|; merging the child that
+    // ends at first-1 into its parent keeps columns contiguous.
+    struct SN {
+        int32_t first, last, parent;
+        int64_t f, true_nnz, stored;
+        bool alive;
+    };
+    std::vector<SN> sn(nfs);
+    for (int32_t s = 0; s < nfs; ++s) {
+        int32_t a = fs_start[s], b = fs_start[s + 1] - 1;
+        int64_t nc = b - a + 1;
+        int64_t f = nc + cc[b];
+        int64_t tn = 0;
+        for (int32_t j = a; j <= b; ++j) tn += cc[j] + 1;
+        sn[s] = SN{a, b, parent[b] >= 0 ? col2fs[parent[b]] : -1, f, tn, nc * f - nc * (nc - 1) / 2, true};
+    }
+    std::vector<int32_t> into(nfs);
+    std::iota(into.begin(), into.end(), 0);
+    auto find = [&](int32_t x) {
+        while (into[x] != x) {
+            into[x] = into[into[x]];
+            x = into[x];
+        }
+        return x;
+    };
+    for (int32_t s = 0; s < nfs; ++s) {
+        // repeatedly absorb the child ending right before our first column
+        while (sn[s].first > 0) {
+            int32_t c = col2fs[sn[s].first - 1];
+            if (!sn[c].alive || sn[c].parent < 0 || find(sn[c].parent) != s) break;
+            int64_t ncc = sn[c].last - sn[c].first + 1, ncp = sn[s].last - sn[s].first + 1;
+            int64_t nc = ncc + ncp;
+            int64_t f = ncc + sn[s].f;
+            int64_t stored = nc * f - nc * (nc - 1) / 2;
+            int64_t tn = sn[c].true_nnz + sn[s].true_nnz;
+            bool ok = (nc <= 16) || ((double)(stored - tn) <= 0.15 * (double)stored);
+            if (!ok) break;
+            sn[c].alive = false;
+            into[c] = s;
+            for (int32_t j = sn[c].first; j <= sn[c].last; ++j) col2fs[j] = s;
+            sn[s].first = sn[c].first;
+            sn[s].f = f;
+            sn[s].true_nnz = tn;
+            sn[s].stored = stored;
+        }
+    }
+    // renumber alive supernodes in column order
+    std::vector<int32_t> newid(nfs, -1);
+    int32_t ns = 0;
+    for (int32_t s = 0; s < nfs; ++s)
+        if (sn[s].alive) newid[s] = ns++;
+    p.ns = ns;
+    p.sn_start.assign(ns + 1, 0);
+    p.sn_nc.assign(ns, 0);
+    for (int32_t s = 0; s < nfs; ++s)
+        if (sn[s].alive) {
+            p.sn_start[newid[s]] = sn[s].first;
+            p.sn_nc[newid[s]] = sn[s].last - sn[s].first + 1;
+        }
+    p.sn_start[ns] = (int32_t)n;
+    p.col_snode.assign(n, 0);
+    for (int32_t s = 0; s < ns; ++s)
+        for (int32_t j = p.sn_start[s]; j < p.sn_start[s + 1]; ++j) p.col_snode[j] = s;
+
+    // ---- 6. row structures (own columns, then update rows ascending) and tree ----
+    p.sn_f.assign(ns, 0);
+    p.sn_parent.assign(ns, -1);
+    p.sn_rows_off.assign(ns + 1, 0);
+    std::vector<std::vector<int32_t>> upd(ns);
+    std::vector<std::vector<int32_t>> children(ns);
+    {
+        std::vector<int32_t> mark(n, -1);
+        for (int32_t s = 0; s < ns; ++s) {
+            int32_t a = p.sn_start[s], b = p.sn_start[s + 1] - 1;
+            std::vector<int32_t> &u = upd[s];
+            // columns of s appear as rows of later vertices: scan their lower lists is expensive;
+            // use the symmetric pattern: rows i > b adjacent to a column j in [a, b]
+            for (int32_t j = a; j <= b; ++j) {
+                int32_t r = p.perm[j];
+                for (int64_t e = rowptr[r]; e < rowptr[r + 1]; ++e) {
+                    int32_t i = p.iperm[col[e]];
+                    if (i > b && mark[i] != s) {
+                        mark[i] = s;
+                        u.push_back(i);
+                    }
+                }
+            }
+            for (int32_t c : children[s])
+                for (int32_t i : upd[c])
+                    if (i > b && mark[i] != s) {
+                        mark[i] = s;
+                        u.push_back(i);
+                    }
+            std::sort(u.begin(), u.end());
+            if (!u.empty()) {
+                int32_t ps = p.col_snode[u[0]];
+                p.sn_parent[s] = ps;
+                children[ps].push_back(s);
+            }
+            p.sn_f[s] = p.sn_nc[s] + (int32_t)u.size();
+        }
+    }
+    for (int32_t s = 0; s < ns; ++s) p.sn_rows_off[s + 1] = p.sn_rows_off[s] + p.sn_f[s];
+    p.rows.resize(p.sn_rows_off[ns]);
+    for (int32_t s = 0; s < ns; ++s) {
+        int64_t o = p.sn_rows_off[s];
+        for (int32_t t = 0; t < p.sn_nc[s]; ++t) p.rows[o + t] = p.sn_start[s] + t;
+        std::copy(upd[s].begin(), upd[s].end(), p.rows.begin() + o + p.sn_nc[s]);
+    }
+    p.ch_ptr.assign(ns + 1, 0);
+    for (int32_t s = 0; s < ns; ++s) p.ch_ptr[s + 1] = p.ch_ptr[s] + (int32_t)children[s].size();
+    p.ch_list.resize(p.ch_ptr[ns]);
+    for (int32_t s = 0; s < ns; ++s) std::copy(children[s].begin(), children[s].end(), p.ch_list.begin() + p.ch_ptr[s]);
+
+    // relative indices of each child's update rows in its parent's row list
+    p.sn_rel_off.assign(ns + 1, 0);
+    for (int32_t s = 0; s < ns; ++s) p.sn_rel_off[s + 1] = p.sn_rel_off[s] + (p.sn_f[s] - p.sn_nc[s]);
+    p.relind.resize(p.sn_rel_off[ns]);
+    for (int32_t s = 0; s < ns; ++s) {
+        int32_t ps = p.sn_parent[s];
+        if (ps < 0) continue;
+        const int32_t *pr = p.rows.data() + p.sn_rows_off[ps];
+        int32_t pf = p.sn_f[ps];
+        int32_t q = 0;
+        for (int32_t t = 0; t < p.sn_f[s] - p.sn_nc[s]; ++t) {
+            int32_t i = upd[s][t];
+            while (q < pf && pr[q] < i) ++q;
+            if (q >= pf || pr[q] != i) fail(MBL_ERR_INVALID, "symbolic: child row missing from parent front");
+            p.relind[p.sn_rel_off[s] + t] = q;
+        }
+    }
+
+    // ---- 7. levels, offsets, assembly map, statistics ----
+    p.sn_level.assign(ns, 0);
+    for (int32_t s = 0; s < ns; ++s)
+        for (int32_t c : children[s]) p.sn_level[s] = std::max(p.sn_level[s], p.sn_level[c] + 1);
+    p.nlevels = 0;
+    for (int32_t s = 0; s < ns; ++s) p.nlevels = std::max(p.nlevels, p.sn_level[s] + 1);
+    p.lvl_ptr.assign(p.nlevels + 1, 0);
+    for (int32_t s = 0; s < ns; ++s) p.lvl_ptr[p.sn_level[s] + 1]++;
+    for (int l = 0; l < p.nlevels; ++l) p.lvl_ptr[l + 1] += p.lvl_ptr[l];
+    p.lvl_fronts.resize(ns);
+    {
+        std::vector<int32_t> fill(p.lvl_ptr.begin(), p.lvl_ptr.end() - 1);
+        for (int32_t s = 0; s < ns; ++s) p.lvl_fronts[fill[p.sn_level[s]]++] = s;
+    }
+    p.sn_fo.assign(ns + 1, 0);
+    p.sn_zo.assign(ns + 1, 0);
+    for (int32_t s = 0; s < ns; ++s) {
+        int64_t f = p.sn_f[s];
+        p.sn_fo[s + 1] = p.sn_fo[s] + f * f;
+        p.sn_zo[s + 1] = p.sn_zo[s] + f;
+    }
+    p.arena_elems = p.sn_fo[ns];
+    p.zwork_elems = p.sn_zo[ns];
+    p.max_front = 0;
+    p.nnz_l = 0;
+    p.flops = 0.0;
+    for (int32_t s = 0; s < ns; ++s) {
+        int64_t f = p.sn_f[s], nc = p.sn_nc[s];
+        p.max_front = std::max<int32_t>(p.max_front, (int32_t)f);
+        p.nnz_l += nc * (nc - 1) / 2 + nc * (f - nc);
+        for (int64_t k = 0; k < nc; ++k) p.flops += (double)(f - k - 1) * (double)(f - k - 1);
+    }
+    // assembly map: CSR entry (r, c) with new indices a >= b goes to column b's front at local row of a
+    p.amap_ptr.assign(n + 1, 0);
+    for (int64_t r = 0; r < n; ++r)
+        for (int64_t e = rowptr[r]; e < rowptr[r + 1]; ++e) {
+            int32_t a = p.iperm[r], b = p.iperm[col[e]];
+            if (a >= b) p.amap_ptr[b + 1]++;
+        }
+    for (int64_t j = 0; j < n; ++j) p.amap_ptr[j + 1] += p.amap_ptr[j];
+    p.amap_src.resize(p.amap_ptr[n]);
+    p.amap_row.resize(p.amap_ptr[n]);
+    {
+        std::vector<int64_t> fill(p.amap_ptr.begin(), p.amap_ptr.end() - 1);
+        for (int64_t r = 0; r < n; ++r)
+            for (int64_t e = rowptr[r]; e < rowptr[r + 1]; ++e) {
+                int32_t a = p.iperm[r], b = p.iperm[col[e]];
+                if (a < b) continue;
+                int32_t s = p.col_snode[b];
+                const int32_t *pr = p.rows.data() + p.sn_rows_off[s];
+                int32_t lr = (int32_t)(std::lower_bound(pr, pr + p.sn_f[s], a) - pr);
+                if (lr >= p.sn_f[s] || pr[lr] != a) fail(MBL_ERR_INVALID, "symbolic: entry outside front");
+                int64_t q = fill[b]++;
+                p.amap_src[q] = e;
+                p.amap_row[q] = lr;
+            }
+    }
+    // assembly items and panel schedule per level
+    p.asm_ptr.assign(p.nlevels + 1, 0);
+    p.lvl_step_ptr.assign(p.nlevels + 1, 0);
+    for (int l = 0; l < p.nlevels; ++l) {
+        int32_t maxnc = 0;
+        for (int32_t q = p.lvl_ptr[l]; q < p.lvl_ptr[l + 1]; ++q) {
+            int32_t s = p.lvl_fronts[q];
+            for (int32_t c0 = 0; c0 < p.sn_f[s]; c0 += ACOLS) p.asm_items.push_back(AsmItem{s, c0});
+            maxnc = std::max(maxnc, p.sn_nc[s]);
+        }
+        p.asm_ptr[l + 1] = (int32_t)p.asm_items.size();
+        for (int32_t kk = 0; kk * NB < maxnc; ++kk) {
+            PanelStep stp{l, kk, (int32_t)p.descs.size(), 0, 0, 0, 0};
+            for (int32_t q = p.lvl_ptr[l]; q < p.lvl_ptr[l + 1]; ++q) {
+                int32_t s = p.lvl_fronts[q];
+                int32_t k0 = kk * NB;
+                if (p.sn_nc[s] <= k0) continue;
+                int32_t w = std::min(NB, p.sn_nc[s] - k0);
+                int32_t m2 = p.sn_f[s] - k0 - w;
+                PanelDesc d{s, k0, w, m2, stp.n2, stp.n3, stp.wsize};
+                int64_t nb2 = (m2 + RB - 1) / RB;
+                int64_t T = (m2 + TB - 1) / TB;
+                stp.n2 += nb2;
+                stp.n3 += T * (T + 1) / 2;
+                stp.wsize += (int64_t)m2 * NB;
+                p.descs.push_back(d);
+            }
+            stp.nd = (int32_t)p.descs.size() - stp.d0;
+            p.max_desc_per_step = std::max<int64_t>(p.max_desc_per_step, stp.nd);
+            p.max_step_n2 = std::max<int64_t>(p.max_step_n2, stp.n2);
+            p.wscratch_elems = std::max(p.wscratch_elems, stp.wsize);
+            p.steps.push_back(stp);
+        }
+        p.lvl_step_ptr[l + 1] = (int32_t)p.steps.size();
+    }
+    p.ms_analyse = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return P;
+}
+
+template <class T>
+static void up(Ctx *ctx, DVec<T> &d, const std::vector<T> &h) {
+    d.alloc(ctx, std::max<size_t>(h.size(), 1));
+    if (!h.empty()) MBL_CUDA(cudaMemcpy(d.data(), h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+}
+
+void upload_plan(Ctx *ctx, Plan &p) {
+    if (p.on_device) return;
+    up(ctx, p.d_perm, p.perm);
+    up(ctx, p.d_iperm, p.iperm);
+    up(ctx, p.d_sn_start, p.sn_start);
+    up(ctx, p.d_sn_nc, p.sn_nc);
+    up(ctx, p.d_sn_f, p.sn_f);
+    up(ctx, p.d_rows, p.rows);
+    up(ctx, p.d_relind, p.relind);
+    up(ctx, p.d_ch_ptr, p.ch_ptr);
+    up(ctx, p.d_ch_list, p.ch_list);
+    up(ctx, p.d_amap_row, p.amap_row);
+    up(ctx, p.d_sn_rows_off, p.sn_rows_off);
+    up(ctx, p.d_sn_fo, p.sn_fo);
+    up(ctx, p.d_sn_zo, p.sn_zo);
+    up(ctx, p.d_sn_rel_off, p.sn_rel_off);
+    up(ctx, p.d_amap_ptr, p.amap_ptr);
+    up(ctx, p.d_amap_src, p.amap_src);
+    up(ctx, p.d_asm_items, p.asm_items);
+    up(ctx, p.d_descs, p.descs);
+    p.on_device = true;
+}
+
+}  // namespace mbl

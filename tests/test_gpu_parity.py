@@ -1,0 +1,188 @@
+"""GPU path versus the CPU oracle, element by element, through the C ABI (needs a GB300).
+
+Bit-exact: fields, basis, ranks, CSR.  Floating point: eigenvalues within 1e-10 ||H||, the same
+window (ties at the edge accepted), residuals <= 1e-10 ||H||, observables within 1e-8 for
+well-conditioned eigenvectors (see parity.py).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from parity import EIG_TOL, OBS_TOL, well_conditioned, window_equivalent
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def g():
+    import paper_1411_0660_gb300 as g
+
+    return g
+
+
+@pytest.fixture(scope="module")
+def ctx(g):
+    return g.Context(0)
+
+
+# ---------------------------------------------------------------- bit-exact setup ----------
+@pytest.mark.parametrize("L", [2, 4, 6, 10, 14, 18, 22])
+def test_fields_basis_rank_bit_exact(g, ctx, orc, L):
+    sec = g.build_sector(ctx, L, 2.5, 1000 + L)
+    assert np.array_equal(sec.fields().view(np.uint64), orc.fields(L, 2.5, 1000 + L).view(np.uint64))
+    st = sec.basis()
+    assert sec.dim == math.comb(L, L // 2)
+    if L <= 20:
+        assert np.array_equal(st, orc.basis(L))
+    r = sec.rank(st)
+    assert np.array_equal(r, np.arange(sec.dim))
+    bad = np.array([0, (1 << L) - 1, 1, (1 << (L // 2 + 1)) - 1], dtype=np.uint32)
+    assert np.all(sec.rank(bad) == -1)
+
+
+@pytest.mark.parametrize("L,h,seed,J", [(2, 1.0, 3, 1.0), (4, 0.0, 0, 1.0), (8, 3.0, 5, 0.7), (12, 2.0, 0, 1.0),
+                                        (16, 5.0, 11, 1.0)])
+def test_csr_bit_exact(g, ctx, orc, L, h, seed, J):
+    hi = orc.fields(L, h, seed)
+    sec = g.build_sector_fields(ctx, L, hi, J) if J != 1.0 else g.build_sector(ctx, L, h, seed)
+    rp, col, val = sec.csr()
+    H = orc.csr(L, hi, J)
+    assert np.array_equal(rp, H.rowptr)
+    assert np.array_equal(col, H.col)
+    assert np.array_equal(val.view(np.uint64), H.val.view(np.uint64))
+
+
+def test_spmv(g, ctx, orc):
+    L = 14
+    sec = g.build_sector(ctx, L, 3.0, 2)
+    H = orc.csr(L, orc.fields(L, 3.0, 2))
+    X = np.random.default_rng(0).standard_normal((sec.dim, 5))
+    Y = sec.spmv(X, shift=0.37)
+    for q in range(5):
+        want = H.matvec(X[:, q], 0.37)
+        assert np.abs(Y[:, q] - want).max() <= 1e-13 * np.abs(want).max()
+
+
+# ---------------------------------------------------------------- extremal bounds ----------
+@pytest.mark.parametrize("L,h,seed", [(4, 1.0, 0), (8, 2.0, 1), (10, 0.5, 2), (12, 3.0, 3), (14, 5.0, 4)])
+def test_extremal_bounds(g, ctx, orc, L, h, seed):
+    sec = g.build_sector(ctx, L, h, seed)
+    lo, hi = g.extremal_bounds(sec)
+    H = orc.csr(L, orc.fields(L, h, seed))
+    if H.n <= 924:
+        w = orc.syev(H.dense(), vectors=False)
+        wlo, whi = w[0], w[-1]
+    else:
+        wlo, whi = orc.extremal_bounds(H)
+    hn = max(abs(wlo), abs(whi))
+    assert abs(lo - wlo) <= 1e-12 * hn and abs(hi - whi) <= 1e-12 * hn
+
+
+# ---------------------------------------------------------------- factorization -------------
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("L,h,seed,eps", [(12, 2.0, 0, 0.5), (14, 3.0, 1, 0.3), (16, 1.0, 2, 0.7)])
+def test_factor_solve_and_inertia(g, ctx, orc, prec, L, h, seed, eps):
+    sec = g.build_sector(ctx, L, h, seed)
+    lo, hi = g.extremal_bounds(sec)
+    sigma = lo + eps * (hi - lo)
+    f = g.factor(sec, sigma, precision=prec)
+    st = f.stats()
+    assert st["n"] == sec.dim and st["nnz_l"] > 0 and st["max_front"] > 0
+    H = orc.csr(L, orc.fields(L, h, seed))
+    B = np.random.default_rng(1).standard_normal((sec.dim, 3))
+    X = f.solve(B, refine=True)
+    hn = max(abs(lo), abs(hi))
+    for q in range(3):
+        r = H.matvec(X[:, q], sigma) - B[:, q]
+        assert np.linalg.norm(r) <= 1e-13 * ((hn + abs(sigma)) * np.linalg.norm(X[:, q]) + np.linalg.norm(B[:, q]))
+    if prec == 0 and L <= 14 and st["perturbed"] == 0:
+        w = orc.syev(H.dense(), vectors=False) if L <= 12 else None
+        if w is not None:
+            assert st["negative"] == int(np.sum(w < sigma))
+
+
+# ---------------------------------------------------------------- eigenpairs + observables ---
+def _check_job(g, ctx, orc, L, h, seed, eps, nev, prec, spectrum=None, block=8):
+    sec = g.build_sector(ctx, L, h, seed)
+    res = g.solve_near(sec, eps, nev, precision=prec, block=block)
+    H = orc.csr(L, orc.fields(L, h, seed))
+    if spectrum is None:
+        spectrum = orc.syev(H.dense(), vectors=False)
+    hn = max(abs(spectrum[0]), abs(spectrum[-1]))
+    sigma = spectrum[0] + eps * (spectrum[-1] - spectrum[0])
+    assert abs(res.sigma - sigma) <= 1e-12 * hn
+    assert res.nconv == nev
+    assert window_equivalent(res.evals, spectrum, sigma, nev, hn)
+    # residuals recomputed with the oracle's H
+    Y = res.evecs
+    for j in range(nev):
+        r = np.linalg.norm(H.matvec(Y[:, j]) - res.evals[j] * Y[:, j])
+        assert r <= EIG_TOL * hn
+        assert abs(np.linalg.norm(Y[:, j]) - 1) < 1e-12
+    assert np.abs(Y.T @ Y - np.eye(nev)).max() < 1e-10
+    # observables on the GPU versus the oracle on the same (GPU) eigenvectors' definitions
+    r_g, rm_g, s1_g, se_g = g.observables(ctx, L, res.evals, res.evecs)
+    r_o, rm_o = orc.gap_ratio(res.evals)
+    assert np.allclose(r_g, r_o, atol=1e-12, equal_nan=True)
+    mask = well_conditioned(spectrum, res.evals, res.resid)
+    st = orc.basis(L)
+    for j in np.nonzero(mask)[0]:
+        assert abs(s1_g[j] - orc.s1p(Y[:, j])) <= OBS_TOL
+        assert abs(se_g[j] - orc.entanglement(L, Y[:, j], st)) <= OBS_TOL
+    return res, spectrum, hn
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_config_L12_h2_seed0(g, ctx, orc, prec):
+    """Headline small case: L=12, h=2.0, seed 0, eps=0.5, nev=20 (FP64 and FP32 fronts)."""
+    res, spectrum, hn = _check_job(g, ctx, orc, 12, 2.0, 0, 0.5, 20, prec)
+    # oracle eigenpairs and observables on the oracle's own eigenvectors
+    job = orc.solve_job(orc.Job(12, 2.0, 0, 0.5, 20), "dense")
+    assert np.abs(np.sort(res.evals) - job.evals).max() <= EIG_TOL * hn
+    mask = well_conditioned(spectrum, job.evals, job.resid) & well_conditioned(spectrum, res.evals, res.resid)
+    _, _, s1_g, se_g = g.observables(ctx, 12, res.evals, res.evecs)
+    assert np.all(np.abs(s1_g - job.s1p)[mask] <= OBS_TOL)
+    assert np.all(np.abs(se_g - job.se)[mask] <= OBS_TOL)
+    assert abs(np.nanmean(job.r) - np.nanmean(orc.gap_ratio(res.evals)[0])) <= 1e-8
+
+
+@pytest.mark.parametrize("L,h,seed,eps,nev,prec", [(12, 0.5, 3, 0.1, 20, 1), (12, 5.0, 4, 0.9, 30, 1),
+                                                   (14, 3.0, 5, 0.5, 50, 1), (14, 1.0, 6, 0.2, 50, 0),
+                                                   (12, 4.0, 7, 0.0, 10, 1), (12, 4.0, 7, 1.0, 10, 1)])
+def test_solve_near_matrix(g, ctx, orc, L, h, seed, eps, nev, prec):
+    _check_job(g, ctx, orc, L, h, seed, eps, nev, prec)
+
+
+@pytest.mark.parametrize("block", [1, 4, 16])
+def test_block_sizes(g, ctx, orc, block):
+    _check_job(g, ctx, orc, 12, 2.5, 8, 0.6, 16, 1, block=block)
+
+
+@pytest.mark.parametrize("L,nev", [(2, 1), (2, 2), (4, 6), (6, 5), (8, 12), (10, 40)])
+def test_dense_route_small_sectors(g, ctx, orc, L, nev):
+    _check_job(g, ctx, orc, L, 1.5, 9, 0.5, nev, 1)
+
+
+def test_observables_on_oracle_vectors(g, ctx, orc):
+    job = orc.solve_job(orc.Job(12, 3.0, 2, 0.4, 20), "dense")
+    r, rm, s1, se = g.observables(ctx, 12, job.evals, job.evecs)
+    assert np.allclose(r, job.r, atol=1e-13, equal_nan=True)
+    assert abs(rm - job.r_mean) < 1e-13
+    assert np.abs(s1 - job.s1p).max() < 1e-11
+    assert np.abs(se - job.se).max() < 1e-11
+
+
+def test_invalid_arguments(g, ctx):
+    with pytest.raises(g.MblError) as e:
+        g.build_sector(ctx, 7, 1.0, 0)
+    assert e.value.code == 1
+    with pytest.raises(g.MblError):
+        g.build_sector(ctx, 24, 1.0, 0)
+    sec = g.build_sector(ctx, 12, 1.0, 0)
+    with pytest.raises(g.MblError):
+        g.solve_near(sec, 1.5, 10)
+    with pytest.raises(g.MblError):
+        g.solve_near(sec, 0.5, 0)
+    with pytest.raises(g.MblError):
+        g.solve_near(sec, 0.5, sec.dim + 1)
