@@ -96,6 +96,17 @@ const char *mbl_version(void);
 const char *mbl_last_error(mbl_ctx *ctx);
 const char *mbl_status_string(int status);
 
+/* Number of kernels this library has launched since it was loaded (all contexts). */
+long long mbl_launch_count(void);
+/* Opt-in device timing by kernel class with CUDA events on the launching stream.  Turning it on
+ * or off clears the totals.  Classes: "factor_fp32" / "factor_fp64" (whole numeric factorization,
+ * work = algorithmic flops), "schur_fp32" / "schur_fp64" (trailing updates, flops),
+ * "trisolve_fp32" / "trisolve_fp64" (forward + backward solve of one block, work = algorithmic
+ * bytes: factor read twice plus the right-hand sides), "refine_spmv" (FP64 residual SpMV, bytes),
+ * "orth" (block Gram-Schmidt, FP64 flops). */
+int mbl_ctx_set_profiling(mbl_ctx *ctx, int on);
+int mbl_ctx_profile_get(mbl_ctx *ctx, const char *name, int64_t *launches, double *ms, double *work);
+
 /* Context on CUDA device `device` with a memory budget (0 = no limit) used for admission. */
 int mbl_ctx_create(int device, size_t hbm_budget_bytes, mbl_ctx **out);
 void mbl_ctx_destroy(mbl_ctx *ctx);

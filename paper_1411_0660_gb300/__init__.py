@@ -22,7 +22,7 @@ from ._capi import MBL_PREC_FP32, MBL_PREC_FP64, FactorStats, Opts, SolveStats
 
 __all__ = ["Context", "Sector", "Factorization", "MblError", "build_sector", "build_sector_fields",
            "extremal_bounds", "factor", "solve_near", "solve_near_dev", "observables", "observables_dev",
-           "default_opts", "MBL_PREC_FP32", "MBL_PREC_FP64"]
+           "default_opts", "launch_count", "MBL_PREC_FP32", "MBL_PREC_FP64"]
 
 
 class MblError(RuntimeError):
@@ -58,6 +58,15 @@ class Context:
         h = ctypes.c_void_p()
         _check(_lib().mbl_ctx_create(device, hbm_budget_bytes, ctypes.byref(h)))
         self.handle = h
+
+    def set_profiling(self, on: bool = True):
+        _check(_lib().mbl_ctx_set_profiling(self.handle, 1 if on else 0), self.handle)
+
+    def profile(self, name: str) -> dict:
+        n, ms, w = ctypes.c_int64(), ctypes.c_double(), ctypes.c_double()
+        _check(_lib().mbl_ctx_profile_get(self.handle, name.encode(), ctypes.byref(n), ctypes.byref(ms),
+                                          ctypes.byref(w)), self.handle)
+        return {"launches": n.value, "ms": ms.value, "work": w.value}
 
     def synchronize(self):
         _check(_lib().mbl_ctx_synchronize(self.handle), self.handle)
@@ -122,6 +131,11 @@ class Sector:
             self.close()
         except Exception:
             pass
+
+
+def launch_count() -> int:
+    """Kernels launched by the library so far (all contexts)."""
+    return int(_lib().mbl_launch_count())
 
 
 def build_sector(ctx: Context, L: int, h: float, seed: int) -> Sector:

@@ -45,6 +45,9 @@ SIGNATURES = [
     ("mbl_version", ctypes.c_char_p, []),
     ("mbl_last_error", ctypes.c_char_p, [c_void_p]),
     ("mbl_status_string", ctypes.c_char_p, [c_int]),
+    ("mbl_launch_count", ctypes.c_longlong, []),
+    ("mbl_ctx_set_profiling", c_int, [c_void_p, c_int]),
+    ("mbl_ctx_profile_get", c_int, [c_void_p, ctypes.c_char_p, P(c_int64), P(c_double), P(c_double)]),
     ("mbl_ctx_create", c_int, [c_int, c_size_t, P(c_void_p)]),
     ("mbl_ctx_destroy", None, [c_void_p]),
     ("mbl_ctx_synchronize", c_int, [c_void_p]),

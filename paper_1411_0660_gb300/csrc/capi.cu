@@ -8,6 +8,50 @@
 
 namespace mbl {
 
+std::atomic<long long> g_launches{0};
+
+cudaEvent_t Ctx::take_event() {
+    if (!event_pool.empty()) {
+        cudaEvent_t e = event_pool.back();
+        event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    MBL_CUDA(cudaEventCreate(&e));
+    return e;
+}
+
+void Ctx::resolve_profile() {
+    for (auto &kv : profile) {
+        ProfAcc &a = kv.second;
+        for (auto &pd : a.pending) {
+            MBL_CUDA(cudaEventSynchronize(pd.e1));
+            float ms = 0.f;
+            MBL_CUDA(cudaEventElapsedTime(&ms, pd.e0, pd.e1));
+            a.ms += ms;
+            a.work += pd.work;
+            a.launches += 1;
+            event_pool.push_back(pd.e0);
+            event_pool.push_back(pd.e1);
+        }
+        a.pending.clear();
+    }
+}
+
+ProfScope::ProfScope(Ctx *c_, const char *name_, double work_, cudaStream_t st_) : c(c_), name(name_), work(work_), st(st_) {
+    if (c && c->prof) {
+        e0 = c->take_event();
+        MBL_CUDA(cudaEventRecord(e0, st));
+    }
+}
+
+ProfScope::~ProfScope() {
+    if (!e0) return;
+    cudaEvent_t e1 = c->take_event();
+    cudaEventRecord(e1, st);
+    c->profile[name].pending.push_back(ProfAcc::Pending{e0, e1, work});
+}
+
 DevMem &DevMem::operator=(DevMem &&o) noexcept {
     if (this != &o) {
         release();
@@ -80,7 +124,10 @@ std::unique_ptr<Factorization> make_factorization(mbl_sector *sec, double sigma,
     MBL_CUDA(cudaEventCreate(&e0));
     MBL_CUDA(cudaEventCreate(&e1));
     MBL_CUDA(cudaEventRecord(e0, st));
-    numeric_factor(*F, st);
+    {
+        ProfScope ps(sec->ctx, prec == MBL_PREC_FP64 ? "factor_fp64" : "factor_fp32", F->plan->flops, st);
+        numeric_factor(*F, st);
+    }
     MBL_CUDA(cudaEventRecord(e1, st));
     MBL_CUDA(cudaEventSynchronize(e1));
     float ms = 0.f;
@@ -180,10 +227,34 @@ int mbl_ctx_create(int device, size_t budget, mbl_ctx **out) {
     return MBL_OK;
 }
 
+long long mbl_launch_count(void) { return mbl::g_launches.load(); }
+
+int mbl_ctx_set_profiling(mbl_ctx *ctx, int on) {
+    if (!ctx) return report(nullptr, MBL_ERR_INVALID, "ctx is NULL");
+    API_TRY
+    ctx->resolve_profile();
+    ctx->profile.clear();
+    ctx->prof = on != 0;
+    API_CATCH(ctx)
+}
+
+int mbl_ctx_profile_get(mbl_ctx *ctx, const char *name, int64_t *launches, double *ms, double *work) {
+    if (!ctx || !name) return report(ctx, MBL_ERR_INVALID, "NULL argument");
+    API_TRY
+    ctx->resolve_profile();
+    auto it = ctx->profile.find(name);
+    if (launches) *launches = it == ctx->profile.end() ? 0 : it->second.launches;
+    if (ms) *ms = it == ctx->profile.end() ? 0.0 : it->second.ms;
+    if (work) *work = it == ctx->profile.end() ? 0.0 : it->second.work;
+    API_CATCH(ctx)
+}
+
 void mbl_ctx_destroy(mbl_ctx *ctx) {
     if (!ctx) return;
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
+    try { ctx->resolve_profile(); } catch (...) {}
+    for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
     ctx->plans.clear();
     ctx->ent.clear();
     cudaStreamDestroy(ctx->stream);

@@ -546,6 +546,10 @@ static void factor_impl(Factorization &fz, cudaStream_t st) {
                 MBL_LAUNCH_CHECK();
             }
             if (stp.n3 > 0) {
+                double fl = 0.0;  // algorithmic flops: lower triangle of the trailing block, 2 per entry per k
+                for (int q = stp.d0; q < stp.d0 + stp.nd; ++q)
+                    fl += (double)p.descs[q].m2 * (p.descs[q].m2 + 1) * p.descs[q].w;
+                ProfScope ps(fz.ctx, sizeof(T) == 8 ? "schur_fp64" : "schur_fp32", fl, st);
                 k_panel_update<T><<<(unsigned)stp.n3, 256, 0, st>>>(dd, stp.nd, p.d_sn_fo.data(), p.d_sn_f.data(), arena,
                                                                     wscr);
                 MBL_LAUNCH_CHECK();
@@ -581,6 +585,8 @@ static void solve_impl(Factorization &fz, const double *B, int64_t ldb, double *
         MBL_CUDA(cudaFuncSetAttribute(k_bwd_partial<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024));
         attr = true;
     }
+    ProfScope ps(fz.ctx, sizeof(T) == 8 ? "trisolve_fp64" : "trisolve_fp32",
+                 2.0 * (double)(pl.nnz_l + n) * sizeof(T) + 16.0 * (double)n * p, st);
     k_perm_in<T><<<g, 256, 0, st>>>(n, p, pl.d_perm.data(), B, ldb, y);
     MBL_LAUNCH_CHECK();
     for (int l = 0; l < pl.nlevels; ++l) {

@@ -267,6 +267,7 @@ void KrylovSchur::orthonormalize_new_block(int m, cudaStream_t st, bool *deflate
 
 void KrylovSchur::start(uint64_t seed, cudaStream_t st) {
     k_zero<<<nblk((int64_t)ldv * ldv), 256, 0, st>>>(T.data(), (int64_t)ldv * ldv);
+    MBL_LAUNCH_CHECK();
     for (int attempt = 0; attempt < 4; ++attempt) {
         k_random_block<<<nblk(n * p), 256, 0, st>>>(n, p, seed + 7919ull * attempt, W.data(), p, 0);
         MBL_LAUNCH_CHECK();
@@ -283,6 +284,7 @@ void KrylovSchur::expand(const OpFn &op, cudaStream_t st) {
     int j = m - p;  // last (unexpanded) block
     op(V.data() + j, ldv, W.data(), st);
     double *Vd = V.data();
+    ProfScope ps(ctx, "orth", 8.0 * (double)n * m * p, st);
     dense_tn(n, Vd, ldv, 0, m, W.data(), p, 0, p, C1.data(), work.data(), st);
     dense_nn_sub(n, Vd, ldv, 0, m, C1.data(), p, W.data(), st);
     dense_tn(n, Vd, ldv, 0, m, W.data(), p, 0, p, C2.data(), work.data(), st);
@@ -300,10 +302,11 @@ void KrylovSchur::expand(const OpFn &op, cudaStream_t st) {
         }
         if (defl) fail(MBL_ERR_INVALID, "Krylov basis cannot be extended (sector too small for the basis)");
         k_zero_R_block<<<1, 1024, 0, st>>>(T.data(), ldv, m, j, p);
+        MBL_LAUNCH_CHECK();
     } else {
         k_write_R<<<1, 1024, 0, st>>>(T.data(), ldv, m, j, p, Rm.data());
+        MBL_LAUNCH_CHECK();
     }
-    MBL_LAUNCH_CHECK();
     copy_cols(n, W.data(), p, 0, V.data(), ldv, m, p, st);
     m += p;
 }
@@ -329,12 +332,14 @@ void KrylovSchur::restart(const std::vector<int> &keep_idx, cudaStream_t st) {
     int k = (int)keep_idx.size();
     MBL_CUDA(cudaMemcpyAsync(keep.data(), keep_idx.data(), k * sizeof(int), cudaMemcpyHostToDevice, st));
     k_gather_S<<<nblk((int64_t)mm * k), 256, 0, st>>>(eigA.data(), mm, keep.data(), k, SK.data());
+    MBL_LAUNCH_CHECK();
     k_Bk<<<nblk((int64_t)p * k), 256, 0, st>>>(T.data(), ldv, mm, p, SK.data(), k, Bk.data());
     MBL_LAUNCH_CHECK();
     dense_nn(n, V.data(), ldv, mm, SK.data(), k, V2.data(), ldv, 0, st);
     copy_cols(n, V.data(), ldv, mm, V2.data(), ldv, k, p, st);
     std::swap(V, V2);
     k_zero<<<nblk((int64_t)ldv * ldv), 256, 0, st>>>(T.data(), (int64_t)ldv * ldv);
+    MBL_LAUNCH_CHECK();
     k_restart_T<<<nblk((int64_t)(k + p) * (k + p)), 256, 0, st>>>(T.data(), ldv, k, p, eigW.data(), keep.data(), Bk.data());
     MBL_LAUNCH_CHECK();
     m = k + p;
@@ -356,8 +361,12 @@ void RefinedSolve::apply(const double *X, int ldx, double *Y, int p, cudaStream_
     int stall = 0;
     std::vector<double> h(3 * p);
     for (int it = 0; it <= max_refine; ++it) {
-        k_refine_resid<<<nb, 256, 0, st>>>(n, sec->rowptr.data(), sec->col.data(), sec->val.data(), fz->sigma, X, ldx,
-                                           Y, R.data(), p, part.data());
+        {
+            ProfScope ps(sec->ctx, "refine_spmv", 12.0 * (double)sec->nnz + 8.0 * (double)n * (3.0 * p + 1.0), st);
+            k_refine_resid<<<nb, 256, 0, st>>>(n, sec->rowptr.data(), sec->col.data(), sec->val.data(), fz->sigma, X,
+                                               ldx, Y, R.data(), p, part.data());
+        }
+        MBL_LAUNCH_CHECK();
         k_reduce_parts<<<1, 128, 0, st>>>((int)nb, 3 * p, part.data(), norms.data());
         MBL_LAUNCH_CHECK();
         MBL_CUDA(cudaMemcpyAsync(h.data(), norms.data(), 3 * p * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -512,12 +521,14 @@ void solve_near(mbl_sector *sec, double eps, int nev, const mbl_opts &o, double 
         HY.alloc(ctx, (size_t)n * nev);
         th.alloc(ctx, nev);
         k_cm_to_rm<<<nblk(n * nev), 256, 0, st>>>(n, nev, d_evecs, Yr.data());
+        MBL_LAUNCH_CHECK();
         launch_spmv(sec, 0.0, Yr.data(), nev, 1, HY.data(), nev, 1, nev, st);
         MBL_CUDA(cudaMemcpyAsync(th.data(), ev.data(), nev * sizeof(double), cudaMemcpyHostToDevice, st));
         unsigned nb = nblk(n * nev);
         part.alloc(ctx, (size_t)nb * 2 * nev);
         nrm.alloc(ctx, 2 * nev);
         k_pair_resid<<<nb, 256, 2 * nev * sizeof(double), st>>>(n, nev, Yr.data(), HY.data(), th.data(), part.data());
+        MBL_LAUNCH_CHECK();
         k_reduce_parts<<<nblk(2 * nev), 256, 0, st>>>((int)nb, 2 * nev, part.data(), nrm.data());
         MBL_LAUNCH_CHECK();
         std::vector<double> hn2(2 * nev), rr(nev);
@@ -632,6 +643,7 @@ void solve_near(mbl_sector *sec, double eps, int nev, const mbl_opts &o, double 
         MBL_CUDA(cudaMemcpyAsync(didx.data(), idx.data(), nev * sizeof(int), cudaMemcpyHostToDevice, st));
         SKs.alloc(ctx, (size_t)mb * nev);
         k_gather_S<<<nblk((int64_t)mb * nev), 256, 0, st>>>(Gs.data(), mb, didx.data(), nev, SKs.data());
+        MBL_LAUNCH_CHECK();
         Ydev.alloc(ctx, (size_t)n * nev);
         dense_nn(n, ks.V.data(), ks.ldv, mb, SKs.data(), nev, Ydev.data(), nev, 0, st);
         HY.alloc(ctx, (size_t)n * nev);
@@ -643,7 +655,9 @@ void solve_near(mbl_sector *sec, double eps, int nev, const mbl_opts &o, double 
         part.alloc(ctx, (size_t)nb * 2 * nev);
         nrm.alloc(ctx, 2 * nev);
         k_pair_resid<<<nb, 256, 2 * nev * sizeof(double), st>>>(n, nev, Ydev.data(), HY.data(), thd.data(), part.data());
+        MBL_LAUNCH_CHECK();
         k_reduce_parts<<<nblk(2 * nev), 256, 0, st>>>((int)nb, 2 * nev, part.data(), nrm.data());
+        MBL_LAUNCH_CHECK();
         k_scale_cols_to_cm<<<nblk(n * nev), 256, 0, st>>>(n, nev, Ydev.data(), nrm.data(), d_evecs);
         MBL_LAUNCH_CHECK();
         std::vector<double> hn2(2 * nev);

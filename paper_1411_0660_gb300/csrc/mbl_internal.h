@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 #include <map>
 #include <memory>
@@ -28,7 +29,14 @@ struct Error {
                                           " at " + __FILE__ + ":" + std::to_string(__LINE__)); \
     } while (0)
 
-#define MBL_LAUNCH_CHECK() MBL_CUDA(cudaGetLastError())
+// Every kernel launch of the library is followed by exactly one MBL_LAUNCH_CHECK(), which also
+// counts it (mbl_launch_count).
+extern std::atomic<long long> g_launches;
+#define MBL_LAUNCH_CHECK()                                           \
+    do {                                                             \
+        ::mbl::g_launches.fetch_add(1, std::memory_order_relaxed);   \
+        MBL_CUDA(cudaGetLastError());                                \
+    } while (0)
 
 struct Ctx;
 
@@ -63,6 +71,17 @@ struct DVec {
     size_t size() const { return n; }
 };
 
+// Opt-in per-class device timing with CUDA events on the launching stream.
+struct ProfAcc {
+    struct Pending {
+        cudaEvent_t e0, e1;
+        double work;
+    };
+    std::vector<Pending> pending;
+    int64_t launches = 0;
+    double ms = 0.0, work = 0.0;
+};
+
 struct Plan;       // symbolic analysis, symbolic.cpp
 struct EntTables;  // entanglement block tables, observables.cu
 
@@ -76,6 +95,22 @@ struct Ctx {
     std::map<int, std::shared_ptr<Plan>> plans;     // per L
     std::map<int, std::shared_ptr<EntTables>> ent;  // per L
     int sm_count = 0;
+    bool prof = false;
+    std::map<std::string, ProfAcc> profile;
+    std::vector<cudaEvent_t> event_pool;
+    cudaEvent_t take_event();
+    void resolve_profile();
+};
+
+// Times the enclosed launches on `st` under class `name` when profiling is on.
+struct ProfScope {
+    Ctx *c;
+    const char *name;
+    double work;
+    cudaStream_t st;
+    cudaEvent_t e0 = nullptr;
+    ProfScope(Ctx *c_, const char *name_, double work_, cudaStream_t st_);
+    ~ProfScope();
 };
 
 }  // namespace mbl

@@ -223,7 +223,9 @@ void build_sector_device(mbl_sector *sec, cudaStream_t st) {
     DVec<int64_t> bsum;
     bsum.alloc(ctx, nb + 1);
     k_scan_blocksum<<<(unsigned)nb, SCAN_B, 0, st>>>(counts.data(), n, bsum.data());
+    MBL_LAUNCH_CHECK();
     k_scan_serial<<<1, 32, 0, st>>>(bsum.data(), nb);
+    MBL_LAUNCH_CHECK();
     k_scan_apply<<<(unsigned)nb, SCAN_B, 0, st>>>(counts.data(), n, bsum.data(), sec->rowptr.data());
     MBL_LAUNCH_CHECK();
     MBL_CUDA(cudaMemcpyAsync(&sec->nnz, sec->rowptr.data() + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));

@@ -37,7 +37,9 @@ def test_fields_basis_rank_bit_exact(g, ctx, orc, L):
         assert np.array_equal(st, orc.basis(L))
     r = sec.rank(st)
     assert np.array_equal(r, np.arange(sec.dim))
-    bad = np.array([0, (1 << L) - 1, 1, (1 << (L // 2 + 1)) - 1], dtype=np.uint32)
+    # wrong popcount (0, all up, L/2 + 1 up) or a bit beyond the chain
+    bad = np.array([0, (1 << L) - 1, (1 << (L // 2 + 1)) - 1, ((1 << (L // 2)) - 1) << (32 - L // 2)],
+                   dtype=np.uint32)
     assert np.all(sec.rank(bad) == -1)
 
 
@@ -103,14 +105,25 @@ def test_factor_solve_and_inertia(g, ctx, orc, prec, L, h, seed, eps):
 
 
 # ---------------------------------------------------------------- eigenpairs + observables ---
-def _check_job(g, ctx, orc, L, h, seed, eps, nev, prec, spectrum=None, block=8):
+def _reference(orc, H, L, eps, nev):
+    """Oracle spectrum around sigma: the full dense spectrum up to L = 12, else the nev + 12
+    eigenvalues nearest sigma from the oracle's shift-invert path (enough to test the window and the
+    gaps of every wanted level)."""
+    if H.n <= 924:
+        w = orc.syev(H.dense(), vectors=False)
+        return w, w[0] + eps * (w[-1] - w[0]), max(abs(w[0]), abs(w[-1]))
+    emin, emax = orc.extremal_bounds(H)
+    sigma = emin + eps * (emax - emin)
+    hn = max(abs(emin), abs(emax))
+    e = orc.nearest_shift_invert(H, sigma, min(H.n, nev + 12), hn)
+    return e.evals, sigma, hn
+
+
+def _check_job(g, ctx, orc, L, h, seed, eps, nev, prec, block=8):
     sec = g.build_sector(ctx, L, h, seed)
     res = g.solve_near(sec, eps, nev, precision=prec, block=block)
     H = orc.csr(L, orc.fields(L, h, seed))
-    if spectrum is None:
-        spectrum = orc.syev(H.dense(), vectors=False)
-    hn = max(abs(spectrum[0]), abs(spectrum[-1]))
-    sigma = spectrum[0] + eps * (spectrum[-1] - spectrum[0])
+    spectrum, sigma, hn = _reference(orc, H, L, eps, nev)
     assert abs(res.sigma - sigma) <= 1e-12 * hn
     assert res.nconv == nev
     assert window_equivalent(res.evals, spectrum, sigma, nev, hn)
