@@ -282,6 +282,7 @@ __global__ void __launch_bounds__(EIG_THREADS) k_syev(const int *mv, const int64
     double *e2 = work + 5 * m;
     double *Z = work + 8 * m;                 // m x m
     double *scr = Z + (size_t)m * m;          // m x m scratch
+    if (threadIdx.x == 0 && info) info[b] = 0;
     if (m <= 0) return;
     if (m == 1) {
         if (threadIdx.x == 0) {

@@ -289,7 +289,10 @@ __global__ void __launch_bounds__(256) k_panel_update(const PanelDesc *descs, in
 }
 
 // ------------------------------------------------------------------------------------------
-// Triangular solves (row-major n x p blocks, p <= 32), multifrontal order.
+// Triangular solves (row-major n x p blocks, p <= 32) in multifrontal order, SPW-wide solve
+// panels.  Per solve panel: forward z_panel <- M z_panel then z_below -= L21 z_panel; backward
+// z_panel <- M^T (z_panel - L21^T x_below).  Own rows of a front hold pivoted-order values
+// between the two sweeps (Zs / yfw); the backward sweep leaves true-order values.
 // ------------------------------------------------------------------------------------------
 template <class T>
 __global__ void k_perm_in(int64_t n, int p, const int32_t *perm, const double *B, int64_t ldb, T *y) {
@@ -309,6 +312,70 @@ __global__ void k_perm_out(int64_t n, int p, const int32_t *perm, const T *x, do
     double v = (double)x[idx];
     double *dst = X + (int64_t)perm[k] * ldx + q;
     *dst = accumulate ? *dst + v : v;
+}
+
+__device__ __forceinline__ int find_sdesc(const SolveDesc *d, int nd, int64_t b) {
+    int lo = 0, hi = nd - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (d[mid].off <= b) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// M of one solve panel, 32 columns per CTA: the forward sequence applied to unit vectors.
+template <class T>
+__global__ void __launch_bounds__(256) k_build_m(const SolveDesc *sdescs, const int64_t *fo, const int32_t *fsz,
+                                                 const int32_t *sn_start, const T *arena, const int32_t *piv,
+                                                 const T *linv_all, T *Mall) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T(*Zc)[33] = reinterpret_cast<T(*)[33]>(smraw);                             // SPW x 33
+    T(*Zp)[33] = reinterpret_cast<T(*)[33]>(smraw + sizeof(T) * SPW * 33);      // NB x 33
+    T(*Li)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(smraw + sizeof(T) * (SPW + NB) * 33);
+    const SolveDesc d = sdescs[blockIdx.x];
+    const int c0 = blockIdx.y * 32;
+    if (c0 >= d.w) return;
+    const int ncol = min(32, d.w - c0), w = d.w, s = d.front, f = fsz[s], k0 = d.k0;
+    const T *F = arena + fo[s];
+    const int64_t g0 = (int64_t)sn_start[s] + k0;
+    for (int idx = threadIdx.x; idx < w * 32; idx += blockDim.x) {
+        int r = idx / 32, c = idx % 32;
+        Zc[r][c] = (c < ncol && r == c0 + c) ? T(1) : T(0);
+    }
+    __syncthreads();
+    for (int u = 0; u < SUBS; ++u) {
+        if (d.fdesc[u] < 0) break;
+        const int s0 = u * NB, ws = min(NB, w - s0);
+        const T *Lsrc = linv_all + (int64_t)d.fdesc[u] * NB * NB;
+        for (int idx = threadIdx.x; idx < ws * ws; idx += blockDim.x) {
+            int t = idx / ws, k = idx % ws;
+            Li[t][k] = Lsrc[t * NB + k];
+        }
+        for (int idx = threadIdx.x; idx < ws * 32; idx += blockDim.x) {
+            int t = idx / 32, c = idx % 32;
+            Zp[t][c] = Zc[piv[g0 + s0 + t] - k0][c];
+        }
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < ws * 32; idx += blockDim.x) {
+            int t = idx / 32, c = idx % 32;
+            T acc = T(0);
+            for (int k = 0; k <= t; ++k) acc += Li[t][k] * Zp[k][c];
+            Zc[s0 + t][c] = acc;
+        }
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < (w - s0 - ws) * 32; idx += blockDim.x) {
+            int r = s0 + ws + idx / 32, c = idx % 32;
+            T acc = T(0);
+            for (int t = 0; t < ws; ++t) acc += F[(int64_t)(k0 + s0 + t) * f + k0 + r] * Zc[s0 + t][c];
+            Zc[r][c] -= acc;
+        }
+        __syncthreads();
+    }
+    T *M = Mall + d.moff;
+    for (int idx = threadIdx.x; idx < ncol * w; idx += blockDim.x) {
+        int c = idx / w, r = idx % w;
+        M[(int64_t)(c0 + c) * w + r] = Zc[r][c];
+    }
 }
 
 template <class T>
@@ -338,72 +405,60 @@ __global__ void __launch_bounds__(256) k_fwd_gather(const AsmItem *items, const 
     }
 }
 
+// forward, one CTA per solve panel: Zs[panel] = M Z[panel]
 template <class T>
-__global__ void __launch_bounds__(256) k_fwd_diag(const PanelDesc *descs, const int64_t *fo, const int64_t *zo,
-                                                  const int32_t *fsz, const int32_t *sn_start, const T *arena,
-                                                  const int32_t *piv, T *Z, int p) {
+__global__ void __launch_bounds__(256) k_fwd_m(const SolveDesc *sdescs, const int64_t *zo, const T *Mall, const T *Z,
+                                               T *Zs, int p) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    T(*Lb)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(smraw);
-    T(*zs)[33] = reinterpret_cast<T(*)[33]>(smraw + sizeof(T) * NB * (NB + 1));
-    const PanelDesc d = descs[blockIdx.x];
-    const int s = d.front, f = fsz[s], k0 = d.k0, w = d.w;
-    const T *F = arena + fo[s];
-    T *z = Z + zo[s] * p;
-    const int64_t g0 = (int64_t)sn_start[s] + k0;
-    for (int idx = threadIdx.x; idx < w * w; idx += blockDim.x) {
-        int r = idx % w, c = idx / w;
-        Lb[r][c] = (r > c) ? F[(int64_t)(k0 + c) * f + k0 + r] : T(0);
-    }
-    for (int idx = threadIdx.x; idx < w * p; idx += blockDim.x) {
-        int t = idx / p, q = idx % p;
-        zs[t][q] = z[(int64_t)piv[g0 + t] * p + q];
-    }
+    T(*zin)[33] = reinterpret_cast<T(*)[33]>(smraw);
+    const SolveDesc d = sdescs[blockIdx.x];
+    const int w = d.w;
+    const T *z = Z + (zo[d.front] + d.k0) * p;
+    T *zs = Zs + (zo[d.front] + d.k0) * p;
+    for (int idx = threadIdx.x; idx < w * p; idx += blockDim.x) zin[idx / p][idx % p] = z[idx];
     __syncthreads();
-    for (int t = 0; t < w; ++t) {
-        for (int idx = threadIdx.x; idx < (w - t - 1) * p; idx += blockDim.x) {
-            int r = t + 1 + idx / p, q = idx % p;
-            zs[r][q] -= Lb[r][t] * zs[t][q];
-        }
-        __syncthreads();
-    }
+    const T *M = Mall + d.moff;
     for (int idx = threadIdx.x; idx < w * p; idx += blockDim.x) {
-        int t = idx / p, q = idx % p;
-        z[(int64_t)(k0 + t) * p + q] = zs[t][q];
+        int r = idx / p, q = idx % p;
+        T acc = T(0);
+        for (int c = 0; c < w; ++c) acc += M[(int64_t)c * w + r] * zin[c][q];
+        zs[idx] = acc;
     }
 }
 
+// forward, rows below each solve panel: Z[r] -= L[r, panel] Zs[panel]
 template <class T>
-__global__ void __launch_bounds__(256) k_fwd_update(const PanelDesc *descs, int nd, const int64_t *fo,
-                                                    const int64_t *zo, const int32_t *fsz, const T *arena, T *Z,
-                                                    int p) {
-    __shared__ T zp[NB][33];
-    const int di = find_desc2(descs, nd, blockIdx.x);
-    const PanelDesc d = descs[di];
+__global__ void __launch_bounds__(256) k_fwd_upd(const SolveDesc *sdescs, int nd, const int64_t *fo, const int64_t *zo,
+                                                 const int32_t *fsz, const T *arena, const T *Zs, T *Z, int p) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T(*zp)[33] = reinterpret_cast<T(*)[33]>(smraw);
+    const int di = find_sdesc(sdescs, nd, blockIdx.x);
+    const SolveDesc d = sdescs[di];
     const int s = d.front, f = fsz[s], k0 = d.k0, w = d.w;
-    const int r0 = k0 + w + (int)(blockIdx.x - d.off2) * RB;
+    const int r0 = k0 + w + (int)(blockIdx.x - d.off) * RB;
+    if (r0 >= f) return;
     const int nr = min(RB, f - r0);
     const T *F = arena + fo[s];
+    const T *zs = Zs + (zo[s] + k0) * p;
     T *z = Z + zo[s] * p;
-    for (int idx = threadIdx.x; idx < w * p; idx += blockDim.x) {
-        int t = idx / p, q = idx % p;
-        zp[t][q] = z[(int64_t)(k0 + t) * p + q];
-    }
+    for (int idx = threadIdx.x; idx < w * p; idx += blockDim.x) zp[idx / p][idx % p] = zs[idx];
     __syncthreads();
     const int i = threadIdx.x % RB;
     if (i >= nr) return;
     for (int q = threadIdx.x / RB; q < p; q += blockDim.x / RB) {
         T acc = T(0);
-        for (int t = 0; t < w; ++t) acc += F[(int64_t)(k0 + t) * f + r0 + i] * zp[t][q];
+        const T *col = F + (int64_t)k0 * f + r0 + i;
+        for (int c = 0; c < w; ++c) acc += col[(int64_t)c * f] * zp[c][q];
         z[(int64_t)(r0 + i) * p + q] -= acc;
     }
 }
 
 template <class T>
 __global__ void k_fwd_finish(const AsmItem *items, const int64_t *zo, const int32_t *nc, const int32_t *sn_start,
-                             const T *Dg, const T *Z, T *yfw, int p) {
+                             const T *Dg, const T *Zs, T *yfw, int p) {
     AsmItem it = items[blockIdx.x];
     const int s = it.front, r0 = it.c0, r1 = min(nc[s], r0 + ACOLS);
-    const T *z = Z + zo[s] * p;
+    const T *z = Zs + zo[s] * p;
     for (int idx = threadIdx.x; idx < (r1 - r0) * p; idx += blockDim.x) {
         int r = r0 + idx / p, q = idx % p;
         int64_t g = (int64_t)sn_start[s] + r;
@@ -425,72 +480,64 @@ __global__ void k_bwd_gather(const AsmItem *items, const int64_t *zo, const int3
     }
 }
 
+// backward, rows below each solve panel: P[block][c][q] = sum_r L[r][k0 + c] Z[r][q]
 template <class T>
-__global__ void __launch_bounds__(256) k_bwd_partial(const PanelDesc *descs, int nd, const int64_t *fo,
-                                                     const int64_t *zo, const int32_t *fsz, const T *arena,
-                                                     const T *Z, int p, T *P) {
+__global__ void __launch_bounds__(256) k_bwd_part(const SolveDesc *sdescs, int nd, const int64_t *fo,
+                                                  const int64_t *zo, const int32_t *fsz, const T *arena, const T *Z,
+                                                  int p, T *P) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    T(*Fs)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(smraw);
-    T(*zsh)[33] = reinterpret_cast<T(*)[33]>(smraw + sizeof(T) * RB * (NB + 1));
-    const int di = find_desc2(descs, nd, blockIdx.x);
-    const PanelDesc d = descs[di];
+    T(*Fs)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(smraw);                        // RB x (NB + 1)
+    T(*zr)[33] = reinterpret_cast<T(*)[33]>(smraw + sizeof(T) * RB * (NB + 1));    // RB x 33
+    const int di = find_sdesc(sdescs, nd, blockIdx.x);
+    const SolveDesc d = sdescs[di];
     const int s = d.front, f = fsz[s], k0 = d.k0, w = d.w;
-    const int r0 = k0 + w + (int)(blockIdx.x - d.off2) * RB;
-    const int nr = min(RB, f - r0);
+    const int r0 = k0 + w + (int)(blockIdx.x - d.off) * RB;
+    const int nr = max(0, min(RB, f - r0));
+    T *out = P + (int64_t)blockIdx.x * SPW * 32;
     const T *F = arena + fo[s];
     const T *z = Z + zo[s] * p;
-    for (int idx = threadIdx.x; idx < nr * w; idx += blockDim.x) {
-        int i = idx % nr, t = idx / nr;
-        Fs[i][t] = F[(int64_t)(k0 + t) * f + r0 + i];
-    }
-    for (int idx = threadIdx.x; idx < nr * p; idx += blockDim.x) {
-        int i = idx / p, q = idx % p;
-        zsh[i][q] = z[(int64_t)(r0 + i) * p + q];
-    }
-    __syncthreads();
-    T *out = P + (int64_t)blockIdx.x * NB * 32;
-    for (int o = threadIdx.x; o < w * p; o += blockDim.x) {
-        int t = o / p, q = o % p;
-        T acc = T(0);
-        for (int i = 0; i < nr; ++i) acc += Fs[i][t] * zsh[i][q];
-        out[t * 32 + q] = acc;
+    for (int idx = threadIdx.x; idx < nr * p; idx += blockDim.x) zr[idx / p][idx % p] = z[(int64_t)r0 * p + idx];
+    for (int cc = 0; cc < w; cc += NB) {
+        const int wc = min(NB, w - cc);
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < nr * wc; idx += blockDim.x) {
+            int i = idx % nr, c = idx / nr;
+            Fs[i][c] = F[(int64_t)(k0 + cc + c) * f + r0 + i];
+        }
+        __syncthreads();
+        for (int o = threadIdx.x; o < wc * p; o += blockDim.x) {
+            int c = o / p, q = o % p;
+            T acc = T(0);
+            for (int i = 0; i < nr; ++i) acc += Fs[i][c] * zr[i][q];
+            out[(cc + c) * 32 + q] = acc;
+        }
     }
 }
 
+// backward, one CTA per solve panel: Z[panel] = M^T (Z[panel] - sum of partials)
 template <class T>
-__global__ void __launch_bounds__(256) k_bwd_diag(const PanelDesc *descs, const int64_t *fo, const int64_t *zo,
-                                                  const int32_t *fsz, const int32_t *sn_start, const T *arena,
-                                                  const int32_t *piv, const T *P, T *Z, int p) {
+__global__ void __launch_bounds__(256) k_bwd_m(const SolveDesc *sdescs, const int64_t *zo, const T *Mall, const T *P,
+                                               T *Z, int p) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    T(*Lb)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(smraw);
-    T(*zs)[33] = reinterpret_cast<T(*)[33]>(smraw + sizeof(T) * NB * (NB + 1));
-    const PanelDesc d = descs[blockIdx.x];
-    const int s = d.front, f = fsz[s], k0 = d.k0, w = d.w;
-    const T *F = arena + fo[s];
-    T *z = Z + zo[s] * p;
-    const int64_t g0 = (int64_t)sn_start[s] + k0;
-    const int64_t nblk = (d.m2 + RB - 1) / RB;
-    for (int idx = threadIdx.x; idx < w * w; idx += blockDim.x) {
-        int r = idx % w, c = idx / w;
-        Lb[r][c] = (r > c) ? F[(int64_t)(k0 + c) * f + k0 + r] : T(0);
-    }
+    T(*zb)[33] = reinterpret_cast<T(*)[33]>(smraw);
+    const SolveDesc d = sdescs[blockIdx.x];
+    const int w = d.w;
+    const int64_t nrb = d.m2 > 0 ? (d.m2 + RB - 1) / RB : 1;
+    T *z = Z + (zo[d.front] + d.k0) * p;
     for (int idx = threadIdx.x; idx < w * p; idx += blockDim.x) {
-        int t = idx / p, q = idx % p;
-        T v = z[(int64_t)(k0 + t) * p + q];
-        for (int64_t b = 0; b < nblk; ++b) v -= P[(d.off2 + b) * NB * 32 + t * 32 + q];
-        zs[t][q] = v;
+        int r = idx / p, q = idx % p;
+        T v = z[idx];
+        for (int64_t b = 0; b < nrb; ++b) v -= P[(d.off + b) * SPW * 32 + r * 32 + q];
+        zb[r][q] = v;
     }
     __syncthreads();
-    for (int r = w - 1; r > 0; --r) {
-        for (int idx = threadIdx.x; idx < r * p; idx += blockDim.x) {
-            int t = idx / p, q = idx % p;
-            zs[t][q] -= Lb[r][t] * zs[r][q];
-        }
-        __syncthreads();
-    }
+    const T *M = Mall + d.moff;
     for (int idx = threadIdx.x; idx < w * p; idx += blockDim.x) {
-        int t = idx / p, q = idx % p;
-        z[(int64_t)piv[g0 + t] * p + q] = zs[t][q];
+        int c = idx / p, q = idx % p;
+        const T *mc = M + (int64_t)c * w;
+        T acc = T(0);
+        for (int r = 0; r < w; ++r) acc += mc[r] * zb[r][q];
+        z[idx] = acc;
     }
 }
 
@@ -510,6 +557,25 @@ __global__ void k_bwd_finish(const AsmItem *items, const int64_t *zo, const int3
 // Host drivers
 // ------------------------------------------------------------------------------------------
 template <class T>
+static size_t build_m_smem() { return sizeof(T) * ((size_t)(SPW + NB) * 33 + (size_t)NB * (NB + 1)); }
+template <class T>
+static size_t panel_vec_smem() { return sizeof(T) * (size_t)SPW * 33; }
+template <class T>
+static size_t bwd_part_smem() { return sizeof(T) * ((size_t)RB * (NB + 1) + (size_t)RB * 33); }
+
+template <class T>
+static void set_solve_attrs() {
+    static bool done = false;
+    if (done) return;
+    MBL_CUDA(cudaFuncSetAttribute(k_build_m<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)build_m_smem<T>()));
+    MBL_CUDA(cudaFuncSetAttribute(k_fwd_m<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)panel_vec_smem<T>()));
+    MBL_CUDA(cudaFuncSetAttribute(k_fwd_upd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)panel_vec_smem<T>()));
+    MBL_CUDA(cudaFuncSetAttribute(k_bwd_m<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)panel_vec_smem<T>()));
+    MBL_CUDA(cudaFuncSetAttribute(k_bwd_part<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwd_part_smem<T>()));
+    done = true;
+}
+
+template <class T>
 static void factor_impl(Factorization &fz, cudaStream_t st) {
     Plan &p = *fz.plan;
     mbl_sector *sec = fz.sec;
@@ -519,10 +585,10 @@ static void factor_impl(Factorization &fz, cudaStream_t st) {
     T *linv = static_cast<T *>(fz.linv.m.p);
     static bool attr = false;
     if (!attr) {
-        MBL_CUDA(cudaFuncSetAttribute(k_panel_trsm<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
-        MBL_CUDA(cudaFuncSetAttribute(k_panel_trsm<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
+        MBL_CUDA(cudaFuncSetAttribute(k_panel_trsm<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
         attr = true;
     }
+    set_solve_attrs<T>();
     size_t trsm_smem = (size_t)(NB + RB) * (NB + 1) * sizeof(T);
     MBL_CUDA(cudaMemsetAsync(fz.counters.data(), 0, 2 * sizeof(unsigned long long), st));
     for (int l = 0; l < p.nlevels; ++l) {
@@ -536,13 +602,14 @@ static void factor_impl(Factorization &fz, cudaStream_t st) {
         for (int si = p.lvl_step_ptr[l]; si < p.lvl_step_ptr[l + 1]; ++si) {
             const PanelStep &stp = p.steps[si];
             const PanelDesc *dd = p.d_descs.data() + stp.d0;
+            T *lv = linv + (int64_t)stp.d0 * NB * NB;
             k_panel_diag<T><<<stp.nd, 256, 0, st>>>(dd, p.d_sn_fo.data(), p.d_sn_f.data(), p.d_sn_start.data(), arena,
-                                                    Dg, fz.piv.data(), linv, fz.tiny, fz.counters.data());
+                                                    Dg, fz.piv.data(), lv, fz.tiny, fz.counters.data());
             MBL_LAUNCH_CHECK();
             if (stp.n2 > 0) {
                 k_panel_trsm<T><<<(unsigned)stp.n2, 256, trsm_smem, st>>>(dd, stp.nd, p.d_sn_fo.data(), p.d_sn_f.data(),
                                                                          p.d_sn_start.data(), arena, Dg, fz.piv.data(),
-                                                                         linv, wscr);
+                                                                         lv, wscr);
                 MBL_LAUNCH_CHECK();
             }
             if (stp.n3 > 0) {
@@ -555,6 +622,14 @@ static void factor_impl(Factorization &fz, cudaStream_t st) {
                 MBL_LAUNCH_CHECK();
             }
         }
+    }
+    // block operators of the solve panels
+    if (!p.sdescs.empty()) {
+        dim3 grid((unsigned)p.sdescs.size(), SPW / 32);
+        k_build_m<T><<<grid, 256, build_m_smem<T>(), st>>>(p.d_sdescs.data(), p.d_sn_fo.data(), p.d_sn_f.data(),
+                                                           p.d_sn_start.data(), arena, fz.piv.data(), linv,
+                                                           static_cast<T *>(fz.M.m.p));
+        MBL_LAUNCH_CHECK();
     }
 }
 
@@ -570,21 +645,17 @@ static void solve_impl(Factorization &fz, const double *B, int64_t ldb, double *
     int64_t n = pl.n;
     T *arena = static_cast<T *>(fz.arena.m.p);
     T *Dg = static_cast<T *>(fz.D.m.p);
+    const T *M = static_cast<const T *>(fz.M.m.p);
     fz.ensure_solve_work(p);
+    set_solve_attrs<T>();
     T *Z = static_cast<T *>(fz.zwork.m.p);
+    T *Zs = static_cast<T *>(fz.zsolved.m.p);
     T *y = static_cast<T *>(fz.ywork.m.p);
     T *yfw = static_cast<T *>(fz.yfw.m.p);
     T *P = static_cast<T *>(fz.pwork.m.p);
     int64_t tot = n * p;
     unsigned g = (unsigned)((tot + 255) / 256);
-    const size_t dsm = sizeof(T) * (size_t)(NB * (NB + 1) + NB * 33);  // Lb + zs (and Fs + zsh, RB == NB)
-    static bool attr = false;
-    if (!attr) {
-        MBL_CUDA(cudaFuncSetAttribute(k_fwd_diag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024));
-        MBL_CUDA(cudaFuncSetAttribute(k_bwd_diag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024));
-        MBL_CUDA(cudaFuncSetAttribute(k_bwd_partial<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024));
-        attr = true;
-    }
+    const size_t vsm = panel_vec_smem<T>(), psm = bwd_part_smem<T>();
     ProfScope ps(fz.ctx, sizeof(T) == 8 ? "trisolve_fp64" : "trisolve_fp32",
                  2.0 * (double)(pl.nnz_l + n) * sizeof(T) + 16.0 * (double)n * p, st);
     k_perm_in<T><<<g, 256, 0, st>>>(n, p, pl.d_perm.data(), B, ldb, y);
@@ -596,19 +667,16 @@ static void solve_impl(Factorization &fz, const double *B, int64_t ldb, double *
                                             pl.d_sn_start.data(), pl.d_ch_ptr.data(), pl.d_ch_list.data(),
                                             pl.d_sn_rel_off.data(), pl.d_relind.data(), y, Z, p);
         MBL_LAUNCH_CHECK();
-        for (int si = pl.lvl_step_ptr[l]; si < pl.lvl_step_ptr[l + 1]; ++si) {
-            const PanelStep &stp = pl.steps[si];
-            const PanelDesc *dd = pl.d_descs.data() + stp.d0;
-            k_fwd_diag<T><<<stp.nd, 256, dsm, st>>>(dd, pl.d_sn_fo.data(), pl.d_sn_zo.data(), pl.d_sn_f.data(),
-                                                  pl.d_sn_start.data(), arena, fz.piv.data(), Z, p);
+        for (int si = pl.lvl_sstep_ptr[l]; si < pl.lvl_sstep_ptr[l + 1]; ++si) {
+            const SolveStep &ss = pl.ssteps[si];
+            const SolveDesc *sd = pl.d_sdescs.data() + ss.d0;
+            k_fwd_m<T><<<ss.nd, 256, vsm, st>>>(sd, pl.d_sn_zo.data(), M, Z, Zs, p);
             MBL_LAUNCH_CHECK();
-            if (stp.n2 > 0) {
-                k_fwd_update<T><<<(unsigned)stp.n2, 256, 0, st>>>(dd, stp.nd, pl.d_sn_fo.data(), pl.d_sn_zo.data(),
-                                                                  pl.d_sn_f.data(), arena, Z, p);
-                MBL_LAUNCH_CHECK();
-            }
+            k_fwd_upd<T><<<(unsigned)ss.nrb, 256, vsm, st>>>(sd, ss.nd, pl.d_sn_fo.data(), pl.d_sn_zo.data(),
+                                                             pl.d_sn_f.data(), arena, Zs, Z, p);
+            MBL_LAUNCH_CHECK();
         }
-        k_fwd_finish<T><<<na, 256, 0, st>>>(items, pl.d_sn_zo.data(), pl.d_sn_nc.data(), pl.d_sn_start.data(), Dg, Z,
+        k_fwd_finish<T><<<na, 256, 0, st>>>(items, pl.d_sn_zo.data(), pl.d_sn_nc.data(), pl.d_sn_start.data(), Dg, Zs,
                                             yfw, p);
         MBL_LAUNCH_CHECK();
     }
@@ -619,16 +687,13 @@ static void solve_impl(Factorization &fz, const double *B, int64_t ldb, double *
                                             pl.d_sn_start.data(), pl.d_sn_rows_off.data(), pl.d_rows.data(), yfw, y, Z,
                                             p);
         MBL_LAUNCH_CHECK();
-        for (int si = pl.lvl_step_ptr[l + 1] - 1; si >= pl.lvl_step_ptr[l]; --si) {
-            const PanelStep &stp = pl.steps[si];
-            const PanelDesc *dd = pl.d_descs.data() + stp.d0;
-            if (stp.n2 > 0) {
-                k_bwd_partial<T><<<(unsigned)stp.n2, 256, dsm, st>>>(dd, stp.nd, pl.d_sn_fo.data(), pl.d_sn_zo.data(),
-                                                                   pl.d_sn_f.data(), arena, Z, p, P);
-                MBL_LAUNCH_CHECK();
-            }
-            k_bwd_diag<T><<<stp.nd, 256, dsm, st>>>(dd, pl.d_sn_fo.data(), pl.d_sn_zo.data(), pl.d_sn_f.data(),
-                                                  pl.d_sn_start.data(), arena, fz.piv.data(), P, Z, p);
+        for (int si = pl.lvl_sstep_ptr[l + 1] - 1; si >= pl.lvl_sstep_ptr[l]; --si) {
+            const SolveStep &ss = pl.ssteps[si];
+            const SolveDesc *sd = pl.d_sdescs.data() + ss.d0;
+            k_bwd_part<T><<<(unsigned)ss.nrb, 256, psm, st>>>(sd, ss.nd, pl.d_sn_fo.data(), pl.d_sn_zo.data(),
+                                                              pl.d_sn_f.data(), arena, Z, p, P);
+            MBL_LAUNCH_CHECK();
+            k_bwd_m<T><<<ss.nd, 256, vsm, st>>>(sd, pl.d_sn_zo.data(), M, P, Z, p);
             MBL_LAUNCH_CHECK();
         }
         k_bwd_finish<T><<<na, 256, 0, st>>>(items, pl.d_sn_zo.data(), pl.d_sn_nc.data(), pl.d_sn_start.data(), Z, y, p);
@@ -650,9 +715,10 @@ void Factorization::ensure_solve_work(int p) {
     size_t es = elem_size();
     Plan &pl = *plan;
     zwork.alloc(ctx, (size_t)pl.zwork_elems * p * es);
+    zsolved.alloc(ctx, (size_t)pl.zwork_elems * p * es);
     ywork.alloc(ctx, (size_t)pl.n * p * es);
     yfw.alloc(ctx, (size_t)pl.n * p * es);
-    pwork.alloc(ctx, (size_t)std::max<int64_t>(pl.max_step_n2, 1) * NB * 32 * es);
+    pwork.alloc(ctx, (size_t)std::max<int64_t>(pl.max_sstep_nrb, 1) * SPW * 32 * es);
     work_p = p;
 }
 
@@ -664,7 +730,8 @@ void Factorization::allocate() {
     piv.alloc(ctx, pl.n);
     counters.alloc(ctx, 2);
     wscr.alloc(ctx, (size_t)std::max<int64_t>(pl.wscratch_elems, 1) * es);
-    linv.alloc(ctx, (size_t)std::max<int64_t>(pl.max_desc_per_step, 1) * NB * NB * es);
+    linv.alloc(ctx, (size_t)std::max<size_t>(pl.descs.size(), 1) * NB * NB * es);
+    M.alloc(ctx, (size_t)std::max<int64_t>(pl.m_elems, 1) * es);
 }
 
 void Factorization::release_scratch() {

@@ -562,132 +562,52 @@ void solve_near(mbl_sector *sec, double eps, int nev, const mbl_opts &o, double 
     OpFn opfn = [&](const double *X, int ldx, double *Y, cudaStream_t s) { op.apply(X, ldx, Y, p, s); };
     KrylovSchur ks(ctx, n, p, ncv);
     ks.start(o.start_seed, st);
+    RitzH rr(ctx, n, ks.ldv, nev);
     std::vector<double> th, rn;
     int k_keep = std::min(ncv - p, nev + (ncv - nev) / 2);
-    double target = o.target_tol;
-    int restarts = 0;
-    std::vector<double> out_ev(nev), out_res(nev);
-    int nc = 0;
-    double mxres = 0;
-    for (int outer = 0; outer < 4; ++outer) {
-        bool converged = false;
-        for (; restarts <= o.max_restarts; ++restarts) {
-            while (!ks.full()) {
-                ks.expand(opfn, st);
-                if (op.stalled && fz->prec == MBL_PREC_FP32) {
-                    // refinement stalled near the shift: fall back to FP64 fronts (same basis)
-                    auto tf1 = std::chrono::steady_clock::now();
-                    fz = make_factorization(sec, sigma, MBL_PREC_FP64, hnorm);
-                    S.ms_factor += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tf1).count();
-                    op.fz = fz.get();
-                    op.stalled = false;
-                    S.fp64_fallback = 1;
-                }
+    // The Krylov-Schur residual of a Ritz pair of (H - sigma)^-1 overestimates the residual on H
+    // (the refined solves carry forward errors along the wanted directions), so it only screens:
+    // convergence is decided by the Rayleigh-Ritz residuals on H.
+    double screen = 1e-6;
+    int restarts = 0, nc = 0;
+    double mxres = INFINITY;
+    for (;; ++restarts) {
+        while (!ks.full()) {
+            ks.expand(opfn, st);
+            if (op.stalled && fz->prec == MBL_PREC_FP32) {
+                // refinement stalled near the shift: fall back to FP64 fronts (same basis)
+                auto tf1 = std::chrono::steady_clock::now();
+                fz = make_factorization(sec, sigma, MBL_PREC_FP64, hnorm);
+                S.ms_factor += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tf1).count();
+                op.fz = fz.get();
+                op.stalled = false;
+                S.fp64_fallback = 1;
             }
-            ks.ritz(st, th, rn);
-            int mm = (int)th.size();
-            std::vector<int> order(mm);
-            std::iota(order.begin(), order.end(), 0);
-            std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return std::fabs(th[a]) > std::fabs(th[b]); });
-            bool ok = true;
-            for (int t = 0; t < nev; ++t) {
-                int i = order[t];
-                double est = (hnorm + std::fabs(sigma)) * rn[i] / std::max(std::fabs(th[i]), 1e-300);
-                if (est > target * hnorm) ok = false;
-            }
-            if (ok) {
-                converged = true;
-                break;
-            }
-            if (restarts == o.max_restarts) break;
-            std::vector<int> keep(order.begin(), order.begin() + k_keep);
-            std::sort(keep.begin(), keep.end());
-            ks.restart(keep, st);
         }
-        // ---- Rayleigh-Ritz of H on the basis V[:, 0:m] ----
-        int mb = ks.m;
-        DVec<double> HV, Gm, Gw, Gwork, Ydev, HY, part, nrm, thd, SKs;
-        DVec<int> gm, ginfo, didx;
-        DVec<int64_t> goff;
-        HV.alloc(ctx, (size_t)n * mb);
-        launch_spmv(sec, 0.0, ks.V.data(), ks.ldv, 1, HV.data(), mb, 1, mb, st);
-        Gm.alloc(ctx, (size_t)mb * mb);
-        DVec<double> Ctmp;
-        Ctmp.alloc(ctx, (size_t)mb * 32);
-        for (int c0 = 0; c0 < mb; c0 += 32) {
-            int w = std::min(32, mb - c0);
-            dense_tn(n, ks.V.data(), ks.ldv, 0, mb, HV.data(), mb, c0, w, Ctmp.data(), ks.work.data(), st);
-            // scatter C (mb x w row-major) into Gm (column-major mb x mb): Gm[(c0+q)*mb + a]
-            copy_cols(mb, Ctmp.data(), w, 0, Gm.data() + (size_t)c0, mb, 0, w, st);
+        ks.ritz(st, th, rn);
+        int mm = (int)th.size();
+        std::vector<int> order(mm);
+        std::iota(order.begin(), order.end(), 0);
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return std::fabs(th[a]) > std::fabs(th[b]); });
+        double worst = 0.0;
+        for (int t = 0; t < nev; ++t) {
+            int i = order[t];
+            worst = std::max(worst, (hnorm + std::fabs(sigma)) * rn[i] / std::max(std::fabs(th[i]), 1e-300) / hnorm);
         }
-        // Gm now row-major with rows a and columns c0+q -> symmetric pack (it is its own transpose)
-        Gw.alloc(ctx, mb);
-        Gwork.alloc(ctx, syev_work_doubles(mb));
-        gm.alloc(ctx, 1);
-        ginfo.alloc(ctx, 1);
-        goff.alloc(ctx, 1);
-        DVec<double> Gs;
-        Gs.alloc(ctx, (size_t)mb * mb);
-        k_pack_sym<<<nblk((int64_t)mb * mb), 256, 0, st>>>(Gm.data(), mb, mb, Gs.data());
-        MBL_LAUNCH_CHECK();
-        int64_t z = 0;
-        MBL_CUDA(cudaMemcpyAsync(gm.data(), &mb, sizeof(int), cudaMemcpyHostToDevice, st));
-        MBL_CUDA(cudaMemcpyAsync(goff.data(), &z, sizeof(int64_t), cudaMemcpyHostToDevice, st));
-        syev_batched(1, gm.data(), goff.data(), goff.data(), Gs.data(), Gw.data(), 1, nullptr, mb, Gwork.data(),
-                     ginfo.data(), st);
-        std::vector<double> gth(mb);
-        MBL_CUDA(cudaMemcpyAsync(gth.data(), Gw.data(), mb * sizeof(double), cudaMemcpyDeviceToHost, st));
-        MBL_CUDA(cudaStreamSynchronize(st));
-        std::vector<int> idx = nearest_sorted(gth, sigma, nev);
-        didx.alloc(ctx, nev);
-        MBL_CUDA(cudaMemcpyAsync(didx.data(), idx.data(), nev * sizeof(int), cudaMemcpyHostToDevice, st));
-        SKs.alloc(ctx, (size_t)mb * nev);
-        k_gather_S<<<nblk((int64_t)mb * nev), 256, 0, st>>>(Gs.data(), mb, didx.data(), nev, SKs.data());
-        MBL_LAUNCH_CHECK();
-        Ydev.alloc(ctx, (size_t)n * nev);
-        dense_nn(n, ks.V.data(), ks.ldv, mb, SKs.data(), nev, Ydev.data(), nev, 0, st);
-        HY.alloc(ctx, (size_t)n * nev);
-        launch_spmv(sec, 0.0, Ydev.data(), nev, 1, HY.data(), nev, 1, nev, st);
-        for (int j = 0; j < nev; ++j) out_ev[j] = gth[idx[j]];
-        thd.alloc(ctx, nev);
-        MBL_CUDA(cudaMemcpyAsync(thd.data(), out_ev.data(), nev * sizeof(double), cudaMemcpyHostToDevice, st));
-        unsigned nb = nblk(n * nev);
-        part.alloc(ctx, (size_t)nb * 2 * nev);
-        nrm.alloc(ctx, 2 * nev);
-        k_pair_resid<<<nb, 256, 2 * nev * sizeof(double), st>>>(n, nev, Ydev.data(), HY.data(), thd.data(), part.data());
-        MBL_LAUNCH_CHECK();
-        k_reduce_parts<<<nblk(2 * nev), 256, 0, st>>>((int)nb, 2 * nev, part.data(), nrm.data());
-        MBL_LAUNCH_CHECK();
-        k_scale_cols_to_cm<<<nblk(n * nev), 256, 0, st>>>(n, nev, Ydev.data(), nrm.data(), d_evecs);
-        MBL_LAUNCH_CHECK();
-        std::vector<double> hn2(2 * nev);
-        MBL_CUDA(cudaMemcpyAsync(hn2.data(), nrm.data(), 2 * nev * sizeof(double), cudaMemcpyDeviceToHost, st));
-        MBL_CUDA(cudaStreamSynchronize(st));
-        nc = 0;
-        mxres = 0;
-        for (int j = 0; j < nev; ++j) {
-            out_res[j] = std::sqrt(hn2[nev + j] / hn2[j]);
-            mxres = std::max(mxres, out_res[j] / hnorm);
-            if (out_res[j] <= o.tol * hnorm) ++nc;
+        bool last = restarts >= o.max_restarts;
+        if (worst <= screen || last) {
+            rr.run(sec, ks, sigma, hnorm, o.tol, d_evecs, st);
+            nc = rr.nconv;
+            mxres = rr.maxres;
+            if (mxres <= o.target_tol || last) break;
+            screen = std::max(1e-14, std::min(screen, worst) * 0.01);
         }
-        if (nc == nev && mxres <= 10.0 * o.target_tol) break;
-        if (!converged && restarts >= o.max_restarts) break;
-        // not yet at the FP64 floor: tighten the transformed-problem target and continue
-        target *= 0.01;
-        std::vector<int> keep;
-        {
-            int mm = (int)th.size();
-            std::vector<int> order(mm);
-            std::iota(order.begin(), order.end(), 0);
-            std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return std::fabs(th[a]) > std::fabs(th[b]); });
-            keep.assign(order.begin(), order.begin() + k_keep);
-            std::sort(keep.begin(), keep.end());
-        }
+        std::vector<int> keep(order.begin(), order.begin() + k_keep);
+        std::sort(keep.begin(), keep.end());
         ks.restart(keep, st);
-        ++restarts;
     }
-    MBL_CUDA(cudaMemcpyAsync(d_evals, out_ev.data(), nev * sizeof(double), cudaMemcpyHostToDevice, st));
-    MBL_CUDA(cudaMemcpyAsync(d_resid, out_res.data(), nev * sizeof(double), cudaMemcpyHostToDevice, st));
+    MBL_CUDA(cudaMemcpyAsync(d_evals, rr.evals.data(), nev * sizeof(double), cudaMemcpyHostToDevice, st));
+    MBL_CUDA(cudaMemcpyAsync(d_resid, rr.resid.data(), nev * sizeof(double), cudaMemcpyHostToDevice, st));
     MBL_CUDA(cudaStreamSynchronize(st));
     *nconv = nc;
     S.restarts = restarts;
@@ -697,6 +617,77 @@ void solve_near(mbl_sector *sec, double eps, int nev, const mbl_opts &o, double 
     S.max_resid = mxres;
     S.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     if (stats) *stats = S;
+}
+
+// ------------------------------------------------------------------------------------------
+// Rayleigh-Ritz of H on the Krylov basis V[:, 0:m]
+// ------------------------------------------------------------------------------------------
+RitzH::RitzH(Ctx *c, int64_t n_, int ldv, int nev_) : ctx(c), n(n_), nev(nev_) {
+    HV.alloc(ctx, (size_t)n * ldv);
+    Gm.alloc(ctx, (size_t)ldv * ldv);
+    Gs.alloc(ctx, (size_t)ldv * ldv);
+    Gw.alloc(ctx, ldv);
+    Gwork.alloc(ctx, syev_work_doubles(ldv));
+    Ctmp.alloc(ctx, (size_t)ldv * 32);
+    work.alloc(ctx, dense_tn_work(n, ldv, 32) + 64);
+    gm.alloc(ctx, 1);
+    ginfo.alloc(ctx, 1);
+    goff.alloc(ctx, 1);
+    didx.alloc(ctx, nev);
+    SKs.alloc(ctx, (size_t)ldv * nev);
+    Y.alloc(ctx, (size_t)n * nev);
+    HY.alloc(ctx, (size_t)n * nev);
+    thd.alloc(ctx, nev);
+    nb = nblk(n * nev);
+    part.alloc(ctx, (size_t)nb * 2 * nev);
+    nrm.alloc(ctx, 2 * nev);
+    evals.assign(nev, 0.0);
+    resid.assign(nev, 0.0);
+    int64_t z = 0;
+    MBL_CUDA(cudaMemcpy(goff.data(), &z, sizeof(int64_t), cudaMemcpyHostToDevice));
+}
+
+void RitzH::run(mbl_sector *sec, KrylovSchur &ks, double sigma, double hnorm, double tol, double *d_evecs,
+                cudaStream_t st) {
+    int mb = ks.m;
+    launch_spmv(sec, 0.0, ks.V.data(), ks.ldv, 1, HV.data(), mb, 1, mb, st);
+    for (int c0 = 0; c0 < mb; c0 += 32) {
+        int w = std::min(32, mb - c0);
+        dense_tn(n, ks.V.data(), ks.ldv, 0, mb, HV.data(), mb, c0, w, Ctmp.data(), work.data(), st);
+        copy_cols(mb, Ctmp.data(), w, 0, Gm.data() + (size_t)c0, mb, 0, w, st);
+    }
+    k_pack_sym<<<nblk((int64_t)mb * mb), 256, 0, st>>>(Gm.data(), mb, mb, Gs.data());
+    MBL_LAUNCH_CHECK();
+    MBL_CUDA(cudaMemcpyAsync(gm.data(), &mb, sizeof(int), cudaMemcpyHostToDevice, st));
+    syev_batched(1, gm.data(), goff.data(), goff.data(), Gs.data(), Gw.data(), 1, nullptr, ks.ldv, Gwork.data(),
+                 ginfo.data(), st);
+    std::vector<double> gth(mb);
+    MBL_CUDA(cudaMemcpyAsync(gth.data(), Gw.data(), mb * sizeof(double), cudaMemcpyDeviceToHost, st));
+    MBL_CUDA(cudaStreamSynchronize(st));
+    std::vector<int> idx = nearest_sorted(gth, sigma, nev);
+    MBL_CUDA(cudaMemcpyAsync(didx.data(), idx.data(), nev * sizeof(int), cudaMemcpyHostToDevice, st));
+    k_gather_S<<<nblk((int64_t)mb * nev), 256, 0, st>>>(Gs.data(), mb, didx.data(), nev, SKs.data());
+    MBL_LAUNCH_CHECK();
+    dense_nn(n, ks.V.data(), ks.ldv, mb, SKs.data(), nev, Y.data(), nev, 0, st);
+    launch_spmv(sec, 0.0, Y.data(), nev, 1, HY.data(), nev, 1, nev, st);
+    for (int j = 0; j < nev; ++j) evals[j] = gth[idx[j]];
+    MBL_CUDA(cudaMemcpyAsync(thd.data(), evals.data(), nev * sizeof(double), cudaMemcpyHostToDevice, st));
+    k_pair_resid<<<nb, 256, 2 * nev * sizeof(double), st>>>(n, nev, Y.data(), HY.data(), thd.data(), part.data());
+    MBL_LAUNCH_CHECK();
+    k_reduce_parts<<<nblk(2 * nev), 256, 0, st>>>((int)nb, 2 * nev, part.data(), nrm.data());
+    MBL_LAUNCH_CHECK();
+    k_scale_cols_to_cm<<<nblk(n * nev), 256, 0, st>>>(n, nev, Y.data(), nrm.data(), d_evecs);
+    MBL_LAUNCH_CHECK();
+    std::vector<double> hn2(2 * nev);
+    MBL_CUDA(cudaMemcpyAsync(hn2.data(), nrm.data(), 2 * nev * sizeof(double), cudaMemcpyDeviceToHost, st));
+    MBL_CUDA(cudaStreamSynchronize(st));
+    nconv = 0;
+    maxres = 0.0;
+    for (int j = 0; j < nev; ++j) {
+        resid[j] = std::sqrt(hn2[nev + j] / hn2[j]);
+        maxres = std::max(maxres, resid[j] / hnorm);
+        if (resid[j] <= tol * hnorm) ++nconv;
+    }
 }
 
 }  // namespace mbl

@@ -48,6 +48,24 @@ struct RefinedSolve {
     void apply(const double *X, int ldx, double *Y, int p, cudaStream_t st);
 };
 
+// Rayleigh-Ritz of H on the whole basis: the nev Ritz pairs nearest sigma and their residuals.
+struct RitzH {
+    Ctx *ctx;
+    int64_t n;
+    int nev;
+    unsigned nb = 0;
+    DVec<double> HV, Gm, Gs, Gw, Gwork, Ctmp, work, SKs, Y, HY, thd, part, nrm;
+    DVec<int> gm, ginfo, didx;
+    DVec<int64_t> goff;
+    std::vector<double> evals, resid;
+    int nconv = 0;
+    double maxres = 0.0;  // max residual / ||H||
+    RitzH(Ctx *c, int64_t n_, int ldv, int nev_);
+    // writes the normalized Ritz vectors (n x nev column-major) to d_evecs
+    void run(mbl_sector *sec, KrylovSchur &ks, double sigma, double hnorm, double tol, double *d_evecs,
+             cudaStream_t st);
+};
+
 void extremal_bounds(mbl_sector *sec, double *emin, double *emax);
 void solve_near(mbl_sector *sec, double eps, int nev, const mbl_opts &o, double *d_evals, double *d_evecs,
                 double *d_resid, int *nconv, double *sigma_used, mbl_solve_stats *stats, cudaStream_t st);

@@ -15,6 +15,8 @@ constexpr int NB = 64;  // panel width of the blocked frontal LDL^T (pivot windo
 constexpr int RB = 64;  // rows per row block (stage 2 / solve updates)
 constexpr int TB = 64;  // tile edge of the trailing (Schur) update
 constexpr int ACOLS = 32;  // columns per assembly work item
+constexpr int SPW = 256;   // width of a solve panel (4 factor panels): one dense block operator M each
+constexpr int SUBS = SPW / NB;
 
 // One active front in one (level, panel) step.
 struct PanelDesc {
@@ -32,6 +34,22 @@ struct PanelStep {
     int32_t d0, nd;  // descriptor range
     int64_t n2, n3;  // row blocks and trailing tiles in this step
     int64_t wsize;   // W21 scratch elements used by this step
+};
+
+// One solve panel: columns [k0, k0 + w) of a front's fully-summed block (w <= SPW).  M (w x w,
+// column-major) is the composite of the factor panels' pivot permutations and unit-lower
+// eliminations restricted to the panel: forward z_panel <- M z_panel, backward x_panel <- M^T z.
+struct SolveDesc {
+    int32_t front, k0, w, m2;        // m2 = f - k0 - w rows below
+    int64_t off;                     // prefix of row blocks (at least one per descriptor)
+    int64_t moff;                    // offset (elements) of M
+    int32_t fdesc[SUBS];             // factor descriptors of the sub-panels (-1 if absent)
+};
+
+struct SolveStep {
+    int32_t level;
+    int32_t d0, nd;
+    int64_t nrb;                     // row blocks in this step (>= nd)
 };
 
 struct AsmItem {     // assembly work item: columns [c0, c0 + ACOLS) of a front
@@ -57,6 +75,10 @@ struct Plan {
     std::vector<PanelStep> steps;
     std::vector<int32_t> lvl_step_ptr;        // steps by level
     std::vector<PanelDesc> descs;
+    std::vector<SolveStep> ssteps;
+    std::vector<int32_t> lvl_sstep_ptr;       // solve steps by level
+    std::vector<SolveDesc> sdescs;
+    int64_t m_elems = 0, max_sstep_nrb = 0;
     int64_t arena_elems = 0, zwork_elems = 0, wscratch_elems = 0, max_desc_per_step = 0;
     int64_t max_step_n2 = 0;
     int64_t nnz_l = 0;
@@ -69,6 +91,7 @@ struct Plan {
     DVec<int64_t> d_sn_rows_off, d_sn_fo, d_sn_zo, d_sn_rel_off, d_amap_ptr, d_amap_src;
     DVec<AsmItem> d_asm_items;
     DVec<PanelDesc> d_descs;
+    DVec<SolveDesc> d_sdescs;
     bool on_device = false;
 };
 

@@ -493,6 +493,10 @@ std::shared_ptr<Plan> build_plan(int L, const std::vector<uint32_t> &states, con
     // assembly items and panel schedule per level
     p.asm_ptr.assign(p.nlevels + 1, 0);
     p.lvl_step_ptr.assign(p.nlevels + 1, 0);
+    p.lvl_sstep_ptr.assign(p.nlevels + 1, 0);
+    std::vector<int64_t> fd_off(ns + 1, 0);  // factor descriptor of (front, panel) at fd_of[fd_off[s] + kk]
+    for (int32_t s = 0; s < ns; ++s) fd_off[s + 1] = fd_off[s] + (p.sn_nc[s] + NB - 1) / NB;
+    std::vector<int32_t> fd_of(fd_off[ns], -1);
     for (int l = 0; l < p.nlevels; ++l) {
         int32_t maxnc = 0;
         for (int32_t q = p.lvl_ptr[l]; q < p.lvl_ptr[l + 1]; ++q) {
@@ -510,6 +514,7 @@ std::shared_ptr<Plan> build_plan(int L, const std::vector<uint32_t> &states, con
                 int32_t w = std::min(NB, p.sn_nc[s] - k0);
                 int32_t m2 = p.sn_f[s] - k0 - w;
                 PanelDesc d{s, k0, w, m2, stp.n2, stp.n3, stp.wsize};
+                fd_of[fd_off[s] + kk] = (int32_t)p.descs.size();
                 int64_t nb2 = (m2 + RB - 1) / RB;
                 int64_t T = (m2 + TB - 1) / TB;
                 stp.n2 += nb2;
@@ -524,6 +529,34 @@ std::shared_ptr<Plan> build_plan(int L, const std::vector<uint32_t> &states, con
             p.steps.push_back(stp);
         }
         p.lvl_step_ptr[l + 1] = (int32_t)p.steps.size();
+        // solve schedule: SPW-wide panels
+        for (int32_t ks = 0; ks * SPW < maxnc; ++ks) {
+            SolveStep ss{l, (int32_t)p.sdescs.size(), 0, 0};
+            for (int32_t q = p.lvl_ptr[l]; q < p.lvl_ptr[l + 1]; ++q) {
+                int32_t s = p.lvl_fronts[q];
+                int32_t k0 = ks * SPW;
+                if (p.sn_nc[s] <= k0) continue;
+                int32_t w = std::min(SPW, p.sn_nc[s] - k0);
+                SolveDesc sd;
+                sd.front = s;
+                sd.k0 = k0;
+                sd.w = w;
+                sd.m2 = p.sn_f[s] - k0 - w;
+                sd.off = ss.nrb;
+                sd.moff = p.m_elems;
+                for (int u = 0; u < SUBS; ++u) {
+                    int32_t kk = (k0 + u * NB) / NB;
+                    sd.fdesc[u] = (u * NB < w) ? fd_of[fd_off[s] + kk] : -1;
+                }
+                ss.nrb += std::max<int64_t>(1, (sd.m2 + RB - 1) / RB);
+                p.m_elems += (int64_t)w * w;
+                p.sdescs.push_back(sd);
+            }
+            ss.nd = (int32_t)p.sdescs.size() - ss.d0;
+            p.max_sstep_nrb = std::max(p.max_sstep_nrb, ss.nrb);
+            p.ssteps.push_back(ss);
+        }
+        p.lvl_sstep_ptr[l + 1] = (int32_t)p.ssteps.size();
     }
     p.ms_analyse = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     return P;
@@ -555,6 +588,7 @@ void upload_plan(Ctx *ctx, Plan &p) {
     up(ctx, p.d_amap_src, p.amap_src);
     up(ctx, p.d_asm_items, p.asm_items);
     up(ctx, p.d_descs, p.descs);
+    up(ctx, p.d_sdescs, p.sdescs);
     p.on_device = true;
 }
 
