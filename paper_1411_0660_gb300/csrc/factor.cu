@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(256) k_assemble(const AsmItem *items, const in
 
 template <class T>
 __global__ void __launch_bounds__(256) k_panel_diag(const PanelDesc *descs, const int64_t *fo, const int32_t *fsz,
-                                                    const int32_t *sn_start, T *arena, T *Dg, int32_t *piv, T *linv,
+                                                    const int32_t *sn_start, T *arena, T *Dg, int32_t *piv,
                                                     double tiny, unsigned long long *counters) {
     __shared__ T B[NB][NB + 1];
     __shared__ int perm[NB];
@@ -166,62 +166,56 @@ __global__ void __launch_bounds__(256) k_panel_diag(const PanelDesc *descs, cons
         Dg[g0 + tid] = B[tid][tid];
         piv[g0 + tid] = k0 + perm[tid];
     }
-    // Linv = L11^-1 (unit lower), row-major NB x NB: Linv[t][k] for k <= t; one thread per column
-    T *Li = linv + (int64_t)blockIdx.x * NB * NB;
-    if (tid < w) {
-        const int c = tid;
-        T x[NB];
-        for (int r = 0; r < w; ++r) x[r] = T(0);
-        x[c] = T(1);
-        for (int r = c + 1; r < w; ++r) {
-            T acc = T(0);
-            for (int k = c; k < r; ++k) acc += B[r][k] * x[k];
-            x[r] = -acc;
-        }
-        for (int r = 0; r < w; ++r) Li[r * NB + c] = x[r];
-    }
 }
 
+// W21 = A21 L11^-T by forward substitution (one thread per row, no explicit inverse), then
+// L21 = W21 D^-1.  The columns of A21 are read in the panel's pivoted order.
 template <class T>
-__global__ void __launch_bounds__(256) k_panel_trsm(const PanelDesc *descs, int nd, const int64_t *fo,
-                                                    const int32_t *fsz, const int32_t *sn_start, T *arena,
-                                                    const T *Dg, const int32_t *piv, const T *linv, T *wscr) {
+__global__ void __launch_bounds__(RB) k_panel_trsm(const PanelDesc *descs, int nd, const int64_t *fo,
+                                                   const int32_t *fsz, const int32_t *sn_start, T *arena,
+                                                   const T *Dg, const int32_t *piv, T *wscr) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    T *Ls = reinterpret_cast<T *>(smraw);      // NB x (NB+1): Ls[t][k]
-    T *As = Ls + NB * (NB + 1);                // RB x (NB+1): As[i][k]
+    T(*Lb)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(smraw);                      // L11
+    T(*As)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(smraw + sizeof(T) * NB * (NB + 1));
     __shared__ T Dinv[NB];
     __shared__ int pv[NB];
     const int di = find_desc2(descs, nd, blockIdx.x);
     const PanelDesc d = descs[di];
     const int s = d.front, f = fsz[s], k0 = d.k0, w = d.w, m2 = d.m2;
-    const int rb = (int)(blockIdx.x - d.off2);
-    const int r0 = k0 + w + rb * RB;
+    const int r0 = k0 + w + (int)(blockIdx.x - d.off2) * RB;
     const int nr = min(RB, f - r0);
     T *F = arena + fo[s];
-    const T *Li = linv + (int64_t)di * NB * NB;
-    const int tid = threadIdx.x, bd = blockDim.x;
+    const int tid = threadIdx.x;
     const int64_t g0 = (int64_t)sn_start[s] + k0;
-    for (int idx = tid; idx < w * w; idx += bd) {
-        int t = idx / w, k = idx % w;
-        Ls[t * (NB + 1) + k] = Li[t * NB + k];
+    for (int idx = tid; idx < w * w; idx += blockDim.x) {
+        int r = idx % w, c = idx / w;
+        Lb[r][c] = (r > c) ? F[(int64_t)(k0 + c) * f + k0 + r] : T(0);
     }
     if (tid < w) {
         Dinv[tid] = T(1) / Dg[g0 + tid];
         pv[tid] = piv[g0 + tid];
     }
     __syncthreads();
-    for (int idx = tid; idx < nr * w; idx += bd) {
+    for (int idx = tid; idx < nr * w; idx += blockDim.x) {
         int i = idx % nr, k = idx / nr;
-        As[i * (NB + 1) + k] = F[(int64_t)pv[k] * f + r0 + i];
+        As[i][k] = F[(int64_t)pv[k] * f + r0 + i];
+    }
+    __syncthreads();
+    if (tid < nr) {
+        T *a = As[tid];
+        for (int t = 1; t < w; ++t) {
+            T acc = a[t];
+            for (int k = 0; k < t; ++k) acc -= a[k] * Lb[t][k];
+            a[t] = acc;
+        }
     }
     __syncthreads();
     T *W = wscr + d.woff;
-    for (int idx = tid; idx < nr * w; idx += bd) {
+    for (int idx = tid; idx < nr * w; idx += blockDim.x) {
         int i = idx % nr, t = idx / nr;
-        T acc = T(0);
-        for (int k = 0; k <= t; ++k) acc += As[i * (NB + 1) + k] * Ls[t * (NB + 1) + k];
-        F[(int64_t)(k0 + t) * f + r0 + i] = acc * Dinv[t];
-        W[(int64_t)(r0 - k0 - w + i) + (int64_t)t * m2] = acc;
+        T x = As[i][t];
+        F[(int64_t)(k0 + t) * f + r0 + i] = x * Dinv[t];
+        W[(int64_t)(r0 - k0 - w + i) + (int64_t)t * m2] = x;
     }
 }
 
@@ -323,15 +317,16 @@ __device__ __forceinline__ int find_sdesc(const SolveDesc *d, int nd, int64_t b)
     return lo;
 }
 
-// M of one solve panel, 32 columns per CTA: the forward sequence applied to unit vectors.
+// M of one solve panel, 32 columns per CTA, in FP64: the forward sequence (pivot permutation,
+// unit-lower substitution, elimination of the later rows of the panel) applied to unit vectors.
 template <class T>
 __global__ void __launch_bounds__(256) k_build_m(const SolveDesc *sdescs, const int64_t *fo, const int32_t *fsz,
                                                  const int32_t *sn_start, const T *arena, const int32_t *piv,
-                                                 const T *linv_all, T *Mall) {
+                                                 double *Mall) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    T(*Zc)[33] = reinterpret_cast<T(*)[33]>(smraw);                             // SPW x 33
-    T(*Zp)[33] = reinterpret_cast<T(*)[33]>(smraw + sizeof(T) * SPW * 33);      // NB x 33
-    T(*Li)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(smraw + sizeof(T) * (SPW + NB) * 33);
+    double(*Zc)[33] = reinterpret_cast<double(*)[33]>(smraw);                          // SPW x 33
+    double(*Zp)[33] = reinterpret_cast<double(*)[33]>(smraw + 8 * SPW * 33);           // NB x 33
+    double(*Lb)[NB + 1] = reinterpret_cast<double(*)[NB + 1]>(smraw + 8 * (SPW + NB) * 33);
     const SolveDesc d = sdescs[blockIdx.x];
     const int c0 = blockIdx.y * 32;
     if (c0 >= d.w) return;
@@ -340,38 +335,46 @@ __global__ void __launch_bounds__(256) k_build_m(const SolveDesc *sdescs, const 
     const int64_t g0 = (int64_t)sn_start[s] + k0;
     for (int idx = threadIdx.x; idx < w * 32; idx += blockDim.x) {
         int r = idx / 32, c = idx % 32;
-        Zc[r][c] = (c < ncol && r == c0 + c) ? T(1) : T(0);
+        Zc[r][c] = (c < ncol && r == c0 + c) ? 1.0 : 0.0;
     }
     __syncthreads();
     for (int u = 0; u < SUBS; ++u) {
-        if (d.fdesc[u] < 0) break;
-        const int s0 = u * NB, ws = min(NB, w - s0);
-        const T *Lsrc = linv_all + (int64_t)d.fdesc[u] * NB * NB;
+        const int s0 = u * NB;
+        if (s0 >= w) break;
+        const int ws = min(NB, w - s0);
         for (int idx = threadIdx.x; idx < ws * ws; idx += blockDim.x) {
-            int t = idx / ws, k = idx % ws;
-            Li[t][k] = Lsrc[t * NB + k];
+            int r = idx % ws, c = idx / ws;
+            Lb[r][c] = (r > c) ? (double)F[(int64_t)(k0 + s0 + c) * f + k0 + s0 + r] : 0.0;
         }
         for (int idx = threadIdx.x; idx < ws * 32; idx += blockDim.x) {
             int t = idx / 32, c = idx % 32;
             Zp[t][c] = Zc[piv[g0 + s0 + t] - k0][c];
         }
         __syncthreads();
+        // forward substitution with the unit-lower L11, one thread per column
+        if (threadIdx.x < 32) {
+            const int c = threadIdx.x;
+            for (int t = 1; t < ws; ++t) {
+                double acc = Zp[t][c];
+                for (int k = 0; k < t; ++k) acc -= Lb[t][k] * Zp[k][c];
+                Zp[t][c] = acc;
+            }
+        }
+        __syncthreads();
         for (int idx = threadIdx.x; idx < ws * 32; idx += blockDim.x) {
             int t = idx / 32, c = idx % 32;
-            T acc = T(0);
-            for (int k = 0; k <= t; ++k) acc += Li[t][k] * Zp[k][c];
-            Zc[s0 + t][c] = acc;
+            Zc[s0 + t][c] = Zp[t][c];
         }
         __syncthreads();
         for (int idx = threadIdx.x; idx < (w - s0 - ws) * 32; idx += blockDim.x) {
             int r = s0 + ws + idx / 32, c = idx % 32;
-            T acc = T(0);
-            for (int t = 0; t < ws; ++t) acc += F[(int64_t)(k0 + s0 + t) * f + k0 + r] * Zc[s0 + t][c];
+            double acc = 0.0;
+            for (int t = 0; t < ws; ++t) acc += (double)F[(int64_t)(k0 + s0 + t) * f + k0 + r] * Zc[s0 + t][c];
             Zc[r][c] -= acc;
         }
         __syncthreads();
     }
-    T *M = Mall + d.moff;
+    double *M = Mall + d.moff;
     for (int idx = threadIdx.x; idx < ncol * w; idx += blockDim.x) {
         int c = idx / w, r = idx % w;
         M[(int64_t)(c0 + c) * w + r] = Zc[r][c];
@@ -407,22 +410,22 @@ __global__ void __launch_bounds__(256) k_fwd_gather(const AsmItem *items, const 
 
 // forward, one CTA per solve panel: Zs[panel] = M Z[panel]
 template <class T>
-__global__ void __launch_bounds__(256) k_fwd_m(const SolveDesc *sdescs, const int64_t *zo, const T *Mall, const T *Z,
-                                               T *Zs, int p) {
+__global__ void __launch_bounds__(256) k_fwd_m(const SolveDesc *sdescs, const int64_t *zo, const double *Mall,
+                                               const T *Z, T *Zs, int p) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    T(*zin)[33] = reinterpret_cast<T(*)[33]>(smraw);
+    double(*zin)[33] = reinterpret_cast<double(*)[33]>(smraw);
     const SolveDesc d = sdescs[blockIdx.x];
     const int w = d.w;
     const T *z = Z + (zo[d.front] + d.k0) * p;
     T *zs = Zs + (zo[d.front] + d.k0) * p;
-    for (int idx = threadIdx.x; idx < w * p; idx += blockDim.x) zin[idx / p][idx % p] = z[idx];
+    for (int idx = threadIdx.x; idx < w * p; idx += blockDim.x) zin[idx / p][idx % p] = (double)z[idx];
     __syncthreads();
-    const T *M = Mall + d.moff;
+    const double *M = Mall + d.moff;
     for (int idx = threadIdx.x; idx < w * p; idx += blockDim.x) {
         int r = idx / p, q = idx % p;
-        T acc = T(0);
+        double acc = 0.0;
         for (int c = 0; c < w; ++c) acc += M[(int64_t)c * w + r] * zin[c][q];
-        zs[idx] = acc;
+        zs[idx] = (T)acc;
     }
 }
 
@@ -516,28 +519,28 @@ __global__ void __launch_bounds__(256) k_bwd_part(const SolveDesc *sdescs, int n
 
 // backward, one CTA per solve panel: Z[panel] = M^T (Z[panel] - sum of partials)
 template <class T>
-__global__ void __launch_bounds__(256) k_bwd_m(const SolveDesc *sdescs, const int64_t *zo, const T *Mall, const T *P,
-                                               T *Z, int p) {
+__global__ void __launch_bounds__(256) k_bwd_m(const SolveDesc *sdescs, const int64_t *zo, const double *Mall,
+                                               const T *P, T *Z, int p) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    T(*zb)[33] = reinterpret_cast<T(*)[33]>(smraw);
+    double(*zb)[33] = reinterpret_cast<double(*)[33]>(smraw);
     const SolveDesc d = sdescs[blockIdx.x];
     const int w = d.w;
     const int64_t nrb = d.m2 > 0 ? (d.m2 + RB - 1) / RB : 1;
     T *z = Z + (zo[d.front] + d.k0) * p;
     for (int idx = threadIdx.x; idx < w * p; idx += blockDim.x) {
         int r = idx / p, q = idx % p;
-        T v = z[idx];
-        for (int64_t b = 0; b < nrb; ++b) v -= P[(d.off + b) * SPW * 32 + r * 32 + q];
+        double v = (double)z[idx];
+        for (int64_t b = 0; b < nrb; ++b) v -= (double)P[(d.off + b) * SPW * 32 + r * 32 + q];
         zb[r][q] = v;
     }
     __syncthreads();
-    const T *M = Mall + d.moff;
+    const double *M = Mall + d.moff;
     for (int idx = threadIdx.x; idx < w * p; idx += blockDim.x) {
         int c = idx / p, q = idx % p;
-        const T *mc = M + (int64_t)c * w;
-        T acc = T(0);
+        const double *mc = M + (int64_t)c * w;
+        double acc = 0.0;
         for (int r = 0; r < w; ++r) acc += mc[r] * zb[r][q];
-        z[idx] = acc;
+        z[idx] = (T)acc;
     }
 }
 
@@ -557,9 +560,11 @@ __global__ void k_bwd_finish(const AsmItem *items, const int64_t *zo, const int3
 // Host drivers
 // ------------------------------------------------------------------------------------------
 template <class T>
-static size_t build_m_smem() { return sizeof(T) * ((size_t)(SPW + NB) * 33 + (size_t)NB * (NB + 1)); }
+static size_t build_m_smem() { return 8 * ((size_t)(SPW + NB) * 33 + (size_t)NB * (NB + 1)); }
 template <class T>
-static size_t panel_vec_smem() { return sizeof(T) * (size_t)SPW * 33; }
+static size_t panel_vec_smem() { return 8 * (size_t)SPW * 33; }
+template <class T>
+static size_t trsm_smem() { return sizeof(T) * (size_t)2 * NB * (NB + 1); }
 template <class T>
 static size_t bwd_part_smem() { return sizeof(T) * ((size_t)RB * (NB + 1) + (size_t)RB * 33); }
 
@@ -582,14 +587,12 @@ static void factor_impl(Factorization &fz, cudaStream_t st) {
     T *arena = static_cast<T *>(fz.arena.m.p);
     T *Dg = static_cast<T *>(fz.D.m.p);
     T *wscr = static_cast<T *>(fz.wscr.m.p);
-    T *linv = static_cast<T *>(fz.linv.m.p);
     static bool attr = false;
     if (!attr) {
-        MBL_CUDA(cudaFuncSetAttribute(k_panel_trsm<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
+        MBL_CUDA(cudaFuncSetAttribute(k_panel_trsm<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)trsm_smem<T>()));
         attr = true;
     }
     set_solve_attrs<T>();
-    size_t trsm_smem = (size_t)(NB + RB) * (NB + 1) * sizeof(T);
     MBL_CUDA(cudaMemsetAsync(fz.counters.data(), 0, 2 * sizeof(unsigned long long), st));
     for (int l = 0; l < p.nlevels; ++l) {
         int na = p.asm_ptr[l + 1] - p.asm_ptr[l];
@@ -602,14 +605,13 @@ static void factor_impl(Factorization &fz, cudaStream_t st) {
         for (int si = p.lvl_step_ptr[l]; si < p.lvl_step_ptr[l + 1]; ++si) {
             const PanelStep &stp = p.steps[si];
             const PanelDesc *dd = p.d_descs.data() + stp.d0;
-            T *lv = linv + (int64_t)stp.d0 * NB * NB;
             k_panel_diag<T><<<stp.nd, 256, 0, st>>>(dd, p.d_sn_fo.data(), p.d_sn_f.data(), p.d_sn_start.data(), arena,
-                                                    Dg, fz.piv.data(), lv, fz.tiny, fz.counters.data());
+                                                    Dg, fz.piv.data(), fz.tiny, fz.counters.data());
             MBL_LAUNCH_CHECK();
             if (stp.n2 > 0) {
-                k_panel_trsm<T><<<(unsigned)stp.n2, 256, trsm_smem, st>>>(dd, stp.nd, p.d_sn_fo.data(), p.d_sn_f.data(),
-                                                                         p.d_sn_start.data(), arena, Dg, fz.piv.data(),
-                                                                         lv, wscr);
+                k_panel_trsm<T><<<(unsigned)stp.n2, RB, trsm_smem<T>(), st>>>(dd, stp.nd, p.d_sn_fo.data(),
+                                                                             p.d_sn_f.data(), p.d_sn_start.data(), arena,
+                                                                             Dg, fz.piv.data(), wscr);
                 MBL_LAUNCH_CHECK();
             }
             if (stp.n3 > 0) {
@@ -627,8 +629,8 @@ static void factor_impl(Factorization &fz, cudaStream_t st) {
     if (!p.sdescs.empty()) {
         dim3 grid((unsigned)p.sdescs.size(), SPW / 32);
         k_build_m<T><<<grid, 256, build_m_smem<T>(), st>>>(p.d_sdescs.data(), p.d_sn_fo.data(), p.d_sn_f.data(),
-                                                           p.d_sn_start.data(), arena, fz.piv.data(), linv,
-                                                           static_cast<T *>(fz.M.m.p));
+                                                           p.d_sn_start.data(), arena, fz.piv.data(),
+                                                           static_cast<double *>(fz.M.m.p));
         MBL_LAUNCH_CHECK();
     }
 }
@@ -645,7 +647,7 @@ static void solve_impl(Factorization &fz, const double *B, int64_t ldb, double *
     int64_t n = pl.n;
     T *arena = static_cast<T *>(fz.arena.m.p);
     T *Dg = static_cast<T *>(fz.D.m.p);
-    const T *M = static_cast<const T *>(fz.M.m.p);
+    const double *M = static_cast<const double *>(fz.M.m.p);
     fz.ensure_solve_work(p);
     set_solve_attrs<T>();
     T *Z = static_cast<T *>(fz.zwork.m.p);
@@ -730,13 +732,9 @@ void Factorization::allocate() {
     piv.alloc(ctx, pl.n);
     counters.alloc(ctx, 2);
     wscr.alloc(ctx, (size_t)std::max<int64_t>(pl.wscratch_elems, 1) * es);
-    linv.alloc(ctx, (size_t)std::max<size_t>(pl.descs.size(), 1) * NB * NB * es);
-    M.alloc(ctx, (size_t)std::max<int64_t>(pl.m_elems, 1) * es);
+    M.alloc(ctx, (size_t)std::max<int64_t>(pl.m_elems, 1) * sizeof(double));
 }
 
-void Factorization::release_scratch() {
-    wscr.release();
-    linv.release();
-}
+void Factorization::release_scratch() { wscr.release(); }
 
 }  // namespace mbl

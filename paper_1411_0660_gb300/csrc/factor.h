@@ -12,7 +12,7 @@ struct Factorization {
     double sigma = 0.0;
     int prec = MBL_PREC_FP32;
     double tiny = 0.0;
-    DVec<char> arena, D, wscr, linv, M, zwork, zsolved, ywork, yfw, pwork;
+    DVec<char> arena, D, wscr, M, zwork, zsolved, ywork, yfw, pwork;
     DVec<int32_t> piv;
     DVec<unsigned long long> counters;  // [0] perturbed pivots, [1] negative pivots
     int work_p = 0;

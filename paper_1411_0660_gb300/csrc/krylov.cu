@@ -555,10 +555,17 @@ void solve_near(mbl_sector *sec, double eps, int nev, const mbl_opts &o, double 
     ncv = std::max(ncv, ((nev + p + p - 1) / p) * p + p);
     if (ncv + p > n) fail(MBL_ERR_INVALID, "Krylov basis larger than the sector");
     if ((ncv + p) * 32 > 8192) fail(MBL_ERR_INVALID, "ncv + block too large (max 256)");
+    // A target at the very edge of the spectrum (eps = 0 or 1) sits on an eigenvalue and makes
+    // H - sigma singular: factor a hair outside the spectrum instead.  The window is still chosen by
+    // distance to sigma; near the edge the nearest eigenvalues are the same.
+    double sigma_f = sigma;
+    const double guard = 1e-8 * hnorm, nudge = 1e-4 * (emax - emin);
+    if (std::fabs(sigma - emin) <= guard) sigma_f = emin - nudge;
+    if (std::fabs(sigma - emax) <= guard) sigma_f = emax + nudge;
     auto tf0 = std::chrono::steady_clock::now();
-    std::unique_ptr<Factorization> fz = make_factorization(sec, sigma, o.precision, hnorm);
+    std::unique_ptr<Factorization> fz = make_factorization(sec, sigma_f, o.precision, hnorm);
     S.ms_factor = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tf0).count();
-    RefinedSolve op{sec, fz.get(), hnorm + std::fabs(sigma), o.refine_tol, o.max_refine};
+    RefinedSolve op{sec, fz.get(), hnorm + std::fabs(sigma_f), o.refine_tol, o.max_refine};
     OpFn opfn = [&](const double *X, int ldx, double *Y, cudaStream_t s) { op.apply(X, ldx, Y, p, s); };
     KrylovSchur ks(ctx, n, p, ncv);
     ks.start(o.start_seed, st);
@@ -577,7 +584,7 @@ void solve_near(mbl_sector *sec, double eps, int nev, const mbl_opts &o, double 
             if (op.stalled && fz->prec == MBL_PREC_FP32) {
                 // refinement stalled near the shift: fall back to FP64 fronts (same basis)
                 auto tf1 = std::chrono::steady_clock::now();
-                fz = make_factorization(sec, sigma, MBL_PREC_FP64, hnorm);
+                fz = make_factorization(sec, sigma_f, MBL_PREC_FP64, hnorm);
                 S.ms_factor += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tf1).count();
                 op.fz = fz.get();
                 op.stalled = false;
@@ -592,7 +599,7 @@ void solve_near(mbl_sector *sec, double eps, int nev, const mbl_opts &o, double 
         double worst = 0.0;
         for (int t = 0; t < nev; ++t) {
             int i = order[t];
-            worst = std::max(worst, (hnorm + std::fabs(sigma)) * rn[i] / std::max(std::fabs(th[i]), 1e-300) / hnorm);
+            worst = std::max(worst, (hnorm + std::fabs(sigma_f)) * rn[i] / std::max(std::fabs(th[i]), 1e-300) / hnorm);
         }
         bool last = restarts >= o.max_restarts;
         if (worst <= screen || last) {
