@@ -64,6 +64,7 @@ typedef struct mbl_opts {
     double refine_tol;    /* refinement stop: ||b - A x|| <= refine_tol (|A||x| + |b|)[1e-15]*/
     int max_refine;       /* refinement steps per application                       [20]   */
     uint64_t start_seed;  /* seed of the random start block                         [12345]*/
+    int tensor_cores;     /* FP32 fronts: Schur updates on tcgen05 (3xTF32) if nonzero [0]   */
 } mbl_opts;
 
 typedef struct mbl_factor_stats {

@@ -13,6 +13,7 @@ numerical-method section, and the observables of the characterization section).
 from __future__ import annotations
 
 import ctypes
+import sys
 from dataclasses import dataclass
 
 import numpy as np
@@ -77,6 +78,10 @@ class Context:
             self.handle = None
 
     def __del__(self):
+        # at interpreter shutdown the release order is arbitrary and the CUDA runtime may be going
+        # away: leave the memory to process exit instead of calling into the library
+        if sys.is_finalizing():
+            return
         try:
             self.close()
         except Exception:
@@ -127,6 +132,10 @@ class Sector:
             self.handle = None
 
     def __del__(self):
+        # at interpreter shutdown the release order is arbitrary and the CUDA runtime may be going
+        # away: leave the memory to process exit instead of calling into the library
+        if sys.is_finalizing():
+            return
         try:
             self.close()
         except Exception:
@@ -182,6 +191,10 @@ class Factorization:
             self.handle = None
 
     def __del__(self):
+        # at interpreter shutdown the release order is arbitrary and the CUDA runtime may be going
+        # away: leave the memory to process exit instead of calling into the library
+        if sys.is_finalizing():
+            return
         try:
             self.close()
         except Exception:

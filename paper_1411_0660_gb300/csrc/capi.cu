@@ -2,6 +2,8 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <mutex>
+#include <set>
 
 #include "krylov.h"
 #include "observables.h"
@@ -9,6 +11,18 @@
 namespace mbl {
 
 std::atomic<long long> g_launches{0};
+
+// Contexts that are alive: objects that outlive their context (a sector or factorization released
+// after mbl_ctx_destroy) free their device memory without touching the dead context.
+static std::mutex g_ctx_mu;
+static std::set<const Ctx *> &live_ctx() {
+    static std::set<const Ctx *> *s = new std::set<const Ctx *>();
+    return *s;
+}
+bool ctx_alive(const Ctx *c) {
+    std::lock_guard<std::mutex> lk(g_ctx_mu);
+    return c && live_ctx().count(c) != 0;
+}
 
 cudaEvent_t Ctx::take_event() {
     if (!event_pool.empty()) {
@@ -86,7 +100,7 @@ void DevMem::alloc(Ctx *c, size_t nbytes) {
 void DevMem::release() {
     if (p) {
         cudaFree(p);
-        if (ctx) ctx->in_use -= bytes;
+        if (ctx && ctx_alive(ctx)) ctx->in_use -= bytes;
     }
     p = nullptr;
     bytes = 0;
@@ -109,7 +123,7 @@ std::shared_ptr<Plan> get_plan(mbl_sector *sec) {
     return P;
 }
 
-std::unique_ptr<Factorization> make_factorization(mbl_sector *sec, double sigma, int prec, double hnorm) {
+std::unique_ptr<Factorization> make_factorization(mbl_sector *sec, double sigma, int prec, double hnorm, bool use_tc) {
     if (prec != MBL_PREC_FP64 && prec != MBL_PREC_FP32) fail(MBL_ERR_INVALID, "unknown precision");
     auto F = std::make_unique<Factorization>();
     F->ctx = sec->ctx;
@@ -118,6 +132,7 @@ std::unique_ptr<Factorization> make_factorization(mbl_sector *sec, double sigma,
     F->sigma = sigma;
     F->prec = prec;
     F->tiny = (prec == MBL_PREC_FP64 ? 1e-12 : 1e-7) * hnorm;
+    F->use_tc = use_tc;
     F->allocate();
     cudaStream_t st = sec->ctx->stream;
     cudaEvent_t e0, e1;
@@ -135,10 +150,11 @@ std::unique_ptr<Factorization> make_factorization(mbl_sector *sec, double sigma,
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     F->ms_factor = ms;
-    unsigned long long cnt[2];
+    unsigned long long cnt[3];
     MBL_CUDA(cudaMemcpy(cnt, F->counters.data(), sizeof(cnt), cudaMemcpyDeviceToHost));
     F->perturbed = (int64_t)cnt[0];
     F->negative = (int64_t)cnt[1];
+    if (cnt[2] != 0) fail(MBL_ERR_TIMEOUT, "tensor-core tile wait timed out in the factorization");
     F->release_scratch();
     return F;
 }
@@ -182,6 +198,7 @@ void mbl_opts_default(mbl_opts *o) {
     o->refine_tol = 1e-15;
     o->max_refine = 20;
     o->start_seed = 12345;
+    o->tensor_cores = 0;
 }
 
 const char *mbl_version(void) { return "mblsi 0.1 (sm_103a)"; }
@@ -217,6 +234,10 @@ int mbl_ctx_create(int device, size_t budget, mbl_ctx **out) {
     MBL_CUDA(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
     MBL_CUDA(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device));
     upload_binomials();
+    {
+        std::lock_guard<std::mutex> lk(g_ctx_mu);
+        live_ctx().insert(c);
+    }
     *out = c;
     c = nullptr;
     }
@@ -250,7 +271,7 @@ int mbl_ctx_profile_get(mbl_ctx *ctx, const char *name, int64_t *launches, doubl
 }
 
 void mbl_ctx_destroy(mbl_ctx *ctx) {
-    if (!ctx) return;
+    if (!ctx || !ctx_alive(ctx)) return;
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
     try { ctx->resolve_profile(); } catch (...) {}
@@ -258,6 +279,10 @@ void mbl_ctx_destroy(mbl_ctx *ctx) {
     ctx->plans.clear();
     ctx->ent.clear();
     cudaStreamDestroy(ctx->stream);
+    {
+        std::lock_guard<std::mutex> lk(g_ctx_mu);
+        live_ctx().erase(ctx);
+    }
     delete ctx;
 }
 
@@ -312,7 +337,7 @@ int mbl_build_sector_fields(mbl_ctx *ctx, int L, const double *h_i, double J, mb
 
 void mbl_sector_destroy(mbl_sector *sec) {
     if (!sec) return;
-    cudaStreamSynchronize(sec->ctx->stream);
+    if (ctx_alive(sec->ctx)) cudaStreamSynchronize(sec->ctx->stream);
     delete sec;
 }
 
@@ -397,7 +422,7 @@ int mbl_factor(mbl_sector *sec, double sigma, const mbl_opts *opts, mbl_factoriz
     double emin, emax;
     extremal_bounds(sec, &emin, &emax);
     double hn = std::max(std::fabs(emin), std::fabs(emax));
-    auto F = make_factorization(sec, sigma, o.precision, hn);
+    auto F = make_factorization(sec, sigma, o.precision, hn, o.tensor_cores != 0);
     mbl_factorization *h = new mbl_factorization();
     h->f = std::move(F);
     *out = h;
@@ -453,7 +478,7 @@ int mbl_factor_solve(mbl_factorization *fh, const double *b, double *x, int nrhs
 
 void mbl_factor_destroy(mbl_factorization *f) {
     if (!f) return;
-    if (f->f) cudaStreamSynchronize(f->f->ctx->stream);
+    if (f->f && ctx_alive(f->f->ctx)) cudaStreamSynchronize(f->f->ctx->stream);
     delete f;
 }
 

@@ -408,24 +408,43 @@ __global__ void __launch_bounds__(256) k_fwd_gather(const AsmItem *items, const 
     }
 }
 
-// forward, one CTA per solve panel: Zs[panel] = M Z[panel]
+constexpr int MCH = 16;  // rows (or columns) of M per CTA in the panel-operator kernels
+
+// forward: Zs[panel rows r0..r0+16) = M[rows, :] Z[panel] (FP64), grid (descs, SPW / MCH).
+// thread (row rr = tid / 16, slice cs = tid % 16) sums columns c = cs, cs + 16, ...; the 16 partial
+// sums of a row are combined with warp shuffles.
 template <class T>
 __global__ void __launch_bounds__(256) k_fwd_m(const SolveDesc *sdescs, const int64_t *zo, const double *Mall,
                                                const T *Z, T *Zs, int p) {
     extern __shared__ __align__(16) unsigned char smraw[];
     double(*zin)[33] = reinterpret_cast<double(*)[33]>(smraw);
     const SolveDesc d = sdescs[blockIdx.x];
-    const int w = d.w;
+    const int w = d.w, r0 = blockIdx.y * MCH;
+    if (r0 >= w) return;
     const T *z = Z + (zo[d.front] + d.k0) * p;
     T *zs = Zs + (zo[d.front] + d.k0) * p;
     for (int idx = threadIdx.x; idx < w * p; idx += blockDim.x) zin[idx / p][idx % p] = (double)z[idx];
     __syncthreads();
     const double *M = Mall + d.moff;
-    for (int idx = threadIdx.x; idx < w * p; idx += blockDim.x) {
-        int r = idx / p, q = idx % p;
-        double acc = 0.0;
-        for (int c = 0; c < w; ++c) acc += M[(int64_t)c * w + r] * zin[c][q];
-        zs[idx] = (T)acc;
+    const int rr = threadIdx.x / 16, cs = threadIdx.x % 16, r = r0 + rr;
+    double acc[32];
+#pragma unroll
+    for (int q = 0; q < 32; ++q) acc[q] = 0.0;
+    if (r < w) {
+#pragma unroll 4
+        for (int c = cs; c < w; c += 16) {
+            const double m = M[(int64_t)c * w + r];
+#pragma unroll
+            for (int q = 0; q < 32; ++q)
+                if (q < p) acc[q] = fma(m, zin[c][q], acc[q]);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 32; ++q) {
+        if (q >= p) break;
+        double v = acc[q];
+        for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (cs == 0 && r < w) zs[(int64_t)r * p + q] = (T)v;
     }
 }
 
@@ -451,6 +470,7 @@ __global__ void __launch_bounds__(256) k_fwd_upd(const SolveDesc *sdescs, int nd
     for (int q = threadIdx.x / RB; q < p; q += blockDim.x / RB) {
         T acc = T(0);
         const T *col = F + (int64_t)k0 * f + r0 + i;
+#pragma unroll 8
         for (int c = 0; c < w; ++c) acc += col[(int64_t)c * f] * zp[c][q];
         z[(int64_t)(r0 + i) * p + q] -= acc;
     }
@@ -511,36 +531,65 @@ __global__ void __launch_bounds__(256) k_bwd_part(const SolveDesc *sdescs, int n
         for (int o = threadIdx.x; o < wc * p; o += blockDim.x) {
             int c = o / p, q = o % p;
             T acc = T(0);
+#pragma unroll 8
             for (int i = 0; i < nr; ++i) acc += Fs[i][c] * zr[i][q];
             out[(cc + c) * 32 + q] = acc;
         }
     }
 }
 
-// backward, one CTA per solve panel: Z[panel] = M^T (Z[panel] - sum of partials)
+// backward, rows r0..r0+16 of each panel: Zs[panel] = Z[panel] - sum over row blocks of the partials
+template <class T>
+__global__ void __launch_bounds__(256) k_bwd_reduce(const SolveDesc *sdescs, const int64_t *zo, const T *P,
+                                                    const T *Z, T *Zs, int p) {
+    const SolveDesc d = sdescs[blockIdx.x];
+    const int w = d.w, r0 = blockIdx.y * MCH;
+    if (r0 >= w) return;
+    const int64_t nrb = d.m2 > 0 ? (d.m2 + RB - 1) / RB : 1;
+    const int64_t off = (zo[d.front] + d.k0) * p;
+    for (int idx = threadIdx.x; idx < MCH * p; idx += blockDim.x) {
+        int r = r0 + idx / p, q = idx % p;
+        if (r >= w) continue;
+        double v = (double)Z[off + (int64_t)r * p + q];
+#pragma unroll 8
+        for (int64_t b = 0; b < nrb; ++b) v -= (double)P[(d.off + b) * SPW * 32 + r * 32 + q];
+        Zs[off + (int64_t)r * p + q] = (T)v;
+    }
+}
+
+// backward: Z[panel columns c0..c0+16) = M[:, cols]^T Zs[panel] (FP64), grid (descs, SPW / MCH)
 template <class T>
 __global__ void __launch_bounds__(256) k_bwd_m(const SolveDesc *sdescs, const int64_t *zo, const double *Mall,
-                                               const T *P, T *Z, int p) {
+                                               const T *Zs, T *Z, int p) {
     extern __shared__ __align__(16) unsigned char smraw[];
     double(*zb)[33] = reinterpret_cast<double(*)[33]>(smraw);
     const SolveDesc d = sdescs[blockIdx.x];
-    const int w = d.w;
-    const int64_t nrb = d.m2 > 0 ? (d.m2 + RB - 1) / RB : 1;
-    T *z = Z + (zo[d.front] + d.k0) * p;
-    for (int idx = threadIdx.x; idx < w * p; idx += blockDim.x) {
-        int r = idx / p, q = idx % p;
-        double v = (double)z[idx];
-        for (int64_t b = 0; b < nrb; ++b) v -= (double)P[(d.off + b) * SPW * 32 + r * 32 + q];
-        zb[r][q] = v;
-    }
+    const int w = d.w, c0 = blockIdx.y * MCH;
+    if (c0 >= w) return;
+    const int64_t off = (zo[d.front] + d.k0) * p;
+    for (int idx = threadIdx.x; idx < w * p; idx += blockDim.x) zb[idx / p][idx % p] = (double)Zs[off + idx];
     __syncthreads();
     const double *M = Mall + d.moff;
-    for (int idx = threadIdx.x; idx < w * p; idx += blockDim.x) {
-        int c = idx / p, q = idx % p;
+    const int cc = threadIdx.x / 16, rs = threadIdx.x % 16, c = c0 + cc;
+    double acc[32];
+#pragma unroll
+    for (int q = 0; q < 32; ++q) acc[q] = 0.0;
+    if (c < w) {
         const double *mc = M + (int64_t)c * w;
-        double acc = 0.0;
-        for (int r = 0; r < w; ++r) acc += mc[r] * zb[r][q];
-        z[idx] = (T)acc;
+#pragma unroll 4
+        for (int r = rs; r < w; r += 16) {
+            const double m = mc[r];
+#pragma unroll
+            for (int q = 0; q < 32; ++q)
+                if (q < p) acc[q] = fma(m, zb[r][q], acc[q]);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 32; ++q) {
+        if (q >= p) break;
+        double v = acc[q];
+        for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (rs == 0 && c < w) Z[off + (int64_t)c * p + q] = (T)v;
     }
 }
 
@@ -593,7 +642,7 @@ static void factor_impl(Factorization &fz, cudaStream_t st) {
         attr = true;
     }
     set_solve_attrs<T>();
-    MBL_CUDA(cudaMemsetAsync(fz.counters.data(), 0, 2 * sizeof(unsigned long long), st));
+    MBL_CUDA(cudaMemsetAsync(fz.counters.data(), 0, 3 * sizeof(unsigned long long), st));
     for (int l = 0; l < p.nlevels; ++l) {
         int na = p.asm_ptr[l + 1] - p.asm_ptr[l];
         k_assemble<T><<<na, 256, 0, st>>>(p.d_asm_items.data() + p.asm_ptr[l], p.d_sn_fo.data(), p.d_sn_f.data(),
@@ -618,10 +667,16 @@ static void factor_impl(Factorization &fz, cudaStream_t st) {
                 double fl = 0.0;  // algorithmic flops: lower triangle of the trailing block, 2 per entry per k
                 for (int q = stp.d0; q < stp.d0 + stp.nd; ++q)
                     fl += (double)p.descs[q].m2 * (p.descs[q].m2 + 1) * p.descs[q].w;
-                ProfScope ps(fz.ctx, sizeof(T) == 8 ? "schur_fp64" : "schur_fp32", fl, st);
-                k_panel_update<T><<<(unsigned)stp.n3, 256, 0, st>>>(dd, stp.nd, p.d_sn_fo.data(), p.d_sn_f.data(), arena,
-                                                                    wscr);
-                MBL_LAUNCH_CHECK();
+                if (sizeof(T) == 4 && fz.use_tc) {
+                    ProfScope ps(fz.ctx, "schur_tc", fl, st);
+                    launch_schur_tc(stp, dd, p, reinterpret_cast<float *>(arena), reinterpret_cast<const float *>(wscr),
+                                    fz.counters.data() + 2, st);
+                } else {
+                    ProfScope ps(fz.ctx, sizeof(T) == 8 ? "schur_fp64" : "schur_fp32", fl, st);
+                    k_panel_update<T><<<(unsigned)stp.n3, 256, 0, st>>>(dd, stp.nd, p.d_sn_fo.data(), p.d_sn_f.data(),
+                                                                        arena, wscr);
+                    MBL_LAUNCH_CHECK();
+                }
             }
         }
     }
@@ -672,7 +727,7 @@ static void solve_impl(Factorization &fz, const double *B, int64_t ldb, double *
         for (int si = pl.lvl_sstep_ptr[l]; si < pl.lvl_sstep_ptr[l + 1]; ++si) {
             const SolveStep &ss = pl.ssteps[si];
             const SolveDesc *sd = pl.d_sdescs.data() + ss.d0;
-            k_fwd_m<T><<<ss.nd, 256, vsm, st>>>(sd, pl.d_sn_zo.data(), M, Z, Zs, p);
+            k_fwd_m<T><<<dim3(ss.nd, SPW / MCH), 256, vsm, st>>>(sd, pl.d_sn_zo.data(), M, Z, Zs, p);
             MBL_LAUNCH_CHECK();
             k_fwd_upd<T><<<(unsigned)ss.nrb, 256, vsm, st>>>(sd, ss.nd, pl.d_sn_fo.data(), pl.d_sn_zo.data(),
                                                              pl.d_sn_f.data(), arena, Zs, Z, p);
@@ -695,7 +750,9 @@ static void solve_impl(Factorization &fz, const double *B, int64_t ldb, double *
             k_bwd_part<T><<<(unsigned)ss.nrb, 256, psm, st>>>(sd, ss.nd, pl.d_sn_fo.data(), pl.d_sn_zo.data(),
                                                               pl.d_sn_f.data(), arena, Z, p, P);
             MBL_LAUNCH_CHECK();
-            k_bwd_m<T><<<ss.nd, 256, vsm, st>>>(sd, pl.d_sn_zo.data(), M, P, Z, p);
+            k_bwd_reduce<T><<<dim3(ss.nd, SPW / MCH), 256, 0, st>>>(sd, pl.d_sn_zo.data(), P, Z, Zs, p);
+            MBL_LAUNCH_CHECK();
+            k_bwd_m<T><<<dim3(ss.nd, SPW / MCH), 256, vsm, st>>>(sd, pl.d_sn_zo.data(), M, Zs, Z, p);
             MBL_LAUNCH_CHECK();
         }
         k_bwd_finish<T><<<na, 256, 0, st>>>(items, pl.d_sn_zo.data(), pl.d_sn_nc.data(), pl.d_sn_start.data(), Z, y, p);
@@ -730,7 +787,7 @@ void Factorization::allocate() {
     arena.alloc(ctx, (size_t)pl.arena_elems * es);
     D.alloc(ctx, (size_t)pl.n * es);
     piv.alloc(ctx, pl.n);
-    counters.alloc(ctx, 2);
+    counters.alloc(ctx, 3);
     wscr.alloc(ctx, (size_t)std::max<int64_t>(pl.wscratch_elems, 1) * es);
     M.alloc(ctx, (size_t)std::max<int64_t>(pl.m_elems, 1) * sizeof(double));
 }

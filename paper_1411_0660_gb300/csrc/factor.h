@@ -14,8 +14,9 @@ struct Factorization {
     double tiny = 0.0;
     DVec<char> arena, D, wscr, M, zwork, zsolved, ywork, yfw, pwork;
     DVec<int32_t> piv;
-    DVec<unsigned long long> counters;  // [0] perturbed pivots, [1] negative pivots
+    DVec<unsigned long long> counters;  // [0] perturbed pivots, [1] negative pivots, [2] wait time-outs
     int work_p = 0;
+    bool use_tc = true;  // tcgen05 Schur updates for FP32 fronts
     int64_t perturbed = 0, negative = 0;
     double ms_factor = 0.0;
 
@@ -24,6 +25,11 @@ struct Factorization {
     void release_scratch();
     void ensure_solve_work(int p);
 };
+
+// tcgen05 trailing update of one panel step (FP32 fronts); err counts bounded-wait time-outs.
+size_t schur_tc_smem();
+void launch_schur_tc(const PanelStep &stp, const PanelDesc *d_descs, const Plan &p, float *arena, const float *wscr,
+                     unsigned long long *err, cudaStream_t st);
 
 // Enqueue the numeric factorization of H - sigma I (allocate() first).
 void numeric_factor(Factorization &fz, cudaStream_t st);
@@ -34,7 +40,8 @@ void factor_solve_raw(Factorization &fz, const double *B, int64_t ldb, double *X
 // Plan of the sector's L (built from the device CSR on first use and cached in the context).
 std::shared_ptr<Plan> get_plan(mbl_sector *sec);
 // Create, allocate and run a factorization (synchronous; fills stats).
-std::unique_ptr<Factorization> make_factorization(mbl_sector *sec, double sigma, int prec, double hnorm);
+std::unique_ptr<Factorization> make_factorization(mbl_sector *sec, double sigma, int prec, double hnorm,
+                                                  bool use_tc = true);
 
 }  // namespace mbl
 

@@ -563,7 +563,7 @@ void solve_near(mbl_sector *sec, double eps, int nev, const mbl_opts &o, double 
     if (std::fabs(sigma - emin) <= guard) sigma_f = emin - nudge;
     if (std::fabs(sigma - emax) <= guard) sigma_f = emax + nudge;
     auto tf0 = std::chrono::steady_clock::now();
-    std::unique_ptr<Factorization> fz = make_factorization(sec, sigma_f, o.precision, hnorm);
+    std::unique_ptr<Factorization> fz = make_factorization(sec, sigma_f, o.precision, hnorm, o.tensor_cores != 0);
     S.ms_factor = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tf0).count();
     RefinedSolve op{sec, fz.get(), hnorm + std::fabs(sigma_f), o.refine_tol, o.max_refine};
     OpFn opfn = [&](const double *X, int ldx, double *Y, cudaStream_t s) { op.apply(X, ldx, Y, p, s); };

@@ -39,6 +39,7 @@ extern std::atomic<long long> g_launches;
     } while (0)
 
 struct Ctx;
+bool ctx_alive(const Ctx *c);
 
 // Device allocation accounted against the context budget (admission control).
 struct DevMem {

@@ -27,12 +27,14 @@ struct PanelDesc {
     int64_t off2;    // prefix count of row blocks (stage 2) before this descriptor in its step
     int64_t off3;    // prefix count of trailing tiles (stage 3) before this descriptor in its step
     int64_t woff;    // offset (elements) of this front's W21 scratch (m2 x NB column-major, ld m2)
+    int64_t off3t;   // prefix count of 128 x 128 tensor-core tiles before this descriptor in its step
 };
 
 struct PanelStep {
     int32_t level, kk;
     int32_t d0, nd;  // descriptor range
     int64_t n2, n3;  // row blocks and trailing tiles in this step
+    int64_t n3t;     // 128 x 128 tensor-core tiles in this step
     int64_t wsize;   // W21 scratch elements used by this step
 };
 

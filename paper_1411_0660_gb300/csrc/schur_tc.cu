@@ -1,0 +1,227 @@
+// schur_tc.cu -- trailing (Schur) update of the frontal matrices on the tcgen05 tensor cores.
+//
+// The dense contraction of the multifrontal LDL^T (numerical-method section of arXiv:1411.0660,
+// through the factorization of H - sigma): C[i][j] -= sum_t L21[i][t] W21[j][t] on the lower
+// triangle of the trailing block, K = panel width (<= 64).  FP32 data, FP32 accumulation.  Each
+// operand x is split into two TF32 pieces x = hi + lo (hi = x rounded to TF32, lo = x - hi), and
+// three kind::tf32 MMAs accumulate hi*hi + hi*lo + lo*hi into a 128 x 128 FP32 tile in tensor
+// memory (TMEM).  One CTA of 128 threads per tile:
+//   1. every thread stages its row's operands into shared memory in the canonical K-major,
+//      no-swizzle core-matrix layout (8 rows x 16 bytes per core matrix), one 16-byte vector per
+//      store, then fences the generic-proxy writes for the tensor core;
+//   2. one thread issues 3 * (K / 8) tcgen05.mma and a tcgen05.commit to an mbarrier;
+//   3. all threads wait on the mbarrier (bounded by %globaltimer: on expiry the CTA flags an
+//      error, skips its epilogue, frees its TMEM and returns), read the accumulator with
+//      tcgen05.ld (warp w owns TMEM lanes 32w..32w+31 = tile rows), and subtract it from the
+//      front in global memory (coalesced along the rows).
+#include "factor.h"
+
+namespace mbl {
+
+namespace {
+
+constexpr int TM = 128, TN = 128, TK = NB;  // tile and maximal K
+constexpr int KG = TK / 4;                   // 16-byte k groups per row
+constexpr uint32_t CORE = 128;               // bytes per core matrix
+constexpr uint32_t SBO = KG * CORE;          // next 8-row group
+constexpr uint32_t LBO = CORE;               // next k group
+constexpr uint32_t OPB = TM * TK * 4;        // bytes per operand piece (32 KB)
+constexpr uint32_t TMEM_COLS = 128;
+
+// instruction descriptor of kind::tf32: D = F32, A = B = TF32, both K-major, N = 128, M = 128
+constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TN >> 3) << 17) |
+                           ((uint32_t)(TM >> 4) << 24);
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((LBO >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((SBO >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;  // fixed 0b001 at bits 46..48; base offset 0, no swizzle
+    return d;
+}
+
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ uint64_t globaltimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// bounded wait on phase `parity` of an mbarrier; returns false on time-out
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, uint64_t limit_ns) {
+    uint64_t t0 = globaltimer();
+    while (true) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(mbar), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (globaltimer() - t0 > limit_ns) return false;
+    }
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+}
+
+__device__ __forceinline__ int find_desc3t(const PanelDesc *d, int nd, int64_t b) {
+    int lo = 0, hi = nd - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (d[mid].off3t <= b) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// stage one operand (128 rows x w <= 64 columns, column-major source with leading dimension ld,
+// rows past `rows` and columns past `w` zero) as TF32 hi and lo pieces
+__device__ __forceinline__ void stage(const float *src, int64_t ld, int rows, int w, unsigned char *hi,
+                                      unsigned char *lo) {
+    const int r = threadIdx.x;  // one row per thread
+    const uint32_t rowoff = (uint32_t)(r >> 3) * SBO + (uint32_t)(r & 7) * 16u;
+#pragma unroll 4
+    for (int c = 0; c < KG; ++c) {
+        float v[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            int k = 4 * c + e;
+            v[e] = (r < rows && k < w) ? src[(int64_t)k * ld + r] : 0.0f;
+        }
+        uint4 h, l;
+        uint32_t hv[4], lv[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            hv[e] = to_tf32(v[e]);
+            lv[e] = to_tf32(v[e] - __uint_as_float(hv[e]));
+        }
+        h = make_uint4(hv[0], hv[1], hv[2], hv[3]);
+        l = make_uint4(lv[0], lv[1], lv[2], lv[3]);
+        *reinterpret_cast<uint4 *>(hi + rowoff + (uint32_t)c * CORE) = h;
+        *reinterpret_cast<uint4 *>(lo + rowoff + (uint32_t)c * CORE) = l;
+    }
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(TM) k_schur_tc(const PanelDesc *descs, int nd, const int64_t *fo, const int32_t *fsz,
+                                                 float *arena, const float *wscr, unsigned long long *err) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tmem_slot;
+    unsigned char *Ahi = sm, *Alo = sm + OPB, *Bhi = sm + 2 * OPB, *Blo = sm + 3 * OPB;
+
+    const int di = find_desc3t(descs, nd, blockIdx.x);
+    const PanelDesc d = descs[di];
+    const int s = d.front, f = fsz[s], k0 = d.k0, w = d.w, m2 = d.m2;
+    const int64_t t = (int64_t)blockIdx.x - d.off3t;
+    int bi = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+    while ((int64_t)(bi + 1) * (bi + 2) / 2 <= t) ++bi;
+    while ((int64_t)bi * (bi + 1) / 2 > t) --bi;
+    const int bj = (int)(t - (int64_t)bi * (bi + 1) / 2);
+    const int base = k0 + w;
+    const int i0 = base + bi * TM, j0 = base + bj * TN;
+    float *F = arena + fo[s];
+    const float *W = wscr + d.woff;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    // TMEM accumulator (one warp allocates) and the completion barrier
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    }
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&mbar)));
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    // operands: A = L21 rows i0.. (columns k0..k0+w of the front), B = W21 rows j0..
+    stage(F + (int64_t)k0 * f + i0, f, min(TM, f - i0), w, Ahi, Alo);
+    stage(W + (j0 - base), m2, min(TN, f - j0), w, Bhi, Blo);
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+
+    if (threadIdx.x == 0) {
+        const int ksteps = (w + 7) / 8;
+        uint32_t acc = 0;
+        for (int ks = 0; ks < ksteps; ++ks) {
+            const uint32_t koff = (uint32_t)ks * 2u * CORE;  // two k groups per MMA (K = 8 TF32)
+            const uint64_t ah = sdesc(smem_u32(Ahi) + koff), al = sdesc(smem_u32(Alo) + koff);
+            const uint64_t bh = sdesc(smem_u32(Bhi) + koff), bl = sdesc(smem_u32(Blo) + koff);
+            const uint64_t as[3] = {ah, ah, al}, bs[3] = {bh, bl, bh};
+#pragma unroll
+            for (int u = 0; u < 3; ++u) {
+                asm volatile(
+                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                    " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                    "l"(as[u]), "l"(bs[u]), "r"(IDESC), "r"(acc));
+                acc = 1;
+            }
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                         smem_u32(&mbar))
+                     : "memory");
+    }
+    const bool ok = mbar_wait(smem_u32(&mbar), 0, 2000000000ull);
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    if (!ok) {
+        if (lane == 0) atomicAdd(err, 1ull);
+        mbar_wait(smem_u32(&mbar), 0, 2000000000ull);  // give the in-flight MMAs a second chance
+    } else {
+        const int gi = i0 + warp * 32 + lane;
+#pragma unroll 1
+        for (int jc = 0; jc < TN; jc += 32) {
+            uint32_t r[32];
+            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)jc, r);
+            if (gi < f) {
+#pragma unroll
+                for (int c = 0; c < 32; ++c) {
+                    const int gj = j0 + jc + c;
+                    if (gj < f && gi >= gj) F[(int64_t)gj * f + gi] -= __uint_as_float(r[c]);
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TMEM_COLS));
+}
+
+size_t schur_tc_smem() { return 4 * (size_t)OPB; }
+
+void launch_schur_tc(const PanelStep &stp, const PanelDesc *d_descs, const Plan &p, float *arena, const float *wscr,
+                     unsigned long long *err, cudaStream_t st) {
+    static bool attr = false;
+    if (!attr) {
+        MBL_CUDA(cudaFuncSetAttribute(k_schur_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)schur_tc_smem()));
+        attr = true;
+    }
+    k_schur_tc<<<(unsigned)stp.n3t, TM, schur_tc_smem(), st>>>(d_descs, stp.nd, p.d_sn_fo.data(), p.d_sn_f.data(), arena,
+                                                               wscr, err);
+    MBL_LAUNCH_CHECK();
+}
+
+}  // namespace mbl

@@ -506,19 +506,21 @@ std::shared_ptr<Plan> build_plan(int L, const std::vector<uint32_t> &states, con
         }
         p.asm_ptr[l + 1] = (int32_t)p.asm_items.size();
         for (int32_t kk = 0; kk * NB < maxnc; ++kk) {
-            PanelStep stp{l, kk, (int32_t)p.descs.size(), 0, 0, 0, 0};
+            PanelStep stp{l, kk, (int32_t)p.descs.size(), 0, 0, 0, 0, 0};
             for (int32_t q = p.lvl_ptr[l]; q < p.lvl_ptr[l + 1]; ++q) {
                 int32_t s = p.lvl_fronts[q];
                 int32_t k0 = kk * NB;
                 if (p.sn_nc[s] <= k0) continue;
                 int32_t w = std::min(NB, p.sn_nc[s] - k0);
                 int32_t m2 = p.sn_f[s] - k0 - w;
-                PanelDesc d{s, k0, w, m2, stp.n2, stp.n3, stp.wsize};
+                PanelDesc d{s, k0, w, m2, stp.n2, stp.n3, stp.wsize, stp.n3t};
                 fd_of[fd_off[s] + kk] = (int32_t)p.descs.size();
                 int64_t nb2 = (m2 + RB - 1) / RB;
                 int64_t T = (m2 + TB - 1) / TB;
                 stp.n2 += nb2;
                 stp.n3 += T * (T + 1) / 2;
+                int64_t Tt = (m2 + 127) / 128;
+                stp.n3t += Tt * (Tt + 1) / 2;
                 stp.wsize += (int64_t)m2 * NB;
                 p.descs.push_back(d);
             }
