@@ -79,6 +79,8 @@ typedef struct mbl_factor_stats {
     double factor_bytes;    /* bytes of the stored factor */
     double front_bytes;     /* bytes of the frontal arena (factor + contribution blocks) */
     double ms_factor;       /* device time of the numeric factorization */
+    double max_abs_l;       /* largest |L_ij| (element growth of the pivoting) */
+    double min_abs_d;       /* smallest |D_jj| */
 } mbl_factor_stats;
 
 typedef struct mbl_solve_stats {

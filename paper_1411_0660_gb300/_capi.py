@@ -31,7 +31,8 @@ class Opts(ctypes.Structure):
 class FactorStats(ctypes.Structure):
     _fields_ = [("n", c_int64), ("nnz_l", c_int64), ("n_supernodes", c_int64), ("max_front", c_int64),
                 ("tree_levels", c_int64), ("perturbed", c_int64), ("negative", c_int64), ("flops", c_double),
-                ("factor_bytes", c_double), ("front_bytes", c_double), ("ms_factor", c_double)]
+                ("factor_bytes", c_double), ("front_bytes", c_double), ("ms_factor", c_double),
+                ("max_abs_l", c_double), ("min_abs_d", c_double)]
 
 
 class SolveStats(ctypes.Structure):

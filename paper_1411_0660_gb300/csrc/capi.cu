@@ -150,10 +150,13 @@ std::unique_ptr<Factorization> make_factorization(mbl_sector *sec, double sigma,
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     F->ms_factor = ms;
-    unsigned long long cnt[3];
+    unsigned long long cnt[5];
     MBL_CUDA(cudaMemcpy(cnt, F->counters.data(), sizeof(cnt), cudaMemcpyDeviceToHost));
     F->perturbed = (int64_t)cnt[0];
     F->negative = (int64_t)cnt[1];
+    uint32_t ml = (uint32_t)(cnt[3] & 0xffffffffu), md = (uint32_t)(cnt[4] & 0xffffffffu);
+    std::memcpy(&F->max_l, &ml, 4);
+    std::memcpy(&F->min_d, &md, 4);
     if (cnt[2] != 0) fail(MBL_ERR_TIMEOUT, "tensor-core tile wait timed out in the factorization");
     F->release_scratch();
     return F;
@@ -444,6 +447,8 @@ int mbl_factor_stats_get(const mbl_factorization *fh, mbl_factor_stats *s) {
     s->factor_bytes = (double)(p.nnz_l + p.n) * f.elem_size();
     s->front_bytes = (double)p.arena_elems * f.elem_size();
     s->ms_factor = f.ms_factor;
+    s->max_abs_l = f.max_l;
+    s->min_abs_d = f.min_d;
     return MBL_OK;
 }
 

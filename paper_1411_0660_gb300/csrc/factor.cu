@@ -165,6 +165,10 @@ __global__ void __launch_bounds__(256) k_panel_diag(const PanelDesc *descs, cons
     if (tid < w) {
         Dg[g0 + tid] = B[tid][tid];
         piv[g0 + tid] = k0 + perm[tid];
+        float lmax = 0.f;
+        for (int r = tid + 1; r < w; ++r) lmax = fmaxf(lmax, (float)tabs(B[r][tid]));
+        atomicMax(reinterpret_cast<unsigned int *>(counters + 3), __float_as_uint(lmax));
+        atomicMin(reinterpret_cast<unsigned int *>(counters + 4), __float_as_uint((float)tabs(B[tid][tid])));
     }
 }
 
@@ -173,7 +177,8 @@ __global__ void __launch_bounds__(256) k_panel_diag(const PanelDesc *descs, cons
 template <class T>
 __global__ void __launch_bounds__(RB) k_panel_trsm(const PanelDesc *descs, int nd, const int64_t *fo,
                                                    const int32_t *fsz, const int32_t *sn_start, T *arena,
-                                                   const T *Dg, const int32_t *piv, T *wscr) {
+                                                   const T *Dg, const int32_t *piv, T *wscr,
+                                                   unsigned long long *stats) {
     extern __shared__ __align__(16) unsigned char smraw[];
     T(*Lb)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(smraw);                      // L11
     T(*As)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(smraw + sizeof(T) * NB * (NB + 1));
@@ -211,12 +216,16 @@ __global__ void __launch_bounds__(RB) k_panel_trsm(const PanelDesc *descs, int n
     }
     __syncthreads();
     T *W = wscr + d.woff;
+    float lmax = 0.f;
     for (int idx = tid; idx < nr * w; idx += blockDim.x) {
         int i = idx % nr, t = idx / nr;
         T x = As[i][t];
-        F[(int64_t)(k0 + t) * f + r0 + i] = x * Dinv[t];
+        T l = x * Dinv[t];
+        F[(int64_t)(k0 + t) * f + r0 + i] = l;
         W[(int64_t)(r0 - k0 - w + i) + (int64_t)t * m2] = x;
+        lmax = fmaxf(lmax, (float)tabs(l));
     }
+    atomicMax(reinterpret_cast<unsigned int *>(stats), __float_as_uint(lmax));
 }
 
 // Trailing update of one 64 x 64 lower tile: C[i][j] -= sum_t L21[i][t] W21[j][t]
@@ -322,7 +331,7 @@ __device__ __forceinline__ int find_sdesc(const SolveDesc *d, int nd, int64_t b)
 template <class T>
 __global__ void __launch_bounds__(256) k_build_m(const SolveDesc *sdescs, const int64_t *fo, const int32_t *fsz,
                                                  const int32_t *sn_start, const T *arena, const int32_t *piv,
-                                                 double *Mall) {
+                                                 T *Mall) {
     extern __shared__ __align__(16) unsigned char smraw[];
     double(*Zc)[33] = reinterpret_cast<double(*)[33]>(smraw);                          // SPW x 33
     double(*Zp)[33] = reinterpret_cast<double(*)[33]>(smraw + 8 * SPW * 33);           // NB x 33
@@ -374,10 +383,10 @@ __global__ void __launch_bounds__(256) k_build_m(const SolveDesc *sdescs, const 
         }
         __syncthreads();
     }
-    double *M = Mall + d.moff;
+    T *M = Mall + d.moff;
     for (int idx = threadIdx.x; idx < ncol * w; idx += blockDim.x) {
         int c = idx / w, r = idx % w;
-        M[(int64_t)(c0 + c) * w + r] = Zc[r][c];
+        M[(int64_t)(c0 + c) * w + r] = (T)Zc[r][c];
     }
 }
 
@@ -408,63 +417,42 @@ __global__ void __launch_bounds__(256) k_fwd_gather(const AsmItem *items, const 
     }
 }
 
-constexpr int MCH = 16;  // rows (or columns) of M per CTA in the panel-operator kernels
+constexpr int MCH = 16;  // columns of M^T per CTA in the backward panel-operator kernel
 
-// forward: Zs[panel rows r0..r0+16) = M[rows, :] Z[panel] (FP64), grid (descs, SPW / MCH).
-// thread (row rr = tid / 16, slice cs = tid % 16) sums columns c = cs, cs + 16, ...; the 16 partial
-// sums of a row are combined with warp shuffles.
+// forward step, one CTA per row block of a solve panel (at least one per panel): zo = M Z[panel]
+// (recomputed by every CTA of the panel; the first one stores it in Zs), then
+// Z[rows of the block] -= L[rows, panel] zo.
 template <class T>
-__global__ void __launch_bounds__(256) k_fwd_m(const SolveDesc *sdescs, const int64_t *zo, const double *Mall,
-                                               const T *Z, T *Zs, int p) {
+__global__ void __launch_bounds__(256) k_fwd_step(const SolveDesc *sdescs, int nd, const int64_t *fo,
+                                                  const int64_t *zo, const int32_t *fsz, const T *arena,
+                                                  const T *Mall, T *Z, T *Zs, int p) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    double(*zin)[33] = reinterpret_cast<double(*)[33]>(smraw);
-    const SolveDesc d = sdescs[blockIdx.x];
-    const int w = d.w, r0 = blockIdx.y * MCH;
-    if (r0 >= w) return;
-    const T *z = Z + (zo[d.front] + d.k0) * p;
-    T *zs = Zs + (zo[d.front] + d.k0) * p;
-    for (int idx = threadIdx.x; idx < w * p; idx += blockDim.x) zin[idx / p][idx % p] = (double)z[idx];
-    __syncthreads();
-    const double *M = Mall + d.moff;
-    const int rr = threadIdx.x / 16, cs = threadIdx.x % 16, r = r0 + rr;
-    double acc[32];
-#pragma unroll
-    for (int q = 0; q < 32; ++q) acc[q] = 0.0;
-    if (r < w) {
-#pragma unroll 4
-        for (int c = cs; c < w; c += 16) {
-            const double m = M[(int64_t)c * w + r];
-#pragma unroll
-            for (int q = 0; q < 32; ++q)
-                if (q < p) acc[q] = fma(m, zin[c][q], acc[q]);
-        }
-    }
-#pragma unroll
-    for (int q = 0; q < 32; ++q) {
-        if (q >= p) break;
-        double v = acc[q];
-        for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (cs == 0 && r < w) zs[(int64_t)r * p + q] = (T)v;
-    }
-}
-
-// forward, rows below each solve panel: Z[r] -= L[r, panel] Zs[panel]
-template <class T>
-__global__ void __launch_bounds__(256) k_fwd_upd(const SolveDesc *sdescs, int nd, const int64_t *fo, const int64_t *zo,
-                                                 const int32_t *fsz, const T *arena, const T *Zs, T *Z, int p) {
-    extern __shared__ __align__(16) unsigned char smraw[];
-    T(*zp)[33] = reinterpret_cast<T(*)[33]>(smraw);
+    T(*zin)[33] = reinterpret_cast<T(*)[33]>(smraw);
+    T(*zp)[33] = reinterpret_cast<T(*)[33]>(smraw + sizeof(T) * SPW * 33);
     const int di = find_sdesc(sdescs, nd, blockIdx.x);
     const SolveDesc d = sdescs[di];
     const int s = d.front, f = fsz[s], k0 = d.k0, w = d.w;
-    const int r0 = k0 + w + (int)(blockIdx.x - d.off) * RB;
+    const int rb = (int)(blockIdx.x - d.off);
+    T *z = Z + zo[s] * p;
+    for (int idx = threadIdx.x; idx < w * p; idx += blockDim.x) zin[idx / p][idx % p] = z[(int64_t)k0 * p + idx];
+    __syncthreads();
+    const T *M = Mall + d.moff;
+    for (int idx = threadIdx.x; idx < w * p; idx += blockDim.x) {
+        const int r = idx / p, q = idx % p;
+        T acc = T(0);
+#pragma unroll 8
+        for (int c = 0; c < w; ++c) acc += M[(int64_t)c * w + r] * zin[c][q];
+        zp[r][q] = acc;
+    }
+    __syncthreads();
+    if (rb == 0) {
+        T *zs = Zs + (zo[s] + k0) * p;
+        for (int idx = threadIdx.x; idx < w * p; idx += blockDim.x) zs[idx] = zp[idx / p][idx % p];
+    }
+    const int r0 = k0 + w + rb * RB;
     if (r0 >= f) return;
     const int nr = min(RB, f - r0);
     const T *F = arena + fo[s];
-    const T *zs = Zs + (zo[s] + k0) * p;
-    T *z = Z + zo[s] * p;
-    for (int idx = threadIdx.x; idx < w * p; idx += blockDim.x) zp[idx / p][idx % p] = zs[idx];
-    __syncthreads();
     const int i = threadIdx.x % RB;
     if (i >= nr) return;
     for (int q = threadIdx.x / RB; q < p; q += blockDim.x / RB) {
@@ -550,44 +538,44 @@ __global__ void __launch_bounds__(256) k_bwd_reduce(const SolveDesc *sdescs, con
     for (int idx = threadIdx.x; idx < MCH * p; idx += blockDim.x) {
         int r = r0 + idx / p, q = idx % p;
         if (r >= w) continue;
-        double v = (double)Z[off + (int64_t)r * p + q];
+        T v = Z[off + (int64_t)r * p + q];
 #pragma unroll 8
-        for (int64_t b = 0; b < nrb; ++b) v -= (double)P[(d.off + b) * SPW * 32 + r * 32 + q];
+        for (int64_t b = 0; b < nrb; ++b) v -= P[(d.off + b) * SPW * 32 + r * 32 + q];
         Zs[off + (int64_t)r * p + q] = (T)v;
     }
 }
 
 // backward: Z[panel columns c0..c0+16) = M[:, cols]^T Zs[panel] (FP64), grid (descs, SPW / MCH)
 template <class T>
-__global__ void __launch_bounds__(256) k_bwd_m(const SolveDesc *sdescs, const int64_t *zo, const double *Mall,
+__global__ void __launch_bounds__(256) k_bwd_m(const SolveDesc *sdescs, const int64_t *zo, const T *Mall,
                                                const T *Zs, T *Z, int p) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    double(*zb)[33] = reinterpret_cast<double(*)[33]>(smraw);
+    T(*zb)[33] = reinterpret_cast<T(*)[33]>(smraw);
     const SolveDesc d = sdescs[blockIdx.x];
     const int w = d.w, c0 = blockIdx.y * MCH;
     if (c0 >= w) return;
     const int64_t off = (zo[d.front] + d.k0) * p;
-    for (int idx = threadIdx.x; idx < w * p; idx += blockDim.x) zb[idx / p][idx % p] = (double)Zs[off + idx];
+    for (int idx = threadIdx.x; idx < w * p; idx += blockDim.x) zb[idx / p][idx % p] = Zs[off + idx];
     __syncthreads();
-    const double *M = Mall + d.moff;
+    const T *M = Mall + d.moff;
     const int cc = threadIdx.x / 16, rs = threadIdx.x % 16, c = c0 + cc;
-    double acc[32];
+    T acc[32];
 #pragma unroll
-    for (int q = 0; q < 32; ++q) acc[q] = 0.0;
+    for (int q = 0; q < 32; ++q) acc[q] = T(0);
     if (c < w) {
-        const double *mc = M + (int64_t)c * w;
+        const T *mc = M + (int64_t)c * w;
 #pragma unroll 4
         for (int r = rs; r < w; r += 16) {
-            const double m = mc[r];
+            const T m = mc[r];
 #pragma unroll
             for (int q = 0; q < 32; ++q)
-                if (q < p) acc[q] = fma(m, zb[r][q], acc[q]);
+                if (q < p) acc[q] += m * zb[r][q];
         }
     }
 #pragma unroll
     for (int q = 0; q < 32; ++q) {
         if (q >= p) break;
-        double v = acc[q];
+        T v = acc[q];
         for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         if (rs == 0 && c < w) Z[off + (int64_t)c * p + q] = (T)v;
     }
@@ -611,7 +599,9 @@ __global__ void k_bwd_finish(const AsmItem *items, const int64_t *zo, const int3
 template <class T>
 static size_t build_m_smem() { return 8 * ((size_t)(SPW + NB) * 33 + (size_t)NB * (NB + 1)); }
 template <class T>
-static size_t panel_vec_smem() { return 8 * (size_t)SPW * 33; }
+static size_t panel_vec_smem() { return sizeof(T) * (size_t)SPW * 33; }
+template <class T>
+static size_t fwd_step_smem() { return 2 * sizeof(T) * (size_t)SPW * 33; }
 template <class T>
 static size_t trsm_smem() { return sizeof(T) * (size_t)2 * NB * (NB + 1); }
 template <class T>
@@ -622,8 +612,7 @@ static void set_solve_attrs() {
     static bool done = false;
     if (done) return;
     MBL_CUDA(cudaFuncSetAttribute(k_build_m<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)build_m_smem<T>()));
-    MBL_CUDA(cudaFuncSetAttribute(k_fwd_m<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)panel_vec_smem<T>()));
-    MBL_CUDA(cudaFuncSetAttribute(k_fwd_upd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)panel_vec_smem<T>()));
+    MBL_CUDA(cudaFuncSetAttribute(k_fwd_step<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_step_smem<T>()));
     MBL_CUDA(cudaFuncSetAttribute(k_bwd_m<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)panel_vec_smem<T>()));
     MBL_CUDA(cudaFuncSetAttribute(k_bwd_part<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwd_part_smem<T>()));
     done = true;
@@ -642,7 +631,8 @@ static void factor_impl(Factorization &fz, cudaStream_t st) {
         attr = true;
     }
     set_solve_attrs<T>();
-    MBL_CUDA(cudaMemsetAsync(fz.counters.data(), 0, 3 * sizeof(unsigned long long), st));
+    MBL_CUDA(cudaMemsetAsync(fz.counters.data(), 0, 5 * sizeof(unsigned long long), st));
+    MBL_CUDA(cudaMemsetAsync(fz.counters.data() + 4, 0x7f, sizeof(unsigned int), st));  // min |d| starts huge
     for (int l = 0; l < p.nlevels; ++l) {
         int na = p.asm_ptr[l + 1] - p.asm_ptr[l];
         k_assemble<T><<<na, 256, 0, st>>>(p.d_asm_items.data() + p.asm_ptr[l], p.d_sn_fo.data(), p.d_sn_f.data(),
@@ -660,7 +650,8 @@ static void factor_impl(Factorization &fz, cudaStream_t st) {
             if (stp.n2 > 0) {
                 k_panel_trsm<T><<<(unsigned)stp.n2, RB, trsm_smem<T>(), st>>>(dd, stp.nd, p.d_sn_fo.data(),
                                                                              p.d_sn_f.data(), p.d_sn_start.data(), arena,
-                                                                             Dg, fz.piv.data(), wscr);
+                                                                             Dg, fz.piv.data(), wscr,
+                                                                             fz.counters.data() + 3);
                 MBL_LAUNCH_CHECK();
             }
             if (stp.n3 > 0) {
@@ -685,7 +676,7 @@ static void factor_impl(Factorization &fz, cudaStream_t st) {
         dim3 grid((unsigned)p.sdescs.size(), SPW / 32);
         k_build_m<T><<<grid, 256, build_m_smem<T>(), st>>>(p.d_sdescs.data(), p.d_sn_fo.data(), p.d_sn_f.data(),
                                                            p.d_sn_start.data(), arena, fz.piv.data(),
-                                                           static_cast<double *>(fz.M.m.p));
+                                                           static_cast<T *>(fz.M.m.p));
         MBL_LAUNCH_CHECK();
     }
 }
@@ -695,28 +686,19 @@ void numeric_factor(Factorization &fz, cudaStream_t st) {
     else factor_impl<float>(fz, st);
 }
 
+// The level x panel sequence between the permutations, on the factorization's internal buffers.
 template <class T>
-static void solve_impl(Factorization &fz, const double *B, int64_t ldb, double *X, int64_t ldx, int p, bool accumulate,
-                       cudaStream_t st) {
+static void solve_levels(Factorization &fz, int p, cudaStream_t st) {
     Plan &pl = *fz.plan;
-    int64_t n = pl.n;
     T *arena = static_cast<T *>(fz.arena.m.p);
     T *Dg = static_cast<T *>(fz.D.m.p);
-    const double *M = static_cast<const double *>(fz.M.m.p);
-    fz.ensure_solve_work(p);
-    set_solve_attrs<T>();
+    const T *M = static_cast<const T *>(fz.M.m.p);
     T *Z = static_cast<T *>(fz.zwork.m.p);
     T *Zs = static_cast<T *>(fz.zsolved.m.p);
     T *y = static_cast<T *>(fz.ywork.m.p);
     T *yfw = static_cast<T *>(fz.yfw.m.p);
     T *P = static_cast<T *>(fz.pwork.m.p);
-    int64_t tot = n * p;
-    unsigned g = (unsigned)((tot + 255) / 256);
-    const size_t vsm = panel_vec_smem<T>(), psm = bwd_part_smem<T>();
-    ProfScope ps(fz.ctx, sizeof(T) == 8 ? "trisolve_fp64" : "trisolve_fp32",
-                 2.0 * (double)(pl.nnz_l + n) * sizeof(T) + 16.0 * (double)n * p, st);
-    k_perm_in<T><<<g, 256, 0, st>>>(n, p, pl.d_perm.data(), B, ldb, y);
-    MBL_LAUNCH_CHECK();
+    const size_t vsm = panel_vec_smem<T>(), fsm = fwd_step_smem<T>(), psm = bwd_part_smem<T>();
     for (int l = 0; l < pl.nlevels; ++l) {
         int na = pl.asm_ptr[l + 1] - pl.asm_ptr[l];
         const AsmItem *items = pl.d_asm_items.data() + pl.asm_ptr[l];
@@ -727,10 +709,8 @@ static void solve_impl(Factorization &fz, const double *B, int64_t ldb, double *
         for (int si = pl.lvl_sstep_ptr[l]; si < pl.lvl_sstep_ptr[l + 1]; ++si) {
             const SolveStep &ss = pl.ssteps[si];
             const SolveDesc *sd = pl.d_sdescs.data() + ss.d0;
-            k_fwd_m<T><<<dim3(ss.nd, SPW / MCH), 256, vsm, st>>>(sd, pl.d_sn_zo.data(), M, Z, Zs, p);
-            MBL_LAUNCH_CHECK();
-            k_fwd_upd<T><<<(unsigned)ss.nrb, 256, vsm, st>>>(sd, ss.nd, pl.d_sn_fo.data(), pl.d_sn_zo.data(),
-                                                             pl.d_sn_f.data(), arena, Zs, Z, p);
+            k_fwd_step<T><<<(unsigned)ss.nrb, 256, fsm, st>>>(sd, ss.nd, pl.d_sn_fo.data(), pl.d_sn_zo.data(),
+                                                              pl.d_sn_f.data(), arena, M, Z, Zs, p);
             MBL_LAUNCH_CHECK();
         }
         k_fwd_finish<T><<<na, 256, 0, st>>>(items, pl.d_sn_zo.data(), pl.d_sn_nc.data(), pl.d_sn_start.data(), Dg, Zs,
@@ -758,6 +738,49 @@ static void solve_impl(Factorization &fz, const double *B, int64_t ldb, double *
         k_bwd_finish<T><<<na, 256, 0, st>>>(items, pl.d_sn_zo.data(), pl.d_sn_nc.data(), pl.d_sn_start.data(), Z, y, p);
         MBL_LAUNCH_CHECK();
     }
+}
+
+template <class T>
+static void solve_impl(Factorization &fz, const double *B, int64_t ldb, double *X, int64_t ldx, int p, bool accumulate,
+                       cudaStream_t st) {
+    Plan &pl = *fz.plan;
+    int64_t n = pl.n;
+    fz.ensure_solve_work(p);
+    set_solve_attrs<T>();
+    T *y = static_cast<T *>(fz.ywork.m.p);
+    int64_t tot = n * p;
+    unsigned g = (unsigned)((tot + 255) / 256);
+    ProfScope ps(fz.ctx, sizeof(T) == 8 ? "trisolve_fp64" : "trisolve_fp32",
+                 2.0 * (double)(pl.nnz_l + n) * sizeof(T) + 16.0 * (double)n * p, st);
+    k_perm_in<T><<<g, 256, 0, st>>>(n, p, pl.d_perm.data(), B, ldb, y);
+    MBL_LAUNCH_CHECK();
+    // the fixed sequence of ~(levels + 4 x solve steps) launches is captured once per block width
+    // and replayed as a CUDA graph
+    if (fz.graph_p != p) {
+        if (fz.graph_exec) {
+            cudaGraphExecDestroy(fz.graph_exec);
+            fz.graph_exec = nullptr;
+        }
+        cudaGraph_t graph;
+        long long before = g_launches.load();
+        MBL_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        try {
+            solve_levels<T>(fz, p, st);
+        } catch (...) {
+            cudaGraph_t dummy;
+            cudaStreamEndCapture(st, &dummy);
+            if (dummy) cudaGraphDestroy(dummy);
+            throw;
+        }
+        MBL_CUDA(cudaStreamEndCapture(st, &graph));
+        fz.graph_nodes = g_launches.load() - before;
+        g_launches.fetch_sub(fz.graph_nodes);  // counted when replayed
+        MBL_CUDA(cudaGraphInstantiate(&fz.graph_exec, graph, 0));
+        cudaGraphDestroy(graph);
+        fz.graph_p = p;
+    }
+    MBL_CUDA(cudaGraphLaunch(fz.graph_exec, st));
+    g_launches.fetch_add(fz.graph_nodes);
     k_perm_out<T><<<g, 256, 0, st>>>(n, p, pl.d_perm.data(), y, X, ldx, accumulate ? 1 : 0);
     MBL_LAUNCH_CHECK();
 }
@@ -787,11 +810,15 @@ void Factorization::allocate() {
     arena.alloc(ctx, (size_t)pl.arena_elems * es);
     D.alloc(ctx, (size_t)pl.n * es);
     piv.alloc(ctx, pl.n);
-    counters.alloc(ctx, 3);
+    counters.alloc(ctx, 5);
     wscr.alloc(ctx, (size_t)std::max<int64_t>(pl.wscratch_elems, 1) * es);
-    M.alloc(ctx, (size_t)std::max<int64_t>(pl.m_elems, 1) * sizeof(double));
+    M.alloc(ctx, (size_t)std::max<int64_t>(pl.m_elems, 1) * es);
 }
 
 void Factorization::release_scratch() { wscr.release(); }
+
+Factorization::~Factorization() {
+    if (graph_exec) cudaGraphExecDestroy(graph_exec);
+}
 
 }  // namespace mbl

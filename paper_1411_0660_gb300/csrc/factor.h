@@ -14,13 +14,20 @@ struct Factorization {
     double tiny = 0.0;
     DVec<char> arena, D, wscr, M, zwork, zsolved, ywork, yfw, pwork;
     DVec<int32_t> piv;
-    DVec<unsigned long long> counters;  // [0] perturbed pivots, [1] negative pivots, [2] wait time-outs
+    // [0] perturbed pivots, [1] negative pivots, [2] wait time-outs, [3] max |l| (float bits, low
+    // word), [4] min |d| (float bits, low word)
+    DVec<unsigned long long> counters;
+    float max_l = 0.f, min_d = 0.f;
     int work_p = 0;
+    cudaGraphExec_t graph_exec = nullptr;  // captured solve sequence for block width graph_p
+    int graph_p = 0;
+    long long graph_nodes = 0;
     bool use_tc = true;  // tcgen05 Schur updates for FP32 fronts
     int64_t perturbed = 0, negative = 0;
     double ms_factor = 0.0;
 
     size_t elem_size() const { return prec == MBL_PREC_FP64 ? sizeof(double) : sizeof(float); }
+    ~Factorization();
     void allocate();
     void release_scratch();
     void ensure_solve_work(int p);

@@ -316,8 +316,11 @@ void KrylovSchur::ritz(cudaStream_t st, std::vector<double> &theta, std::vector<
     k_pack_sym<<<nblk((int64_t)mm * mm), 256, 0, st>>>(T.data(), ldv, mm, eigA.data());
     MBL_LAUNCH_CHECK();
     MBL_CUDA(cudaMemcpyAsync(eigM.data(), &mm, sizeof(int), cudaMemcpyHostToDevice, st));
-    syev_batched(1, eigM.data(), eigOff.data(), eigOff.data(), eigA.data(), eigW.data(), 1, nullptr, ldv,
-                 eigWork.data(), eigInfo.data(), st);
+    {
+        ProfScope ps(ctx, "syev_krylov", (double)mm, st);
+        syev_batched(1, eigM.data(), eigOff.data(), eigOff.data(), eigA.data(), eigW.data(), 1, nullptr, ldv,
+                     eigWork.data(), eigInfo.data(), st);
+    }
     k_ritz_resid<<<nblk(mm, 128), 128, 0, st>>>(T.data(), ldv, mm, p, eigA.data(), res.data());
     MBL_LAUNCH_CHECK();
     theta.resize(mm);
@@ -419,6 +422,123 @@ static void dense_eigen(mbl_sector *sec, bool vecs, DVec<double> &A, DVec<double
     if (hinfo != 0) fail(MBL_ERR_NOT_CONVERGED, "dense eigensolver did not converge");
 }
 
+// ---- single-vector Lanczos for E_min, E_max ----
+// alpha_j, beta_j from the two Gram-Schmidt passes and the norm; v_{j+1} = w / beta_j
+__global__ void k_lanczos_norm_part(int64_t n, const double *w, double *part) {
+    __shared__ double red[32];
+    double s = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        s += w[i] * w[i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
+        part[blockIdx.x] = t;
+    }
+}
+
+__global__ void k_lanczos_coef(int nb, const double *part, int j, const double *c1, const double *c2, double *alpha,
+                               double *beta) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double s = 0.0;
+    for (int b = 0; b < nb; ++b) s += part[b];
+    alpha[j] = c1[j] + c2[j];
+    beta[j] = sqrt(s);
+}
+
+__global__ void k_lanczos_next(int64_t n, const double *w, const double *beta, int j, double *V, int ldv) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double b = beta[j];
+    V[i * ldv + j + 1] = b > 0.0 ? w[i] / b : 0.0;
+}
+
+__global__ void k_normalize_first(int64_t n, double *V, int ldv, const double *part, int nb) {
+    __shared__ double inv;
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int b = 0; b < nb; ++b) s += part[b];
+        inv = 1.0 / sqrt(s);
+    }
+    __syncthreads();
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        V[i * ldv] *= inv;
+}
+
+__device__ int tri_sturm(int m, const double *a, const double *b, double x) {
+    const double pivmin = 1e-300;
+    int c = 0;
+    double q = a[0] - x;
+    if (fabs(q) < pivmin) q = -pivmin;
+    c += q < 0.0;
+    for (int i = 1; i < m; ++i) {
+        q = (a[i] - x) - b[i - 1] * b[i - 1] / q;
+        if (fabs(q) < pivmin) q = -pivmin;
+        c += q < 0.0;
+    }
+    return c;
+}
+
+// Extreme eigenvalues of the Lanczos tridiagonal T (alpha, beta) by bisection, and the last component
+// of their unit eigenvectors by two steps of inverse iteration.  out = {lo, hi, z_lo, z_hi}.
+__global__ void k_tridiag_extremes(int m, const double *a, const double *b, double *scratch, double *out) {
+    const int which = threadIdx.x;
+    if (which > 1) return;
+    double gl = a[0], gu = a[0];
+    for (int i = 0; i < m; ++i) {
+        double r = (i > 0 ? fabs(b[i - 1]) : 0.0) + (i + 1 < m ? fabs(b[i]) : 0.0);
+        gl = fmin(gl, a[i] - r);
+        gu = fmax(gu, a[i] + r);
+    }
+    const int j = which == 0 ? 0 : m - 1;
+    double lo = gl - 1e-12 * (fabs(gl) + fabs(gu)), hi = gu + 1e-12 * (fabs(gl) + fabs(gu));
+    for (int it = 0; it < 200; ++it) {
+        double mid = 0.5 * (lo + hi);
+        if (mid == lo || mid == hi) break;
+        if (tri_sturm(m, a, b, mid) > j) hi = mid; else lo = mid;
+    }
+    const double lam = 0.5 * (lo + hi);
+    // inverse iteration on T - lam I (LU with partial pivoting of the tridiagonal)
+    double *u1 = scratch + (size_t)which * 6 * m, *u2 = u1 + m, *u3 = u2 + m, *l = u3 + m, *x = l + m, *fl = x + m;
+    const double tiny = 1e-15 * (fabs(gl) + fabs(gu)) + 1e-300;
+    double aa = a[0] - lam, bb = m > 1 ? b[0] : 0.0;
+    for (int i = 0; i < m - 1; ++i) {
+        double c = b[i], an = a[i + 1] - lam, bn = (i + 1 < m - 1) ? b[i + 1] : 0.0;
+        if (fabs(aa) >= fabs(c)) {
+            if (aa == 0.0) aa = tiny;
+            double mult = c / aa;
+            u1[i] = aa; u2[i] = bb; u3[i] = 0.0; l[i] = mult; fl[i] = 0.0;
+            aa = an - mult * bb;
+            bb = bn;
+        } else {
+            double mult = aa / c;
+            u1[i] = c; u2[i] = an; u3[i] = bn; l[i] = mult; fl[i] = 1.0;
+            aa = bb - mult * an;
+            bb = -mult * bn;
+        }
+    }
+    if (fabs(aa) < tiny) aa = aa >= 0.0 ? tiny : -tiny;
+    u1[m - 1] = aa;
+    for (int i = 0; i < m; ++i) x[i] = 1.0 / sqrt((double)m) * ((i & 1) ? 1.0 : 0.7);
+    for (int it = 0; it < 3; ++it) {
+        for (int i = 0; i < m - 1; ++i) {
+            if (fl[i] != 0.0) { double t = x[i]; x[i] = x[i + 1]; x[i + 1] = t; }
+            x[i + 1] -= l[i] * x[i];
+        }
+        x[m - 1] /= u1[m - 1];
+        if (m > 1) x[m - 2] = (x[m - 2] - u2[m - 2] * x[m - 1]) / u1[m - 2];
+        for (int i = m - 3; i >= 0; --i) x[i] = (x[i] - u2[i] * x[i + 1] - u3[i] * x[i + 2]) / u1[i];
+        double nrm = 0.0;
+        for (int i = 0; i < m; ++i) nrm += x[i] * x[i];
+        nrm = sqrt(nrm);
+        for (int i = 0; i < m; ++i) x[i] /= nrm;
+    }
+    out[which] = lam;
+    out[2 + which] = x[m - 1];
+}
+
 void extremal_bounds(mbl_sector *sec, double *emin, double *emax) {
     if (sec->have_bounds) {
         *emin = sec->emin;
@@ -426,6 +546,7 @@ void extremal_bounds(mbl_sector *sec, double *emin, double *emax) {
         return;
     }
     cudaStream_t st = sec->ctx->stream;
+    Ctx *ctx = sec->ctx;
     int64_t n = sec->n;
     if (n <= DENSE_MAX_N) {
         DVec<double> A, w;
@@ -439,32 +560,56 @@ void extremal_bounds(mbl_sector *sec, double *emin, double *emax) {
         *emax = sec->emax;
         return;
     }
-    const int p = 4, ncv = 48;
-    KrylovSchur ks(sec->ctx, n, p, ncv);
-    OpFn op = [&](const double *X, int ldx, double *Y, cudaStream_t s) {
-        launch_spmv(sec, 0.0, X, ldx, 1, Y, p, 1, p, s);
-    };
-    ks.start(0xB0B5EEDull, st);
-    std::vector<double> th, rn;
+    ProfScope ps(ctx, "extremal_bounds", 0.0, st);
+    const int mmax = (int)std::min<int64_t>(n - 1, 480);
+    const int ldv = mmax + 1;
+    DVec<double> V, W, C1, C2, work, alpha, beta, part, scr, out;
+    V.alloc(ctx, (size_t)n * ldv);
+    W.alloc(ctx, n);
+    C1.alloc(ctx, ldv);
+    C2.alloc(ctx, ldv);
+    work.alloc(ctx, dense_tn_work(n, ldv, 1) + 64);
+    alpha.alloc(ctx, ldv);
+    beta.alloc(ctx, ldv);
+    const int nb = 256;
+    part.alloc(ctx, nb);
+    scr.alloc(ctx, 12 * (size_t)ldv);
+    out.alloc(ctx, 4);
+    k_random_block<<<nblk(n), 256, 0, st>>>(n, 1, 0xB0B5EEDull, V.data(), ldv, 0);
+    MBL_LAUNCH_CHECK();
+    // the first column is strided; normalize through a contiguous copy
+    copy_cols(n, V.data(), ldv, 0, W.data(), 1, 0, 1, st);
+    k_lanczos_norm_part<<<nb, 256, 0, st>>>(n, W.data(), part.data());
+    MBL_LAUNCH_CHECK();
+    k_normalize_first<<<nb, 256, 0, st>>>(n, V.data(), ldv, part.data(), nb);
+    MBL_LAUNCH_CHECK();
     double lo = 0, hi = 0;
     bool done = false;
-    for (int rs = 0; rs < 200 && !done; ++rs) {
-        while (!ks.full()) ks.expand(op, st);
-        ks.ritz(st, th, rn);
-        int mm = (int)th.size();
-        double hn = std::max(std::fabs(th.front()), std::fabs(th.back()));
-        lo = th.front();
-        hi = th.back();
-        if (rn.front() <= 1e-13 * hn && rn.back() <= 1e-13 * hn) {
-            done = true;
-            break;
+    for (int j = 0; j < mmax && !done; ++j) {
+        launch_spmv(sec, 0.0, V.data() + j, ldv, 1, W.data(), 1, 1, 1, st);
+        dense_tn(n, V.data(), ldv, 0, j + 1, W.data(), 1, 0, 1, C1.data(), work.data(), st);
+        dense_nn_sub(n, V.data(), ldv, 0, j + 1, C1.data(), 1, W.data(), st);
+        dense_tn(n, V.data(), ldv, 0, j + 1, W.data(), 1, 0, 1, C2.data(), work.data(), st);
+        dense_nn_sub(n, V.data(), ldv, 0, j + 1, C2.data(), 1, W.data(), st);
+        k_lanczos_norm_part<<<nb, 256, 0, st>>>(n, W.data(), part.data());
+        MBL_LAUNCH_CHECK();
+        k_lanczos_coef<<<1, 32, 0, st>>>(nb, part.data(), j, C1.data(), C2.data(), alpha.data(), beta.data());
+        MBL_LAUNCH_CHECK();
+        k_lanczos_next<<<nblk(n), 256, 0, st>>>(n, W.data(), beta.data(), j, V.data(), ldv);
+        MBL_LAUNCH_CHECK();
+        const int m = j + 1;
+        if ((m >= 16 && m % 8 == 0) || m == mmax) {
+            k_tridiag_extremes<<<1, 32, 0, st>>>(m, alpha.data(), beta.data(), scr.data(), out.data());
+            MBL_LAUNCH_CHECK();
+            double h[4], bj;
+            MBL_CUDA(cudaMemcpyAsync(h, out.data(), 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
+            MBL_CUDA(cudaMemcpyAsync(&bj, beta.data() + j, sizeof(double), cudaMemcpyDeviceToHost, st));
+            MBL_CUDA(cudaStreamSynchronize(st));
+            lo = h[0];
+            hi = h[1];
+            double hn = std::max(std::fabs(lo), std::fabs(hi));
+            if ((std::fabs(bj * h[2]) <= 1e-13 * hn && std::fabs(bj * h[3]) <= 1e-13 * hn) || bj <= 1e-14 * hn) done = true;
         }
-        // keep the 12 lowest and 12 highest Ritz pairs
-        std::vector<int> keep;
-        int kk = std::min(12, mm / 2 - p);
-        for (int i = 0; i < kk; ++i) keep.push_back(i);
-        for (int i = mm - kk; i < mm; ++i) keep.push_back(i);
-        ks.restart(keep, st);
     }
     if (!done) fail(MBL_ERR_NOT_CONVERGED, "extremal Lanczos did not converge");
     sec->emin = lo;
@@ -666,8 +811,11 @@ void RitzH::run(mbl_sector *sec, KrylovSchur &ks, double sigma, double hnorm, do
     k_pack_sym<<<nblk((int64_t)mb * mb), 256, 0, st>>>(Gm.data(), mb, mb, Gs.data());
     MBL_LAUNCH_CHECK();
     MBL_CUDA(cudaMemcpyAsync(gm.data(), &mb, sizeof(int), cudaMemcpyHostToDevice, st));
-    syev_batched(1, gm.data(), goff.data(), goff.data(), Gs.data(), Gw.data(), 1, nullptr, ks.ldv, Gwork.data(),
-                 ginfo.data(), st);
+    {
+        ProfScope ps(ctx, "syev_rr", (double)mb, st);
+        syev_batched(1, gm.data(), goff.data(), goff.data(), Gs.data(), Gw.data(), 1, nullptr, ks.ldv, Gwork.data(),
+                     ginfo.data(), st);
+    }
     std::vector<double> gth(mb);
     MBL_CUDA(cudaMemcpyAsync(gth.data(), Gw.data(), mb * sizeof(double), cudaMemcpyDeviceToHost, st));
     MBL_CUDA(cudaStreamSynchronize(st));
