@@ -65,6 +65,8 @@ typedef struct mbl_opts {
     int max_refine;       /* refinement steps per application                       [20]   */
     uint64_t start_seed;  /* seed of the random start block                         [12345]*/
     int tensor_cores;     /* FP32 fronts: Schur updates on tcgen05 (3xTF32) if nonzero [0]   */
+    int refine_mode;      /* 0: plain iterative refinement, 1: FGMRES with the factor as    */
+                          /*    right preconditioner (FP64 Arnoldi per right-hand side)  [1]   */
 } mbl_opts;
 
 typedef struct mbl_factor_stats {

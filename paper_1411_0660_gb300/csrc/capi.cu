@@ -202,6 +202,7 @@ void mbl_opts_default(mbl_opts *o) {
     o->max_refine = 20;
     o->start_seed = 12345;
     o->tensor_cores = 0;
+    o->refine_mode = 1;
 }
 
 const char *mbl_version(void) { return "mblsi 0.1 (sm_103a)"; }
@@ -466,6 +467,7 @@ int mbl_factor_solve(mbl_factorization *fh, const double *b, double *x, int nrhs
     extremal_bounds(f.sec, &emin, &emax);
     double hn = std::max(std::fabs(emin), std::fabs(emax));
     RefinedSolve rs{f.sec, &f, hn + std::fabs(f.sigma), 1e-15, 20};
+    rs.gmres = 1;
     for (int c0 = 0; c0 < nrhs; c0 += 32) {
         int p = std::min(32, nrhs - c0);
         B.alloc(ctx, (size_t)n * p);

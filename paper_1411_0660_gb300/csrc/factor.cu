@@ -90,12 +90,41 @@ __global__ void __launch_bounds__(256) k_assemble(const AsmItem *items, const in
     }
 }
 
+// Largest |entry| of each panel column over the rows below the panel (current values), per step
+// descriptor: cmax[di * NB + c] (float bits, atomicMax).  Used by the pivot choice of k_panel_diag.
+template <class T>
+__global__ void __launch_bounds__(RB) k_panel_colmax(const PanelDesc *descs, int nd, const int64_t *fo,
+                                                     const int32_t *fsz, const T *arena, unsigned int *cmax) {
+    __shared__ float red[RB / 32];
+    const int di = find_desc2(descs, nd, blockIdx.x);
+    const PanelDesc d = descs[di];
+    const int s = d.front, f = fsz[s], k0 = d.k0, w = d.w;
+    const int r0 = k0 + w + (int)(blockIdx.x - d.off2) * RB;
+    const int nr = min(RB, f - r0);
+    const T *F = arena + fo[s];
+    const int i = threadIdx.x, lane = i & 31, wp = i >> 5;
+    for (int c = 0; c < w; ++c) {
+        float v = (i < nr) ? (float)tabs(F[(int64_t)(k0 + c) * f + r0 + i]) : 0.f;
+        for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+        if (lane == 0) red[wp] = v;
+        __syncthreads();
+        if (i == 0) {
+            float m = 0.f;
+            for (int u = 0; u < RB / 32; ++u) m = fmaxf(m, red[u]);
+            atomicMax(cmax + (size_t)di * NB + c, __float_as_uint(m));
+        }
+        __syncthreads();
+    }
+}
+
 template <class T>
 __global__ void __launch_bounds__(256) k_panel_diag(const PanelDesc *descs, const int64_t *fo, const int32_t *fsz,
                                                     const int32_t *sn_start, T *arena, T *Dg, int32_t *piv,
-                                                    double tiny, unsigned long long *counters) {
+                                                    double tiny, unsigned long long *counters,
+                                                    const unsigned int *cmax) {
     __shared__ T B[NB][NB + 1];
     __shared__ int perm[NB];
+    __shared__ float cm[NB];
     __shared__ int s_j;
     __shared__ T s_d;
     const PanelDesc d = descs[blockIdx.x];
@@ -106,20 +135,33 @@ __global__ void __launch_bounds__(256) k_panel_diag(const PanelDesc *descs, cons
         int r = idx % w, c = idx / w;
         B[r][c] = (r >= c) ? F[(int64_t)(k0 + c) * f + k0 + r] : T(0);
     }
-    if (tid < w) perm[tid] = tid;
+    if (tid < w) {
+        perm[tid] = tid;
+        cm[tid] = __uint_as_float(cmax[(size_t)blockIdx.x * NB + tid]);
+    }
     __syncthreads();
     for (int t = 0; t < w; ++t) {
+        // pivot: the candidate whose diagonal is largest relative to the rest of its column (inside the
+        // block and, from before this panel, in the rows below), which bounds the multipliers
         if (tid < 32) {
-            T best = T(-1);
+            float best = -1.f, bd = -1.f;
             int bj = t;
-            for (int i = t + tid; i < w; i += 32) {
-                T v = tabs(B[i][i]);
-                if (v > best) { best = v; bj = i; }
+            for (int j = t + tid; j < w; j += 32) {
+                float dj = (float)tabs(B[j][j]);
+                float om = cm[perm[j]];
+                for (int i = t; i < w; ++i) {
+                    if (i == j) continue;
+                    float v = (float)tabs(i > j ? B[i][j] : B[j][i]);
+                    om = fmaxf(om, v);
+                }
+                float sc = om > 0.f ? dj / om : 3.0e38f;
+                if (sc > best || (sc == best && dj > bd)) { best = sc; bd = dj; bj = j; }
             }
             for (int o = 16; o > 0; o >>= 1) {
-                T ov = __shfl_down_sync(0xffffffffu, best, o);
+                float ob = __shfl_down_sync(0xffffffffu, best, o);
+                float od = __shfl_down_sync(0xffffffffu, bd, o);
                 int oj = __shfl_down_sync(0xffffffffu, bj, o);
-                if (ov > best || (ov == best && oj < bj)) { best = ov; bj = oj; }
+                if (ob > best || (ob == best && (od > bd || (od == bd && oj < bj)))) { best = ob; bd = od; bj = oj; }
             }
             if (tid == 0) s_j = bj;
         }
@@ -419,49 +461,74 @@ __global__ void __launch_bounds__(256) k_fwd_gather(const AsmItem *items, const 
 
 constexpr int MCH = 16;  // columns of M^T per CTA in the backward panel-operator kernel
 
-// forward step, one CTA per row block of a solve panel (at least one per panel): zo = M Z[panel]
-// (recomputed by every CTA of the panel; the first one stores it in Zs), then
-// Z[rows of the block] -= L[rows, panel] zo.
+// forward, rows r0..r0+16 of each solve panel: Zs[rows] = M[rows, :] Z[panel], grid (descs, SPW / MCH)
 template <class T>
-__global__ void __launch_bounds__(256) k_fwd_step(const SolveDesc *sdescs, int nd, const int64_t *fo,
-                                                  const int64_t *zo, const int32_t *fsz, const T *arena,
-                                                  const T *Mall, T *Z, T *Zs, int p) {
+__global__ void __launch_bounds__(256) k_fwd_m(const SolveDesc *sdescs, const int64_t *zo, const T *Mall, const T *Z,
+                                               T *Zs, int p) {
     extern __shared__ __align__(16) unsigned char smraw[];
     T(*zin)[33] = reinterpret_cast<T(*)[33]>(smraw);
-    T(*zp)[33] = reinterpret_cast<T(*)[33]>(smraw + sizeof(T) * SPW * 33);
+    const SolveDesc d = sdescs[blockIdx.x];
+    const int w = d.w, r0 = blockIdx.y * MCH;
+    if (r0 >= w) return;
+    const int64_t off = (zo[d.front] + d.k0) * p;
+    for (int idx = threadIdx.x; idx < w * p; idx += blockDim.x) zin[idx / p][idx % p] = Z[off + idx];
+    __syncthreads();
+    const T *M = Mall + d.moff;
+    const int rr = threadIdx.x / 16, cs = threadIdx.x % 16, r = r0 + rr;
+    T acc[32];
+#pragma unroll
+    for (int q = 0; q < 32; ++q) acc[q] = T(0);
+    if (r < w) {
+#pragma unroll 4
+        for (int c = cs; c < w; c += 16) {
+            const T m = M[(int64_t)c * w + r];
+#pragma unroll
+            for (int q = 0; q < 32; ++q)
+                if (q < p) acc[q] += m * zin[c][q];
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 32; ++q) {
+        if (q >= p) break;
+        T v = acc[q];
+        for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (cs == 0 && r < w) Zs[off + (int64_t)r * p + q] = v;
+    }
+}
+
+// forward, rows below each solve panel: Z[r] -= L[r, panel] Zs[panel]; one thread per row (RB per
+// CTA), every right-hand side in registers, the column loop unrolled for loads in flight.
+template <class T>
+__global__ void __launch_bounds__(RB) k_fwd_upd(const SolveDesc *sdescs, int nd, const int64_t *fo, const int64_t *zo,
+                                                const int32_t *fsz, const T *arena, const T *Zs, T *Z, int p) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T(*zp)[33] = reinterpret_cast<T(*)[33]>(smraw);
     const int di = find_sdesc(sdescs, nd, blockIdx.x);
     const SolveDesc d = sdescs[di];
     const int s = d.front, f = fsz[s], k0 = d.k0, w = d.w;
-    const int rb = (int)(blockIdx.x - d.off);
-    T *z = Z + zo[s] * p;
-    for (int idx = threadIdx.x; idx < w * p; idx += blockDim.x) zin[idx / p][idx % p] = z[(int64_t)k0 * p + idx];
-    __syncthreads();
-    const T *M = Mall + d.moff;
-    for (int idx = threadIdx.x; idx < w * p; idx += blockDim.x) {
-        const int r = idx / p, q = idx % p;
-        T acc = T(0);
-#pragma unroll 8
-        for (int c = 0; c < w; ++c) acc += M[(int64_t)c * w + r] * zin[c][q];
-        zp[r][q] = acc;
-    }
-    __syncthreads();
-    if (rb == 0) {
-        T *zs = Zs + (zo[s] + k0) * p;
-        for (int idx = threadIdx.x; idx < w * p; idx += blockDim.x) zs[idx] = zp[idx / p][idx % p];
-    }
-    const int r0 = k0 + w + rb * RB;
+    const int r0 = k0 + w + (int)(blockIdx.x - d.off) * RB;
     if (r0 >= f) return;
     const int nr = min(RB, f - r0);
-    const T *F = arena + fo[s];
-    const int i = threadIdx.x % RB;
+    const T *zs = Zs + (zo[s] + k0) * p;
+    for (int idx = threadIdx.x; idx < w * p; idx += blockDim.x) zp[idx / p][idx % p] = zs[idx];
+    __syncthreads();
+    const int i = threadIdx.x;
     if (i >= nr) return;
-    for (int q = threadIdx.x / RB; q < p; q += blockDim.x / RB) {
-        T acc = T(0);
-        const T *col = F + (int64_t)k0 * f + r0 + i;
-#pragma unroll 8
-        for (int c = 0; c < w; ++c) acc += col[(int64_t)c * f] * zp[c][q];
-        z[(int64_t)(r0 + i) * p + q] -= acc;
+    const T *col = arena + fo[s] + (int64_t)k0 * f + r0 + i;
+    T acc[32];
+#pragma unroll
+    for (int q = 0; q < 32; ++q) acc[q] = T(0);
+#pragma unroll 16
+    for (int c = 0; c < w; ++c) {
+        const T l = col[(int64_t)c * f];
+#pragma unroll
+        for (int q = 0; q < 32; ++q)
+            if (q < p) acc[q] += l * zp[c][q];
     }
+    T *z = Z + (zo[s] + r0 + i) * p;
+#pragma unroll
+    for (int q = 0; q < 32; ++q)
+        if (q < p) z[q] -= acc[q];
 }
 
 template <class T>
@@ -502,13 +569,15 @@ __global__ void __launch_bounds__(256) k_bwd_part(const SolveDesc *sdescs, int n
     const int di = find_sdesc(sdescs, nd, blockIdx.x);
     const SolveDesc d = sdescs[di];
     const int s = d.front, f = fsz[s], k0 = d.k0, w = d.w;
+    const int cc = blockIdx.y * NB;  // this CTA's 64 columns of the panel
+    if (cc >= w) return;
     const int r0 = k0 + w + (int)(blockIdx.x - d.off) * RB;
     const int nr = max(0, min(RB, f - r0));
     T *out = P + (int64_t)blockIdx.x * SPW * 32;
     const T *F = arena + fo[s];
     const T *z = Z + zo[s] * p;
     for (int idx = threadIdx.x; idx < nr * p; idx += blockDim.x) zr[idx / p][idx % p] = z[(int64_t)r0 * p + idx];
-    for (int cc = 0; cc < w; cc += NB) {
+    {
         const int wc = min(NB, w - cc);
         __syncthreads();
         for (int idx = threadIdx.x; idx < nr * wc; idx += blockDim.x) {
@@ -601,8 +670,6 @@ static size_t build_m_smem() { return 8 * ((size_t)(SPW + NB) * 33 + (size_t)NB 
 template <class T>
 static size_t panel_vec_smem() { return sizeof(T) * (size_t)SPW * 33; }
 template <class T>
-static size_t fwd_step_smem() { return 2 * sizeof(T) * (size_t)SPW * 33; }
-template <class T>
 static size_t trsm_smem() { return sizeof(T) * (size_t)2 * NB * (NB + 1); }
 template <class T>
 static size_t bwd_part_smem() { return sizeof(T) * ((size_t)RB * (NB + 1) + (size_t)RB * 33); }
@@ -612,7 +679,8 @@ static void set_solve_attrs() {
     static bool done = false;
     if (done) return;
     MBL_CUDA(cudaFuncSetAttribute(k_build_m<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)build_m_smem<T>()));
-    MBL_CUDA(cudaFuncSetAttribute(k_fwd_step<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_step_smem<T>()));
+    MBL_CUDA(cudaFuncSetAttribute(k_fwd_m<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)panel_vec_smem<T>()));
+    MBL_CUDA(cudaFuncSetAttribute(k_fwd_upd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)panel_vec_smem<T>()));
     MBL_CUDA(cudaFuncSetAttribute(k_bwd_m<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)panel_vec_smem<T>()));
     MBL_CUDA(cudaFuncSetAttribute(k_bwd_part<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwd_part_smem<T>()));
     done = true;
@@ -644,8 +712,15 @@ static void factor_impl(Factorization &fz, cudaStream_t st) {
         for (int si = p.lvl_step_ptr[l]; si < p.lvl_step_ptr[l + 1]; ++si) {
             const PanelStep &stp = p.steps[si];
             const PanelDesc *dd = p.d_descs.data() + stp.d0;
+            unsigned int *cmax = static_cast<unsigned int *>(fz.cmax.m.p);
+            MBL_CUDA(cudaMemsetAsync(cmax, 0, (size_t)stp.nd * NB * sizeof(unsigned int), st));
+            if (stp.n2 > 0) {
+                k_panel_colmax<T><<<(unsigned)stp.n2, RB, 0, st>>>(dd, stp.nd, p.d_sn_fo.data(), p.d_sn_f.data(), arena,
+                                                                   cmax);
+                MBL_LAUNCH_CHECK();
+            }
             k_panel_diag<T><<<stp.nd, 256, 0, st>>>(dd, p.d_sn_fo.data(), p.d_sn_f.data(), p.d_sn_start.data(), arena,
-                                                    Dg, fz.piv.data(), fz.tiny, fz.counters.data());
+                                                    Dg, fz.piv.data(), fz.tiny, fz.counters.data(), cmax);
             MBL_LAUNCH_CHECK();
             if (stp.n2 > 0) {
                 k_panel_trsm<T><<<(unsigned)stp.n2, RB, trsm_smem<T>(), st>>>(dd, stp.nd, p.d_sn_fo.data(),
@@ -698,7 +773,7 @@ static void solve_levels(Factorization &fz, int p, cudaStream_t st) {
     T *y = static_cast<T *>(fz.ywork.m.p);
     T *yfw = static_cast<T *>(fz.yfw.m.p);
     T *P = static_cast<T *>(fz.pwork.m.p);
-    const size_t vsm = panel_vec_smem<T>(), fsm = fwd_step_smem<T>(), psm = bwd_part_smem<T>();
+    const size_t vsm = panel_vec_smem<T>(), psm = bwd_part_smem<T>();
     for (int l = 0; l < pl.nlevels; ++l) {
         int na = pl.asm_ptr[l + 1] - pl.asm_ptr[l];
         const AsmItem *items = pl.d_asm_items.data() + pl.asm_ptr[l];
@@ -709,8 +784,10 @@ static void solve_levels(Factorization &fz, int p, cudaStream_t st) {
         for (int si = pl.lvl_sstep_ptr[l]; si < pl.lvl_sstep_ptr[l + 1]; ++si) {
             const SolveStep &ss = pl.ssteps[si];
             const SolveDesc *sd = pl.d_sdescs.data() + ss.d0;
-            k_fwd_step<T><<<(unsigned)ss.nrb, 256, fsm, st>>>(sd, ss.nd, pl.d_sn_fo.data(), pl.d_sn_zo.data(),
-                                                              pl.d_sn_f.data(), arena, M, Z, Zs, p);
+            k_fwd_m<T><<<dim3(ss.nd, SPW / MCH), 256, vsm, st>>>(sd, pl.d_sn_zo.data(), M, Z, Zs, p);
+            MBL_LAUNCH_CHECK();
+            k_fwd_upd<T><<<(unsigned)ss.nrb, RB, vsm, st>>>(sd, ss.nd, pl.d_sn_fo.data(), pl.d_sn_zo.data(),
+                                                            pl.d_sn_f.data(), arena, Zs, Z, p);
             MBL_LAUNCH_CHECK();
         }
         k_fwd_finish<T><<<na, 256, 0, st>>>(items, pl.d_sn_zo.data(), pl.d_sn_nc.data(), pl.d_sn_start.data(), Dg, Zs,
@@ -727,8 +804,9 @@ static void solve_levels(Factorization &fz, int p, cudaStream_t st) {
         for (int si = pl.lvl_sstep_ptr[l + 1] - 1; si >= pl.lvl_sstep_ptr[l]; --si) {
             const SolveStep &ss = pl.ssteps[si];
             const SolveDesc *sd = pl.d_sdescs.data() + ss.d0;
-            k_bwd_part<T><<<(unsigned)ss.nrb, 256, psm, st>>>(sd, ss.nd, pl.d_sn_fo.data(), pl.d_sn_zo.data(),
-                                                              pl.d_sn_f.data(), arena, Z, p, P);
+            k_bwd_part<T><<<dim3((unsigned)ss.nrb, SUBS), 256, psm, st>>>(sd, ss.nd, pl.d_sn_fo.data(),
+                                                                          pl.d_sn_zo.data(), pl.d_sn_f.data(), arena, Z,
+                                                                          p, P);
             MBL_LAUNCH_CHECK();
             k_bwd_reduce<T><<<dim3(ss.nd, SPW / MCH), 256, 0, st>>>(sd, pl.d_sn_zo.data(), P, Z, Zs, p);
             MBL_LAUNCH_CHECK();
@@ -812,10 +890,14 @@ void Factorization::allocate() {
     piv.alloc(ctx, pl.n);
     counters.alloc(ctx, 5);
     wscr.alloc(ctx, (size_t)std::max<int64_t>(pl.wscratch_elems, 1) * es);
+    cmax.alloc(ctx, (size_t)std::max<int64_t>(pl.max_desc_per_step, 1) * NB * sizeof(unsigned int));
     M.alloc(ctx, (size_t)std::max<int64_t>(pl.m_elems, 1) * es);
 }
 
-void Factorization::release_scratch() { wscr.release(); }
+void Factorization::release_scratch() {
+    wscr.release();
+    cmax.release();
+}
 
 Factorization::~Factorization() {
     if (graph_exec) cudaGraphExecDestroy(graph_exec);

@@ -12,7 +12,7 @@ struct Factorization {
     double sigma = 0.0;
     int prec = MBL_PREC_FP32;
     double tiny = 0.0;
-    DVec<char> arena, D, wscr, M, zwork, zsolved, ywork, yfw, pwork;
+    DVec<char> arena, D, wscr, cmax, M, zwork, zsolved, ywork, yfw, pwork;
     DVec<int32_t> piv;
     // [0] perturbed pivots, [1] negative pivots, [2] wait time-outs, [3] max |l| (float bits, low
     // word), [4] min |d| (float bits, low word)

@@ -351,46 +351,240 @@ void KrylovSchur::restart(const std::vector<int> &keep_idx, cudaStream_t st) {
 // ------------------------------------------------------------------------------------------
 // refined shift-invert operator
 // ------------------------------------------------------------------------------------------
+double RefinedSolve::residual(const double *X, int ldx, double *Y, int p, cudaStream_t st, std::vector<double> *rn,
+                              std::vector<double> *lim) {
+    int64_t n = sec->n;
+    unsigned nb = nblk(n * p);
+    if (part.size() < (size_t)nb * 3 * p) part.alloc(sec->ctx, (size_t)nb * 3 * p);
+    {
+        ProfScope ps(sec->ctx, "refine_spmv", 12.0 * (double)sec->nnz + 8.0 * (double)n * (3.0 * p + 1.0), st);
+        k_refine_resid<<<nb, 256, 0, st>>>(n, sec->rowptr.data(), sec->col.data(), sec->val.data(), fz->sigma, X, ldx, Y,
+                                           R.data(), p, part.data());
+        MBL_LAUNCH_CHECK();
+    }
+    k_reduce_parts<<<1, 128, 0, st>>>((int)nb, 3 * p, part.data(), norms.data());
+    MBL_LAUNCH_CHECK();
+    std::vector<double> h(3 * p);
+    MBL_CUDA(cudaMemcpyAsync(h.data(), norms.data(), 3 * p * sizeof(double), cudaMemcpyDeviceToHost, st));
+    MBL_CUDA(cudaStreamSynchronize(st));
+    double worst = 0.0, rmax = 0.0;
+    if (rn) rn->assign(p, 0.0);
+    if (lim) lim->assign(p, 0.0);
+    for (int q = 0; q < p; ++q) {
+        double r = std::sqrt(h[q]), yn = std::sqrt(h[p + q]), bn = std::sqrt(h[2 * p + q]);
+        double l = rtol * (anorm * yn + bn);
+        worst = std::max(worst, l > 0 ? r / l : (r > 0 ? INFINITY : 0.0));
+        rmax = std::max(rmax, r / std::max(bn, 1e-300));
+        if (rn) (*rn)[q] = r;
+        if (lim) (*lim)[q] = l;
+    }
+    last_rel = rmax;
+    return worst;
+}
+
 void RefinedSolve::apply(const double *X, int ldx, double *Y, int p, cudaStream_t st) {
     int64_t n = sec->n;
     if (R.size() < (size_t)n * p) R.alloc(sec->ctx, (size_t)n * p);
-    unsigned nb = nblk(n * p);
-    if (part.size() < (size_t)nb * 3 * p) part.alloc(sec->ctx, (size_t)nb * 3 * p);
-    if (norms.size() < (size_t)3 * p) norms.alloc(sec->ctx, 3 * 32);
+    if (norms.size() < (size_t)3 * 32) norms.alloc(sec->ctx, 3 * 32);
     factor_solve_raw(*fz, X, ldx, Y, p, p, false, st);
     ++solves;
     ++applies;
+    if (gmres) apply_fgmres(X, ldx, Y, p, st);
+    else apply_plain(X, ldx, Y, p, st);
+}
+
+void RefinedSolve::apply_plain(const double *X, int ldx, double *Y, int p, cudaStream_t st) {
     double prev = INFINITY;
     int stall = 0;
-    std::vector<double> h(3 * p);
     for (int it = 0; it <= max_refine; ++it) {
-        {
-            ProfScope ps(sec->ctx, "refine_spmv", 12.0 * (double)sec->nnz + 8.0 * (double)n * (3.0 * p + 1.0), st);
-            k_refine_resid<<<nb, 256, 0, st>>>(n, sec->rowptr.data(), sec->col.data(), sec->val.data(), fz->sigma, X,
-                                               ldx, Y, R.data(), p, part.data());
-        }
-        MBL_LAUNCH_CHECK();
-        k_reduce_parts<<<1, 128, 0, st>>>((int)nb, 3 * p, part.data(), norms.data());
-        MBL_LAUNCH_CHECK();
-        MBL_CUDA(cudaMemcpyAsync(h.data(), norms.data(), 3 * p * sizeof(double), cudaMemcpyDeviceToHost, st));
-        MBL_CUDA(cudaStreamSynchronize(st));
-        double worst = 0.0, rmax = 0.0;
-        for (int q = 0; q < p; ++q) {
-            double rn = std::sqrt(h[q]), yn = std::sqrt(h[p + q]), bn = std::sqrt(h[2 * p + q]);
-            double lim = rtol * (anorm * yn + bn);
-            worst = std::max(worst, lim > 0 ? rn / lim : (rn > 0 ? INFINITY : 0.0));
-            rmax = std::max(rmax, rn / std::max(bn, 1e-300));
-        }
-        last_rel = rmax;
+        double worst = residual(X, ldx, Y, p, st);
         if (worst <= 1.0) break;
         if (it == max_refine) { stalled = true; break; }
-        if (rmax > 0.5 * prev) {
+        if (last_rel > 0.5 * prev) {
             if (++stall >= 2) { stalled = true; break; }
         } else stall = 0;
-        prev = rmax;
+        prev = last_rel;
         factor_solve_raw(*fz, R.data(), p, Y, p, p, true, st);
         ++solves;
     }
+}
+
+// ---- FGMRES refinement kernels (all p columns in lockstep, each with its own Krylov space) ----
+// V blocks are n x p row-major; column q of block i is the i-th Arnoldi vector of right-hand side q.
+__global__ void k_gm_dots_part(int64_t n, int k1, int p, const double *V, int64_t vstride, const double *W,
+                               double *part, int64_t rows_per) {
+    // part[chunk][i * p + q] = sum over the chunk's rows of V_i[row][q] W[row][q], i < k1
+    extern __shared__ double acc[];
+    for (int t = threadIdx.x; t < k1 * p; t += blockDim.x) acc[t] = 0.0;
+    __syncthreads();
+    int64_t r0 = (int64_t)blockIdx.x * rows_per, r1 = min(n, r0 + rows_per);
+    for (int t = threadIdx.x; t < k1 * p; t += blockDim.x) {
+        int i = t / p, q = t % p;
+        const double *v = V + (int64_t)i * vstride;
+        double s = 0.0;
+        for (int64_t r = r0; r < r1; ++r) s = fma(v[r * p + q], W[r * p + q], s);
+        acc[t] = s;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < k1 * p; t += blockDim.x) part[(size_t)blockIdx.x * k1 * p + t] = acc[t];
+}
+
+__global__ void k_gm_sub(int64_t n, int k1, int p, const double *V, int64_t vstride, const double *h, double *W) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n * p) return;
+    int q = (int)(t % p);
+    double s = 0.0;
+    for (int i = 0; i < k1; ++i) s = fma(V[(int64_t)i * vstride + t], h[i * p + q], s);
+    W[t] -= s;
+}
+
+// normalize W into V_{k+1}; the norms (one per column) come from a dots pass with V = W
+__global__ void k_gm_scale(int64_t n, int p, const double *W, const double *nrm2, double *Vn) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n * p) return;
+    double nn = sqrt(nrm2[t % p]);
+    Vn[t] = nn > 0.0 ? W[t] / nn : 0.0;
+}
+
+// Hessenberg bookkeeping per column q (one thread each): store column k of H (h1 + h2 from the two
+// Gram-Schmidt passes, h_{k+1,k} = |w|), apply the earlier Givens rotations, make a new one, update g.
+// Layout per column: Hc[(kmax+1) x kmax] column-major, cs/sn[kmax], g[kmax+1].
+__global__ void k_gm_givens(int p, int k, int kmax, const double *h1, const double *h2, const double *nrm2,
+                            double *Hall, double *res) {
+    int q = threadIdx.x;
+    if (q >= p) return;
+    const int ld = kmax + 1;
+    double *Hc = Hall + (size_t)q * (ld * kmax + 3 * ld);
+    double *cs = Hc + ld * kmax, *sn = cs + ld, *g = sn + ld;
+    double *col = Hc + (size_t)k * ld;
+    for (int i = 0; i <= k; ++i) col[i] = h1[i * p + q] + h2[i * p + q];
+    col[k + 1] = sqrt(nrm2[q]);
+    for (int i = 0; i < k; ++i) {
+        double a = col[i], b = col[i + 1];
+        col[i] = cs[i] * a + sn[i] * b;
+        col[i + 1] = -sn[i] * a + cs[i] * b;
+    }
+    double a = col[k], b = col[k + 1];
+    double r = hypot(a, b);
+    double c = r > 0.0 ? a / r : 1.0, s_ = r > 0.0 ? b / r : 0.0;
+    cs[k] = c;
+    sn[k] = s_;
+    col[k] = r;
+    col[k + 1] = 0.0;
+    g[k + 1] = -s_ * g[k];
+    g[k] = c * g[k];
+    res[q] = fabs(g[k + 1]);
+}
+
+__global__ void k_gm_init(int p, int kmax, const double *beta2, double *Hall) {
+    int q = threadIdx.x;
+    if (q >= p) return;
+    const int ld = kmax + 1;
+    double *Hc = Hall + (size_t)q * (ld * kmax + 3 * ld);
+    double *g = Hc + ld * kmax + 2 * ld;
+    for (int i = 0; i < ld; ++i) g[i] = 0.0;
+    g[0] = sqrt(beta2[q]);
+}
+
+// y = H^{-1} g (upper triangular, k columns), per column q
+__global__ void k_gm_solve(int p, int k, int kmax, const double *Hall, double *Y) {
+    int q = threadIdx.x;
+    if (q >= p) return;
+    const int ld = kmax + 1;
+    const double *Hc = Hall + (size_t)q * (ld * kmax + 3 * ld);
+    const double *g = Hc + ld * kmax + 2 * ld;
+    for (int i = k - 1; i >= 0; --i) {
+        double s = g[i];
+        for (int j = i + 1; j < k; ++j) s -= Hc[(size_t)j * ld + i] * Y[j * p + q];
+        Y[i * p + q] = Hc[(size_t)i * ld + i] != 0.0 ? s / Hc[(size_t)i * ld + i] : 0.0;
+    }
+}
+
+// X += sum_i Z_i y_i (per column)
+__global__ void k_gm_update(int64_t n, int k, int p, const double *Z, int64_t zstride, const double *y, double *X) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n * p) return;
+    int q = (int)(t % p);
+    double s = 0.0;
+    for (int i = 0; i < k; ++i) s = fma(Z[(int64_t)i * zstride + t], y[i * p + q], s);
+    X[t] += s;
+}
+
+void RefinedSolve::apply_fgmres(const double *X, int ldx, double *Y, int p, cudaStream_t st) {
+    const int64_t n = sec->n;
+    Ctx *ctx = sec->ctx;
+    const int64_t blk = n * p;
+    if (GV.size() < (size_t)blk * (kmax + 1)) GV.alloc(ctx, (size_t)blk * (kmax + 1));
+    if (GZ.size() < (size_t)blk * kmax) GZ.alloc(ctx, (size_t)blk * kmax);
+    if (GW.size() < (size_t)blk) GW.alloc(ctx, blk);
+    const int ld = kmax + 1;
+    if (Gh.size() < (size_t)p * (ld * kmax + 3 * ld) + 2 * (size_t)ld * p + 3 * 32)
+        Gh.alloc(ctx, (size_t)p * (ld * kmax + 3 * ld) + 2 * (size_t)ld * p + 3 * 32);
+    const int64_t rows_per = std::max<int64_t>(1, (n + 303) / 304);
+    const int nch = (int)((n + rows_per - 1) / rows_per);
+    if (Gdots.size() < (size_t)nch * ld * p) Gdots.alloc(ctx, (size_t)nch * ld * p);
+    if (Gy.size() < (size_t)kmax * p + 64) Gy.alloc(ctx, (size_t)kmax * p + 64);
+    double *Hall = Gh.data();
+    double *h1 = Hall + (size_t)p * (ld * kmax + 3 * ld), *h2 = h1 + (size_t)ld * p, *nr = h2 + (size_t)ld * p;
+    const unsigned nbk = nblk(blk);
+    auto dots = [&](int k1, const double *V, int64_t vstride, const double *W, double *out) {
+        size_t smem = (size_t)k1 * p * sizeof(double);
+        k_gm_dots_part<<<nch, 256, smem, st>>>(n, k1, p, V, vstride, W, Gdots.data(), rows_per);
+        MBL_LAUNCH_CHECK();
+        k_reduce_parts<<<nblk(k1 * p), 256, 0, st>>>(nch, k1 * p, Gdots.data(), out);
+        MBL_LAUNCH_CHECK();
+    };
+    double prev = INFINITY;
+    for (int outer = 0; outer < 4; ++outer) {
+        std::vector<double> rn, lim;
+        double worst = residual(X, ldx, Y, p, st, &rn, &lim);
+        if (worst <= 1.0) return;
+        if (outer > 0 && last_rel > 0.5 * prev) { stalled = true; return; }
+        prev = last_rel;
+        // V_0 = R / |R|, g = |R| e_1
+        dots(1, R.data(), 0, R.data(), nr);
+        k_gm_scale<<<nbk, 256, 0, st>>>(n, p, R.data(), nr, GV.data());
+        MBL_LAUNCH_CHECK();
+        k_gm_init<<<1, 32, 0, st>>>(p, kmax, nr, Hall);
+        MBL_LAUNCH_CHECK();
+        int k = 0;
+        for (; k < kmax; ++k) {
+            double *Vk = GV.data() + (size_t)k * blk, *Zk = GZ.data() + (size_t)k * blk;
+            // Z_k = M^-1 V_k ; W = (H - sigma) Z_k
+            k_zero<<<nblk(blk), 256, 0, st>>>(Zk, blk);
+            MBL_LAUNCH_CHECK();
+            factor_solve_raw(*fz, Vk, p, Zk, p, p, false, st);
+            ++solves;
+            launch_spmv(sec, fz->sigma, Zk, p, 1, GW.data(), p, 1, p, st);
+            // two Gram-Schmidt passes against V_0..V_k (each column its own space)
+            dots(k + 1, GV.data(), blk, GW.data(), h1);
+            k_gm_sub<<<nbk, 256, 0, st>>>(n, k + 1, p, GV.data(), blk, h1, GW.data());
+            MBL_LAUNCH_CHECK();
+            dots(k + 1, GV.data(), blk, GW.data(), h2);
+            k_gm_sub<<<nbk, 256, 0, st>>>(n, k + 1, p, GV.data(), blk, h2, GW.data());
+            MBL_LAUNCH_CHECK();
+            dots(1, GW.data(), 0, GW.data(), nr);
+            k_gm_givens<<<1, 32, 0, st>>>(p, k, kmax, h1, h2, nr, Hall, nr + 32);
+            MBL_LAUNCH_CHECK();
+            k_gm_scale<<<nbk, 256, 0, st>>>(n, p, GW.data(), nr, GV.data() + (size_t)(k + 1) * blk);
+            MBL_LAUNCH_CHECK();
+            std::vector<double> est(p);
+            MBL_CUDA(cudaMemcpyAsync(est.data(), nr + 32, p * sizeof(double), cudaMemcpyDeviceToHost, st));
+            MBL_CUDA(cudaStreamSynchronize(st));
+            bool ok = true;
+            for (int q = 0; q < p; ++q) ok = ok && est[q] <= 0.5 * lim[q];
+            if (ok) {
+                ++k;
+                break;
+            }
+        }
+        k_gm_solve<<<1, 32, 0, st>>>(p, k, kmax, Hall, Gy.data());
+        MBL_LAUNCH_CHECK();
+        k_gm_update<<<nbk, 256, 0, st>>>(n, k, p, GZ.data(), blk, Gy.data(), Y);
+        MBL_LAUNCH_CHECK();
+    }
+    double worst = residual(X, ldx, Y, p, st);
+    if (worst > 1.0) stalled = true;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -711,6 +905,7 @@ void solve_near(mbl_sector *sec, double eps, int nev, const mbl_opts &o, double 
     std::unique_ptr<Factorization> fz = make_factorization(sec, sigma_f, o.precision, hnorm, o.tensor_cores != 0);
     S.ms_factor = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tf0).count();
     RefinedSolve op{sec, fz.get(), hnorm + std::fabs(sigma_f), o.refine_tol, o.max_refine};
+    op.gmres = o.refine_mode;
     OpFn opfn = [&](const double *X, int ldx, double *Y, cudaStream_t s) { op.apply(X, ldx, Y, p, s); };
     KrylovSchur ks(ctx, n, p, ncv);
     ks.start(o.start_seed, st);

@@ -44,8 +44,17 @@ struct RefinedSolve {
     int solves = 0, applies = 0;
     bool stalled = false;
     double last_rel = 0.0;
-    DVec<double> R, part, norms;
+    int gmres = 1;     // 1: FGMRES refinement (factor as right preconditioner); 0: plain refinement
+    int kmax = 12;     // FGMRES inner dimension
+    DVec<double> R, part, norms, GV, GZ, GW, Gh, Gy, Gdots;
     void apply(const double *X, int ldx, double *Y, int p, cudaStream_t st);
+
+  private:
+    // true residual R = B - (H - sigma) Y; returns the worst ratio ||r_q|| / (rtol (anorm ||y_q|| + ||b_q||))
+    double residual(const double *X, int ldx, double *Y, int p, cudaStream_t st, std::vector<double> *rn = nullptr,
+                    std::vector<double> *lim = nullptr);
+    void apply_plain(const double *X, int ldx, double *Y, int p, cudaStream_t st);
+    void apply_fgmres(const double *X, int ldx, double *Y, int p, cudaStream_t st);
 };
 
 // Rayleigh-Ritz of H on the whole basis: the nev Ritz pairs nearest sigma and their residuals.
