@@ -105,7 +105,9 @@ def run_reference(args):
     pairs = 0
     with ctx.Pool(cores) as pool:
         for s in range(args.warmup + args.steps):
-            jobs = [(16, h, seed, eps, NEV) for (h, seed, eps) in jobs_for_step(s, per_step)]
+            # warm-up steps only start the workers (imports, oracle library load): one L=12 job each
+            Ls = 16 if s >= args.warmup else 12
+            jobs = [(Ls, h, seed, eps, NEV if Ls == 16 else 20) for (h, seed, eps) in jobs_for_step(s, per_step)]
             t0 = time.perf_counter()
             res = pool.map(_oracle_job, jobs)
             dt = time.perf_counter() - t0
@@ -157,7 +159,8 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--batch", type=int, default=6)
+    ap.add_argument("--batch", type=int, default=3)
+    ap.add_argument("--e2e-jobs", type=int, default=2)
     ap.add_argument("--impl", default="gb300")
     ap.add_argument("--fp64-jobs", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -216,8 +219,11 @@ def main():
         os.path.join(ROOT, "gpurun_out")) else "/tmp/clocks_bench.csv")
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     pairs, lat = 0, []
+    nvtx = getattr(torch.cuda, "nvtx", None)
     with clocks:
         torch.cuda.synchronize()
+        if nvtx is not None:
+            nvtx.range_push("timed")
         e0.record()
         for s in range(args.steps):
             for (h, seed, eps) in jobs_for_step(args.warmup + s, args.batch, rank, world):
@@ -227,6 +233,8 @@ def main():
                 pairs += nc
         e1.record()
         torch.cuda.synchronize()
+        if nvtx is not None:
+            nvtx.range_pop()
     ms = e0.elapsed_time(e1)
     launches = g.launch_count() - l0
     prof = {k: ctx.profile(k) for k in ("factor_fp32", "schur_fp32", "trisolve_fp32", "refine_spmv", "orth")}
@@ -259,19 +267,18 @@ def main():
         fp64 = {"value": p64 / (t64 / 1e3), "unit": "eigenpairs/s", "jobs": args.fp64_jobs,
                 "ms_per_job": t64 / args.fp64_jobs, "factor_ms_per_job": f64["ms"] / max(1, f64["launches"])}
 
-    # ---- end to end through the host API (host fields in, host eigenpairs and observables out) ----
-    import oracle as _unused  # noqa: F401  (not used on this path; keeps import order stable)
-    del _unused
-    hf = np.zeros(L)
-    ev_h = np.zeros(NEV)
+    # ---- end to end through the host API: host fields in, host eigenpairs and observables out ----
+    e2e_jobs = jobs_for_step(args.warmup, max(1, args.e2e_jobs), rank, world)
+    host_fields = []
+    for (h, seed, eps) in e2e_jobs:  # the jobs' inputs (disorder realizations), prepared untimed
+        sec0 = g.build_sector(ctx, L, h, seed)
+        host_fields.append(np.ascontiguousarray(sec0.fields()))
+        sec0.close()
+    torch.cuda.synchronize()
     t_e2e0 = time.perf_counter()
     e_pairs = 0
     h2d = d2h = 0
-    for (h, seed, eps) in jobs_for_step(args.warmup, args.batch, rank, world):
-        # the job's input is its field vector, copied from host memory
-        sec0 = g.build_sector(ctx, L, h, seed)
-        hf[:] = sec0.fields()
-        sec0.close()
+    for (h, seed, eps), hf in zip(e2e_jobs, host_fields):
         sec = g.build_sector_fields(ctx, L, hf, 1.0)
         res = g.solve_near(sec, eps, NEV)
         r, rm, s1, se = g.observables(ctx, L, res.evals, res.evecs)
@@ -280,7 +287,9 @@ def main():
         h2d += hf.nbytes + res.evals.nbytes + res.evecs.nbytes
         d2h += res.evals.nbytes + res.evecs.nbytes + res.resid.nbytes + r.nbytes + 8 + s1.nbytes + se.nbytes
     e2e_s = time.perf_counter() - t_e2e0
-    e2e = {"value": e_pairs / e2e_s, "unit": "eigenpairs/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+    ne = len(e2e_jobs)
+    e2e = {"value": e_pairs / e2e_s, "unit": "eigenpairs/s", "h2d_bytes_per_step": h2d * args.batch // ne,
+           "d2h_bytes_per_step": d2h * args.batch // ne, "jobs": ne}
 
     # ---- roofline of the dominant kernel class ----
     peaks = measured_peaks()

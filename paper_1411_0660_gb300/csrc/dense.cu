@@ -201,7 +201,6 @@ void chol_qr(int64_t n, double *X, int p, double *R, double *G, double *work, in
 // Batched small symmetric eigensolver.
 // ------------------------------------------------------------------------------------------
 constexpr int EIG_THREADS = 512;
-constexpr int EIG_SMEM_MAX_M = 160;
 
 size_t syev_work_doubles(int mmax, bool vecs) {
     // d, e, beta, v, p, e^2 (8m with slack) [+ Z (m*m) + sort scratch (m*m) with eigenvectors]
@@ -209,13 +208,27 @@ size_t syev_work_doubles(int mmax, bool vecs) {
     return 8 * m + (vecs ? 2 * m * m : 0) + 64;
 }
 
-__device__ double block_sum(double v, double *red) {
+template <class R>
+struct Num;
+template <>
+struct Num<double> {
+    static __device__ __forceinline__ double eps() { return DBL_EPSILON; }
+    static __device__ __forceinline__ double tiny() { return DBL_MIN; }
+};
+template <>
+struct Num<float> {
+    static __device__ __forceinline__ float eps() { return FLT_EPSILON; }
+    static __device__ __forceinline__ float tiny() { return FLT_MIN; }
+};
+
+template <class R>
+__device__ R block_sum(R v, R *red) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     __syncthreads();
     if (lane == 0) red[w] = v;
     __syncthreads();
-    double s = 0.0;
+    R s = R(0);
     int nw = (blockDim.x + 31) >> 5;
     for (int i = 0; i < nw; ++i) s += red[i];
     __syncthreads();
@@ -223,15 +236,16 @@ __device__ double block_sum(double v, double *red) {
 }
 
 // Sturm count: number of eigenvalues of T(d, e2) below x.
-__device__ int sturm_count(int m, const double *d, const double *e2, double x, double pivmin) {
+template <class R>
+__device__ int sturm_count(int m, const R *d, const R *e2, R x, R pivmin) {
     int c = 0;
-    double q = d[0] - x;
+    R q = d[0] - x;
     if (fabs(q) < pivmin) q = -pivmin;
-    c += q < 0.0;
+    c += q < R(0);
     for (int i = 1; i < m; ++i) {
         q = (d[i] - x) - e2[i - 1] / q;
         if (fabs(q) < pivmin) q = -pivmin;
-        c += q < 0.0;
+        c += q < R(0);
     }
     return c;
 }
@@ -239,22 +253,27 @@ __device__ int sturm_count(int m, const double *d, const double *e2, double x, d
 // One implicit QL sweep on the unreduced block lo..hi of (d, e), recording the rotations:
 // T <- J^T T J with J = [[c, s], [-s, c]] in planes (hi-1, hi), ..., (lo, lo+1); the first rotation
 // zeroes the upper entry of the last column of T - mu I, the others chase the bulge upward.
-__device__ int ql_sweep_record(int lo, int hi, double *d, double *e, double *cs, double *sn) {
-    double delta = 0.5 * (d[lo + 1] - d[lo]);
-    double b = e[lo];
-    double mu = d[lo] - b * b / (delta + copysign(hypot(delta, b), delta));
-    double x = d[hi] - mu, z = e[hi - 1];
+template <class R>
+__device__ void ql_sweep_record(int lo, int hi, R *d, R *e, R *cs, R *sn) {
+    R delta = R(0.5) * (d[lo + 1] - d[lo]);
+    R b = e[lo];
+    R mu = d[lo] - b * b / (delta + copysign(hypot(delta, b), delta));
+    R x = d[hi] - mu, z = e[hi - 1];
     for (int k = hi - 1; k >= lo; --k) {
-        double r = hypot(x, z);
-        double c = 1.0, s = 0.0;
-        if (r != 0.0) { c = x / r; s = z / r; }
+        R r = hypot(x, z);
+        R c = R(1), s = R(0);
+        if (r != R(0)) {
+            R ir = R(1) / r;
+            c = x * ir;
+            s = z * ir;
+        }
         if (k < hi - 1) e[k + 1] = r;
-        double a = d[k], bb = e[k], dd = d[k + 1];
-        d[k] = a * c * c - 2.0 * bb * c * s + dd * s * s;
-        d[k + 1] = a * s * s + 2.0 * bb * c * s + dd * c * c;
+        R a = d[k], bb = e[k], dd = d[k + 1];
+        d[k] = a * c * c - R(2) * bb * c * s + dd * s * s;
+        d[k + 1] = a * s * s + R(2) * bb * c * s + dd * c * c;
         e[k] = (a - dd) * c * s + bb * (c * c - s * s);
         if (k > lo) {
-            double bulge = s * e[k - 1];
+            R bulge = s * e[k - 1];
             e[k - 1] = c * e[k - 1];
             x = e[k];
             z = bulge;
@@ -262,26 +281,28 @@ __device__ int ql_sweep_record(int lo, int hi, double *d, double *e, double *cs,
         cs[k] = c;
         sn[k] = s;
     }
-    return hi - lo;
 }
 
-// A: m x m column-major (lda = m) at A + aoff[b]; W: eigenvalues at W + woff[b];
-// vecs: eigenvectors into A (columns ascending); info[b] = 1 if QL did not converge.
+// A: m x m column-major FP64 (lda = m) at A + aoff[b]; W: eigenvalues (FP64) at W + woff[b];
+// vecs: eigenvectors into A (columns ascending); info[b] = 1 if QL did not converge.  The arithmetic
+// runs in R (FP32 or FP64); with R = float the matrix must fit in shared memory.
+template <class R>
 __global__ void __launch_bounds__(EIG_THREADS) k_syev(const int *mv, const int64_t *aoff, const int64_t *woff,
-                                                      double *Aall, double *Wall, int vecs, const int *selall,
-                                                      double *workall, size_t wstride, int *info) {
-    extern __shared__ double sm[];
-    __shared__ double red[EIG_THREADS / 32];
-    __shared__ double s_gl, s_gu, s_pivmin;
+                                                      double *Aall, double *Wall, int vecs, double *workall,
+                                                      size_t wstride, int *info, int smem_m) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    R *sm = reinterpret_cast<R *>(smraw);
+    __shared__ R red[EIG_THREADS / 32];
+    __shared__ R s_gl, s_gu, s_pivmin;
     int b = blockIdx.x;
     int m = mv[b];
     double *Ag = Aall + aoff[b];
     double *W = Wall + woff[b];
-    double *work = workall + (size_t)b * wstride;
-    double *d = work, *e = work + m, *beta = work + 2 * m, *vv = work + 3 * m, *pp = work + 4 * m;
-    double *e2 = work + 5 * m;
-    double *Z = work + 8 * m;                 // m x m
-    double *scr = Z + (size_t)m * m;          // m x m scratch
+    R *work = reinterpret_cast<R *>(workall + (size_t)b * wstride);
+    R *d = work, *e = work + m, *beta = work + 2 * m, *vv = work + 3 * m, *pp = work + 4 * m;
+    R *e2 = work + 5 * m;
+    R *Z = work + 8 * m;                 // m x m
+    R *scr = Z + (size_t)m * m;          // m x m scratch
     if (threadIdx.x == 0 && info) info[b] = 0;
     if (m <= 0) return;
     if (m == 1) {
@@ -291,48 +312,51 @@ __global__ void __launch_bounds__(EIG_THREADS) k_syev(const int *mv, const int64
         }
         return;
     }
-    bool in_smem = m <= EIG_SMEM_MAX_M;
-    double *a = in_smem ? sm : Ag;
-    int lda = m;
+    const bool in_smem = m <= smem_m;  // the launch's dynamic shared memory holds smem_m^2 entries
+    R *a;
     if (in_smem) {
-        for (int t = threadIdx.x; t < m * m; t += blockDim.x) a[t] = Ag[t];
+        a = sm;
+        for (int t = threadIdx.x; t < m * m; t += blockDim.x) a[t] = (R)Ag[t];
         __syncthreads();
+    } else {
+        a = reinterpret_cast<R *>(Ag);  // only instantiated for R = double (checked by the launcher)
     }
+    int lda = m;
     // ---- 1. Householder tridiagonalization ----
     for (int k = 0; k + 2 < m; ++k) {
         int len = m - k - 1;
-        double *x = a + (size_t)k * lda + (k + 1);
-        double loc = 0.0;
+        R *x = a + (size_t)k * lda + (k + 1);
+        R loc = R(0);
         for (int i = threadIdx.x; i < len; i += blockDim.x) loc += x[i] * x[i];
-        double alpha2 = block_sum(loc, red);
-        if (alpha2 == 0.0) {
-            if (threadIdx.x == 0) beta[k] = 0.0;
+        R alpha2 = block_sum(loc, red);
+        if (alpha2 == R(0)) {
+            if (threadIdx.x == 0) beta[k] = R(0);
             __syncthreads();
             continue;
         }
-        double x0 = x[0];
-        double sgn = x0 >= 0.0 ? 1.0 : -1.0;
-        double alpha = sqrt(alpha2);
-        double v0 = x0 + sgn * alpha;
-        loc = 0.0;
+        R x0 = x[0];
+        R sgn = x0 >= R(0) ? R(1) : R(-1);
+        R alpha = sqrt(alpha2);
+        R v0 = x0 + sgn * alpha;
+        R iv0 = R(1) / v0;
+        loc = R(0);
         for (int i = threadIdx.x; i < len; i += blockDim.x) {
-            double v = (i == 0) ? 1.0 : x[i] / v0;
+            R v = (i == 0) ? R(1) : x[i] * iv0;
             vv[i] = v;
             if (i > 0) loc += v * v;
         }
-        double vtv = 1.0 + block_sum(loc, red);
-        double bk = 2.0 / vtv;
-        // p = bk * A22 v (full symmetric storage)
-        double *A22 = a + (size_t)(k + 1) * lda + (k + 1);
+        R vtv = R(1) + block_sum(loc, red);
+        R bk = R(2) / vtv;
+        R *A22 = a + (size_t)(k + 1) * lda + (k + 1);
         for (int i = threadIdx.x; i < len; i += blockDim.x) {
-            double s = 0.0;
+            R s = R(0);
             for (int j = 0; j < len; ++j) s = fma(A22[(size_t)j * lda + i], vv[j], s);
             pp[i] = bk * s;
         }
         __syncthreads();
-        loc = 0.0;
+        loc = R(0);
         for (int i = threadIdx.x; i < len; i += blockDim.x) loc += pp[i] * vv[i];
-        double K = 0.5 * bk * block_sum(loc, red);
+        R K = R(0.5) * bk * block_sum(loc, red);
         for (int i = threadIdx.x; i < len; i += blockDim.x) pp[i] -= K * vv[i];
         __syncthreads();
         for (int t = threadIdx.x; t < len * len; t += blockDim.x) {
@@ -354,38 +378,39 @@ __global__ void __launch_bounds__(EIG_THREADS) k_syev(const int *mv, const int64
     __syncthreads();
     // ---- 2. eigenvalues only: bisection ----
     if (!vecs) {
-    if (threadIdx.x == 0) {
-        double gl = d[0], gu = d[0], emax2 = 0.0;
-        for (int i = 0; i < m; ++i) {
-            double r = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i + 1 < m ? fabs(e[i]) : 0.0);
-            gl = fmin(gl, d[i] - r);
-            gu = fmax(gu, d[i] + r);
-            if (i + 1 < m) emax2 = fmax(emax2, e2[i]);
+        if (threadIdx.x == 0) {
+            R gl = d[0], gu = d[0], emax2 = R(0);
+            for (int i = 0; i < m; ++i) {
+                R r = (i > 0 ? fabs(e[i - 1]) : R(0)) + (i + 1 < m ? fabs(e[i]) : R(0));
+                gl = fmin(gl, d[i] - r);
+                gu = fmax(gu, d[i] + r);
+                if (i + 1 < m) emax2 = fmax(emax2, e2[i]);
+            }
+            R tn = fmax(fabs(gl), fabs(gu));
+            gl -= R(2) * Num<R>::eps() * tn * (R)m + Num<R>::tiny();
+            gu += R(2) * Num<R>::eps() * tn * (R)m + Num<R>::tiny();
+            s_gl = gl;
+            s_gu = gu;
+            s_pivmin = Num<R>::tiny() * fmax(R(1), emax2);
         }
-        double tn = fmax(fabs(gl), fabs(gu));
-        gl -= 2.0 * DBL_EPSILON * tn * m + 1e-300;
-        gu += 2.0 * DBL_EPSILON * tn * m + 1e-300;
-        s_gl = gl;
-        s_gu = gu;
-        s_pivmin = DBL_MIN * fmax(1.0, emax2);
-    }
-    __syncthreads();
-    for (int j = threadIdx.x; j < m; j += blockDim.x) {
-        double lo = s_gl, hi = s_gu;
-        for (int it = 0; it < 200; ++it) {
-            double mid = 0.5 * (lo + hi);
-            if (hi - lo <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + 4.0 * s_pivmin || mid == lo || mid == hi)
-                break;
-            if (sturm_count(m, d, e2, mid, s_pivmin) > j) hi = mid; else lo = mid;
+        __syncthreads();
+        for (int j = threadIdx.x; j < m; j += blockDim.x) {
+            R lo = s_gl, hi = s_gu;
+            for (int it = 0; it < 200; ++it) {
+                R mid = R(0.5) * (lo + hi);
+                if (hi - lo <= R(2) * Num<R>::eps() * fmax(fabs(lo), fabs(hi)) + R(4) * s_pivmin || mid == lo ||
+                    mid == hi)
+                    break;
+                if (sturm_count(m, d, e2, mid, s_pivmin) > j) hi = mid; else lo = mid;
+            }
+            W[j] = (double)(R(0.5) * (lo + hi));
         }
-        W[j] = 0.5 * (lo + hi);
-    }
-    return;
+        return;
     }
     // ---- 3. implicit QL on (d, e) accumulating Z (row-major m x m, starts as identity) ----
     {
-        double *cs = pp, *sn = vv;  // reuse the Householder scratch for the sweep's rotations
-        for (int t = threadIdx.x; t < m * m; t += blockDim.x) Z[t] = ((t / m) == (t % m)) ? 1.0 : 0.0;
+        R *cs = pp, *sn = vv;  // reuse the Householder scratch for the sweep's rotations
+        for (int t = threadIdx.x; t < m * m; t += blockDim.x) Z[t] = ((t / m) == (t % m)) ? R(1) : R(0);
         __shared__ int s_lo, s_hi, s_done, s_fail;
         if (threadIdx.x == 0) { s_lo = 0; s_done = 0; s_fail = 0; }
         __syncthreads();
@@ -395,10 +420,15 @@ __global__ void __launch_bounds__(EIG_THREADS) k_syev(const int *mv, const int64
                 int lo = s_lo;
                 s_hi = -1;
                 while (lo < m - 1) {
-                    if (fabs(e[lo]) <= DBL_EPSILON * (fabs(d[lo]) + fabs(d[lo + 1]))) { e[lo] = 0.0; ++lo; iter = 0; continue; }
+                    if (fabs(e[lo]) <= Num<R>::eps() * (fabs(d[lo]) + fabs(d[lo + 1]))) {
+                        e[lo] = R(0);
+                        ++lo;
+                        iter = 0;
+                        continue;
+                    }
                     int hi = lo + 1;
-                    while (hi < m - 1 && !(fabs(e[hi]) <= DBL_EPSILON * (fabs(d[hi]) + fabs(d[hi + 1])))) ++hi;
-                    if (hi < m - 1) e[hi] = 0.0;
+                    while (hi < m - 1 && !(fabs(e[hi]) <= Num<R>::eps() * (fabs(d[hi]) + fabs(d[hi + 1])))) ++hi;
+                    if (hi < m - 1) e[hi] = R(0);
                     if (++iter > 100) { s_fail = 1; lo = m; break; }
                     ql_sweep_record(lo, hi, d, e, cs, sn);
                     s_hi = hi;
@@ -411,10 +441,10 @@ __global__ void __launch_bounds__(EIG_THREADS) k_syev(const int *mv, const int64
             if (s_hi >= 0) {
                 int lo = s_lo, hi = s_hi;
                 for (int r = threadIdx.x; r < m; r += blockDim.x) {
-                    double *zr = Z + (size_t)r * m;
+                    R *zr = Z + (size_t)r * m;
                     for (int k = hi - 1; k >= lo; --k) {
-                        double c = cs[k], sv = sn[k];
-                        double a0 = zr[k], a1 = zr[k + 1];
+                        R c = cs[k], sv = sn[k];
+                        R a0 = zr[k], a1 = zr[k + 1];
                         zr[k] = c * a0 - sv * a1;
                         zr[k + 1] = sv * a0 + c * a1;
                     }
@@ -424,19 +454,18 @@ __global__ void __launch_bounds__(EIG_THREADS) k_syev(const int *mv, const int64
             if (s_done) break;
         }
         if (threadIdx.x == 0) {
-            // selection sort of the eigenvalues; record the permutation in cs (as doubles)
-            for (int i = 0; i < m; ++i) cs[i] = (double)i;
+            // selection sort of the eigenvalues; the permutation is kept in cs
+            for (int i = 0; i < m; ++i) cs[i] = (R)i;
             for (int i = 0; i < m - 1; ++i) {
                 int mi = i;
                 for (int j = i + 1; j < m; ++j) if (d[j] < d[mi]) mi = j;
-                double t = d[i]; d[i] = d[mi]; d[mi] = t;
+                R t = d[i]; d[i] = d[mi]; d[mi] = t;
                 t = cs[i]; cs[i] = cs[mi]; cs[mi] = t;
             }
             if (info) info[b] = s_fail;
         }
         __syncthreads();
-        for (int j = threadIdx.x; j < m; j += blockDim.x) W[j] = d[j];
-        // gather sorted columns of Z (row-major) into column-major scratch e2.. -> use scr
+        for (int j = threadIdx.x; j < m; j += blockDim.x) W[j] = (double)d[j];
         for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
             int c = t / m, r = t % m;
             scr[t] = Z[(size_t)r * m + (int)cs[c]];
@@ -448,36 +477,71 @@ __global__ void __launch_bounds__(EIG_THREADS) k_syev(const int *mv, const int64
     // ---- 4. back-transformation y = H_0 ... H_{m-3} z, one warp per vector ----
     int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int c = warp; c < m; c += nw) {
-        double *z = Z + (size_t)c * m;
+        R *z = Z + (size_t)c * m;
         for (int k = m - 3; k >= 0; --k) {
-            double bk = beta[k];
-            if (bk == 0.0) continue;
-            const double *vk = a + (size_t)k * lda + (k + 1);
+            R bk = beta[k];
+            if (bk == R(0)) continue;
+            const R *vk = a + (size_t)k * lda + (k + 1);
             int len = m - k - 1;
-            double s = 0.0;
-            for (int i = lane; i < len; i += 32) s += (i == 0 ? 1.0 : vk[i]) * z[k + 1 + i];
+            R s = R(0);
+            for (int i = lane; i < len; i += 32) s += (i == 0 ? R(1) : vk[i]) * z[k + 1 + i];
             for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
             s *= bk;
-            for (int i = lane; i < len; i += 32) z[k + 1 + i] -= s * (i == 0 ? 1.0 : vk[i]);
+            for (int i = lane; i < len; i += 32) z[k + 1 + i] -= s * (i == 0 ? R(1) : vk[i]);
             __syncwarp();
         }
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < m * m; t += blockDim.x) Ag[t] = Z[t];
+    for (int t = threadIdx.x; t < m * m; t += blockDim.x) Ag[t] = (double)Z[t];
 }
 
 void syev_batched(int batch, const int *d_m, const int64_t *d_aoff, const int64_t *d_woff, double *d_A,
-                  double *d_w, int vecs, const int *d_sel, int mmax, double *d_work, int *d_info, cudaStream_t st) {
+                  double *d_w, int vecs, const int *d_sel, int mmax, double *d_work, int *d_info, cudaStream_t st,
+                  bool fp32) {
+    (void)d_sel;
     if (batch <= 0) return;
-    size_t smem = mmax <= EIG_SMEM_MAX_M ? (size_t)mmax * mmax * sizeof(double) : 0;
     static bool attr = false;
     if (!attr) {
-        MBL_CUDA(cudaFuncSetAttribute(k_syev, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        MBL_CUDA(cudaFuncSetAttribute(k_syev<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       EIG_SMEM_MAX_M * EIG_SMEM_MAX_M * sizeof(double)));
+        MBL_CUDA(cudaFuncSetAttribute(k_syev<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      EIG_SMEM_MAX_M * EIG_SMEM_MAX_M * sizeof(float)));
         attr = true;
     }
-    k_syev<<<batch, EIG_THREADS, smem, st>>>(d_m, d_aoff, d_woff, d_A, d_w, vecs, d_sel, d_work,
-                                             syev_work_doubles(mmax, vecs != 0), d_info);
+    if (fp32) {
+        if (mmax > EIG_SMEM_MAX_M) fail(MBL_ERR_INVALID, "FP32 small eigensolver limited to order 160");
+        k_syev<float><<<batch, EIG_THREADS, (size_t)mmax * mmax * sizeof(float), st>>>(
+            d_m, d_aoff, d_woff, d_A, d_w, vecs, d_work, syev_work_doubles(mmax, vecs != 0), d_info, mmax);
+    } else {
+        size_t smem = mmax <= EIG_SMEM_MAX_M ? (size_t)mmax * mmax * sizeof(double) : 0;
+        k_syev<double><<<batch, EIG_THREADS, smem, st>>>(d_m, d_aoff, d_woff, d_A, d_w, vecs, d_work,
+                                                         syev_work_doubles(mmax, vecs != 0), d_info,
+                                                         mmax <= EIG_SMEM_MAX_M ? mmax : 0);
+    }
+    MBL_LAUNCH_CHECK();
+}
+
+// C (M x N, column-major ldc) = alpha op(A) op(B) + beta C, op = transpose if the flag is set;
+// small FP64 matrices, one thread per output.
+__global__ void k_gemm_small(int ta, int tb, int M, int N, int K, double alpha, const double *A, int lda,
+                             const double *B, int ldb, double beta, double *C, int ldc) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= M * N) return;
+    int i = t % M, j = t / M;
+    double s = 0.0;
+    for (int k = 0; k < K; ++k) {
+        double a = ta ? A[(size_t)i * lda + k] : A[(size_t)k * lda + i];
+        double b = tb ? B[(size_t)k * ldb + j] : B[(size_t)j * ldb + k];
+        s = fma(a, b, s);
+    }
+    C[(size_t)j * ldc + i] = alpha * s + (beta == 0.0 ? 0.0 : beta * C[(size_t)j * ldc + i]);
+}
+
+void gemm_small(bool ta, bool tb, int M, int N, int K, double alpha, const double *A, int lda, const double *B,
+                int ldb, double beta, double *C, int ldc, cudaStream_t st) {
+    if (M <= 0 || N <= 0) return;
+    k_gemm_small<<<(M * N + 127) / 128, 128, 0, st>>>(ta ? 1 : 0, tb ? 1 : 0, M, N, K, alpha, A, lda, B, ldb, beta, C,
+                                                      ldc);
     MBL_LAUNCH_CHECK();
 }
 

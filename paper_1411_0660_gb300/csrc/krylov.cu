@@ -110,13 +110,14 @@ __global__ void k_Bk(const double *T, int ldt, int mm, int p, const double *SK, 
     Bk[t] = s;
 }
 
-__global__ void k_restart_T(double *T, int ldt, int k, int p, const double *theta, const int *keep, const double *Bk) {
+// New T after a thick restart: [[Tk, Bk^T], [Bk, 0]] with Tk (k x k, ld k) symmetrized.
+__global__ void k_restart_T(double *T, int ldt, int k, int p, const double *Tk, const double *Bk) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     int K = k + p;
     if (t >= K * K) return;
     int r = t % K, c = t / K;
     double v = 0.0;
-    if (r < k && c < k) v = (r == c) ? theta[keep[r]] : 0.0;
+    if (r < k && c < k) v = 0.5 * (Tk[(size_t)c * k + r] + Tk[(size_t)r * k + c]);
     else if (r >= k && c < k) v = Bk[(r - k) * k + c];
     else if (r < k && c >= k) v = Bk[(c - k) * k + r];
     T[(size_t)c * ldt + r] = v;
@@ -239,6 +240,9 @@ KrylovSchur::KrylovSchur(Ctx *c, int64_t n_, int p_, int ncv_) : ctx(c), n(n_), 
     res.alloc(ctx, ldv);
     keep.alloc(ctx, ldv);
     SK.alloc(ctx, (size_t)ldv * ldv);
+    NS1.alloc(ctx, (size_t)ldv * ldv);
+    NS2.alloc(ctx, (size_t)ldv * ldv);
+    NS3.alloc(ctx, (size_t)ldv * ldv);
     Bk.alloc(ctx, (size_t)p * ldv);
     int64_t zero2[2] = {0, 0};
     MBL_CUDA(cudaMemcpy(eigOff.data(), zero2, sizeof(zero2), cudaMemcpyHostToDevice));
@@ -318,8 +322,10 @@ void KrylovSchur::ritz(cudaStream_t st, std::vector<double> &theta, std::vector<
     MBL_CUDA(cudaMemcpyAsync(eigM.data(), &mm, sizeof(int), cudaMemcpyHostToDevice, st));
     {
         ProfScope ps(ctx, "syev_krylov", (double)mm, st);
+        // FP32 is enough here: the kept vectors are re-orthonormalized and T re-projected in FP64 at
+        // the restart, and convergence is decided by the FP64 Rayleigh-Ritz on H
         syev_batched(1, eigM.data(), eigOff.data(), eigOff.data(), eigA.data(), eigW.data(), 1, nullptr, ldv,
-                     eigWork.data(), eigInfo.data(), st);
+                     eigWork.data(), eigInfo.data(), st, ldv <= EIG_SMEM_MAX_M);
     }
     k_ritz_resid<<<nblk(mm, 128), 128, 0, st>>>(T.data(), ldv, mm, p, eigA.data(), res.data());
     MBL_LAUNCH_CHECK();
@@ -334,16 +340,29 @@ void KrylovSchur::restart(const std::vector<int> &keep_idx, cudaStream_t st) {
     int mm = m - p;
     int k = (int)keep_idx.size();
     MBL_CUDA(cudaMemcpyAsync(keep.data(), keep_idx.data(), k * sizeof(int), cudaMemcpyHostToDevice, st));
-    k_gather_S<<<nblk((int64_t)mm * k), 256, 0, st>>>(eigA.data(), mm, keep.data(), k, SK.data());
+    // Y = S_keep^T (k x mm, column-major ld k) from the FP32 Ritz vectors
+    double *Y = SK.data(), *Y2 = NS1.data(), *Gk = NS2.data(), *Q = NS3.data();
+    k_gather_S<<<nblk((int64_t)mm * k), 256, 0, st>>>(eigA.data(), mm, keep.data(), k, Y);
     MBL_LAUNCH_CHECK();
-    k_Bk<<<nblk((int64_t)p * k), 256, 0, st>>>(T.data(), ldv, mm, p, SK.data(), k, Bk.data());
+    // Newton-Schulz in FP64: S <- S (3 I - S^T S) / 2, i.e. Y <- 1.5 Y - 0.5 (Y Y^T) Y; two steps take
+    // an orthogonality defect of FP32 size (~1e-6) to FP64 rounding
+    for (int it = 0; it < 2; ++it) {
+        gemm_small(false, true, k, k, mm, 1.0, Y, k, Y, k, 0.0, Gk, k, st);
+        MBL_CUDA(cudaMemcpyAsync(Y2, Y, (size_t)k * mm * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        gemm_small(false, false, k, mm, k, -0.5, Gk, k, Y, k, 1.5, Y2, k, st);
+        std::swap(Y, Y2);
+    }
+    // exact projection of the expanded T onto the kept vectors: Tk = S^T T S (no diagonal assumed)
+    gemm_small(false, true, mm, k, mm, 1.0, T.data(), ldv, Y, k, 0.0, Q, mm, st);
+    gemm_small(false, false, k, k, mm, 1.0, Y, k, Q, mm, 0.0, Gk, k, st);
+    k_Bk<<<nblk((int64_t)p * k), 256, 0, st>>>(T.data(), ldv, mm, p, Y, k, Bk.data());
     MBL_LAUNCH_CHECK();
-    dense_nn(n, V.data(), ldv, mm, SK.data(), k, V2.data(), ldv, 0, st);
+    dense_nn(n, V.data(), ldv, mm, Y, k, V2.data(), ldv, 0, st);
     copy_cols(n, V.data(), ldv, mm, V2.data(), ldv, k, p, st);
     std::swap(V, V2);
     k_zero<<<nblk((int64_t)ldv * ldv), 256, 0, st>>>(T.data(), (int64_t)ldv * ldv);
     MBL_LAUNCH_CHECK();
-    k_restart_T<<<nblk((int64_t)(k + p) * (k + p)), 256, 0, st>>>(T.data(), ldv, k, p, eigW.data(), keep.data(), Bk.data());
+    k_restart_T<<<nblk((int64_t)(k + p) * (k + p)), 256, 0, st>>>(T.data(), ldv, k, p, Gk, Bk.data());
     MBL_LAUNCH_CHECK();
     m = k + p;
 }

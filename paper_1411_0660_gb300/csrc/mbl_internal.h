@@ -168,8 +168,14 @@ void chol_qr(int64_t n, double *X, int p, double *R, double *G, double *work, in
 // lda_b) -> eigenvalues ascending w_b, eigenvectors (if vecs) overwrite A_b.
 size_t syev_work_doubles(int mmax, bool vecs = true);
 // sel (optional, indexed like w): eigenvectors are computed only where sel != 0 (others zero).
+constexpr int EIG_SMEM_MAX_M = 160;  // largest order the small eigensolver keeps in shared memory
+// fp32: run the reduction and the QL iteration in FP32 (order <= 160; used where FP32 eigenvectors
+// are enough, e.g. Krylov-Schur restarts, which are re-orthonormalized in FP64).
 void syev_batched(int batch, const int *d_m, const int64_t *d_aoff, const int64_t *d_woff, double *d_A,
                   double *d_w, int vecs, const int *d_sel, int mmax, double *d_work, int *d_info,
-                  cudaStream_t st);
+                  cudaStream_t st, bool fp32 = false);
+// C = alpha op(A) op(B) + beta C for small column-major FP64 matrices
+void gemm_small(bool ta, bool tb, int M, int N, int K, double alpha, const double *A, int lda, const double *B,
+                int ldb, double beta, double *C, int ldc, cudaStream_t st);
 
 }  // namespace mbl
