@@ -79,18 +79,46 @@ DevMem &DevMem::operator=(DevMem &&o) noexcept {
     return *this;
 }
 
+// Device memory comes from one stream-ordered pool per device that keeps freed blocks cached
+// (release threshold: unlimited): a job's factor, fronts and Krylov basis are reused by the next
+// job without cudaMalloc/cudaFree, whose implicit device synchronization would stall the other
+// contexts' streams.  mbl_ctx_destroy trims the pool.
+static std::mutex g_pool_mu;
+static cudaMemPool_t device_pool(int device) {
+    static std::map<int, cudaMemPool_t> *pools = new std::map<int, cudaMemPool_t>();
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    auto it = pools->find(device);
+    if (it != pools->end()) return it->second;
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = device;
+    cudaMemPool_t pool;
+    MBL_CUDA(cudaMemPoolCreate(&pool, &props));
+    uint64_t thr = UINT64_MAX;
+    MBL_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr));
+    (*pools)[device] = pool;
+    return pool;
+}
+
+void trim_device_pool(int device) { cudaMemPoolTrimTo(device_pool(device), 0); }
+
 void DevMem::alloc(Ctx *c, size_t nbytes) {
     release();
     if (nbytes == 0) nbytes = 16;
     if (c->budget && c->in_use + nbytes > c->budget)
         fail(MBL_ERR_OOM, "allocation of " + std::to_string(nbytes) + " bytes exceeds the context budget");
-    cudaError_t e = cudaMalloc(&p, nbytes);
+    cudaError_t e = cudaMallocFromPoolAsync(&p, nbytes, device_pool(c->device), c->stream);
     if (e == cudaErrorMemoryAllocation) {
         (void)cudaGetLastError();
         p = nullptr;
-        fail(MBL_ERR_OOM, "cudaMalloc of " + std::to_string(nbytes) + " bytes failed");
+        fail(MBL_ERR_OOM, "device allocation of " + std::to_string(nbytes) + " bytes failed");
     }
     MBL_CUDA(e);
+    // a block reused from another stream may still be waited on by that stream's work: settle it
+    // before any copy outside this stream touches the block
+    MBL_CUDA(cudaStreamSynchronize(c->stream));
     bytes = nbytes;
     ctx = c;
     c->in_use += nbytes;
@@ -99,8 +127,9 @@ void DevMem::alloc(Ctx *c, size_t nbytes) {
 
 void DevMem::release() {
     if (p) {
-        cudaFree(p);
-        if (ctx && ctx_alive(ctx)) ctx->in_use -= bytes;
+        const bool live = ctx && ctx_alive(ctx);
+        cudaFreeAsync(p, live ? ctx->stream : (cudaStream_t)0);
+        if (live) ctx->in_use -= bytes;
     }
     p = nullptr;
     bytes = 0;
@@ -282,12 +311,15 @@ void mbl_ctx_destroy(mbl_ctx *ctx) {
     for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
     ctx->plans.clear();
     ctx->ent.clear();
+    cudaStreamSynchronize(ctx->stream);
     cudaStreamDestroy(ctx->stream);
     {
         std::lock_guard<std::mutex> lk(g_ctx_mu);
         live_ctx().erase(ctx);
     }
+    const int dev = ctx->device;
     delete ctx;
+    trim_device_pool(dev);
 }
 
 int mbl_ctx_synchronize(mbl_ctx *ctx) {

@@ -368,6 +368,15 @@ __device__ __forceinline__ int find_sdesc(const SolveDesc *d, int nd, int64_t b)
     return lo;
 }
 
+__device__ __forceinline__ int find_sdesc_b(const SolveDesc *d, int nd, int64_t b) {
+    int lo = 0, hi = nd - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (d[mid].offb <= b) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
 // M of one solve panel, 32 columns per CTA, in FP64: the forward sequence (pivot permutation,
 // unit-lower substitution, elimination of the later rows of the panel) applied to unit vectors.
 template <class T>
@@ -459,76 +468,126 @@ __global__ void __launch_bounds__(256) k_fwd_gather(const AsmItem *items, const 
     }
 }
 
-constexpr int MCH = 16;  // columns of M^T per CTA in the backward panel-operator kernel
-
-// forward, rows r0..r0+16 of each solve panel: Zs[rows] = M[rows, :] Z[panel], grid (descs, SPW / MCH)
+// G = [M; L21 M] in place of a solve panel's column block [k0, f) x [k0, k0 + w): RBB rows per
+// CTA (grid: the step's backward row tiles); each CTA owns its rows, so the update is in place.
 template <class T>
-__global__ void __launch_bounds__(256) k_fwd_m(const SolveDesc *sdescs, const int64_t *zo, const T *Mall, const T *Z,
-                                               T *Zs, int p) {
+__global__ void __launch_bounds__(256) k_apply_m(const SolveDesc *sdescs, int nd, const int64_t *fo,
+                                                 const int32_t *fsz, T *arena, const T *Mall) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    T(*zin)[33] = reinterpret_cast<T(*)[33]>(smraw);
-    const SolveDesc d = sdescs[blockIdx.x];
-    const int w = d.w, r0 = blockIdx.y * MCH;
-    if (r0 >= w) return;
-    const int64_t off = (zo[d.front] + d.k0) * p;
-    for (int idx = threadIdx.x; idx < w * p; idx += blockDim.x) zin[idx / p][idx % p] = Z[off + idx];
-    __syncthreads();
+    T *As = reinterpret_cast<T *>(smraw);  // RBB x (SPW + 1), row-major
+    T *Ms = As + RBB * (SPW + 1);          // 32 x SPW chunk of M, row-major
+    const int di = find_sdesc_b(sdescs, nd, blockIdx.x);
+    const SolveDesc d = sdescs[di];
+    const int s = d.front, f = fsz[s], k0 = d.k0, w = d.w;
+    const int r0 = (int)(blockIdx.x - d.offb) * RBB;  // first row, relative to k0
+    const int nr = min(RBB, w + d.m2 - r0);
+    if (nr <= 0) return;
+    T *F = arena + fo[s];
     const T *M = Mall + d.moff;
-    const int rr = threadIdx.x / 16, cs = threadIdx.x % 16, r = r0 + rr;
-    T acc[32];
+    const int tr = threadIdx.x % 16, tc = threadIdx.x / 16;
+    T acc[4][16];
 #pragma unroll
-    for (int q = 0; q < 32; ++q) acc[q] = T(0);
-    if (r < w) {
-#pragma unroll 4
-        for (int c = cs; c < w; c += 16) {
-            const T m = M[(int64_t)c * w + r];
+    for (int i = 0; i < 4; ++i)
 #pragma unroll
-            for (int q = 0; q < 32; ++q)
-                if (q < p) acc[q] += m * zin[c][q];
+        for (int j = 0; j < 16; ++j) acc[i][j] = T(0);
+    if (r0 + nr > w) {  // the tile has rows of L21
+        for (int idx = threadIdx.x; idx < RBB * w; idx += blockDim.x) {
+            int i = idx % RBB, c = idx / RBB;
+            As[i * (SPW + 1) + c] = i < nr ? F[(int64_t)(k0 + c) * f + k0 + r0 + i] : T(0);
+        }
+        for (int kc0 = 0; kc0 < w; kc0 += 32) {
+            const int kc = min(32, w - kc0);
+            __syncthreads();
+            for (int idx = threadIdx.x; idx < 32 * SPW; idx += blockDim.x) {
+                int k = idx % 32, c = idx / 32;
+                Ms[k * SPW + c] = (k < kc && c < w) ? M[(int64_t)c * w + kc0 + k] : T(0);
+            }
+            __syncthreads();
+            for (int k = 0; k < kc; ++k) {
+                T a[4], bv[16];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) a[i] = As[(tr + 16 * i) * (SPW + 1) + kc0 + k];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) bv[j] = Ms[k * SPW + tc + 16 * j];
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) acc[i][j] += a[i] * bv[j];
+            }
         }
     }
 #pragma unroll
-    for (int q = 0; q < 32; ++q) {
-        if (q >= p) break;
-        T v = acc[q];
-        for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (cs == 0 && r < w) Zs[off + (int64_t)r * p + q] = v;
+    for (int i = 0; i < 4; ++i) {
+        const int row = tr + 16 * i;
+        if (row >= nr) continue;
+        const int rr = r0 + row;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const int col = tc + 16 * j;
+            if (col >= w) continue;
+            F[(int64_t)(k0 + col) * f + k0 + rr] = rr < w ? M[(int64_t)col * w + rr] : acc[i][j];
+        }
     }
 }
 
-// forward, rows below each solve panel: Z[r] -= L[r, panel] Zs[panel]; one thread per row (RB per
-// CTA), every right-hand side in registers, the column loop unrolled for loads in flight.
-template <class T>
-__global__ void __launch_bounds__(RB) k_fwd_upd(const SolveDesc *sdescs, int nd, const int64_t *fo, const int64_t *zo,
-                                                const int32_t *fsz, const T *arena, const T *Zs, T *Z, int p) {
+// Forward solve step, RBF rows of [k0, f) per CTA: with z = Z[panel] (PB >= p, zero-padded),
+// rows of the panel get Zs = M z and rows below get Z -= (L21 M) z.  Warp j takes columns
+// [32 j, 32 j + 32) of the panel; the eight partial sums meet in shared memory.
+template <class T, int PB>
+__global__ void __launch_bounds__(256) k_fwd_step(const SolveDesc *sdescs, int nd, const int64_t *fo,
+                                                  const int64_t *zo, const int32_t *fsz, const T *arena, T *Z, T *Zs,
+                                                  int p) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    T(*zp)[33] = reinterpret_cast<T(*)[33]>(smraw);
+    T *zp = reinterpret_cast<T *>(smraw);  // SPW x PB; afterwards the 8 x PB x RBF partials
     const int di = find_sdesc(sdescs, nd, blockIdx.x);
     const SolveDesc d = sdescs[di];
     const int s = d.front, f = fsz[s], k0 = d.k0, w = d.w;
-    const int r0 = k0 + w + (int)(blockIdx.x - d.off) * RB;
-    if (r0 >= f) return;
-    const int nr = min(RB, f - r0);
-    const T *zs = Zs + (zo[s] + k0) * p;
-    for (int idx = threadIdx.x; idx < w * p; idx += blockDim.x) zp[idx / p][idx % p] = zs[idx];
-    __syncthreads();
-    const int i = threadIdx.x;
-    if (i >= nr) return;
-    const T *col = arena + fo[s] + (int64_t)k0 * f + r0 + i;
-    T acc[32];
-#pragma unroll
-    for (int q = 0; q < 32; ++q) acc[q] = T(0);
-#pragma unroll 16
-    for (int c = 0; c < w; ++c) {
-        const T l = col[(int64_t)c * f];
-#pragma unroll
-        for (int q = 0; q < 32; ++q)
-            if (q < p) acc[q] += l * zp[c][q];
+    const int r0 = (int)(blockIdx.x - d.off) * RBF;  // relative to k0
+    const int nr = min(RBF, w + d.m2 - r0);
+    const int64_t zb = zo[s] + k0;
+    for (int idx = threadIdx.x; idx < w * PB; idx += blockDim.x) {
+        int c = idx / PB, q = idx % PB;
+        zp[idx] = q < p ? Z[(zb + c) * p + q] : T(0);
     }
-    T *z = Z + (zo[s] + r0 + i) * p;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    T acc[PB];
 #pragma unroll
-    for (int q = 0; q < 32; ++q)
-        if (q < p) z[q] -= acc[q];
+    for (int q = 0; q < PB; ++q) acc[q] = T(0);
+    const int c0 = wp * 32, c1 = min(w, c0 + 32);
+    if (lane < nr && c0 < c1) {
+        const T *g = arena + fo[s] + (int64_t)k0 * f + k0 + r0 + lane;
+        if (c1 - c0 == 32) {
+            T lv[32];
+#pragma unroll
+            for (int c = 0; c < 32; ++c) lv[c] = g[(int64_t)(c0 + c) * f];
+#pragma unroll
+            for (int c = 0; c < 32; ++c)
+#pragma unroll
+                for (int q = 0; q < PB; ++q) acc[q] += lv[c] * zp[(c0 + c) * PB + q];
+        } else {
+            for (int c = c0; c < c1; ++c) {
+                const T l = g[(int64_t)c * f];
+#pragma unroll
+                for (int q = 0; q < PB; ++q) acc[q] += l * zp[c * PB + q];
+            }
+        }
+    }
+    __syncthreads();
+    T *red = zp;
+#pragma unroll
+    for (int q = 0; q < PB; ++q) red[(wp * PB + q) * RBF + lane] = acc[q];
+    __syncthreads();
+    for (int o = threadIdx.x; o < RBF * PB; o += blockDim.x) {
+        const int i = o % RBF, q = o / RBF;
+        if (i >= nr || q >= p) continue;
+        T v = T(0);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v += red[(j * PB + q) * RBF + i];
+        const int rr = r0 + i;
+        if (rr < w) Zs[(zb + rr) * p + q] = v;
+        else Z[(zb + rr) * p + q] -= v;
+    }
 }
 
 template <class T>
@@ -558,96 +617,81 @@ __global__ void k_bwd_gather(const AsmItem *items, const int64_t *zo, const int3
     }
 }
 
-// backward, rows below each solve panel: P[block][c][q] = sum_r L[r][k0 + c] Z[r][q]
-template <class T>
-__global__ void __launch_bounds__(256) k_bwd_part(const SolveDesc *sdescs, int nd, const int64_t *fo,
-                                                  const int64_t *zo, const int32_t *fsz, const T *arena, const T *Z,
-                                                  int p, T *P) {
+// Backward solve step, tiles of RBB rows x RBB columns of G = [M; L21 M] (grid: row tiles x column
+// chunks): x_panel = G^T v with v = [y_panel; -x_below].  Each tile writes its partial sums; the
+// last tile of a (panel, column chunk) to finish (counted with an atomic, after a fence) adds the
+// partials in tile order and writes the panel's x into Zs, then re-arms the counter.  The panel's
+// rows of Z hold the forward result y (pivoted order); rows below the panel come from Zs (fully
+// summed rows solved by later panels) or Z (the ancestors' x).
+template <class T, int PB>
+__global__ void __launch_bounds__(256) k_bwd_step(const SolveDesc *sdescs, int nd, const int64_t *fo,
+                                                  const int64_t *zo, const int32_t *fsz, const int32_t *nc,
+                                                  const T *arena, const T *Z, T *Zs, T *P, unsigned int *cnt, int p) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    T(*Fs)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(smraw);                        // RB x (NB + 1)
-    T(*zr)[33] = reinterpret_cast<T(*)[33]>(smraw + sizeof(T) * RB * (NB + 1));    // RB x 33
-    const int di = find_sdesc(sdescs, nd, blockIdx.x);
+    T(*Gs)[RBB + 1] = reinterpret_cast<T(*)[RBB + 1]>(smraw);   // RBB x (RBB + 1)
+    T *vs = reinterpret_cast<T *>(smraw + sizeof(T) * RBB * (RBB + 1));  // RBB x PB
+    __shared__ int s_last;
+    const int di = find_sdesc_b(sdescs, nd, blockIdx.x);
     const SolveDesc d = sdescs[di];
-    const int s = d.front, f = fsz[s], k0 = d.k0, w = d.w;
-    const int cc = blockIdx.y * NB;  // this CTA's 64 columns of the panel
-    if (cc >= w) return;
-    const int r0 = k0 + w + (int)(blockIdx.x - d.off) * RB;
-    const int nr = max(0, min(RB, f - r0));
-    T *out = P + (int64_t)blockIdx.x * SPW * 32;
+    const int cc = blockIdx.y * RBB;
+    if (cc >= d.w) return;
+    const int s = d.front, f = fsz[s], k0 = d.k0, w = d.w, ncs = nc[s];
+    const int b = (int)(blockIdx.x - d.offb);
+    const int nb = (w + d.m2 + RBB - 1) / RBB;
+    const int r0 = b * RBB;  // relative to k0
+    const int nr = min(RBB, w + d.m2 - r0);
+    const int wc = min(RBB, w - cc);
+    const int64_t zb = zo[s] + k0;
     const T *F = arena + fo[s];
-    const T *z = Z + zo[s] * p;
-    for (int idx = threadIdx.x; idx < nr * p; idx += blockDim.x) zr[idx / p][idx % p] = z[(int64_t)r0 * p + idx];
-    {
-        const int wc = min(NB, w - cc);
-        __syncthreads();
-        for (int idx = threadIdx.x; idx < nr * wc; idx += blockDim.x) {
-            int i = idx % nr, c = idx / nr;
-            Fs[i][c] = F[(int64_t)(k0 + cc + c) * f + r0 + i];
+    for (int idx = threadIdx.x; idx < RBB * PB; idx += blockDim.x) {
+        const int i = idx / PB, q = idx % PB;
+        T v = T(0);
+        if (i < nr && q < p) {
+            const int rr = r0 + i;
+            if (rr < w) v = Z[(zb + rr) * p + q];
+            else if (k0 + rr < ncs) v = -Zs[(zb + rr) * p + q];
+            else v = -Z[(zb + rr) * p + q];
         }
-        __syncthreads();
-        for (int o = threadIdx.x; o < wc * p; o += blockDim.x) {
-            int c = o / p, q = o % p;
-            T acc = T(0);
-#pragma unroll 8
-            for (int i = 0; i < nr; ++i) acc += Fs[i][c] * zr[i][q];
-            out[(cc + c) * 32 + q] = acc;
-        }
+        vs[idx] = v;
     }
-}
-
-// backward, rows r0..r0+16 of each panel: Zs[panel] = Z[panel] - sum over row blocks of the partials
-template <class T>
-__global__ void __launch_bounds__(256) k_bwd_reduce(const SolveDesc *sdescs, const int64_t *zo, const T *P,
-                                                    const T *Z, T *Zs, int p) {
-    const SolveDesc d = sdescs[blockIdx.x];
-    const int w = d.w, r0 = blockIdx.y * MCH;
-    if (r0 >= w) return;
-    const int64_t nrb = d.m2 > 0 ? (d.m2 + RB - 1) / RB : 1;
-    const int64_t off = (zo[d.front] + d.k0) * p;
-    for (int idx = threadIdx.x; idx < MCH * p; idx += blockDim.x) {
-        int r = r0 + idx / p, q = idx % p;
-        if (r >= w) continue;
-        T v = Z[off + (int64_t)r * p + q];
-#pragma unroll 8
-        for (int64_t b = 0; b < nrb; ++b) v -= P[(d.off + b) * SPW * 32 + r * 32 + q];
-        Zs[off + (int64_t)r * p + q] = (T)v;
+    for (int idx = threadIdx.x; idx < RBB * RBB; idx += blockDim.x) {
+        const int i = idx % RBB, c = idx / RBB;
+        Gs[i][c] = (i < nr && c < wc) ? F[(int64_t)(k0 + cc + c) * f + k0 + r0 + i] : T(0);
     }
-}
-
-// backward: Z[panel columns c0..c0+16) = M[:, cols]^T Zs[panel] (FP64), grid (descs, SPW / MCH)
-template <class T>
-__global__ void __launch_bounds__(256) k_bwd_m(const SolveDesc *sdescs, const int64_t *zo, const T *Mall,
-                                               const T *Zs, T *Z, int p) {
-    extern __shared__ __align__(16) unsigned char smraw[];
-    T(*zb)[33] = reinterpret_cast<T(*)[33]>(smraw);
-    const SolveDesc d = sdescs[blockIdx.x];
-    const int w = d.w, c0 = blockIdx.y * MCH;
-    if (c0 >= w) return;
-    const int64_t off = (zo[d.front] + d.k0) * p;
-    for (int idx = threadIdx.x; idx < w * p; idx += blockDim.x) zb[idx / p][idx % p] = Zs[off + idx];
     __syncthreads();
-    const T *M = Mall + d.moff;
-    const int cc = threadIdx.x / 16, rs = threadIdx.x % 16, c = c0 + cc;
-    T acc[32];
+    constexpr int QP = PB / 4;
+    const int c = threadIdx.x % RBB, qg = threadIdx.x / RBB;
+    T acc[QP];
 #pragma unroll
-    for (int q = 0; q < 32; ++q) acc[q] = T(0);
-    if (c < w) {
-        const T *mc = M + (int64_t)c * w;
-#pragma unroll 4
-        for (int r = rs; r < w; r += 16) {
-            const T m = mc[r];
+    for (int k = 0; k < QP; ++k) acc[k] = T(0);
+#pragma unroll 8
+    for (int i = 0; i < RBB; ++i) {
+        const T gv = Gs[i][c];
 #pragma unroll
-            for (int q = 0; q < 32; ++q)
-                if (q < p) acc[q] += m * zb[r][q];
-        }
+        for (int k = 0; k < QP; ++k) acc[k] += gv * vs[i * PB + qg + 4 * k];
     }
+    const int64_t tile = (int64_t)RBB * PB;
+    T *out = P + ((d.offb + b) * SUBS + blockIdx.y) * tile;
 #pragma unroll
-    for (int q = 0; q < 32; ++q) {
-        if (q >= p) break;
-        T v = acc[q];
-        for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (rs == 0 && c < w) Z[off + (int64_t)c * p + q] = (T)v;
+    for (int k = 0; k < QP; ++k) out[(qg + 4 * k) * RBB + c] = acc[k];
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned int prev = atomicAdd(&cnt[(size_t)di * SUBS + blockIdx.y], 1u);
+        s_last = prev == (unsigned int)(nb - 1);
     }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    const T *src0 = P + (d.offb * SUBS + blockIdx.y) * tile;
+    for (int o = threadIdx.x; o < wc * p; o += blockDim.x) {
+        const int cq = o % wc, q = o / wc;
+        const T *src = src0 + q * RBB + cq;
+        T v = T(0);
+        for (int bb = 0; bb < nb; ++bb) v += __ldcg(src + (int64_t)bb * SUBS * tile);
+        Zs[(zb + cc + cq) * p + q] = v;
+    }
+    if (threadIdx.x == 0) cnt[(size_t)di * SUBS + blockIdx.y] = 0u;
 }
 
 template <class T>
@@ -668,21 +712,32 @@ __global__ void k_bwd_finish(const AsmItem *items, const int64_t *zo, const int3
 template <class T>
 static size_t build_m_smem() { return 8 * ((size_t)(SPW + NB) * 33 + (size_t)NB * (NB + 1)); }
 template <class T>
-static size_t panel_vec_smem() { return sizeof(T) * (size_t)SPW * 33; }
-template <class T>
 static size_t trsm_smem() { return sizeof(T) * (size_t)2 * NB * (NB + 1); }
 template <class T>
-static size_t bwd_part_smem() { return sizeof(T) * ((size_t)RB * (NB + 1) + (size_t)RB * 33); }
+static size_t apply_m_smem() { return sizeof(T) * ((size_t)RBB * (SPW + 1) + (size_t)32 * SPW); }
+template <class T, int PB>
+static size_t fwd_step_smem() { return sizeof(T) * (size_t)SPW * PB; }
+template <class T, int PB>
+static size_t bwd_step_smem() { return sizeof(T) * ((size_t)RBB * (RBB + 1) + (size_t)RBB * PB); }
+static int rhs_pad(int p) { return p <= 8 ? 8 : (p <= 16 ? 16 : 32); }
+
+template <class T, int PB>
+static void set_step_attrs() {
+    MBL_CUDA(cudaFuncSetAttribute(k_fwd_step<T, PB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)fwd_step_smem<T, PB>()));
+    MBL_CUDA(cudaFuncSetAttribute(k_bwd_step<T, PB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)bwd_step_smem<T, PB>()));
+}
 
 template <class T>
 static void set_solve_attrs() {
     static bool done = false;
     if (done) return;
     MBL_CUDA(cudaFuncSetAttribute(k_build_m<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)build_m_smem<T>()));
-    MBL_CUDA(cudaFuncSetAttribute(k_fwd_m<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)panel_vec_smem<T>()));
-    MBL_CUDA(cudaFuncSetAttribute(k_fwd_upd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)panel_vec_smem<T>()));
-    MBL_CUDA(cudaFuncSetAttribute(k_bwd_m<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)panel_vec_smem<T>()));
-    MBL_CUDA(cudaFuncSetAttribute(k_bwd_part<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwd_part_smem<T>()));
+    MBL_CUDA(cudaFuncSetAttribute(k_apply_m<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)apply_m_smem<T>()));
+    set_step_attrs<T, 8>();
+    set_step_attrs<T, 16>();
+    set_step_attrs<T, 32>();
     done = true;
 }
 
@@ -746,13 +801,19 @@ static void factor_impl(Factorization &fz, cudaStream_t st) {
             }
         }
     }
-    // block operators of the solve panels
+    // block operators of the solve panels, then G = [M; L21 M] in place of each panel's column block
     if (!p.sdescs.empty()) {
         dim3 grid((unsigned)p.sdescs.size(), SPW / 32);
         k_build_m<T><<<grid, 256, build_m_smem<T>(), st>>>(p.d_sdescs.data(), p.d_sn_fo.data(), p.d_sn_f.data(),
                                                            p.d_sn_start.data(), arena, fz.piv.data(),
                                                            static_cast<T *>(fz.M.m.p));
         MBL_LAUNCH_CHECK();
+        for (const SolveStep &ss : p.ssteps) {
+            k_apply_m<T><<<(unsigned)ss.nrbb, 256, apply_m_smem<T>(), st>>>(p.d_sdescs.data() + ss.d0, ss.nd,
+                                                                           p.d_sn_fo.data(), p.d_sn_f.data(), arena,
+                                                                           static_cast<const T *>(fz.M.m.p));
+            MBL_LAUNCH_CHECK();
+        }
     }
 }
 
@@ -762,18 +823,18 @@ void numeric_factor(Factorization &fz, cudaStream_t st) {
 }
 
 // The level x panel sequence between the permutations, on the factorization's internal buffers.
-template <class T>
+template <class T, int PB>
 static void solve_levels(Factorization &fz, int p, cudaStream_t st) {
     Plan &pl = *fz.plan;
     T *arena = static_cast<T *>(fz.arena.m.p);
     T *Dg = static_cast<T *>(fz.D.m.p);
-    const T *M = static_cast<const T *>(fz.M.m.p);
     T *Z = static_cast<T *>(fz.zwork.m.p);
     T *Zs = static_cast<T *>(fz.zsolved.m.p);
     T *y = static_cast<T *>(fz.ywork.m.p);
     T *yfw = static_cast<T *>(fz.yfw.m.p);
     T *P = static_cast<T *>(fz.pwork.m.p);
-    const size_t vsm = panel_vec_smem<T>(), psm = bwd_part_smem<T>();
+    unsigned int *cnt = fz.scnt.data();
+    const size_t fsm = fwd_step_smem<T, PB>(), bsm = bwd_step_smem<T, PB>();
     for (int l = 0; l < pl.nlevels; ++l) {
         int na = pl.asm_ptr[l + 1] - pl.asm_ptr[l];
         const AsmItem *items = pl.d_asm_items.data() + pl.asm_ptr[l];
@@ -784,10 +845,8 @@ static void solve_levels(Factorization &fz, int p, cudaStream_t st) {
         for (int si = pl.lvl_sstep_ptr[l]; si < pl.lvl_sstep_ptr[l + 1]; ++si) {
             const SolveStep &ss = pl.ssteps[si];
             const SolveDesc *sd = pl.d_sdescs.data() + ss.d0;
-            k_fwd_m<T><<<dim3(ss.nd, SPW / MCH), 256, vsm, st>>>(sd, pl.d_sn_zo.data(), M, Z, Zs, p);
-            MBL_LAUNCH_CHECK();
-            k_fwd_upd<T><<<(unsigned)ss.nrb, RB, vsm, st>>>(sd, ss.nd, pl.d_sn_fo.data(), pl.d_sn_zo.data(),
-                                                            pl.d_sn_f.data(), arena, Zs, Z, p);
+            k_fwd_step<T, PB><<<(unsigned)ss.nrb, 256, fsm, st>>>(sd, ss.nd, pl.d_sn_fo.data(), pl.d_sn_zo.data(),
+                                                                 pl.d_sn_f.data(), arena, Z, Zs, p);
             MBL_LAUNCH_CHECK();
         }
         k_fwd_finish<T><<<na, 256, 0, st>>>(items, pl.d_sn_zo.data(), pl.d_sn_nc.data(), pl.d_sn_start.data(), Dg, Zs,
@@ -804,17 +863,23 @@ static void solve_levels(Factorization &fz, int p, cudaStream_t st) {
         for (int si = pl.lvl_sstep_ptr[l + 1] - 1; si >= pl.lvl_sstep_ptr[l]; --si) {
             const SolveStep &ss = pl.ssteps[si];
             const SolveDesc *sd = pl.d_sdescs.data() + ss.d0;
-            k_bwd_part<T><<<dim3((unsigned)ss.nrb, SUBS), 256, psm, st>>>(sd, ss.nd, pl.d_sn_fo.data(),
-                                                                          pl.d_sn_zo.data(), pl.d_sn_f.data(), arena, Z,
-                                                                          p, P);
-            MBL_LAUNCH_CHECK();
-            k_bwd_reduce<T><<<dim3(ss.nd, SPW / MCH), 256, 0, st>>>(sd, pl.d_sn_zo.data(), P, Z, Zs, p);
-            MBL_LAUNCH_CHECK();
-            k_bwd_m<T><<<dim3(ss.nd, SPW / MCH), 256, vsm, st>>>(sd, pl.d_sn_zo.data(), M, Zs, Z, p);
+            k_bwd_step<T, PB><<<dim3((unsigned)ss.nrbb, SUBS), 256, bsm, st>>>(
+                sd, ss.nd, pl.d_sn_fo.data(), pl.d_sn_zo.data(), pl.d_sn_f.data(), pl.d_sn_nc.data(), arena, Z, Zs, P,
+                cnt + (size_t)ss.d0 * SUBS, p);
             MBL_LAUNCH_CHECK();
         }
-        k_bwd_finish<T><<<na, 256, 0, st>>>(items, pl.d_sn_zo.data(), pl.d_sn_nc.data(), pl.d_sn_start.data(), Z, y, p);
+        k_bwd_finish<T><<<na, 256, 0, st>>>(items, pl.d_sn_zo.data(), pl.d_sn_nc.data(), pl.d_sn_start.data(), Zs, y,
+                                            p);
         MBL_LAUNCH_CHECK();
+    }
+}
+
+template <class T>
+static void solve_levels_p(Factorization &fz, int p, cudaStream_t st) {
+    switch (rhs_pad(p)) {
+        case 8: solve_levels<T, 8>(fz, p, st); break;
+        case 16: solve_levels<T, 16>(fz, p, st); break;
+        default: solve_levels<T, 32>(fz, p, st); break;
     }
 }
 
@@ -843,7 +908,7 @@ static void solve_impl(Factorization &fz, const double *B, int64_t ldb, double *
         long long before = g_launches.load();
         MBL_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
         try {
-            solve_levels<T>(fz, p, st);
+            solve_levels_p<T>(fz, p, st);
         } catch (...) {
             cudaGraph_t dummy;
             cudaStreamEndCapture(st, &dummy);
@@ -878,7 +943,7 @@ void Factorization::ensure_solve_work(int p) {
     zsolved.alloc(ctx, (size_t)pl.zwork_elems * p * es);
     ywork.alloc(ctx, (size_t)pl.n * p * es);
     yfw.alloc(ctx, (size_t)pl.n * p * es);
-    pwork.alloc(ctx, (size_t)std::max<int64_t>(pl.max_sstep_nrb, 1) * SPW * 32 * es);
+    pwork.alloc(ctx, (size_t)std::max<int64_t>(pl.max_sstep_nrbb, 1) * SUBS * RBB * rhs_pad(p) * es);
     work_p = p;
 }
 
@@ -892,11 +957,14 @@ void Factorization::allocate() {
     wscr.alloc(ctx, (size_t)std::max<int64_t>(pl.wscratch_elems, 1) * es);
     cmax.alloc(ctx, (size_t)std::max<int64_t>(pl.max_desc_per_step, 1) * NB * sizeof(unsigned int));
     M.alloc(ctx, (size_t)std::max<int64_t>(pl.m_elems, 1) * es);
+    scnt.alloc(ctx, std::max<size_t>(pl.sdescs.size() * SUBS, 1));
+    MBL_CUDA(cudaMemset(scnt.data(), 0, std::max<size_t>(pl.sdescs.size() * SUBS, 1) * sizeof(unsigned int)));
 }
 
 void Factorization::release_scratch() {
     wscr.release();
     cmax.release();
+    M.release();  // folded into the fronts (G = [M; L21 M])
 }
 
 Factorization::~Factorization() {

@@ -14,6 +14,7 @@ struct Factorization {
     double tiny = 0.0;
     DVec<char> arena, D, wscr, cmax, M, zwork, zsolved, ywork, yfw, pwork;
     DVec<int32_t> piv;
+    DVec<unsigned int> scnt;  // per (solve panel, column chunk) arrival counters of the backward step
     // [0] perturbed pivots, [1] negative pivots, [2] wait time-outs, [3] max |l| (float bits, low
     // word), [4] min |d| (float bits, low word)
     DVec<unsigned long long> counters;

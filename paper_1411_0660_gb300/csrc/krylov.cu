@@ -79,6 +79,58 @@ __global__ void k_pack_sym(const double *T, int ldt, int mm, double *A) {
     A[t] = 0.5 * (T[(size_t)c * ldt + r] + T[(size_t)r * ldt + c]);
 }
 
+// One step of iterative refinement of a symmetric eigendecomposition (Ogita and Aishima, 2018):
+// with X the approximate eigenvectors (m x m), G = X^T X and S = X^T A X, the refined eigenvalues are
+// lambda_i = S_ii / G_ii and X <- X (I + E) with E_ii = r_ii / 2 and, for |lambda_i - lambda_j| > delta,
+// E_ij = (S_ij + lambda_j r_ij) / (lambda_j - lambda_i), where r = I - G; closer pairs (a cluster
+// at the current accuracy) take E_ij = r_ij / 2, which refines the cluster's subspace.  delta =
+// 2 (||S - diag(lambda)|| + ||A|| ||r||), Frobenius norms and ||A|| ~ max |lambda|.  One CTA.
+__global__ void __launch_bounds__(1024) k_oa_step(int m, const double *G, const double *S, double *lam, double *E) {
+    __shared__ double red[3][32];
+    __shared__ double s_delta;
+    const int t = threadIdx.x;
+    for (int i = t; i < m; i += blockDim.x) lam[i] = S[(size_t)i * m + i] / G[(size_t)i * m + i];
+    __syncthreads();
+    double off = 0.0, rr = 0.0, amax = 0.0;
+    for (int idx = t; idx < m * m; idx += blockDim.x) {
+        const int i = idx % m, j = idx / m;
+        const double r = (i == j ? 1.0 : 0.0) - G[idx];
+        const double sv = S[idx] - (i == j ? lam[i] : 0.0);
+        off += sv * sv;
+        rr += r * r;
+        if (i == j) amax = fmax(amax, fabs(lam[i]));
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        off += __shfl_xor_sync(0xffffffffu, off, o);
+        rr += __shfl_xor_sync(0xffffffffu, rr, o);
+        amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    }
+    if ((t & 31) == 0) {
+        red[0][t >> 5] = off;
+        red[1][t >> 5] = rr;
+        red[2][t >> 5] = amax;
+    }
+    __syncthreads();
+    if (t == 0) {
+        double a = 0.0, b = 0.0, c = 0.0;
+        for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) {
+            a += red[0][w];
+            b += red[1][w];
+            c = fmax(c, red[2][w]);
+        }
+        s_delta = 2.0 * (sqrt(a) + c * sqrt(b));
+    }
+    __syncthreads();
+    const double delta = s_delta;
+    for (int idx = t; idx < m * m; idx += blockDim.x) {
+        const int i = idx % m, j = idx / m;
+        const double r = (i == j ? 1.0 : 0.0) - G[idx];
+        double e = 0.5 * r;
+        if (i != j && fabs(lam[j] - lam[i]) > delta) e = (S[idx] + lam[j] * r) / (lam[j] - lam[i]);
+        E[idx] = e;
+    }
+}
+
 // res[i] = || T[mm:mm+p, 0:mm] S[:, i] ||
 __global__ void k_ritz_resid(const double *T, int ldt, int mm, int p, const double *S, double *res) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -243,6 +295,7 @@ KrylovSchur::KrylovSchur(Ctx *c, int64_t n_, int p_, int ncv_) : ctx(c), n(n_), 
     NS1.alloc(ctx, (size_t)ldv * ldv);
     NS2.alloc(ctx, (size_t)ldv * ldv);
     NS3.alloc(ctx, (size_t)ldv * ldv);
+    Ts.alloc(ctx, (size_t)ldv * ldv);
     Bk.alloc(ctx, (size_t)p * ldv);
     int64_t zero2[2] = {0, 0};
     MBL_CUDA(cudaMemcpy(eigOff.data(), zero2, sizeof(zero2), cudaMemcpyHostToDevice));
@@ -319,13 +372,38 @@ void KrylovSchur::ritz(cudaStream_t st, std::vector<double> &theta, std::vector<
     int mm = m - p;
     k_pack_sym<<<nblk((int64_t)mm * mm), 256, 0, st>>>(T.data(), ldv, mm, eigA.data());
     MBL_LAUNCH_CHECK();
+    k_pack_sym<<<nblk((int64_t)mm * mm), 256, 0, st>>>(T.data(), ldv, mm, Ts.data());
+    MBL_LAUNCH_CHECK();
     MBL_CUDA(cudaMemcpyAsync(eigM.data(), &mm, sizeof(int), cudaMemcpyHostToDevice, st));
+    const bool fp32 = ldv <= EIG_SMEM_MAX_M;
     {
         ProfScope ps(ctx, "syev_krylov", (double)mm, st);
-        // FP32 is enough here: the kept vectors are re-orthonormalized and T re-projected in FP64 at
-        // the restart, and convergence is decided by the FP64 Rayleigh-Ritz on H
+        // FP32 reduction and QL, then two steps of FP64 refinement of the whole decomposition: a
+        // thick restart keeps an invariant subspace of T, so the kept vectors must be accurate to
+        // FP64 rounding (an FP32-accurate subspace would cap the attainable residuals near 1e-7)
         syev_batched(1, eigM.data(), eigOff.data(), eigOff.data(), eigA.data(), eigW.data(), 1, nullptr, ldv,
-                     eigWork.data(), eigInfo.data(), st, ldv <= EIG_SMEM_MAX_M);
+                     eigWork.data(), eigInfo.data(), st, fp32);
+        int info = 0;
+        MBL_CUDA(cudaMemcpyAsync(&info, eigInfo.data(), sizeof(int), cudaMemcpyDeviceToHost, st));
+        MBL_CUDA(cudaStreamSynchronize(st));
+        if (fp32 && info != 0) {  // QL did not converge in FP32: redo in FP64
+            k_pack_sym<<<nblk((int64_t)mm * mm), 256, 0, st>>>(T.data(), ldv, mm, eigA.data());
+            MBL_LAUNCH_CHECK();
+            syev_batched(1, eigM.data(), eigOff.data(), eigOff.data(), eigA.data(), eigW.data(), 1, nullptr, ldv,
+                         eigWork.data(), eigInfo.data(), st, false);
+        }
+        if (fp32) {
+            double *X = eigA.data(), *G = NS1.data(), *Q = NS2.data(), *Sx = NS3.data();
+            for (int it = 0; it < 2; ++it) {
+                gemm_small(true, false, mm, mm, mm, 1.0, X, mm, X, mm, 0.0, G, mm, st);
+                gemm_small(false, false, mm, mm, mm, 1.0, Ts.data(), mm, X, mm, 0.0, Q, mm, st);
+                gemm_small(true, false, mm, mm, mm, 1.0, X, mm, Q, mm, 0.0, Sx, mm, st);
+                k_oa_step<<<1, 1024, 0, st>>>(mm, G, Sx, eigW.data(), Q);  // E into Q
+                MBL_LAUNCH_CHECK();
+                MBL_CUDA(cudaMemcpyAsync(G, X, (size_t)mm * mm * sizeof(double), cudaMemcpyDeviceToDevice, st));
+                gemm_small(false, false, mm, mm, mm, 1.0, G, mm, Q, mm, 1.0, X, mm, st);  // X += X E
+            }
+        }
     }
     k_ritz_resid<<<nblk(mm, 128), 128, 0, st>>>(T.data(), ldv, mm, p, eigA.data(), res.data());
     MBL_LAUNCH_CHECK();

@@ -38,20 +38,27 @@ struct PanelStep {
     int64_t wsize;   // W21 scratch elements used by this step
 };
 
-// One solve panel: columns [k0, k0 + w) of a front's fully-summed block (w <= SPW).  M (w x w,
-// column-major) is the composite of the factor panels' pivot permutations and unit-lower
-// eliminations restricted to the panel: forward z_panel <- M z_panel, backward x_panel <- M^T z.
+constexpr int RBF = 32;  // rows per CTA of a forward solve step
+constexpr int RBB = 64;  // rows (and columns) per tile of a backward solve step
+
+// One solve panel: columns [k0, k0 + w) of a front's fully-summed block (w <= SPW).  M (w x w) is
+// the composite of the factor panels' pivot permutations and unit-lower eliminations restricted
+// to the panel.  Once the factorization is done the panel's column block [k0, f) x [k0, k0 + w)
+// holds G = [M; L21 M], so that the forward step is z_panel <- M z_panel, z_below -= (L21 M) z_panel
+// (with z_panel read before the update) and the backward step is x_panel <- G^T [y_panel; -x_below].
 struct SolveDesc {
     int32_t front, k0, w, m2;        // m2 = f - k0 - w rows below
-    int64_t off;                     // prefix of row blocks (at least one per descriptor)
-    int64_t moff;                    // offset (elements) of M
+    int64_t off;                     // prefix of forward row blocks (RBF rows of [k0, f)) in the step
+    int64_t offb;                    // prefix of backward row tiles (RBB rows of [k0, f)) in the step
+    int64_t moff;                    // offset (elements) of M while it is built
     int32_t fdesc[SUBS];             // factor descriptors of the sub-panels (-1 if absent)
 };
 
 struct SolveStep {
     int32_t level;
     int32_t d0, nd;
-    int64_t nrb;                     // row blocks in this step (>= nd)
+    int64_t nrb;                     // forward row blocks in this step
+    int64_t nrbb;                    // backward row tiles in this step
 };
 
 struct AsmItem {     // assembly work item: columns [c0, c0 + ACOLS) of a front
@@ -80,7 +87,7 @@ struct Plan {
     std::vector<SolveStep> ssteps;
     std::vector<int32_t> lvl_sstep_ptr;       // solve steps by level
     std::vector<SolveDesc> sdescs;
-    int64_t m_elems = 0, max_sstep_nrb = 0;
+    int64_t m_elems = 0, max_sstep_nrbb = 0;
     int64_t arena_elems = 0, zwork_elems = 0, wscratch_elems = 0, max_desc_per_step = 0;
     int64_t max_step_n2 = 0;
     int64_t nnz_l = 0;
