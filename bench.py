@@ -28,6 +28,8 @@ L = 18
 NEV = 50
 HS = [0.5, 1.0, 2.0, 3.0, 4.0, 5.0]
 EPS = [0.1, 0.5, 0.9]
+PROF_KEYS = ("factor_fp32", "schur_fp32", "schur_tc", "trisolve_fp32", "refine_spmv", "orth", "syev_krylov",
+             "syev_rr", "extremal_bounds", "op_apply", "ks_restart", "ritz_h", "observables", "sector_build")
 METRIC = "eigenpairs/s near eps (res<=1e-10||H||), L=18, mixed vs FP64; p50/p99 latency"
 
 
@@ -154,17 +156,57 @@ def cpu_baseline_sample(seconds: float = 20.0):
 
 
 # --------------------------------------------------------------------------------------------
+def run_case(args):
+    """A single-operation case for profilers: one L-site sector (h = 3, seed 5), one factorization of
+    H - sigma at eps = 0.5, then --reps unrefined block solves with 8 right-hand sides."""
+    import numpy as np
+
+    import paper_1411_0660_gb300 as g
+
+    ctx = g.Context(0)
+    sec = g.build_sector(ctx, args.L, 3.0, 5)
+    lo, hi = g.extremal_bounds(sec)
+    prec = g.MBL_PREC_FP64 if args.precision == "fp64" else g.MBL_PREC_FP32
+    f = g.factor(sec, lo + 0.5 * (hi - lo), precision=prec, tensor_cores=args.tensor_cores)
+    B = np.random.default_rng(0).standard_normal((sec.dim, 8))
+    import torch
+
+    nvtx = getattr(torch.cuda, "nvtx", None)
+    t0 = time.perf_counter()
+    if nvtx is not None:
+        nvtx.range_push("solve")
+    for _ in range(args.reps if args.case == "solve" else 0):
+        f.solve(B, refine=False)
+    if nvtx is not None:
+        nvtx.range_pop()
+    dt = time.perf_counter() - t0
+    print(json.dumps({"case": args.case, "L": args.L, "precision": args.precision, "reps": args.reps,
+                      "solve_s_per_rep": dt / max(1, args.reps), "factor": f.stats()}))
+    f.close()
+    sec.close()
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--case", choices=["factor", "solve"], default=None,
+                    help="run one factorization (and --reps solves) instead of the benchmark")
+    ap.add_argument("--L", type=int, default=18)
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--tensor-cores", type=int, default=0)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--batch", type=int, default=3)
-    ap.add_argument("--e2e-jobs", type=int, default=2)
+    ap.add_argument("--batch", type=int, default=6)
+    ap.add_argument("--e2e-stride", type=int, default=3)
     ap.add_argument("--impl", default="gb300")
-    ap.add_argument("--fp64-jobs", type=int, default=2)
+    ap.add_argument("--fp64-stride", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
+    if args.case:
+        return run_case(args)
     if args.impl == "reference":
         return run_reference(args)
 
@@ -219,25 +261,34 @@ def main():
         os.path.join(ROOT, "gpurun_out")) else "/tmp/clocks_bench.csv")
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     pairs, lat = 0, []
+    timed_jobs = [j for s in range(args.steps) for j in jobs_for_step(args.warmup + s, args.batch, rank, world)]
+    job_ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(timed_jobs) + 1)]
+    job_pairs, job_stats = [], []
+    ev_mixed = torch.empty((len(timed_jobs), NEV), dtype=torch.float64, device="cuda")
     nvtx = getattr(torch.cuda, "nvtx", None)
     with clocks:
         torch.cuda.synchronize()
         if nvtx is not None:
             nvtx.range_push("timed")
         e0.record()
-        for s in range(args.steps):
-            for (h, seed, eps) in jobs_for_step(args.warmup + s, args.batch, rank, world):
-                t0 = time.perf_counter()
-                nc, st = device_job(h, seed, eps, g.MBL_PREC_FP32)
-                lat.append(time.perf_counter() - t0)
-                pairs += nc
+        for i, (h, seed, eps) in enumerate(timed_jobs):
+            job_ev[i].record()
+            t0 = time.perf_counter()
+            nc, st = device_job(h, seed, eps, g.MBL_PREC_FP32)
+            lat.append(time.perf_counter() - t0)
+            pairs += nc
+            job_pairs.append(nc)
+            job_stats.append(st)
+            ev_mixed[i].copy_(d_ev)
+        job_ev[-1].record()
         e1.record()
         torch.cuda.synchronize()
         if nvtx is not None:
             nvtx.range_pop()
     ms = e0.elapsed_time(e1)
+    job_ms = [job_ev[i].elapsed_time(job_ev[i + 1]) for i in range(len(timed_jobs))]
     launches = g.launch_count() - l0
-    prof = {k: ctx.profile(k) for k in ("factor_fp32", "schur_fp32", "trisolve_fp32", "refine_spmv", "orth")}
+    prof = {k: ctx.profile(k) for k in PROF_KEYS}
     ctx.set_profiling(False)
     tmax = ms
     if dist:
@@ -248,27 +299,45 @@ def main():
         tmax, pairs = float(t[0]), int(tt[0])
     value = pairs / (tmax / 1e3)
 
-    # ---- FP64 fronts on a few jobs (the plain FP64 GPU path) ----
+    # ---- the plain FP64 GPU path on a subset of the same jobs (every third one: all h and eps) ----
+    sub = list(range(0, len(timed_jobs), max(1, args.fp64_stride)))
     fp64 = None
-    if args.fp64_jobs > 0:
+    if args.fp64_stride > 0 and sub:
         ctx.set_profiling(True)
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
         p64 = 0
-        for (h, seed, eps) in jobs_for_step(args.warmup, args.fp64_jobs, rank, world):
+        ev64 = {}
+        for i in sub:
+            h, seed, eps = timed_jobs[i]
             nc, st = device_job(h, seed, eps, g.MBL_PREC_FP64)
             p64 += nc
+            ev64[i] = d_ev.clone()
         b.record()
         torch.cuda.synchronize()
         t64 = a.elapsed_time(b)
         f64 = ctx.profile("factor_fp64")
         ctx.set_profiling(False)
-        fp64 = {"value": p64 / (t64 / 1e3), "unit": "eigenpairs/s", "jobs": args.fp64_jobs,
-                "ms_per_job": t64 / args.fp64_jobs, "factor_ms_per_job": f64["ms"] / max(1, f64["launches"])}
+        t_mixed = sum(job_ms[i] for i in sub)
+        p_mixed = sum(job_pairs[i] for i in sub)
+        fp64 = {"value": p64 / (t64 / 1e3), "unit": "eigenpairs/s", "jobs": len(sub),
+                "ms_per_job": t64 / len(sub), "factor_ms_per_job": f64["ms"] / max(1, f64["launches"]),
+                "mixed_same_jobs": {"value": p_mixed / (t_mixed / 1e3), "ms_per_job": t_mixed / len(sub)},
+                "mixed_over_fp64": (p_mixed / t_mixed) / max(p64 / t64, 1e-30)}
+        torch.cuda.synchronize()
+        # per result: mixed-precision eigenvalues against the FP64 path's, relative to ||H|| ~ |E| scale
+        for i in sub:
+            h, seed, eps = timed_jobs[i]
+            sec = g.build_sector(ctx, L, h, seed)
+            lo, hi = g.extremal_bounds(sec)
+            sec.close()
+            d = (ev_mixed[i] - ev64[i]).abs().max().item()
+            job_stats[i]["max_dev_vs_fp64"] = d / max(abs(lo), abs(hi))
 
     # ---- end to end through the host API: host fields in, host eigenpairs and observables out ----
-    e2e_jobs = jobs_for_step(args.warmup, max(1, args.e2e_jobs), rank, world)
+    e2e_idx = list(range(0, len(timed_jobs), max(1, args.e2e_stride)))
+    e2e_jobs = [timed_jobs[i] for i in e2e_idx]
     host_fields = []
     for (h, seed, eps) in e2e_jobs:  # the jobs' inputs (disorder realizations), prepared untimed
         sec0 = g.build_sector(ctx, L, h, seed)
@@ -289,32 +358,37 @@ def main():
     e2e_s = time.perf_counter() - t_e2e0
     ne = len(e2e_jobs)
     e2e = {"value": e_pairs / e2e_s, "unit": "eigenpairs/s", "h2d_bytes_per_step": h2d * args.batch // ne,
-           "d2h_bytes_per_step": d2h * args.batch // ne, "jobs": ne}
+           "d2h_bytes_per_step": d2h * args.batch // ne, "jobs": ne,
+           "device_same_jobs": sum(job_pairs[i] for i in e2e_idx) / (sum(job_ms[i] for i in e2e_idx) / 1e3)}
 
     # ---- roofline of the dominant kernel class ----
     peaks = measured_peaks()
-    dom = max(("schur_fp32", "trisolve_fp32", "refine_spmv", "orth"), key=lambda k: prof[k]["ms"])
+    dom = max(("schur_fp32", "schur_tc", "trisolve_fp32", "refine_spmv", "orth"), key=lambda k: prof[k]["ms"])
     P = prof[dom]
     per_launch_ms = P["ms"] / max(1, P["launches"])
     per_launch_work = P["work"] / max(1, P["launches"])
+    clk = 2070.0
     if dom in ("trisolve_fp32", "refine_spmv"):
         achieved = per_launch_work / (per_launch_ms / 1e3) / 1e9
         peak = peaks["hbm_gbs"] if peaks else 6800.0
-        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "kernel": dom, "peak_source": "measured" if peaks else "fallback"}
+        roof = {"bound": "hbm", "unit": "GB/s", "peak_source": "measured copy" if peaks else "fallback"}
+    elif dom == "schur_tc":
+        # 3xTF32 on tcgen05: algorithmic flops counted once; TF32 dense peak = measured BF16 x 1.1/2.25
+        achieved = per_launch_work / (per_launch_ms / 1e3) / 1e12
+        bf = (peaks or {}).get("bf16_tflops", 1900.0)
+        peak = bf * 1.1 / 2.25
+        roof = {"bound": "tensor", "unit": "TFLOP/s",
+                "peak_source": "measured BF16 x nominal TF32/BF16 ratio (1.1/2.25)" if peaks else "fallback"}
     elif dom == "schur_fp32":
         achieved = per_launch_work / (per_launch_ms / 1e3) / 1e12
-        # SIMT FP32 path: the bound is the FP32 CUDA-core rate (152 SMs x 128 lanes x 2 x clock)
-        clk = (peaks or {}).get("sm_max_mhz", 2070.0)
         peak = 152 * 128 * 2 * clk * 1e6 / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": dom, "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x max clock"}
+        roof = {"bound": "alu", "unit": "TFLOP/s", "peak_source": "152 SM x 128 FP32 lanes x 2 x 2070 MHz"}
     else:
         achieved = per_launch_work / (per_launch_ms / 1e3) / 1e12
-        clk = (peaks or {}).get("sm_max_mhz", 2070.0)
-        peak = 1.25
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": dom, "peak_source": "nominal FP64 1.25 TFLOP/s"}
+        peak = 152 * 2 * 2 * clk * 1e6 / 1e12
+        roof = {"bound": "alu", "unit": "TFLOP/s", "peak_source": "152 SM x 2 FP64 FMA/clk x 2 x 2070 MHz"}
+    roof.update({"achieved": achieved, "peak": peak, "frac": achieved / peak, "traffic": None, "kernel": dom,
+                 "launch_ms": per_launch_ms, "work_per_launch": per_launch_work})
 
     if rank == 0:
         lat_ms = sorted(1e3 * x for x in lat)
@@ -331,6 +405,12 @@ def main():
             "latency_ms": {"p50": lat_ms[len(lat_ms) // 2], "p99": lat_ms[min(len(lat_ms) - 1,
                                                                               int(0.99 * len(lat_ms)))]},
             "fp64_path": fp64,
+            "per_job": [{"h": j[0], "seed": j[1], "eps": j[2], "nconv": job_pairs[i], "ms": round(job_ms[i], 1),
+                         "max_resid_rel": job_stats[i]["max_resid"], "restarts": job_stats[i]["restarts"],
+                         "solves": job_stats[i]["solves"], "fp64_fallback": job_stats[i]["fp64_fallback"],
+                         **({"max_dev_vs_fp64": job_stats[i]["max_dev_vs_fp64"]}
+                            if "max_dev_vs_fp64" in job_stats[i] else {})}
+                        for i, j in enumerate(timed_jobs)],
             "roofline": roof,
             "profile": prof,
             "e2e": e2e,

@@ -186,6 +186,60 @@ int mbl_observables_dev(mbl_ctx *ctx, int L, int nev, const double *d_evals,
                         const double *d_evecs, double *d_r, double *d_r_mean, double *d_s1p,
                         double *d_se, void *stream);
 
+/* ---- Serving: request loop with continuous batching and HBM admission -------------------
+ * Not in the paper, which diagonalizes one realization per batch job; this is the serving
+ * pattern for streams of (L, h, seed, eps, nev) requests of mixed L.
+ *
+ * mbl_server_start creates `slots` worker threads on the context's device, each with its own
+ * stream and scratch, sharing the context's symbolic analyses.  Requests start in arrival order as
+ * workers free up; before the solve a worker reserves the job's estimated peak HBM (from the
+ * symbolic plan of its L) against `budget_bytes` (0 = 85% of the free device memory, capped by the
+ * context budget) and waits while it does not fit, so jobs run side by side as memory allows.  A
+ * job runs the same steps as mbl_build_sector + mbl_solve_near + mbl_observables and gives the
+ * same result as those calls alone.  Errors: MBL_ERR_INVALID (bad slots, server already running). */
+typedef struct mbl_request {
+    int L;            /* even, 2..22 */
+    double h;         /* disorder strength, fields from the seeded stream (as mbl_build_sector) */
+    uint64_t seed;
+    double eps;       /* target energy density in [0, 1] */
+    int nev;
+    int precision;    /* MBL_PREC_FP32 (mixed) or MBL_PREC_FP64 */
+    int want_vectors; /* keep the eigenvectors for mbl_poll */
+} mbl_request;
+
+/* Filled by mbl_poll / mbl_wait.  The array fields are caller-owned outputs set before the call
+ * (NULL = not wanted): evals[nev], resid[nev], r[nev-2], s1p[nev], se[nev], evecs[dim*nev]
+ * (column-major; only if the request had want_vectors).  Times are host milliseconds since
+ * mbl_server_start: submission, admission (HBM reserved, solve starts), completion. */
+typedef struct mbl_result {
+    int status;       /* MBL_OK, MBL_ERR_NOT_CONVERGED (partial), or the job's error */
+    int nconv, nev, L;
+    int64_t dim;
+    double sigma, r_mean;
+    double t_submit_ms, t_admit_ms, t_end_ms;
+    size_t reserved_bytes;
+    double *evals, *resid, *r, *s1p, *se, *evecs;
+} mbl_result;
+
+typedef struct mbl_server_stats {
+    int64_t submitted, completed, failed;
+    int running, queued, slots;
+    size_t budget_bytes, reserved_bytes, peak_reserved_bytes;
+} mbl_server_stats;
+
+int mbl_server_start(mbl_ctx *ctx, int slots, size_t budget_bytes);
+/* Queue a request; *ticket identifies it.  MBL_ERR_INVALID for bad arguments or no server. */
+int mbl_submit(mbl_ctx *ctx, const mbl_request *req, uint64_t *ticket);
+/* Non-blocking: MBL_PENDING while queued or running; otherwise fills *out, returns the job's
+ * status and forgets the ticket (a second poll gives MBL_ERR_INVALID). */
+int mbl_poll(mbl_ctx *ctx, uint64_t ticket, mbl_result *out);
+/* Blocking variant; timeout_s <= 0 waits without limit, else MBL_PENDING after timeout_s. */
+int mbl_wait(mbl_ctx *ctx, uint64_t ticket, double timeout_s, mbl_result *out);
+int mbl_server_stats_get(mbl_ctx *ctx, mbl_server_stats *out);
+/* Stop the workers: running jobs finish, queued ones are dropped with their results.  Called by
+ * mbl_ctx_destroy.  Must not overlap mbl_wait/mbl_poll on the same context. */
+int mbl_server_stop(mbl_ctx *ctx);
+
 #ifdef __cplusplus
 }
 #endif

@@ -23,7 +23,7 @@ from ._capi import MBL_PREC_FP32, MBL_PREC_FP64, FactorStats, Opts, SolveStats
 
 __all__ = ["Context", "Sector", "Factorization", "MblError", "build_sector", "build_sector_fields",
            "extremal_bounds", "factor", "solve_near", "solve_near_dev", "observables", "observables_dev",
-           "default_opts", "launch_count", "MBL_PREC_FP32", "MBL_PREC_FP64"]
+           "default_opts", "launch_count", "Server", "ServedResult", "MBL_PREC_FP32", "MBL_PREC_FP64"]
 
 
 class MblError(RuntimeError):
@@ -263,3 +263,90 @@ def observables_dev(ctx: Context, L: int, nev: int, d_evals, d_evecs, d_r, d_rme
                                       ctypes.c_void_p(d_evecs.data_ptr()), ctypes.c_void_p(d_r.data_ptr()),
                                       ctypes.c_void_p(d_rmean.data_ptr()), ctypes.c_void_p(d_s1p.data_ptr()),
                                       ctypes.c_void_p(d_se.data_ptr()), s), ctx.handle)
+
+
+# ------------------------------------------------------------------------------------------
+# Serving (continuous batching with HBM admission): a thin face of mbl_server_* / mbl_submit /
+# mbl_poll / mbl_wait.
+# ------------------------------------------------------------------------------------------
+@dataclass
+class ServedResult:
+    status: int
+    nconv: int
+    L: int
+    dim: int
+    sigma: float
+    evals: np.ndarray
+    resid: np.ndarray
+    r: np.ndarray
+    r_mean: float
+    s1p: np.ndarray
+    se: np.ndarray
+    evecs: np.ndarray | None
+    t_submit_ms: float
+    t_admit_ms: float
+    t_end_ms: float
+    reserved_bytes: int
+
+
+def _dim_of(L: int) -> int:
+    n = 1
+    for i in range(1, L // 2 + 1):
+        n = n * (L // 2 + i) // i
+    return n
+
+
+class Server:
+    """Worker threads of a context serving (L, h, seed, eps, nev) requests as memory allows."""
+
+    def __init__(self, ctx: Context, slots: int = 4, hbm_budget_bytes: int = 0):
+        self.ctx = ctx
+        self._req = {}
+        _check(_lib().mbl_server_start(ctx.handle, slots, hbm_budget_bytes), ctx.handle)
+
+    def submit(self, L: int, h: float, seed: int, eps: float, nev: int, precision: int = MBL_PREC_FP32,
+               want_vectors: bool = False) -> int:
+        q = _capi.Request(L, float(h), seed, float(eps), nev, precision, 1 if want_vectors else 0)
+        t = ctypes.c_uint64()
+        _check(_lib().mbl_submit(self.ctx.handle, ctypes.byref(q), ctypes.byref(t)), self.ctx.handle)
+        self._req[t.value] = (L, nev, want_vectors)
+        return t.value
+
+    def _collect(self, ticket: int, timeout_s: float | None):
+        L, nev, vec = self._req[ticket]
+        n = _dim_of(L)
+        ev, rs, r, s1, se = (np.zeros(nev), np.zeros(nev), np.zeros(max(nev - 2, 1)), np.zeros(nev),
+                             np.zeros(nev))
+        V = np.zeros((n, nev), order="F") if vec else None
+        out = _capi.Result()
+        out.evals, out.resid, out.r, out.s1p, out.se = (_ptr(ev), _ptr(rs), _ptr(r), _ptr(s1), _ptr(se))
+        out.evecs = _ptr(V) if vec else None
+        if timeout_s is None:
+            rc = _lib().mbl_poll(self.ctx.handle, ticket, ctypes.byref(out))
+        else:
+            rc = _lib().mbl_wait(self.ctx.handle, ticket, float(timeout_s), ctypes.byref(out))
+        if rc == _capi.MBL_PENDING:
+            return None
+        del self._req[ticket]
+        if rc not in (_capi.MBL_OK, _capi.MBL_ERR_NOT_CONVERGED):
+            _check(rc, self.ctx.handle)
+        return ServedResult(rc, out.nconv, out.L, out.dim, out.sigma, ev, rs, r[: max(nev - 2, 0)], out.r_mean, s1,
+                            se, V, out.t_submit_ms, out.t_admit_ms, out.t_end_ms, out.reserved_bytes)
+
+    def poll(self, ticket: int):
+        """The result if finished, else None (non-blocking)."""
+        return self._collect(ticket, None)
+
+    def wait(self, ticket: int, timeout_s: float = 0.0):
+        """Block until finished (timeout_s <= 0: no limit); None if the timeout expired."""
+        return self._collect(ticket, timeout_s)
+
+    def stats(self) -> dict:
+        st = _capi.ServerStats()
+        _check(_lib().mbl_server_stats_get(self.ctx.handle, ctypes.byref(st)), self.ctx.handle)
+        return {f: getattr(st, f) for f, _ in _capi.ServerStats._fields_}
+
+    def stop(self):
+        if self.ctx.handle:
+            _lib().mbl_server_stop(self.ctx.handle)
+

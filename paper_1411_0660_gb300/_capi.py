@@ -40,6 +40,24 @@ class SolveStats(ctypes.Structure):
                 ("krylov_dim", c_int), ("max_resid", c_double), ("ms_total", c_double), ("ms_factor", c_double)]
 
 
+class Request(ctypes.Structure):
+    _fields_ = [("L", c_int), ("h", c_double), ("seed", c_uint64), ("eps", c_double), ("nev", c_int),
+                ("precision", c_int), ("want_vectors", c_int)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("status", c_int), ("nconv", c_int), ("nev", c_int), ("L", c_int), ("dim", c_int64),
+                ("sigma", c_double), ("r_mean", c_double), ("t_submit_ms", c_double), ("t_admit_ms", c_double),
+                ("t_end_ms", c_double), ("reserved_bytes", c_size_t), ("evals", c_void_p), ("resid", c_void_p),
+                ("r", c_void_p), ("s1p", c_void_p), ("se", c_void_p), ("evecs", c_void_p)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", c_int64), ("completed", c_int64), ("failed", c_int64), ("running", c_int),
+                ("queued", c_int), ("slots", c_int), ("budget_bytes", c_size_t), ("reserved_bytes", c_size_t),
+                ("peak_reserved_bytes", c_size_t)]
+
+
 # (name, restype, argtypes); every entry point of include/mblsi.h
 SIGNATURES = [
     ("mbl_opts_default", None, [P(Opts)]),
@@ -74,6 +92,12 @@ SIGNATURES = [
                                 c_void_p]),
     ("mbl_observables_dev", c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                     c_void_p, c_void_p]),
+    ("mbl_server_start", c_int, [c_void_p, c_int, c_size_t]),
+    ("mbl_submit", c_int, [c_void_p, P(Request), P(c_uint64)]),
+    ("mbl_poll", c_int, [c_void_p, c_uint64, P(Result)]),
+    ("mbl_wait", c_int, [c_void_p, c_uint64, c_double, P(Result)]),
+    ("mbl_server_stats_get", c_int, [c_void_p, P(ServerStats)]),
+    ("mbl_server_stop", c_int, [c_void_p]),
 ]
 
 _lib = None

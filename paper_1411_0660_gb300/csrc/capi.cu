@@ -137,18 +137,21 @@ void DevMem::release() {
 
 std::shared_ptr<Plan> get_plan(mbl_sector *sec) {
     Ctx *ctx = sec->ctx;
-    auto it = ctx->plans.find(sec->L);
-    if (it != ctx->plans.end()) return it->second;
+    std::shared_ptr<PlanCache> cache = ctx->plans;
+    std::lock_guard<std::mutex> lk(cache->mu);
+    auto it = cache->m.find(sec->L);
+    if (it != cache->m.end()) return it->second;
     int64_t n = sec->n;
     std::vector<uint32_t> st(n);
     std::vector<int64_t> rp(n + 1);
     std::vector<int32_t> col(sec->nnz);
+    MBL_CUDA(cudaStreamSynchronize(ctx->stream));
     MBL_CUDA(cudaMemcpy(st.data(), sec->states.data(), n * sizeof(uint32_t), cudaMemcpyDeviceToHost));
     MBL_CUDA(cudaMemcpy(rp.data(), sec->rowptr.data(), (n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost));
     MBL_CUDA(cudaMemcpy(col.data(), sec->col.data(), sec->nnz * sizeof(int32_t), cudaMemcpyDeviceToHost));
     auto P = build_plan(sec->L, st, rp, col);
     upload_plan(ctx, *P);
-    ctx->plans[sec->L] = P;
+    cache->m[sec->L] = P;
     return P;
 }
 
@@ -305,11 +308,16 @@ int mbl_ctx_profile_get(mbl_ctx *ctx, const char *name, int64_t *launches, doubl
 
 void mbl_ctx_destroy(mbl_ctx *ctx) {
     if (!ctx || !ctx_alive(ctx)) return;
+    server_shutdown(ctx);
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
     try { ctx->resolve_profile(); } catch (...) {}
     for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
-    ctx->plans.clear();
+    {
+        std::lock_guard<std::mutex> lk(ctx->plans->mu);
+        if (ctx->plans.use_count() == 1) ctx->plans->m.clear();
+    }
+    ctx->plans.reset();
     ctx->ent.clear();
     cudaStreamSynchronize(ctx->stream);
     cudaStreamDestroy(ctx->stream);
@@ -343,6 +351,7 @@ static int build_common(mbl_ctx *ctx, int L, const double *h_host, double J, boo
     int64_t n = 1;
     for (int i = 1; i <= L / 2; ++i) n = n * (L / 2 + i) / i;
     s->n = n;
+    ProfScope ps(ctx, "sector_build", (double)n, ctx->stream);
     s->d_hfield.alloc(ctx, 32);
     if (from_seed) {
         launch_fields(L, h, seed, s->d_hfield.data(), ctx->stream);

@@ -85,7 +85,7 @@ void dense_tn(int64_t n, const double *V, int ldv, int c0, int k, const double *
     if (rows_per < 1) rows_per = 1;
     int nch = (int)((n + rows_per - 1) / rows_per);
     size_t smem = (size_t)TN_ROWS * (k + p) * sizeof(double);
-    static bool attr = false;
+    static std::atomic<bool> attr{false};  // per process: one device
     if (!attr) {
         MBL_CUDA(cudaFuncSetAttribute(k_tn_partial, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
         attr = true;
@@ -500,7 +500,7 @@ void syev_batched(int batch, const int *d_m, const int64_t *d_aoff, const int64_
                   bool fp32) {
     (void)d_sel;
     if (batch <= 0) return;
-    static bool attr = false;
+    static std::atomic<bool> attr{false};  // per process: one device
     if (!attr) {
         MBL_CUDA(cudaFuncSetAttribute(k_syev<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       EIG_SMEM_MAX_M * EIG_SMEM_MAX_M * sizeof(double)));

@@ -441,33 +441,6 @@ __global__ void __launch_bounds__(256) k_build_m(const SolveDesc *sdescs, const 
     }
 }
 
-template <class T>
-__global__ void __launch_bounds__(256) k_fwd_gather(const AsmItem *items, const int64_t *zo, const int32_t *fsz,
-                                                    const int32_t *nc, const int32_t *sn_start, const int32_t *ch_ptr,
-                                                    const int32_t *ch_list, const int64_t *rel_off,
-                                                    const int32_t *relind, const T *y, T *Z, int p) {
-    AsmItem it = items[blockIdx.x];
-    const int s = it.front, f = fsz[s], r0 = it.c0, r1 = min(f, r0 + ACOLS), ncs = nc[s];
-    T *z = Z + zo[s] * p;
-    for (int idx = threadIdx.x; idx < (r1 - r0) * p; idx += blockDim.x) {
-        int r = r0 + idx / p, q = idx % p;
-        z[(int64_t)r * p + q] = (r < ncs) ? y[((int64_t)sn_start[s] + r) * p + q] : T(0);
-    }
-    __syncthreads();
-    for (int qq = ch_ptr[s]; qq < ch_ptr[s + 1]; ++qq) {
-        int ch = ch_list[qq];
-        int ncc = nc[ch], uc = fsz[ch] - ncc;
-        const int32_t *rel = relind + rel_off[ch];
-        int alo = lower_bound_i32(rel, uc, r0), ahi = lower_bound_i32(rel, uc, r1);
-        const T *zc = Z + zo[ch] * p;
-        for (int idx = threadIdx.x; idx < (ahi - alo) * p; idx += blockDim.x) {
-            int a = alo + idx / p, q = idx % p;
-            z[(int64_t)rel[a] * p + q] += zc[(int64_t)(ncc + a) * p + q];
-        }
-        __syncthreads();
-    }
-}
-
 // G = [M; L21 M] in place of a solve panel's column block [k0, f) x [k0, k0 + w): RBB rows per
 // CTA (grid: the step's backward row tiles); each CTA owns its rows, so the update is in place.
 template <class T>
@@ -539,28 +512,35 @@ __global__ void __launch_bounds__(256) k_fwd_step(const SolveDesc *sdescs, int n
                                                   int p) {
     extern __shared__ __align__(16) unsigned char smraw[];
     T *zp = reinterpret_cast<T *>(smraw);  // SPW x PB; afterwards the 8 x PB x RBF partials
+    pdl_trigger();
     const int di = find_sdesc(sdescs, nd, blockIdx.x);
     const SolveDesc d = sdescs[di];
     const int s = d.front, f = fsz[s], k0 = d.k0, w = d.w;
     const int r0 = (int)(blockIdx.x - d.off) * RBF;  // relative to k0
     const int nr = min(RBF, w + d.m2 - r0);
     const int64_t zb = zo[s] + k0;
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    const int c0 = wp * 32, c1 = min(w, c0 + 32);
+    const bool active = lane < nr && c0 < c1, full = c1 - c0 == 32;
+    const T *g = arena + fo[s] + (int64_t)k0 * f + k0 + r0 + lane;
+    // the factor does not change during a solve: stream this thread's row of G before waiting for
+    // the previous step
+    T lv[32];
+    if (active && full) {
+#pragma unroll
+        for (int c = 0; c < 32; ++c) lv[c] = g[(int64_t)(c0 + c) * f];
+    }
+    pdl_wait();
     for (int idx = threadIdx.x; idx < w * PB; idx += blockDim.x) {
         int c = idx / PB, q = idx % PB;
         zp[idx] = q < p ? Z[(zb + c) * p + q] : T(0);
     }
     __syncthreads();
-    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
     T acc[PB];
 #pragma unroll
     for (int q = 0; q < PB; ++q) acc[q] = T(0);
-    const int c0 = wp * 32, c1 = min(w, c0 + 32);
-    if (lane < nr && c0 < c1) {
-        const T *g = arena + fo[s] + (int64_t)k0 * f + k0 + r0 + lane;
-        if (c1 - c0 == 32) {
-            T lv[32];
-#pragma unroll
-            for (int c = 0; c < 32; ++c) lv[c] = g[(int64_t)(c0 + c) * f];
+    if (active) {
+        if (full) {
 #pragma unroll
             for (int c = 0; c < 32; ++c)
 #pragma unroll
@@ -590,12 +570,37 @@ __global__ void __launch_bounds__(256) k_fwd_step(const SolveDesc *sdescs, int n
     }
 }
 
+// Forward gather of one level from the row lists: Z[dst] = y[own] (or 0) + the children's
+// contributions in tree order; one thread per (row, right-hand side).
+template <class T>
+__global__ void k_fwd_gather_rows(int64_t nrows, const int64_t *dst, const int64_t *own, const int64_t *cptr,
+                                  const int64_t *src, const T *y, T *Z, int p) {
+    pdl_trigger();
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t row = t / p;
+    const int q = (int)(t - row * p);
+    int64_t o = -1, d = 0, c0 = 0, c1 = 0;
+    if (row < nrows) {
+        o = own[row];
+        d = dst[row];
+        c0 = cptr[row];
+        c1 = cptr[row + 1];
+    }
+    pdl_wait();
+    if (row >= nrows) return;
+    T v = o >= 0 ? y[o * p + q] : T(0);
+    for (int64_t c = c0; c < c1; ++c) v += Z[src[c] * p + q];
+    Z[d * p + q] = v;
+}
+
 template <class T>
 __global__ void k_fwd_finish(const AsmItem *items, const int64_t *zo, const int32_t *nc, const int32_t *sn_start,
                              const T *Dg, const T *Zs, T *yfw, int p) {
+    pdl_trigger();
     AsmItem it = items[blockIdx.x];
     const int s = it.front, r0 = it.c0, r1 = min(nc[s], r0 + ACOLS);
     const T *z = Zs + zo[s] * p;
+    pdl_wait();
     for (int idx = threadIdx.x; idx < (r1 - r0) * p; idx += blockDim.x) {
         int r = r0 + idx / p, q = idx % p;
         int64_t g = (int64_t)sn_start[s] + r;
@@ -607,10 +612,12 @@ template <class T>
 __global__ void k_bwd_gather(const AsmItem *items, const int64_t *zo, const int32_t *fsz, const int32_t *nc,
                              const int32_t *sn_start, const int64_t *rows_off, const int32_t *rows, const T *yfw,
                              const T *x, T *Z, int p) {
+    pdl_trigger();
     AsmItem it = items[blockIdx.x];
     const int s = it.front, f = fsz[s], r0 = it.c0, r1 = min(f, r0 + ACOLS), ncs = nc[s];
     T *z = Z + zo[s] * p;
     const int32_t *rw = rows + rows_off[s];
+    pdl_wait();
     for (int idx = threadIdx.x; idx < (r1 - r0) * p; idx += blockDim.x) {
         int r = r0 + idx / p, q = idx % p;
         z[(int64_t)r * p + q] = (r < ncs) ? yfw[((int64_t)sn_start[s] + r) * p + q] : x[(int64_t)rw[r] * p + q];
@@ -631,10 +638,14 @@ __global__ void __launch_bounds__(256) k_bwd_step(const SolveDesc *sdescs, int n
     T(*Gs)[RBB + 1] = reinterpret_cast<T(*)[RBB + 1]>(smraw);   // RBB x (RBB + 1)
     T *vs = reinterpret_cast<T *>(smraw + sizeof(T) * RBB * (RBB + 1));  // RBB x PB
     __shared__ int s_last;
+    pdl_trigger();
     const int di = find_sdesc_b(sdescs, nd, blockIdx.x);
     const SolveDesc d = sdescs[di];
     const int cc = blockIdx.y * RBB;
-    if (cc >= d.w) return;
+    if (cc >= d.w) {
+        pdl_wait();
+        return;
+    }
     const int s = d.front, f = fsz[s], k0 = d.k0, w = d.w, ncs = nc[s];
     const int b = (int)(blockIdx.x - d.offb);
     const int nb = (w + d.m2 + RBB - 1) / RBB;
@@ -643,6 +654,12 @@ __global__ void __launch_bounds__(256) k_bwd_step(const SolveDesc *sdescs, int n
     const int wc = min(RBB, w - cc);
     const int64_t zb = zo[s] + k0;
     const T *F = arena + fo[s];
+    // the tile of G does not depend on the previous step: load it before waiting
+    for (int idx = threadIdx.x; idx < RBB * RBB; idx += blockDim.x) {
+        const int i = idx % RBB, c = idx / RBB;
+        Gs[i][c] = (i < nr && c < wc) ? F[(int64_t)(k0 + cc + c) * f + k0 + r0 + i] : T(0);
+    }
+    pdl_wait();
     for (int idx = threadIdx.x; idx < RBB * PB; idx += blockDim.x) {
         const int i = idx / PB, q = idx % PB;
         T v = T(0);
@@ -653,10 +670,6 @@ __global__ void __launch_bounds__(256) k_bwd_step(const SolveDesc *sdescs, int n
             else v = -Z[(zb + rr) * p + q];
         }
         vs[idx] = v;
-    }
-    for (int idx = threadIdx.x; idx < RBB * RBB; idx += blockDim.x) {
-        const int i = idx % RBB, c = idx / RBB;
-        Gs[i][c] = (i < nr && c < wc) ? F[(int64_t)(k0 + cc + c) * f + k0 + r0 + i] : T(0);
     }
     __syncthreads();
     constexpr int QP = PB / 4;
@@ -687,9 +700,15 @@ __global__ void __launch_bounds__(256) k_bwd_step(const SolveDesc *sdescs, int n
     for (int o = threadIdx.x; o < wc * p; o += blockDim.x) {
         const int cq = o % wc, q = o / wc;
         const T *src = src0 + q * RBB + cq;
-        T v = T(0);
-        for (int bb = 0; bb < nb; ++bb) v += __ldcg(src + (int64_t)bb * SUBS * tile);
-        Zs[(zb + cc + cq) * p + q] = v;
+        const int64_t stride = (int64_t)SUBS * tile;
+        T v4[4] = {T(0), T(0), T(0), T(0)};
+        int bb = 0;
+        for (; bb + 4 <= nb; bb += 4) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) v4[u] += __ldcg(src + (int64_t)(bb + u) * stride);
+        }
+        for (; bb < nb; ++bb) v4[0] += __ldcg(src + (int64_t)bb * stride);
+        Zs[(zb + cc + cq) * p + q] = (v4[0] + v4[1]) + (v4[2] + v4[3]);
     }
     if (threadIdx.x == 0) cnt[(size_t)di * SUBS + blockIdx.y] = 0u;
 }
@@ -697,9 +716,11 @@ __global__ void __launch_bounds__(256) k_bwd_step(const SolveDesc *sdescs, int n
 template <class T>
 __global__ void k_bwd_finish(const AsmItem *items, const int64_t *zo, const int32_t *nc, const int32_t *sn_start,
                              const T *Z, T *x, int p) {
+    pdl_trigger();
     AsmItem it = items[blockIdx.x];
     const int s = it.front, r0 = it.c0, r1 = min(nc[s], r0 + ACOLS);
     const T *z = Z + zo[s] * p;
+    pdl_wait();
     for (int idx = threadIdx.x; idx < (r1 - r0) * p; idx += blockDim.x) {
         int r = r0 + idx / p, q = idx % p;
         x[((int64_t)sn_start[s] + r) * p + q] = z[(int64_t)r * p + q];
@@ -731,7 +752,7 @@ static void set_step_attrs() {
 
 template <class T>
 static void set_solve_attrs() {
-    static bool done = false;
+    static std::atomic<bool> done{false};
     if (done) return;
     MBL_CUDA(cudaFuncSetAttribute(k_build_m<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)build_m_smem<T>()));
     MBL_CUDA(cudaFuncSetAttribute(k_apply_m<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)apply_m_smem<T>()));
@@ -748,7 +769,7 @@ static void factor_impl(Factorization &fz, cudaStream_t st) {
     T *arena = static_cast<T *>(fz.arena.m.p);
     T *Dg = static_cast<T *>(fz.D.m.p);
     T *wscr = static_cast<T *>(fz.wscr.m.p);
-    static bool attr = false;
+    static std::atomic<bool> attr{false};  // per process: one device
     if (!attr) {
         MBL_CUDA(cudaFuncSetAttribute(k_panel_trsm<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)trsm_smem<T>()));
         attr = true;
@@ -838,39 +859,36 @@ static void solve_levels(Factorization &fz, int p, cudaStream_t st) {
     for (int l = 0; l < pl.nlevels; ++l) {
         int na = pl.asm_ptr[l + 1] - pl.asm_ptr[l];
         const AsmItem *items = pl.d_asm_items.data() + pl.asm_ptr[l];
-        k_fwd_gather<T><<<na, 256, 0, st>>>(items, pl.d_sn_zo.data(), pl.d_sn_f.data(), pl.d_sn_nc.data(),
-                                            pl.d_sn_start.data(), pl.d_ch_ptr.data(), pl.d_ch_list.data(),
-                                            pl.d_sn_rel_off.data(), pl.d_relind.data(), y, Z, p);
-        MBL_LAUNCH_CHECK();
+        {
+            const int64_t f0 = pl.lvl_fg_ptr[l], nrows = pl.lvl_fg_ptr[l + 1] - f0;
+            launch_pdl(k_fwd_gather_rows<T>, dim3((unsigned)((nrows * p + 255) / 256)), dim3(256), 0, st, nrows,
+                       pl.d_fg_dst.data() + f0, pl.d_fg_own.data() + f0, pl.d_fg_cptr.data() + f0,
+                       (const int64_t *)pl.d_fg_src.data(), (const T *)y, Z, p);
+        }
         for (int si = pl.lvl_sstep_ptr[l]; si < pl.lvl_sstep_ptr[l + 1]; ++si) {
             const SolveStep &ss = pl.ssteps[si];
             const SolveDesc *sd = pl.d_sdescs.data() + ss.d0;
-            k_fwd_step<T, PB><<<(unsigned)ss.nrb, 256, fsm, st>>>(sd, ss.nd, pl.d_sn_fo.data(), pl.d_sn_zo.data(),
-                                                                 pl.d_sn_f.data(), arena, Z, Zs, p);
-            MBL_LAUNCH_CHECK();
+            launch_pdl(k_fwd_step<T, PB>, dim3((unsigned)ss.nrb), dim3(256), fsm, st, sd, ss.nd,
+                       pl.d_sn_fo.data(), pl.d_sn_zo.data(), pl.d_sn_f.data(), (const T *)arena, Z, Zs, p);
         }
-        k_fwd_finish<T><<<na, 256, 0, st>>>(items, pl.d_sn_zo.data(), pl.d_sn_nc.data(), pl.d_sn_start.data(), Dg, Zs,
-                                            yfw, p);
-        MBL_LAUNCH_CHECK();
+        launch_pdl(k_fwd_finish<T>, dim3(na), dim3(256), 0, st, items, pl.d_sn_zo.data(), pl.d_sn_nc.data(),
+                   pl.d_sn_start.data(), (const T *)Dg, (const T *)Zs, yfw, p);
     }
     for (int l = pl.nlevels - 1; l >= 0; --l) {
         int na = pl.asm_ptr[l + 1] - pl.asm_ptr[l];
         const AsmItem *items = pl.d_asm_items.data() + pl.asm_ptr[l];
-        k_bwd_gather<T><<<na, 256, 0, st>>>(items, pl.d_sn_zo.data(), pl.d_sn_f.data(), pl.d_sn_nc.data(),
-                                            pl.d_sn_start.data(), pl.d_sn_rows_off.data(), pl.d_rows.data(), yfw, y, Z,
-                                            p);
-        MBL_LAUNCH_CHECK();
+        launch_pdl(k_bwd_gather<T>, dim3(na), dim3(256), 0, st, items, pl.d_sn_zo.data(), pl.d_sn_f.data(),
+                   pl.d_sn_nc.data(), pl.d_sn_start.data(), pl.d_sn_rows_off.data(), pl.d_rows.data(),
+                   (const T *)yfw, (const T *)y, Z, p);
         for (int si = pl.lvl_sstep_ptr[l + 1] - 1; si >= pl.lvl_sstep_ptr[l]; --si) {
             const SolveStep &ss = pl.ssteps[si];
             const SolveDesc *sd = pl.d_sdescs.data() + ss.d0;
-            k_bwd_step<T, PB><<<dim3((unsigned)ss.nrbb, SUBS), 256, bsm, st>>>(
-                sd, ss.nd, pl.d_sn_fo.data(), pl.d_sn_zo.data(), pl.d_sn_f.data(), pl.d_sn_nc.data(), arena, Z, Zs, P,
-                cnt + (size_t)ss.d0 * SUBS, p);
-            MBL_LAUNCH_CHECK();
+            launch_pdl(k_bwd_step<T, PB>, dim3((unsigned)ss.nrbb, SUBS), dim3(256), bsm, st, sd, ss.nd,
+                       pl.d_sn_fo.data(), pl.d_sn_zo.data(), pl.d_sn_f.data(), pl.d_sn_nc.data(), (const T *)arena,
+                       (const T *)Z, Zs, P, cnt + (size_t)ss.d0 * SUBS, p);
         }
-        k_bwd_finish<T><<<na, 256, 0, st>>>(items, pl.d_sn_zo.data(), pl.d_sn_nc.data(), pl.d_sn_start.data(), Zs, y,
-                                            p);
-        MBL_LAUNCH_CHECK();
+        launch_pdl(k_bwd_finish<T>, dim3(na), dim3(256), 0, st, items, pl.d_sn_zo.data(), pl.d_sn_nc.data(),
+                   pl.d_sn_start.data(), (const T *)Zs, y, p);
     }
 }
 

@@ -415,6 +415,7 @@ void KrylovSchur::ritz(cudaStream_t st, std::vector<double> &theta, std::vector<
 }
 
 void KrylovSchur::restart(const std::vector<int> &keep_idx, cudaStream_t st) {
+    ProfScope ps_all(ctx, "ks_restart", (double)keep_idx.size(), st);
     int mm = m - p;
     int k = (int)keep_idx.size();
     MBL_CUDA(cudaMemcpyAsync(keep.data(), keep_idx.data(), k * sizeof(int), cudaMemcpyHostToDevice, st));
@@ -480,6 +481,7 @@ double RefinedSolve::residual(const double *X, int ldx, double *Y, int p, cudaSt
 }
 
 void RefinedSolve::apply(const double *X, int ldx, double *Y, int p, cudaStream_t st) {
+    ProfScope ps_all(sec->ctx, "op_apply", (double)p, st);
     int64_t n = sec->n;
     if (R.size() < (size_t)n * p) R.alloc(sec->ctx, (size_t)n * p);
     if (norms.size() < (size_t)3 * 32) norms.alloc(sec->ctx, 3 * 32);
@@ -1021,6 +1023,8 @@ void solve_near(mbl_sector *sec, double eps, int nev, const mbl_opts &o, double 
             if (op.stalled && fz->prec == MBL_PREC_FP32) {
                 // refinement stalled near the shift: fall back to FP64 fronts (same basis)
                 auto tf1 = std::chrono::steady_clock::now();
+                op.fz = nullptr;
+                fz.reset();  // free the FP32 fronts first: the two factors never coexist in HBM
                 fz = make_factorization(sec, sigma_f, MBL_PREC_FP64, hnorm);
                 S.ms_factor += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tf1).count();
                 op.fz = fz.get();
@@ -1093,6 +1097,7 @@ RitzH::RitzH(Ctx *c, int64_t n_, int ldv, int nev_) : ctx(c), n(n_), nev(nev_) {
 
 void RitzH::run(mbl_sector *sec, KrylovSchur &ks, double sigma, double hnorm, double tol, double *d_evecs,
                 cudaStream_t st) {
+    ProfScope ps_all(ctx, "ritz_h", (double)nev, st);
     int mb = ks.m;
     launch_spmv(sec, 0.0, ks.V.data(), ks.ldv, 1, HV.data(), mb, 1, mb, st);
     for (int c0 = 0; c0 < mb; c0 += 32) {

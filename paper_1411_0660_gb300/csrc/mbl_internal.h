@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <atomic>
+#include <mutex>
 #include <cstdint>
 #include <map>
 #include <memory>
@@ -37,6 +38,30 @@ extern std::atomic<long long> g_launches;
         ::mbl::g_launches.fetch_add(1, std::memory_order_relaxed);   \
         MBL_CUDA(cudaGetLastError());                                \
     } while (0)
+
+// Programmatic dependent launch (sm_90+): a kernel launched with launch_pdl may start while its
+// predecessor in the stream is still running.  It must execute pdl_wait() -- which returns once
+// the predecessor grid has completed and its writes are visible -- before it touches anything the
+// predecessor writes or reads, and on every path before it exits (so that completion stays
+// transitive along the stream).  pdl_trigger() lets the successor launch early.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+void launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    MBL_CUDA(cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...));
+    MBL_LAUNCH_CHECK();
+}
 
 struct Ctx;
 bool ctx_alive(const Ctx *c);
@@ -86,6 +111,13 @@ struct ProfAcc {
 struct Plan;       // symbolic analysis, symbolic.cpp
 struct EntTables;  // entanglement block tables, observables.cu
 
+// Symbolic analyses by L.  Shared by a context and its serving workers; `mu` serializes lookups
+// and the (one-off) builds.
+struct PlanCache {
+    std::mutex mu;
+    std::map<int, std::shared_ptr<Plan>> m;
+};
+
 struct Ctx {
     int device = 0;
     size_t budget = 0;  // 0 = unlimited
@@ -93,15 +125,17 @@ struct Ctx {
     size_t peak = 0;
     cudaStream_t stream = nullptr;
     std::string last_error;
-    std::map<int, std::shared_ptr<Plan>> plans;     // per L
+    std::shared_ptr<PlanCache> plans = std::make_shared<PlanCache>();  // per L; shared with serving workers
     std::map<int, std::shared_ptr<EntTables>> ent;  // per L
     int sm_count = 0;
     bool prof = false;
     std::map<std::string, ProfAcc> profile;
     std::vector<cudaEvent_t> event_pool;
+    struct Server *server = nullptr;  // serving workers (server.cu), if started
     cudaEvent_t take_event();
     void resolve_profile();
 };
+void server_shutdown(Ctx *ctx);
 
 // Times the enclosed launches on `st` under class `name` when profiling is on.
 struct ProfScope {

@@ -153,6 +153,7 @@ EntTables &ent_tables(Ctx *ctx, int L) {
 
 void observables_dev(Ctx *ctx, int L, int nev, const double *d_evals, const double *d_evecs, double *d_r,
                      double *d_rmean, double *d_s1p, double *d_se, cudaStream_t st) {
+    ProfScope ps_all(ctx, "observables", (double)nev, st);
     int64_t n = host_binom(L, L / 2);
     if (nev < 1 || nev > n) fail(MBL_ERR_INVALID, "observables: nev must be in [1, dim]");
     if (nev > 2 || d_rmean) {
@@ -192,7 +193,7 @@ void observables_dev(Ctx *ctx, int L, int nev, const double *d_evals, const doub
     MBL_CUDA(cudaMemcpyAsync(dm.data(), hm.data(), batch * sizeof(int), cudaMemcpyHostToDevice, st));
     MBL_CUDA(cudaMemcpyAsync(dgo.data(), hg.data(), batch * sizeof(int64_t), cudaMemcpyHostToDevice, st));
     MBL_CUDA(cudaMemcpyAsync(dwo.data(), hw.data(), batch * sizeof(int64_t), cudaMemcpyHostToDevice, st));
-    static bool attr = false;
+    static std::atomic<bool> attr{false};  // per process: one device
     if (!attr) {
         MBL_CUDA(cudaFuncSetAttribute(k_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, 12288 * 8));
         attr = true;

@@ -87,6 +87,11 @@ struct Plan {
     std::vector<SolveStep> ssteps;
     std::vector<int32_t> lvl_sstep_ptr;       // solve steps by level
     std::vector<SolveDesc> sdescs;
+    // forward-solve gather as row lists: for every row of every front of a level (levels in order),
+    // its work row in Z, its own right-hand-side row (-1 below the fully summed block) and the Z
+    // rows of the children's contribution blocks that land on it (children in tree order)
+    std::vector<int64_t> lvl_fg_ptr;          // rows by level (nlevels + 1)
+    std::vector<int64_t> fg_dst, fg_own, fg_cptr, fg_src;
     int64_t m_elems = 0, max_sstep_nrbb = 0;
     int64_t arena_elems = 0, zwork_elems = 0, wscratch_elems = 0, max_desc_per_step = 0;
     int64_t max_step_n2 = 0;
@@ -101,6 +106,7 @@ struct Plan {
     DVec<AsmItem> d_asm_items;
     DVec<PanelDesc> d_descs;
     DVec<SolveDesc> d_sdescs;
+    DVec<int64_t> d_fg_dst, d_fg_own, d_fg_cptr, d_fg_src;
     bool on_device = false;
 };
 

@@ -214,7 +214,7 @@ size_t schur_tc_smem() { return 4 * (size_t)OPB; }
 
 void launch_schur_tc(const PanelStep &stp, const PanelDesc *d_descs, const Plan &p, float *arena, const float *wscr,
                      unsigned long long *err, cudaStream_t st) {
-    static bool attr = false;
+    static std::atomic<bool> attr{false};  // per process: one device
     if (!attr) {
         MBL_CUDA(cudaFuncSetAttribute(k_schur_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)schur_tc_smem()));
         attr = true;

@@ -1,0 +1,350 @@
+// server.cu -- serving: a request loop with continuous batching and HBM admission.
+//
+// A context may start a server: `slots` worker threads, each with its own child context (own CUDA
+// stream, own scratch) that shares the parent's symbolic analyses (plan cache).  Requests
+// (L, h, seed, eps, nev) queue in arrival order; a free worker takes the oldest, builds the sector
+// (and, once per L, the plan), estimates the HBM the job will hold from the plan (fronts, factor,
+// solve work, Krylov basis, outputs) and waits until that much of the server budget is free.  Jobs
+// of different sizes then run side by side on the device, each on its worker's stream; a finished
+// job returns its reservation and wakes the waiting workers.  Every job goes through the same
+// entry points as a single call (sector build, shift-invert eigensolve, observables), so its
+// result is the one it would have alone.
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <thread>
+
+#include "factor.h"
+#include "krylov.h"
+#include "observables.h"
+
+namespace mbl {
+
+namespace {
+
+double now_ms(std::chrono::steady_clock::time_point t0) {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+}
+
+// Upper estimate of the device bytes one job holds at its peak (plan of its L known).
+size_t job_bytes(const Plan &p, int nev, int block, int prec) {
+    const double n = (double)p.n, es = prec == MBL_PREC_FP64 ? 8.0 : 4.0;
+    const int pb = std::max(1, std::min(32, block));
+    const double pad = pb <= 8 ? 8 : (pb <= 16 ? 16 : 32);
+    const double ldv = 2.0 * nev + 3.0 * pb;
+    double b = 0.0;
+    b += 20.0 * n + 12.0 * (double)p.nnzA;                                   // sector
+    b += (double)p.arena_elems * es + n * (es + 4.0);                        // fronts, D, pivots
+    b += (double)std::max<int64_t>(p.wscratch_elems, 1) * es + (double)p.m_elems * es;
+    b += 2.0 * (double)p.zwork_elems * pb * es + 2.0 * n * pb * es;         // solve work
+    b += (double)p.max_sstep_nrbb * SUBS * RBB * pad * es;
+    b += 8.0 * n * (3.0 * ldv + 2.0 * nev + 30.0 * pb);                      // Krylov, Rayleigh-Ritz, refinement
+    b += 8.0 * n * 480.0;                                                    // extremal-bounds Lanczos basis
+    return (size_t)(1.10 * b) + ((size_t)64 << 20);
+}
+
+struct Job {
+    mbl_request req{};
+    int state = 0;  // 0 queued, 1 running, 2 done
+    int status = MBL_OK;
+    std::string err;
+    int nconv = 0;
+    int64_t dim = 0;
+    double sigma = 0.0, r_mean = 0.0;
+    double t_submit = 0.0, t_admit = 0.0, t_end = 0.0;
+    size_t reserved = 0;
+    std::vector<double> evals, resid, r, s1p, se, evecs;
+};
+
+}  // namespace
+
+struct Server {
+    Ctx *parent = nullptr;
+    std::vector<mbl_ctx *> wctx;
+    std::vector<std::thread> threads;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_mem, cv_done;
+    std::deque<uint64_t> queue;
+    std::map<uint64_t, std::unique_ptr<Job>> jobs;
+    uint64_t next_ticket = 1;
+    size_t budget = 0, reserved = 0, peak_reserved = 0;
+    int64_t submitted = 0, completed = 0, failed = 0;
+    int running = 0;
+    bool stop = false;
+    std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
+
+    void worker(int i);
+    void run(Job &J, mbl_ctx *w);
+};
+
+void Server::run(Job &J, mbl_ctx *w) {
+    const mbl_request &q = J.req;
+    mbl_sector *sec = nullptr;
+    bool held = false;
+    try {
+        int rc = mbl_build_sector(w, q.L, q.h, q.seed, &sec);
+        if (rc != MBL_OK) fail(rc, mbl_last_error(w));
+        std::shared_ptr<Plan> plan = get_plan(sec);
+        mbl_opts o;
+        mbl_opts_default(&o);
+        o.precision = q.precision;
+        const size_t est = job_bytes(*plan, q.nev, o.block, o.precision);
+        {
+            std::unique_lock<std::mutex> lk(mu);
+            if (est > budget) fail(MBL_ERR_OOM, "request needs more HBM than the server budget");
+            cv_mem.wait(lk, [&] { return stop || reserved + est <= budget; });
+            if (stop) fail(MBL_ERR_INVALID, "server stopped");
+            reserved += est;
+            peak_reserved = std::max(peak_reserved, reserved);
+            held = true;
+            J.reserved = est;
+            J.t_admit = now_ms(t0);
+        }
+        const int64_t n = sec->n;
+        const int nev = q.nev;
+        J.dim = n;
+        DVec<double> de, dv, dr, dobs;
+        de.alloc(w, nev);
+        dv.alloc(w, (size_t)n * nev);
+        dr.alloc(w, nev);
+        dobs.alloc(w, (size_t)3 * nev + 1);
+        int nconv = 0;
+        double sigma = 0.0;
+        rc = mbl_solve_near_dev(sec, q.eps, nev, &o, de.data(), dv.data(), dr.data(), &nconv, &sigma, nullptr,
+                                nullptr);
+        if (rc != MBL_OK && rc != MBL_ERR_NOT_CONVERGED) fail(rc, mbl_last_error(w));
+        J.status = rc;
+        if (rc != MBL_OK) J.err = mbl_last_error(w);
+        double *d_r = dobs.data(), *d_rm = d_r + nev, *d_s1 = d_rm + 1, *d_se = d_s1 + nev;
+        int rc2 = mbl_observables_dev(w, q.L, nev, de.data(), dv.data(), d_r, d_rm, d_s1, d_se, nullptr);
+        if (rc2 != MBL_OK) fail(rc2, mbl_last_error(w));
+        MBL_CUDA(cudaStreamSynchronize(w->stream));
+        J.nconv = nconv;
+        J.sigma = sigma;
+        J.evals.resize(nev);
+        J.resid.resize(nev);
+        J.r.resize(std::max(nev - 2, 0));
+        J.s1p.resize(nev);
+        J.se.resize(nev);
+        std::vector<double> obs((size_t)3 * nev + 1);
+        MBL_CUDA(cudaMemcpy(J.evals.data(), de.data(), nev * sizeof(double), cudaMemcpyDeviceToHost));
+        MBL_CUDA(cudaMemcpy(J.resid.data(), dr.data(), nev * sizeof(double), cudaMemcpyDeviceToHost));
+        MBL_CUDA(cudaMemcpy(obs.data(), dobs.data(), obs.size() * sizeof(double), cudaMemcpyDeviceToHost));
+        std::copy(obs.begin(), obs.begin() + std::max(nev - 2, 0), J.r.begin());
+        J.r_mean = obs[nev];
+        std::copy(obs.begin() + nev + 1, obs.begin() + 2 * nev + 1, J.s1p.begin());
+        std::copy(obs.begin() + 2 * nev + 1, obs.end(), J.se.begin());
+        if (q.want_vectors) {
+            J.evecs.resize((size_t)n * nev);
+            MBL_CUDA(cudaMemcpy(J.evecs.data(), dv.data(), (size_t)n * nev * sizeof(double), cudaMemcpyDeviceToHost));
+        }
+    } catch (const Error &e) {
+        J.status = e.code;
+        J.err = e.msg;
+    } catch (const std::exception &e) {
+        J.status = MBL_ERR_CUDA;
+        J.err = e.what();
+    }
+    if (sec) mbl_sector_destroy(sec);
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        J.t_end = now_ms(t0);  // before the reservation returns: the next admission comes after it
+        if (held) reserved -= J.reserved;
+    }
+    cv_mem.notify_all();
+}
+
+void Server::worker(int i) {
+    mbl_ctx *w = wctx[i];
+    cudaSetDevice(w->device);
+    for (;;) {
+        uint64_t t;
+        Job *J;
+        {
+            std::unique_lock<std::mutex> lk(mu);
+            cv_work.wait(lk, [&] { return stop || !queue.empty(); });
+            if (stop) return;
+            t = queue.front();
+            queue.pop_front();
+            J = jobs[t].get();
+            J->state = 1;
+            ++running;
+        }
+        run(*J, w);
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            J->state = 2;
+            --running;
+            ++completed;
+            if (J->status != MBL_OK) ++failed;
+        }
+        cv_done.notify_all();
+    }
+}
+
+void server_shutdown(Ctx *ctx) {
+    Server *s = ctx->server;
+    if (!s) return;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+    }
+    s->cv_work.notify_all();
+    s->cv_mem.notify_all();
+    for (auto &th : s->threads) th.join();
+    for (mbl_ctx *w : s->wctx) mbl_ctx_destroy(w);
+    ctx->server = nullptr;
+    delete s;
+}
+
+}  // namespace mbl
+
+using namespace mbl;
+
+namespace {
+
+int srv_report(mbl_ctx *ctx, int code, const std::string &msg) {
+    if (ctx) ctx->last_error = msg;
+    return code;
+}
+
+void fill_result(const Job &J, mbl_result *out) {
+    out->status = J.status;
+    out->nconv = J.nconv;
+    out->nev = J.req.nev;
+    out->L = J.req.L;
+    out->dim = J.dim;
+    out->sigma = J.sigma;
+    out->r_mean = J.r_mean;
+    out->t_submit_ms = J.t_submit;
+    out->t_admit_ms = J.t_admit;
+    out->t_end_ms = J.t_end;
+    out->reserved_bytes = J.reserved;
+    auto put = [](double *dst, const std::vector<double> &v) {
+        if (dst && !v.empty()) std::copy(v.begin(), v.end(), dst);
+    };
+    put(out->evals, J.evals);
+    put(out->resid, J.resid);
+    put(out->r, J.r);
+    put(out->s1p, J.s1p);
+    put(out->se, J.se);
+    put(out->evecs, J.evecs);
+}
+
+}  // namespace
+
+int mbl_server_start(mbl_ctx *ctx, int slots, size_t budget_bytes) {
+    if (!ctx) return MBL_ERR_INVALID;
+    if (slots < 1 || slots > 64) return srv_report(ctx, MBL_ERR_INVALID, "slots must be in [1, 64]");
+    if (ctx->server) return srv_report(ctx, MBL_ERR_INVALID, "server already running");
+    try {
+        MBL_CUDA(cudaSetDevice(ctx->device));
+        size_t fr = 0, tot = 0;
+        MBL_CUDA(cudaMemGetInfo(&fr, &tot));
+        auto s = std::make_unique<Server>();
+        s->parent = ctx;
+        s->budget = budget_bytes ? budget_bytes : (size_t)(0.85 * (double)fr);
+        if (ctx->budget) s->budget = std::min(s->budget, ctx->budget);
+        for (int i = 0; i < slots; ++i) {
+            mbl_ctx *w = nullptr;
+            int rc = mbl_ctx_create(ctx->device, 0, &w);
+            if (rc != MBL_OK) {
+                for (mbl_ctx *x : s->wctx) mbl_ctx_destroy(x);
+                return srv_report(ctx, rc, "worker context: " + std::string(mbl_last_error(nullptr)));
+            }
+            w->plans = ctx->plans;
+            s->wctx.push_back(w);
+        }
+        Server *raw = s.release();
+        ctx->server = raw;
+        for (int i = 0; i < slots; ++i) raw->threads.emplace_back([raw, i] { raw->worker(i); });
+    } catch (const Error &e) {
+        return srv_report(ctx, e.code, e.msg);
+    } catch (const std::exception &e) {
+        return srv_report(ctx, MBL_ERR_CUDA, e.what());
+    }
+    return MBL_OK;
+}
+
+int mbl_submit(mbl_ctx *ctx, const mbl_request *req, uint64_t *ticket) {
+    if (!ctx || !req || !ticket) return MBL_ERR_INVALID;
+    Server *s = ctx->server;
+    if (!s) return srv_report(ctx, MBL_ERR_INVALID, "no server: call mbl_server_start first");
+    if (req->L < 2 || req->L > 22 || (req->L & 1)) return srv_report(ctx, MBL_ERR_INVALID, "L must be even, 2..22");
+    if (!(req->eps >= 0.0 && req->eps <= 1.0)) return srv_report(ctx, MBL_ERR_INVALID, "eps must be in [0, 1]");
+    if (req->h < 0.0 || req->nev < 1) return srv_report(ctx, MBL_ERR_INVALID, "h >= 0 and nev >= 1 required");
+    if (req->precision != MBL_PREC_FP32 && req->precision != MBL_PREC_FP64)
+        return srv_report(ctx, MBL_ERR_INVALID, "unknown precision");
+    auto J = std::make_unique<Job>();
+    J->req = *req;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        J->t_submit = now_ms(s->t0);
+        *ticket = s->next_ticket++;
+        s->jobs[*ticket] = std::move(J);
+        s->queue.push_back(*ticket);
+        ++s->submitted;
+    }
+    s->cv_work.notify_one();
+    return MBL_OK;
+}
+
+int mbl_poll(mbl_ctx *ctx, uint64_t ticket, mbl_result *out) {
+    if (!ctx || !out) return MBL_ERR_INVALID;
+    Server *s = ctx->server;
+    if (!s) return srv_report(ctx, MBL_ERR_INVALID, "no server");
+    std::unique_ptr<Job> J;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        auto it = s->jobs.find(ticket);
+        if (it == s->jobs.end()) return srv_report(ctx, MBL_ERR_INVALID, "unknown ticket");
+        if (it->second->state != 2) return MBL_PENDING;
+        J = std::move(it->second);
+        s->jobs.erase(it);
+    }
+    fill_result(*J, out);
+    if (J->status != MBL_OK) ctx->last_error = J->err;
+    return J->status;
+}
+
+int mbl_wait(mbl_ctx *ctx, uint64_t ticket, double timeout_s, mbl_result *out) {
+    if (!ctx || !out) return MBL_ERR_INVALID;
+    Server *s = ctx->server;
+    if (!s) return srv_report(ctx, MBL_ERR_INVALID, "no server");
+    {
+        std::unique_lock<std::mutex> lk(s->mu);
+        auto ready = [&] {
+            auto it = s->jobs.find(ticket);
+            return it == s->jobs.end() || it->second->state == 2;
+        };
+        if (timeout_s > 0) {
+            if (!s->cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s), ready)) return MBL_PENDING;
+        } else {
+            s->cv_done.wait(lk, ready);
+        }
+    }
+    return mbl_poll(ctx, ticket, out);
+}
+
+int mbl_server_stats_get(mbl_ctx *ctx, mbl_server_stats *out) {
+    if (!ctx || !out) return MBL_ERR_INVALID;
+    Server *s = ctx->server;
+    if (!s) return srv_report(ctx, MBL_ERR_INVALID, "no server");
+    std::lock_guard<std::mutex> lk(s->mu);
+    out->submitted = s->submitted;
+    out->completed = s->completed;
+    out->failed = s->failed;
+    out->running = s->running;
+    out->queued = (int)s->queue.size();
+    out->slots = (int)s->wctx.size();
+    out->budget_bytes = s->budget;
+    out->reserved_bytes = s->reserved;
+    out->peak_reserved_bytes = s->peak_reserved;
+    return MBL_OK;
+}
+
+int mbl_server_stop(mbl_ctx *ctx) {
+    if (!ctx) return MBL_ERR_INVALID;
+    server_shutdown(ctx);
+    return MBL_OK;
+}

@@ -562,6 +562,29 @@ std::shared_ptr<Plan> build_plan(int L, const std::vector<uint32_t> &states, con
         }
         p.lvl_sstep_ptr[l + 1] = (int32_t)p.ssteps.size();
     }
+    // forward-solve gather lists
+    p.lvl_fg_ptr.assign(p.nlevels + 1, 0);
+    p.fg_cptr.push_back(0);
+    for (int l = 0; l < p.nlevels; ++l) {
+        for (int32_t q = p.lvl_ptr[l]; q < p.lvl_ptr[l + 1]; ++q) {
+            const int32_t s = p.lvl_fronts[q];
+            const int32_t f = p.sn_f[s], ncs = p.sn_nc[s];
+            std::vector<std::vector<int64_t>> in(f);
+            for (int32_t c = p.ch_ptr[s]; c < p.ch_ptr[s + 1]; ++c) {
+                const int32_t ch = p.ch_list[c];
+                const int32_t uc = p.sn_f[ch] - p.sn_nc[ch];
+                for (int32_t a = 0; a < uc; ++a)
+                    in[p.relind[p.sn_rel_off[ch] + a]].push_back(p.sn_zo[ch] + p.sn_nc[ch] + a);
+            }
+            for (int32_t r = 0; r < f; ++r) {
+                p.fg_dst.push_back(p.sn_zo[s] + r);
+                p.fg_own.push_back(r < ncs ? (int64_t)p.sn_start[s] + r : -1);
+                p.fg_src.insert(p.fg_src.end(), in[r].begin(), in[r].end());
+                p.fg_cptr.push_back((int64_t)p.fg_src.size());
+            }
+        }
+        p.lvl_fg_ptr[l + 1] = (int64_t)p.fg_dst.size();
+    }
     p.ms_analyse = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     return P;
 }
@@ -593,6 +616,10 @@ void upload_plan(Ctx *ctx, Plan &p) {
     up(ctx, p.d_asm_items, p.asm_items);
     up(ctx, p.d_descs, p.descs);
     up(ctx, p.d_sdescs, p.sdescs);
+    up(ctx, p.d_fg_dst, p.fg_dst);
+    up(ctx, p.d_fg_own, p.fg_own);
+    up(ctx, p.d_fg_cptr, p.fg_cptr);
+    up(ctx, p.d_fg_src, p.fg_src);
     p.on_device = true;
 }
 
