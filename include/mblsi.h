@@ -186,6 +186,19 @@ int mbl_observables_dev(mbl_ctx *ctx, int L, int nev, const double *d_evals,
                         const double *d_evecs, double *d_r, double *d_r_mean, double *d_s1p,
                         double *d_se, void *stream);
 
+/* Half-chain entanglement entropy (the se output of mbl_observables_dev) computed without any
+ * device allocation.  The paper has no counterpart: it exists for callers that cannot allocate
+ * device memory (a worker whose admitted jobs already hold the whole HBM budget; a loop that must
+ * not trigger the device-wide synchronization of cudaFree).  Its scratch is a fixed 12 MiB device
+ * array in the library, whose address is taken once per device when a context is created.  Limits:
+ * even L <= 16 and 1 <= nev <= 64 (MBL_ERR_INVALID otherwise).  d_evecs: n x nev column-major
+ * device array; d_se: nev device outputs; enqueued on `stream` (NULL = context stream) and
+ * complete when the stream reaches it.  The scratch is shared by all callers on the device:
+ * overlapping calls race and must be serialized by the caller.  MBL_ERR_CUDA if the scratch
+ * address could not be taken on this device. */
+int mbl_entanglement_noalloc_dev(mbl_ctx *ctx, int L, int nev, const double *d_evecs, double *d_se,
+                                 void *stream);
+
 /* ---- Serving: request loop with continuous batching and HBM admission -------------------
  * Not in the paper, which diagonalizes one realization per batch job; this is the serving
  * pattern for streams of (L, h, seed, eps, nev) requests of mixed L.

@@ -23,7 +23,7 @@ from ._capi import MBL_PREC_FP32, MBL_PREC_FP64, FactorStats, Opts, SolveStats
 
 __all__ = ["Context", "Sector", "Factorization", "MblError", "build_sector", "build_sector_fields",
            "extremal_bounds", "factor", "solve_near", "solve_near_dev", "observables", "observables_dev",
-           "default_opts", "launch_count", "Server", "ServedResult", "MBL_PREC_FP32", "MBL_PREC_FP64"]
+           "default_opts", "launch_count", "entanglement_noalloc_dev", "Server", "ServedResult", "MBL_PREC_FP32", "MBL_PREC_FP64"]
 
 
 class MblError(RuntimeError):
@@ -263,6 +263,15 @@ def observables_dev(ctx: Context, L: int, nev: int, d_evals, d_evecs, d_r, d_rme
                                       ctypes.c_void_p(d_evecs.data_ptr()), ctypes.c_void_p(d_r.data_ptr()),
                                       ctypes.c_void_p(d_rmean.data_ptr()), ctypes.c_void_p(d_s1p.data_ptr()),
                                       ctypes.c_void_p(d_se.data_ptr()), s), ctx.handle)
+
+
+def entanglement_noalloc_dev(ctx: Context, L: int, nev: int, d_evecs, d_se, stream=None):
+    """S^E of nev device vectors with no device allocation (static library scratch; L <= 16,
+    nev <= 64).  d_evecs: torch float64 CUDA tensor of dim*nev (column-major), d_se: nev.
+    Calls on one device must not overlap."""
+    s = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
+    _check(_lib().mbl_entanglement_noalloc_dev(ctx.handle, L, nev, ctypes.c_void_p(d_evecs.data_ptr()),
+                                               ctypes.c_void_p(d_se.data_ptr()), s), ctx.handle)
 
 
 # ------------------------------------------------------------------------------------------

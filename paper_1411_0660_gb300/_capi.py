@@ -92,6 +92,7 @@ SIGNATURES = [
                                 c_void_p]),
     ("mbl_observables_dev", c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                     c_void_p, c_void_p]),
+    ("mbl_entanglement_noalloc_dev", c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p]),
     ("mbl_server_start", c_int, [c_void_p, c_int, c_size_t]),
     ("mbl_submit", c_int, [c_void_p, P(Request), P(c_uint64)]),
     ("mbl_poll", c_int, [c_void_p, c_uint64, P(Result)]),

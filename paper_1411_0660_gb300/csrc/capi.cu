@@ -270,6 +270,7 @@ int mbl_ctx_create(int device, size_t budget, mbl_ctx **out) {
     MBL_CUDA(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
     MBL_CUDA(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device));
     upload_binomials();
+    noalloc_setup(device);
     {
         std::lock_guard<std::mutex> lk(g_ctx_mu);
         live_ctx().insert(c);
@@ -615,3 +616,12 @@ int mbl_observables(mbl_ctx *ctx, int L, int nev, const double *evals, const dou
 }
 
 }  // extern "C"
+
+int mbl_entanglement_noalloc_dev(mbl_ctx *ctx, int L, int nev, const double *d_evecs, double *d_se, void *stream) {
+    if (!ctx || !d_evecs || !d_se) return report(ctx, MBL_ERR_INVALID, "NULL argument");
+    API_TRY
+    MBL_CUDA(cudaSetDevice(ctx->device));
+    cudaStream_t st = stream ? (cudaStream_t)stream : ctx->stream;
+    entanglement_noalloc(ctx, L, nev, d_evecs, d_se, st);
+    API_CATCH(ctx)
+}

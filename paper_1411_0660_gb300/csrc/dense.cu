@@ -495,6 +495,11 @@ __global__ void __launch_bounds__(EIG_THREADS) k_syev(const int *mv, const int64
     for (int t = threadIdx.x; t < m * m; t += blockDim.x) Ag[t] = (double)Z[t];
 }
 
+cudaError_t syev_preload() {
+    cudaFuncAttributes fa;
+    return cudaFuncGetAttributes(&fa, k_syev<double>);
+}
+
 void syev_batched(int batch, const int *d_m, const int64_t *d_aoff, const int64_t *d_woff, double *d_A,
                   double *d_w, int vecs, const int *d_sel, int mmax, double *d_work, int *d_info, cudaStream_t st,
                   bool fp32) {

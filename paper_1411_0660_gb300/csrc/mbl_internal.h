@@ -208,6 +208,8 @@ constexpr int EIG_SMEM_MAX_M = 160;  // largest order the small eigensolver keep
 void syev_batched(int batch, const int *d_m, const int64_t *d_aoff, const int64_t *d_woff, double *d_A,
                   double *d_w, int vecs, const int *d_sel, int mmax, double *d_work, int *d_info,
                   cudaStream_t st, bool fp32 = false);
+// load the FP64 small-eigensolver kernel now (kernels otherwise load lazily on first launch)
+cudaError_t syev_preload();
 // C = alpha op(A) op(B) + beta C for small column-major FP64 matrices
 void gemm_small(bool ta, bool tb, int M, int N, int K, double alpha, const double *A, int lda, const double *B,
                 int ldb, double beta, double *C, int ldc, cudaStream_t st);

@@ -15,5 +15,8 @@ struct EntTables {
 EntTables &ent_tables(Ctx *ctx, int L);
 void observables_dev(Ctx *ctx, int L, int nev, const double *d_evals, const double *d_evecs, double *d_r,
                      double *d_rmean, double *d_s1p, double *d_se, cudaStream_t st);
+// S^E of nev vectors (L <= 16, nev <= 64) on a static device scratch, no allocation (noalloc.cu)
+void noalloc_setup(int device);
+void entanglement_noalloc(Ctx *ctx, int L, int nev, const double *d_evecs, double *d_se, cudaStream_t st);
 
 }  // namespace mbl
