@@ -1,19 +1,24 @@
 """Benchmark: converged eigenpairs per second near a target energy density, L = 18.
 
 Workload (the L = 18 shift-invert configuration): dim 48 620, nev = 50 eigenpairs nearest
-sigma = E_min + eps (E_max - E_min), h in {0.5, 1, 2, 3, 4, 5}, eps in {0.1, 0.5, 0.9}.  One step
-is one batch of `--batch` jobs (L, h, seed, eps) run through the whole path: sector build
-(fields, basis, CSR), extremal bounds, numeric factorization (FP32 fronts, FP64 refinement),
-block shift-invert Lanczos, Rayleigh-Ritz on H, observables.  The symbolic analysis of the L = 18
-pattern is setup (built once in warm-up, excluded).  Metric: sum of converged eigenpairs
-(residual <= 1e-10 ||H||) divided by the timed device span.
+sigma = E_min + eps (E_max - E_min), h in {0.5, 1, 2, 3, 4, 5}, eps in {0.1, 0.5, 0.9}.  A step is
+one batch of `--batch` jobs (L, h, seed, eps) run through the whole path: sector build from the
+job's fields, extremal bounds, numeric factorization (FP32 fronts on tcgen05, FP64 refinement),
+block shift-invert Lanczos, Rayleigh-Ritz on H, observables.  The timed region runs all K steps'
+jobs in the served form (continuous batching on `--slots` worker streams with HBM admission): the
+value is the converged eigenpairs (residual <= 1e-10 ||H||) over the device span of those jobs
+(CUDA events).  The same jobs then run one after another on one stream for the kernel profile and
+the roofline, and a subset runs on the plain FP64 path for the mixed-versus-FP64 comparison.  The
+symbolic analysis of the L = 18 pattern is setup (built once in warm-up, excluded).
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--batch B] [--impl reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--batch B] [--slots S] [--impl reference]
+    python bench.py --case {factor,solve} [--L L] [--reps R] [--precision fp32|fp64]   (profiler cases)
 """
 from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -29,7 +34,8 @@ NEV = 50
 HS = [0.5, 1.0, 2.0, 3.0, 4.0, 5.0]
 EPS = [0.1, 0.5, 0.9]
 PROF_KEYS = ("factor_fp32", "schur_fp32", "schur_tc", "trisolve_fp32", "refine_spmv", "orth", "syev_krylov",
-             "syev_rr", "extremal_bounds", "op_apply", "ks_restart", "ritz_h", "observables", "sector_build")
+             "syev_rr", "extremal_bounds", "op_apply", "ks_restart", "ritz_h", "observables", "sector_build",
+             "syev_fp32", "syev_fallback", "oa_refine", "trisolve_fp64", "factor_fp64")
 METRIC = "eigenpairs/s near eps (res<=1e-10||H||), L=18, mixed vs FP64; p50/p99 latency"
 
 
@@ -167,11 +173,15 @@ def run_case(args):
     sec = g.build_sector(ctx, args.L, 3.0, 5)
     lo, hi = g.extremal_bounds(sec)
     prec = g.MBL_PREC_FP64 if args.precision == "fp64" else g.MBL_PREC_FP32
-    f = g.factor(sec, lo + 0.5 * (hi - lo), precision=prec, tensor_cores=args.tensor_cores)
-    B = np.random.default_rng(0).standard_normal((sec.dim, 8))
     import torch
 
     nvtx = getattr(torch.cuda, "nvtx", None)
+    if nvtx is not None:
+        nvtx.range_push("factor")
+    f = g.factor(sec, lo + 0.5 * (hi - lo), precision=prec, tensor_cores=args.tensor_cores)
+    if nvtx is not None:
+        nvtx.range_pop()
+    B = np.random.default_rng(0).standard_normal((sec.dim, 8))
     t0 = time.perf_counter()
     if nvtx is not None:
         nvtx.range_push("solve")
@@ -195,12 +205,12 @@ def main():
     ap.add_argument("--L", type=int, default=18)
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
-    ap.add_argument("--tensor-cores", type=int, default=0)
+    ap.add_argument("--tensor-cores", type=int, default=1)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--batch", type=int, default=6)
-    ap.add_argument("--e2e-stride", type=int, default=3)
+    ap.add_argument("--slots", type=int, default=4, help="concurrent jobs (worker streams) in the timed region")
     ap.add_argument("--impl", default="gb300")
     ap.add_argument("--fp64-stride", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -254,42 +264,45 @@ def main():
     if dist:
         dist.barrier()
 
-    # ---- device-resident timed region ----
-    ctx.set_profiling(True)
-    l0 = g.launch_count()
+    timed_jobs = [j for s in range(args.steps) for j in jobs_for_step(args.warmup + s, args.batch, rank, world)]
     clocks = ClockSampler(os.path.join(ROOT, "gpurun_out", "clocks_bench.csv") if os.path.isdir(
         os.path.join(ROOT, "gpurun_out")) else "/tmp/clocks_bench.csv")
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    pairs, lat = 0, []
-    timed_jobs = [j for s in range(args.steps) for j in jobs_for_step(args.warmup + s, args.batch, rank, world)]
-    job_ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(timed_jobs) + 1)]
-    job_pairs, job_stats = [], []
-    ev_mixed = torch.empty((len(timed_jobs), NEV), dtype=torch.float64, device="cuda")
     nvtx = getattr(torch.cuda, "nvtx", None)
+
+    # ---- timed region: the served (continuously batched) form, all K steps' jobs in flight ----
+    # Jobs run on `slots` worker streams as HBM allows; the span is measured on the device with the
+    # jobs' CUDA events (first start to last end, relative to one reference event).
+    # the jobs' inputs: their disorder realizations h_i (host arrays, prepared untimed)
+    host_fields = []
+    for (h, seed, eps) in timed_jobs:
+        sec0 = g.build_sector(ctx, L, h, seed)
+        host_fields.append(np.ascontiguousarray(sec0.fields()))
+        sec0.close()
+    srv = g.Server(ctx, slots=args.slots)
+    for t in [srv.submit(L, h, seed, eps, NEV) for (h, seed, eps) in jobs_for_step(0, args.slots, rank, world)]:
+        srv.wait(t)  # worker warm-up: kernels loaded, graphs captured once per worker
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    l0 = g.launch_count()
     with clocks:
         torch.cuda.synchronize()
         if nvtx is not None:
             nvtx.range_push("timed")
-        e0.record()
-        for i, (h, seed, eps) in enumerate(timed_jobs):
-            job_ev[i].record()
-            t0 = time.perf_counter()
-            nc, st = device_job(h, seed, eps, g.MBL_PREC_FP32)
-            lat.append(time.perf_counter() - t0)
-            pairs += nc
-            job_pairs.append(nc)
-            job_stats.append(st)
-            ev_mixed[i].copy_(d_ev)
-        job_ev[-1].record()
-        e1.record()
+        t_host0 = time.perf_counter()
+        tickets = [srv.submit(L, h, seed, eps, NEV, want_vectors=True, fields=hf)
+                   for (h, seed, eps), hf in zip(timed_jobs, host_fields)]
+        served = [srv.wait(t) for t in tickets]
         torch.cuda.synchronize()
+        t_host = time.perf_counter() - t_host0
         if nvtx is not None:
             nvtx.range_pop()
-    ms = e0.elapsed_time(e1)
-    job_ms = [job_ev[i].elapsed_time(job_ev[i + 1]) for i in range(len(timed_jobs))]
     launches = g.launch_count() - l0
-    prof = {k: ctx.profile(k) for k in PROF_KEYS}
-    ctx.set_profiling(False)
+    srv_stats = srv.stats()
+    srv.stop()
+    ms = max(r.d_end_ms for r in served) - min(r.d_start_ms for r in served)
+    pairs = sum(r.nconv for r in served)
+    lat = [(r.t_end_ms - r.t_submit_ms) / 1e3 for r in served]
     tmax = ms
     if dist:
         t = torch.tensor([ms, pairs], dtype=torch.float64, device="cuda")
@@ -298,6 +311,26 @@ def main():
         dist.all_reduce(tt, op=dist.ReduceOp.SUM)
         tmax, pairs = float(t[0]), int(tt[0])
     value = pairs / (tmax / 1e3)
+
+    # ---- the same jobs one after another on one stream (profiled): kernel breakdown, roofline ----
+    ctx.set_profiling(True)
+    job_ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(timed_jobs) + 1)]
+    job_pairs, job_stats = [], []
+    ev_mixed = torch.empty((len(timed_jobs), NEV), dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    for i, (h, seed, eps) in enumerate(timed_jobs):
+        job_ev[i].record()
+        nc, st = device_job(h, seed, eps, g.MBL_PREC_FP32)
+        job_pairs.append(nc)
+        job_stats.append(st)
+        ev_mixed[i].copy_(d_ev)
+    job_ev[-1].record()
+    torch.cuda.synchronize()
+    job_ms = [job_ev[i].elapsed_time(job_ev[i + 1]) for i in range(len(timed_jobs))]
+    prof = {k: ctx.profile(k) for k in PROF_KEYS}
+    ctx.set_profiling(False)
+    sequential = {"value": sum(job_pairs) / (sum(job_ms) / 1e3), "unit": "eigenpairs/s",
+                  "ms_per_job": sum(job_ms) / len(job_ms)}
 
     # ---- the plain FP64 GPU path on a subset of the same jobs (every third one: all h and eps) ----
     sub = list(range(0, len(timed_jobs), max(1, args.fp64_stride)))
@@ -324,7 +357,8 @@ def main():
         fp64 = {"value": p64 / (t64 / 1e3), "unit": "eigenpairs/s", "jobs": len(sub),
                 "ms_per_job": t64 / len(sub), "factor_ms_per_job": f64["ms"] / max(1, f64["launches"]),
                 "mixed_same_jobs": {"value": p_mixed / (t_mixed / 1e3), "ms_per_job": t_mixed / len(sub)},
-                "mixed_over_fp64": (p_mixed / t_mixed) / max(p64 / t64, 1e-30)}
+                "mixed_over_fp64": (p_mixed / t_mixed) / max(p64 / t64, 1e-30),
+                "served_mixed_over_fp64": value / max(p64 / (t64 / 1e3), 1e-30)}
         torch.cuda.synchronize()
         # per result: mixed-precision eigenvalues against the FP64 path's, relative to ||H|| ~ |E| scale
         for i in sub:
@@ -335,31 +369,15 @@ def main():
             d = (ev_mixed[i] - ev64[i]).abs().max().item()
             job_stats[i]["max_dev_vs_fp64"] = d / max(abs(lo), abs(hi))
 
-    # ---- end to end through the host API: host fields in, host eigenpairs and observables out ----
-    e2e_idx = list(range(0, len(timed_jobs), max(1, args.e2e_stride)))
-    e2e_jobs = [timed_jobs[i] for i in e2e_idx]
-    host_fields = []
-    for (h, seed, eps) in e2e_jobs:  # the jobs' inputs (disorder realizations), prepared untimed
-        sec0 = g.build_sector(ctx, L, h, seed)
-        host_fields.append(np.ascontiguousarray(sec0.fields()))
-        sec0.close()
-    torch.cuda.synchronize()
-    t_e2e0 = time.perf_counter()
-    e_pairs = 0
-    h2d = d2h = 0
-    for (h, seed, eps), hf in zip(e2e_jobs, host_fields):
-        sec = g.build_sector_fields(ctx, L, hf, 1.0)
-        res = g.solve_near(sec, eps, NEV)
-        r, rm, s1, se = g.observables(ctx, L, res.evals, res.evecs)
-        sec.close()
-        e_pairs += res.nconv
-        h2d += hf.nbytes + res.evals.nbytes + res.evecs.nbytes
-        d2h += res.evals.nbytes + res.evecs.nbytes + res.resid.nbytes + r.nbytes + 8 + s1.nbytes + se.nbytes
-    e2e_s = time.perf_counter() - t_e2e0
-    ne = len(e2e_jobs)
-    e2e = {"value": e_pairs / e2e_s, "unit": "eigenpairs/s", "h2d_bytes_per_step": h2d * args.batch // ne,
-           "d2h_bytes_per_step": d2h * args.batch // ne, "jobs": ne,
-           "device_same_jobs": sum(job_pairs[i] for i in e2e_idx) / (sum(job_ms[i] for i in e2e_idx) / 1e3)}
+    # ---- end to end: the timed served region itself, on the host clock (host fields in; eigenvalues,
+    # residuals, observables and eigenvectors back in host memory) ----
+    n_dim = math.comb(L, L // 2)
+    h2d_job = L * 8
+    d2h_job = 8 * (NEV * 4 + (NEV - 2) + n_dim * NEV)
+    e2e = {"value": pairs / t_host, "unit": "eigenpairs/s", "h2d_bytes_per_step": h2d_job * args.batch,
+           "d2h_bytes_per_step": d2h_job * args.batch,
+           "note": "host wall time of the timed served region; inputs h_i copied from host memory per job, "
+                   "eigenvalues, residuals, observables and eigenvectors copied back"}
 
     # ---- roofline of the dominant kernel class ----
     peaks = measured_peaks()
@@ -397,13 +415,18 @@ def main():
             "warmup": args.warmup, "ms_per_step": tmax / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32 fronts + f64 refinement", "data": "synthetic",
             "config": {"workload": "L=18 shift-invert: dim 48620, nev=50, h in {0.5,1,2,3,4,5}, eps in "
-                                   "{0.1,0.5,0.9}, seeds 1000+k", "L": L, "nev": NEV, "jobs_per_step": args.batch,
+                                   "{0.1,0.5,0.9}, seeds 1000+k; served on worker streams", "L": L, "nev": NEV,
+                       "jobs_per_step": args.batch, "slots": args.slots,
                        "parallelism": f"replicas x{world}", "l2": "working set (factor ~0.5 GB, fronts ~3 GB) "
                                                                   "far above the 129 MB L2"},
             "gpu_launches": launches,
             "clocks": clocks.summary(local),
             "latency_ms": {"p50": lat_ms[len(lat_ms) // 2], "p99": lat_ms[min(len(lat_ms) - 1,
-                                                                              int(0.99 * len(lat_ms)))]},
+                                                                              int(0.99 * len(lat_ms)))],
+                           "note": "submission to completion; all timed jobs submitted at once"},
+            "served": {"slots": args.slots, "host_s": t_host, "peak_reserved_gb": srv_stats["peak_reserved_bytes"] / 1e9,
+                       "budget_gb": srv_stats["budget_bytes"] / 1e9},
+            "sequential": sequential,
             "fp64_path": fp64,
             "per_job": [{"h": j[0], "seed": j[1], "eps": j[2], "nconv": job_pairs[i], "ms": round(job_ms[i], 1),
                          "max_resid_rel": job_stats[i]["max_resid"], "restarts": job_stats[i]["restarts"],

@@ -64,7 +64,7 @@ typedef struct mbl_opts {
     double refine_tol;    /* refinement stop: ||b - A x|| <= refine_tol (|A||x| + |b|)[1e-15]*/
     int max_refine;       /* refinement steps per application                       [20]   */
     uint64_t start_seed;  /* seed of the random start block                         [12345]*/
-    int tensor_cores;     /* FP32 fronts: Schur updates on tcgen05 (3xTF32) if nonzero [0]   */
+    int tensor_cores;     /* FP32 fronts: Schur updates on tcgen05 (3xTF32) if nonzero [1]   */
     int refine_mode;      /* 0: plain iterative refinement, 1: FGMRES with the factor as    */
                           /*    right preconditioner (FP64 Arnoldi per right-hand side)  [1]   */
 } mbl_opts;
@@ -214,6 +214,7 @@ typedef struct mbl_request {
     int L;            /* even, 2..22 */
     double h;         /* disorder strength, fields from the seeded stream (as mbl_build_sector) */
     uint64_t seed;
+    const double *fields; /* optional h_i[L] (host, copied at submission; J = 1) instead of (h, seed) */
     double eps;       /* target energy density in [0, 1] */
     int nev;
     int precision;    /* MBL_PREC_FP32 (mixed) or MBL_PREC_FP64 */
@@ -223,13 +224,16 @@ typedef struct mbl_request {
 /* Filled by mbl_poll / mbl_wait.  The array fields are caller-owned outputs set before the call
  * (NULL = not wanted): evals[nev], resid[nev], r[nev-2], s1p[nev], se[nev], evecs[dim*nev]
  * (column-major; only if the request had want_vectors).  Times are host milliseconds since
- * mbl_server_start: submission, admission (HBM reserved, solve starts), completion. */
+ * mbl_server_start: submission, admission (HBM reserved, solve starts), completion; d_start_ms and
+ * d_end_ms are the device-side (CUDA event) start and end of the job's work on its worker stream,
+ * in milliseconds after an event recorded on the context stream at mbl_server_start. */
 typedef struct mbl_result {
     int status;       /* MBL_OK, MBL_ERR_NOT_CONVERGED (partial), or the job's error */
     int nconv, nev, L;
     int64_t dim;
     double sigma, r_mean;
     double t_submit_ms, t_admit_ms, t_end_ms;
+    double d_start_ms, d_end_ms;
     size_t reserved_bytes;
     double *evals, *resid, *r, *s1p, *se, *evecs;
 } mbl_result;

@@ -295,6 +295,8 @@ class ServedResult:
     t_submit_ms: float
     t_admit_ms: float
     t_end_ms: float
+    d_start_ms: float
+    d_end_ms: float
     reserved_bytes: int
 
 
@@ -314,8 +316,15 @@ class Server:
         _check(_lib().mbl_server_start(ctx.handle, slots, hbm_budget_bytes), ctx.handle)
 
     def submit(self, L: int, h: float, seed: int, eps: float, nev: int, precision: int = MBL_PREC_FP32,
-               want_vectors: bool = False) -> int:
-        q = _capi.Request(L, float(h), seed, float(eps), nev, precision, 1 if want_vectors else 0)
+               want_vectors: bool = False, fields: np.ndarray | None = None) -> int:
+        """Queue a job; `fields` (h_i, length L) replaces the seeded disorder of (h, seed)."""
+        fp = None
+        if fields is not None:
+            fields = np.ascontiguousarray(fields, dtype=np.float64)
+            if fields.shape != (L,):
+                raise ValueError("fields must have length L")
+            fp = _ptr(fields)
+        q = _capi.Request(L, float(h), seed, fp, float(eps), nev, precision, 1 if want_vectors else 0)
         t = ctypes.c_uint64()
         _check(_lib().mbl_submit(self.ctx.handle, ctypes.byref(q), ctypes.byref(t)), self.ctx.handle)
         self._req[t.value] = (L, nev, want_vectors)
@@ -340,7 +349,8 @@ class Server:
         if rc not in (_capi.MBL_OK, _capi.MBL_ERR_NOT_CONVERGED):
             _check(rc, self.ctx.handle)
         return ServedResult(rc, out.nconv, out.L, out.dim, out.sigma, ev, rs, r[: max(nev - 2, 0)], out.r_mean, s1,
-                            se, V, out.t_submit_ms, out.t_admit_ms, out.t_end_ms, out.reserved_bytes)
+                            se, V, out.t_submit_ms, out.t_admit_ms, out.t_end_ms, out.d_start_ms, out.d_end_ms,
+                            out.reserved_bytes)
 
     def poll(self, ticket: int):
         """The result if finished, else None (non-blocking)."""

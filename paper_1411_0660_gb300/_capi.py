@@ -41,14 +41,15 @@ class SolveStats(ctypes.Structure):
 
 
 class Request(ctypes.Structure):
-    _fields_ = [("L", c_int), ("h", c_double), ("seed", c_uint64), ("eps", c_double), ("nev", c_int),
-                ("precision", c_int), ("want_vectors", c_int)]
+    _fields_ = [("L", c_int), ("h", c_double), ("seed", c_uint64), ("fields", c_void_p), ("eps", c_double),
+                ("nev", c_int), ("precision", c_int), ("want_vectors", c_int)]
 
 
 class Result(ctypes.Structure):
     _fields_ = [("status", c_int), ("nconv", c_int), ("nev", c_int), ("L", c_int), ("dim", c_int64),
                 ("sigma", c_double), ("r_mean", c_double), ("t_submit_ms", c_double), ("t_admit_ms", c_double),
-                ("t_end_ms", c_double), ("reserved_bytes", c_size_t), ("evals", c_void_p), ("resid", c_void_p),
+                ("t_end_ms", c_double), ("d_start_ms", c_double), ("d_end_ms", c_double),
+                ("reserved_bytes", c_size_t), ("evals", c_void_p), ("resid", c_void_p),
                 ("r", c_void_p), ("s1p", c_void_p), ("se", c_void_p), ("evecs", c_void_p)]
 
 

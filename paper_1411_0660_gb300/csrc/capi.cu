@@ -233,7 +233,7 @@ void mbl_opts_default(mbl_opts *o) {
     o->refine_tol = 1e-15;
     o->max_refine = 20;
     o->start_seed = 12345;
-    o->tensor_cores = 0;
+    o->tensor_cores = 1;
     o->refine_mode = 1;
 }
 

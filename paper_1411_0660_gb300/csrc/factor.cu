@@ -368,6 +368,27 @@ __device__ __forceinline__ int find_sdesc(const SolveDesc *d, int nd, int64_t b)
     return lo;
 }
 
+__device__ __forceinline__ int find_sdesc_k(const SolveDesc *d, int nd, int64_t b) {
+    int lo = 0, hi = nd - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (d[mid].offk <= b) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// shared <- global copies that do not hold up the issuing thread (sm_80+ cp.async)
+template <class T>
+__device__ __forceinline__ void cp_async_elem(T *smem, const T *gmem) {
+    const unsigned int sa = (unsigned int)__cvta_generic_to_shared(smem);
+    if (sizeof(T) == 8) asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gmem) : "memory");
+    else asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
 __device__ __forceinline__ int find_sdesc_b(const SolveDesc *d, int nd, int64_t b) {
     int lo = 0, hi = nd - 1;
     while (lo < hi) {
@@ -508,8 +529,8 @@ __global__ void __launch_bounds__(256) k_apply_m(const SolveDesc *sdescs, int nd
 // [32 j, 32 j + 32) of the panel; the eight partial sums meet in shared memory.
 template <class T, int PB>
 __global__ void __launch_bounds__(256) k_fwd_step(const SolveDesc *sdescs, int nd, const int64_t *fo,
-                                                  const int64_t *zo, const int32_t *fsz, const T *arena, T *Z, T *Zs,
-                                                  int p) {
+                                                  const int64_t *zo, const int32_t *fsz, const int32_t *sn_start,
+                                                  const T *arena, const T *Dg, T *Z, T *Zs, T *yfw, int p) {
     extern __shared__ __align__(16) unsigned char smraw[];
     T *zp = reinterpret_cast<T *>(smraw);  // SPW x PB; afterwards the 8 x PB x RBF partials
     pdl_trigger();
@@ -565,8 +586,14 @@ __global__ void __launch_bounds__(256) k_fwd_step(const SolveDesc *sdescs, int n
 #pragma unroll
         for (int j = 0; j < 8; ++j) v += red[(j * PB + q) * RBF + i];
         const int rr = r0 + i;
-        if (rr < w) Zs[(zb + rr) * p + q] = v;
-        else Z[(zb + rr) * p + q] -= v;
+        if (rr < w) {
+            // a panel row is final here: also its diagonal-scaled value for the backward sweep
+            const int64_t gr = (int64_t)sn_start[s] + k0 + rr;
+            Zs[(zb + rr) * p + q] = v;
+            yfw[gr * p + q] = v / Dg[gr];
+        } else {
+            Z[(zb + rr) * p + q] -= v;
+        }
     }
 }
 
@@ -594,21 +621,6 @@ __global__ void k_fwd_gather_rows(int64_t nrows, const int64_t *dst, const int64
 }
 
 template <class T>
-__global__ void k_fwd_finish(const AsmItem *items, const int64_t *zo, const int32_t *nc, const int32_t *sn_start,
-                             const T *Dg, const T *Zs, T *yfw, int p) {
-    pdl_trigger();
-    AsmItem it = items[blockIdx.x];
-    const int s = it.front, r0 = it.c0, r1 = min(nc[s], r0 + ACOLS);
-    const T *z = Zs + zo[s] * p;
-    pdl_wait();
-    for (int idx = threadIdx.x; idx < (r1 - r0) * p; idx += blockDim.x) {
-        int r = r0 + idx / p, q = idx % p;
-        int64_t g = (int64_t)sn_start[s] + r;
-        yfw[g * p + q] = z[(int64_t)r * p + q] / Dg[g];
-    }
-}
-
-template <class T>
 __global__ void k_bwd_gather(const AsmItem *items, const int64_t *zo, const int32_t *fsz, const int32_t *nc,
                              const int32_t *sn_start, const int64_t *rows_off, const int32_t *rows, const T *yfw,
                              const T *x, T *Z, int p) {
@@ -624,22 +636,24 @@ __global__ void k_bwd_gather(const AsmItem *items, const int64_t *zo, const int3
     }
 }
 
-// Backward solve step, tiles of RBB rows x RBB columns of G = [M; L21 M] (grid: row tiles x column
-// chunks): x_panel = G^T v with v = [y_panel; -x_below].  Each tile writes its partial sums; the
-// last tile of a (panel, column chunk) to finish (counted with an atomic, after a fence) adds the
-// partials in tile order and writes the panel's x into Zs, then re-arms the counter.  The panel's
-// rows of Z hold the forward result y (pivoted order); rows below the panel come from Zs (fully
-// summed rows solved by later panels) or Z (the ancestors' x).
+// Backward solve step, blocks of RBK rows x RBB columns of G = [M; L21 M] (grid: row blocks x
+// column chunks): x_panel = G^T v with v = [y_panel; -x_below].  The block of G is copied to shared
+// memory asynchronously before waiting for the previous step (G does not change during a solve).
+// Each block writes its partial sums; the last block of a (panel, column chunk) to finish (counted
+// with an atomic, after a fence) adds the partials in block order, writes the panel's x into Zs
+// and re-arms the counter.  The panel's rows of Z hold the forward result y (pivoted order); rows
+// below the panel come from Zs (fully summed rows solved by later panels) or Z (the ancestors' x).
 template <class T, int PB>
 __global__ void __launch_bounds__(256) k_bwd_step(const SolveDesc *sdescs, int nd, const int64_t *fo,
                                                   const int64_t *zo, const int32_t *fsz, const int32_t *nc,
-                                                  const T *arena, const T *Z, T *Zs, T *P, unsigned int *cnt, int p) {
+                                                  const int32_t *sn_start, const T *arena, const T *Z, T *Zs, T *P,
+                                                  unsigned int *cnt, T *x, int p) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    T(*Gs)[RBB + 1] = reinterpret_cast<T(*)[RBB + 1]>(smraw);   // RBB x (RBB + 1)
-    T *vs = reinterpret_cast<T *>(smraw + sizeof(T) * RBB * (RBB + 1));  // RBB x PB
+    T *Gs = reinterpret_cast<T *>(smraw);  // RBK x (RBB + 1), row-major
+    T *vs = Gs + RBK * (RBB + 1);          // RBK x PB
     __shared__ int s_last;
     pdl_trigger();
-    const int di = find_sdesc_b(sdescs, nd, blockIdx.x);
+    const int di = find_sdesc_k(sdescs, nd, blockIdx.x);
     const SolveDesc d = sdescs[di];
     const int cc = blockIdx.y * RBB;
     if (cc >= d.w) {
@@ -647,20 +661,21 @@ __global__ void __launch_bounds__(256) k_bwd_step(const SolveDesc *sdescs, int n
         return;
     }
     const int s = d.front, f = fsz[s], k0 = d.k0, w = d.w, ncs = nc[s];
-    const int b = (int)(blockIdx.x - d.offb);
-    const int nb = (w + d.m2 + RBB - 1) / RBB;
-    const int r0 = b * RBB;  // relative to k0
-    const int nr = min(RBB, w + d.m2 - r0);
+    const int b = (int)(blockIdx.x - d.offk);
+    const int nb = (w + d.m2 + RBK - 1) / RBK;
+    const int r0 = b * RBK;  // relative to k0
+    const int nr = min(RBK, w + d.m2 - r0);
     const int wc = min(RBB, w - cc);
     const int64_t zb = zo[s] + k0;
-    const T *F = arena + fo[s];
-    // the tile of G does not depend on the previous step: load it before waiting
-    for (int idx = threadIdx.x; idx < RBB * RBB; idx += blockDim.x) {
-        const int i = idx % RBB, c = idx / RBB;
-        Gs[i][c] = (i < nr && c < wc) ? F[(int64_t)(k0 + cc + c) * f + k0 + r0 + i] : T(0);
+    const T *F = arena + fo[s] + (int64_t)(k0 + cc) * f + k0 + r0;
+    for (int idx = threadIdx.x; idx < RBK * RBB; idx += blockDim.x) {
+        const int i = idx % RBK, c = idx / RBK;
+        T *dst = Gs + i * (RBB + 1) + c;
+        if (i < nr && c < wc) cp_async_elem(dst, F + (int64_t)c * f + i);
+        else *dst = T(0);
     }
     pdl_wait();
-    for (int idx = threadIdx.x; idx < RBB * PB; idx += blockDim.x) {
+    for (int idx = threadIdx.x; idx < RBK * PB; idx += blockDim.x) {
         const int i = idx / PB, q = idx % PB;
         T v = T(0);
         if (i < nr && q < p) {
@@ -671,20 +686,22 @@ __global__ void __launch_bounds__(256) k_bwd_step(const SolveDesc *sdescs, int n
         }
         vs[idx] = v;
     }
+    cp_async_wait_all();
     __syncthreads();
     constexpr int QP = PB / 4;
     const int c = threadIdx.x % RBB, qg = threadIdx.x / RBB;
     T acc[QP];
 #pragma unroll
     for (int k = 0; k < QP; ++k) acc[k] = T(0);
+    const int nrr = (nr + 7) & ~7;  // padded rows of Gs and vs are zero
 #pragma unroll 8
-    for (int i = 0; i < RBB; ++i) {
-        const T gv = Gs[i][c];
+    for (int i = 0; i < nrr; ++i) {
+        const T gv = Gs[i * (RBB + 1) + c];
 #pragma unroll
         for (int k = 0; k < QP; ++k) acc[k] += gv * vs[i * PB + qg + 4 * k];
     }
     const int64_t tile = (int64_t)RBB * PB;
-    T *out = P + ((d.offb + b) * SUBS + blockIdx.y) * tile;
+    T *out = P + ((d.offk + b) * SUBS + blockIdx.y) * tile;
 #pragma unroll
     for (int k = 0; k < QP; ++k) out[(qg + 4 * k) * RBB + c] = acc[k];
     __threadfence();
@@ -696,7 +713,7 @@ __global__ void __launch_bounds__(256) k_bwd_step(const SolveDesc *sdescs, int n
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    const T *src0 = P + (d.offb * SUBS + blockIdx.y) * tile;
+    const T *src0 = P + (d.offk * SUBS + blockIdx.y) * tile;
     for (int o = threadIdx.x; o < wc * p; o += blockDim.x) {
         const int cq = o % wc, q = o / wc;
         const T *src = src0 + q * RBB + cq;
@@ -708,23 +725,11 @@ __global__ void __launch_bounds__(256) k_bwd_step(const SolveDesc *sdescs, int n
             for (int u = 0; u < 4; ++u) v4[u] += __ldcg(src + (int64_t)(bb + u) * stride);
         }
         for (; bb < nb; ++bb) v4[0] += __ldcg(src + (int64_t)bb * stride);
-        Zs[(zb + cc + cq) * p + q] = (v4[0] + v4[1]) + (v4[2] + v4[3]);
+        const T xv = (v4[0] + v4[1]) + (v4[2] + v4[3]);
+        Zs[(zb + cc + cq) * p + q] = xv;
+        x[((int64_t)sn_start[s] + k0 + cc + cq) * p + q] = xv;
     }
     if (threadIdx.x == 0) cnt[(size_t)di * SUBS + blockIdx.y] = 0u;
-}
-
-template <class T>
-__global__ void k_bwd_finish(const AsmItem *items, const int64_t *zo, const int32_t *nc, const int32_t *sn_start,
-                             const T *Z, T *x, int p) {
-    pdl_trigger();
-    AsmItem it = items[blockIdx.x];
-    const int s = it.front, r0 = it.c0, r1 = min(nc[s], r0 + ACOLS);
-    const T *z = Z + zo[s] * p;
-    pdl_wait();
-    for (int idx = threadIdx.x; idx < (r1 - r0) * p; idx += blockDim.x) {
-        int r = r0 + idx / p, q = idx % p;
-        x[((int64_t)sn_start[s] + r) * p + q] = z[(int64_t)r * p + q];
-    }
 }
 
 // ------------------------------------------------------------------------------------------
@@ -739,7 +744,7 @@ static size_t apply_m_smem() { return sizeof(T) * ((size_t)RBB * (SPW + 1) + (si
 template <class T, int PB>
 static size_t fwd_step_smem() { return sizeof(T) * (size_t)SPW * PB; }
 template <class T, int PB>
-static size_t bwd_step_smem() { return sizeof(T) * ((size_t)RBB * (RBB + 1) + (size_t)RBB * PB); }
+static size_t bwd_step_smem() { return sizeof(T) * ((size_t)RBK * (RBB + 1) + (size_t)RBK * PB); }
 static int rhs_pad(int p) { return p <= 8 ? 8 : (p <= 16 ? 16 : 32); }
 
 template <class T, int PB>
@@ -869,10 +874,9 @@ static void solve_levels(Factorization &fz, int p, cudaStream_t st) {
             const SolveStep &ss = pl.ssteps[si];
             const SolveDesc *sd = pl.d_sdescs.data() + ss.d0;
             launch_pdl(k_fwd_step<T, PB>, dim3((unsigned)ss.nrb), dim3(256), fsm, st, sd, ss.nd,
-                       pl.d_sn_fo.data(), pl.d_sn_zo.data(), pl.d_sn_f.data(), (const T *)arena, Z, Zs, p);
+                       pl.d_sn_fo.data(), pl.d_sn_zo.data(), pl.d_sn_f.data(), pl.d_sn_start.data(),
+                       (const T *)arena, (const T *)Dg, Z, Zs, yfw, p);
         }
-        launch_pdl(k_fwd_finish<T>, dim3(na), dim3(256), 0, st, items, pl.d_sn_zo.data(), pl.d_sn_nc.data(),
-                   pl.d_sn_start.data(), (const T *)Dg, (const T *)Zs, yfw, p);
     }
     for (int l = pl.nlevels - 1; l >= 0; --l) {
         int na = pl.asm_ptr[l + 1] - pl.asm_ptr[l];
@@ -883,12 +887,10 @@ static void solve_levels(Factorization &fz, int p, cudaStream_t st) {
         for (int si = pl.lvl_sstep_ptr[l + 1] - 1; si >= pl.lvl_sstep_ptr[l]; --si) {
             const SolveStep &ss = pl.ssteps[si];
             const SolveDesc *sd = pl.d_sdescs.data() + ss.d0;
-            launch_pdl(k_bwd_step<T, PB>, dim3((unsigned)ss.nrbb, SUBS), dim3(256), bsm, st, sd, ss.nd,
-                       pl.d_sn_fo.data(), pl.d_sn_zo.data(), pl.d_sn_f.data(), pl.d_sn_nc.data(), (const T *)arena,
-                       (const T *)Z, Zs, P, cnt + (size_t)ss.d0 * SUBS, p);
+            launch_pdl(k_bwd_step<T, PB>, dim3((unsigned)ss.nrbk, SUBS), dim3(256), bsm, st, sd, ss.nd,
+                       pl.d_sn_fo.data(), pl.d_sn_zo.data(), pl.d_sn_f.data(), pl.d_sn_nc.data(),
+                       pl.d_sn_start.data(), (const T *)arena, (const T *)Z, Zs, P, cnt + (size_t)ss.d0 * SUBS, y, p);
         }
-        launch_pdl(k_bwd_finish<T>, dim3(na), dim3(256), 0, st, items, pl.d_sn_zo.data(), pl.d_sn_nc.data(),
-                   pl.d_sn_start.data(), (const T *)Zs, y, p);
     }
 }
 
@@ -961,7 +963,7 @@ void Factorization::ensure_solve_work(int p) {
     zsolved.alloc(ctx, (size_t)pl.zwork_elems * p * es);
     ywork.alloc(ctx, (size_t)pl.n * p * es);
     yfw.alloc(ctx, (size_t)pl.n * p * es);
-    pwork.alloc(ctx, (size_t)std::max<int64_t>(pl.max_sstep_nrbb, 1) * SUBS * RBB * rhs_pad(p) * es);
+    pwork.alloc(ctx, (size_t)std::max<int64_t>(pl.max_sstep_nrbk, 1) * SUBS * RBB * rhs_pad(p) * es);
     work_p = p;
 }
 

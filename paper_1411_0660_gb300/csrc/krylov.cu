@@ -381,18 +381,23 @@ void KrylovSchur::ritz(cudaStream_t st, std::vector<double> &theta, std::vector<
         // FP32 reduction and QL, then two steps of FP64 refinement of the whole decomposition: a
         // thick restart keeps an invariant subspace of T, so the kept vectors must be accurate to
         // FP64 rounding (an FP32-accurate subspace would cap the attainable residuals near 1e-7)
-        syev_batched(1, eigM.data(), eigOff.data(), eigOff.data(), eigA.data(), eigW.data(), 1, nullptr, ldv,
-                     eigWork.data(), eigInfo.data(), st, fp32);
+        {
+            ProfScope ps1(ctx, fp32 ? "syev_fp32" : "syev_fp64", (double)mm, st);
+            syev_batched(1, eigM.data(), eigOff.data(), eigOff.data(), eigA.data(), eigW.data(), 1, nullptr, ldv,
+                         eigWork.data(), eigInfo.data(), st, fp32);
+        }
         int info = 0;
         MBL_CUDA(cudaMemcpyAsync(&info, eigInfo.data(), sizeof(int), cudaMemcpyDeviceToHost, st));
         MBL_CUDA(cudaStreamSynchronize(st));
         if (fp32 && info != 0) {  // QL did not converge in FP32: redo in FP64
+            ProfScope ps2(ctx, "syev_fallback", (double)mm, st);
             k_pack_sym<<<nblk((int64_t)mm * mm), 256, 0, st>>>(T.data(), ldv, mm, eigA.data());
             MBL_LAUNCH_CHECK();
             syev_batched(1, eigM.data(), eigOff.data(), eigOff.data(), eigA.data(), eigW.data(), 1, nullptr, ldv,
                          eigWork.data(), eigInfo.data(), st, false);
         }
         if (fp32) {
+            ProfScope ps3(ctx, "oa_refine", (double)mm, st);
             double *X = eigA.data(), *G = NS1.data(), *Q = NS2.data(), *Sx = NS3.data();
             for (int it = 0; it < 2; ++it) {
                 gemm_small(true, false, mm, mm, mm, 1.0, X, mm, X, mm, 0.0, G, mm, st);
@@ -1016,7 +1021,7 @@ void solve_near(mbl_sector *sec, double eps, int nev, const mbl_opts &o, double 
     // convergence is decided by the Rayleigh-Ritz residuals on H.
     double screen = 1e-6;
     int restarts = 0, nc = 0;
-    double mxres = INFINITY;
+    double mxres = INFINITY, prev_rr = INFINITY;
     for (;; ++restarts) {
         while (!ks.full()) {
             ks.expand(opfn, st);
@@ -1048,6 +1053,10 @@ void solve_near(mbl_sector *sec, double eps, int nev, const mbl_opts &o, double 
             nc = rr.nconv;
             mxres = rr.maxres;
             if (mxres <= o.target_tol || last) break;
+            // every pair already meets the acceptance bound and the residuals stopped improving
+            // (less than 2x since the previous check): the attainable floor is reached
+            if (nc >= nev && prev_rr <= 2.0 * mxres) break;
+            prev_rr = mxres;
             screen = std::max(1e-14, std::min(screen, worst) * 0.01);
         }
         std::vector<int> keep(order.begin(), order.begin() + k_keep);

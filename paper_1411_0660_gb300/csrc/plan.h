@@ -39,7 +39,8 @@ struct PanelStep {
 };
 
 constexpr int RBF = 32;  // rows per CTA of a forward solve step
-constexpr int RBB = 64;  // rows (and columns) per tile of a backward solve step
+constexpr int RBB = 64;   // columns per chunk of a backward solve step; rows per CTA of the G = [M; L21 M] build
+constexpr int RBK = 256;  // rows per CTA of a backward solve step
 
 // One solve panel: columns [k0, k0 + w) of a front's fully-summed block (w <= SPW).  M (w x w) is
 // the composite of the factor panels' pivot permutations and unit-lower eliminations restricted
@@ -49,7 +50,8 @@ constexpr int RBB = 64;  // rows (and columns) per tile of a backward solve step
 struct SolveDesc {
     int32_t front, k0, w, m2;        // m2 = f - k0 - w rows below
     int64_t off;                     // prefix of forward row blocks (RBF rows of [k0, f)) in the step
-    int64_t offb;                    // prefix of backward row tiles (RBB rows of [k0, f)) in the step
+    int64_t offb;                    // prefix of RBB-row tiles of [k0, f) in the step (G build)
+    int64_t offk;                    // prefix of backward row blocks (RBK rows of [k0, f)) in the step
     int64_t moff;                    // offset (elements) of M while it is built
     int32_t fdesc[SUBS];             // factor descriptors of the sub-panels (-1 if absent)
 };
@@ -58,7 +60,8 @@ struct SolveStep {
     int32_t level;
     int32_t d0, nd;
     int64_t nrb;                     // forward row blocks in this step
-    int64_t nrbb;                    // backward row tiles in this step
+    int64_t nrbb;                    // RBB-row tiles in this step
+    int64_t nrbk;                    // backward row blocks in this step
 };
 
 struct AsmItem {     // assembly work item: columns [c0, c0 + ACOLS) of a front
@@ -92,7 +95,7 @@ struct Plan {
     // rows of the children's contribution blocks that land on it (children in tree order)
     std::vector<int64_t> lvl_fg_ptr;          // rows by level (nlevels + 1)
     std::vector<int64_t> fg_dst, fg_own, fg_cptr, fg_src;
-    int64_t m_elems = 0, max_sstep_nrbb = 0;
+    int64_t m_elems = 0, max_sstep_nrbb = 0, max_sstep_nrbk = 0;
     int64_t arena_elems = 0, zwork_elems = 0, wscratch_elems = 0, max_desc_per_step = 0;
     int64_t max_step_n2 = 0;
     int64_t nnz_l = 0;

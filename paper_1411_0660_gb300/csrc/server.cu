@@ -37,7 +37,7 @@ size_t job_bytes(const Plan &p, int nev, int block, int prec) {
     b += (double)p.arena_elems * es + n * (es + 4.0);                        // fronts, D, pivots
     b += (double)std::max<int64_t>(p.wscratch_elems, 1) * es + (double)p.m_elems * es;
     b += 2.0 * (double)p.zwork_elems * pb * es + 2.0 * n * pb * es;         // solve work
-    b += (double)p.max_sstep_nrbb * SUBS * RBB * pad * es;
+    b += (double)p.max_sstep_nrbk * SUBS * RBB * pad * es;
     b += 8.0 * n * (3.0 * ldv + 2.0 * nev + 30.0 * pb);                      // Krylov, Rayleigh-Ritz, refinement
     b += 8.0 * n * 480.0;                                                    // extremal-bounds Lanczos basis
     return (size_t)(1.10 * b) + ((size_t)64 << 20);
@@ -45,6 +45,7 @@ size_t job_bytes(const Plan &p, int nev, int block, int prec) {
 
 struct Job {
     mbl_request req{};
+    std::vector<double> fields;  // explicit disorder (copied at submission), empty = from (h, seed)
     int state = 0;  // 0 queued, 1 running, 2 done
     int status = MBL_OK;
     std::string err;
@@ -52,6 +53,7 @@ struct Job {
     int64_t dim = 0;
     double sigma = 0.0, r_mean = 0.0;
     double t_submit = 0.0, t_admit = 0.0, t_end = 0.0;
+    double d_start = 0.0, d_end = 0.0;  // device clock (CUDA events), ms after the server's reference event
     size_t reserved = 0;
     std::vector<double> evals, resid, r, s1p, se, evecs;
 };
@@ -72,6 +74,7 @@ struct Server {
     int running = 0;
     bool stop = false;
     std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
+    cudaEvent_t ref = nullptr;  // recorded at start on the parent stream: origin of the device times
 
     void worker(int i);
     void run(Job &J, mbl_ctx *w);
@@ -82,7 +85,8 @@ void Server::run(Job &J, mbl_ctx *w) {
     mbl_sector *sec = nullptr;
     bool held = false;
     try {
-        int rc = mbl_build_sector(w, q.L, q.h, q.seed, &sec);
+        int rc = J.fields.empty() ? mbl_build_sector(w, q.L, q.h, q.seed, &sec)
+                                  : mbl_build_sector_fields(w, q.L, J.fields.data(), 1.0, &sec);
         if (rc != MBL_OK) fail(rc, mbl_last_error(w));
         std::shared_ptr<Plan> plan = get_plan(sec);
         mbl_opts o;
@@ -103,6 +107,16 @@ void Server::run(Job &J, mbl_ctx *w) {
         const int64_t n = sec->n;
         const int nev = q.nev;
         J.dim = n;
+        struct EvPair {
+            cudaEvent_t a = nullptr, b = nullptr;
+            ~EvPair() {
+                if (a) cudaEventDestroy(a);
+                if (b) cudaEventDestroy(b);
+            }
+        } ev;
+        MBL_CUDA(cudaEventCreate(&ev.a));
+        MBL_CUDA(cudaEventCreate(&ev.b));
+        MBL_CUDA(cudaEventRecord(ev.a, w->stream));
         DVec<double> de, dv, dr, dobs;
         de.alloc(w, nev);
         dv.alloc(w, (size_t)n * nev);
@@ -118,7 +132,13 @@ void Server::run(Job &J, mbl_ctx *w) {
         double *d_r = dobs.data(), *d_rm = d_r + nev, *d_s1 = d_rm + 1, *d_se = d_s1 + nev;
         int rc2 = mbl_observables_dev(w, q.L, nev, de.data(), dv.data(), d_r, d_rm, d_s1, d_se, nullptr);
         if (rc2 != MBL_OK) fail(rc2, mbl_last_error(w));
+        MBL_CUDA(cudaEventRecord(ev.b, w->stream));
         MBL_CUDA(cudaStreamSynchronize(w->stream));
+        float ta = 0.f, tb = 0.f;
+        MBL_CUDA(cudaEventElapsedTime(&ta, ref, ev.a));
+        MBL_CUDA(cudaEventElapsedTime(&tb, ref, ev.b));
+        J.d_start = ta;
+        J.d_end = tb;
         J.nconv = nconv;
         J.sigma = sigma;
         J.evals.resize(nev);
@@ -193,6 +213,7 @@ void server_shutdown(Ctx *ctx) {
     s->cv_mem.notify_all();
     for (auto &th : s->threads) th.join();
     for (mbl_ctx *w : s->wctx) mbl_ctx_destroy(w);
+    if (s->ref) cudaEventDestroy(s->ref);
     ctx->server = nullptr;
     delete s;
 }
@@ -219,6 +240,8 @@ void fill_result(const Job &J, mbl_result *out) {
     out->t_submit_ms = J.t_submit;
     out->t_admit_ms = J.t_admit;
     out->t_end_ms = J.t_end;
+    out->d_start_ms = J.d_start;
+    out->d_end_ms = J.d_end;
     out->reserved_bytes = J.reserved;
     auto put = [](double *dst, const std::vector<double> &v) {
         if (dst && !v.empty()) std::copy(v.begin(), v.end(), dst);
@@ -255,6 +278,9 @@ int mbl_server_start(mbl_ctx *ctx, int slots, size_t budget_bytes) {
             w->plans = ctx->plans;
             s->wctx.push_back(w);
         }
+        MBL_CUDA(cudaEventCreate(&s->ref));
+        MBL_CUDA(cudaEventRecord(s->ref, ctx->stream));
+        MBL_CUDA(cudaEventSynchronize(s->ref));
         Server *raw = s.release();
         ctx->server = raw;
         for (int i = 0; i < slots; ++i) raw->threads.emplace_back([raw, i] { raw->worker(i); });
@@ -277,6 +303,8 @@ int mbl_submit(mbl_ctx *ctx, const mbl_request *req, uint64_t *ticket) {
         return srv_report(ctx, MBL_ERR_INVALID, "unknown precision");
     auto J = std::make_unique<Job>();
     J->req = *req;
+    if (req->fields) J->fields.assign(req->fields, req->fields + req->L);
+    J->req.fields = nullptr;
     {
         std::lock_guard<std::mutex> lk(s->mu);
         J->t_submit = now_ms(s->t0);

@@ -533,7 +533,7 @@ std::shared_ptr<Plan> build_plan(int L, const std::vector<uint32_t> &states, con
         p.lvl_step_ptr[l + 1] = (int32_t)p.steps.size();
         // solve schedule: SPW-wide panels
         for (int32_t ks = 0; ks * SPW < maxnc; ++ks) {
-            SolveStep ss{l, (int32_t)p.sdescs.size(), 0, 0, 0};
+            SolveStep ss{l, (int32_t)p.sdescs.size(), 0, 0, 0, 0};
             for (int32_t q = p.lvl_ptr[l]; q < p.lvl_ptr[l + 1]; ++q) {
                 int32_t s = p.lvl_fronts[q];
                 int32_t k0 = ks * SPW;
@@ -546,6 +546,7 @@ std::shared_ptr<Plan> build_plan(int L, const std::vector<uint32_t> &states, con
                 sd.m2 = p.sn_f[s] - k0 - w;
                 sd.off = ss.nrb;
                 sd.offb = ss.nrbb;
+                sd.offk = ss.nrbk;
                 sd.moff = p.m_elems;
                 for (int u = 0; u < SUBS; ++u) {
                     int32_t kk = (k0 + u * NB) / NB;
@@ -553,11 +554,13 @@ std::shared_ptr<Plan> build_plan(int L, const std::vector<uint32_t> &states, con
                 }
                 ss.nrb += (w + sd.m2 + RBF - 1) / RBF;
                 ss.nrbb += (w + sd.m2 + RBB - 1) / RBB;
+                ss.nrbk += (w + sd.m2 + RBK - 1) / RBK;
                 p.m_elems += (int64_t)w * w;
                 p.sdescs.push_back(sd);
             }
             ss.nd = (int32_t)p.sdescs.size() - ss.d0;
             p.max_sstep_nrbb = std::max(p.max_sstep_nrbb, ss.nrbb);
+            p.max_sstep_nrbk = std::max(p.max_sstep_nrbk, ss.nrbk);
             p.ssteps.push_back(ss);
         }
         p.lvl_sstep_ptr[l + 1] = (int32_t)p.ssteps.size();
