@@ -318,6 +318,8 @@ def main():
     job_pairs, job_stats = [], []
     ev_mixed = torch.empty((len(timed_jobs), NEV), dtype=torch.float64, device="cuda")
     torch.cuda.synchronize()
+    if nvtx is not None:
+        nvtx.range_push("sequential")
     for i, (h, seed, eps) in enumerate(timed_jobs):
         job_ev[i].record()
         nc, st = device_job(h, seed, eps, g.MBL_PREC_FP32)
@@ -326,6 +328,8 @@ def main():
         ev_mixed[i].copy_(d_ev)
     job_ev[-1].record()
     torch.cuda.synchronize()
+    if nvtx is not None:
+        nvtx.range_pop()
     job_ms = [job_ev[i].elapsed_time(job_ev[i + 1]) for i in range(len(timed_jobs))]
     prof = {k: ctx.profile(k) for k in PROF_KEYS}
     ctx.set_profiling(False)

@@ -67,6 +67,7 @@ typedef struct mbl_opts {
     int tensor_cores;     /* FP32 fronts: Schur updates on tcgen05 (3xTF32) if nonzero [1]   */
     int refine_mode;      /* 0: plain iterative refinement, 1: FGMRES with the factor as    */
                           /*    right preconditioner (FP64 Arnoldi per right-hand side)  [1]   */
+    int gmres_restart;    /* FGMRES inner dimension before a restart (1..64)          [12]   */
 } mbl_opts;
 
 typedef struct mbl_factor_stats {

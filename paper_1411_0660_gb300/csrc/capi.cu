@@ -11,6 +11,7 @@
 namespace mbl {
 
 std::atomic<long long> g_launches{0};
+thread_local long long t_launches = 0;
 
 // Contexts that are alive: objects that outlive their context (a sector or factorization released
 // after mbl_ctx_destroy) free their device memory without touching the dead context.
@@ -235,6 +236,7 @@ void mbl_opts_default(mbl_opts *o) {
     o->start_seed = 12345;
     o->tensor_cores = 1;
     o->refine_mode = 1;
+    o->gmres_restart = 12;
 }
 
 const char *mbl_version(void) { return "mblsi 0.1 (sm_103a)"; }

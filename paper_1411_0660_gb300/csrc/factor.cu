@@ -95,25 +95,20 @@ __global__ void __launch_bounds__(256) k_assemble(const AsmItem *items, const in
 template <class T>
 __global__ void __launch_bounds__(RB) k_panel_colmax(const PanelDesc *descs, int nd, const int64_t *fo,
                                                      const int32_t *fsz, const T *arena, unsigned int *cmax) {
-    __shared__ float red[RB / 32];
     const int di = find_desc2(descs, nd, blockIdx.x);
     const PanelDesc d = descs[di];
     const int s = d.front, f = fsz[s], k0 = d.k0, w = d.w;
     const int r0 = k0 + w + (int)(blockIdx.x - d.off2) * RB;
     const int nr = min(RB, f - r0);
     const T *F = arena + fo[s];
-    const int i = threadIdx.x, lane = i & 31, wp = i >> 5;
-    for (int c = 0; c < w; ++c) {
-        float v = (i < nr) ? (float)tabs(F[(int64_t)(k0 + c) * f + r0 + i]) : 0.f;
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    // warp wp takes columns wp, wp + nw, ...; its lanes cover the block's rows
+    for (int c = wp; c < w; c += nw) {
+        const T *col = F + (int64_t)(k0 + c) * f + r0;
+        float v = 0.f;
+        for (int i = lane; i < nr; i += 32) v = fmaxf(v, (float)tabs(col[i]));
         for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-        if (lane == 0) red[wp] = v;
-        __syncthreads();
-        if (i == 0) {
-            float m = 0.f;
-            for (int u = 0; u < RB / 32; ++u) m = fmaxf(m, red[u]);
-            atomicMax(cmax + (size_t)di * NB + c, __float_as_uint(m));
-        }
-        __syncthreads();
+        if (lane == 0) atomicMax(cmax + (size_t)di * NB + c, __float_as_uint(v));
     }
 }
 
@@ -127,6 +122,8 @@ __global__ void __launch_bounds__(256) k_panel_diag(const PanelDesc *descs, cons
     __shared__ float cm[NB];
     __shared__ int s_j;
     __shared__ T s_d;
+    __shared__ float s_best[8], s_bd[8];
+    __shared__ int s_bj[8];
     const PanelDesc d = descs[blockIdx.x];
     const int s = d.front, f = fsz[s], k0 = d.k0, w = d.w;
     T *F = arena + fo[s];
@@ -142,28 +139,45 @@ __global__ void __launch_bounds__(256) k_panel_diag(const PanelDesc *descs, cons
     __syncthreads();
     for (int t = 0; t < w; ++t) {
         // pivot: the candidate whose diagonal is largest relative to the rest of its column (inside the
-        // block and, from before this panel, in the rows below), which bounds the multipliers
-        if (tid < 32) {
-            float best = -1.f, bd = -1.f;
-            int bj = t;
-            for (int j = t + tid; j < w; j += 32) {
-                float dj = (float)tabs(B[j][j]);
-                float om = cm[perm[j]];
-                for (int i = t; i < w; ++i) {
+        // block and, from before this panel, in the rows below), which bounds the multipliers.  Warp
+        // wp scores candidates t + wp, t + wp + 8, ...; its lanes share each column's maximum.  Order:
+        // largest score, then largest |d|, then the smallest index.
+        {
+            const int lane = tid & 31, wp = tid >> 5;
+            float best = -1.f, bdg = -1.f;
+            int bj = w;
+            for (int j = t + wp; j < w; j += 8) {
+                float om = 0.f;
+                for (int i = t + lane; i < w; i += 32) {
                     if (i == j) continue;
-                    float v = (float)tabs(i > j ? B[i][j] : B[j][i]);
-                    om = fmaxf(om, v);
+                    om = fmaxf(om, (float)tabs(i > j ? B[i][j] : B[j][i]));
                 }
-                float sc = om > 0.f ? dj / om : 3.0e38f;
-                if (sc > best || (sc == best && dj > bd)) { best = sc; bd = dj; bj = j; }
+                for (int o = 16; o > 0; o >>= 1) om = fmaxf(om, __shfl_xor_sync(0xffffffffu, om, o));
+                om = fmaxf(om, cm[perm[j]]);
+                const float dj = (float)tabs(B[j][j]);
+                const float sc = om > 0.f ? dj / om : 3.0e38f;
+                if (sc > best || (sc == best && dj > bdg)) { best = sc; bdg = dj; bj = j; }
             }
-            for (int o = 16; o > 0; o >>= 1) {
-                float ob = __shfl_down_sync(0xffffffffu, best, o);
-                float od = __shfl_down_sync(0xffffffffu, bd, o);
-                int oj = __shfl_down_sync(0xffffffffu, bj, o);
-                if (ob > best || (ob == best && (od > bd || (od == bd && oj < bj)))) { best = ob; bd = od; bj = oj; }
+            if (lane == 0) {
+                s_best[wp] = best;
+                s_bd[wp] = bdg;
+                s_bj[wp] = bj;
             }
-            if (tid == 0) s_j = bj;
+            __syncthreads();
+            if (tid == 0) {
+                float b0 = s_best[0], d0 = s_bd[0];
+                int j0 = s_bj[0];
+                for (int u = 1; u < 8; ++u) {
+                    const float ob = s_best[u], od = s_bd[u];
+                    const int oj = s_bj[u];
+                    if (oj < w && (ob > b0 || (ob == b0 && (od > d0 || (od == d0 && oj < j0))))) {
+                        b0 = ob;
+                        d0 = od;
+                        j0 = oj;
+                    }
+                }
+                s_j = j0 < w ? j0 : t;
+            }
         }
         __syncthreads();
         const int j = s_j;
@@ -925,7 +939,7 @@ static void solve_impl(Factorization &fz, const double *B, int64_t ldb, double *
             fz.graph_exec = nullptr;
         }
         cudaGraph_t graph;
-        long long before = g_launches.load();
+        const long long before = t_launches;
         MBL_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
         try {
             solve_levels_p<T>(fz, p, st);
@@ -936,7 +950,8 @@ static void solve_impl(Factorization &fz, const double *B, int64_t ldb, double *
             throw;
         }
         MBL_CUDA(cudaStreamEndCapture(st, &graph));
-        fz.graph_nodes = g_launches.load() - before;
+        fz.graph_nodes = t_launches - before;
+        t_launches = before;
         g_launches.fetch_sub(fz.graph_nodes);  // counted when replayed
         MBL_CUDA(cudaGraphInstantiate(&fz.graph_exec, graph, 0));
         cudaGraphDestroy(graph);

@@ -131,6 +131,21 @@ __global__ void __launch_bounds__(1024) k_oa_step(int m, const double *G, const 
     }
 }
 
+// `steps` refinement steps of the eigendecomposition X, lam of the symmetric m x m matrix A
+// (all column-major, ld m); G, Q, S are m x m scratch.
+static void refine_eig(int m, const double *A, double *X, double *lam, int steps, double *G, double *Q, double *S,
+                       cudaStream_t st) {
+    for (int it = 0; it < steps; ++it) {
+        gemm_small(true, false, m, m, m, 1.0, X, m, X, m, 0.0, G, m, st);
+        gemm_small(false, false, m, m, m, 1.0, A, m, X, m, 0.0, Q, m, st);
+        gemm_small(true, false, m, m, m, 1.0, X, m, Q, m, 0.0, S, m, st);
+        k_oa_step<<<1, 1024, 0, st>>>(m, G, S, lam, Q);  // E into Q
+        MBL_LAUNCH_CHECK();
+        MBL_CUDA(cudaMemcpyAsync(G, X, (size_t)m * m * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        gemm_small(false, false, m, m, m, 1.0, G, m, Q, m, 1.0, X, m, st);  // X += X E
+    }
+}
+
 // res[i] = || T[mm:mm+p, 0:mm] S[:, i] ||
 __global__ void k_ritz_resid(const double *T, int ldt, int mm, int p, const double *S, double *res) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -398,16 +413,7 @@ void KrylovSchur::ritz(cudaStream_t st, std::vector<double> &theta, std::vector<
         }
         if (fp32) {
             ProfScope ps3(ctx, "oa_refine", (double)mm, st);
-            double *X = eigA.data(), *G = NS1.data(), *Q = NS2.data(), *Sx = NS3.data();
-            for (int it = 0; it < 2; ++it) {
-                gemm_small(true, false, mm, mm, mm, 1.0, X, mm, X, mm, 0.0, G, mm, st);
-                gemm_small(false, false, mm, mm, mm, 1.0, Ts.data(), mm, X, mm, 0.0, Q, mm, st);
-                gemm_small(true, false, mm, mm, mm, 1.0, X, mm, Q, mm, 0.0, Sx, mm, st);
-                k_oa_step<<<1, 1024, 0, st>>>(mm, G, Sx, eigW.data(), Q);  // E into Q
-                MBL_LAUNCH_CHECK();
-                MBL_CUDA(cudaMemcpyAsync(G, X, (size_t)mm * mm * sizeof(double), cudaMemcpyDeviceToDevice, st));
-                gemm_small(false, false, mm, mm, mm, 1.0, G, mm, Q, mm, 1.0, X, mm, st);  // X += X E
-            }
+            refine_eig(mm, Ts.data(), eigA.data(), eigW.data(), 2, NS1.data(), NS2.data(), NS3.data(), st);
         }
     }
     k_ritz_resid<<<nblk(mm, 128), 128, 0, st>>>(T.data(), ldv, mm, p, eigA.data(), res.data());
@@ -1010,6 +1016,7 @@ void solve_near(mbl_sector *sec, double eps, int nev, const mbl_opts &o, double 
     S.ms_factor = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tf0).count();
     RefinedSolve op{sec, fz.get(), hnorm + std::fabs(sigma_f), o.refine_tol, o.max_refine};
     op.gmres = o.refine_mode;
+    op.kmax = std::max(1, std::min(64, o.gmres_restart));
     OpFn opfn = [&](const double *X, int ldx, double *Y, cudaStream_t s) { op.apply(X, ldx, Y, p, s); };
     KrylovSchur ks(ctx, n, p, ncv);
     ks.start(o.start_seed, st);
@@ -1083,6 +1090,10 @@ RitzH::RitzH(Ctx *c, int64_t n_, int ldv, int nev_) : ctx(c), n(n_), nev(nev_) {
     HV.alloc(ctx, (size_t)n * ldv);
     Gm.alloc(ctx, (size_t)ldv * ldv);
     Gs.alloc(ctx, (size_t)ldv * ldv);
+    Gsym.alloc(ctx, (size_t)ldv * ldv);
+    Gr1.alloc(ctx, (size_t)ldv * ldv);
+    Gr2.alloc(ctx, (size_t)ldv * ldv);
+    Gr3.alloc(ctx, (size_t)ldv * ldv);
     Gw.alloc(ctx, ldv);
     Gwork.alloc(ctx, syev_work_doubles(ldv));
     Ctmp.alloc(ctx, (size_t)ldv * 32);
@@ -1118,9 +1129,27 @@ void RitzH::run(mbl_sector *sec, KrylovSchur &ks, double sigma, double hnorm, do
     MBL_LAUNCH_CHECK();
     MBL_CUDA(cudaMemcpyAsync(gm.data(), &mb, sizeof(int), cudaMemcpyHostToDevice, st));
     {
+        // FP32 eigensolve refined to FP64 accuracy by two Ogita-Aishima steps (the residuals of the
+        // returned pairs are recomputed on H below, so they certify the result); FP64 if FP32 fails
         ProfScope ps(ctx, "syev_rr", (double)mb, st);
+        const bool fp32 = ks.ldv <= EIG_SMEM_MAX_M;
+        MBL_CUDA(cudaMemcpyAsync(Gsym.data(), Gs.data(), (size_t)mb * mb * sizeof(double), cudaMemcpyDeviceToDevice,
+                                 st));
         syev_batched(1, gm.data(), goff.data(), goff.data(), Gs.data(), Gw.data(), 1, nullptr, ks.ldv, Gwork.data(),
-                     ginfo.data(), st);
+                     ginfo.data(), st, fp32);
+        int info = 0;
+        if (fp32) {
+            MBL_CUDA(cudaMemcpyAsync(&info, ginfo.data(), sizeof(int), cudaMemcpyDeviceToHost, st));
+            MBL_CUDA(cudaStreamSynchronize(st));
+        }
+        if (fp32 && info != 0) {
+            MBL_CUDA(cudaMemcpyAsync(Gs.data(), Gsym.data(), (size_t)mb * mb * sizeof(double),
+                                     cudaMemcpyDeviceToDevice, st));
+            syev_batched(1, gm.data(), goff.data(), goff.data(), Gs.data(), Gw.data(), 1, nullptr, ks.ldv,
+                         Gwork.data(), ginfo.data(), st, false);
+        } else if (fp32) {
+            refine_eig(mb, Gsym.data(), Gs.data(), Gw.data(), 2, Gr1.data(), Gr2.data(), Gr3.data(), st);
+        }
     }
     std::vector<double> gth(mb);
     MBL_CUDA(cudaMemcpyAsync(gth.data(), Gw.data(), mb * sizeof(double), cudaMemcpyDeviceToHost, st));

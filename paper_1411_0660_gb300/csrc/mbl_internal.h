@@ -33,9 +33,11 @@ struct Error {
 // Every kernel launch of the library is followed by exactly one MBL_LAUNCH_CHECK(), which also
 // counts it (mbl_launch_count).
 extern std::atomic<long long> g_launches;
+extern thread_local long long t_launches;  // this thread's share (graph capture counts its own launches)
 #define MBL_LAUNCH_CHECK()                                           \
     do {                                                             \
         ::mbl::g_launches.fetch_add(1, std::memory_order_relaxed);   \
+        ++::mbl::t_launches;                                         \
         MBL_CUDA(cudaGetLastError());                                \
     } while (0)
 

@@ -5,15 +5,17 @@
 // triangle of the trailing block, K = panel width (<= 64).  FP32 data, FP32 accumulation.  Each
 // operand x is split into two TF32 pieces x = hi + lo (hi = x rounded to TF32, lo = x - hi), and
 // three kind::tf32 MMAs accumulate hi*hi + hi*lo + lo*hi into a 128 x 128 FP32 tile in tensor
-// memory (TMEM).  One CTA of 128 threads per tile:
-//   1. every thread stages its row's operands into shared memory in the canonical K-major,
-//      no-swizzle core-matrix layout (8 rows x 16 bytes per core matrix), one 16-byte vector per
-//      store, then fences the generic-proxy writes for the tensor core;
-//   2. one thread issues 3 * (K / 8) tcgen05.mma and a tcgen05.commit to an mbarrier;
-//   3. all threads wait on the mbarrier (bounded by %globaltimer: on expiry the CTA flags an
+// memory (TMEM).  One CTA of 256 threads per tile; every memory access that does not depend on
+// the MMA is issued first so that their latencies overlap:
+//   1. the raw FP32 operand tiles go to shared memory by cp.async, and each thread loads its 64
+//      entries of the C tile (row = TMEM lane, half of the columns) into registers;
+//   2. the raw tiles are split into TF32 hi/lo pieces in the canonical K-major, no-swizzle
+//      core-matrix layout (8 rows x 16 bytes per core matrix), then fenced for the tensor core;
+//   3. one thread issues 3 * (K / 8) tcgen05.mma and a tcgen05.commit to an mbarrier;
+//   4. all threads wait on the mbarrier (bounded by %globaltimer: on expiry the CTA flags an
 //      error, skips its epilogue, frees its TMEM and returns), read the accumulator with
-//      tcgen05.ld (warp w owns TMEM lanes 32w..32w+31 = tile rows), and subtract it from the
-//      front in global memory (coalesced along the rows).
+//      tcgen05.ld (warps w and w + 4 share TMEM lanes 32(w mod 4).., each taking 64 columns) and
+//      store C - acc, coalesced along the rows.
 #include "factor.h"
 
 namespace mbl {
@@ -27,6 +29,7 @@ constexpr uint32_t SBO = KG * CORE;          // next 8-row group
 constexpr uint32_t LBO = CORE;               // next k group
 constexpr uint32_t OPB = TM * TK * 4;        // bytes per operand piece (32 KB)
 constexpr uint32_t TMEM_COLS = 128;
+constexpr int THREADS = 256;
 
 // instruction descriptor of kind::tf32: D = F32, A = B = TF32, both K-major, N = 128, M = 128
 constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TN >> 3) << 17) |
@@ -93,42 +96,21 @@ __device__ __forceinline__ int find_desc3t(const PanelDesc *d, int nd, int64_t b
     return lo;
 }
 
-// stage one operand (128 rows x w <= 64 columns, column-major source with leading dimension ld,
-// rows past `rows` and columns past `w` zero) as TF32 hi and lo pieces
-__device__ __forceinline__ void stage(const float *src, int64_t ld, int rows, int w, unsigned char *hi,
-                                      unsigned char *lo) {
-    const int r = threadIdx.x;  // one row per thread
-    const uint32_t rowoff = (uint32_t)(r >> 3) * SBO + (uint32_t)(r & 7) * 16u;
-#pragma unroll 4
-    for (int c = 0; c < KG; ++c) {
-        float v[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            int k = 4 * c + e;
-            v[e] = (r < rows && k < w) ? src[(int64_t)k * ld + r] : 0.0f;
-        }
-        uint4 h, l;
-        uint32_t hv[4], lv[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            hv[e] = to_tf32(v[e]);
-            lv[e] = to_tf32(v[e] - __uint_as_float(hv[e]));
-        }
-        h = make_uint4(hv[0], hv[1], hv[2], hv[3]);
-        l = make_uint4(lv[0], lv[1], lv[2], lv[3]);
-        *reinterpret_cast<uint4 *>(hi + rowoff + (uint32_t)c * CORE) = h;
-        *reinterpret_cast<uint4 *>(lo + rowoff + (uint32_t)c * CORE) = l;
-    }
+__device__ __forceinline__ void cp_async4(float *smem, const float *gmem) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
 }
 
 }  // namespace
 
-__global__ void __launch_bounds__(TM) k_schur_tc(const PanelDesc *descs, int nd, const int64_t *fo, const int32_t *fsz,
-                                                 float *arena, const float *wscr, unsigned long long *err) {
+__global__ void __launch_bounds__(THREADS) k_schur_tc(const PanelDesc *descs, int nd, const int64_t *fo,
+                                                      const int32_t *fsz, float *arena, const float *wscr,
+                                                      unsigned long long *err) {
     extern __shared__ __align__(1024) unsigned char sm[];
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tmem_slot;
     unsigned char *Ahi = sm, *Alo = sm + OPB, *Bhi = sm + 2 * OPB, *Blo = sm + 3 * OPB;
+    float *Araw = reinterpret_cast<float *>(sm + 4 * OPB);  // [k][row], TK x TM
+    float *Braw = Araw + TK * TM;
 
     const int di = find_desc3t(descs, nd, blockIdx.x);
     const PanelDesc d = descs[di];
@@ -143,7 +125,27 @@ __global__ void __launch_bounds__(TM) k_schur_tc(const PanelDesc *descs, int nd,
     float *F = arena + fo[s];
     const float *W = wscr + d.woff;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int quarter = warp & 3, half = warp >> 2;
 
+    // 1a. raw operands: A = L21 rows i0.. (front columns k0..k0+w), B = W21 rows j0.. (ld m2)
+    const int rowsA = min(TM, f - i0), rowsB = min(TN, f - j0);
+    for (int idx = threadIdx.x; idx < TK * TM; idx += THREADS) {
+        const int k = idx / TM, r = idx % TM;
+        float *da = Araw + idx, *db = Braw + idx;
+        if (k < w && r < rowsA) cp_async4(da, F + (int64_t)(k0 + k) * f + i0 + r);
+        else *da = 0.0f;
+        if (k < w && r < rowsB) cp_async4(db, W + (int64_t)k * m2 + (j0 - base) + r);
+        else *db = 0.0f;
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    // 1b. this thread's part of C: row gi, columns j0 + 64 half + c (lower triangle only)
+    const int gi = i0 + quarter * 32 + lane;
+    float cv[64];
+#pragma unroll
+    for (int c = 0; c < 64; ++c) {
+        const int gj = j0 + 64 * half + c;
+        cv[c] = (gi < f && gj < f && gi >= gj) ? F[(int64_t)gj * f + gi] : 0.0f;
+    }
     // TMEM accumulator (one warp allocates) and the completion barrier
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_slot)),
@@ -154,15 +156,33 @@ __global__ void __launch_bounds__(TM) k_schur_tc(const PanelDesc *descs, int nd,
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&mbar)));
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
-    // operands: A = L21 rows i0.. (columns k0..k0+w of the front), B = W21 rows j0..
-    stage(F + (int64_t)k0 * f + i0, f, min(TM, f - i0), w, Ahi, Alo);
-    stage(W + (j0 - base), m2, min(TN, f - j0), w, Bhi, Blo);
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncthreads();
+    // 2. TF32 hi/lo pieces in the canonical layout, one 16-byte core-matrix row per unit
+    for (int u = threadIdx.x; u < TM * KG; u += THREADS) {
+        const int r = u % TM, c = u / TM;
+        const uint32_t off = (uint32_t)(r >> 3) * SBO + (uint32_t)(r & 7) * 16u + (uint32_t)c * CORE;
+        uint32_t ah[4], al[4], bh[4], bl[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const float va = Araw[(4 * c + e) * TM + r], vb = Braw[(4 * c + e) * TM + r];
+            ah[e] = to_tf32(va);
+            al[e] = to_tf32(va - __uint_as_float(ah[e]));
+            bh[e] = to_tf32(vb);
+            bl[e] = to_tf32(vb - __uint_as_float(bh[e]));
+        }
+        *reinterpret_cast<uint4 *>(Ahi + off) = make_uint4(ah[0], ah[1], ah[2], ah[3]);
+        *reinterpret_cast<uint4 *>(Alo + off) = make_uint4(al[0], al[1], al[2], al[3]);
+        *reinterpret_cast<uint4 *>(Bhi + off) = make_uint4(bh[0], bh[1], bh[2], bh[3]);
+        *reinterpret_cast<uint4 *>(Blo + off) = make_uint4(bl[0], bl[1], bl[2], bl[3]);
+    }
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     const uint32_t tmem = tmem_slot;
 
+    // 3. the MMAs
     if (threadIdx.x == 0) {
         const int ksteps = (w + 7) / 8;
         uint32_t acc = 0;
@@ -184,23 +204,21 @@ __global__ void __launch_bounds__(TM) k_schur_tc(const PanelDesc *descs, int nd,
                          smem_u32(&mbar))
                      : "memory");
     }
+    // 4. bounded wait, then C - acc for this thread's row and 64 columns
     const bool ok = mbar_wait(smem_u32(&mbar), 0, 2000000000ull);
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     if (!ok) {
         if (lane == 0) atomicAdd(err, 1ull);
         mbar_wait(smem_u32(&mbar), 0, 2000000000ull);  // give the in-flight MMAs a second chance
     } else {
-        const int gi = i0 + warp * 32 + lane;
-#pragma unroll 1
-        for (int jc = 0; jc < TN; jc += 32) {
-            uint32_t r[32];
-            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)jc, r);
-            if (gi < f) {
 #pragma unroll
-                for (int c = 0; c < 32; ++c) {
-                    const int gj = j0 + jc + c;
-                    if (gj < f && gi >= gj) F[(int64_t)gj * f + gi] -= __uint_as_float(r[c]);
-                }
+        for (int jc = 0; jc < 64; jc += 32) {
+            uint32_t r[32];
+            tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(64 * half + jc), r);
+#pragma unroll
+            for (int c = 0; c < 32; ++c) {
+                const int gj = j0 + 64 * half + jc + c;
+                if (gi < f && gj < f && gi >= gj) F[(int64_t)gj * f + gi] = cv[jc + c] - __uint_as_float(r[c]);
             }
         }
     }
@@ -210,7 +228,7 @@ __global__ void __launch_bounds__(TM) k_schur_tc(const PanelDesc *descs, int nd,
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TMEM_COLS));
 }
 
-size_t schur_tc_smem() { return 4 * (size_t)OPB; }
+size_t schur_tc_smem() { return 4 * (size_t)OPB + 2 * (size_t)TK * TM * sizeof(float); }
 
 void launch_schur_tc(const PanelStep &stp, const PanelDesc *d_descs, const Plan &p, float *arena, const float *wscr,
                      unsigned long long *err, cudaStream_t st) {
@@ -219,7 +237,7 @@ void launch_schur_tc(const PanelStep &stp, const PanelDesc *d_descs, const Plan 
         MBL_CUDA(cudaFuncSetAttribute(k_schur_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)schur_tc_smem()));
         attr = true;
     }
-    k_schur_tc<<<(unsigned)stp.n3t, TM, schur_tc_smem(), st>>>(d_descs, stp.nd, p.d_sn_fo.data(), p.d_sn_f.data(), arena,
+    k_schur_tc<<<(unsigned)stp.n3t, THREADS, schur_tc_smem(), st>>>(d_descs, stp.nd, p.d_sn_fo.data(), p.d_sn_f.data(), arena,
                                                                wscr, err);
     MBL_LAUNCH_CHECK();
 }
