@@ -1090,10 +1090,6 @@ RitzH::RitzH(Ctx *c, int64_t n_, int ldv, int nev_) : ctx(c), n(n_), nev(nev_) {
     HV.alloc(ctx, (size_t)n * ldv);
     Gm.alloc(ctx, (size_t)ldv * ldv);
     Gs.alloc(ctx, (size_t)ldv * ldv);
-    Gsym.alloc(ctx, (size_t)ldv * ldv);
-    Gr1.alloc(ctx, (size_t)ldv * ldv);
-    Gr2.alloc(ctx, (size_t)ldv * ldv);
-    Gr3.alloc(ctx, (size_t)ldv * ldv);
     Gw.alloc(ctx, ldv);
     Gwork.alloc(ctx, syev_work_doubles(ldv));
     Ctmp.alloc(ctx, (size_t)ldv * 32);
@@ -1129,27 +1125,11 @@ void RitzH::run(mbl_sector *sec, KrylovSchur &ks, double sigma, double hnorm, do
     MBL_LAUNCH_CHECK();
     MBL_CUDA(cudaMemcpyAsync(gm.data(), &mb, sizeof(int), cudaMemcpyHostToDevice, st));
     {
-        // FP32 eigensolve refined to FP64 accuracy by two Ogita-Aishima steps (the residuals of the
-        // returned pairs are recomputed on H below, so they certify the result); FP64 if FP32 fails
+        // FP64: the returned vectors must be accurate one by one, and two refinement steps from FP32
+        // do not separate Ritz values that are closer than the FP32 eigensolver resolves
         ProfScope ps(ctx, "syev_rr", (double)mb, st);
-        const bool fp32 = ks.ldv <= EIG_SMEM_MAX_M;
-        MBL_CUDA(cudaMemcpyAsync(Gsym.data(), Gs.data(), (size_t)mb * mb * sizeof(double), cudaMemcpyDeviceToDevice,
-                                 st));
         syev_batched(1, gm.data(), goff.data(), goff.data(), Gs.data(), Gw.data(), 1, nullptr, ks.ldv, Gwork.data(),
-                     ginfo.data(), st, fp32);
-        int info = 0;
-        if (fp32) {
-            MBL_CUDA(cudaMemcpyAsync(&info, ginfo.data(), sizeof(int), cudaMemcpyDeviceToHost, st));
-            MBL_CUDA(cudaStreamSynchronize(st));
-        }
-        if (fp32 && info != 0) {
-            MBL_CUDA(cudaMemcpyAsync(Gs.data(), Gsym.data(), (size_t)mb * mb * sizeof(double),
-                                     cudaMemcpyDeviceToDevice, st));
-            syev_batched(1, gm.data(), goff.data(), goff.data(), Gs.data(), Gw.data(), 1, nullptr, ks.ldv,
-                         Gwork.data(), ginfo.data(), st, false);
-        } else if (fp32) {
-            refine_eig(mb, Gsym.data(), Gs.data(), Gw.data(), 2, Gr1.data(), Gr2.data(), Gr3.data(), st);
-        }
+                     ginfo.data(), st);
     }
     std::vector<double> gth(mb);
     MBL_CUDA(cudaMemcpyAsync(gth.data(), Gw.data(), mb * sizeof(double), cudaMemcpyDeviceToHost, st));
