@@ -61,13 +61,13 @@ typedef struct mbl_opts {
     int max_restarts;     /* thick restarts before MBL_ERR_NOT_CONVERGED            [60]   */
     double tol;           /* accept when ||H y - theta y|| <= tol ||H||              [1e-10]*/
     double target_tol;    /* converge towards this (the FP64 floor)                  [1e-13]*/
-    double refine_tol;    /* refinement stop: ||b - A x|| <= refine_tol (|A||x| + |b|)[1e-15]*/
+    double refine_tol;    /* refinement stop: ||b - A x|| <= refine_tol (|A||x| + |b|)[1e-14]*/
     int max_refine;       /* refinement steps per application                       [20]   */
     uint64_t start_seed;  /* seed of the random start block                         [12345]*/
     int tensor_cores;     /* FP32 fronts: Schur updates on tcgen05 (3xTF32) if nonzero [1]   */
     int refine_mode;      /* 0: plain iterative refinement, 1: FGMRES with the factor as    */
                           /*    right preconditioner (FP64 Arnoldi per right-hand side)  [1]   */
-    int gmres_restart;    /* FGMRES inner dimension before a restart (1..64)          [12]   */
+    int gmres_restart;    /* FGMRES inner dimension before a restart (1..64)          [24]   */
 } mbl_opts;
 
 typedef struct mbl_factor_stats {

@@ -231,12 +231,12 @@ void mbl_opts_default(mbl_opts *o) {
     o->max_restarts = 60;
     o->tol = 1e-10;
     o->target_tol = 1e-13;
-    o->refine_tol = 1e-15;
+    o->refine_tol = 1e-14;
     o->max_refine = 20;
     o->start_seed = 12345;
     o->tensor_cores = 1;
     o->refine_mode = 1;
-    o->gmres_restart = 12;
+    o->gmres_restart = 24;
 }
 
 const char *mbl_version(void) { return "mblsi 0.1 (sm_103a)"; }

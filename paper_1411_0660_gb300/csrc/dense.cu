@@ -407,7 +407,7 @@ __global__ void __launch_bounds__(EIG_THREADS) k_syev(const int *mv, const int64
         }
         return;
     }
-    // ---- 3. implicit QL on (d, e) accumulating Z (row-major m x m, starts as identity) ----
+    // ---- 3. implicit QL on (d, e) accumulating Z (column-major m x m, starts as identity) ----
     {
         R *cs = pp, *sn = vv;  // reuse the Householder scratch for the sweep's rotations
         for (int t = threadIdx.x; t < m * m; t += blockDim.x) Z[t] = ((t / m) == (t % m)) ? R(1) : R(0);
@@ -440,14 +440,17 @@ __global__ void __launch_bounds__(EIG_THREADS) k_syev(const int *mv, const int64
             __syncthreads();
             if (s_hi >= 0) {
                 int lo = s_lo, hi = s_hi;
+                // Z is column-major (column k contiguous): thread r walks its row down the sweep,
+                // carrying the rotated entry of column k + 1; accesses coalesce across threads
                 for (int r = threadIdx.x; r < m; r += blockDim.x) {
-                    R *zr = Z + (size_t)r * m;
+                    R a1 = Z[(size_t)hi * m + r];
                     for (int k = hi - 1; k >= lo; --k) {
-                        R c = cs[k], sv = sn[k];
-                        R a0 = zr[k], a1 = zr[k + 1];
-                        zr[k] = c * a0 - sv * a1;
-                        zr[k + 1] = sv * a0 + c * a1;
+                        const R c = cs[k], sv = sn[k];
+                        const R a0 = Z[(size_t)k * m + r];
+                        Z[(size_t)(k + 1) * m + r] = sv * a0 + c * a1;
+                        a1 = c * a0 - sv * a1;
                     }
+                    Z[(size_t)lo * m + r] = a1;
                 }
             }
             __syncthreads();
@@ -468,7 +471,7 @@ __global__ void __launch_bounds__(EIG_THREADS) k_syev(const int *mv, const int64
         for (int j = threadIdx.x; j < m; j += blockDim.x) W[j] = (double)d[j];
         for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
             int c = t / m, r = t % m;
-            scr[t] = Z[(size_t)r * m + (int)cs[c]];
+            scr[t] = Z[(size_t)(int)cs[c] * m + r];
         }
         __syncthreads();
         for (int t = threadIdx.x; t < m * m; t += blockDim.x) Z[t] = scr[t];

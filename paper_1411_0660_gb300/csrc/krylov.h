@@ -45,7 +45,7 @@ struct RefinedSolve {
     bool stalled = false;
     double last_rel = 0.0;
     int gmres = 1;     // 1: FGMRES refinement (factor as right preconditioner); 0: plain refinement
-    int kmax = 12;     // FGMRES inner dimension
+    int kmax = 24;     // FGMRES inner dimension
     DVec<double> R, part, norms, GV, GZ, GW, Gh, Gy, Gdots;
     void apply(const double *X, int ldx, double *Y, int p, cudaStream_t st);
 
