@@ -210,7 +210,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--batch", type=int, default=6)
-    ap.add_argument("--slots", type=int, default=4, help="concurrent jobs (worker streams) in the timed region")
+    ap.add_argument("--slots", type=int, default=8, help="concurrent jobs (worker streams) in the timed region")
     ap.add_argument("--impl", default="gb300")
     ap.add_argument("--fp64-stride", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")

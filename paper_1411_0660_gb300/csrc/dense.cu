@@ -201,6 +201,7 @@ void chol_qr(int64_t n, double *X, int p, double *R, double *G, double *work, in
 // Batched small symmetric eigensolver.
 // ------------------------------------------------------------------------------------------
 constexpr int EIG_THREADS = 512;
+constexpr int EIG_QL_MAX = 512;  // tridiagonal order kept in shared memory during the QL sweeps
 
 size_t syev_work_doubles(int mmax, bool vecs) {
     // d, e, beta, v, p, e^2 (8m with slack) [+ Z (m*m) + sort scratch (m*m) with eigenvectors]
@@ -409,7 +410,20 @@ __global__ void __launch_bounds__(EIG_THREADS) k_syev(const int *mv, const int64
     }
     // ---- 3. implicit QL on (d, e) accumulating Z (column-major m x m, starts as identity) ----
     {
+        // the sweeps run on one thread as a chain of dependent updates of d, e and the rotation list:
+        // keep those in shared memory (global memory would put an L2 round trip in every link)
+        __shared__ R q_d[EIG_QL_MAX], q_e[EIG_QL_MAX], q_cs[EIG_QL_MAX], q_sn[EIG_QL_MAX];
         R *cs = pp, *sn = vv;  // reuse the Householder scratch for the sweep's rotations
+        if (m <= EIG_QL_MAX) {
+            for (int i = threadIdx.x; i < m; i += blockDim.x) {
+                q_d[i] = d[i];
+                q_e[i] = e[i];
+            }
+            d = q_d;
+            e = q_e;
+            cs = q_cs;
+            sn = q_sn;
+        }
         for (int t = threadIdx.x; t < m * m; t += blockDim.x) Z[t] = ((t / m) == (t % m)) ? R(1) : R(0);
         __shared__ int s_lo, s_hi, s_done, s_fail;
         if (threadIdx.x == 0) { s_lo = 0; s_done = 0; s_fail = 0; }
