@@ -178,7 +178,8 @@ def run_case(args):
     nvtx = getattr(torch.cuda, "nvtx", None)
     if nvtx is not None:
         nvtx.range_push("factor")
-    f = g.factor(sec, lo + 0.5 * (hi - lo), precision=prec, tensor_cores=args.tensor_cores)
+    f = g.factor(sec, lo + 0.5 * (hi - lo), precision=prec, tensor_cores=args.tensor_cores,
+                 solve_dataflow=args.dataflow)
     if nvtx is not None:
         nvtx.range_pop()
     B = np.random.default_rng(0).standard_normal((sec.dim, 8))
@@ -206,6 +207,7 @@ def main():
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--tensor-cores", type=int, default=1)
+    ap.add_argument("--dataflow", type=int, default=1, help="solve sweeps as persistent dataflow kernels")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)

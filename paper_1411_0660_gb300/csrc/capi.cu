@@ -156,7 +156,8 @@ std::shared_ptr<Plan> get_plan(mbl_sector *sec) {
     return P;
 }
 
-std::unique_ptr<Factorization> make_factorization(mbl_sector *sec, double sigma, int prec, double hnorm, bool use_tc) {
+std::unique_ptr<Factorization> make_factorization(mbl_sector *sec, double sigma, int prec, double hnorm, bool use_tc,
+                                                  bool dataflow) {
     if (prec != MBL_PREC_FP64 && prec != MBL_PREC_FP32) fail(MBL_ERR_INVALID, "unknown precision");
     auto F = std::make_unique<Factorization>();
     F->ctx = sec->ctx;
@@ -166,6 +167,7 @@ std::unique_ptr<Factorization> make_factorization(mbl_sector *sec, double sigma,
     F->prec = prec;
     F->tiny = (prec == MBL_PREC_FP64 ? 1e-12 : 1e-7) * hnorm;
     F->use_tc = use_tc;
+    F->dataflow = dataflow;
     F->allocate();
     cudaStream_t st = sec->ctx->stream;
     cudaEvent_t e0, e1;
@@ -237,6 +239,7 @@ void mbl_opts_default(mbl_opts *o) {
     o->tensor_cores = 1;
     o->refine_mode = 1;
     o->gmres_restart = 24;
+    o->solve_dataflow = 1;
 }
 
 const char *mbl_version(void) { return "mblsi 0.1 (sm_103a)"; }
@@ -470,7 +473,7 @@ int mbl_factor(mbl_sector *sec, double sigma, const mbl_opts *opts, mbl_factoriz
     double emin, emax;
     extremal_bounds(sec, &emin, &emax);
     double hn = std::max(std::fabs(emin), std::fabs(emax));
-    auto F = make_factorization(sec, sigma, o.precision, hn, o.tensor_cores != 0);
+    auto F = make_factorization(sec, sigma, o.precision, hn, o.tensor_cores != 0, o.solve_dataflow != 0);
     mbl_factorization *h = new mbl_factorization();
     h->f = std::move(F);
     *out = h;
@@ -523,6 +526,9 @@ int mbl_factor_solve(mbl_factorization *fh, const double *b, double *x, int nrhs
         for (int q = 0; q < p; ++q) copy_cols(n, X.data(), p, q, cm.data() + (size_t)(c0 + q) * n, 1, 0, 1, st);
     }
     MBL_CUDA(cudaStreamSynchronize(st));
+    unsigned long long tmo = 0;
+    MBL_CUDA(cudaMemcpy(&tmo, f.counters.data() + 2, sizeof(tmo), cudaMemcpyDeviceToHost));
+    if (tmo != 0) fail(MBL_ERR_TIMEOUT, "a triangular-solve dependency wait timed out");
     MBL_CUDA(cudaMemcpy(x, cm.data(), (size_t)n * nrhs * sizeof(double), cudaMemcpyDeviceToHost));
     API_CATCH(ctx)
 }

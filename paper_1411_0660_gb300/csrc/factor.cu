@@ -942,7 +942,8 @@ static void solve_impl(Factorization &fz, const double *B, int64_t ldb, double *
         const long long before = t_launches;
         MBL_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
         try {
-            solve_levels_p<T>(fz, p, st);
+            if (fz.dataflow) solve_dataflow<T>(fz, p, st);
+            else solve_levels_p<T>(fz, p, st);
         } catch (...) {
             cudaGraph_t dummy;
             cudaStreamEndCapture(st, &dummy);
@@ -978,7 +979,8 @@ void Factorization::ensure_solve_work(int p) {
     zsolved.alloc(ctx, (size_t)pl.zwork_elems * p * es);
     ywork.alloc(ctx, (size_t)pl.n * p * es);
     yfw.alloc(ctx, (size_t)pl.n * p * es);
-    pwork.alloc(ctx, (size_t)std::max<int64_t>(pl.max_sstep_nrbk, 1) * SUBS * RBB * rhs_pad(p) * es);
+    pwork.alloc(ctx, (size_t)std::max<int64_t>(std::max<int64_t>(pl.max_sstep_nrbk * SUBS, pl.df_pslots), 1) * RBB *
+                         rhs_pad(p) * es);
     work_p = p;
 }
 
@@ -993,6 +995,7 @@ void Factorization::allocate() {
     cmax.alloc(ctx, (size_t)std::max<int64_t>(pl.max_desc_per_step, 1) * NB * sizeof(unsigned int));
     M.alloc(ctx, (size_t)std::max<int64_t>(pl.m_elems, 1) * es);
     scnt.alloc(ctx, std::max<size_t>(pl.sdescs.size() * SUBS, 1));
+    dfcnt.alloc(ctx, (size_t)4 * pl.ns + 2);
     MBL_CUDA(cudaMemset(scnt.data(), 0, std::max<size_t>(pl.sdescs.size() * SUBS, 1) * sizeof(unsigned int)));
 }
 

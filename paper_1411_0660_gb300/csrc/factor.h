@@ -15,6 +15,8 @@ struct Factorization {
     DVec<char> arena, D, wscr, cmax, M, zwork, zsolved, ywork, yfw, pwork;
     DVec<int32_t> piv;
     DVec<unsigned int> scnt;  // per (solve panel, column chunk) arrival counters of the backward step
+    DVec<int32_t> dfcnt;      // dataflow solve: per-front completion counters (4 ns) and two tickets
+    bool dataflow = true;     // solves as one persistent kernel per sweep (else level-by-level launches)
     // [0] perturbed pivots, [1] negative pivots, [2] wait time-outs, [3] max |l| (float bits, low
     // word), [4] min |d| (float bits, low word)
     DVec<unsigned long long> counters;
@@ -39,6 +41,10 @@ size_t schur_tc_smem();
 void launch_schur_tc(const PanelStep &stp, const PanelDesc *d_descs, const Plan &p, float *arena, const float *wscr,
                      unsigned long long *err, cudaStream_t st);
 
+// Both sweeps of a block solve as dataflow kernels (solve_df.cu), between the permutations.
+template <class T>
+void solve_dataflow(Factorization &fz, int p, cudaStream_t st);
+
 // Enqueue the numeric factorization of H - sigma I (allocate() first).
 void numeric_factor(Factorization &fz, cudaStream_t st);
 // X (n x p row-major FP64, row stride ldx) (+)= (L D L^T)^-1 B, B row stride ldb; 1 <= p <= 32.
@@ -49,7 +55,7 @@ void factor_solve_raw(Factorization &fz, const double *B, int64_t ldb, double *X
 std::shared_ptr<Plan> get_plan(mbl_sector *sec);
 // Create, allocate and run a factorization (synchronous; fills stats).
 std::unique_ptr<Factorization> make_factorization(mbl_sector *sec, double sigma, int prec, double hnorm,
-                                                  bool use_tc = true);
+                                                  bool use_tc = true, bool dataflow = true);
 
 }  // namespace mbl
 

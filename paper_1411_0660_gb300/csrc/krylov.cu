@@ -1012,7 +1012,8 @@ void solve_near(mbl_sector *sec, double eps, int nev, const mbl_opts &o, double 
     if (std::fabs(sigma - emin) <= guard) sigma_f = emin - nudge;
     if (std::fabs(sigma - emax) <= guard) sigma_f = emax + nudge;
     auto tf0 = std::chrono::steady_clock::now();
-    std::unique_ptr<Factorization> fz = make_factorization(sec, sigma_f, o.precision, hnorm, o.tensor_cores != 0);
+    std::unique_ptr<Factorization> fz =
+        make_factorization(sec, sigma_f, o.precision, hnorm, o.tensor_cores != 0, o.solve_dataflow != 0);
     S.ms_factor = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tf0).count();
     RefinedSolve op{sec, fz.get(), hnorm + std::fabs(sigma_f), o.refine_tol, o.max_refine};
     op.gmres = o.refine_mode;
@@ -1037,7 +1038,7 @@ void solve_near(mbl_sector *sec, double eps, int nev, const mbl_opts &o, double 
                 auto tf1 = std::chrono::steady_clock::now();
                 op.fz = nullptr;
                 fz.reset();  // free the FP32 fronts first: the two factors never coexist in HBM
-                fz = make_factorization(sec, sigma_f, MBL_PREC_FP64, hnorm);
+                fz = make_factorization(sec, sigma_f, MBL_PREC_FP64, hnorm, true, o.solve_dataflow != 0);
                 S.ms_factor += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tf1).count();
                 op.fz = fz.get();
                 op.stalled = false;
@@ -1069,6 +1070,12 @@ void solve_near(mbl_sector *sec, double eps, int nev, const mbl_opts &o, double 
         std::vector<int> keep(order.begin(), order.begin() + k_keep);
         std::sort(keep.begin(), keep.end());
         ks.restart(keep, st);
+    }
+    {
+        unsigned long long tmo = 0;  // bounded waits of the dataflow solves that expired
+        MBL_CUDA(cudaMemcpyAsync(&tmo, fz->counters.data() + 2, sizeof(tmo), cudaMemcpyDeviceToHost, st));
+        MBL_CUDA(cudaStreamSynchronize(st));
+        if (tmo != 0) fail(MBL_ERR_TIMEOUT, "a triangular-solve dependency wait timed out");
     }
     MBL_CUDA(cudaMemcpyAsync(d_evals, rr.evals.data(), nev * sizeof(double), cudaMemcpyHostToDevice, st));
     MBL_CUDA(cudaMemcpyAsync(d_resid, rr.resid.data(), nev * sizeof(double), cudaMemcpyHostToDevice, st));

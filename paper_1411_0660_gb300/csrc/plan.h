@@ -64,6 +64,15 @@ struct SolveStep {
     int64_t nrbk;                    // backward row blocks in this step
 };
 
+// Work item of the dataflow (persistent) solve: kind 0 = gather of rows [GR a, GR a + GR) of a
+// front; kind 1 = panel step: solve descriptor a, row block b (RBF rows forward, RBK rows backward),
+// column chunk cc (backward only).  Item lists are in a topological order of their dependencies.
+constexpr int GR = 64;  // rows per gather item
+struct SolveItem {
+    int16_t kind, cc;
+    int32_t front, a, b;
+};
+
 struct AsmItem {     // assembly work item: columns [c0, c0 + ACOLS) of a front
     int32_t front, c0;
 };
@@ -95,6 +104,14 @@ struct Plan {
     // rows of the children's contribution blocks that land on it (children in tree order)
     std::vector<int64_t> lvl_fg_ptr;          // rows by level (nlevels + 1)
     std::vector<int64_t> fg_dst, fg_own, fg_cptr, fg_src;
+    // dataflow solve: item lists and completion targets.  Per front: gather items, forward blocks
+    // over all panels, backward (panel, column chunk) reductions over all panels, first fg row; per
+    // solve descriptor: forward blocks of the front's earlier panels, backward chunks of its later
+    // panels, and its first slot in the global backward-partials buffer.
+    std::vector<SolveItem> df_fwd, df_bwd;
+    std::vector<int32_t> df_gchunks, df_ftotal, df_btotal, df_fprefix, df_bprefix;
+    std::vector<int64_t> df_fg_off, df_poff;
+    int64_t df_pslots = 0;
     int64_t m_elems = 0, max_sstep_nrbb = 0, max_sstep_nrbk = 0;
     int64_t arena_elems = 0, zwork_elems = 0, wscratch_elems = 0, max_desc_per_step = 0;
     int64_t max_step_n2 = 0;
@@ -105,11 +122,15 @@ struct Plan {
 
     // device mirror
     DVec<int32_t> d_perm, d_iperm, d_sn_start, d_sn_nc, d_sn_f, d_rows, d_relind, d_ch_ptr, d_ch_list, d_amap_row;
+    DVec<int32_t> d_sn_parent;
     DVec<int64_t> d_sn_rows_off, d_sn_fo, d_sn_zo, d_sn_rel_off, d_amap_ptr, d_amap_src;
     DVec<AsmItem> d_asm_items;
     DVec<PanelDesc> d_descs;
     DVec<SolveDesc> d_sdescs;
     DVec<int64_t> d_fg_dst, d_fg_own, d_fg_cptr, d_fg_src;
+    DVec<SolveItem> d_df_fwd, d_df_bwd;
+    DVec<int32_t> d_df_gchunks, d_df_ftotal, d_df_btotal, d_df_fprefix, d_df_bprefix;
+    DVec<int64_t> d_df_fg_off, d_df_poff;
     bool on_device = false;
 };
 

@@ -588,6 +588,81 @@ std::shared_ptr<Plan> build_plan(int L, const std::vector<uint32_t> &states, con
         }
         p.lvl_fg_ptr[l + 1] = (int64_t)p.fg_dst.size();
     }
+    // dataflow solve tables.  Forward order: level by level, gathers of the level's fronts, then
+    // its panel steps in order; backward: levels in reverse, gathers, then panel steps last to first.
+    {
+        const int32_t ns_ = p.ns;
+        p.df_gchunks.assign(ns_, 0);
+        p.df_ftotal.assign(ns_, 0);
+        p.df_btotal.assign(ns_, 0);
+        p.df_fg_off.assign(ns_, 0);
+        p.df_fprefix.assign(p.sdescs.size(), 0);
+        p.df_bprefix.assign(p.sdescs.size(), 0);
+        p.df_poff.assign(p.sdescs.size(), 0);
+        {
+            int64_t row = 0;
+            for (int l = 0; l < p.nlevels; ++l)
+                for (int32_t q = p.lvl_ptr[l]; q < p.lvl_ptr[l + 1]; ++q) {
+                    const int32_t s = p.lvl_fronts[q];
+                    p.df_fg_off[s] = row;
+                    row += p.sn_f[s];
+                }
+        }
+        std::vector<std::vector<int32_t>> panels(ns_);  // solve descriptors of each front, in panel order
+        for (size_t q = 0; q < p.sdescs.size(); ++q) panels[p.sdescs[q].front].push_back((int32_t)q);
+        for (int32_t s = 0; s < ns_; ++s) {
+            p.df_gchunks[s] = (p.sn_f[s] + GR - 1) / GR;
+            int32_t acc = 0;
+            for (int32_t q : panels[s]) {
+                const SolveDesc &d = p.sdescs[q];
+                p.df_fprefix[q] = acc;
+                acc += (d.w + d.m2 + RBF - 1) / RBF;
+            }
+            p.df_ftotal[s] = acc;
+            acc = 0;
+            for (auto it = panels[s].rbegin(); it != panels[s].rend(); ++it) {
+                const SolveDesc &d = p.sdescs[*it];
+                p.df_bprefix[*it] = acc;
+                acc += (d.w + RBB - 1) / RBB;
+            }
+            p.df_btotal[s] = acc;
+        }
+        int64_t slots = 0;
+        for (size_t q = 0; q < p.sdescs.size(); ++q) {
+            p.df_poff[q] = slots;
+            slots += (int64_t)((p.sdescs[q].w + p.sdescs[q].m2 + RBK - 1) / RBK) * SUBS;
+        }
+        p.df_pslots = slots;
+        for (int l = 0; l < p.nlevels; ++l) {
+            for (int32_t q = p.lvl_ptr[l]; q < p.lvl_ptr[l + 1]; ++q) {
+                const int32_t s = p.lvl_fronts[q];
+                for (int32_t c = 0; c < p.df_gchunks[s]; ++c) p.df_fwd.push_back(SolveItem{0, 0, s, c, 0});
+            }
+            for (int si = p.lvl_sstep_ptr[l]; si < p.lvl_sstep_ptr[l + 1]; ++si) {
+                const SolveStep &ss = p.ssteps[si];
+                for (int32_t q = ss.d0; q < ss.d0 + ss.nd; ++q) {
+                    const SolveDesc &d = p.sdescs[q];
+                    const int32_t nb = (d.w + d.m2 + RBF - 1) / RBF;
+                    for (int32_t b = 0; b < nb; ++b) p.df_fwd.push_back(SolveItem{1, 0, d.front, q, b});
+                }
+            }
+        }
+        for (int l = p.nlevels - 1; l >= 0; --l) {
+            for (int32_t q = p.lvl_ptr[l]; q < p.lvl_ptr[l + 1]; ++q) {
+                const int32_t s = p.lvl_fronts[q];
+                for (int32_t c = 0; c < p.df_gchunks[s]; ++c) p.df_bwd.push_back(SolveItem{0, 0, s, c, 0});
+            }
+            for (int si = p.lvl_sstep_ptr[l + 1] - 1; si >= p.lvl_sstep_ptr[l]; --si) {
+                const SolveStep &ss = p.ssteps[si];
+                for (int32_t q = ss.d0; q < ss.d0 + ss.nd; ++q) {
+                    const SolveDesc &d = p.sdescs[q];
+                    const int32_t nb = (d.w + d.m2 + RBK - 1) / RBK;
+                    for (int32_t b = 0; b < nb; ++b)
+                        for (int16_t cc = 0; cc * RBB < d.w; ++cc) p.df_bwd.push_back(SolveItem{1, cc, d.front, q, b});
+                }
+            }
+        }
+    }
     p.ms_analyse = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     return P;
 }
@@ -623,6 +698,16 @@ void upload_plan(Ctx *ctx, Plan &p) {
     up(ctx, p.d_fg_own, p.fg_own);
     up(ctx, p.d_fg_cptr, p.fg_cptr);
     up(ctx, p.d_fg_src, p.fg_src);
+    up(ctx, p.d_sn_parent, p.sn_parent);
+    up(ctx, p.d_df_fwd, p.df_fwd);
+    up(ctx, p.d_df_bwd, p.df_bwd);
+    up(ctx, p.d_df_gchunks, p.df_gchunks);
+    up(ctx, p.d_df_ftotal, p.df_ftotal);
+    up(ctx, p.d_df_btotal, p.df_btotal);
+    up(ctx, p.d_df_fprefix, p.df_fprefix);
+    up(ctx, p.d_df_bprefix, p.df_bprefix);
+    up(ctx, p.d_df_fg_off, p.df_fg_off);
+    up(ctx, p.d_df_poff, p.df_poff);
     p.on_device = true;
 }
 
