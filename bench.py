@@ -207,7 +207,7 @@ def main():
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--tensor-cores", type=int, default=1)
-    ap.add_argument("--dataflow", type=int, default=1, help="solve sweeps as persistent dataflow kernels")
+    ap.add_argument("--dataflow", type=int, default=0, help="solve sweeps as persistent dataflow kernels")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)

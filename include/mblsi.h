@@ -68,8 +68,8 @@ typedef struct mbl_opts {
     int refine_mode;      /* 0: plain iterative refinement, 1: FGMRES with the factor as    */
                           /*    right preconditioner (FP64 Arnoldi per right-hand side)  [1]   */
     int gmres_restart;    /* FGMRES inner dimension before a restart (1..64)          [24]   */
-    int solve_dataflow;   /* solves as one persistent dataflow kernel per sweep; 0 = one   */
-                          /*    launch per level and solve panel                        [1]    */
+    int solve_dataflow;   /* 1: solves as one persistent dataflow kernel per sweep; 0: one */
+                          /*    graph-captured launch per level gather and solve panel  [0]    */
 } mbl_opts;
 
 typedef struct mbl_factor_stats {

@@ -239,7 +239,7 @@ void mbl_opts_default(mbl_opts *o) {
     o->tensor_cores = 1;
     o->refine_mode = 1;
     o->gmres_restart = 24;
-    o->solve_dataflow = 1;
+    o->solve_dataflow = 0;
 }
 
 const char *mbl_version(void) { return "mblsi 0.1 (sm_103a)"; }

@@ -16,7 +16,7 @@ struct Factorization {
     DVec<int32_t> piv;
     DVec<unsigned int> scnt;  // per (solve panel, column chunk) arrival counters of the backward step
     DVec<int32_t> dfcnt;      // dataflow solve: per-front completion counters (4 ns) and two tickets
-    bool dataflow = true;     // solves as one persistent kernel per sweep (else level-by-level launches)
+    bool dataflow = false;    // solves as one persistent kernel per sweep (else level-by-level launches)
     // [0] perturbed pivots, [1] negative pivots, [2] wait time-outs, [3] max |l| (float bits, low
     // word), [4] min |d| (float bits, low word)
     DVec<unsigned long long> counters;
@@ -55,7 +55,7 @@ void factor_solve_raw(Factorization &fz, const double *B, int64_t ldb, double *X
 std::shared_ptr<Plan> get_plan(mbl_sector *sec);
 // Create, allocate and run a factorization (synchronous; fills stats).
 std::unique_ptr<Factorization> make_factorization(mbl_sector *sec, double sigma, int prec, double hnorm,
-                                                  bool use_tc = true, bool dataflow = true);
+                                                  bool use_tc = true, bool dataflow = false);
 
 }  // namespace mbl
 

@@ -16,6 +16,8 @@
 #include <functional>
 #include <numeric>
 
+#include <cfloat>
+
 #include "krylov.h"
 
 namespace mbl {
@@ -128,6 +130,43 @@ __global__ void __launch_bounds__(1024) k_oa_step(int m, const double *G, const 
         double e = 0.5 * r;
         if (i != j && fabs(lam[j] - lam[i]) > delta) e = (S[idx] + lam[j] * r) / (lam[j] - lam[i]);
         E[idx] = e;
+    }
+}
+
+// Quality of an eigendecomposition after refinement: out = {||I - G||_F, ||S - diag(S)||_F, max|S_ii|}
+// with G = X^T X and S = X^T A X.  One CTA.
+__global__ void __launch_bounds__(1024) k_oa_norms(int m, const double *G, const double *S, double *out) {
+    __shared__ double red[3][32];
+    const int t = threadIdx.x;
+    double rr = 0.0, off = 0.0, amax = 0.0;
+    for (int idx = t; idx < m * m; idx += blockDim.x) {
+        const int i = idx % m, j = idx / m;
+        const double r = (i == j ? 1.0 : 0.0) - G[idx];
+        rr += r * r;
+        if (i != j) off += S[idx] * S[idx];
+        else amax = fmax(amax, fabs(S[idx]));
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        rr += __shfl_xor_sync(0xffffffffu, rr, o);
+        off += __shfl_xor_sync(0xffffffffu, off, o);
+        amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    }
+    if ((t & 31) == 0) {
+        red[0][t >> 5] = rr;
+        red[1][t >> 5] = off;
+        red[2][t >> 5] = amax;
+    }
+    __syncthreads();
+    if (t == 0) {
+        double a = 0.0, b = 0.0, c = 0.0;
+        for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) {
+            a += red[0][w];
+            b += red[1][w];
+            c = fmax(c, red[2][w]);
+        }
+        out[0] = sqrt(a);
+        out[1] = sqrt(b);
+        out[2] = c;
     }
 }
 
@@ -788,7 +827,9 @@ __device__ int tri_sturm(int m, const double *a, const double *b, double x) {
 // Extreme eigenvalues of the Lanczos tridiagonal T (alpha, beta) by bisection, and the last component
 // of their unit eigenvectors by two steps of inverse iteration.  out = {lo, hi, z_lo, z_hi}.
 __global__ void k_tridiag_extremes(int m, const double *a, const double *b, double *scratch, double *out) {
-    const int which = threadIdx.x;
+    // warp 0 finds the smallest eigenvalue, warp 1 the largest: multisection, each lane one Sturm
+    // count per round (32 points split the bracket into 33 parts), then lane 0 inverse-iterates
+    const int which = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (which > 1) return;
     double gl = a[0], gu = a[0];
     for (int i = 0; i < m; ++i) {
@@ -798,11 +839,20 @@ __global__ void k_tridiag_extremes(int m, const double *a, const double *b, doub
     }
     const int j = which == 0 ? 0 : m - 1;
     double lo = gl - 1e-12 * (fabs(gl) + fabs(gu)), hi = gu + 1e-12 * (fabs(gl) + fabs(gu));
-    for (int it = 0; it < 200; ++it) {
-        double mid = 0.5 * (lo + hi);
-        if (mid == lo || mid == hi) break;
-        if (tri_sturm(m, a, b, mid) > j) hi = mid; else lo = mid;
+    for (int it = 0; it < 64; ++it) {
+        const double step = (hi - lo) / 33.0;
+        const double x = lo + (lane + 1) * step;
+        const bool above = x < hi && tri_sturm(m, a, b, x) > j;  // x lies above eigenvalue j
+        const unsigned int mask = __ballot_sync(0xffffffffu, above);
+        const int first = mask ? __ffs(mask) - 1 : 32;  // first point above it (32: none)
+        const double nlo = first == 0 ? lo : lo + first * step;
+        const double nhi = first == 32 ? hi : lo + (first + 1) * step;
+        if (nlo == lo && nhi == hi) break;  // no progress at this precision
+        lo = nlo;
+        hi = fmin(nhi, hi);
+        if (hi - lo <= 4.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi))) break;
     }
+    if (lane != 0) return;
     const double lam = 0.5 * (lo + hi);
     // inverse iteration on T - lam I (LU with partial pivoting of the tridiagonal)
     double *u1 = scratch + (size_t)which * 6 * m, *u2 = u1 + m, *u3 = u2 + m, *l = u3 + m, *x = l + m, *fl = x + m;
@@ -903,7 +953,7 @@ void extremal_bounds(mbl_sector *sec, double *emin, double *emax) {
         MBL_LAUNCH_CHECK();
         const int m = j + 1;
         if ((m >= 16 && m % 8 == 0) || m == mmax) {
-            k_tridiag_extremes<<<1, 32, 0, st>>>(m, alpha.data(), beta.data(), scr.data(), out.data());
+            k_tridiag_extremes<<<1, 64, 0, st>>>(m, alpha.data(), beta.data(), scr.data(), out.data());
             MBL_LAUNCH_CHECK();
             double h[4], bj;
             MBL_CUDA(cudaMemcpyAsync(h, out.data(), 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -1097,6 +1147,10 @@ RitzH::RitzH(Ctx *c, int64_t n_, int ldv, int nev_) : ctx(c), n(n_), nev(nev_) {
     HV.alloc(ctx, (size_t)n * ldv);
     Gm.alloc(ctx, (size_t)ldv * ldv);
     Gs.alloc(ctx, (size_t)ldv * ldv);
+    Gsym.alloc(ctx, (size_t)ldv * ldv);
+    Gr1.alloc(ctx, (size_t)ldv * ldv);
+    Gr2.alloc(ctx, (size_t)ldv * ldv);
+    Gr3.alloc(ctx, (size_t)ldv * ldv);
     Gw.alloc(ctx, ldv);
     Gwork.alloc(ctx, syev_work_doubles(ldv));
     Ctmp.alloc(ctx, (size_t)ldv * 32);
@@ -1132,11 +1186,36 @@ void RitzH::run(mbl_sector *sec, KrylovSchur &ks, double sigma, double hnorm, do
     MBL_LAUNCH_CHECK();
     MBL_CUDA(cudaMemcpyAsync(gm.data(), &mb, sizeof(int), cudaMemcpyHostToDevice, st));
     {
-        // FP64: the returned vectors must be accurate one by one, and two refinement steps from FP32
-        // do not separate Ritz values that are closer than the FP32 eigensolver resolves
+        // FP32 eigensolve refined by three Ogita-Aishima steps in FP64; accepted only if the result is
+        // orthonormal and diagonalizes G to FP64 accuracy (close Ritz values can need more steps than
+        // that), otherwise the FP64 eigensolver runs.  The pairs' residuals on H are recomputed below.
         ProfScope ps(ctx, "syev_rr", (double)mb, st);
-        syev_batched(1, gm.data(), goff.data(), goff.data(), Gs.data(), Gw.data(), 1, nullptr, ks.ldv, Gwork.data(),
-                     ginfo.data(), st);
+        const bool fp32 = ks.ldv <= EIG_SMEM_MAX_M;
+        bool ok = false;
+        if (fp32) {
+            MBL_CUDA(cudaMemcpyAsync(Gsym.data(), Gs.data(), (size_t)mb * mb * sizeof(double), cudaMemcpyDeviceToDevice,
+                                     st));
+            syev_batched(1, gm.data(), goff.data(), goff.data(), Gs.data(), Gw.data(), 1, nullptr, ks.ldv,
+                         Gwork.data(), ginfo.data(), st, true);
+            refine_eig(mb, Gsym.data(), Gs.data(), Gw.data(), 3, Gr1.data(), Gr2.data(), Gr3.data(), st);
+            gemm_small(true, false, mb, mb, mb, 1.0, Gs.data(), mb, Gs.data(), mb, 0.0, Gr1.data(), mb, st);
+            gemm_small(false, false, mb, mb, mb, 1.0, Gsym.data(), mb, Gs.data(), mb, 0.0, Gr2.data(), mb, st);
+            gemm_small(true, false, mb, mb, mb, 1.0, Gs.data(), mb, Gr2.data(), mb, 0.0, Gr3.data(), mb, st);
+            k_oa_norms<<<1, 1024, 0, st>>>(mb, Gr1.data(), Gr3.data(), Gr2.data());
+            MBL_LAUNCH_CHECK();
+            double q[3];
+            int info = 0;
+            MBL_CUDA(cudaMemcpyAsync(q, Gr2.data(), sizeof(q), cudaMemcpyDeviceToHost, st));
+            MBL_CUDA(cudaMemcpyAsync(&info, ginfo.data(), sizeof(int), cudaMemcpyDeviceToHost, st));
+            MBL_CUDA(cudaStreamSynchronize(st));
+            ok = info == 0 && q[0] <= 1e-12 && q[1] <= 1e-12 * std::max(q[2], 1e-300);
+            if (!ok)
+                MBL_CUDA(cudaMemcpyAsync(Gs.data(), Gsym.data(), (size_t)mb * mb * sizeof(double),
+                                         cudaMemcpyDeviceToDevice, st));
+        }
+        if (!ok)
+            syev_batched(1, gm.data(), goff.data(), goff.data(), Gs.data(), Gw.data(), 1, nullptr, ks.ldv,
+                         Gwork.data(), ginfo.data(), st);
     }
     std::vector<double> gth(mb);
     MBL_CUDA(cudaMemcpyAsync(gth.data(), Gw.data(), mb * sizeof(double), cudaMemcpyDeviceToHost, st));

@@ -119,9 +119,9 @@ def _reference(orc, H, L, eps, nev):
     return e.evals, sigma, hn
 
 
-def _check_job(g, ctx, orc, L, h, seed, eps, nev, prec, block=8):
+def _check_job(g, ctx, orc, L, h, seed, eps, nev, prec, block=8, **kw):
     sec = g.build_sector(ctx, L, h, seed)
-    res = g.solve_near(sec, eps, nev, precision=prec, block=block)
+    res = g.solve_near(sec, eps, nev, precision=prec, block=block, **kw)
     H = orc.csr(L, orc.fields(L, h, seed))
     spectrum, sigma, hn = _reference(orc, H, L, eps, nev)
     assert abs(res.sigma - sigma) <= 1e-12 * hn
@@ -170,6 +170,22 @@ def test_solve_near_matrix(g, ctx, orc, L, h, seed, eps, nev, prec):
 @pytest.mark.parametrize("block", [1, 4, 16])
 def test_block_sizes(g, ctx, orc, block):
     _check_job(g, ctx, orc, 12, 2.5, 8, 0.6, 16, 1, block=block)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("L", [12, 16])
+def test_dataflow_solve_matches_level_sequence(g, ctx, prec, L):
+    """The persistent dataflow sweeps compute the same block solve as the launch sequence."""
+    sec = g.build_sector(ctx, L, 2.0, 31)
+    lo, hi = g.extremal_bounds(sec)
+    sigma = lo + 0.45 * (hi - lo)
+    B = np.random.default_rng(2).standard_normal((sec.dim, 8))
+    X = [g.factor(sec, sigma, precision=prec, solve_dataflow=df).solve(B, refine=False) for df in (0, 1)]
+    assert np.max(np.abs(X[1] - X[0])) <= 1e-12 * np.max(np.abs(X[0]))
+
+
+def test_dataflow_solve_near(g, ctx, orc):
+    _check_job(g, ctx, orc, 14, 3.0, 5, 0.5, 50, 1, solve_dataflow=1)
 
 
 @pytest.mark.parametrize("L,nev", [(2, 1), (2, 2), (4, 6), (6, 5), (8, 12), (10, 40)])
