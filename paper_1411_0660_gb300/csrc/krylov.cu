@@ -1186,9 +1186,9 @@ void RitzH::run(mbl_sector *sec, KrylovSchur &ks, double sigma, double hnorm, do
     MBL_LAUNCH_CHECK();
     MBL_CUDA(cudaMemcpyAsync(gm.data(), &mb, sizeof(int), cudaMemcpyHostToDevice, st));
     {
-        // FP32 eigensolve refined by three Ogita-Aishima steps in FP64; accepted only if the result is
-        // orthonormal and diagonalizes G to FP64 accuracy (close Ritz values can need more steps than
-        // that), otherwise the FP64 eigensolver runs.  The pairs' residuals on H are recomputed below.
+        // FP32 eigensolve refined by two Ogita-Aishima steps and re-orthonormalized in FP64; accepted
+        // only if the result is orthonormal and diagonalizes G to FP64 accuracy, otherwise the FP64
+        // eigensolver runs.  The pairs' residuals on H are recomputed below.
         ProfScope ps(ctx, "syev_rr", (double)mb, st);
         const bool fp32 = ks.ldv <= EIG_SMEM_MAX_M;
         bool ok = false;
@@ -1197,7 +1197,16 @@ void RitzH::run(mbl_sector *sec, KrylovSchur &ks, double sigma, double hnorm, do
                                      st));
             syev_batched(1, gm.data(), goff.data(), goff.data(), Gs.data(), Gw.data(), 1, nullptr, ks.ldv,
                          Gwork.data(), ginfo.data(), st, true);
-            refine_eig(mb, Gsym.data(), Gs.data(), Gw.data(), 3, Gr1.data(), Gr2.data(), Gr3.data(), st);
+            refine_eig(mb, Gsym.data(), Gs.data(), Gw.data(), 2, Gr1.data(), Gr2.data(), Gr3.data(), st);
+            // the refinement can leave close pairs slightly non-orthogonal: two Newton-Schulz steps
+            // X <- 1.5 X - 0.5 X (X^T X); mixing inside a near-degenerate pair only costs residual
+            // angle x gap, which the diagonalization check below bounds
+            for (int it = 0; it < 2; ++it) {
+                gemm_small(true, false, mb, mb, mb, 1.0, Gs.data(), mb, Gs.data(), mb, 0.0, Gr1.data(), mb, st);
+                MBL_CUDA(cudaMemcpyAsync(Gr2.data(), Gs.data(), (size_t)mb * mb * sizeof(double),
+                                         cudaMemcpyDeviceToDevice, st));
+                gemm_small(false, false, mb, mb, mb, -0.5, Gr2.data(), mb, Gr1.data(), mb, 1.5, Gs.data(), mb, st);
+            }
             gemm_small(true, false, mb, mb, mb, 1.0, Gs.data(), mb, Gs.data(), mb, 0.0, Gr1.data(), mb, st);
             gemm_small(false, false, mb, mb, mb, 1.0, Gsym.data(), mb, Gs.data(), mb, 0.0, Gr2.data(), mb, st);
             gemm_small(true, false, mb, mb, mb, 1.0, Gs.data(), mb, Gr2.data(), mb, 0.0, Gr3.data(), mb, st);
@@ -1213,9 +1222,11 @@ void RitzH::run(mbl_sector *sec, KrylovSchur &ks, double sigma, double hnorm, do
                 MBL_CUDA(cudaMemcpyAsync(Gs.data(), Gsym.data(), (size_t)mb * mb * sizeof(double),
                                          cudaMemcpyDeviceToDevice, st));
         }
-        if (!ok)
+        if (!ok) {
+            ProfScope ps2(ctx, "syev_rr_fp64", (double)mb, st);
             syev_batched(1, gm.data(), goff.data(), goff.data(), Gs.data(), Gw.data(), 1, nullptr, ks.ldv,
                          Gwork.data(), ginfo.data(), st);
+        }
     }
     std::vector<double> gth(mb);
     MBL_CUDA(cudaMemcpyAsync(gth.data(), Gw.data(), mb * sizeof(double), cudaMemcpyDeviceToHost, st));
