@@ -199,11 +199,79 @@ def run_case(args):
     return 0
 
 
+def run_workload(args):
+    """Other configurations of the workload table, each printing its own JSON line:
+    l16batch -- batched small sizes: L = 16, h in {1, 2.5, 4} x eps in {0.1, ..., 0.9} x `--seeds`
+                seeds, nev = 50, FP64 fronts, all submitted at once to a server of `--slots` streams;
+    serve    -- a serving stream: Poisson arrivals (`--rate` per second, `--requests` requests) of
+                L in {14, 16, 18, 20} weighted 4:3:2:1, h ~ U[0.5, 5], seed = request id,
+                eps ~ U[0.05, 0.95], nev = 50, mixed precision; p50/p99 latency and throughput."""
+    import numpy as np
+    import torch
+
+    import paper_1411_0660_gb300 as g
+
+    ctx = g.Context(0)
+    srv = g.Server(ctx, slots=args.slots)
+    if args.workload == "l16batch":
+        jobs = [(16, h, s, e / 10.0, g.MBL_PREC_FP64) for s in range(args.seeds) for h in (1.0, 2.5, 4.0)
+                for e in range(1, 10)]
+        for t in [srv.submit(16, 1.0, 10 ** 6 + k, 0.5, 50, precision=g.MBL_PREC_FP64) for k in range(args.slots)]:
+            srv.wait(t)  # warm-up: plan, kernels, graphs
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        tickets = [srv.submit(L_, h, s, e, 50, precision=pr) for (L_, h, s, e, pr) in jobs]
+        out = [srv.wait(t) for t in tickets]
+        host_s = time.perf_counter() - t0
+    else:
+        rng = np.random.default_rng(12345)
+        Ls = rng.choice([14, 16, 18, 20], size=args.requests, p=[0.4, 0.3, 0.2, 0.1])
+        gaps = rng.exponential(1.0 / args.rate, size=args.requests)
+        hs = rng.uniform(0.5, 5.0, size=args.requests)
+        es = rng.uniform(0.05, 0.95, size=args.requests)
+        for L_ in (14, 16, 18, 20):  # warm-up: one request per size builds the plans
+            srv.wait(srv.submit(L_, 1.0, 10 ** 6 + L_, 0.5, 50))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        tickets, due = [], 0.0
+        for k in range(args.requests):
+            due += gaps[k]
+            delay = due - (time.perf_counter() - t0)
+            if delay > 0:
+                time.sleep(delay)
+            tickets.append(srv.submit(int(Ls[k]), float(hs[k]), k, float(es[k]), 50))
+        out = [srv.wait(t) for t in tickets]
+        host_s = time.perf_counter() - t0
+        jobs = list(zip(Ls.tolist(), hs.tolist(), range(args.requests), es.tolist()))
+    st = srv.stats()
+    srv.stop()
+    span_ms = max(r.d_end_ms for r in out) - min(r.d_start_ms for r in out)
+    pairs = sum(r.nconv for r in out)
+    lat = sorted((r.t_end_ms - r.t_submit_ms) for r in out)
+    line = {"workload": args.workload, "jobs": len(out), "slots": args.slots,
+            "eigenpairs_per_s": pairs / (span_ms / 1e3), "eigenpairs_per_s_host": pairs / host_s,
+            "converged": pairs, "requested": 50 * len(out), "device_span_s": span_ms / 1e3, "host_s": host_s,
+            "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+                           "max": lat[-1]},
+            "min_nconv": min(r.nconv for r in out), "peak_reserved_gb": st["peak_reserved_bytes"] / 1e9,
+            "failed": st["failed"]}
+    if args.workload == "serve":
+        line.update({"rate_per_s": args.rate, "by_L": {str(L_): sum(1 for j in jobs if j[0] == L_) for L_ in (14, 16, 18, 20)}})
+    print(json.dumps(line))
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--case", choices=["factor", "solve"], default=None,
                     help="run one factorization (and --reps solves) instead of the benchmark")
     ap.add_argument("--L", type=int, default=18)
+    ap.add_argument("--workload", choices=["l18", "l16batch", "serve"], default="l18",
+                    help="l18: the benchmark line; l16batch / serve: the batched and serving configurations")
+    ap.add_argument("--seeds", type=int, default=8, help="l16batch: seeds per (h, eps)")
+    ap.add_argument("--requests", type=int, default=40, help="serve: number of requests")
+    ap.add_argument("--rate", type=float, default=4.0, help="serve: mean arrivals per second")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--tensor-cores", type=int, default=1)
@@ -219,6 +287,8 @@ def main():
     args = ap.parse_args()
     if args.case:
         return run_case(args)
+    if args.workload != "l18":
+        return run_workload(args)
     if args.impl == "reference":
         return run_reference(args)
 
