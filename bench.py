@@ -254,7 +254,9 @@ def run_workload(args):
             "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
                            "max": lat[-1]},
             "min_nconv": min(r.nconv for r in out), "peak_reserved_gb": st["peak_reserved_bytes"] / 1e9,
-            "failed": st["failed"]}
+            "failed": st["failed"],
+            "not_converged": [{"L": int(j[0]), "h": float(j[1]), "seed": int(j[2]), "eps": float(j[3]),
+                               "nconv": r.nconv, "status": r.status} for j, r in zip(jobs, out) if r.status != 0]}
     if args.workload == "serve":
         line.update({"rate_per_s": args.rate, "by_L": {str(L_): sum(1 for j in jobs if j[0] == L_) for L_ in (14, 16, 18, 20)}})
     print(json.dumps(line))

@@ -1129,6 +1129,7 @@ RitzH::RitzH(Ctx *c, int64_t n_, int ldv, int nev_) : ctx(c), n(n_), nev(nev_) {
     Gr1.alloc(ctx, (size_t)ldv * ldv);
     Gr2.alloc(ctx, (size_t)ldv * ldv);
     Gr3.alloc(ctx, (size_t)ldv * ldv);
+    M2.alloc(ctx, (size_t)ldv * ldv);
     Gw.alloc(ctx, ldv);
     Gwork.alloc(ctx, syev_work_doubles(ldv));
     Ctmp.alloc(ctx, (size_t)ldv * 32);
@@ -1150,6 +1151,16 @@ RitzH::RitzH(Ctx *c, int64_t n_, int ldv, int nev_) : ctx(c), n(n_), nev(nev_) {
     MBL_CUDA(cudaMemcpy(goff.data(), &z, sizeof(int64_t), cudaMemcpyHostToDevice));
 }
 
+// Residual norms of all Ritz pairs of H on an orthonormal basis V: with M2 = (HV)^T (HV),
+// Q = M2 S and the Ritz pair (theta_j, V s_j), ||H V s_j - theta_j V s_j||^2 = s_j^T Q e_j - theta_j^2.
+__global__ void k_ritz_all_resid(int m, const double *S, const double *Q, const double *theta, double *out) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= m) return;
+    double s = 0.0;
+    for (int i = 0; i < m; ++i) s += S[(size_t)j * m + i] * Q[(size_t)j * m + i];
+    out[j] = sqrt(fmax(0.0, s - theta[j] * theta[j]));
+}
+
 void RitzH::run(mbl_sector *sec, KrylovSchur &ks, double sigma, double hnorm, double tol, double *d_evecs,
                 cudaStream_t st) {
     ProfScope ps_all(ctx, "ritz_h", (double)nev, st);
@@ -1159,6 +1170,13 @@ void RitzH::run(mbl_sector *sec, KrylovSchur &ks, double sigma, double hnorm, do
         int w = std::min(32, mb - c0);
         dense_tn(n, ks.V.data(), ks.ldv, 0, mb, HV.data(), mb, c0, w, Ctmp.data(), work.data(), st);
         copy_cols(mb, Ctmp.data(), w, 0, Gm.data() + (size_t)c0, mb, 0, w, st);
+    }
+    // M2 = (HV)^T (HV): residuals of every Ritz pair, to keep spurious interior Ritz values (which
+    // plain Rayleigh-Ritz produces for a subspace that mixes both sides of sigma) out of the window
+    for (int c0 = 0; c0 < mb; c0 += 32) {
+        int w = std::min(32, mb - c0);
+        dense_tn(n, HV.data(), mb, 0, mb, HV.data(), mb, c0, w, Ctmp.data(), work.data(), st);
+        copy_cols(mb, Ctmp.data(), w, 0, M2.data() + (size_t)c0, mb, 0, w, st);
     }
     k_pack_sym<<<nblk((int64_t)mb * mb), 256, 0, st>>>(Gm.data(), mb, mb, Gs.data());
     MBL_LAUNCH_CHECK();
@@ -1207,10 +1225,25 @@ void RitzH::run(mbl_sector *sec, KrylovSchur &ks, double sigma, double hnorm, do
                          Gwork.data(), ginfo.data(), st);
         }
     }
-    std::vector<double> gth(mb);
+    gemm_small(false, false, mb, mb, mb, 1.0, M2.data(), mb, Gs.data(), mb, 0.0, Gr1.data(), mb, st);
+    k_ritz_all_resid<<<nblk(mb, 128), 128, 0, st>>>(mb, Gs.data(), Gr1.data(), Gw.data(), Gr2.data());
+    MBL_LAUNCH_CHECK();
+    std::vector<double> gth(mb), gres(mb);
     MBL_CUDA(cudaMemcpyAsync(gth.data(), Gw.data(), mb * sizeof(double), cudaMemcpyDeviceToHost, st));
+    MBL_CUDA(cudaMemcpyAsync(gres.data(), Gr2.data(), mb * sizeof(double), cudaMemcpyDeviceToHost, st));
     MBL_CUDA(cudaStreamSynchronize(st));
-    std::vector<int> idx = nearest_sorted(gth, sigma, nev);
+    // candidates: Ritz pairs with residual <= 1e-3 ||H|| (a spurious value sits near 0.1 ||H||)
+    std::vector<int> cand;
+    for (int j = 0; j < mb; ++j)
+        if (gres[j] <= 1e-3 * hnorm) cand.push_back(j);
+    std::vector<int> idx;
+    if ((int)cand.size() >= nev) {
+        std::vector<double> cth(cand.size());
+        for (size_t u = 0; u < cand.size(); ++u) cth[u] = gth[cand[u]];
+        for (int u : nearest_sorted(cth, sigma, nev)) idx.push_back(cand[u]);
+    } else {
+        idx = nearest_sorted(gth, sigma, nev);
+    }
     MBL_CUDA(cudaMemcpyAsync(didx.data(), idx.data(), nev * sizeof(int), cudaMemcpyHostToDevice, st));
     k_gather_S<<<nblk((int64_t)mb * nev), 256, 0, st>>>(Gs.data(), mb, didx.data(), nev, SKs.data());
     MBL_LAUNCH_CHECK();

@@ -188,6 +188,29 @@ def test_dataflow_solve_near(g, ctx, orc):
     _check_job(g, ctx, orc, 14, 3.0, 5, 0.5, 50, 1, solve_dataflow=1)
 
 
+@pytest.mark.parametrize("L,h,seed,eps,prec", [(16, 1.0, 1, 0.4, 0), (16, 2.5, 1, 0.6, 0)])
+def test_window_has_no_spurious_ritz_values(g, ctx, orc, L, h, seed, eps, prec):
+    """Jobs where plain Rayleigh-Ritz on H kept a spurious interior Ritz value in the window: every
+    returned pair must be an eigenpair (oracle residual), and the window [min, max] must hold exactly
+    nev eigenvalues, counted by the oracle's LDL^T inertia (Sylvester) at both ends."""
+    nev = 50
+    sec = g.build_sector(ctx, L, h, seed)
+    res = g.solve_near(sec, eps, nev, precision=prec)
+    lo, hi = g.extremal_bounds(sec)
+    sec.close()
+    hn = max(abs(lo), abs(hi))
+    assert res.nconv == nev
+    H = orc.csr(L, orc.fields(L, h, seed))
+    for j in range(nev):
+        assert np.linalg.norm(H.matvec(res.evecs[:, j]) - res.evals[j] * res.evecs[:, j]) <= EIG_TOL * hn
+    ev = np.sort(res.evals)
+    gap_lo, gap_hi = 0.5 * (ev[1] - ev[0]), 0.5 * (ev[-1] - ev[-2])
+    F = orc.LDLT(H)
+    below_lo = F.factor(ev[0] - min(gap_lo, 1e-9 * hn)).negative
+    below_hi = F.factor(ev[-1] + min(gap_hi, 1e-9 * hn)).negative
+    assert below_hi - below_lo == nev
+
+
 @pytest.mark.parametrize("L,nev", [(2, 1), (2, 2), (4, 6), (6, 5), (8, 12), (10, 40)])
 def test_dense_route_small_sectors(g, ctx, orc, L, nev):
     _check_job(g, ctx, orc, L, 1.5, 9, 0.5, nev, 1)
