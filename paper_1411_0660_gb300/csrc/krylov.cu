@@ -1151,6 +1151,11 @@ RitzH::RitzH(Ctx *c, int64_t n_, int ldv, int nev_) : ctx(c), n(n_), nev(nev_) {
     MBL_CUDA(cudaMemcpy(goff.data(), &z, sizeof(int64_t), cudaMemcpyHostToDevice));
 }
 
+__global__ void k_copy_diag(int m, const double *S, double *out) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < m) out[j] = S[(size_t)j * m + j];
+}
+
 // Residual norms of all Ritz pairs of H on an orthonormal basis V: with M2 = (HV)^T (HV),
 // Q = M2 S and the Ritz pair (theta_j, V s_j), ||H V s_j - theta_j V s_j||^2 = s_j^T Q e_j - theta_j^2.
 __global__ void k_ritz_all_resid(int m, const double *S, const double *Q, const double *theta, double *out) {
@@ -1215,9 +1220,14 @@ void RitzH::run(mbl_sector *sec, KrylovSchur &ks, double sigma, double hnorm, do
             for (double v : th) amax = std::max(amax, std::fabs(v));
             ok = info == 0;
             for (int j : nearest_sorted(th, sigma, nev)) ok = ok && q[j] <= 1e-12 && q[mb + j] <= 1e-12 * amax;
-            if (!ok)
+            if (ok) {
+                // the Ritz values are the Rayleigh quotients of the final vectors: diag(X^T G X)
+                k_copy_diag<<<nblk(mb, 128), 128, 0, st>>>(mb, Gr3.data(), Gw.data());
+                MBL_LAUNCH_CHECK();
+            } else {
                 MBL_CUDA(cudaMemcpyAsync(Gs.data(), Gsym.data(), (size_t)mb * mb * sizeof(double),
                                          cudaMemcpyDeviceToDevice, st));
+            }
         }
         if (!ok) {
             ProfScope ps2(ctx, "syev_rr_fp64", (double)mb, st);
