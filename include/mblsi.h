@@ -70,6 +70,7 @@ typedef struct mbl_opts {
     int gmres_restart;    /* FGMRES inner dimension before a restart (1..64)          [24]   */
     int solve_dataflow;   /* 1: solves as one persistent dataflow kernel per sweep; 0: one */
                           /*    graph-captured launch per level gather and solve panel  [0]    */
+    int deflate;          /* FGMRES preconditioner deflated by the kept Ritz vectors    [1]    */
 } mbl_opts;
 
 typedef struct mbl_factor_stats {

@@ -26,7 +26,7 @@ class Opts(ctypes.Structure):
     _fields_ = [("precision", c_int), ("block", c_int), ("ncv", c_int), ("max_restarts", c_int),
                 ("tol", c_double), ("target_tol", c_double), ("refine_tol", c_double), ("max_refine", c_int),
                 ("start_seed", c_uint64), ("tensor_cores", c_int), ("refine_mode", c_int),
-                ("gmres_restart", c_int), ("solve_dataflow", c_int)]
+                ("gmres_restart", c_int), ("solve_dataflow", c_int), ("deflate", c_int)]
 
 
 class FactorStats(ctypes.Structure):

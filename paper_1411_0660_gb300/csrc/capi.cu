@@ -240,6 +240,7 @@ void mbl_opts_default(mbl_opts *o) {
     o->refine_mode = 1;
     o->gmres_restart = 24;
     o->solve_dataflow = 0;
+    o->deflate = 1;
 }
 
 const char *mbl_version(void) { return "mblsi 0.1 (sm_103a)"; }

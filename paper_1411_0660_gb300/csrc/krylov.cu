@@ -328,6 +328,7 @@ KrylovSchur::KrylovSchur(Ctx *c, int64_t n_, int p_, int ncv_) : ctx(c), n(n_), 
     NS2.alloc(ctx, (size_t)ldv * ldv);
     NS3.alloc(ctx, (size_t)ldv * ldv);
     Ts.alloc(ctx, (size_t)ldv * ldv);
+    chk.alloc(ctx, (size_t)2 * ldv);
     Bk.alloc(ctx, (size_t)p * ldv);
     int64_t zero2[2] = {0, 0};
     MBL_CUDA(cudaMemcpy(eigOff.data(), zero2, sizeof(zero2), cudaMemcpyHostToDevice));
@@ -400,7 +401,7 @@ void KrylovSchur::expand(const OpFn &op, cudaStream_t st) {
     m += p;
 }
 
-void KrylovSchur::ritz(cudaStream_t st, std::vector<double> &theta, std::vector<double> &rnorm) {
+void KrylovSchur::ritz(cudaStream_t st, std::vector<double> &theta, std::vector<double> &rnorm, int nkeep) {
     int mm = m - p;
     k_pack_sym<<<nblk((int64_t)mm * mm), 256, 0, st>>>(T.data(), ldv, mm, eigA.data());
     MBL_LAUNCH_CHECK();
@@ -421,16 +422,37 @@ void KrylovSchur::ritz(cudaStream_t st, std::vector<double> &theta, std::vector<
         int info = 0;
         MBL_CUDA(cudaMemcpyAsync(&info, eigInfo.data(), sizeof(int), cudaMemcpyDeviceToHost, st));
         MBL_CUDA(cudaStreamSynchronize(st));
-        if (fp32 && info != 0) {  // QL did not converge in FP32: redo in FP64
+        bool ok = !fp32;
+        if (fp32 && info == 0) {
+            ProfScope ps3(ctx, "oa_refine", (double)mm, st);
+            refine_eig(mm, Ts.data(), eigA.data(), eigW.data(), 2, NS1.data(), NS2.data(), NS3.data(), st);
+            // accept only if the columns the restart may keep (largest |theta|) are orthonormal and
+            // invariant to FP64 accuracy relative to ||T||; a wide spread of |theta| (sigma very
+            // close to an eigenvalue) can leave them at FP32 accuracy
+            const double *X = eigA.data();
+            gemm_small(true, false, mm, mm, mm, 1.0, X, mm, X, mm, 0.0, NS1.data(), mm, st);
+            gemm_small(false, false, mm, mm, mm, 1.0, Ts.data(), mm, X, mm, 0.0, NS2.data(), mm, st);
+            gemm_small(true, false, mm, mm, mm, 1.0, X, mm, NS2.data(), mm, 0.0, NS3.data(), mm, st);
+            k_oa_colnorms<<<nblk(mm, 128), 128, 0, st>>>(mm, NS1.data(), NS3.data(), chk.data());
+            MBL_LAUNCH_CHECK();
+            std::vector<double> q((size_t)2 * mm), th(mm);
+            MBL_CUDA(cudaMemcpyAsync(q.data(), chk.data(), q.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+            MBL_CUDA(cudaMemcpyAsync(th.data(), eigW.data(), mm * sizeof(double), cudaMemcpyDeviceToHost, st));
+            MBL_CUDA(cudaStreamSynchronize(st));
+            std::vector<int> ord(mm);
+            std::iota(ord.begin(), ord.end(), 0);
+            std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return std::fabs(th[a]) > std::fabs(th[b]); });
+            const double tmax = std::fabs(th[ord[0]]);
+            ok = true;
+            for (int u = 0; u < std::min(nkeep, mm); ++u)
+                ok = ok && q[ord[u]] <= 1e-12 && q[mm + ord[u]] <= 1e-12 * tmax;
+        }
+        if (!ok && fp32) {  // FP32 QL failed or the refined kept vectors are not FP64-accurate
             ProfScope ps2(ctx, "syev_fallback", (double)mm, st);
             k_pack_sym<<<nblk((int64_t)mm * mm), 256, 0, st>>>(T.data(), ldv, mm, eigA.data());
             MBL_LAUNCH_CHECK();
             syev_batched(1, eigM.data(), eigOff.data(), eigOff.data(), eigA.data(), eigW.data(), 1, nullptr, ldv,
                          eigWork.data(), eigInfo.data(), st, false);
-        }
-        if (fp32) {
-            ProfScope ps3(ctx, "oa_refine", (double)mm, st);
-            refine_eig(mm, Ts.data(), eigA.data(), eigW.data(), 2, NS1.data(), NS2.data(), NS3.data(), st);
         }
     }
     k_ritz_resid<<<nblk(mm, 128), 128, 0, st>>>(T.data(), ldv, mm, p, eigA.data(), res.data());
@@ -637,6 +659,122 @@ __global__ void k_gm_update(int64_t n, int k, int p, const double *Z, int64_t zs
     X[t] += s;
 }
 
+// In-place inverse of a k x k row-major matrix by Gauss-Jordan elimination with partial pivoting
+// (one CTA, matrix in shared memory).  *flag = 0 if a pivot vanished.
+__global__ void __launch_bounds__(512) k_small_inverse(int k, double *A, int *flag) {
+    extern __shared__ double sa[];
+    __shared__ int perm[128], s_p;
+    __shared__ double s_piv;
+    const int t = threadIdx.x;
+    for (int i = t; i < k * k; i += blockDim.x) sa[i] = A[i];
+    if (t == 0) *flag = 1;
+    __syncthreads();
+    for (int j = 0; j < k; ++j) {
+        if (t == 0) {
+            int p = j;
+            double best = fabs(sa[j * k + j]);
+            for (int i = j + 1; i < k; ++i)
+                if (fabs(sa[i * k + j]) > best) {
+                    best = fabs(sa[i * k + j]);
+                    p = i;
+                }
+            s_p = p;
+            perm[j] = p;
+        }
+        __syncthreads();
+        const int p = s_p;
+        if (p != j)
+            for (int c = t; c < k; c += blockDim.x) {
+                const double x = sa[j * k + c];
+                sa[j * k + c] = sa[p * k + c];
+                sa[p * k + c] = x;
+            }
+        __syncthreads();
+        if (t == 0) {
+            s_piv = sa[j * k + j];
+            if (!(fabs(s_piv) > 1e-300)) {
+                *flag = 0;
+                s_piv = 1.0;
+            }
+            sa[j * k + j] = 1.0;
+        }
+        __syncthreads();
+        const double ip = 1.0 / s_piv;
+        for (int c = t; c < k; c += blockDim.x) sa[j * k + c] *= ip;
+        __syncthreads();
+        for (int idx = t; idx < k * k; idx += blockDim.x) {
+            const int i = idx / k, c = idx % k;
+            if (i == j || c == j) continue;
+            sa[i * k + c] -= sa[i * k + j] * sa[j * k + c];
+        }
+        __syncthreads();
+        for (int i = t; i < k; i += blockDim.x)
+            if (i != j) sa[i * k + j] = -sa[i * k + j] * sa[j * k + j];
+        __syncthreads();
+    }
+    // the row swaps of the elimination become column swaps of the inverse, undone in reverse order
+    for (int j = k - 1; j >= 0; --j) {
+        const int p = perm[j];
+        if (p != j)
+            for (int i = t; i < k; i += blockDim.x) {
+                const double x = sa[i * k + j];
+                sa[i * k + j] = sa[i * k + p];
+                sa[i * k + p] = x;
+            }
+        __syncthreads();
+    }
+    for (int i = t; i < k * k; i += blockDim.x) A[i] = sa[i];
+}
+
+void RefinedSolve::set_deflation(const double *U_, int ldu_, int k, cudaStream_t st) {
+    kd = 0;
+    if (k <= 0) return;
+    k = std::min(k, 90);
+    const int64_t n = sec->n;
+    Ctx *ctx = sec->ctx;
+    if (AU.size() < (size_t)n * k) AU.alloc(ctx, (size_t)n * k);
+    if (Einv.size() < (size_t)k * k) Einv.alloc(ctx, (size_t)k * k);
+    if (Dc0.size() < (size_t)k * 32) Dc0.alloc(ctx, (size_t)k * 32);
+    if (Dc1.size() < (size_t)k * 32) Dc1.alloc(ctx, (size_t)k * 32);
+    if (Dwork.size() < dense_tn_work(n, k, std::max(k, 32)) + 64) Dwork.alloc(ctx, dense_tn_work(n, k, std::max(k, 32)) + 64);
+    if (Dflag.size() < 1) Dflag.alloc(ctx, 1);
+    // A U, then E = U^T A U (k x k, row-major) and its inverse
+    launch_spmv(sec, fz->sigma, U_, ldu_, 1, AU.data(), k, 1, k, st);
+    dense_tn(n, U_, ldu_, 0, k, AU.data(), k, 0, k, Einv.data(), Dwork.data(), st);
+    static std::atomic<bool> attr{false};  // per process: one device
+    if (!attr) {
+        MBL_CUDA(cudaFuncSetAttribute(k_small_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, 90 * 90 * 8));
+        attr = true;
+    }
+    k_small_inverse<<<1, 512, (size_t)k * k * sizeof(double), st>>>(k, Einv.data(), Dflag.data());
+    MBL_LAUNCH_CHECK();
+    int ok = 0;
+    MBL_CUDA(cudaMemcpyAsync(&ok, Dflag.data(), sizeof(int), cudaMemcpyDeviceToHost, st));
+    MBL_CUDA(cudaStreamSynchronize(st));
+    if (!ok) return;
+    U = U_;
+    ldu = ldu_;
+    kd = k;
+}
+
+void RefinedSolve::precondition(const double *V, double *Z, int p, cudaStream_t st) {
+    if (kd == 0) {
+        factor_solve_raw(*fz, V, p, Z, p, p, false, st);
+        return;
+    }
+    const int64_t n = sec->n;
+    if (Dt.size() < (size_t)n * p) Dt.alloc(sec->ctx, (size_t)n * p);
+    // c = E^-1 U^T v  (kd x p, row-major)
+    dense_tn(n, U, ldu, 0, kd, V, p, 0, p, Dc0.data(), Dwork.data(), st);
+    gemm_small(false, false, p, kd, kd, 1.0, Dc0.data(), p, Einv.data(), kd, 0.0, Dc1.data(), p, st);
+    // z = M^-1 (v - A U c) + U c
+    MBL_CUDA(cudaMemcpyAsync(Dt.data(), V, (size_t)n * p * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    dense_nn_sub(n, AU.data(), kd, 0, kd, Dc1.data(), p, Dt.data(), st);
+    factor_solve_raw(*fz, Dt.data(), p, Z, p, p, false, st);
+    gemm_small(false, false, p, kd, kd, -1.0, Dc0.data(), p, Einv.data(), kd, 0.0, Dc1.data(), p, st);
+    dense_nn_sub(n, U, ldu, 0, kd, Dc1.data(), p, Z, st);
+}
+
 void RefinedSolve::apply_fgmres(const double *X, int ldx, double *Y, int p, cudaStream_t st) {
     const int64_t n = sec->n;
     Ctx *ctx = sec->ctx;
@@ -680,7 +818,7 @@ void RefinedSolve::apply_fgmres(const double *X, int ldx, double *Y, int p, cuda
             // Z_k = M^-1 V_k ; W = (H - sigma) Z_k
             k_zero<<<nblk(blk), 256, 0, st>>>(Zk, blk);
             MBL_LAUNCH_CHECK();
-            factor_solve_raw(*fz, Vk, p, Zk, p, p, false, st);
+            precondition(Vk, Zk, p, st);
             ++solves;
             launch_spmv(sec, fz->sigma, Zk, p, 1, GW.data(), p, 1, p, st);
             // two Gram-Schmidt passes against V_0..V_k (each column its own space)
@@ -1073,7 +1211,7 @@ void solve_near(mbl_sector *sec, double eps, int nev, const mbl_opts &o, double 
                 S.fp64_fallback = 1;
             }
         }
-        ks.ritz(st, th, rn);
+        ks.ritz(st, th, rn, k_keep);
         int mm = (int)th.size();
         std::vector<int> order(mm);
         std::iota(order.begin(), order.end(), 0);
@@ -1098,6 +1236,9 @@ void solve_near(mbl_sector *sec, double eps, int nev, const mbl_opts &o, double 
         std::vector<int> keep(order.begin(), order.begin() + k_keep);
         std::sort(keep.begin(), keep.end());
         ks.restart(keep, st);
+        // the kept Ritz vectors approximate the eigenvectors nearest sigma, where the factor is
+        // weakest: deflate them from the refinement's preconditioner
+        if (op.gmres && o.deflate) op.set_deflation(ks.V.data(), ks.ldv, std::min(k_keep, 90), st);
     }
     {
         unsigned long long tmo = 0;  // bounded waits of the dataflow solves that expired

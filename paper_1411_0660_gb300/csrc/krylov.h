@@ -17,7 +17,7 @@ struct KrylovSchur {
     int64_t n;
     int p, ncv, ldv;
     int m = 0;  // basis columns; the first m - p have been expanded
-    DVec<double> V, V2, W, T, C1, C2, R1, R2, Rm, G, work, eigA, eigW, eigWork, res, SK, NS1, NS2, NS3, Ts, Bk;
+    DVec<double> V, V2, W, T, C1, C2, R1, R2, Rm, G, work, eigA, eigW, eigWork, res, SK, NS1, NS2, NS3, Ts, chk, Bk;
     DVec<int> flag, eigInfo, eigM, keep;
     DVec<int64_t> eigOff;
 
@@ -26,7 +26,8 @@ struct KrylovSchur {
     void start(uint64_t seed, cudaStream_t st);
     void expand(const OpFn &op, cudaStream_t st);
     // Ritz values (ascending) of the expanded part and their Krylov-Schur residual norms
-    void ritz(cudaStream_t st, std::vector<double> &theta, std::vector<double> &rnorm);
+    // nkeep: how many of the largest |theta| the next restart may keep (their accuracy is checked)
+    void ritz(cudaStream_t st, std::vector<double> &theta, std::vector<double> &rnorm, int nkeep);
     // keep the listed Ritz pairs (indices into the last ritz() result) plus the residual block
     void restart(const std::vector<int> &keep_idx, cudaStream_t st);
 
@@ -47,7 +48,17 @@ struct RefinedSolve {
     int gmres = 1;     // 1: FGMRES refinement (factor as right preconditioner); 0: plain refinement
     int kmax = 24;     // FGMRES inner dimension
     DVec<double> R, part, norms, GV, GZ, GW, Gh, Gy, Gdots;
+    // Deflation of the preconditioner (FGMRES mode): with U (n x kd, row stride ldu) approximate
+    // eigenvectors nearest sigma and A = H - sigma, the preconditioner is
+    //   P = M^-1 (I - A Q) + Q,   Q = U (U^T A U)^-1 U^T,
+    // M the factor: the directions where the factor is weakest are solved in span(U) exactly.
+    const double *U = nullptr;
+    int ldu = 0, kd = 0;
+    DVec<double> AU, Einv, Dc0, Dc1, Dt, Dwork;
+    DVec<int> Dflag;
     void apply(const double *X, int ldx, double *Y, int p, cudaStream_t st);
+    // Use U[:, 0:k] (k <= 90; k = 0 switches deflation off); U must stay unchanged until the next call.
+    void set_deflation(const double *U_, int ldu_, int k, cudaStream_t st);
 
   private:
     // true residual R = B - (H - sigma) Y; returns the worst ratio ||r_q|| / (rtol (anorm ||y_q|| + ||b_q||))
@@ -55,6 +66,7 @@ struct RefinedSolve {
                     std::vector<double> *lim = nullptr);
     void apply_plain(const double *X, int ldx, double *Y, int p, cudaStream_t st);
     void apply_fgmres(const double *X, int ldx, double *Y, int p, cudaStream_t st);
+    void precondition(const double *V, double *Z, int p, cudaStream_t st);  // Z = P V (n x p, ld p)
 };
 
 // Rayleigh-Ritz of H on the whole basis: the nev Ritz pairs nearest sigma and their residuals.
