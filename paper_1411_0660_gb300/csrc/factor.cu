@@ -15,6 +15,7 @@
 #include <cfloat>
 
 #include "factor.h"
+#include "solve_tile.cuh"
 
 namespace mbl {
 
@@ -391,18 +392,6 @@ __device__ __forceinline__ int find_sdesc_k(const SolveDesc *d, int nd, int64_t 
     return lo;
 }
 
-// shared <- global copies that do not hold up the issuing thread (sm_80+ cp.async)
-template <class T>
-__device__ __forceinline__ void cp_async_elem(T *smem, const T *gmem) {
-    const unsigned int sa = (unsigned int)__cvta_generic_to_shared(smem);
-    if (sizeof(T) == 8) asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gmem) : "memory");
-    else asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() {
-    asm volatile("cp.async.commit_group;" ::: "memory");
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
-}
-
 __device__ __forceinline__ int find_sdesc_b(const SolveDesc *d, int nd, int64_t b) {
     int lo = 0, hi = nd - 1;
     while (lo < hi) {
@@ -476,11 +465,12 @@ __global__ void __launch_bounds__(256) k_build_m(const SolveDesc *sdescs, const 
     }
 }
 
-// G = [M; L21 M] in place of a solve panel's column block [k0, f) x [k0, k0 + w): RBB rows per
-// CTA (grid: the step's backward row tiles); each CTA owns its rows, so the update is in place.
+// G = [M; L21 M] of a solve panel (rows [k0, f) of the front x the panel's w columns) into the
+// packed solve factor (column-major, leading dimension sg_ld(f - k0)): RBB rows per CTA (grid: the
+// step's RBB-row tiles).
 template <class T>
 __global__ void __launch_bounds__(256) k_apply_m(const SolveDesc *sdescs, int nd, const int64_t *fo,
-                                                 const int32_t *fsz, T *arena, const T *Mall) {
+                                                 const int32_t *fsz, const T *arena, const T *Mall, T *Gp) {
     extern __shared__ __align__(16) unsigned char smraw[];
     T *As = reinterpret_cast<T *>(smraw);  // RBB x (SPW + 1), row-major
     T *Ms = As + RBB * (SPW + 1);          // 32 x SPW chunk of M, row-major
@@ -490,8 +480,10 @@ __global__ void __launch_bounds__(256) k_apply_m(const SolveDesc *sdescs, int nd
     const int r0 = (int)(blockIdx.x - d.offb) * RBB;  // first row, relative to k0
     const int nr = min(RBB, w + d.m2 - r0);
     if (nr <= 0) return;
-    T *F = arena + fo[s];
+    const T *F = arena + fo[s];
     const T *M = Mall + d.moff;
+    T *G = Gp + d.goff;
+    const int64_t ld = sg_ld(w + d.m2);
     const int tr = threadIdx.x % 16, tc = threadIdx.x / 16;
     T acc[4][16];
 #pragma unroll
@@ -533,7 +525,7 @@ __global__ void __launch_bounds__(256) k_apply_m(const SolveDesc *sdescs, int nd
         for (int j = 0; j < 16; ++j) {
             const int col = tc + 16 * j;
             if (col >= w) continue;
-            F[(int64_t)(k0 + col) * f + k0 + rr] = rr < w ? M[(int64_t)col * w + rr] : acc[i][j];
+            G[(int64_t)col * ld + rr] = rr < w ? M[(int64_t)col * w + rr] : acc[i][j];
         }
     }
 }
@@ -542,28 +534,28 @@ __global__ void __launch_bounds__(256) k_apply_m(const SolveDesc *sdescs, int nd
 // rows of the panel get Zs = M z and rows below get Z -= (L21 M) z.  Warp j takes columns
 // [32 j, 32 j + 32) of the panel; the eight partial sums meet in shared memory.
 template <class T, int PB>
-__global__ void __launch_bounds__(256) k_fwd_step(const SolveDesc *sdescs, int nd, const int64_t *fo,
-                                                  const int64_t *zo, const int32_t *fsz, const int32_t *sn_start,
-                                                  const T *arena, const T *Dg, T *Z, T *Zs, T *yfw, int p) {
+__global__ void __launch_bounds__(256) k_fwd_step(const SolveDesc *sdescs, int nd, const int64_t *zo,
+                                                  const int32_t *sn_start, const T *Gp, const T *Dg, T *Z, T *Zs,
+                                                  T *yfw, int p) {
     extern __shared__ __align__(16) unsigned char smraw[];
     T *zp = reinterpret_cast<T *>(smraw);  // SPW x PB; afterwards the 8 x PB x RBF partials
     pdl_trigger();
     const int di = find_sdesc(sdescs, nd, blockIdx.x);
     const SolveDesc d = sdescs[di];
-    const int s = d.front, f = fsz[s], k0 = d.k0, w = d.w;
+    const int s = d.front, k0 = d.k0, w = d.w;
     const int r0 = (int)(blockIdx.x - d.off) * RBF;  // relative to k0
     const int nr = min(RBF, w + d.m2 - r0);
-    const int64_t zb = zo[s] + k0;
+    const int64_t zb = zo[s] + k0, ld = sg_ld(w + d.m2);
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
     const int c0 = wp * 32, c1 = min(w, c0 + 32);
     const bool active = lane < nr && c0 < c1, full = c1 - c0 == 32;
-    const T *g = arena + fo[s] + (int64_t)k0 * f + k0 + r0 + lane;
+    const T *g = Gp + d.goff + r0 + lane;
     // the factor does not change during a solve: stream this thread's row of G before waiting for
     // the previous step
     T lv[32];
     if (active && full) {
 #pragma unroll
-        for (int c = 0; c < 32; ++c) lv[c] = g[(int64_t)(c0 + c) * f];
+        for (int c = 0; c < 32; ++c) lv[c] = g[(int64_t)(c0 + c) * ld];
     }
     pdl_wait();
     for (int idx = threadIdx.x; idx < w * PB; idx += blockDim.x) {
@@ -582,7 +574,7 @@ __global__ void __launch_bounds__(256) k_fwd_step(const SolveDesc *sdescs, int n
                 for (int q = 0; q < PB; ++q) acc[q] += lv[c] * zp[(c0 + c) * PB + q];
         } else {
             for (int c = c0; c < c1; ++c) {
-                const T l = g[(int64_t)c * f];
+                const T l = g[(int64_t)c * ld];
 #pragma unroll
                 for (int q = 0; q < PB; ++q) acc[q] += l * zp[c * PB + q];
             }
@@ -650,21 +642,23 @@ __global__ void k_bwd_gather(const AsmItem *items, const int64_t *zo, const int3
     }
 }
 
-// Backward solve step, blocks of RBK rows x RBB columns of G = [M; L21 M] (grid: row blocks x
-// column chunks): x_panel = G^T v with v = [y_panel; -x_below].  The block of G is copied to shared
-// memory asynchronously before waiting for the previous step (G does not change during a solve).
-// Each block writes its partial sums; the last block of a (panel, column chunk) to finish (counted
-// with an atomic, after a fence) adds the partials in block order, writes the panel's x into Zs
+// Backward solve step, tiles of RBK rows x RBB columns of G = [M; L21 M] (grid: row blocks x
+// column chunks): x_panel = G^T v with v = [y_panel; -x_below].  The tile is copied from the packed
+// solve factor to shared memory (16-byte cp.async) before waiting for the previous step (G does
+// not change during a solve).  A panel with one row block writes x directly; otherwise each block
+// writes its partial sums and the last block of a (panel, column chunk) to finish (counted with an
+// atomic, after a fence) adds the partials in a fixed order, writes the panel's x into Zs and x,
 // and re-arms the counter.  The panel's rows of Z hold the forward result y (pivoted order); rows
 // below the panel come from Zs (fully summed rows solved by later panels) or Z (the ancestors' x).
 template <class T, int PB>
-__global__ void __launch_bounds__(256) k_bwd_step(const SolveDesc *sdescs, int nd, const int64_t *fo,
-                                                  const int64_t *zo, const int32_t *fsz, const int32_t *nc,
-                                                  const int32_t *sn_start, const T *arena, const T *Z, T *Zs, T *P,
-                                                  unsigned int *cnt, T *x, int p) {
+__global__ void __launch_bounds__(256) k_bwd_step(const SolveDesc *sdescs, int nd, const int64_t *zo,
+                                                  const int32_t *nc, const int32_t *sn_start, const T *Gp,
+                                                  const T *Z, T *Zs, T *P, unsigned int *cnt, T *x, int p) {
+    constexpr int E = 16 / sizeof(T);
     extern __shared__ __align__(16) unsigned char smraw[];
-    T *Gs = reinterpret_cast<T *>(smraw);  // RBK x (RBB + 1), row-major
-    T *vs = Gs + RBK * (RBB + 1);          // RBK x PB
+    T *Gs = reinterpret_cast<T *>(smraw);    // RBB columns x bwd_ldg rows
+    T *vs = Gs + RBB * bwd_ldg<T>();         // RBK x PB
+    T *red = PB == 8 ? Gs : vs + RBK * PB;  // 8 warps x 8 x RBB partial sums
     __shared__ int s_last;
     pdl_trigger();
     const int di = find_sdesc_k(sdescs, nd, blockIdx.x);
@@ -674,20 +668,13 @@ __global__ void __launch_bounds__(256) k_bwd_step(const SolveDesc *sdescs, int n
         pdl_wait();
         return;
     }
-    const int s = d.front, f = fsz[s], k0 = d.k0, w = d.w, ncs = nc[s];
-    const int b = (int)(blockIdx.x - d.offk);
-    const int nb = (w + d.m2 + RBK - 1) / RBK;
+    const int s = d.front, k0 = d.k0, w = d.w, ncs = nc[s], R = w + d.m2;
+    const int b = (int)(blockIdx.x - d.offk), nb = (R + RBK - 1) / RBK;
     const int r0 = b * RBK;  // relative to k0
-    const int nr = min(RBK, w + d.m2 - r0);
+    const int nr = min(RBK, R - r0), nrv = (nr + E - 1) / E;
     const int wc = min(RBB, w - cc);
-    const int64_t zb = zo[s] + k0;
-    const T *F = arena + fo[s] + (int64_t)(k0 + cc) * f + k0 + r0;
-    for (int idx = threadIdx.x; idx < RBK * RBB; idx += blockDim.x) {
-        const int i = idx % RBK, c = idx / RBK;
-        T *dst = Gs + i * (RBB + 1) + c;
-        if (i < nr && c < wc) cp_async_elem(dst, F + (int64_t)c * f + i);
-        else *dst = T(0);
-    }
+    const int64_t zb = zo[s] + k0, ld = sg_ld(R);
+    bwd_tile_issue(Gs, Gp + d.goff + (int64_t)cc * ld + r0, ld, wc, nrv);
     pdl_wait();
     for (int idx = threadIdx.x; idx < RBK * PB; idx += blockDim.x) {
         const int i = idx / PB, q = idx % PB;
@@ -700,24 +687,29 @@ __global__ void __launch_bounds__(256) k_bwd_step(const SolveDesc *sdescs, int n
         }
         vs[idx] = v;
     }
-    cp_async_wait_all();
+    cp_async_commit_wait();
     __syncthreads();
-    constexpr int QP = PB / 4;
-    const int c = threadIdx.x % RBB, qg = threadIdx.x / RBB;
-    T acc[QP];
-#pragma unroll
-    for (int k = 0; k < QP; ++k) acc[k] = T(0);
-    const int nrr = (nr + 7) & ~7;  // padded rows of Gs and vs are zero
-#pragma unroll 8
-    for (int i = 0; i < nrr; ++i) {
-        const T gv = Gs[i * (RBB + 1) + c];
-#pragma unroll
-        for (int k = 0; k < QP; ++k) acc[k] += gv * vs[i * PB + qg + 4 * k];
-    }
     const int64_t tile = (int64_t)RBB * PB;
     T *out = P + ((d.offk + b) * SUBS + blockIdx.y) * tile;
+    T *zsp = Zs + (zb + cc) * p, *xp = x + ((int64_t)sn_start[s] + k0 + cc) * p;
 #pragma unroll
-    for (int k = 0; k < QP; ++k) out[(qg + 4 * k) * RBB + c] = acc[k];
+    for (int q0 = 0; q0 < PB; q0 += 8) {
+        T o2[2];
+        bwd_tile_product<T, PB>(Gs, vs, red, nrv * E, q0, o2);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int o = threadIdx.x + 256 * h, q = q0 + o / RBB, c = o % RBB;
+            if (nb == 1) {
+                if (c < wc && q < p) {
+                    zsp[c * p + q] = o2[h];
+                    xp[c * p + q] = o2[h];
+                }
+            } else {
+                out[q * RBB + c] = o2[h];
+            }
+        }
+    }
+    if (nb == 1) return;
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -727,22 +719,7 @@ __global__ void __launch_bounds__(256) k_bwd_step(const SolveDesc *sdescs, int n
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    const T *src0 = P + (d.offk * SUBS + blockIdx.y) * tile;
-    for (int o = threadIdx.x; o < wc * p; o += blockDim.x) {
-        const int cq = o % wc, q = o / wc;
-        const T *src = src0 + q * RBB + cq;
-        const int64_t stride = (int64_t)SUBS * tile;
-        T v4[4] = {T(0), T(0), T(0), T(0)};
-        int bb = 0;
-        for (; bb + 4 <= nb; bb += 4) {
-#pragma unroll
-            for (int u = 0; u < 4; ++u) v4[u] += __ldcg(src + (int64_t)(bb + u) * stride);
-        }
-        for (; bb < nb; ++bb) v4[0] += __ldcg(src + (int64_t)bb * stride);
-        const T xv = (v4[0] + v4[1]) + (v4[2] + v4[3]);
-        Zs[(zb + cc + cq) * p + q] = xv;
-        x[((int64_t)sn_start[s] + k0 + cc + cq) * p + q] = xv;
-    }
+    bwd_finish<T, PB>(P + (d.offk * SUBS + blockIdx.y) * tile, (int64_t)SUBS * tile, nb, wc, p, zsp, xp, Gs);
     if (threadIdx.x == 0) cnt[(size_t)di * SUBS + blockIdx.y] = 0u;
 }
 
@@ -758,7 +735,7 @@ static size_t apply_m_smem() { return sizeof(T) * ((size_t)RBB * (SPW + 1) + (si
 template <class T, int PB>
 static size_t fwd_step_smem() { return sizeof(T) * (size_t)SPW * PB; }
 template <class T, int PB>
-static size_t bwd_step_smem() { return sizeof(T) * ((size_t)RBK * (RBB + 1) + (size_t)RBK * PB); }
+static size_t bwd_step_smem() { return bwd_tile_smem<T, PB>(); }
 static int rhs_pad(int p) { return p <= 8 ? 8 : (p <= 16 ? 16 : 32); }
 
 template <class T, int PB>
@@ -841,17 +818,19 @@ static void factor_impl(Factorization &fz, cudaStream_t st) {
             }
         }
     }
-    // block operators of the solve panels, then G = [M; L21 M] in place of each panel's column block
+    // block operators of the solve panels, then G = [M; L21 M] of each panel into the packed solve factor
     if (!p.sdescs.empty()) {
         dim3 grid((unsigned)p.sdescs.size(), SPW / 32);
         k_build_m<T><<<grid, 256, build_m_smem<T>(), st>>>(p.d_sdescs.data(), p.d_sn_fo.data(), p.d_sn_f.data(),
                                                            p.d_sn_start.data(), arena, fz.piv.data(),
                                                            static_cast<T *>(fz.M.m.p));
         MBL_LAUNCH_CHECK();
+        T *Gp = static_cast<T *>(fz.gpk.m.p);
+        MBL_CUDA(cudaMemsetAsync(Gp, 0, (size_t)p.sg_elems * sizeof(T), st));  // padding rows stay zero
         for (const SolveStep &ss : p.ssteps) {
             k_apply_m<T><<<(unsigned)ss.nrbb, 256, apply_m_smem<T>(), st>>>(p.d_sdescs.data() + ss.d0, ss.nd,
                                                                            p.d_sn_fo.data(), p.d_sn_f.data(), arena,
-                                                                           static_cast<const T *>(fz.M.m.p));
+                                                                           static_cast<const T *>(fz.M.m.p), Gp);
             MBL_LAUNCH_CHECK();
         }
     }
@@ -866,7 +845,7 @@ void numeric_factor(Factorization &fz, cudaStream_t st) {
 template <class T, int PB>
 static void solve_levels(Factorization &fz, int p, cudaStream_t st) {
     Plan &pl = *fz.plan;
-    T *arena = static_cast<T *>(fz.arena.m.p);
+    const T *Gp = static_cast<const T *>(fz.gpk.m.p);
     T *Dg = static_cast<T *>(fz.D.m.p);
     T *Z = static_cast<T *>(fz.zwork.m.p);
     T *Zs = static_cast<T *>(fz.zsolved.m.p);
@@ -888,8 +867,7 @@ static void solve_levels(Factorization &fz, int p, cudaStream_t st) {
             const SolveStep &ss = pl.ssteps[si];
             const SolveDesc *sd = pl.d_sdescs.data() + ss.d0;
             launch_pdl(k_fwd_step<T, PB>, dim3((unsigned)ss.nrb), dim3(256), fsm, st, sd, ss.nd,
-                       pl.d_sn_fo.data(), pl.d_sn_zo.data(), pl.d_sn_f.data(), pl.d_sn_start.data(),
-                       (const T *)arena, (const T *)Dg, Z, Zs, yfw, p);
+                       pl.d_sn_zo.data(), pl.d_sn_start.data(), Gp, (const T *)Dg, Z, Zs, yfw, p);
         }
     }
     for (int l = pl.nlevels - 1; l >= 0; --l) {
@@ -902,8 +880,8 @@ static void solve_levels(Factorization &fz, int p, cudaStream_t st) {
             const SolveStep &ss = pl.ssteps[si];
             const SolveDesc *sd = pl.d_sdescs.data() + ss.d0;
             launch_pdl(k_bwd_step<T, PB>, dim3((unsigned)ss.nrbk, SUBS), dim3(256), bsm, st, sd, ss.nd,
-                       pl.d_sn_fo.data(), pl.d_sn_zo.data(), pl.d_sn_f.data(), pl.d_sn_nc.data(),
-                       pl.d_sn_start.data(), (const T *)arena, (const T *)Z, Zs, P, cnt + (size_t)ss.d0 * SUBS, y, p);
+                       pl.d_sn_zo.data(), pl.d_sn_nc.data(), pl.d_sn_start.data(), Gp, (const T *)Z, Zs, P,
+                       cnt + (size_t)ss.d0 * SUBS, y, p);
         }
     }
 }
@@ -994,6 +972,7 @@ void Factorization::allocate() {
     wscr.alloc(ctx, (size_t)std::max<int64_t>(pl.wscratch_elems, 1) * es);
     cmax.alloc(ctx, (size_t)std::max<int64_t>(pl.max_desc_per_step, 1) * NB * sizeof(unsigned int));
     M.alloc(ctx, (size_t)std::max<int64_t>(pl.m_elems, 1) * es);
+    gpk.alloc(ctx, (size_t)std::max<int64_t>(pl.sg_elems, 1) * es);
     scnt.alloc(ctx, std::max<size_t>(pl.sdescs.size() * SUBS, 1));
     dfcnt.alloc(ctx, (size_t)4 * pl.ns + 2);
     MBL_CUDA(cudaMemset(scnt.data(), 0, std::max<size_t>(pl.sdescs.size() * SUBS, 1) * sizeof(unsigned int)));
@@ -1002,7 +981,8 @@ void Factorization::allocate() {
 void Factorization::release_scratch() {
     wscr.release();
     cmax.release();
-    M.release();  // folded into the fronts (G = [M; L21 M])
+    M.release();      // folded into G = [M; L21 M]
+    arena.release();  // the solves read only the packed G and D
 }
 
 Factorization::~Factorization() {

@@ -13,6 +13,7 @@ struct Factorization {
     int prec = MBL_PREC_FP32;
     double tiny = 0.0;
     DVec<char> arena, D, wscr, cmax, M, zwork, zsolved, ywork, yfw, pwork;
+    DVec<char> gpk;           // packed solve factor: every solve panel's G = [M; L21 M] (Plan::sg_elems)
     DVec<int32_t> piv;
     DVec<unsigned int> scnt;  // per (solve panel, column chunk) arrival counters of the backward step
     DVec<int32_t> dfcnt;      // dataflow solve: per-front completion counters (4 ns) and two tickets

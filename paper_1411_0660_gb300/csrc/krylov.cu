@@ -328,7 +328,6 @@ KrylovSchur::KrylovSchur(Ctx *c, int64_t n_, int p_, int ncv_) : ctx(c), n(n_), 
     NS2.alloc(ctx, (size_t)ldv * ldv);
     NS3.alloc(ctx, (size_t)ldv * ldv);
     Ts.alloc(ctx, (size_t)ldv * ldv);
-    chk.alloc(ctx, (size_t)2 * ldv);
     Bk.alloc(ctx, (size_t)p * ldv);
     int64_t zero2[2] = {0, 0};
     MBL_CUDA(cudaMemcpy(eigOff.data(), zero2, sizeof(zero2), cudaMemcpyHostToDevice));
@@ -401,7 +400,7 @@ void KrylovSchur::expand(const OpFn &op, cudaStream_t st) {
     m += p;
 }
 
-void KrylovSchur::ritz(cudaStream_t st, std::vector<double> &theta, std::vector<double> &rnorm, int nkeep) {
+void KrylovSchur::ritz(cudaStream_t st, std::vector<double> &theta, std::vector<double> &rnorm) {
     int mm = m - p;
     k_pack_sym<<<nblk((int64_t)mm * mm), 256, 0, st>>>(T.data(), ldv, mm, eigA.data());
     MBL_LAUNCH_CHECK();
@@ -422,37 +421,16 @@ void KrylovSchur::ritz(cudaStream_t st, std::vector<double> &theta, std::vector<
         int info = 0;
         MBL_CUDA(cudaMemcpyAsync(&info, eigInfo.data(), sizeof(int), cudaMemcpyDeviceToHost, st));
         MBL_CUDA(cudaStreamSynchronize(st));
-        bool ok = !fp32;
-        if (fp32 && info == 0) {
-            ProfScope ps3(ctx, "oa_refine", (double)mm, st);
-            refine_eig(mm, Ts.data(), eigA.data(), eigW.data(), 2, NS1.data(), NS2.data(), NS3.data(), st);
-            // accept only if the columns the restart may keep (largest |theta|) are orthonormal and
-            // invariant to FP64 accuracy relative to ||T||; a wide spread of |theta| (sigma very
-            // close to an eigenvalue) can leave them at FP32 accuracy
-            const double *X = eigA.data();
-            gemm_small(true, false, mm, mm, mm, 1.0, X, mm, X, mm, 0.0, NS1.data(), mm, st);
-            gemm_small(false, false, mm, mm, mm, 1.0, Ts.data(), mm, X, mm, 0.0, NS2.data(), mm, st);
-            gemm_small(true, false, mm, mm, mm, 1.0, X, mm, NS2.data(), mm, 0.0, NS3.data(), mm, st);
-            k_oa_colnorms<<<nblk(mm, 128), 128, 0, st>>>(mm, NS1.data(), NS3.data(), chk.data());
-            MBL_LAUNCH_CHECK();
-            std::vector<double> q((size_t)2 * mm), th(mm);
-            MBL_CUDA(cudaMemcpyAsync(q.data(), chk.data(), q.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
-            MBL_CUDA(cudaMemcpyAsync(th.data(), eigW.data(), mm * sizeof(double), cudaMemcpyDeviceToHost, st));
-            MBL_CUDA(cudaStreamSynchronize(st));
-            std::vector<int> ord(mm);
-            std::iota(ord.begin(), ord.end(), 0);
-            std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return std::fabs(th[a]) > std::fabs(th[b]); });
-            const double tmax = std::fabs(th[ord[0]]);
-            ok = true;
-            for (int u = 0; u < std::min(nkeep, mm); ++u)
-                ok = ok && q[ord[u]] <= 1e-12 && q[mm + ord[u]] <= 1e-12 * tmax;
-        }
-        if (!ok && fp32) {  // FP32 QL failed or the refined kept vectors are not FP64-accurate
+        if (fp32 && info != 0) {  // QL did not converge in FP32: redo in FP64
             ProfScope ps2(ctx, "syev_fallback", (double)mm, st);
             k_pack_sym<<<nblk((int64_t)mm * mm), 256, 0, st>>>(T.data(), ldv, mm, eigA.data());
             MBL_LAUNCH_CHECK();
             syev_batched(1, eigM.data(), eigOff.data(), eigOff.data(), eigA.data(), eigW.data(), 1, nullptr, ldv,
                          eigWork.data(), eigInfo.data(), st, false);
+        }
+        if (fp32) {
+            ProfScope ps3(ctx, "oa_refine", (double)mm, st);
+            refine_eig(mm, Ts.data(), eigA.data(), eigW.data(), 2, NS1.data(), NS2.data(), NS3.data(), st);
         }
     }
     k_ritz_resid<<<nblk(mm, 128), 128, 0, st>>>(T.data(), ldv, mm, p, eigA.data(), res.data());
@@ -1200,7 +1178,9 @@ void solve_near(mbl_sector *sec, double eps, int nev, const mbl_opts &o, double 
         while (!ks.full()) {
             ks.expand(opfn, st);
             if (op.stalled && fz->prec == MBL_PREC_FP32) {
-                // refinement stalled near the shift: fall back to FP64 fronts (same basis)
+                // refinement stalled near the shift: refactor with FP64 fronts.  The Krylov-Schur
+                // relation built so far holds only to the accuracy of the stalled solves, and thick
+                // restarts would carry that error along for good: start the iteration again.
                 auto tf1 = std::chrono::steady_clock::now();
                 op.fz = nullptr;
                 fz.reset();  // free the FP32 fronts first: the two factors never coexist in HBM
@@ -1208,10 +1188,14 @@ void solve_near(mbl_sector *sec, double eps, int nev, const mbl_opts &o, double 
                 S.ms_factor += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tf1).count();
                 op.fz = fz.get();
                 op.stalled = false;
+                op.clear_deflation();  // its vectors live in the basis that start() overwrites
                 S.fp64_fallback = 1;
+                ks.start(o.start_seed, st);
+                screen = 1e-6;
+                prev_rr = INFINITY;
             }
         }
-        ks.ritz(st, th, rn, k_keep);
+        ks.ritz(st, th, rn);
         int mm = (int)th.size();
         std::vector<int> order(mm);
         std::iota(order.begin(), order.end(), 0);

@@ -17,7 +17,7 @@ struct KrylovSchur {
     int64_t n;
     int p, ncv, ldv;
     int m = 0;  // basis columns; the first m - p have been expanded
-    DVec<double> V, V2, W, T, C1, C2, R1, R2, Rm, G, work, eigA, eigW, eigWork, res, SK, NS1, NS2, NS3, Ts, chk, Bk;
+    DVec<double> V, V2, W, T, C1, C2, R1, R2, Rm, G, work, eigA, eigW, eigWork, res, SK, NS1, NS2, NS3, Ts, Bk;
     DVec<int> flag, eigInfo, eigM, keep;
     DVec<int64_t> eigOff;
 
@@ -26,8 +26,7 @@ struct KrylovSchur {
     void start(uint64_t seed, cudaStream_t st);
     void expand(const OpFn &op, cudaStream_t st);
     // Ritz values (ascending) of the expanded part and their Krylov-Schur residual norms
-    // nkeep: how many of the largest |theta| the next restart may keep (their accuracy is checked)
-    void ritz(cudaStream_t st, std::vector<double> &theta, std::vector<double> &rnorm, int nkeep);
+    void ritz(cudaStream_t st, std::vector<double> &theta, std::vector<double> &rnorm);
     // keep the listed Ritz pairs (indices into the last ritz() result) plus the residual block
     void restart(const std::vector<int> &keep_idx, cudaStream_t st);
 
@@ -59,6 +58,7 @@ struct RefinedSolve {
     void apply(const double *X, int ldx, double *Y, int p, cudaStream_t st);
     // Use U[:, 0:k] (k <= 90; k = 0 switches deflation off); U must stay unchanged until the next call.
     void set_deflation(const double *U_, int ldu_, int k, cudaStream_t st);
+    void clear_deflation() { kd = 0; }
 
   private:
     // true residual R = B - (H - sigma) Y; returns the worst ratio ||r_q|| / (rtol (anorm ||y_q|| + ||b_q||))

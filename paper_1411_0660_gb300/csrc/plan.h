@@ -53,8 +53,17 @@ struct SolveDesc {
     int64_t offb;                    // prefix of RBB-row tiles of [k0, f) in the step (G build)
     int64_t offk;                    // prefix of backward row blocks (RBK rows of [k0, f)) in the step
     int64_t moff;                    // offset (elements) of M while it is built
+    int64_t goff;                    // offset (elements) of G in the packed solve factor
     int32_t fdesc[SUBS];             // factor descriptors of the sub-panels (-1 if absent)
 };
+
+// Leading dimension of a panel's G (rows [k0, f) of the front) in the packed solve factor: rows
+// padded to a multiple of 4 elements, so that every column starts on a 16-byte boundary; the
+// padding rows are zero.
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+inline int64_t sg_ld(int64_t rows) { return (rows + 3) & ~(int64_t)3; }
 
 struct SolveStep {
     int32_t level;
@@ -113,6 +122,7 @@ struct Plan {
     std::vector<int64_t> df_fg_off, df_poff;
     int64_t df_pslots = 0;
     int64_t m_elems = 0, max_sstep_nrbb = 0, max_sstep_nrbk = 0;
+    int64_t sg_elems = 0;                     // packed solve factor (all panels' G, padded columns)
     int64_t arena_elems = 0, zwork_elems = 0, wscratch_elems = 0, max_desc_per_step = 0;
     int64_t max_step_n2 = 0;
     int64_t nnz_l = 0;

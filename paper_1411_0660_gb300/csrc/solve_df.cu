@@ -17,6 +17,7 @@
 // counter, settles its copies in flight and stops.  Producers fence their writes before they
 // count; consumers read produced data through L2 (ld.cg).
 #include "factor.h"
+#include "solve_tile.cuh"
 
 namespace mbl {
 
@@ -74,20 +75,9 @@ __device__ __forceinline__ void df_signal(int32_t *c) {
     if (threadIdx.x == 0) atomicAdd(c, 1);
 }
 
-template <class T>
-__device__ __forceinline__ void df_cp_async(T *smem, const T *gmem) {
-    const unsigned int sa = (unsigned int)__cvta_generic_to_shared(smem);
-    if (sizeof(T) == 8) asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gmem) : "memory");
-    else asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void df_cp_wait() {
-    asm volatile("cp.async.commit_group;" ::: "memory");
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
-}
-
 // ---------------------------------------------------------------------------------------------
 template <class T, int PB>
-__global__ void __launch_bounds__(256) k_df_fwd(DfArgs A, const T *arena, const T *Dg, const T *y, T *Z, T *Zs,
+__global__ void __launch_bounds__(256) k_df_fwd(DfArgs A, const T *Gp, const T *Dg, const T *y, T *Z, T *Zs,
                                                 T *yfw, int p) {
     extern __shared__ __align__(16) unsigned char smraw[];
     T *zp = reinterpret_cast<T *>(smraw);  // SPW x PB; afterwards the 8 x PB x RBF partials
@@ -128,17 +118,17 @@ __global__ void __launch_bounds__(256) k_df_fwd(DfArgs A, const T *arena, const 
         // ---- forward panel step, rows [RBF b, RBF b + RBF) of the panel's column block
         const int qd = it.a;
         const SolveDesc d = A.sdescs[qd];
-        const int f = A.fsz[s], k0 = d.k0, w = d.w;
+        const int k0 = d.k0, w = d.w;
         const int r0 = it.b * RBF;
         const int nr = min(RBF, w + d.m2 - r0);
-        const int64_t zb = A.zo[s] + k0;
+        const int64_t zb = A.zo[s] + k0, ld = sg_ld(w + d.m2);
         const int c0 = wp * 32, c1 = min(w, c0 + 32);
         const bool active = lane < nr && c0 < c1, full = c1 - c0 == 32;
-        const T *g = arena + A.fo[s] + (int64_t)k0 * f + k0 + r0 + lane;
+        const T *g = Gp + d.goff + r0 + lane;
         T lv[32];
         if (active && full) {  // the factor is read-only: load it before waiting
 #pragma unroll
-            for (int c = 0; c < 32; ++c) lv[c] = g[(int64_t)(c0 + c) * f];
+            for (int c = 0; c < 32; ++c) lv[c] = g[(int64_t)(c0 + c) * ld];
         }
         if (tid == 0) s_ok = df_wait(A.gcnt + s, A.gchunks[s], A.err) && df_wait(A.fcnt + s, A.fprefix[qd], A.err);
         __syncthreads();
@@ -159,7 +149,7 @@ __global__ void __launch_bounds__(256) k_df_fwd(DfArgs A, const T *arena, const 
                     for (int q = 0; q < PB; ++q) acc[q] += lv[c] * zp[(c0 + c) * PB + q];
             } else {
                 for (int c = c0; c < c1; ++c) {
-                    const T l = g[(int64_t)c * f];
+                    const T l = g[(int64_t)c * ld];
 #pragma unroll
                     for (int q = 0; q < PB; ++q) acc[q] += l * zp[c * PB + q];
                 }
@@ -192,11 +182,13 @@ __global__ void __launch_bounds__(256) k_df_fwd(DfArgs A, const T *arena, const 
 
 // ---------------------------------------------------------------------------------------------
 template <class T, int PB>
-__global__ void __launch_bounds__(256) k_df_bwd(DfArgs A, const T *arena, const T *yfw, T *x, T *Z, T *Zs, T *P,
+__global__ void __launch_bounds__(256) k_df_bwd(DfArgs A, const T *Gp, const T *yfw, T *x, T *Z, T *Zs, T *P,
                                                 int p) {
+    constexpr int E = 16 / sizeof(T);
     extern __shared__ __align__(16) unsigned char smraw[];
-    T *Gs = reinterpret_cast<T *>(smraw);  // RBK x (RBB + 1), row-major
-    T *vs = Gs + RBK * (RBB + 1);          // RBK x PB
+    T *Gs = reinterpret_cast<T *>(smraw);    // RBB columns x bwd_ldg rows
+    T *vs = Gs + RBB * bwd_ldg<T>();         // RBK x PB
+    T *red = PB == 8 ? Gs : vs + RBK * PB;  // 8 warps x 8 x RBB partial sums
     __shared__ int s_t, s_ok, s_last;
     const int tid = threadIdx.x;
     for (;;) {
@@ -228,24 +220,18 @@ __global__ void __launch_bounds__(256) k_df_bwd(DfArgs A, const T *arena, const 
         // ---- backward panel step: rows [RBK b, ..) x columns [RBB cc, ..) of G
         const int qd = it.a;
         const SolveDesc d = A.sdescs[qd];
-        const int f = A.fsz[s], k0 = d.k0, w = d.w, ncs = A.nc[s];
+        const int k0 = d.k0, w = d.w, ncs = A.nc[s], R = w + d.m2;
         const int ci = it.cc, cc = ci * RBB;
-        const int nb = (w + d.m2 + RBK - 1) / RBK;
+        const int nb = (R + RBK - 1) / RBK;
         const int r0 = it.b * RBK;
-        const int nr = min(RBK, w + d.m2 - r0);
+        const int nr = min(RBK, R - r0), nrv = (nr + E - 1) / E;
         const int wc = min(RBB, w - cc);
-        const int64_t zb = A.zo[s] + k0;
-        const T *F = arena + A.fo[s] + (int64_t)(k0 + cc) * f + k0 + r0;
-        for (int idx = tid; idx < RBK * RBB; idx += blockDim.x) {  // read-only: copy before waiting
-            const int i = idx % RBK, c = idx / RBK;
-            T *dst = Gs + i * (RBB + 1) + c;
-            if (i < nr && c < wc) df_cp_async(dst, F + (int64_t)c * f + i);
-            else *dst = T(0);
-        }
+        const int64_t zb = A.zo[s] + k0, ld = sg_ld(R);
+        bwd_tile_issue(Gs, Gp + d.goff + (int64_t)cc * ld + r0, ld, wc, nrv);  // read-only: copy before waiting
         if (tid == 0) s_ok = df_wait(A.bgcnt + s, A.gchunks[s], A.err) && df_wait(A.bcnt + s, A.bprefix[qd], A.err);
         __syncthreads();
         if (!s_ok) {
-            df_cp_wait();
+            cp_async_commit_wait();
             return;
         }
         for (int idx = tid; idx < RBK * PB; idx += blockDim.x) {
@@ -259,50 +245,41 @@ __global__ void __launch_bounds__(256) k_df_bwd(DfArgs A, const T *arena, const 
             }
             vs[idx] = v;
         }
-        df_cp_wait();
+        cp_async_commit_wait();
         __syncthreads();
-        constexpr int QP = PB / 4;
-        const int c = tid % RBB, qg = tid / RBB;
-        T acc[QP];
-#pragma unroll
-        for (int k = 0; k < QP; ++k) acc[k] = T(0);
-        const int nrr = (nr + 7) & ~7;
-#pragma unroll 8
-        for (int i = 0; i < nrr; ++i) {
-            const T gv = Gs[i * (RBB + 1) + c];
-#pragma unroll
-            for (int k = 0; k < QP; ++k) acc[k] += gv * vs[i * PB + qg + 4 * k];
-        }
         const int64_t tile = (int64_t)RBB * PB;
         T *out = P + (A.poff[qd] + (int64_t)it.b * SUBS + ci) * tile;
+        T *zsp = Zs + (zb + cc) * p, *xp = x + ((int64_t)A.sn_start[s] + k0 + cc) * p;
 #pragma unroll
-        for (int k = 0; k < QP; ++k) out[(qg + 4 * k) * RBB + c] = acc[k];
-        __threadfence();
-        __syncthreads();
-        if (tid == 0) {
-            const unsigned int prev = atomicAdd(&A.arrive[(size_t)qd * SUBS + ci], 1u);
-            s_last = prev == (unsigned int)(nb - 1);
-        }
-        __syncthreads();
-        if (!s_last) continue;
-        __threadfence();
-        const T *src0 = P + (A.poff[qd] + ci) * tile;
-        for (int o = tid; o < wc * p; o += blockDim.x) {
-            const int cq = o % wc, q = o / wc;
-            const T *src = src0 + q * RBB + cq;
-            const int64_t stride = (int64_t)SUBS * tile;
-            T v4[4] = {T(0), T(0), T(0), T(0)};
-            int bb = 0;
-            for (; bb + 4 <= nb; bb += 4) {
+        for (int q0 = 0; q0 < PB; q0 += 8) {
+            T o2[2];
+            bwd_tile_product<T, PB>(Gs, vs, red, nrv * E, q0, o2);
 #pragma unroll
-                for (int u = 0; u < 4; ++u) v4[u] += __ldcg(src + (int64_t)(bb + u) * stride);
+            for (int h = 0; h < 2; ++h) {
+                const int o = tid + 256 * h, q = q0 + o / RBB, c = o % RBB;
+                if (nb == 1) {
+                    if (c < wc && q < p) {
+                        zsp[c * p + q] = o2[h];
+                        xp[c * p + q] = o2[h];
+                    }
+                } else {
+                    out[q * RBB + c] = o2[h];
+                }
             }
-            for (; bb < nb; ++bb) v4[0] += __ldcg(src + (int64_t)bb * stride);
-            const T xv = (v4[0] + v4[1]) + (v4[2] + v4[3]);
-            Zs[(zb + cc + cq) * p + q] = xv;
-            x[((int64_t)A.sn_start[s] + k0 + cc + cq) * p + q] = xv;
         }
-        if (tid == 0) A.arrive[(size_t)qd * SUBS + ci] = 0u;
+        if (nb > 1) {
+            __threadfence();
+            __syncthreads();
+            if (tid == 0) {
+                const unsigned int prev = atomicAdd(&A.arrive[(size_t)qd * SUBS + ci], 1u);
+                s_last = prev == (unsigned int)(nb - 1);
+            }
+            __syncthreads();
+            if (!s_last) continue;
+            __threadfence();
+            bwd_finish<T, PB>(P + (A.poff[qd] + ci) * tile, (int64_t)SUBS * tile, nb, wc, p, zsp, xp, Gs);
+            if (tid == 0) A.arrive[(size_t)qd * SUBS + ci] = 0u;
+        }
         df_signal(A.bcnt + s);
     }
 }
@@ -310,7 +287,7 @@ __global__ void __launch_bounds__(256) k_df_bwd(DfArgs A, const T *arena, const 
 template <class T, int PB>
 size_t df_fwd_smem() { return sizeof(T) * (size_t)SPW * PB; }
 template <class T, int PB>
-size_t df_bwd_smem() { return sizeof(T) * ((size_t)RBK * (RBB + 1) + (size_t)RBK * PB); }
+size_t df_bwd_smem() { return bwd_tile_smem<T, PB>(); }
 
 template <class T, int PB>
 void df_sweeps(Factorization &fz, int p, cudaStream_t st) {
@@ -361,7 +338,7 @@ void df_sweeps(Factorization &fz, int p, cudaStream_t st) {
     A.bcnt = cnt + 3 * ns;
     A.arrive = fz.scnt.data();
     A.err = fz.counters.data() + 2;
-    T *arena = static_cast<T *>(fz.arena.m.p);
+    const T *Gp = static_cast<const T *>(fz.gpk.m.p);
     const T *Dg = static_cast<const T *>(fz.D.m.p);
     T *Z = static_cast<T *>(fz.zwork.m.p);
     T *Zs = static_cast<T *>(fz.zsolved.m.p);
@@ -372,13 +349,13 @@ void df_sweeps(Factorization &fz, int p, cudaStream_t st) {
     A.nitems = (int)pl.df_fwd.size();
     A.ticket = reinterpret_cast<unsigned int *>(cnt + 4 * ns);
     k_df_fwd<T, PB><<<std::min(grid_f, std::max(1, A.nitems)), 256, df_fwd_smem<T, PB>(), st>>>(
-        A, arena, Dg, y, Z, Zs, yfw, p);
+        A, Gp, Dg, y, Z, Zs, yfw, p);
     MBL_LAUNCH_CHECK();
     A.items = pl.d_df_bwd.data();
     A.nitems = (int)pl.df_bwd.size();
     A.ticket = reinterpret_cast<unsigned int *>(cnt + 4 * ns + 1);
-    k_df_bwd<T, PB><<<std::min(grid_b, std::max(1, A.nitems)), 256, df_bwd_smem<T, PB>(), st>>>(A, arena, yfw, y, Z,
-                                                                                                 Zs, P, p);
+    k_df_bwd<T, PB><<<std::min(grid_b, std::max(1, A.nitems)), 256, df_bwd_smem<T, PB>(), st>>>(A, Gp, yfw, y, Z, Zs,
+                                                                                                 P, p);
     MBL_LAUNCH_CHECK();
 }
 

@@ -548,6 +548,7 @@ std::shared_ptr<Plan> build_plan(int L, const std::vector<uint32_t> &states, con
                 sd.offb = ss.nrbb;
                 sd.offk = ss.nrbk;
                 sd.moff = p.m_elems;
+                sd.goff = p.sg_elems;
                 for (int u = 0; u < SUBS; ++u) {
                     int32_t kk = (k0 + u * NB) / NB;
                     sd.fdesc[u] = (u * NB < w) ? fd_of[fd_off[s] + kk] : -1;
@@ -556,6 +557,7 @@ std::shared_ptr<Plan> build_plan(int L, const std::vector<uint32_t> &states, con
                 ss.nrbb += (w + sd.m2 + RBB - 1) / RBB;
                 ss.nrbk += (w + sd.m2 + RBK - 1) / RBK;
                 p.m_elems += (int64_t)w * w;
+                p.sg_elems += sg_ld(w + sd.m2) * w;
                 p.sdescs.push_back(sd);
             }
             ss.nd = (int32_t)p.sdescs.size() - ss.d0;
