@@ -16,6 +16,11 @@ What each function computes and the passage it follows:
 * ``gap_ratio``         r^(n), "level statistics" paragraph
 * ``s1p``               S_1^P, "Hilbert space localization" paragraph
 * ``entanglement``      S^E = -Tr rho_A ln rho_A, "entanglement entropy" paragraph
+* ``kl``                KL divergence of nearby eigenstates, "level statistics and eigenvectors
+                        similarity" paragraph
+* ``sqp``               S_q^P, q != 1, "Hilbert space localization" paragraph
+* ``fluct``             bipartite fluctuation F of S^z_A, "entanglement entropy" paragraph
+* ``dynf``              dynamic spin fraction f, supplementary section on the dynamical spin fraction
 """
 from __future__ import annotations
 
@@ -89,6 +94,14 @@ def lib():
             getattr(L, nm).argtypes = [ctypes.c_void_p]
             getattr(L, nm).restype = ctypes.c_int64
         L.orc_ldlt_free.argtypes = [ctypes.c_void_p]
+        L.orc_kl.argtypes = [ctypes.c_int64, _f64p, _f64p]
+        L.orc_kl.restype = ctypes.c_double
+        L.orc_sqp.argtypes = [ctypes.c_int64, _f64p, ctypes.c_double]
+        L.orc_sqp.restype = ctypes.c_double
+        L.orc_fluct.argtypes = [ctypes.c_int, _u32p, ctypes.c_int64, _f64p]
+        L.orc_fluct.restype = ctypes.c_double
+        L.orc_dynf.argtypes = [ctypes.c_int, _u32p, ctypes.c_int64, _f64p]
+        L.orc_dynf.restype = ctypes.c_double
         L.orc_nearest_shift_invert.argtypes = [ctypes.c_int64, _i64p, _i32p, _f64p, ctypes.c_double, ctypes.c_int,
                                                ctypes.c_double, _f64p, _f64p, _f64p]
         L.orc_gap_ratio.argtypes = [ctypes.c_int, _f64p, _f64p, ctypes.POINTER(ctypes.c_double)]
@@ -271,6 +284,29 @@ def entanglement(L: int, y: np.ndarray, states: np.ndarray | None = None) -> flo
     st = basis(L) if states is None else states
     y = np.ascontiguousarray(y, dtype=np.float64)
     return float(lib().orc_entanglement(L, st, len(st), y))
+
+
+def kl(y: np.ndarray, z: np.ndarray) -> float:
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    z = np.ascontiguousarray(z, dtype=np.float64)
+    return float(lib().orc_kl(len(y), y, z))
+
+
+def sqp(y: np.ndarray, q: float) -> float:
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    return float(lib().orc_sqp(len(y), y, float(q)))
+
+
+def fluct(L: int, y: np.ndarray, states: np.ndarray | None = None) -> float:
+    st = basis(L) if states is None else states
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    return float(lib().orc_fluct(L, st, len(st), y))
+
+
+def dynf(L: int, y: np.ndarray, states: np.ndarray | None = None) -> float:
+    st = basis(L) if states is None else states
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    return float(lib().orc_dynf(L, st, len(st), y))
 
 
 # ---------------------------------------------------------------------------------------------

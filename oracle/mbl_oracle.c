@@ -807,3 +807,58 @@ double orc_entanglement(int L, const uint32_t *states, int64_t n, const double *
     free(as); free(bs);
     return S;
 }
+
+double orc_kl(int64_t n, const double *y, const double *z) {
+    double ny = dot(n, y, y), nz = dot(n, z, z), s = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        double p = y[i] * y[i] / ny, q = z[i] * z[i] / nz;
+        if (p == 0.0) continue;
+        if (q == 0.0) return INFINITY;
+        s += p * log(p / q);
+    }
+    return s;
+}
+
+double orc_sqp(int64_t n, const double *y, double q) {
+    double ny = dot(n, y, y), s = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        double p = y[i] * y[i] / ny;
+        if (p > 0.0) s += pow(p, q);
+    }
+    return log(s) / (1.0 - q);
+}
+
+/* S^z of the sites 0 .. L/2-1 of a basis state: (#up - #down) / 2 */
+static double sz_half(int L, uint32_t s) {
+    int up = 0;
+    for (int i = 0; i < L / 2; ++i) up += (s >> i) & 1u;
+    return 0.5 * (double)(2 * up - L / 2);
+}
+
+double orc_fluct(int L, const uint32_t *states, int64_t n, const double *y) {
+    double ny = dot(n, y, y), m1 = 0.0, m2 = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        double p = y[i] * y[i] / ny, m = sz_half(L, states[i]);
+        m1 += p * m;
+        m2 += p * m * m;
+    }
+    return m2 - m1 * m1;
+}
+
+double orc_dynf(int L, const uint32_t *states, int64_t n, const double *y) {
+    const double pi = 3.14159265358979323846;
+    double ny = dot(n, y, y), re = 0.0, im = 0.0, mm = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        double p = y[i] * y[i] / ny, mr = 0.0, mi = 0.0;
+        for (int j = 0; j < L; ++j) {
+            double sz = ((states[i] >> j) & 1u) ? 0.5 : -0.5;
+            mr += sz * cos(2.0 * pi * j / L);
+            mi += sz * sin(2.0 * pi * j / L);
+        }
+        re += p * mr;
+        im += p * mi;
+        mm += p * (mr * mr + mi * mi);
+    }
+    if (mm == 0.0) return NAN;
+    return 1.0 - (re * re + im * im) / mm;
+}

@@ -101,6 +101,20 @@ void orc_gap_ratio(int nev, const double *evals, double *r, double *r_mean);
 double orc_s1p(int64_t n, const double *y);
 /* Half-chain entanglement entropy (A = sites 0 .. L/2-1) of the sector vector y. */
 double orc_entanglement(int L, const uint32_t *states, int64_t n, const double *y);
+/* Kullback-Leibler divergence KL = sum_i p_i ln(p_i / q_i) of the weights p of y and q of z
+ * ("level statistics and eigenvectors similarity" paragraph); terms with p_i = 0 are 0, a term with
+ * p_i > 0 = q_i makes it +infinity. */
+double orc_kl(int64_t n, const double *y, const double *z);
+/* Participation entropy of order q != 1: S_q^P = ln(sum_i p_i^q) / (1 - q) ("Hilbert space
+ * localization" paragraph). */
+double orc_sqp(int64_t n, const double *y, double q);
+/* Bipartite fluctuation F = <(S^z_A)^2> - <S^z_A>^2 of the half chain A = sites 0 .. L/2-1
+ * ("entanglement entropy" paragraph); S^z_A is diagonal in the basis. */
+double orc_fluct(int L, const uint32_t *states, int64_t n, const double *y);
+/* Dynamic spin fraction f = 1 - |<M>|^2 / <M^dagger M>, M = sum_j S^z_j exp(2 pi i j / L)
+ * (supplementary section on the dynamical spin fraction); M is diagonal in the basis.  NaN if
+ * <M^dagger M> = 0. */
+double orc_dynf(int L, const uint32_t *states, int64_t n, const double *y);
 
 #ifdef __cplusplus
 }

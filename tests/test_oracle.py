@@ -335,3 +335,95 @@ def test_entanglement_product_state_zero(orc):
     y = np.zeros(len(st))
     y[5] = 1.0
     assert orc.entanglement(L, y, st) == 0.0
+
+
+# ------------------------------- further eigenvector observables (characterization section) ----
+def _popcount(x):
+    return bin(int(x)).count("1")
+
+
+def test_kl_limits_and_goe_value(orc):
+    """KL = sum p ln(p/q), "level statistics and eigenvectors similarity" paragraph: zero for
+    equal weights, ln n from a basis state to the uniform vector, non-negative (Gibbs), infinite
+    where q vanishes under p, and 2 for two independent real Gaussian vectors (the paper's KL_GOE)."""
+    n = 924
+    rng = np.random.default_rng(3)
+    y = rng.standard_normal(n)
+    assert abs(orc.kl(y, -2.5 * y)) < 1e-14
+    e = np.zeros(n)
+    e[100] = 1.0
+    assert abs(orc.kl(e, np.ones(n)) - math.log(n)) < 1e-12
+    for _ in range(5):
+        a, b = rng.standard_normal(n), rng.standard_normal(n)
+        assert orc.kl(a, b) > 0.0
+    z = y.copy()
+    z[7] = 0.0
+    assert orc.kl(y, z) == math.inf and math.isfinite(orc.kl(z, y))
+    goe = _gold("paper_values.json")["kl_goe"]["value"]
+    a, b = rng.standard_normal(200000), rng.standard_normal(200000)
+    assert abs(orc.kl(a, b) - goe) < 0.05
+
+
+def test_sqp_limits(orc):
+    """S_q^P = ln(sum p^q)/(1 - q), "Hilbert space localization" paragraph: 0 for a basis state,
+    ln n for the uniform vector at every q, S_2 = ln n - ln 3 for a large Gaussian vector
+    (E[x^4] = 3), S_q -> S_1 as q -> 1, and S_q non-increasing in q."""
+    n = 3432
+    e = np.zeros(n)
+    e[5] = 3.0
+    for q in (0.5, 2.0, 3.0):
+        assert abs(orc.sqp(e, q)) < 1e-15
+        assert abs(orc.sqp(np.ones(n), q) - math.log(n)) < 1e-12
+    g = np.random.default_rng(5).standard_normal(200000)
+    assert abs(orc.sqp(g, 2.0) - (math.log(200000) - math.log(3.0))) < 0.03
+    y = np.random.default_rng(6).standard_normal(n)
+    assert abs(orc.sqp(y, 1.0 + 1e-7) - orc.s1p(y)) < 1e-5
+    assert abs(orc.sqp(y, 1.0 - 1e-7) - orc.s1p(y)) < 1e-5
+    assert orc.sqp(y, 3.0) <= orc.sqp(y, 2.0) <= orc.s1p(y) <= orc.sqp(y, 0.5)
+
+
+@pytest.mark.parametrize("L", [4, 6, 8, 10, 12])
+def test_fluct_closed_forms(orc, L):
+    """F = <(S^z_A)^2> - <S^z_A>^2 on A = sites 0..L/2-1: zero on a basis state; on the uniform
+    vector of the S^z = 0 sector the number of up spins in A is hypergeometric, so
+    F = (L/2)(1/2)(1/2)(L/2)/(L-1) = L^2 / (16 (L - 1)); on (e_s + e_t)/sqrt2 it is (m_s - m_t)^2/4."""
+    st = orc.basis(L)
+    n = len(st)
+    e = np.zeros(n)
+    e[n // 3] = 1.0
+    assert abs(orc.fluct(L, e, st)) < 1e-15
+    assert abs(orc.fluct(L, np.ones(n), st) - L * L / (16.0 * (L - 1))) < 1e-12
+    mask = (1 << (L // 2)) - 1
+    mA = np.array([_popcount(s & mask) - L / 4 for s in st])
+    s, t = int(np.argmax(mA)), int(np.argmin(mA))
+    y = np.zeros(n)
+    y[s] = y[t] = 1.0
+    assert abs(orc.fluct(L, y, st) - (mA[s] - mA[t]) ** 2 / 4) < 1e-12
+
+
+@pytest.mark.parametrize("L", [2, 4, 6, 8, 10])
+def test_dynf_limits(orc, L):
+    """f = 1 - |<M>|^2 / <M^+ M>, M = sum_j S^z_j e^{2 pi i j/L} (supplementary section): 0 on a
+    basis state with M != 0 (the domain wall of L/2 up spins has |M| = 1/sin(pi/L)), 1 on the
+    uniform vector (every S^z_j averages to zero over the sector) and on the domain wall plus its
+    spin flip, in [0, 1] always, and unchanged by a translation of the chain."""
+    st = orc.basis(L)
+    n = len(st)
+    wall = (1 << (L // 2)) - 1
+    iw = int(np.searchsorted(st, wall))
+    iflip = int(np.searchsorted(st, ((1 << L) - 1) ^ wall))
+    e = np.zeros(n)
+    e[iw] = 1.0
+    assert abs(orc.dynf(L, e, st)) < 1e-13
+    assert abs(orc.dynf(L, np.ones(n), st) - 1.0) < 1e-13
+    e[iflip] = 1.0
+    assert abs(orc.dynf(L, e, st) - 1.0) < 1e-13
+    rng = np.random.default_rng(L)
+    rot = np.array([int(np.searchsorted(st, ((s << 1) | (s >> (L - 1))) & ((1 << L) - 1))) for s in st])
+    for _ in range(4):
+        y = rng.standard_normal(n) * np.exp(-rng.uniform(0, 4, n))
+        f = orc.dynf(L, y, st)
+        assert -1e-14 <= f <= 1 + 1e-14
+        yt = np.zeros(n)
+        yt[rot] = y  # the translated state: site j -> j + 1
+        assert abs(orc.dynf(L, yt, st) - f) < 1e-12
