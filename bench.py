@@ -13,6 +13,7 @@ symbolic analysis of the L = 18 pattern is setup (built once in warm-up, exclude
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--batch B] [--slots S] [--impl reference]
     python bench.py --case {factor,solve} [--L L] [--reps R] [--precision fp32|fp64]   (profiler cases)
+    python bench.py --case observables [--L L] [--reps R]   (the eigenvector observables on nev = 50 vectors)
 """
 from __future__ import annotations
 
@@ -191,10 +192,75 @@ def run_case(args):
     if nvtx is not None:
         nvtx.range_pop()
     dt = time.perf_counter() - t0
-    print(json.dumps({"case": args.case, "L": args.L, "precision": args.precision, "reps": args.reps,
-                      "solve_s_per_rep": dt / max(1, args.reps), "factor": f.stats()}))
+    line = {"case": args.case, "L": args.L, "precision": args.precision, "reps": args.reps,
+            "solve_s_per_rep": dt / max(1, args.reps), "factor": f.stats()}
+    if args.case == "solve" and args.trace:
+        # per-launch device clocks of one more solve: where the sequence spends its time
+        f.set_trace(True)
+        for _ in range(2):
+            f.solve(B, refine=False)
+        t0s, t1s, kind = f.trace()
+        base = int(t0s.min())
+        rec = [[int(k), (int(a) - base) / 1e3, (int(b) - base) / 1e3] for k, a, b in zip(kind, t0s, t1s)]
+        prev = 0.0
+        crit = {0: 0.0, 1: 0.0, 2: 0.0}
+        for k, a, b in rec:  # time each launch adds after its predecessor finished
+            crit[k] += b - max(prev, a)
+            prev = b
+        line["trace"] = {"launches": len(rec), "span_us": rec[-1][2] - rec[0][1] if rec else 0.0,
+                         "critical_us": {"gather": crit[0], "forward": crit[1], "backward": crit[2]}}
+        with open(args.trace, "w") as fo:
+            json.dump({"records_us": rec, "kinds": "0 gather, 1 forward step, 2 backward step"}, fo)
+    print(json.dumps(line))
     f.close()
     sec.close()
+    ctx.close()
+    return 0
+
+
+def run_observables_case(args):
+    """Device time of the eigenvector observables on nev = 50 seeded random unit vectors of the
+    L-site sector (their cost does not depend on the vectors): mbl_observables_dev (r, S_1^P, S_E)
+    and mbl_observables_extra_dev (KL, S_2^P, F, f).  The roofline is the extra observables'
+    algorithmic traffic, one read of the n x nev vectors, over their CUDA-event time."""
+    import numpy as np
+    import torch
+
+    import paper_1411_0660_gb300 as g
+
+    ctx = g.Context(0)
+    n, nev = math.comb(args.L, args.L // 2), NEV
+    dev = torch.device("cuda:0")
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(1234)
+    Y = torch.randn(nev, n, dtype=torch.float64, device=dev, generator=gen)
+    Y /= Y.norm(dim=1, keepdim=True)
+    Y = Y.reshape(-1).contiguous()  # column-major n x nev
+    ev = torch.linspace(-1.0, 1.0, nev, dtype=torch.float64, device=dev)
+    outs = [torch.zeros(m, dtype=torch.float64, device=dev) for m in (nev - 2, 1, nev, nev)]
+    outx = [torch.zeros(m, dtype=torch.float64, device=dev) for m in (nev - 1, nev, nev, nev)]
+    st = torch.cuda.current_stream()
+    for _ in range(3):
+        g.observables_dev(ctx, args.L, nev, ev, Y, *outs, stream=st)
+        g.observables_extra_dev(ctx, args.L, nev, Y, 2.0, *outx, stream=st)
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    torch.cuda.synchronize()
+    e[0].record(st)
+    for _ in range(args.reps):
+        g.observables_dev(ctx, args.L, nev, ev, Y, *outs, stream=st)
+    e[1].record(st)
+    e[2].record(st)
+    for _ in range(args.reps):
+        g.observables_extra_dev(ctx, args.L, nev, Y, 2.0, *outx, stream=st)
+    e[3].record(st)
+    torch.cuda.synchronize()
+    ms_base = e[0].elapsed_time(e[1]) / args.reps
+    ms_extra = e[2].elapsed_time(e[3]) / args.reps
+    peak = (measured_peaks() or {}).get("hbm_gbs")
+    gbs = 8.0 * n * nev / (ms_extra * 1e-3) / 1e9
+    print(json.dumps({"case": "observables", "L": args.L, "n": n, "nev": nev, "ms_r_s1p_se": ms_base,
+                      "ms_kl_sqp_fluct_dynf": ms_extra, "extra_gbs": gbs, "hbm_peak_gbs": peak,
+                      "extra_frac": gbs / peak if peak else None}))
     ctx.close()
     return 0
 
@@ -266,7 +332,7 @@ def run_workload(args):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--case", choices=["factor", "solve"], default=None,
+    ap.add_argument("--case", choices=["factor", "solve", "observables"], default=None,
                     help="run one factorization (and --reps solves) instead of the benchmark")
     ap.add_argument("--L", type=int, default=18)
     ap.add_argument("--workload", choices=["l18", "l16batch", "serve"], default="l18",
@@ -278,6 +344,7 @@ def main():
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--tensor-cores", type=int, default=1)
     ap.add_argument("--dataflow", type=int, default=0, help="solve sweeps as persistent dataflow kernels")
+    ap.add_argument("--trace", default=None, help="--case solve: write per-launch device clocks of one solve here")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
@@ -287,6 +354,8 @@ def main():
     ap.add_argument("--fp64-stride", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
+    if args.case == "observables":
+        return run_observables_case(args)
     if args.case:
         return run_case(args)
     if args.workload != "l18":

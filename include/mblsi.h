@@ -158,6 +158,17 @@ int mbl_factor_stats_get(const mbl_factorization *f, mbl_factor_stats *stats);
 /* x = (H - sigma)^-1 b for nrhs right-hand sides (host, n x nrhs column-major), with FP64
  * iterative refinement when `refine` is nonzero. */
 int mbl_factor_solve(mbl_factorization *f, const double *b, double *x, int nrhs, int refine);
+/* Launch trace of the level-by-level triangular solve, a diagnostic with no counterpart in the
+ * paper.  With on != 0 every later solve of f records, for each kernel launch of its sequence, the
+ * device clock (%globaltimer, ns) when the launch's first CTA started and when its last CTA
+ * finished; on = 0 stops recording.  Switching recaptures the solve graph.  MBL_ERR_INVALID for a
+ * factorization made with solve_dataflow. */
+int mbl_factor_trace(mbl_factorization *f, int on);
+/* Copies the records of the latest solve: up to cap launches in sequence order into t0[], t1[] and
+ * kind[] (0 forward gather, 1 forward panel step, 2 backward panel step); *count = number recorded
+ * (0 when tracing is off). */
+int mbl_factor_trace_get(mbl_factorization *f, unsigned long long *t0, unsigned long long *t1, int *kind,
+                         int cap, int *count);
 void mbl_factor_destroy(mbl_factorization *f);
 
 /* The nev eigenpairs of the sector nearest sigma = E_min + eps (E_max - E_min): block
@@ -189,6 +200,26 @@ int mbl_observables(mbl_ctx *ctx, int L, int nev, const double *evals, const dou
 int mbl_observables_dev(mbl_ctx *ctx, int L, int nev, const double *d_evals,
                         const double *d_evecs, double *d_r, double *d_r_mean, double *d_s1p,
                         double *d_se, void *stream);
+
+/* Further eigenvector observables of the characterization section and its supplement, on the
+ * columns of evecs (n x nev column-major, host; ascending eigenvalues, so adjacent columns are
+ * adjacent eigenstates).  With p_i = y_i^2 / |y|^2 of a column y:
+ *   kl[k]    (nev-1) Kullback-Leibler divergence sum_i p_i ln(p_i / q_i) of column k (p) and column
+ *            k+1 (q), "level statistics and eigenvectors similarity" paragraph; +infinity if some
+ *            q_i = 0 < p_i;
+ *   sqp[j]   participation entropy S_q^P = ln(sum_i p_i^q) / (1 - q), q > 0 and q != 1, "Hilbert
+ *            space localization" paragraph (q = 1 is the s1p output of mbl_observables);
+ *   fluct[j] bipartite fluctuation <(S^z_A)^2> - <S^z_A>^2 of A = sites 0 .. L/2-1, "entanglement
+ *            entropy" paragraph;
+ *   dynf[j]  dynamic spin fraction 1 - |<M>|^2 / <M^+ M>, M = sum_j S^z_j exp(2 pi i j / L), of the
+ *            supplementary section (NaN if <M^+ M> = 0).
+ * Errors: MBL_ERR_INVALID for odd L, L outside 2..22, nev outside [1, dim], q <= 0 or q = 1. */
+int mbl_observables_extra(mbl_ctx *ctx, int L, int nev, const double *evecs, double q, double *kl,
+                          double *sqp, double *fluct, double *dynf);
+/* Same on device arrays, enqueued on `stream` (NULL = context stream); returns when complete. */
+int mbl_observables_extra_dev(mbl_ctx *ctx, int L, int nev, const double *d_evecs, double q,
+                              double *d_kl, double *d_sqp, double *d_fluct, double *d_dynf,
+                              void *stream);
 
 /* Half-chain entanglement entropy (the se output of mbl_observables_dev) computed without any
  * device allocation.  The paper has no counterpart: it exists for callers that cannot allocate

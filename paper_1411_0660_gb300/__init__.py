@@ -176,6 +176,22 @@ class Factorization:
         _check(_lib().mbl_factor_stats_get(self.handle, ctypes.byref(s)), self.sec.ctx.handle)
         return {f: getattr(s, f) for f, _ in FactorStats._fields_}
 
+    def set_trace(self, on: bool = True):
+        """Record per-launch start/end device clocks of later solves (diagnostic)."""
+        _check(_lib().mbl_factor_trace(self.handle, 1 if on else 0), self.sec.ctx.handle)
+
+    def trace(self):
+        """(t0_ns, t1_ns, kind) arrays of the latest traced solve; kind 0 gather, 1 forward, 2 backward."""
+        cnt = ctypes.c_int()
+        _check(_lib().mbl_factor_trace_get(self.handle, None, None, None, 0, ctypes.byref(cnt)), self.sec.ctx.handle)
+        n = cnt.value
+        t0 = np.zeros(max(n, 1), dtype=np.uint64)
+        t1 = np.zeros(max(n, 1), dtype=np.uint64)
+        kind = np.zeros(max(n, 1), dtype=np.int32)
+        _check(_lib().mbl_factor_trace_get(self.handle, t0.ctypes.data, t1.ctypes.data, kind.ctypes.data, n,
+                                           ctypes.byref(cnt)), self.sec.ctx.handle)
+        return t0[:n], t1[:n], kind[:n]
+
     def solve(self, b: np.ndarray, refine: bool = True) -> np.ndarray:
         B = np.asfortranarray(b, dtype=np.float64)
         if B.ndim == 1:
@@ -263,6 +279,26 @@ def observables_dev(ctx: Context, L: int, nev: int, d_evals, d_evecs, d_r, d_rme
                                       ctypes.c_void_p(d_evecs.data_ptr()), ctypes.c_void_p(d_r.data_ptr()),
                                       ctypes.c_void_p(d_rmean.data_ptr()), ctypes.c_void_p(d_s1p.data_ptr()),
                                       ctypes.c_void_p(d_se.data_ptr()), s), ctx.handle)
+
+
+def observables_extra(ctx: Context, L: int, evecs: np.ndarray, q: float = 2.0):
+    """KL of adjacent columns (nev - 1), S_q^P, bipartite fluctuation F and dynamic fraction f of
+    the columns of evecs (dim x nev, ascending eigenvalues)."""
+    V = np.asfortranarray(evecs, dtype=np.float64)
+    nev = V.shape[1]
+    kl = np.zeros(max(nev - 1, 1))
+    sqp, fl, dyn = np.zeros(nev), np.zeros(nev), np.zeros(nev)
+    _check(_lib().mbl_observables_extra(ctx.handle, L, nev, _ptr(V), float(q), _ptr(kl), _ptr(sqp), _ptr(fl),
+                                        _ptr(dyn)), ctx.handle)
+    return kl[: max(nev - 1, 0)], sqp, fl, dyn
+
+
+def observables_extra_dev(ctx: Context, L: int, nev: int, d_evecs, q, d_kl, d_sqp, d_fluct, d_dynf, stream=None):
+    s = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
+    _check(_lib().mbl_observables_extra_dev(ctx.handle, L, nev, ctypes.c_void_p(d_evecs.data_ptr()), float(q),
+                                            ctypes.c_void_p(d_kl.data_ptr()), ctypes.c_void_p(d_sqp.data_ptr()),
+                                            ctypes.c_void_p(d_fluct.data_ptr()), ctypes.c_void_p(d_dynf.data_ptr()),
+                                            s), ctx.handle)
 
 
 def entanglement_noalloc_dev(ctx: Context, L: int, nev: int, d_evecs, d_se, stream=None):

@@ -90,10 +90,16 @@ SIGNATURES = [
                                P(c_double), P(SolveStats)]),
     ("mbl_solve_near_dev", c_int, [c_void_p, c_double, c_int, P(Opts), c_void_p, c_void_p, c_void_p, P(c_int),
                                    P(c_double), P(SolveStats), c_void_p]),
+    ("mbl_factor_trace", c_int, [c_void_p, c_int]),
+    ("mbl_factor_trace_get", c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int, P(c_int)]),
     ("mbl_observables", c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                 c_void_p]),
     ("mbl_observables_dev", c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                     c_void_p, c_void_p]),
+    ("mbl_observables_extra", c_int, [c_void_p, c_int, c_int, c_void_p, c_double, c_void_p, c_void_p, c_void_p,
+                                      c_void_p]),
+    ("mbl_observables_extra_dev", c_int, [c_void_p, c_int, c_int, c_void_p, c_double, c_void_p, c_void_p,
+                                          c_void_p, c_void_p, c_void_p]),
     ("mbl_entanglement_noalloc_dev", c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p]),
     ("mbl_server_start", c_int, [c_void_p, c_int, c_size_t]),
     ("mbl_submit", c_int, [c_void_p, P(Request), P(c_uint64)]),

@@ -501,6 +501,37 @@ int mbl_factor_stats_get(const mbl_factorization *fh, mbl_factor_stats *s) {
     return MBL_OK;
 }
 
+int mbl_factor_trace(mbl_factorization *fh, int on) {
+    if (!fh) return report(nullptr, MBL_ERR_INVALID, "NULL argument");
+    Factorization &f = *fh->f;
+    if (f.dataflow && on) return report(f.ctx, MBL_ERR_INVALID, "the launch trace covers the level-by-level solve");
+    f.trace_on = on != 0;
+    f.graph_p = 0;  // recapture the solve sequence with or without the trace records
+    return MBL_OK;
+}
+
+int mbl_factor_trace_get(mbl_factorization *fh, unsigned long long *t0, unsigned long long *t1, int *kind, int cap,
+                         int *count) {
+    if (!fh || !count || (cap > 0 && (!t0 || !t1 || !kind))) return report(nullptr, MBL_ERR_INVALID, "NULL argument");
+    Factorization &f = *fh->f;
+    Ctx *ctx = f.ctx;
+    API_TRY
+    const int nrec = f.trace_on ? (int)f.trace_kind.size() : 0;
+    *count = nrec;
+    const int m = std::min(cap, nrec);
+    if (m > 0) {
+        std::vector<LaunchTrace> h(m);
+        MBL_CUDA(cudaStreamSynchronize(ctx->stream));
+        MBL_CUDA(cudaMemcpy(h.data(), f.trace.data(), m * sizeof(LaunchTrace), cudaMemcpyDeviceToHost));
+        for (int i = 0; i < m; ++i) {
+            t0[i] = h[i].t0;
+            t1[i] = h[i].t1;
+            kind[i] = f.trace_kind[i];
+        }
+    }
+    API_CATCH(ctx)
+}
+
 int mbl_factor_solve(mbl_factorization *fh, const double *b, double *x, int nrhs, int refine) {
     if (!fh || !b || !x || nrhs < 1) return report(nullptr, MBL_ERR_INVALID, "bad argument");
     Factorization &f = *fh->f;
@@ -621,6 +652,42 @@ int mbl_observables(mbl_ctx *ctx, int L, int nev, const double *evals, const dou
     if (r_mean) MBL_CUDA(cudaMemcpy(r_mean, drm.data(), sizeof(double), cudaMemcpyDeviceToHost));
     MBL_CUDA(cudaMemcpy(s1p, ds.data(), nev * sizeof(double), cudaMemcpyDeviceToHost));
     MBL_CUDA(cudaMemcpy(se, dse.data(), nev * sizeof(double), cudaMemcpyDeviceToHost));
+    API_CATCH(ctx)
+}
+
+int mbl_observables_extra_dev(mbl_ctx *ctx, int L, int nev, const double *d_evecs, double q, double *d_kl,
+                              double *d_sqp, double *d_fluct, double *d_dynf, void *stream) {
+    if (!ctx || !d_evecs || !d_sqp || !d_fluct || !d_dynf || (nev > 1 && !d_kl))
+        return report(ctx, MBL_ERR_INVALID, "NULL argument");
+    if (L < 2 || L > 22 || (L & 1)) return report(ctx, MBL_ERR_INVALID, "L must be even with 2 <= L <= 22");
+    API_TRY
+    MBL_CUDA(cudaSetDevice(ctx->device));
+    cudaStream_t st = stream ? (cudaStream_t)stream : ctx->stream;
+    observables_extra_dev(ctx, L, nev, d_evecs, q, d_kl, d_sqp, d_fluct, d_dynf, st);
+    API_CATCH(ctx)
+}
+
+int mbl_observables_extra(mbl_ctx *ctx, int L, int nev, const double *evecs, double q, double *kl, double *sqp,
+                          double *fluct, double *dynf) {
+    if (!ctx || !evecs || !sqp || !fluct || !dynf || (nev > 1 && !kl))
+        return report(ctx, MBL_ERR_INVALID, "NULL argument");
+    if (L < 2 || L > 22 || (L & 1)) return report(ctx, MBL_ERR_INVALID, "L must be even with 2 <= L <= 22");
+    API_TRY
+    int64_t n = 1;
+    for (int i = 1; i <= L / 2; ++i) n = n * (L / 2 + i) / i;
+    if (nev < 1 || nev > n) fail(MBL_ERR_INVALID, "nev must be in [1, dim]");
+    DVec<double> dv, dk, dq, df, dd;
+    dv.alloc(ctx, (size_t)n * nev);
+    dk.alloc(ctx, std::max(nev - 1, 1));
+    dq.alloc(ctx, nev);
+    df.alloc(ctx, nev);
+    dd.alloc(ctx, nev);
+    MBL_CUDA(cudaMemcpy(dv.data(), evecs, (size_t)n * nev * sizeof(double), cudaMemcpyHostToDevice));
+    observables_extra_dev(ctx, L, nev, dv.data(), q, dk.data(), dq.data(), df.data(), dd.data(), ctx->stream);
+    if (nev > 1) MBL_CUDA(cudaMemcpy(kl, dk.data(), (nev - 1) * sizeof(double), cudaMemcpyDeviceToHost));
+    MBL_CUDA(cudaMemcpy(sqp, dq.data(), nev * sizeof(double), cudaMemcpyDeviceToHost));
+    MBL_CUDA(cudaMemcpy(fluct, df.data(), nev * sizeof(double), cudaMemcpyDeviceToHost));
+    MBL_CUDA(cudaMemcpy(dynf, dd.data(), nev * sizeof(double), cudaMemcpyDeviceToHost));
     API_CATCH(ctx)
 }
 

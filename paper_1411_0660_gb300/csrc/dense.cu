@@ -25,18 +25,20 @@ constexpr int TN_MAXKP = 8192;  // PER (8) outputs x 1024 threads
 
 size_t dense_tn_work(int64_t n, int k, int p) { return (size_t)TN_CHUNKS * (size_t)k * (size_t)p; }
 
-__global__ void k_tn_partial(int64_t n, const double *__restrict__ V, int ldv, int c0, int k,
+// Partial sums of C = V^T X over row chunks, in the arithmetic of V's type (X is read as FP64).
+template <class TV>
+__global__ void k_tn_partial(int64_t n, const TV *__restrict__ V, int ldv, int c0, int k,
                              const double *__restrict__ X, int ldx, int x0, int p, double *__restrict__ work,
                              int64_t rows_per) {
-    extern __shared__ double sm[];
-    double *sv = sm;                 // TN_ROWS x k
-    double *sx = sm + TN_ROWS * k;   // TN_ROWS x p
+    extern __shared__ __align__(16) unsigned char smraw_tn[];
+    TV *sv = reinterpret_cast<TV *>(smraw_tn);  // TN_ROWS x k
+    TV *sx = sv + TN_ROWS * k;                  // TN_ROWS x p
     int64_t r0 = (int64_t)blockIdx.x * rows_per, r1 = min(n, r0 + rows_per);
     int kp = k * p;
     constexpr int PER = 8;
-    double acc[PER];
+    TV acc[PER];
 #pragma unroll
-    for (int u = 0; u < PER; ++u) acc[u] = 0.0;
+    for (int u = 0; u < PER; ++u) acc[u] = TV(0);
     for (int64_t rb = r0; rb < r1; rb += TN_ROWS) {
         int nr = (int)min((int64_t)TN_ROWS, r1 - rb);
         for (int t = threadIdx.x; t < nr * k; t += blockDim.x) {
@@ -45,7 +47,7 @@ __global__ void k_tn_partial(int64_t n, const double *__restrict__ V, int ldv, i
         }
         for (int t = threadIdx.x; t < nr * p; t += blockDim.x) {
             int r = t / p, q = t - r * p;
-            sx[r * p + q] = X[(rb + r) * ldx + x0 + q];
+            sx[r * p + q] = (TV)X[(rb + r) * ldx + x0 + q];
         }
         __syncthreads();
 #pragma unroll
@@ -53,7 +55,7 @@ __global__ void k_tn_partial(int64_t n, const double *__restrict__ V, int ldv, i
             int o = threadIdx.x + u * blockDim.x;
             if (o < kp) {
                 int a = o / p, q = o - a * p;
-                double s = acc[u];
+                TV s = acc[u];
                 for (int r = 0; r < nr; ++r) s = fma(sv[r * k + a], sx[r * p + q], s);
                 acc[u] = s;
             }
@@ -63,7 +65,7 @@ __global__ void k_tn_partial(int64_t n, const double *__restrict__ V, int ldv, i
 #pragma unroll
     for (int u = 0; u < PER; ++u) {
         int o = threadIdx.x + u * blockDim.x;
-        if (o < kp) work[(size_t)blockIdx.x * kp + o] = acc[u];
+        if (o < kp) work[(size_t)blockIdx.x * kp + o] = (double)acc[u];
     }
 }
 
@@ -75,8 +77,9 @@ __global__ void k_tn_reduce(int nch, int kp, const double *__restrict__ work, do
     C[o] = s;
 }
 
-void dense_tn(int64_t n, const double *V, int ldv, int c0, int k, const double *X, int ldx, int x0, int p,
-              double *C, double *work, cudaStream_t st) {
+template <class TV>
+static void dense_tn_t(int64_t n, const TV *V, int ldv, int c0, int k, const double *X, int ldx, int x0, int p,
+                       double *C, double *work, cudaStream_t st) {
     if (k <= 0 || p <= 0) return;
     if (k * p > TN_MAXKP) fail(MBL_ERR_INVALID, "dense_tn: block too wide");
     int threads = 1024;
@@ -84,35 +87,55 @@ void dense_tn(int64_t n, const double *V, int ldv, int c0, int k, const double *
     int64_t rows_per = (n + TN_CHUNKS - 1) / TN_CHUNKS;
     if (rows_per < 1) rows_per = 1;
     int nch = (int)((n + rows_per - 1) / rows_per);
-    size_t smem = (size_t)TN_ROWS * (k + p) * sizeof(double);
+    size_t smem = (size_t)TN_ROWS * (k + p) * sizeof(TV);
     static std::atomic<bool> attr{false};  // per process: one device
     if (!attr) {
-        MBL_CUDA(cudaFuncSetAttribute(k_tn_partial, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        MBL_CUDA(cudaFuncSetAttribute(k_tn_partial<TV>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
         attr = true;
     }
-    k_tn_partial<<<nch, threads, smem, st>>>(n, V, ldv, c0, k, X, ldx, x0, p, work, rows_per);
+    k_tn_partial<TV><<<nch, threads, smem, st>>>(n, V, ldv, c0, k, X, ldx, x0, p, work, rows_per);
     MBL_LAUNCH_CHECK();
     k_tn_reduce<<<(k * p + 255) / 256, 256, 0, st>>>(nch, k * p, work, C);
     MBL_LAUNCH_CHECK();
 }
 
-__global__ void k_nn_sub(int64_t n, const double *__restrict__ V, int ldv, int c0, int k,
+void dense_tn(int64_t n, const double *V, int ldv, int c0, int k, const double *X, int ldx, int x0, int p,
+              double *C, double *work, cudaStream_t st) {
+    dense_tn_t(n, V, ldv, c0, k, X, ldx, x0, p, C, work, st);
+}
+
+void dense_tn32(int64_t n, const float *V, int ldv, int c0, int k, const double *X, int ldx, int x0, int p,
+                double *C, double *work, cudaStream_t st) {
+    dense_tn_t(n, V, ldv, c0, k, X, ldx, x0, p, C, work, st);
+}
+
+// X -= V C (V row-major n x k at column c0, C k x p row-major); the sum in V's type.
+template <class TV>
+__global__ void k_nn_sub(int64_t n, const TV *__restrict__ V, int ldv, int c0, int k,
                          const double *__restrict__ C, int p, double *__restrict__ X) {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int64_t i = t / p;
     int q = (int)(t - i * p);
     if (i >= n) return;
-    const double *v = V + i * ldv + c0;
-    double s = 0.0;
-    for (int a = 0; a < k; ++a) s = fma(v[a], C[a * p + q], s);
-    X[i * p + q] -= s;
+    const TV *v = V + i * ldv + c0;
+    TV s = TV(0);
+    for (int a = 0; a < k; ++a) s = fma(v[a], (TV)C[a * p + q], s);
+    X[i * p + q] -= (double)s;
 }
 
 void dense_nn_sub(int64_t n, const double *V, int ldv, int c0, int k, const double *C, int p, double *X,
                   cudaStream_t st) {
     if (k <= 0) return;
     int64_t tot = n * p;
-    k_nn_sub<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(n, V, ldv, c0, k, C, p, X);
+    k_nn_sub<double><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(n, V, ldv, c0, k, C, p, X);
+    MBL_LAUNCH_CHECK();
+}
+
+void dense_nn_sub32(int64_t n, const float *V, int ldv, int c0, int k, const double *C, int p, double *X,
+                    cudaStream_t st) {
+    if (k <= 0) return;
+    int64_t tot = n * p;
+    k_nn_sub<float><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(n, V, ldv, c0, k, C, p, X);
     MBL_LAUNCH_CHECK();
 }
 

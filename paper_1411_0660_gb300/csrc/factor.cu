@@ -466,17 +466,21 @@ __global__ void __launch_bounds__(256) k_build_m(const SolveDesc *sdescs, const 
 }
 
 // G = [M; L21 M] of a solve panel (rows [k0, f) of the front x the panel's w columns) into the
-// packed solve factor (column-major, leading dimension sg_ld(f - k0)): RBB rows per CTA (grid: the
-// step's RBB-row tiles).
+// packed solve factor (column-major, leading dimension sg_ld(f - k0)).  CTA (x: the step's RBB-row
+// tiles, y: 256-column halves of the panel) computes a 64 x 256 block of L21 M in 32-deep chunks
+// of the contraction (16 x 16 threads, 4 x 16 outputs each); rows of the panel itself take M.
 template <class T>
 __global__ void __launch_bounds__(256) k_apply_m(const SolveDesc *sdescs, int nd, const int64_t *fo,
                                                  const int32_t *fsz, const T *arena, const T *Mall, T *Gp) {
+    constexpr int KC = 32, CW = 256, MSL = CW + 1;
     extern __shared__ __align__(16) unsigned char smraw[];
-    T *As = reinterpret_cast<T *>(smraw);  // RBB x (SPW + 1), row-major
-    T *Ms = As + RBB * (SPW + 1);          // 32 x SPW chunk of M, row-major
+    T *As = reinterpret_cast<T *>(smraw);  // RBB x (KC + 1): rows of L21, one contraction chunk
+    T *Ms = As + RBB * (KC + 1);           // KC x MSL: the chunk of M
     const int di = find_sdesc_b(sdescs, nd, blockIdx.x);
     const SolveDesc d = sdescs[di];
     const int s = d.front, f = fsz[s], k0 = d.k0, w = d.w;
+    const int cb = blockIdx.y * CW;  // first column of this half
+    if (cb >= w) return;
     const int r0 = (int)(blockIdx.x - d.offb) * RBB;  // first row, relative to k0
     const int nr = min(RBB, w + d.m2 - r0);
     if (nr <= 0) return;
@@ -491,24 +495,25 @@ __global__ void __launch_bounds__(256) k_apply_m(const SolveDesc *sdescs, int nd
 #pragma unroll
         for (int j = 0; j < 16; ++j) acc[i][j] = T(0);
     if (r0 + nr > w) {  // the tile has rows of L21
-        for (int idx = threadIdx.x; idx < RBB * w; idx += blockDim.x) {
-            int i = idx % RBB, c = idx / RBB;
-            As[i * (SPW + 1) + c] = i < nr ? F[(int64_t)(k0 + c) * f + k0 + r0 + i] : T(0);
-        }
-        for (int kc0 = 0; kc0 < w; kc0 += 32) {
-            const int kc = min(32, w - kc0);
+        for (int kc0 = 0; kc0 < w; kc0 += KC) {
+            const int kc = min(KC, w - kc0);
             __syncthreads();
-            for (int idx = threadIdx.x; idx < 32 * SPW; idx += blockDim.x) {
-                int k = idx % 32, c = idx / 32;
-                Ms[k * SPW + c] = (k < kc && c < w) ? M[(int64_t)c * w + kc0 + k] : T(0);
+            for (int idx = threadIdx.x; idx < RBB * KC; idx += blockDim.x) {
+                const int i = idx % RBB, k = idx / RBB;
+                As[i * (KC + 1) + k] = (i < nr && k < kc) ? F[(int64_t)(k0 + kc0 + k) * f + k0 + r0 + i] : T(0);
+            }
+            for (int idx = threadIdx.x; idx < KC * CW; idx += blockDim.x) {
+                const int k = idx % KC, c = idx / KC;
+                Ms[k * MSL + c] = (k < kc && cb + c < w) ? M[(int64_t)(cb + c) * w + kc0 + k] : T(0);
             }
             __syncthreads();
-            for (int k = 0; k < kc; ++k) {
+#pragma unroll 4
+            for (int k = 0; k < KC; ++k) {
                 T a[4], bv[16];
 #pragma unroll
-                for (int i = 0; i < 4; ++i) a[i] = As[(tr + 16 * i) * (SPW + 1) + kc0 + k];
+                for (int i = 0; i < 4; ++i) a[i] = As[(tr + 16 * i) * (KC + 1) + k];
 #pragma unroll
-                for (int j = 0; j < 16; ++j) bv[j] = Ms[k * SPW + tc + 16 * j];
+                for (int j = 0; j < 16; ++j) bv[j] = Ms[k * MSL + tc + 16 * j];
 #pragma unroll
                 for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -523,7 +528,7 @@ __global__ void __launch_bounds__(256) k_apply_m(const SolveDesc *sdescs, int nd
         const int rr = r0 + row;
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
-            const int col = tc + 16 * j;
+            const int col = cb + tc + 16 * j;
             if (col >= w) continue;
             G[(int64_t)col * ld + rr] = rr < w ? M[(int64_t)col * w + rr] : acc[i][j];
         }
@@ -532,11 +537,15 @@ __global__ void __launch_bounds__(256) k_apply_m(const SolveDesc *sdescs, int nd
 
 // Forward solve step, RBF rows of [k0, f) per CTA: with z = Z[panel] (PB >= p, zero-padded),
 // rows of the panel get Zs = M z and rows below get Z -= (L21 M) z.  Warp j takes columns
-// [32 j, 32 j + 32) of the panel; the eight partial sums meet in shared memory.
+// [32 j, 32 j + 32) of each 256-column half of the panel; the eight partial sums meet in shared
+// memory.  The CTA's rows of G are streamed into registers before waiting for the previous step
+// (FP32: both halves; FP64: the first).
 template <class T, int PB>
 __global__ void __launch_bounds__(256) k_fwd_step(const SolveDesc *sdescs, int nd, const int64_t *zo,
                                                   const int32_t *sn_start, const T *Gp, const T *Dg, T *Z, T *Zs,
-                                                  T *yfw, int p) {
+                                                  T *yfw, int p, LaunchTrace *tr) {
+    TraceScope trace_scope(tr);
+    constexpr int NH = (SPW + 255) / 256, NPF = sizeof(T) == 4 ? NH : 1;
     extern __shared__ __align__(16) unsigned char smraw[];
     T *zp = reinterpret_cast<T *>(smraw);  // SPW x PB; afterwards the 8 x PB x RBF partials
     pdl_trigger();
@@ -547,15 +556,15 @@ __global__ void __launch_bounds__(256) k_fwd_step(const SolveDesc *sdescs, int n
     const int nr = min(RBF, w + d.m2 - r0);
     const int64_t zb = zo[s] + k0, ld = sg_ld(w + d.m2);
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-    const int c0 = wp * 32, c1 = min(w, c0 + 32);
-    const bool active = lane < nr && c0 < c1, full = c1 - c0 == 32;
     const T *g = Gp + d.goff + r0 + lane;
-    // the factor does not change during a solve: stream this thread's row of G before waiting for
-    // the previous step
-    T lv[32];
-    if (active && full) {
+    T lv[NPF][32];
 #pragma unroll
-        for (int c = 0; c < 32; ++c) lv[c] = g[(int64_t)(c0 + c) * ld];
+    for (int h = 0; h < NPF; ++h) {
+        const int c0 = h * 256 + wp * 32;
+        if (lane < nr && c0 + 32 <= w) {
+#pragma unroll
+            for (int c = 0; c < 32; ++c) lv[h][c] = g[(int64_t)(c0 + c) * ld];
+        }
     }
     pdl_wait();
     for (int idx = threadIdx.x; idx < w * PB; idx += blockDim.x) {
@@ -566,12 +575,15 @@ __global__ void __launch_bounds__(256) k_fwd_step(const SolveDesc *sdescs, int n
     T acc[PB];
 #pragma unroll
     for (int q = 0; q < PB; ++q) acc[q] = T(0);
-    if (active) {
-        if (full) {
+#pragma unroll
+    for (int h = 0; h < NH; ++h) {
+        const int c0 = h * 256 + wp * 32, c1 = min(w, c0 + 32);
+        if (lane >= nr || c0 >= c1) continue;
+        if (h < NPF && c1 - c0 == 32) {
 #pragma unroll
             for (int c = 0; c < 32; ++c)
 #pragma unroll
-                for (int q = 0; q < PB; ++q) acc[q] += lv[c] * zp[(c0 + c) * PB + q];
+                for (int q = 0; q < PB; ++q) acc[q] += lv[h < NPF ? h : 0][c] * zp[(c0 + c) * PB + q];
         } else {
             for (int c = c0; c < c1; ++c) {
                 const T l = g[(int64_t)c * ld];
@@ -603,11 +615,20 @@ __global__ void __launch_bounds__(256) k_fwd_step(const SolveDesc *sdescs, int n
     }
 }
 
+__global__ void k_trace_reset(LaunchTrace *tr, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        tr[i].t0 = ~0ull;
+        tr[i].t1 = 0ull;
+    }
+}
+
 // Forward gather of one level from the row lists: Z[dst] = y[own] (or 0) + the children's
 // contributions in tree order; one thread per (row, right-hand side).
 template <class T>
 __global__ void k_fwd_gather_rows(int64_t nrows, const int64_t *dst, const int64_t *own, const int64_t *cptr,
-                                  const int64_t *src, const T *y, T *Z, int p) {
+                                  const int64_t *src, const T *y, T *Z, int p, LaunchTrace *tr) {
+    TraceScope trace_scope(tr);
     pdl_trigger();
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t row = t / p;
@@ -626,34 +647,22 @@ __global__ void k_fwd_gather_rows(int64_t nrows, const int64_t *dst, const int64
     Z[d * p + q] = v;
 }
 
-template <class T>
-__global__ void k_bwd_gather(const AsmItem *items, const int64_t *zo, const int32_t *fsz, const int32_t *nc,
-                             const int32_t *sn_start, const int64_t *rows_off, const int32_t *rows, const T *yfw,
-                             const T *x, T *Z, int p) {
-    pdl_trigger();
-    AsmItem it = items[blockIdx.x];
-    const int s = it.front, f = fsz[s], r0 = it.c0, r1 = min(f, r0 + ACOLS), ncs = nc[s];
-    T *z = Z + zo[s] * p;
-    const int32_t *rw = rows + rows_off[s];
-    pdl_wait();
-    for (int idx = threadIdx.x; idx < (r1 - r0) * p; idx += blockDim.x) {
-        int r = r0 + idx / p, q = idx % p;
-        z[(int64_t)r * p + q] = (r < ncs) ? yfw[((int64_t)sn_start[s] + r) * p + q] : x[(int64_t)rw[r] * p + q];
-    }
-}
-
 // Backward solve step, tiles of RBK rows x RBB columns of G = [M; L21 M] (grid: row blocks x
 // column chunks): x_panel = G^T v with v = [y_panel; -x_below].  The tile is copied from the packed
 // solve factor to shared memory (16-byte cp.async) before waiting for the previous step (G does
 // not change during a solve).  A panel with one row block writes x directly; otherwise each block
 // writes its partial sums and the last block of a (panel, column chunk) to finish (counted with an
 // atomic, after a fence) adds the partials in a fixed order, writes the panel's x into Zs and x,
-// and re-arms the counter.  The panel's rows of Z hold the forward result y (pivoted order); rows
-// below the panel come from Zs (fully summed rows solved by later panels) or Z (the ancestors' x).
+// and re-arms the counter.  v is read in place: the panel's rows from the forward result yfw
+// (pivoted order), rows of later panels from Zs, and the rows of the contribution block -- the
+// ancestors' x, final by now -- from x through the front's row list (static, read before waiting).
 template <class T, int PB>
 __global__ void __launch_bounds__(256) k_bwd_step(const SolveDesc *sdescs, int nd, const int64_t *zo,
-                                                  const int32_t *nc, const int32_t *sn_start, const T *Gp,
-                                                  const T *Z, T *Zs, T *P, unsigned int *cnt, T *x, int p) {
+                                                  const int32_t *nc, const int32_t *sn_start,
+                                                  const int64_t *rows_off, const int32_t *rows, const T *Gp,
+                                                  const T *yfw, T *Zs, T *P, unsigned int *cnt, T *x, int p,
+                                                  LaunchTrace *tr) {
+    TraceScope trace_scope(tr);
     constexpr int E = 16 / sizeof(T);
     extern __shared__ __align__(16) unsigned char smraw[];
     T *Gs = reinterpret_cast<T *>(smraw);    // RBB columns x bwd_ldg rows
@@ -675,17 +684,25 @@ __global__ void __launch_bounds__(256) k_bwd_step(const SolveDesc *sdescs, int n
     const int wc = min(RBB, w - cc);
     const int64_t zb = zo[s] + k0, ld = sg_ld(R);
     bwd_tile_issue(Gs, Gp + d.goff + (int64_t)cc * ld + r0, ld, wc, nrv);
+    // thread i loads row i of v
+    static_assert(RBK == 256, "one row of v per thread");
+    const int i = threadIdx.x, rr = r0 + i;
+    const int kind = i >= nr ? 0 : (rr < w ? 1 : (k0 + rr < ncs ? 2 : 3));
+    const int64_t src = kind == 1 ? ((int64_t)sn_start[s] + k0 + rr) * p
+                      : kind == 2 ? (zb + rr) * p
+                      : kind == 3 ? (int64_t)rows[rows_off[s] + k0 + rr] * p : 0;
     pdl_wait();
-    for (int idx = threadIdx.x; idx < RBK * PB; idx += blockDim.x) {
-        const int i = idx / PB, q = idx % PB;
-        T v = T(0);
-        if (i < nr && q < p) {
-            const int rr = r0 + i;
-            if (rr < w) v = Z[(zb + rr) * p + q];
-            else if (k0 + rr < ncs) v = -Zs[(zb + rr) * p + q];
-            else v = -Z[(zb + rr) * p + q];
+    {
+        T *vr = vs + i * PB;
+        if (kind == 0) {
+#pragma unroll
+            for (int q = 0; q < PB; ++q) vr[q] = T(0);
+        } else {
+            const T *sp = kind == 1 ? yfw + src : (kind == 2 ? Zs + src : x + src);
+            const T sg = kind == 1 ? T(1) : T(-1);
+#pragma unroll
+            for (int q = 0; q < PB; ++q) vr[q] = q < p ? sg * sp[q] : T(0);
         }
-        vs[idx] = v;
     }
     cp_async_commit_wait();
     __syncthreads();
@@ -731,7 +748,7 @@ static size_t build_m_smem() { return 8 * ((size_t)(SPW + NB) * 33 + (size_t)NB 
 template <class T>
 static size_t trsm_smem() { return sizeof(T) * (size_t)2 * NB * (NB + 1); }
 template <class T>
-static size_t apply_m_smem() { return sizeof(T) * ((size_t)RBB * (SPW + 1) + (size_t)32 * SPW); }
+static size_t apply_m_smem() { return sizeof(T) * ((size_t)RBB * 33 + (size_t)32 * 257); }
 template <class T, int PB>
 static size_t fwd_step_smem() { return sizeof(T) * (size_t)SPW * PB; }
 template <class T, int PB>
@@ -828,7 +845,7 @@ static void factor_impl(Factorization &fz, cudaStream_t st) {
         T *Gp = static_cast<T *>(fz.gpk.m.p);
         MBL_CUDA(cudaMemsetAsync(Gp, 0, (size_t)p.sg_elems * sizeof(T), st));  // padding rows stay zero
         for (const SolveStep &ss : p.ssteps) {
-            k_apply_m<T><<<(unsigned)ss.nrbb, 256, apply_m_smem<T>(), st>>>(p.d_sdescs.data() + ss.d0, ss.nd,
+            k_apply_m<T><<<dim3((unsigned)ss.nrbb, (SPW + 255) / 256), 256, apply_m_smem<T>(), st>>>(p.d_sdescs.data() + ss.d0, ss.nd,
                                                                            p.d_sn_fo.data(), p.d_sn_f.data(), arena,
                                                                            static_cast<const T *>(fz.M.m.p), Gp);
             MBL_LAUNCH_CHECK();
@@ -854,34 +871,43 @@ static void solve_levels(Factorization &fz, int p, cudaStream_t st) {
     T *P = static_cast<T *>(fz.pwork.m.p);
     unsigned int *cnt = fz.scnt.data();
     const size_t fsm = fwd_step_smem<T, PB>(), bsm = bwd_step_smem<T, PB>();
+    // launch trace: one record per launch below, reset at the start of every solve
+    const int ntr = pl.nlevels + 2 * (int)pl.ssteps.size();
+    LaunchTrace *trb = nullptr;
+    if (fz.trace_on) {
+        if (fz.trace.size() < (size_t)ntr) fz.trace.alloc(fz.ctx, ntr);
+        trb = fz.trace.data();
+        k_trace_reset<<<(ntr + 255) / 256, 256, 0, st>>>(trb, ntr);
+        MBL_LAUNCH_CHECK();
+        fz.trace_kind.clear();
+    }
+    int it = 0;
+    auto next_tr = [&](int kind) -> LaunchTrace * {
+        if (!trb) return nullptr;
+        fz.trace_kind.push_back(kind);
+        return trb + it++;
+    };
     for (int l = 0; l < pl.nlevels; ++l) {
-        int na = pl.asm_ptr[l + 1] - pl.asm_ptr[l];
-        const AsmItem *items = pl.d_asm_items.data() + pl.asm_ptr[l];
         {
             const int64_t f0 = pl.lvl_fg_ptr[l], nrows = pl.lvl_fg_ptr[l + 1] - f0;
             launch_pdl(k_fwd_gather_rows<T>, dim3((unsigned)((nrows * p + 255) / 256)), dim3(256), 0, st, nrows,
                        pl.d_fg_dst.data() + f0, pl.d_fg_own.data() + f0, pl.d_fg_cptr.data() + f0,
-                       (const int64_t *)pl.d_fg_src.data(), (const T *)y, Z, p);
+                       (const int64_t *)pl.d_fg_src.data(), (const T *)y, Z, p, next_tr(0));
         }
         for (int si = pl.lvl_sstep_ptr[l]; si < pl.lvl_sstep_ptr[l + 1]; ++si) {
             const SolveStep &ss = pl.ssteps[si];
             const SolveDesc *sd = pl.d_sdescs.data() + ss.d0;
             launch_pdl(k_fwd_step<T, PB>, dim3((unsigned)ss.nrb), dim3(256), fsm, st, sd, ss.nd,
-                       pl.d_sn_zo.data(), pl.d_sn_start.data(), Gp, (const T *)Dg, Z, Zs, yfw, p);
+                       pl.d_sn_zo.data(), pl.d_sn_start.data(), Gp, (const T *)Dg, Z, Zs, yfw, p, next_tr(1));
         }
     }
     for (int l = pl.nlevels - 1; l >= 0; --l) {
-        int na = pl.asm_ptr[l + 1] - pl.asm_ptr[l];
-        const AsmItem *items = pl.d_asm_items.data() + pl.asm_ptr[l];
-        launch_pdl(k_bwd_gather<T>, dim3(na), dim3(256), 0, st, items, pl.d_sn_zo.data(), pl.d_sn_f.data(),
-                   pl.d_sn_nc.data(), pl.d_sn_start.data(), pl.d_sn_rows_off.data(), pl.d_rows.data(),
-                   (const T *)yfw, (const T *)y, Z, p);
         for (int si = pl.lvl_sstep_ptr[l + 1] - 1; si >= pl.lvl_sstep_ptr[l]; --si) {
             const SolveStep &ss = pl.ssteps[si];
             const SolveDesc *sd = pl.d_sdescs.data() + ss.d0;
             launch_pdl(k_bwd_step<T, PB>, dim3((unsigned)ss.nrbk, SUBS), dim3(256), bsm, st, sd, ss.nd,
-                       pl.d_sn_zo.data(), pl.d_sn_nc.data(), pl.d_sn_start.data(), Gp, (const T *)Z, Zs, P,
-                       cnt + (size_t)ss.d0 * SUBS, y, p);
+                       pl.d_sn_zo.data(), pl.d_sn_nc.data(), pl.d_sn_start.data(), pl.d_sn_rows_off.data(),
+                       pl.d_rows.data(), Gp, (const T *)yfw, Zs, P, cnt + (size_t)ss.d0 * SUBS, y, p, next_tr(2));
         }
     }
 }

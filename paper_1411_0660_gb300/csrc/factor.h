@@ -27,6 +27,10 @@ struct Factorization {
     int graph_p = 0;
     long long graph_nodes = 0;
     bool use_tc = true;  // tcgen05 Schur updates for FP32 fronts
+    // launch trace of the level-by-level solve (opt-in; recaptures the solve graph when switched)
+    bool trace_on = false;
+    DVec<LaunchTrace> trace;
+    std::vector<int> trace_kind;  // per traced launch: 0 forward gather, 1 forward step, 2 backward step
     int64_t perturbed = 0, negative = 0;
     double ms_factor = 0.0;
 

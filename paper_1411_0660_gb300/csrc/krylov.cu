@@ -704,6 +704,14 @@ __global__ void __launch_bounds__(512) k_small_inverse(int k, double *A, int *fl
     for (int i = t; i < k * k; i += blockDim.x) A[i] = sa[i];
 }
 
+// dst (n x k row-major, FP32) = src[:, 0:k] (row stride lds)
+__global__ void k_cols_to_f32(int64_t n, const double *src, int lds, int k, float *dst) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n * k) return;
+    const int64_t i = t / k;
+    dst[t] = (float)src[i * lds + (t - i * k)];
+}
+
 void RefinedSolve::set_deflation(const double *U_, int ldu_, int k, cudaStream_t st) {
     kd = 0;
     if (k <= 0) return;
@@ -716,6 +724,8 @@ void RefinedSolve::set_deflation(const double *U_, int ldu_, int k, cudaStream_t
     if (Dc1.size() < (size_t)k * 32) Dc1.alloc(ctx, (size_t)k * 32);
     if (Dwork.size() < dense_tn_work(n, k, std::max(k, 32)) + 64) Dwork.alloc(ctx, dense_tn_work(n, k, std::max(k, 32)) + 64);
     if (Dflag.size() < 1) Dflag.alloc(ctx, 1);
+    if (U32.size() < (size_t)n * k) U32.alloc(ctx, (size_t)n * k);
+    if (AU32.size() < (size_t)n * k) AU32.alloc(ctx, (size_t)n * k);
     // A U, then E = U^T A U (k x k, row-major) and its inverse
     launch_spmv(sec, fz->sigma, U_, ldu_, 1, AU.data(), k, 1, k, st);
     dense_tn(n, U_, ldu_, 0, k, AU.data(), k, 0, k, Einv.data(), Dwork.data(), st);
@@ -730,8 +740,10 @@ void RefinedSolve::set_deflation(const double *U_, int ldu_, int k, cudaStream_t
     MBL_CUDA(cudaMemcpyAsync(&ok, Dflag.data(), sizeof(int), cudaMemcpyDeviceToHost, st));
     MBL_CUDA(cudaStreamSynchronize(st));
     if (!ok) return;
-    U = U_;
-    ldu = ldu_;
+    k_cols_to_f32<<<nblk(n * k), 256, 0, st>>>(n, U_, ldu_, k, U32.data());
+    MBL_LAUNCH_CHECK();
+    k_cols_to_f32<<<nblk(n * k), 256, 0, st>>>(n, AU.data(), k, k, AU32.data());
+    MBL_LAUNCH_CHECK();
     kd = k;
 }
 
@@ -743,14 +755,14 @@ void RefinedSolve::precondition(const double *V, double *Z, int p, cudaStream_t 
     const int64_t n = sec->n;
     if (Dt.size() < (size_t)n * p) Dt.alloc(sec->ctx, (size_t)n * p);
     // c = E^-1 U^T v  (kd x p, row-major)
-    dense_tn(n, U, ldu, 0, kd, V, p, 0, p, Dc0.data(), Dwork.data(), st);
+    dense_tn32(n, U32.data(), kd, 0, kd, V, p, 0, p, Dc0.data(), Dwork.data(), st);
     gemm_small(false, false, p, kd, kd, 1.0, Dc0.data(), p, Einv.data(), kd, 0.0, Dc1.data(), p, st);
     // z = M^-1 (v - A U c) + U c
     MBL_CUDA(cudaMemcpyAsync(Dt.data(), V, (size_t)n * p * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    dense_nn_sub(n, AU.data(), kd, 0, kd, Dc1.data(), p, Dt.data(), st);
+    dense_nn_sub32(n, AU32.data(), kd, 0, kd, Dc1.data(), p, Dt.data(), st);
     factor_solve_raw(*fz, Dt.data(), p, Z, p, p, false, st);
     gemm_small(false, false, p, kd, kd, -1.0, Dc0.data(), p, Einv.data(), kd, 0.0, Dc1.data(), p, st);
-    dense_nn_sub(n, U, ldu, 0, kd, Dc1.data(), p, Z, st);
+    dense_nn_sub32(n, U32.data(), kd, 0, kd, Dc1.data(), p, Z, st);
 }
 
 void RefinedSolve::apply_fgmres(const double *X, int ldx, double *Y, int p, cudaStream_t st) {

@@ -51,12 +51,14 @@ struct RefinedSolve {
     // eigenvectors nearest sigma and A = H - sigma, the preconditioner is
     //   P = M^-1 (I - A Q) + Q,   Q = U (U^T A U)^-1 U^T,
     // M the factor: the directions where the factor is weakest are solved in span(U) exactly.
-    const double *U = nullptr;
-    int ldu = 0, kd = 0;
+    // (U^T A U)^-1 is formed in FP64; U and A U are kept as FP32 copies (n x kd), since the
+    // preconditioner needs them only to FP32 accuracy and FP64 products would cost ~20x more.
+    int kd = 0;
     DVec<double> AU, Einv, Dc0, Dc1, Dt, Dwork;
+    DVec<float> U32, AU32;
     DVec<int> Dflag;
     void apply(const double *X, int ldx, double *Y, int p, cudaStream_t st);
-    // Use U[:, 0:k] (k <= 90; k = 0 switches deflation off); U must stay unchanged until the next call.
+    // Use U[:, 0:k] (k <= 90; k = 0 switches deflation off); U is copied.
     void set_deflation(const double *U_, int ldu_, int k, cudaStream_t st);
     void clear_deflation() { kd = 0; }
 

@@ -49,6 +49,28 @@ extern thread_local long long t_launches;  // this thread's share (graph capture
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
+// Opt-in launch trace of the triangular solves: per launch, the %globaltimer (ns) when its first
+// CTA started and when its last CTA finished (thread 0 of each CTA; atomics on two words).
+struct LaunchTrace {
+    unsigned long long t0, t1;
+};
+#ifdef __CUDACC__
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+struct TraceScope {
+    LaunchTrace *tr;
+    __device__ explicit TraceScope(LaunchTrace *t) : tr(t) {
+        if (tr && threadIdx.x == 0) atomicMin(&tr->t0, global_ns());
+    }
+    __device__ ~TraceScope() {
+        if (tr && threadIdx.x == 0) atomicMax(&tr->t1, global_ns());
+    }
+};
+#endif
+
 template <typename... KArgs, typename... Args>
 void launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, Args... args) {
     cudaLaunchConfig_t cfg = {};
@@ -190,6 +212,11 @@ void dense_tn(int64_t n, const double *V, int ldv, int c0, int k, const double *
 // X -= V[:, c0:c0+k] C  (C k x p row-major)
 void dense_nn_sub(int64_t n, const double *V, int ldv, int c0, int k, const double *C, int p, double *X,
                   cudaStream_t st);
+// FP32-stored V (the products summed in FP32): dense_tn and dense_nn_sub for preconditioner work.
+void dense_tn32(int64_t n, const float *V, int ldv, int c0, int k, const double *X, int ldx, int x0, int p,
+                double *C, double *work, cudaStream_t st);
+void dense_nn_sub32(int64_t n, const float *V, int ldv, int c0, int k, const double *C, int p, double *X,
+                    cudaStream_t st);
 // Y[:, 0:m] = V[:, 0:k] S  (S k x m row-major, Y n x ldy row-major starting at column y0)
 void dense_nn(int64_t n, const double *V, int ldv, int k, const double *S, int m, double *Y, int ldy,
               int y0, cudaStream_t st);

@@ -1,7 +1,12 @@
 // observables.cu -- eigenvector observables of arXiv:1411.0660, characterization section:
 //   (i)   gap ratio r^(n) = min(d_n, d_{n+1}) / max(d_n, d_{n+1}), d_n = E_n - E_{n-1};
 //   (iii) participation entropy S_1^P = -sum_i p_i ln p_i, p_i = |<i|n>|^2 in the S^z basis;
-//   (ii)  half-chain entanglement entropy S^E = -Tr rho_A ln rho_A for A = sites 0..L/2-1.
+//   (ii)  half-chain entanglement entropy S^E = -Tr rho_A ln rho_A for A = sites 0..L/2-1;
+// and, in observables_extra_dev: the Kullback-Leibler divergence KL = sum_i p_i ln(p_i / q_i) of
+// adjacent eigenvectors (i), S_q^P = ln(sum_i p_i^q) / (1 - q) (iii), the bipartite fluctuation
+// F = <(S^z_A)^2> - <S^z_A>^2 (ii), and the dynamic spin fraction f = 1 - |<M>|^2 / <M^+ M>,
+// M = sum_j S^z_j e^{2 pi i j / L}, of the supplementary section.  S^z_A and M are diagonal in the
+// S^z basis, so all are reductions over the weights p_i = y_i^2 / |y|^2.
 // For S^E the vector is split by the magnetization n_A of the half chain: the block
 // M_{n_A}[a][b] = psi(a + b 2^{L/2}) (a with n_A up spins, b with L/2 - n_A) has Gram matrix
 // M M^T whose eigenvalues are the Schmidt weights of that block; all blocks of all vectors go to
@@ -135,6 +140,14 @@ EntTables &ent_tables(Ctx *ctx, int L) {
         for (uint32_t a : as)
             for (uint32_t b : bs) idx.push_back((int32_t)host_rank(a | (b << LA)));
     }
+    {
+        std::vector<uint32_t> st;
+        st.reserve((size_t)host_binom(L, L / 2));
+        for (uint32_t s = 0; s < (1u << L); ++s)
+            if (__builtin_popcount(s) == L / 2) st.push_back(s);
+        T->d_states.alloc(ctx, st.size());
+        MBL_CUDA(cudaMemcpy(T->d_states.data(), st.data(), st.size() * 4, cudaMemcpyHostToDevice));
+    }
     T->nblk = (int)da.size();
     T->dA = da;
     T->dAmax = *std::max_element(da.begin(), da.end());
@@ -149,6 +162,117 @@ EntTables &ent_tables(Ctx *ctx, int L) {
     EntTables &ref = *T;
     ctx->ent[L] = T;
     return ref;
+}
+
+// One CTA per vector: A = sum y^2 and the weighted sums sum y^2 g(s) of g = (y^2)^(q), m_A, m_A^2,
+// Re M, Im M, |M|^2, combined into S_q^P, F and f.  out_nrm2[j] = A.
+__global__ void k_moments(int64_t n, int L, const uint32_t *states, const double *Y, double q, double *sqp,
+                          double *fluct, double *dynf, double *out_nrm2) {
+    __shared__ double cs[32], sn[32];
+    __shared__ double red[7][32];
+    if (threadIdx.x < L) {
+        sincospi(2.0 * threadIdx.x / L, &sn[threadIdx.x], &cs[threadIdx.x]);
+    }
+    __syncthreads();
+    const double *y = Y + (int64_t)blockIdx.x * n;
+    const uint32_t maskA = (1u << (L / 2)) - 1u;
+    double v[7] = {0, 0, 0, 0, 0, 0, 0};
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        const double w = y[i] * y[i];
+        const uint32_t s = states[i];
+        const double mA = 0.5 * (double)(2 * __popc(s & maskA) - L / 2);
+        double mr = 0.0, mi = 0.0;
+        for (int j = 0; j < L; ++j) {
+            const double sz = ((s >> j) & 1u) ? 0.5 : -0.5;
+            mr += sz * cs[j];
+            mi += sz * sn[j];
+        }
+        v[0] += w;
+        if (w > 0.0) v[1] += q == 2.0 ? w * w : pow(w, q);
+        v[2] += w * mA;
+        v[3] += w * mA * mA;
+        v[4] += w * mr;
+        v[5] += w * mi;
+        v[6] += w * (mr * mr + mi * mi);
+    }
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+        double a = v[k];
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+        if (lane == 0) red[k][wp] = a;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t[7];
+        for (int k = 0; k < 7; ++k) {
+            t[k] = 0.0;
+            for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t[k] += red[k][i];
+        }
+        const double A = t[0];
+        sqp[blockIdx.x] = (log(t[1]) - q * log(A)) / (1.0 - q);
+        const double m1 = t[2] / A;
+        fluct[blockIdx.x] = t[3] / A - m1 * m1;
+        dynf[blockIdx.x] = t[6] == 0.0 ? NAN : 1.0 - (t[4] * t[4] + t[5] * t[5]) / (A * t[6]);
+        out_nrm2[blockIdx.x] = A;
+    }
+}
+
+// One CTA per adjacent pair (j, j + 1): KL = sum_i p_i (ln y_j,i^2 - ln y_j+1,i^2) + ln A_j+1 - ln A_j
+// over the terms with p_i > 0; +infinity if such a term has q_i = 0.
+__global__ void k_kl(int64_t n, const double *Y, const double *nrm2, double *kl) {
+    __shared__ double red[32];
+    __shared__ int rinf[32];
+    const double *y = Y + (int64_t)blockIdx.x * n, *z = y + n;
+    double a = 0.0;
+    int inf = 0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        const double p = y[i] * y[i], qq = z[i] * z[i];
+        if (p == 0.0) continue;
+        if (qq == 0.0) {
+            inf = 1;
+            continue;
+        }
+        a += p * (log(p) - log(qq));
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        inf |= __shfl_down_sync(0xffffffffu, inf, o);
+    }
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    if (lane == 0) {
+        red[wp] = a;
+        rinf[wp] = inf;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        int f = 0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+            t += red[i];
+            f |= rinf[i];
+        }
+        const double Aj = nrm2[blockIdx.x], Ak = nrm2[blockIdx.x + 1];
+        kl[blockIdx.x] = f ? INFINITY : t / Aj + log(Ak) - log(Aj);
+    }
+}
+
+void observables_extra_dev(Ctx *ctx, int L, int nev, const double *d_evecs, double q, double *d_kl, double *d_sqp,
+                           double *d_fluct, double *d_dynf, cudaStream_t st) {
+    ProfScope ps_all(ctx, "observables", (double)nev, st);
+    const int64_t n = host_binom(L, L / 2);
+    if (nev < 1 || nev > n) fail(MBL_ERR_INVALID, "observables: nev must be in [1, dim]");
+    if (!(q > 0.0) || q == 1.0 || !std::isfinite(q)) fail(MBL_ERR_INVALID, "observables: q must be positive and not 1");
+    EntTables &E = ent_tables(ctx, L);
+    DVec<double> nrm2;
+    nrm2.alloc(ctx, nev);
+    k_moments<<<nev, 256, 0, st>>>(n, L, E.d_states.data(), d_evecs, q, d_sqp, d_fluct, d_dynf, nrm2.data());
+    MBL_LAUNCH_CHECK();
+    if (nev > 1) {
+        k_kl<<<nev - 1, 256, 0, st>>>(n, d_evecs, nrm2.data(), d_kl);
+        MBL_LAUNCH_CHECK();
+    }
+    MBL_CUDA(cudaStreamSynchronize(st));
 }
 
 void observables_dev(Ctx *ctx, int L, int nev, const double *d_evals, const double *d_evecs, double *d_r,

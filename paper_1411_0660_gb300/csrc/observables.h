@@ -1,4 +1,5 @@
-// observables.h -- gap ratio, participation entropy and half-chain entanglement entropy.
+// observables.h -- eigenvector observables: gap ratio, participation entropies, half-chain
+// entanglement entropy, KL divergence of adjacent eigenvectors, bipartite fluctuation, dynamic fraction.
 #pragma once
 
 #include "mbl_internal.h"
@@ -10,11 +11,15 @@ struct EntTables {
     std::vector<int32_t> dA;
     DVec<int32_t> d_idx, d_dA, d_dB;  // idx: ranks of a + b 2^{L/2}, block after block, row-major dA x dB
     DVec<int64_t> d_boff;
+    DVec<uint32_t> d_states;  // the sector's basis states in ascending order
 };
 
 EntTables &ent_tables(Ctx *ctx, int L);
 void observables_dev(Ctx *ctx, int L, int nev, const double *d_evals, const double *d_evecs, double *d_r,
                      double *d_rmean, double *d_s1p, double *d_se, cudaStream_t st);
+// KL of adjacent vectors (nev - 1), S_q^P, bipartite fluctuation F and dynamic fraction f (nev each)
+void observables_extra_dev(Ctx *ctx, int L, int nev, const double *d_evecs, double q, double *d_kl, double *d_sqp,
+                           double *d_fluct, double *d_dynf, cudaStream_t st);
 // S^E of nev vectors (L <= 16, nev <= 64) on a static device scratch, no allocation (noalloc.cu)
 void noalloc_setup(int device);
 void entanglement_noalloc(Ctx *ctx, int L, int nev, const double *d_evecs, double *d_se, cudaStream_t st);

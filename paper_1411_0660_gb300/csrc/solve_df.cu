@@ -122,13 +122,16 @@ __global__ void __launch_bounds__(256) k_df_fwd(DfArgs A, const T *Gp, const T *
         const int r0 = it.b * RBF;
         const int nr = min(RBF, w + d.m2 - r0);
         const int64_t zb = A.zo[s] + k0, ld = sg_ld(w + d.m2);
-        const int c0 = wp * 32, c1 = min(w, c0 + 32);
-        const bool active = lane < nr && c0 < c1, full = c1 - c0 == 32;
+        constexpr int NH = (SPW + 255) / 256, NPF = sizeof(T) == 4 ? NH : 1;
         const T *g = Gp + d.goff + r0 + lane;
-        T lv[32];
-        if (active && full) {  // the factor is read-only: load it before waiting
+        T lv[NPF][32];
 #pragma unroll
-            for (int c = 0; c < 32; ++c) lv[c] = g[(int64_t)(c0 + c) * ld];
+        for (int h = 0; h < NPF; ++h) {  // the factor is read-only: load it before waiting
+            const int c0 = h * 256 + wp * 32;
+            if (lane < nr && c0 + 32 <= w) {
+#pragma unroll
+                for (int c = 0; c < 32; ++c) lv[h][c] = g[(int64_t)(c0 + c) * ld];
+            }
         }
         if (tid == 0) s_ok = df_wait(A.gcnt + s, A.gchunks[s], A.err) && df_wait(A.fcnt + s, A.fprefix[qd], A.err);
         __syncthreads();
@@ -141,12 +144,15 @@ __global__ void __launch_bounds__(256) k_df_fwd(DfArgs A, const T *Gp, const T *
         T acc[PB];
 #pragma unroll
         for (int q = 0; q < PB; ++q) acc[q] = T(0);
-        if (active) {
-            if (full) {
+#pragma unroll
+        for (int h = 0; h < NH; ++h) {
+            const int c0 = h * 256 + wp * 32, c1 = min(w, c0 + 32);
+            if (lane >= nr || c0 >= c1) continue;
+            if (h < NPF && c1 - c0 == 32) {
 #pragma unroll
                 for (int c = 0; c < 32; ++c)
 #pragma unroll
-                    for (int q = 0; q < PB; ++q) acc[q] += lv[c] * zp[(c0 + c) * PB + q];
+                    for (int q = 0; q < PB; ++q) acc[q] += lv[h < NPF ? h : 0][c] * zp[(c0 + c) * PB + q];
             } else {
                 for (int c = c0; c < c1; ++c) {
                     const T l = g[(int64_t)c * ld];
