@@ -36,7 +36,8 @@ HS = [0.5, 1.0, 2.0, 3.0, 4.0, 5.0]
 EPS = [0.1, 0.5, 0.9]
 PROF_KEYS = ("factor_fp32", "schur_fp32", "schur_tc", "trisolve_fp32", "refine_spmv", "orth", "syev_krylov",
              "syev_rr", "extremal_bounds", "op_apply", "ks_restart", "ritz_h", "observables", "sector_build",
-             "syev_fp32", "syev_fallback", "oa_refine", "trisolve_fp64", "factor_fp64", "syev_rr_fp64")
+             "syev_fp32", "syev_fallback", "oa_refine", "trisolve_fp64", "factor_fp64", "syev_rr_fp64",
+             "gm_deflate", "gm_spmv", "gm_orth", "f_assemble", "f_panel", "f_build_g")
 METRIC = "eigenpairs/s near eps (res<=1e-10||H||), L=18, mixed vs FP64; p50/p99 latency"
 
 
@@ -203,14 +204,16 @@ def run_case(args):
         base = int(t0s.min())
         rec = [[int(k), (int(a) - base) / 1e3, (int(b) - base) / 1e3] for k, a, b in zip(kind, t0s, t1s)]
         prev = 0.0
-        crit = {0: 0.0, 1: 0.0, 2: 0.0}
+        crit = {0: 0.0, 1: 0.0, 2: 0.0, 3: 0.0}
         for k, a, b in rec:  # time each launch adds after its predecessor finished
             crit[k] += b - max(prev, a)
             prev = b
         line["trace"] = {"launches": len(rec), "span_us": rec[-1][2] - rec[0][1] if rec else 0.0,
-                         "critical_us": {"gather": crit[0], "forward": crit[1], "backward": crit[2]}}
+                         "critical_us": {"gather": crit[0], "forward": crit[1], "backward_start": crit[2],
+                                         "backward_update": crit[3]}}
         with open(args.trace, "w") as fo:
-            json.dump({"records_us": rec, "kinds": "0 gather, 1 forward step, 2 backward step"}, fo)
+            json.dump({"records_us": rec, "kinds": "0 gather, 1 forward step, 2 backward level start, "
+                                                   "3 backward update"}, fo)
     print(json.dumps(line))
     f.close()
     sec.close()

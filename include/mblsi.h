@@ -165,7 +165,8 @@ int mbl_factor_solve(mbl_factorization *f, const double *b, double *x, int nrhs,
  * factorization made with solve_dataflow. */
 int mbl_factor_trace(mbl_factorization *f, int on);
 /* Copies the records of the latest solve: up to cap launches in sequence order into t0[], t1[] and
- * kind[] (0 forward gather, 1 forward panel step, 2 backward panel step); *count = number recorded
+ * kind[] (0 forward gather, 1 forward panel step, 2 backward level start, 3 backward update);
+ * *count = number recorded
  * (0 when tracing is off). */
 int mbl_factor_trace_get(mbl_factorization *f, unsigned long long *t0, unsigned long long *t1, int *kind,
                          int cap, int *count);
@@ -216,7 +217,9 @@ int mbl_observables_dev(mbl_ctx *ctx, int L, int nev, const double *d_evals,
  * Errors: MBL_ERR_INVALID for odd L, L outside 2..22, nev outside [1, dim], q <= 0 or q = 1. */
 int mbl_observables_extra(mbl_ctx *ctx, int L, int nev, const double *evecs, double q, double *kl,
                           double *sqp, double *fluct, double *dynf);
-/* Same on device arrays, enqueued on `stream` (NULL = context stream); returns when complete. */
+/* Same on device arrays, enqueued on `stream` (NULL = context stream) without synchronizing: the
+ * outputs are complete when the stream reaches this point.  Scratch comes from the context's
+ * per-L cache, so calls on one context must not overlap. */
 int mbl_observables_extra_dev(mbl_ctx *ctx, int L, int nev, const double *d_evecs, double q,
                               double *d_kl, double *d_sqp, double *d_fluct, double *d_dynf,
                               void *stream);

@@ -181,7 +181,8 @@ class Factorization:
         _check(_lib().mbl_factor_trace(self.handle, 1 if on else 0), self.sec.ctx.handle)
 
     def trace(self):
-        """(t0_ns, t1_ns, kind) arrays of the latest traced solve; kind 0 gather, 1 forward, 2 backward."""
+        """(t0_ns, t1_ns, kind) arrays of the latest traced solve; kind 0 gather, 1 forward step,
+        2 backward level start, 3 backward update."""
         cnt = ctypes.c_int()
         _check(_lib().mbl_factor_trace_get(self.handle, None, None, None, 0, ctypes.byref(cnt)), self.sec.ctx.handle)
         n = cnt.value

@@ -505,9 +505,12 @@ int mbl_factor_trace(mbl_factorization *fh, int on) {
     if (!fh) return report(nullptr, MBL_ERR_INVALID, "NULL argument");
     Factorization &f = *fh->f;
     if (f.dataflow && on) return report(f.ctx, MBL_ERR_INVALID, "the launch trace covers the level-by-level solve");
+    API_TRY
+    if (on && f.trace.size() == 0)
+        f.trace.alloc(f.ctx, 2 * (size_t)f.plan->nlevels + f.plan->ssteps.size() + f.plan->bupd.size());
     f.trace_on = on != 0;
     f.graph_p = 0;  // recapture the solve sequence with or without the trace records
-    return MBL_OK;
+    API_CATCH(f.ctx)
 }
 
 int mbl_factor_trace_get(mbl_factorization *fh, unsigned long long *t0, unsigned long long *t1, int *kind, int cap,
@@ -684,6 +687,7 @@ int mbl_observables_extra(mbl_ctx *ctx, int L, int nev, const double *evecs, dou
     dd.alloc(ctx, nev);
     MBL_CUDA(cudaMemcpy(dv.data(), evecs, (size_t)n * nev * sizeof(double), cudaMemcpyHostToDevice));
     observables_extra_dev(ctx, L, nev, dv.data(), q, dk.data(), dq.data(), df.data(), dd.data(), ctx->stream);
+    MBL_CUDA(cudaStreamSynchronize(ctx->stream));
     if (nev > 1) MBL_CUDA(cudaMemcpy(kl, dk.data(), (nev - 1) * sizeof(double), cudaMemcpyDeviceToHost));
     MBL_CUDA(cudaMemcpy(sqp, dq.data(), nev * sizeof(double), cudaMemcpyDeviceToHost));
     MBL_CUDA(cudaMemcpy(fluct, df.data(), nev * sizeof(double), cudaMemcpyDeviceToHost));

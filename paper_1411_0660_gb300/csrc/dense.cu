@@ -69,12 +69,14 @@ __global__ void k_tn_partial(int64_t n, const TV *__restrict__ V, int ldv, int c
     }
 }
 
+// C[o] = sum_c work[c * kp + o]: one warp per output, lanes over the chunks, a fixed summation order.
 __global__ void k_tn_reduce(int nch, int kp, const double *__restrict__ work, double *__restrict__ C) {
-    int o = blockIdx.x * blockDim.x + threadIdx.x;
+    const int o = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
     if (o >= kp) return;
     double s = 0.0;
-    for (int c = 0; c < nch; ++c) s += work[(size_t)c * kp + o];
-    C[o] = s;
+    for (int c = lane; c < nch; c += 32) s += work[(size_t)c * kp + o];
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if (lane == 0) C[o] = s;
 }
 
 template <class TV>
@@ -95,7 +97,7 @@ static void dense_tn_t(int64_t n, const TV *V, int ldv, int c0, int k, const dou
     }
     k_tn_partial<TV><<<nch, threads, smem, st>>>(n, V, ldv, c0, k, X, ldx, x0, p, work, rows_per);
     MBL_LAUNCH_CHECK();
-    k_tn_reduce<<<(k * p + 255) / 256, 256, 0, st>>>(nch, k * p, work, C);
+    k_tn_reduce<<<(unsigned)((k * p + 7) / 8), 256, 0, st>>>(nch, k * p, work, C);
     MBL_LAUNCH_CHECK();
 }
 
@@ -109,10 +111,11 @@ void dense_tn32(int64_t n, const float *V, int ldv, int c0, int k, const double 
     dense_tn_t(n, V, ldv, c0, k, X, ldx, x0, p, C, work, st);
 }
 
-// X -= V C (V row-major n x k at column c0, C k x p row-major); the sum in V's type.
+// Xout = Xin - V C (V row-major n x k at column c0, C k x p row-major; Xin may be Xout); the sum in
+// V's type.
 template <class TV>
 __global__ void k_nn_sub(int64_t n, const TV *__restrict__ V, int ldv, int c0, int k,
-                         const double *__restrict__ C, int p, double *__restrict__ X) {
+                         const double *__restrict__ C, int p, const double *Xin, double *Xout) {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int64_t i = t / p;
     int q = (int)(t - i * p);
@@ -120,22 +123,22 @@ __global__ void k_nn_sub(int64_t n, const TV *__restrict__ V, int ldv, int c0, i
     const TV *v = V + i * ldv + c0;
     TV s = TV(0);
     for (int a = 0; a < k; ++a) s = fma(v[a], (TV)C[a * p + q], s);
-    X[i * p + q] -= (double)s;
+    Xout[i * p + q] = Xin[i * p + q] - (double)s;
 }
 
 void dense_nn_sub(int64_t n, const double *V, int ldv, int c0, int k, const double *C, int p, double *X,
                   cudaStream_t st) {
     if (k <= 0) return;
     int64_t tot = n * p;
-    k_nn_sub<double><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(n, V, ldv, c0, k, C, p, X);
+    k_nn_sub<double><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(n, V, ldv, c0, k, C, p, X, X);
     MBL_LAUNCH_CHECK();
 }
 
-void dense_nn_sub32(int64_t n, const float *V, int ldv, int c0, int k, const double *C, int p, double *X,
-                    cudaStream_t st) {
+void dense_nn_sub32(int64_t n, const float *V, int ldv, int c0, int k, const double *C, int p, const double *Xin,
+                    double *Xout, cudaStream_t st) {
     if (k <= 0) return;
     int64_t tot = n * p;
-    k_nn_sub<float><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(n, V, ldv, c0, k, C, p, X);
+    k_nn_sub<float><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(n, V, ldv, c0, k, C, p, Xin, Xout);
     MBL_LAUNCH_CHECK();
 }
 

@@ -119,16 +119,17 @@ __global__ void __launch_bounds__(256) k_panel_diag(const PanelDesc *descs, cons
                                                     double tiny, unsigned long long *counters,
                                                     const unsigned int *cmax) {
     __shared__ T B[NB][NB + 1];
+    __shared__ T lcol[NB];
     __shared__ int perm[NB];
     __shared__ float cm[NB];
-    __shared__ int s_j;
-    __shared__ T s_d;
-    __shared__ float s_best[8], s_bd[8];
-    __shared__ int s_bj[8];
+    __shared__ float s_sc[2], s_dd[2];
+    __shared__ int s_jj[2];
+    __shared__ unsigned int s_npert, s_nneg;
+    static_assert(NB == 64, "the pivot search runs on two warps, one thread per candidate");
     const PanelDesc d = descs[blockIdx.x];
     const int s = d.front, f = fsz[s], k0 = d.k0, w = d.w;
     T *F = arena + fo[s];
-    const int tid = threadIdx.x, bd = blockDim.x;
+    const int tid = threadIdx.x, bd = blockDim.x, lane = tid & 31, wp = tid >> 5;
     for (int idx = tid; idx < w * w; idx += bd) {
         int r = idx % w, c = idx / w;
         B[r][c] = (r >= c) ? F[(int64_t)(k0 + c) * f + k0 + r] : T(0);
@@ -137,51 +138,47 @@ __global__ void __launch_bounds__(256) k_panel_diag(const PanelDesc *descs, cons
         perm[tid] = tid;
         cm[tid] = __uint_as_float(cmax[(size_t)blockIdx.x * NB + tid]);
     }
+    if (tid == 0) s_npert = s_nneg = 0u;
     __syncthreads();
     for (int t = 0; t < w; ++t) {
         // pivot: the candidate whose diagonal is largest relative to the rest of its column (inside the
-        // block and, from before this panel, in the rows below), which bounds the multipliers.  Warp
-        // wp scores candidates t + wp, t + wp + 8, ...; its lanes share each column's maximum.  Order:
-        // largest score, then largest |d|, then the smallest index.
-        {
-            const int lane = tid & 31, wp = tid >> 5;
-            float best = -1.f, bdg = -1.f;
-            int bj = w;
-            for (int j = t + wp; j < w; j += 8) {
-                float om = 0.f;
-                for (int i = t + lane; i < w; i += 32) {
-                    if (i == j) continue;
-                    om = fmaxf(om, (float)tabs(i > j ? B[i][j] : B[j][i]));
+        // block and, from before this panel, in the rows below), which bounds the multipliers.  Thread
+        // j of the first two warps scores candidate j; order: largest score, then largest |d|, then the
+        // smallest index.
+        if (wp < 2) {
+            float sc = -1.f, dj = -1.f;
+            int jj = w;
+            const int j = tid;
+            if (j >= t && j < w) {
+                float om = cm[perm[j]];
+                for (int i = t; i < j; ++i) om = fmaxf(om, (float)tabs(B[j][i]));
+                for (int i = j + 1; i < w; ++i) om = fmaxf(om, (float)tabs(B[i][j]));
+                dj = (float)tabs(B[j][j]);
+                sc = om > 0.f ? dj / om : 3.0e38f;
+                jj = j;
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                const float osc = __shfl_xor_sync(0xffffffffu, sc, o), odj = __shfl_xor_sync(0xffffffffu, dj, o);
+                const int ojj = __shfl_xor_sync(0xffffffffu, jj, o);
+                if (ojj < w && (osc > sc || (osc == sc && (odj > dj || (odj == dj && ojj < jj))))) {
+                    sc = osc;
+                    dj = odj;
+                    jj = ojj;
                 }
-                for (int o = 16; o > 0; o >>= 1) om = fmaxf(om, __shfl_xor_sync(0xffffffffu, om, o));
-                om = fmaxf(om, cm[perm[j]]);
-                const float dj = (float)tabs(B[j][j]);
-                const float sc = om > 0.f ? dj / om : 3.0e38f;
-                if (sc > best || (sc == best && dj > bdg)) { best = sc; bdg = dj; bj = j; }
             }
             if (lane == 0) {
-                s_best[wp] = best;
-                s_bd[wp] = bdg;
-                s_bj[wp] = bj;
-            }
-            __syncthreads();
-            if (tid == 0) {
-                float b0 = s_best[0], d0 = s_bd[0];
-                int j0 = s_bj[0];
-                for (int u = 1; u < 8; ++u) {
-                    const float ob = s_best[u], od = s_bd[u];
-                    const int oj = s_bj[u];
-                    if (oj < w && (ob > b0 || (ob == b0 && (od > d0 || (od == d0 && oj < j0))))) {
-                        b0 = ob;
-                        d0 = od;
-                        j0 = oj;
-                    }
-                }
-                s_j = j0 < w ? j0 : t;
+                s_sc[wp] = sc;
+                s_dd[wp] = dj;
+                s_jj[wp] = jj;
             }
         }
         __syncthreads();
-        const int j = s_j;
+        int j = s_jj[0];
+        {
+            const int oj = s_jj[1];
+            if (oj < w && (j >= w || s_sc[1] > s_sc[0] || (s_sc[1] == s_sc[0] && s_dd[1] > s_dd[0]))) j = oj;
+            if (j >= w) j = t;
+        }
         if (j != t) {
             for (int c = tid; c < t; c += bd) { T x = B[t][c]; B[t][c] = B[j][c]; B[j][c] = x; }
             for (int c = t + 1 + tid; c < j; c += bd) { T x = B[c][t]; B[c][t] = B[j][c]; B[j][c] = x; }
@@ -192,26 +189,32 @@ __global__ void __launch_bounds__(256) k_panel_diag(const PanelDesc *descs, cons
             }
         }
         __syncthreads();
+        // the pivot (a tiny one replaced by +-tiny, statically), then the column: lcol keeps the
+        // unscaled entries, the column itself becomes L's
+        T dv = B[t][t];
+        const bool pert = !(tabs(dv) >= (T)tiny);
+        if (pert) dv = (dv >= T(0)) ? (T)tiny : (T)(-tiny);
         if (tid == 0) {
-            T dv = B[t][t];
-            if (!(tabs(dv) >= (T)tiny)) {
-                dv = (dv >= T(0)) ? (T)tiny : (T)(-tiny);
-                atomicAdd(&counters[0], 1ull);
-            }
-            if (dv < T(0)) atomicAdd(&counters[1], 1ull);
-            B[t][t] = dv;
-            s_d = dv;
+            s_npert += pert ? 1u : 0u;
+            s_nneg += dv < T(0) ? 1u : 0u;
+        }
+        for (int r = t + 1 + tid; r < w; r += bd) {
+            const T u = B[r][t];
+            lcol[r] = u;
+            B[r][t] = u / dv;
         }
         __syncthreads();
-        const T dv = s_d;
+        if (tid == 0) B[t][t] = dv;
         const int m = w - t - 1;
         for (int idx = tid; idx < m * m; idx += bd) {
             int r = t + 1 + idx % m, c = t + 1 + idx / m;
-            if (r >= c) B[r][c] -= B[r][t] * (B[c][t] / dv);
+            if (r >= c) B[r][c] -= lcol[r] * B[c][t];
         }
         __syncthreads();
-        for (int r = t + 1 + tid; r < w; r += bd) B[r][t] /= dv;
-        __syncthreads();
+    }
+    if (tid == 0) {
+        if (s_npert) atomicAdd(&counters[0], (unsigned long long)s_npert);
+        if (s_nneg) atomicAdd(&counters[1], (unsigned long long)s_nneg);
     }
     // write L11 (strictly lower), D on the diagonal, pivots
     for (int idx = tid; idx < w * w; idx += bd) {
@@ -374,24 +377,6 @@ __global__ void k_perm_out(int64_t n, int p, const int32_t *perm, const T *x, do
     *dst = accumulate ? *dst + v : v;
 }
 
-__device__ __forceinline__ int find_sdesc(const SolveDesc *d, int nd, int64_t b) {
-    int lo = 0, hi = nd - 1;
-    while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (d[mid].off <= b) lo = mid; else hi = mid - 1;
-    }
-    return lo;
-}
-
-__device__ __forceinline__ int find_sdesc_k(const SolveDesc *d, int nd, int64_t b) {
-    int lo = 0, hi = nd - 1;
-    while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (d[mid].offk <= b) lo = mid; else hi = mid - 1;
-    }
-    return lo;
-}
-
 __device__ __forceinline__ int find_sdesc_b(const SolveDesc *d, int nd, int64_t b) {
     int lo = 0, hi = nd - 1;
     while (lo < hi) {
@@ -541,7 +526,7 @@ __global__ void __launch_bounds__(256) k_apply_m(const SolveDesc *sdescs, int nd
 // memory.  The CTA's rows of G are streamed into registers before waiting for the previous step
 // (FP32: both halves; FP64: the first).
 template <class T, int PB>
-__global__ void __launch_bounds__(256) k_fwd_step(const SolveDesc *sdescs, int nd, const int64_t *zo,
+__global__ void __launch_bounds__(256) k_fwd_step(const SolveDesc *sdescs, const int32_t *blk_desc, const int64_t *zo,
                                                   const int32_t *sn_start, const T *Gp, const T *Dg, T *Z, T *Zs,
                                                   T *yfw, int p, LaunchTrace *tr) {
     TraceScope trace_scope(tr);
@@ -549,7 +534,7 @@ __global__ void __launch_bounds__(256) k_fwd_step(const SolveDesc *sdescs, int n
     extern __shared__ __align__(16) unsigned char smraw[];
     T *zp = reinterpret_cast<T *>(smraw);  // SPW x PB; afterwards the 8 x PB x RBF partials
     pdl_trigger();
-    const int di = find_sdesc(sdescs, nd, blockIdx.x);
+    const int di = blk_desc[blockIdx.x];
     const SolveDesc d = sdescs[di];
     const int s = d.front, k0 = d.k0, w = d.w;
     const int r0 = (int)(blockIdx.x - d.off) * RBF;  // relative to k0
@@ -566,10 +551,26 @@ __global__ void __launch_bounds__(256) k_fwd_step(const SolveDesc *sdescs, int n
             for (int c = 0; c < 32; ++c) lv[h][c] = g[(int64_t)(c0 + c) * ld];
         }
     }
+    // this thread's outputs o = threadIdx.x + 256 u (row i = o % RBF, right-hand side q = o / RBF):
+    // the pivots of panel rows are static (read before waiting); the rows below are read together
+    // with the panel's z, so that only one round trip follows the wait
+    constexpr int NO = RBF * PB / 256;
+    static_assert(NO * 256 == RBF * PB, "outputs per thread");
+    T dg[NO], zold[NO];
+#pragma unroll
+    for (int u = 0; u < NO; ++u) {
+        const int o = threadIdx.x + 256 * u, i = o % RBF, q = o / RBF, rr = r0 + i;
+        dg[u] = (i < nr && q < p && rr < w) ? Dg[(int64_t)sn_start[s] + k0 + rr] : T(1);
+    }
     pdl_wait();
     for (int idx = threadIdx.x; idx < w * PB; idx += blockDim.x) {
         int c = idx / PB, q = idx % PB;
         zp[idx] = q < p ? Z[(zb + c) * p + q] : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < NO; ++u) {
+        const int o = threadIdx.x + 256 * u, i = o % RBF, q = o / RBF, rr = r0 + i;
+        zold[u] = (i < nr && q < p && rr >= w) ? Z[(zb + rr) * p + q] : T(0);
     }
     __syncthreads();
     T acc[PB];
@@ -597,8 +598,9 @@ __global__ void __launch_bounds__(256) k_fwd_step(const SolveDesc *sdescs, int n
 #pragma unroll
     for (int q = 0; q < PB; ++q) red[(wp * PB + q) * RBF + lane] = acc[q];
     __syncthreads();
-    for (int o = threadIdx.x; o < RBF * PB; o += blockDim.x) {
-        const int i = o % RBF, q = o / RBF;
+#pragma unroll
+    for (int u = 0; u < NO; ++u) {
+        const int o = threadIdx.x + 256 * u, i = o % RBF, q = o / RBF;
         if (i >= nr || q >= p) continue;
         T v = T(0);
 #pragma unroll
@@ -608,9 +610,198 @@ __global__ void __launch_bounds__(256) k_fwd_step(const SolveDesc *sdescs, int n
             // a panel row is final here: also its diagonal-scaled value for the backward sweep
             const int64_t gr = (int64_t)sn_start[s] + k0 + rr;
             Zs[(zb + rr) * p + q] = v;
-            yfw[gr * p + q] = v / Dg[gr];
+            yfw[gr * p + q] = v / dg[u];
         } else {
-            Z[(zb + rr) * p + q] -= v;
+            Z[(zb + rr) * p + q] = zold[u] - v;
+        }
+    }
+}
+
+// Narrow steps (every panel of the step at most 32 columns wide, e.g. the leaves of the tree): one
+// warp per 32-row block (RBF) instead of CTAs of RBF rows x 8 column chunks, most of which would idle.
+// Forward: lane c holds z_panel row c; lane r accumulates row r of the block's G z, the z values
+// broadcast by shuffles.  The block's rows of G and the panel's pivots are read before the wait on
+// the previous step.
+template <class T, int PB>
+__global__ void __launch_bounds__(256) k_fwd_narrow(const SolveDesc *sdescs, const int32_t *blk_desc, int nblk,
+                                                    const int64_t *zo, const int32_t *sn_start, const T *Gp,
+                                                    const T *Dg, T *Z, T *Zs, T *yfw, int p, LaunchTrace *tr) {
+    static_assert(RBF == 32, "one warp per row block");
+    TraceScope trace_scope(tr);
+    pdl_trigger();
+    const int lane = threadIdx.x & 31, item = blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (item >= nblk) {
+        pdl_wait();
+        return;
+    }
+    const SolveDesc d = sdescs[blk_desc[item]];
+    const int s = d.front, k0 = d.k0, w = d.w, R = w + d.m2;
+    const int r = (int)(item - d.off) * RBF + lane;  // this lane's row, relative to k0
+    const int64_t zb = zo[s] + k0, ld = sg_ld(R), g0 = (int64_t)sn_start[s] + k0;
+    const T *G = Gp + d.goff + r;
+    T gl[32];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) gl[c] = (c < w && r < R) ? G[(int64_t)c * ld] : T(0);
+    const T dg = r < w ? Dg[g0 + r] : T(1);
+    pdl_wait();
+    T zr[PB], zold[PB];
+#pragma unroll
+    for (int q = 0; q < PB; ++q) {
+        zr[q] = (lane < w && q < p) ? Z[(zb + lane) * p + q] : T(0);
+        zold[q] = (r >= w && r < R && q < p) ? Z[(zb + r) * p + q] : T(0);
+    }
+    T acc[PB];
+#pragma unroll
+    for (int q = 0; q < PB; ++q) acc[q] = T(0);
+#pragma unroll
+    for (int c = 0; c < 32; ++c) {
+        if (c >= w) break;
+#pragma unroll
+        for (int q = 0; q < PB; ++q) acc[q] += gl[c] * __shfl_sync(0xffffffffu, zr[q], c);
+    }
+    if (r < R) {
+#pragma unroll
+        for (int q = 0; q < PB; ++q) {
+            if (q >= p) break;
+            if (r < w) {
+                Zs[(zb + r) * p + q] = acc[q];
+                yfw[(g0 + r) * p + q] = acc[q] / dg;
+            } else {
+                Z[(zb + r) * p + q] = zold[q] - acc[q];
+            }
+        }
+    }
+}
+
+// Backward narrow step: lane c accumulates x_panel[c] = sum_r G[r][c] v[r] over 32-row chunks;
+// lane j of a chunk reads row j of v (yfw, Zs or the ancestors' x, as in k_bwd_step) and the
+// values broadcast by shuffles.  Every panel is handled by one warp, so there are no partial sums.
+template <class T, int PB>
+__global__ void __launch_bounds__(256) k_bwd_narrow(const SolveDesc *sdescs, int nd, const int64_t *zo,
+                                                    const int32_t *nc, const int32_t *sn_start,
+                                                    const int64_t *rows_off, const int32_t *rows, const T *Gp,
+                                                    const T *yfw, T *Zs, T *x, int p, LaunchTrace *tr) {
+    TraceScope trace_scope(tr);
+    pdl_trigger();
+    const int lane = threadIdx.x & 31, di = blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (di >= nd) {
+        pdl_wait();
+        return;
+    }
+    const SolveDesc d = sdescs[di];
+    const int s = d.front, k0 = d.k0, w = d.w, R = w + d.m2, ncs = nc[s];
+    const int64_t zb = zo[s] + k0, ld = sg_ld(R), g0 = (int64_t)sn_start[s] + k0;
+    const T *G = Gp + d.goff + (int64_t)lane * ld;  // this lane's column
+    const int32_t *rw = rows + rows_off[s] + k0;
+    T gl[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) gl[j] = (lane < w && j < R) ? G[j] : T(0);
+    const int rowx = lane < R && k0 + lane >= ncs ? rw[lane] : 0;
+    pdl_wait();
+    T acc[PB];
+#pragma unroll
+    for (int q = 0; q < PB; ++q) acc[q] = T(0);
+    for (int rb = 0; rb < R; rb += 32) {
+        const int rr = rb + lane;
+        T vr[PB];
+        {
+            const T *sp = nullptr;
+            T sg = T(0);
+            if (rr < R) {
+                if (rr < w) {
+                    sp = yfw + (g0 + rr) * p;
+                    sg = T(1);
+                } else if (k0 + rr < ncs) {
+                    sp = Zs + (zb + rr) * p;
+                    sg = T(-1);
+                } else {
+                    sp = x + (int64_t)(rb == 0 ? rowx : rw[rr]) * p;
+                    sg = T(-1);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < PB; ++q) vr[q] = (sp && q < p) ? sg * sp[q] : T(0);
+        }
+        if (rb > 0) {  // this chunk's column entries, all loads in flight before the products
+#pragma unroll
+            for (int j = 0; j < 32; ++j) gl[j] = (lane < w && rb + j < R) ? G[rb + j] : T(0);
+        }
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+#pragma unroll
+            for (int q = 0; q < PB; ++q) acc[q] += gl[j] * __shfl_sync(0xffffffffu, vr[q], j);
+    }
+    if (lane < w) {
+#pragma unroll
+        for (int q = 0; q < PB; ++q) {
+            if (q >= p) break;
+            Zs[(zb + lane) * p + q] = acc[q];
+            x[(g0 + lane) * p + q] = acc[q];
+        }
+    }
+}
+
+// Backward update (grid: the launch's (i, j) items x column chunks of panel i): acc_i -= G_i[rows of
+// panel j]^T x_j for an earlier panel i of the same front, where x_j = acc_j (in Zs) is final.  The
+// RBK x RBB tile of G_i is copied before waiting.  When panel j directly follows panel i this is the
+// last contribution to acc_i, which is then written to x as well.  Each accumulator chunk has one
+// writer per launch, so the updates are deterministic.
+template <class T, int PB>
+__global__ void __launch_bounds__(256) k_bwd_update(const SolveDesc *sdescs, const int32_t *items, const int64_t *zo,
+                                                    const int32_t *sn_start, const T *Gp, T *Zs, T *x, int p,
+                                                    LaunchTrace *tr) {
+    TraceScope trace_scope(tr);
+    constexpr int E = 16 / sizeof(T);
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T *Gs = reinterpret_cast<T *>(smraw);    // RBB columns x bwd_ldg rows
+    T *vs = Gs + RBB * bwd_ldg<T>();         // RBK x PB
+    T *red = PB == 8 ? Gs : vs + RBK * PB;  // 8 warps x 8 x RBB partial sums
+    pdl_trigger();
+    const SolveDesc di = sdescs[items[2 * blockIdx.x]], dj = sdescs[items[2 * blockIdx.x + 1]];
+    const int cc = blockIdx.y * RBB;
+    if (cc >= di.w) {
+        pdl_wait();
+        return;
+    }
+    const int s = di.front, wc = min(RBB, di.w - cc), wj = dj.w, nrv = (wj + E - 1) / E;
+    const int64_t ldi = sg_ld(di.w + di.m2);
+    bwd_tile_issue(Gs, Gp + di.goff + (int64_t)cc * ldi + (dj.k0 - di.k0), ldi, wc, nrv);
+    const int64_t zi = zo[s] + di.k0 + cc, zj = zo[s] + dj.k0;
+    const bool fin = dj.k0 == di.k0 + di.w;
+    pdl_wait();
+    {
+        static_assert(RBK == 256, "one row of v per thread");
+        const int r = threadIdx.x;
+        T *vr = vs + r * PB;
+#pragma unroll
+        for (int q = 0; q < PB; ++q) vr[q] = (r < wj && q < p) ? Zs[(zj + r) * p + q] : T(0);
+    }
+    // the accumulator entries this thread updates: outputs o = threadIdx.x + 256 h of each 8-wide
+    // chunk of right-hand sides (column c = o % RBB, q = q0 + o / RBB)
+    constexpr int NQ = PB / 8;
+    T old[NQ][2];
+#pragma unroll
+    for (int u = 0; u < NQ; ++u)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int o = threadIdx.x + 256 * h, q = 8 * u + o / RBB, c = o % RBB;
+            old[u][h] = (c < wc && q < p) ? Zs[(zi + c) * p + q] : T(0);
+        }
+    cp_async_commit_wait();
+    __syncthreads();
+    T *xp = x + ((int64_t)sn_start[s] + di.k0 + cc) * p;
+#pragma unroll
+    for (int u = 0; u < NQ; ++u) {
+        T o2[2];
+        bwd_tile_product<T, PB>(Gs, vs, red, nrv * E, 8 * u, o2);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int o = threadIdx.x + 256 * h, q = 8 * u + o / RBB, c = o % RBB;
+            if (c < wc && q < p) {
+                const T v = old[u][h] - o2[h];
+                Zs[(zi + c) * p + q] = v;
+                if (fin) xp[c * p + q] = v;
+            }
         }
     }
 }
@@ -647,17 +838,18 @@ __global__ void k_fwd_gather_rows(int64_t nrows, const int64_t *dst, const int64
     Z[d * p + q] = v;
 }
 
-// Backward solve step, tiles of RBK rows x RBB columns of G = [M; L21 M] (grid: row blocks x
-// column chunks): x_panel = G^T v with v = [y_panel; -x_below].  The tile is copied from the packed
-// solve factor to shared memory (16-byte cp.async) before waiting for the previous step (G does
-// not change during a solve).  A panel with one row block writes x directly; otherwise each block
-// writes its partial sums and the last block of a (panel, column chunk) to finish (counted with an
-// atomic, after a fence) adds the partials in a fixed order, writes the panel's x into Zs and x,
-// and re-arms the counter.  v is read in place: the panel's rows from the forward result yfw
-// (pivoted order), rows of later panels from Zs, and the rows of the contribution block -- the
-// ancestors' x, final by now -- from x through the front's row list (static, read before waiting).
+// Start of the backward sweep of one level (grid: the level's row blocks x column chunks), tiles
+// of RBK rows x RBB columns of G = [M; L21 M]: each panel's accumulator acc = G^T v with
+// v = [y_panel; 0; -x_cb] -- the panel's forward result yfw (pivoted order), zero on the rows of the
+// front's later panels (their share is subtracted by k_bwd_update once their x is known), and the
+// contribution block's x, fixed by the ancestors and read through the front's row list (static,
+// read before waiting).  The tile is copied from the packed solve factor to shared memory (16-byte
+// cp.async) before waiting for the previous launch.  A panel with one row block writes directly;
+// otherwise each block writes its partial sums and the last block of a (panel, column chunk) to
+// finish (counted with an atomic, after a fence) adds the partials in a fixed order and re-arms the
+// counter.  The accumulator goes to Zs; for the front's last panel it is final and goes to x too.
 template <class T, int PB>
-__global__ void __launch_bounds__(256) k_bwd_step(const SolveDesc *sdescs, int nd, const int64_t *zo,
+__global__ void __launch_bounds__(256) k_bwd_step(const SolveDesc *sdescs, const int32_t *blk_desc, const int64_t *zo,
                                                   const int32_t *nc, const int32_t *sn_start,
                                                   const int64_t *rows_off, const int32_t *rows, const T *Gp,
                                                   const T *yfw, T *Zs, T *P, unsigned int *cnt, T *x, int p,
@@ -670,7 +862,7 @@ __global__ void __launch_bounds__(256) k_bwd_step(const SolveDesc *sdescs, int n
     T *red = PB == 8 ? Gs : vs + RBK * PB;  // 8 warps x 8 x RBB partial sums
     __shared__ int s_last;
     pdl_trigger();
-    const int di = find_sdesc_k(sdescs, nd, blockIdx.x);
+    const int di = blk_desc[blockIdx.x];
     const SolveDesc d = sdescs[di];
     const int cc = blockIdx.y * RBB;
     if (cc >= d.w) {
@@ -678,18 +870,17 @@ __global__ void __launch_bounds__(256) k_bwd_step(const SolveDesc *sdescs, int n
         return;
     }
     const int s = d.front, k0 = d.k0, w = d.w, ncs = nc[s], R = w + d.m2;
-    const int b = (int)(blockIdx.x - d.offk), nb = (R + RBK - 1) / RBK;
+    const int b = (int)(blockIdx.x - d.offk_l), nb = (R + RBK - 1) / RBK;
     const int r0 = b * RBK;  // relative to k0
     const int nr = min(RBK, R - r0), nrv = (nr + E - 1) / E;
     const int wc = min(RBB, w - cc);
     const int64_t zb = zo[s] + k0, ld = sg_ld(R);
     bwd_tile_issue(Gs, Gp + d.goff + (int64_t)cc * ld + r0, ld, wc, nrv);
-    // thread i loads row i of v
+    // thread i loads row i of v: the panel's y, zero on later panels' rows, -x on the contribution block
     static_assert(RBK == 256, "one row of v per thread");
     const int i = threadIdx.x, rr = r0 + i;
-    const int kind = i >= nr ? 0 : (rr < w ? 1 : (k0 + rr < ncs ? 2 : 3));
+    const int kind = i >= nr ? 0 : (rr < w ? 1 : (k0 + rr < ncs ? 0 : 3));
     const int64_t src = kind == 1 ? ((int64_t)sn_start[s] + k0 + rr) * p
-                      : kind == 2 ? (zb + rr) * p
                       : kind == 3 ? (int64_t)rows[rows_off[s] + k0 + rr] * p : 0;
     pdl_wait();
     {
@@ -698,7 +889,7 @@ __global__ void __launch_bounds__(256) k_bwd_step(const SolveDesc *sdescs, int n
 #pragma unroll
             for (int q = 0; q < PB; ++q) vr[q] = T(0);
         } else {
-            const T *sp = kind == 1 ? yfw + src : (kind == 2 ? Zs + src : x + src);
+            const T *sp = kind == 1 ? yfw + src : x + src;
             const T sg = kind == 1 ? T(1) : T(-1);
 #pragma unroll
             for (int q = 0; q < PB; ++q) vr[q] = q < p ? sg * sp[q] : T(0);
@@ -707,8 +898,9 @@ __global__ void __launch_bounds__(256) k_bwd_step(const SolveDesc *sdescs, int n
     cp_async_commit_wait();
     __syncthreads();
     const int64_t tile = (int64_t)RBB * PB;
-    T *out = P + ((d.offk + b) * SUBS + blockIdx.y) * tile;
-    T *zsp = Zs + (zb + cc) * p, *xp = x + ((int64_t)sn_start[s] + k0 + cc) * p;
+    T *out = P + ((d.offk_l + b) * SUBS + blockIdx.y) * tile;
+    T *zsp = Zs + (zb + cc) * p;
+    T *xp = k0 + w >= ncs ? x + ((int64_t)sn_start[s] + k0 + cc) * p : nullptr;
 #pragma unroll
     for (int q0 = 0; q0 < PB; q0 += 8) {
         T o2[2];
@@ -719,7 +911,7 @@ __global__ void __launch_bounds__(256) k_bwd_step(const SolveDesc *sdescs, int n
             if (nb == 1) {
                 if (c < wc && q < p) {
                     zsp[c * p + q] = o2[h];
-                    xp[c * p + q] = o2[h];
+                    if (xp) xp[c * p + q] = o2[h];
                 }
             } else {
                 out[q * RBB + c] = o2[h];
@@ -736,7 +928,7 @@ __global__ void __launch_bounds__(256) k_bwd_step(const SolveDesc *sdescs, int n
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    bwd_finish<T, PB>(P + (d.offk * SUBS + blockIdx.y) * tile, (int64_t)SUBS * tile, nb, wc, p, zsp, xp, Gs);
+    bwd_finish<T, PB>(P + (d.offk_l * SUBS + blockIdx.y) * tile, (int64_t)SUBS * tile, nb, wc, p, zsp, xp, Gs);
     if (threadIdx.x == 0) cnt[(size_t)di * SUBS + blockIdx.y] = 0u;
 }
 
@@ -760,6 +952,8 @@ static void set_step_attrs() {
     MBL_CUDA(cudaFuncSetAttribute(k_fwd_step<T, PB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)fwd_step_smem<T, PB>()));
     MBL_CUDA(cudaFuncSetAttribute(k_bwd_step<T, PB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)bwd_step_smem<T, PB>()));
+    MBL_CUDA(cudaFuncSetAttribute(k_bwd_update<T, PB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)bwd_step_smem<T, PB>()));
 }
 
@@ -792,31 +986,37 @@ static void factor_impl(Factorization &fz, cudaStream_t st) {
     MBL_CUDA(cudaMemsetAsync(fz.counters.data() + 4, 0x7f, sizeof(unsigned int), st));  // min |d| starts huge
     for (int l = 0; l < p.nlevels; ++l) {
         int na = p.asm_ptr[l + 1] - p.asm_ptr[l];
-        k_assemble<T><<<na, 256, 0, st>>>(p.d_asm_items.data() + p.asm_ptr[l], p.d_sn_fo.data(), p.d_sn_f.data(),
-                                          p.d_sn_nc.data(), p.d_sn_start.data(), p.d_ch_ptr.data(),
-                                          p.d_ch_list.data(), p.d_sn_rel_off.data(), p.d_relind.data(),
-                                          p.d_amap_ptr.data(), p.d_amap_src.data(), p.d_amap_row.data(),
-                                          sec->val.data(), fz.sigma, arena);
-        MBL_LAUNCH_CHECK();
+        {
+            ProfScope ps_asm(fz.ctx, "f_assemble", 0.0, st);
+            k_assemble<T><<<na, 256, 0, st>>>(p.d_asm_items.data() + p.asm_ptr[l], p.d_sn_fo.data(), p.d_sn_f.data(),
+                                              p.d_sn_nc.data(), p.d_sn_start.data(), p.d_ch_ptr.data(),
+                                              p.d_ch_list.data(), p.d_sn_rel_off.data(), p.d_relind.data(),
+                                              p.d_amap_ptr.data(), p.d_amap_src.data(), p.d_amap_row.data(),
+                                              sec->val.data(), fz.sigma, arena);
+            MBL_LAUNCH_CHECK();
+        }
         for (int si = p.lvl_step_ptr[l]; si < p.lvl_step_ptr[l + 1]; ++si) {
             const PanelStep &stp = p.steps[si];
             const PanelDesc *dd = p.d_descs.data() + stp.d0;
             unsigned int *cmax = static_cast<unsigned int *>(fz.cmax.m.p);
-            MBL_CUDA(cudaMemsetAsync(cmax, 0, (size_t)stp.nd * NB * sizeof(unsigned int), st));
-            if (stp.n2 > 0) {
-                k_panel_colmax<T><<<(unsigned)stp.n2, RB, 0, st>>>(dd, stp.nd, p.d_sn_fo.data(), p.d_sn_f.data(), arena,
-                                                                   cmax);
+            {  // pivot search, diagonal block and trsm of the panel
+                ProfScope ps_pan(fz.ctx, "f_panel", 0.0, st);
+                MBL_CUDA(cudaMemsetAsync(cmax, 0, (size_t)stp.nd * NB * sizeof(unsigned int), st));
+                if (stp.n2 > 0) {
+                    k_panel_colmax<T><<<(unsigned)stp.n2, RB, 0, st>>>(dd, stp.nd, p.d_sn_fo.data(), p.d_sn_f.data(), arena,
+                                                                       cmax);
+                    MBL_LAUNCH_CHECK();
+                }
+                k_panel_diag<T><<<stp.nd, 256, 0, st>>>(dd, p.d_sn_fo.data(), p.d_sn_f.data(), p.d_sn_start.data(), arena,
+                                                        Dg, fz.piv.data(), fz.tiny, fz.counters.data(), cmax);
                 MBL_LAUNCH_CHECK();
-            }
-            k_panel_diag<T><<<stp.nd, 256, 0, st>>>(dd, p.d_sn_fo.data(), p.d_sn_f.data(), p.d_sn_start.data(), arena,
-                                                    Dg, fz.piv.data(), fz.tiny, fz.counters.data(), cmax);
-            MBL_LAUNCH_CHECK();
-            if (stp.n2 > 0) {
-                k_panel_trsm<T><<<(unsigned)stp.n2, RB, trsm_smem<T>(), st>>>(dd, stp.nd, p.d_sn_fo.data(),
-                                                                             p.d_sn_f.data(), p.d_sn_start.data(), arena,
-                                                                             Dg, fz.piv.data(), wscr,
-                                                                             fz.counters.data() + 3);
-                MBL_LAUNCH_CHECK();
+                if (stp.n2 > 0) {
+                    k_panel_trsm<T><<<(unsigned)stp.n2, RB, trsm_smem<T>(), st>>>(dd, stp.nd, p.d_sn_fo.data(),
+                                                                                 p.d_sn_f.data(), p.d_sn_start.data(), arena,
+                                                                                 Dg, fz.piv.data(), wscr,
+                                                                                 fz.counters.data() + 3);
+                    MBL_LAUNCH_CHECK();
+                }
             }
             if (stp.n3 > 0) {
                 double fl = 0.0;  // algorithmic flops: lower triangle of the trailing block, 2 per entry per k
@@ -837,6 +1037,7 @@ static void factor_impl(Factorization &fz, cudaStream_t st) {
     }
     // block operators of the solve panels, then G = [M; L21 M] of each panel into the packed solve factor
     if (!p.sdescs.empty()) {
+        ProfScope ps_g(fz.ctx, "f_build_g", 0.0, st);
         dim3 grid((unsigned)p.sdescs.size(), SPW / 32);
         k_build_m<T><<<grid, 256, build_m_smem<T>(), st>>>(p.d_sdescs.data(), p.d_sn_fo.data(), p.d_sn_f.data(),
                                                            p.d_sn_start.data(), arena, fz.piv.data(),
@@ -872,10 +1073,9 @@ static void solve_levels(Factorization &fz, int p, cudaStream_t st) {
     unsigned int *cnt = fz.scnt.data();
     const size_t fsm = fwd_step_smem<T, PB>(), bsm = bwd_step_smem<T, PB>();
     // launch trace: one record per launch below, reset at the start of every solve
-    const int ntr = pl.nlevels + 2 * (int)pl.ssteps.size();
+    const int ntr = 2 * pl.nlevels + (int)pl.ssteps.size() + (int)pl.bupd.size();
     LaunchTrace *trb = nullptr;
-    if (fz.trace_on) {
-        if (fz.trace.size() < (size_t)ntr) fz.trace.alloc(fz.ctx, ntr);
+    if (fz.trace_on && fz.trace.size() >= (size_t)ntr) {  // allocated when tracing is switched on
         trb = fz.trace.data();
         k_trace_reset<<<(ntr + 255) / 256, 256, 0, st>>>(trb, ntr);
         MBL_LAUNCH_CHECK();
@@ -897,17 +1097,35 @@ static void solve_levels(Factorization &fz, int p, cudaStream_t st) {
         for (int si = pl.lvl_sstep_ptr[l]; si < pl.lvl_sstep_ptr[l + 1]; ++si) {
             const SolveStep &ss = pl.ssteps[si];
             const SolveDesc *sd = pl.d_sdescs.data() + ss.d0;
-            launch_pdl(k_fwd_step<T, PB>, dim3((unsigned)ss.nrb), dim3(256), fsm, st, sd, ss.nd,
+            if (ss.maxw <= 32) {
+                launch_pdl(k_fwd_narrow<T, PB>, dim3((unsigned)((ss.nrb + 7) / 8)), dim3(256), 0, st, sd,
+                           (const int32_t *)pl.d_fblk_desc.data() + ss.fblk0, (int)ss.nrb, pl.d_sn_zo.data(),
+                           pl.d_sn_start.data(), Gp, (const T *)Dg, Z, Zs, yfw, p, next_tr(1));
+                continue;
+            }
+            launch_pdl(k_fwd_step<T, PB>, dim3((unsigned)ss.nrb), dim3(256), fsm, st, sd,
+                       (const int32_t *)pl.d_fblk_desc.data() + ss.fblk0,
                        pl.d_sn_zo.data(), pl.d_sn_start.data(), Gp, (const T *)Dg, Z, Zs, yfw, p, next_tr(1));
         }
     }
     for (int l = pl.nlevels - 1; l >= 0; --l) {
-        for (int si = pl.lvl_sstep_ptr[l + 1] - 1; si >= pl.lvl_sstep_ptr[l]; --si) {
-            const SolveStep &ss = pl.ssteps[si];
-            const SolveDesc *sd = pl.d_sdescs.data() + ss.d0;
-            launch_pdl(k_bwd_step<T, PB>, dim3((unsigned)ss.nrbk, SUBS), dim3(256), bsm, st, sd, ss.nd,
+        const SolveDesc *sdl = pl.d_sdescs.data() + pl.lvl_d0[l];
+        if (pl.lvl_maxw[l] <= 32 && pl.lvl_maxr[l] <= 512) {  // single narrow, short panels: a warp each
+            launch_pdl(k_bwd_narrow<T, PB>, dim3((unsigned)((pl.lvl_nd[l] + 7) / 8)), dim3(256), 0, st, sdl,
+                       pl.lvl_nd[l], pl.d_sn_zo.data(), pl.d_sn_nc.data(), pl.d_sn_start.data(),
+                       pl.d_sn_rows_off.data(), pl.d_rows.data(), Gp, (const T *)yfw, Zs, y, p, next_tr(2));
+        } else {
+            launch_pdl(k_bwd_step<T, PB>, dim3((unsigned)pl.lvl_nrbk[l], (pl.lvl_maxw[l] + RBB - 1) / RBB), dim3(256),
+                       bsm, st, sdl, (const int32_t *)pl.d_lvl_bblk_desc.data() + pl.lvl_bblk0[l],
                        pl.d_sn_zo.data(), pl.d_sn_nc.data(), pl.d_sn_start.data(), pl.d_sn_rows_off.data(),
-                       pl.d_rows.data(), Gp, (const T *)yfw, Zs, P, cnt + (size_t)ss.d0 * SUBS, y, p, next_tr(2));
+                       pl.d_rows.data(), Gp, (const T *)yfw, Zs, P, cnt + (size_t)pl.lvl_d0[l] * SUBS, y, p,
+                       next_tr(2));
+        }
+        for (int u = pl.bu_ptr[l]; u < pl.bu_ptr[l + 1]; ++u) {
+            const BwdUpd &bu = pl.bupd[u];
+            launch_pdl(k_bwd_update<T, PB>, dim3((unsigned)bu.nit, SUBS), dim3(256), bsm, st,
+                       (const SolveDesc *)pl.d_sdescs.data(), (const int32_t *)pl.d_bu_items.data() + 2 * bu.it0,
+                       pl.d_sn_zo.data(), pl.d_sn_start.data(), Gp, Zs, y, p, next_tr(3));
         }
     }
 }
@@ -983,7 +1201,7 @@ void Factorization::ensure_solve_work(int p) {
     zsolved.alloc(ctx, (size_t)pl.zwork_elems * p * es);
     ywork.alloc(ctx, (size_t)pl.n * p * es);
     yfw.alloc(ctx, (size_t)pl.n * p * es);
-    pwork.alloc(ctx, (size_t)std::max<int64_t>(std::max<int64_t>(pl.max_sstep_nrbk * SUBS, pl.df_pslots), 1) * RBB *
+    pwork.alloc(ctx, (size_t)std::max<int64_t>(std::max<int64_t>(pl.max_lvl_nrbk * SUBS, pl.df_pslots), 1) * RBB *
                          rhs_pad(p) * es);
     work_p = p;
 }

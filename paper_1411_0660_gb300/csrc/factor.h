@@ -30,7 +30,7 @@ struct Factorization {
     // launch trace of the level-by-level solve (opt-in; recaptures the solve graph when switched)
     bool trace_on = false;
     DVec<LaunchTrace> trace;
-    std::vector<int> trace_kind;  // per traced launch: 0 forward gather, 1 forward step, 2 backward step
+    std::vector<int> trace_kind;  // per traced launch: 0 forward gather, 1 forward step, 2/3 backward start/update
     int64_t perturbed = 0, negative = 0;
     double ms_factor = 0.0;
 

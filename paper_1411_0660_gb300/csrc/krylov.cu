@@ -240,13 +240,18 @@ __global__ void k_refine_resid(int64_t n, const int64_t *__restrict__ rowptr, co
     }
 }
 
+// out[u] = sum_b part[b * w + u], u < w: one warp per output, lanes over the partial blocks (all
+// loads in flight at once), summed in a fixed order (lane-strided, then a shuffle tree).  Launch
+// with reduce_grid(w) blocks of 256 threads.
 __global__ void k_reduce_parts(int nb, int w, const double *part, double *out) {
-    int u = blockIdx.x * blockDim.x + threadIdx.x;
+    const int u = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
     if (u >= w) return;
     double s = 0.0;
-    for (int b = 0; b < nb; ++b) s += part[(size_t)b * w + u];
-    out[u] = s;
+    for (int b = lane; b < nb; b += 32) s += part[(size_t)b * w + u];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) out[u] = s;
 }
+static unsigned reduce_grid(int w) { return (unsigned)((w + 7) / 8); }
 
 // per-CTA partial sums of |X_q|^2 and |Y_q - theta_q X_q|^2 for m columns (row-major, ld m)
 __global__ void k_pair_resid(int64_t n, int m, const double *X, const double *HX, const double *theta, double *part) {
@@ -488,7 +493,7 @@ double RefinedSolve::residual(const double *X, int ldx, double *Y, int p, cudaSt
                                            R.data(), p, part.data());
         MBL_LAUNCH_CHECK();
     }
-    k_reduce_parts<<<1, 128, 0, st>>>((int)nb, 3 * p, part.data(), norms.data());
+    k_reduce_parts<<<reduce_grid(3 * p), 256, 0, st>>>((int)nb, 3 * p, part.data(), norms.data());
     MBL_LAUNCH_CHECK();
     std::vector<double> h(3 * p);
     MBL_CUDA(cudaMemcpyAsync(h.data(), norms.data(), 3 * p * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -538,22 +543,40 @@ void RefinedSolve::apply_plain(const double *X, int ldx, double *Y, int p, cudaS
 
 // ---- FGMRES refinement kernels (all p columns in lockstep, each with its own Krylov space) ----
 // V blocks are n x p row-major; column q of block i is the i-th Arnoldi vector of right-hand side q.
+// part[chunk][i * p + q] = sum over the chunk's rows r of V_i[r][q] W[r][q], i < k1.  Thread t < S
+// (S = the largest multiple of p up to the block size) walks the chunk's row-major elements with
+// stride S, so its column q = t % p is fixed and the loads coalesce; sixteen V_i at a time are
+// accumulated in registers, then the threads of each q are added in shared memory (16 x blockDim).
 __global__ void k_gm_dots_part(int64_t n, int k1, int p, const double *V, int64_t vstride, const double *W,
                                double *part, int64_t rows_per) {
-    // part[chunk][i * p + q] = sum over the chunk's rows of V_i[row][q] W[row][q], i < k1
-    extern __shared__ double acc[];
-    for (int t = threadIdx.x; t < k1 * p; t += blockDim.x) acc[t] = 0.0;
-    __syncthreads();
-    int64_t r0 = (int64_t)blockIdx.x * rows_per, r1 = min(n, r0 + rows_per);
-    for (int t = threadIdx.x; t < k1 * p; t += blockDim.x) {
-        int i = t / p, q = t % p;
-        const double *v = V + (int64_t)i * vstride;
-        double s = 0.0;
-        for (int64_t r = r0; r < r1; ++r) s = fma(v[r * p + q], W[r * p + q], s);
-        acc[t] = s;
+    extern __shared__ double red[];
+    const int t = threadIdx.x, nt = blockDim.x, S = (nt / p) * p;
+    const int64_t r0 = (int64_t)blockIdx.x * rows_per, r1 = min(n, r0 + rows_per);
+    const int64_t e0 = r0 * p, e1 = r1 * p;
+    for (int i0 = 0; i0 < k1; i0 += 16) {
+        const int ni = min(16, k1 - i0);
+        double acc[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) acc[i] = 0.0;
+        if (t < S) {
+            for (int64_t e = e0 + t; e < e1; e += S) {
+                const double wv = W[e];
+#pragma unroll
+                for (int i = 0; i < 16; ++i)
+                    if (i < ni) acc[i] = fma(V[(int64_t)(i0 + i) * vstride + e], wv, acc[i]);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 16; ++i) red[i * nt + t] = t < S ? acc[i] : 0.0;
+        __syncthreads();
+        for (int o = t; o < ni * p; o += nt) {
+            const int i = o / p, q = o - i * p;
+            double sum = 0.0;
+            for (int u = q; u < S; u += p) sum += red[i * nt + u];
+            part[(size_t)blockIdx.x * k1 * p + (size_t)(i0 + i) * p + q] = sum;
+        }
+        __syncthreads();
     }
-    __syncthreads();
-    for (int t = threadIdx.x; t < k1 * p; t += blockDim.x) part[(size_t)blockIdx.x * k1 * p + t] = acc[t];
 }
 
 __global__ void k_gm_sub(int64_t n, int k1, int p, const double *V, int64_t vstride, const double *h, double *W) {
@@ -754,15 +777,18 @@ void RefinedSolve::precondition(const double *V, double *Z, int p, cudaStream_t 
     }
     const int64_t n = sec->n;
     if (Dt.size() < (size_t)n * p) Dt.alloc(sec->ctx, (size_t)n * p);
-    // c = E^-1 U^T v  (kd x p, row-major)
-    dense_tn32(n, U32.data(), kd, 0, kd, V, p, 0, p, Dc0.data(), Dwork.data(), st);
-    gemm_small(false, false, p, kd, kd, 1.0, Dc0.data(), p, Einv.data(), kd, 0.0, Dc1.data(), p, st);
-    // z = M^-1 (v - A U c) + U c
-    MBL_CUDA(cudaMemcpyAsync(Dt.data(), V, (size_t)n * p * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    dense_nn_sub32(n, AU32.data(), kd, 0, kd, Dc1.data(), p, Dt.data(), st);
+    {
+        ProfScope ps(sec->ctx, "gm_deflate", 0.0, st);
+        // c = E^-1 U^T v  (kd x p, row-major)
+        dense_tn32(n, U32.data(), kd, 0, kd, V, p, 0, p, Dc0.data(), Dwork.data(), st);
+        gemm_small(false, false, p, kd, kd, 1.0, Dc0.data(), p, Einv.data(), kd, 0.0, Dc1.data(), p, st);
+        // z = M^-1 (v - A U c) + U c
+        dense_nn_sub32(n, AU32.data(), kd, 0, kd, Dc1.data(), p, V, Dt.data(), st);
+    }
     factor_solve_raw(*fz, Dt.data(), p, Z, p, p, false, st);
+    ProfScope ps(sec->ctx, "gm_deflate", 0.0, st);
     gemm_small(false, false, p, kd, kd, -1.0, Dc0.data(), p, Einv.data(), kd, 0.0, Dc1.data(), p, st);
-    dense_nn_sub32(n, U32.data(), kd, 0, kd, Dc1.data(), p, Z, st);
+    dense_nn_sub32(n, U32.data(), kd, 0, kd, Dc1.data(), p, Z, Z, st);
 }
 
 void RefinedSolve::apply_fgmres(const double *X, int ldx, double *Y, int p, cudaStream_t st) {
@@ -783,10 +809,9 @@ void RefinedSolve::apply_fgmres(const double *X, int ldx, double *Y, int p, cuda
     double *h1 = Hall + (size_t)p * (ld * kmax + 3 * ld), *h2 = h1 + (size_t)ld * p, *nr = h2 + (size_t)ld * p;
     const unsigned nbk = nblk(blk);
     auto dots = [&](int k1, const double *V, int64_t vstride, const double *W, double *out) {
-        size_t smem = (size_t)k1 * p * sizeof(double);
-        k_gm_dots_part<<<nch, 256, smem, st>>>(n, k1, p, V, vstride, W, Gdots.data(), rows_per);
+        k_gm_dots_part<<<nch, 256, 16 * 256 * sizeof(double), st>>>(n, k1, p, V, vstride, W, Gdots.data(), rows_per);
         MBL_LAUNCH_CHECK();
-        k_reduce_parts<<<nblk(k1 * p), 256, 0, st>>>(nch, k1 * p, Gdots.data(), out);
+        k_reduce_parts<<<reduce_grid(k1 * p), 256, 0, st>>>(nch, k1 * p, Gdots.data(), out);
         MBL_LAUNCH_CHECK();
     };
     double prev = INFINITY;
@@ -806,11 +831,13 @@ void RefinedSolve::apply_fgmres(const double *X, int ldx, double *Y, int p, cuda
         for (; k < kmax; ++k) {
             double *Vk = GV.data() + (size_t)k * blk, *Zk = GZ.data() + (size_t)k * blk;
             // Z_k = M^-1 V_k ; W = (H - sigma) Z_k
-            k_zero<<<nblk(blk), 256, 0, st>>>(Zk, blk);
-            MBL_LAUNCH_CHECK();
-            precondition(Vk, Zk, p, st);
+            precondition(Vk, Zk, p, st);  // writes all of Z_k
             ++solves;
-            launch_spmv(sec, fz->sigma, Zk, p, 1, GW.data(), p, 1, p, st);
+            {
+                ProfScope ps(ctx, "gm_spmv", 0.0, st);
+                launch_spmv(sec, fz->sigma, Zk, p, 1, GW.data(), p, 1, p, st);
+            }
+            ProfScope ps_o(ctx, "gm_orth", 0.0, st);
             // two Gram-Schmidt passes against V_0..V_k (each column its own space)
             dots(k + 1, GV.data(), blk, GW.data(), h1);
             k_gm_sub<<<nbk, 256, 0, st>>>(n, k + 1, p, GV.data(), blk, h1, GW.data());
@@ -1134,7 +1161,7 @@ void solve_near(mbl_sector *sec, double eps, int nev, const mbl_opts &o, double 
         nrm.alloc(ctx, 2 * nev);
         k_pair_resid<<<nb, 256, 2 * nev * sizeof(double), st>>>(n, nev, Yr.data(), HY.data(), th.data(), part.data());
         MBL_LAUNCH_CHECK();
-        k_reduce_parts<<<nblk(2 * nev), 256, 0, st>>>((int)nb, 2 * nev, part.data(), nrm.data());
+        k_reduce_parts<<<reduce_grid(2 * nev), 256, 0, st>>>((int)nb, 2 * nev, part.data(), nrm.data());
         MBL_LAUNCH_CHECK();
         std::vector<double> hn2(2 * nev), rr(nev);
         MBL_CUDA(cudaMemcpyAsync(hn2.data(), nrm.data(), 2 * nev * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -1400,7 +1427,7 @@ void RitzH::run(mbl_sector *sec, KrylovSchur &ks, double sigma, double hnorm, do
     MBL_CUDA(cudaMemcpyAsync(thd.data(), evals.data(), nev * sizeof(double), cudaMemcpyHostToDevice, st));
     k_pair_resid<<<nb, 256, 2 * nev * sizeof(double), st>>>(n, nev, Y.data(), HY.data(), thd.data(), part.data());
     MBL_LAUNCH_CHECK();
-    k_reduce_parts<<<nblk(2 * nev), 256, 0, st>>>((int)nb, 2 * nev, part.data(), nrm.data());
+    k_reduce_parts<<<reduce_grid(2 * nev), 256, 0, st>>>((int)nb, 2 * nev, part.data(), nrm.data());
     MBL_LAUNCH_CHECK();
     k_scale_cols_to_cm<<<nblk(n * nev), 256, 0, st>>>(n, nev, Y.data(), nrm.data(), d_evecs);
     MBL_LAUNCH_CHECK();

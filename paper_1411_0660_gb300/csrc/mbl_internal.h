@@ -215,8 +215,8 @@ void dense_nn_sub(int64_t n, const double *V, int ldv, int c0, int k, const doub
 // FP32-stored V (the products summed in FP32): dense_tn and dense_nn_sub for preconditioner work.
 void dense_tn32(int64_t n, const float *V, int ldv, int c0, int k, const double *X, int ldx, int x0, int p,
                 double *C, double *work, cudaStream_t st);
-void dense_nn_sub32(int64_t n, const float *V, int ldv, int c0, int k, const double *C, int p, double *X,
-                    cudaStream_t st);
+void dense_nn_sub32(int64_t n, const float *V, int ldv, int c0, int k, const double *C, int p, const double *Xin,
+                    double *Xout, cudaStream_t st);  // Xout = Xin - V C
 // Y[:, 0:m] = V[:, 0:k] S  (S k x m row-major, Y n x ldy row-major starting at column y0)
 void dense_nn(int64_t n, const double *V, int ldv, int k, const double *S, int m, double *Y, int ldy,
               int y0, cudaStream_t st);

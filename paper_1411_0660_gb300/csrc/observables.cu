@@ -121,6 +121,24 @@ static int64_t host_rank(uint32_t s) {
     return r;
 }
 
+// Per basis state: m_A = S^z of sites 0 .. L/2-1 and M = sum_j S^z_j e^{2 pi i j / L}.
+__global__ void k_state_tables(int64_t n, int L, const uint32_t *states, double *mA, double *Mre, double *Mim) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t s = states[i];
+    mA[i] = 0.5 * (double)(2 * __popc(s & ((1u << (L / 2)) - 1u)) - L / 2);
+    double mr = 0.0, mi = 0.0;
+    for (int j = 0; j < L; ++j) {
+        double sj, cj;
+        sincospi(2.0 * j / L, &sj, &cj);
+        const double sz = ((s >> j) & 1u) ? 0.5 : -0.5;
+        mr += sz * cj;
+        mi += sz * sj;
+    }
+    Mre[i] = mr;
+    Mim[i] = mi;
+}
+
 EntTables &ent_tables(Ctx *ctx, int L) {
     auto it = ctx->ent.find(L);
     if (it != ctx->ent.end()) return *it->second;
@@ -147,6 +165,14 @@ EntTables &ent_tables(Ctx *ctx, int L) {
             if (__builtin_popcount(s) == L / 2) st.push_back(s);
         T->d_states.alloc(ctx, st.size());
         MBL_CUDA(cudaMemcpy(T->d_states.data(), st.data(), st.size() * 4, cudaMemcpyHostToDevice));
+        T->d_mA.alloc(ctx, st.size());
+        T->d_Mre.alloc(ctx, st.size());
+        T->d_Mim.alloc(ctx, st.size());
+        k_state_tables<<<(unsigned)((st.size() + 255) / 256), 256, 0, ctx->stream>>>((int64_t)st.size(), L,
+                                                                                T->d_states.data(), T->d_mA.data(),
+                                                                                T->d_Mre.data(), T->d_Mim.data());
+        MBL_LAUNCH_CHECK();
+        MBL_CUDA(cudaStreamSynchronize(ctx->stream));
     }
     T->nblk = (int)da.size();
     T->dA = da;
@@ -164,69 +190,69 @@ EntTables &ent_tables(Ctx *ctx, int L) {
     return ref;
 }
 
-// One CTA per vector: A = sum y^2 and the weighted sums sum y^2 g(s) of g = (y^2)^(q), m_A, m_A^2,
-// Re M, Im M, |M|^2, combined into S_q^P, F and f.  out_nrm2[j] = A.
-__global__ void k_moments(int64_t n, int L, const uint32_t *states, const double *Y, double q, double *sqp,
-                          double *fluct, double *dynf, double *out_nrm2) {
-    __shared__ double cs[32], sn[32];
-    __shared__ double red[7][32];
-    if (threadIdx.x < L) {
-        sincospi(2.0 * threadIdx.x / L, &sn[threadIdx.x], &cs[threadIdx.x]);
-    }
-    __syncthreads();
-    const double *y = Y + (int64_t)blockIdx.x * n;
-    const uint32_t maskA = (1u << (L / 2)) - 1u;
-    double v[7] = {0, 0, 0, 0, 0, 0, 0};
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+constexpr int OBS_NS = 7;  // weighted sums per vector: y^2, (y^2)^q, m_A, m_A^2, Re M, Im M, |M|^2
+
+// CTA (chunk c, vector j): partial sums of the chunk's rows, part[(j * nch + c) * OBS_NS + k].
+__global__ void __launch_bounds__(256) k_moments_part(int64_t n, int nch, const double *Y, const double *mA,
+                                                      const double *Mre, const double *Mim, double q, double *part) {
+    __shared__ double red[OBS_NS][8];
+    const int j = blockIdx.y, c = blockIdx.x;
+    const int64_t per = (n + nch - 1) / nch, r0 = (int64_t)c * per, r1 = min(n, r0 + per);
+    const double *y = Y + (int64_t)j * n;
+    double v[OBS_NS] = {0, 0, 0, 0, 0, 0, 0};
+    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
         const double w = y[i] * y[i];
-        const uint32_t s = states[i];
-        const double mA = 0.5 * (double)(2 * __popc(s & maskA) - L / 2);
-        double mr = 0.0, mi = 0.0;
-        for (int j = 0; j < L; ++j) {
-            const double sz = ((s >> j) & 1u) ? 0.5 : -0.5;
-            mr += sz * cs[j];
-            mi += sz * sn[j];
-        }
+        const double a = mA[i], mr = Mre[i], mi = Mim[i];
         v[0] += w;
         if (w > 0.0) v[1] += q == 2.0 ? w * w : pow(w, q);
-        v[2] += w * mA;
-        v[3] += w * mA * mA;
+        v[2] += w * a;
+        v[3] += w * a * a;
         v[4] += w * mr;
         v[5] += w * mi;
         v[6] += w * (mr * mr + mi * mi);
     }
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
 #pragma unroll
-    for (int k = 0; k < 7; ++k) {
-        double a = v[k];
-        for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
-        if (lane == 0) red[k][wp] = a;
+    for (int k = 0; k < OBS_NS; ++k) {
+        double t = v[k];
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+        if (lane == 0) red[k][wp] = t;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double t[7];
-        for (int k = 0; k < 7; ++k) {
-            t[k] = 0.0;
-            for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t[k] += red[k][i];
-        }
-        const double A = t[0];
-        sqp[blockIdx.x] = (log(t[1]) - q * log(A)) / (1.0 - q);
-        const double m1 = t[2] / A;
-        fluct[blockIdx.x] = t[3] / A - m1 * m1;
-        dynf[blockIdx.x] = t[6] == 0.0 ? NAN : 1.0 - (t[4] * t[4] + t[5] * t[5]) / (A * t[6]);
-        out_nrm2[blockIdx.x] = A;
+    if (threadIdx.x < OBS_NS) {
+        double t = 0.0;
+        for (int i = 0; i < 8; ++i) t += red[threadIdx.x][i];
+        part[((int64_t)j * nch + c) * OBS_NS + threadIdx.x] = t;
     }
 }
 
-// One CTA per adjacent pair (j, j + 1): KL = sum_i p_i (ln y_j,i^2 - ln y_j+1,i^2) + ln A_j+1 - ln A_j
-// over the terms with p_i > 0; +infinity if such a term has q_i = 0.
-__global__ void k_kl(int64_t n, const double *Y, const double *nrm2, double *kl) {
-    __shared__ double red[32];
-    __shared__ int rinf[32];
-    const double *y = Y + (int64_t)blockIdx.x * n, *z = y + n;
+// Thread j: chunk sums in order, then S_q^P, F, f and |y_j|^2.
+__global__ void k_moments_fin(int nev, int nch, const double *part, double q, double *sqp, double *fluct,
+                              double *dynf, double *nrm2) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= nev) return;
+    double t[OBS_NS] = {0, 0, 0, 0, 0, 0, 0};
+    for (int c = 0; c < nch; ++c)
+        for (int k = 0; k < OBS_NS; ++k) t[k] += part[((int64_t)j * nch + c) * OBS_NS + k];
+    const double A = t[0];
+    sqp[j] = (log(t[1]) - q * log(A)) / (1.0 - q);
+    const double m1 = t[2] / A;
+    fluct[j] = t[3] / A - m1 * m1;
+    dynf[j] = t[6] == 0.0 ? NAN : 1.0 - (t[4] * t[4] + t[5] * t[5]) / (A * t[6]);
+    nrm2[j] = A;
+}
+
+// CTA (chunk c, pair j = (j, j + 1)): partial sum of y_j^2 (ln y_j^2 - ln y_j+1^2) over the terms with
+// y_j != 0, and whether such a term has y_j+1 = 0; part[(j * nch + c) * 2 + {0, 1}].
+__global__ void __launch_bounds__(256) k_kl_part(int64_t n, int nch, const double *Y, double *part) {
+    __shared__ double red[8];
+    __shared__ int rinf[8];
+    const int j = blockIdx.y, c = blockIdx.x;
+    const int64_t per = (n + nch - 1) / nch, r0 = (int64_t)c * per, r1 = min(n, r0 + per);
+    const double *y = Y + (int64_t)j * n, *z = y + n;
     double a = 0.0;
     int inf = 0;
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
         const double p = y[i] * y[i], qq = z[i] * z[i];
         if (p == 0.0) continue;
         if (qq == 0.0) {
@@ -248,13 +274,26 @@ __global__ void k_kl(int64_t n, const double *Y, const double *nrm2, double *kl)
     if (threadIdx.x == 0) {
         double t = 0.0;
         int f = 0;
-        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+        for (int i = 0; i < 8; ++i) {
             t += red[i];
             f |= rinf[i];
         }
-        const double Aj = nrm2[blockIdx.x], Ak = nrm2[blockIdx.x + 1];
-        kl[blockIdx.x] = f ? INFINITY : t / Aj + log(Ak) - log(Aj);
+        part[((int64_t)j * nch + c) * 2] = t;
+        part[((int64_t)j * nch + c) * 2 + 1] = f;
     }
+}
+
+// Thread j: KL_j = sum_c part / A_j + ln A_j+1 - ln A_j (+infinity if a chunk flagged q_i = 0 < p_i).
+__global__ void k_kl_fin(int npair, int nch, const double *part, const double *nrm2, double *kl) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= npair) return;
+    double t = 0.0;
+    bool f = false;
+    for (int c = 0; c < nch; ++c) {
+        t += part[((int64_t)j * nch + c) * 2];
+        f = f || part[((int64_t)j * nch + c) * 2 + 1] != 0.0;
+    }
+    kl[j] = f ? INFINITY : t / nrm2[j] + log(nrm2[j + 1]) - log(nrm2[j]);
 }
 
 void observables_extra_dev(Ctx *ctx, int L, int nev, const double *d_evecs, double q, double *d_kl, double *d_sqp,
@@ -264,15 +303,30 @@ void observables_extra_dev(Ctx *ctx, int L, int nev, const double *d_evecs, doub
     if (nev < 1 || nev > n) fail(MBL_ERR_INVALID, "observables: nev must be in [1, dim]");
     if (!(q > 0.0) || q == 1.0 || !std::isfinite(q)) fail(MBL_ERR_INVALID, "observables: q must be positive and not 1");
     EntTables &E = ent_tables(ctx, L);
-    DVec<double> nrm2;
-    nrm2.alloc(ctx, nev);
-    k_moments<<<nev, 256, 0, st>>>(n, L, E.d_states.data(), d_evecs, q, d_sqp, d_fluct, d_dynf, nrm2.data());
+    // about two CTAs per SM over all vectors, chunks of at least 2048 rows
+    const int nch = (int)std::max<int64_t>(1, std::min<int64_t>((2 * ctx->sm_count + nev - 1) / nev, n / 2048));
+    const size_t need_part = (size_t)nev * nch * OBS_NS, need_nrm = (size_t)nev;
+    if (E.x_part_cap < need_part) {
+        E.x_part.alloc(ctx, need_part);
+        E.x_part_cap = need_part;
+    }
+    if (E.x_nrm_cap < need_nrm) {
+        E.x_nrm.alloc(ctx, need_nrm);
+        E.x_nrm_cap = need_nrm;
+    }
+    k_moments_part<<<dim3(nch, nev), 256, 0, st>>>(n, nch, d_evecs, E.d_mA.data(), E.d_Mre.data(), E.d_Mim.data(), q,
+                                                   E.x_part.data());
+    MBL_LAUNCH_CHECK();
+    k_moments_fin<<<(nev + 127) / 128, 128, 0, st>>>(nev, nch, E.x_part.data(), q, d_sqp, d_fluct, d_dynf,
+                                                     E.x_nrm.data());
     MBL_LAUNCH_CHECK();
     if (nev > 1) {
-        k_kl<<<nev - 1, 256, 0, st>>>(n, d_evecs, nrm2.data(), d_kl);
+        // the moments' partials are consumed: reuse the buffer (2 per pair and chunk <= 7 per vector and chunk)
+        k_kl_part<<<dim3(nch, nev - 1), 256, 0, st>>>(n, nch, d_evecs, E.x_part.data());
+        MBL_LAUNCH_CHECK();
+        k_kl_fin<<<(nev + 126) / 128, 128, 0, st>>>(nev - 1, nch, E.x_part.data(), E.x_nrm.data(), d_kl);
         MBL_LAUNCH_CHECK();
     }
-    MBL_CUDA(cudaStreamSynchronize(st));
 }
 
 void observables_dev(Ctx *ctx, int L, int nev, const double *d_evals, const double *d_evecs, double *d_r,

@@ -54,6 +54,7 @@ struct SolveDesc {
     int64_t offk;                    // prefix of backward row blocks (RBK rows of [k0, f)) in the step
     int64_t moff;                    // offset (elements) of M while it is built
     int64_t goff;                    // offset (elements) of G in the packed solve factor
+    int64_t offk_l;                  // prefix of backward row blocks within the level (level-wide launch)
     int32_t fdesc[SUBS];             // factor descriptors of the sub-panels (-1 if absent)
 };
 
@@ -71,6 +72,18 @@ struct SolveStep {
     int64_t nrb;                     // forward row blocks in this step
     int64_t nrbb;                    // RBB-row tiles in this step
     int64_t nrbk;                    // backward row blocks in this step
+    int32_t maxw;                    // widest panel of the step (backward column chunks = ceil(maxw / RBB))
+    int64_t fblk0, bblk0;            // first entries of the step in fblk_desc / bblk_desc
+};
+
+// Backward sweep, level by level: one launch over every panel of the level starts each panel's
+// accumulator acc_i = G_i^T [y_i; 0; -x_cb] (its own rows and the contribution block, whose x the
+// ancestors have fixed); then, for j = K-1 .. 1 (K panels in the level's widest front), one launch
+// subtracts G_i[rows of panel j]^T x_j from acc_i for every earlier panel i < j of every front with
+// more than j panels (x_j = acc_j is final by then).  BwdUpd lists the (i, j) pairs of one launch.
+struct BwdUpd {
+    int32_t level, j;
+    int64_t it0, nit;                // items bu_items[it0 .. it0 + nit): (descriptor of i, descriptor of j)
 };
 
 // Work item of the dataflow (persistent) solve: kind 0 = gather of rows [GR a, GR a + GR) of a
@@ -108,6 +121,19 @@ struct Plan {
     std::vector<SolveStep> ssteps;
     std::vector<int32_t> lvl_sstep_ptr;       // solve steps by level
     std::vector<SolveDesc> sdescs;
+    // per forward (RBF rows) and backward (RBK rows) row block of each solve step, the index of its
+    // descriptor within the step: one load instead of a search
+    std::vector<int32_t> fblk_desc, bblk_desc;
+    // level-wide backward start: per level its first descriptor, count, widest panel, row blocks and
+    // block -> descriptor table (relative to the level's first descriptor, offsets in lvl_bblk0)
+    std::vector<int32_t> lvl_d0, lvl_nd, lvl_maxw, lvl_maxr;  // maxr: most rows of a panel's G
+    std::vector<int64_t> lvl_nrbk, lvl_bblk0;
+    std::vector<int32_t> lvl_bblk_desc;
+    int64_t max_lvl_nrbk = 0;
+    // backward updates: per level, launches in order (bu_ptr by level), items as descriptor pairs
+    std::vector<BwdUpd> bupd;
+    std::vector<int32_t> bu_ptr;
+    std::vector<int32_t> bu_items;   // 2 per item
     // forward-solve gather as row lists: for every row of every front of a level (levels in order),
     // its work row in Z, its own right-hand-side row (-1 below the fully summed block) and the Z
     // rows of the children's contribution blocks that land on it (children in tree order)
@@ -137,6 +163,7 @@ struct Plan {
     DVec<AsmItem> d_asm_items;
     DVec<PanelDesc> d_descs;
     DVec<SolveDesc> d_sdescs;
+    DVec<int32_t> d_fblk_desc, d_bblk_desc, d_lvl_bblk_desc, d_bu_items;
     DVec<int64_t> d_fg_dst, d_fg_own, d_fg_cptr, d_fg_src;
     DVec<SolveItem> d_df_fwd, d_df_bwd;
     DVec<int32_t> d_df_gchunks, d_df_ftotal, d_df_btotal, d_df_fprefix, d_df_bprefix;

@@ -38,7 +38,7 @@ size_t job_bytes(const Plan &p, int nev, int block, int prec) {
     b += (double)std::max<int64_t>(p.wscratch_elems, 1) * es + (double)p.m_elems * es;
     b += (double)p.sg_elems * es;                                            // packed solve factor
     b += 2.0 * (double)p.zwork_elems * pb * es + 2.0 * n * pb * es;         // solve work
-    b += (double)p.max_sstep_nrbk * SUBS * RBB * pad * es;
+    b += (double)std::max(p.max_sstep_nrbk, p.max_lvl_nrbk) * SUBS * RBB * pad * es;
     b += 8.0 * n * (3.0 * ldv + 2.0 * nev + 30.0 * pb);                      // Krylov, Rayleigh-Ritz, refinement
     b += 8.0 * n * 480.0;                                                    // extremal-bounds Lanczos basis
     return (size_t)(1.10 * b) + ((size_t)64 << 20);

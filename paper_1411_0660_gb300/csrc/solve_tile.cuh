@@ -110,8 +110,9 @@ __device__ __forceinline__ void bwd_tile_product(const T *Gs, const T *vs, T *re
 }
 
 // Last block of a (panel, column chunk): add the nb partial tiles ([q][c], RBB x PB each, stride
-// apart) in a fixed order and write x_panel -- columns c < wc, right-hand sides q < p -- to
-// zs[c p + q] and xo[c p + q].  comb: scratch of 2 x RBB x PB in shared memory.  256 threads.
+// apart) in a fixed order and write the result -- columns c < wc, right-hand sides q < p -- to
+// zs[c p + q] and, unless xo is null, xo[c p + q].  comb: scratch of 2 x RBB x PB in shared memory.
+// 256 threads.
 template <class T, int PB>
 __device__ void bwd_finish(const T *src, int64_t stride, int nb, int wc, int p, T *zs, T *xo, T *comb) {
     constexpr int E = 16 / sizeof(T), NV = RBB * PB / E;
@@ -138,7 +139,7 @@ __device__ void bwd_finish(const T *src, int64_t stride, int nb, int wc, int p, 
                 const int q = o / RBB, c = o % RBB;
                 if (c < wc && q < p) {
                     zs[c * p + q] = acc[e];
-                    xo[c * p + q] = acc[e];
+                    if (xo) xo[c * p + q] = acc[e];
                 }
             }
         }
@@ -151,7 +152,7 @@ __device__ void bwd_finish(const T *src, int64_t stride, int nb, int wc, int p, 
             const int q = o / RBB, c = o % RBB;
             if (c < wc && q < p) {
                 zs[c * p + q] = v;
-                xo[c * p + q] = v;
+                if (xo) xo[c * p + q] = v;
             }
         }
     }

@@ -16,6 +16,7 @@
 // fundamental supernodes, relaxed amalgamation, and supernodal row structures by merging the
 // children's update rows.
 #include <algorithm>
+#include <map>
 #include <chrono>
 #include <cmath>
 #include <numeric>
@@ -494,6 +495,7 @@ std::shared_ptr<Plan> build_plan(int L, const std::vector<uint32_t> &states, con
     p.asm_ptr.assign(p.nlevels + 1, 0);
     p.lvl_step_ptr.assign(p.nlevels + 1, 0);
     p.lvl_sstep_ptr.assign(p.nlevels + 1, 0);
+    p.bu_ptr.assign(1, 0);
     std::vector<int64_t> fd_off(ns + 1, 0);  // factor descriptor of (front, panel) at fd_of[fd_off[s] + kk]
     for (int32_t s = 0; s < ns; ++s) fd_off[s + 1] = fd_off[s] + (p.sn_nc[s] + NB - 1) / NB;
     std::vector<int32_t> fd_of(fd_off[ns], -1);
@@ -533,7 +535,8 @@ std::shared_ptr<Plan> build_plan(int L, const std::vector<uint32_t> &states, con
         p.lvl_step_ptr[l + 1] = (int32_t)p.steps.size();
         // solve schedule: SPW-wide panels
         for (int32_t ks = 0; ks * SPW < maxnc; ++ks) {
-            SolveStep ss{l, (int32_t)p.sdescs.size(), 0, 0, 0, 0};
+            SolveStep ss{l, (int32_t)p.sdescs.size(), 0, 0, 0, 0, 0, (int64_t)p.fblk_desc.size(),
+                         (int64_t)p.bblk_desc.size()};
             for (int32_t q = p.lvl_ptr[l]; q < p.lvl_ptr[l + 1]; ++q) {
                 int32_t s = p.lvl_fronts[q];
                 int32_t k0 = ks * SPW;
@@ -556,6 +559,10 @@ std::shared_ptr<Plan> build_plan(int L, const std::vector<uint32_t> &states, con
                 ss.nrb += (w + sd.m2 + RBF - 1) / RBF;
                 ss.nrbb += (w + sd.m2 + RBB - 1) / RBB;
                 ss.nrbk += (w + sd.m2 + RBK - 1) / RBK;
+                ss.maxw = std::max(ss.maxw, w);
+                const int32_t local = (int32_t)p.sdescs.size() - ss.d0;
+                for (int32_t b = 0; b < (w + sd.m2 + RBF - 1) / RBF; ++b) p.fblk_desc.push_back(local);
+                for (int32_t b = 0; b < (w + sd.m2 + RBK - 1) / RBK; ++b) p.bblk_desc.push_back(local);
                 p.m_elems += (int64_t)w * w;
                 p.sg_elems += sg_ld(w + sd.m2) * w;
                 p.sdescs.push_back(sd);
@@ -566,6 +573,52 @@ std::shared_ptr<Plan> build_plan(int L, const std::vector<uint32_t> &states, con
             p.ssteps.push_back(ss);
         }
         p.lvl_sstep_ptr[l + 1] = (int32_t)p.ssteps.size();
+        // backward: level-wide start over the level's descriptors (contiguous), then the updates
+        {
+            const int32_t d0 = p.ssteps[p.lvl_sstep_ptr[l]].d0;
+            const int32_t d1 = (int32_t)p.sdescs.size();
+            int64_t nrbk = 0;
+            int32_t maxw = 0, maxr = 0;
+            p.lvl_d0.push_back(d0);
+            p.lvl_nd.push_back(d1 - d0);
+            p.lvl_bblk0.push_back((int64_t)p.lvl_bblk_desc.size());
+            std::vector<std::vector<int32_t>> panels_of;  // per front of the level: its descriptors in panel order
+            std::map<int32_t, int32_t> slot;
+            for (int32_t q = d0; q < d1; ++q) {
+                SolveDesc &sd = p.sdescs[q];
+                sd.offk_l = nrbk;
+                const int32_t nb = (sd.w + sd.m2 + RBK - 1) / RBK;
+                for (int32_t b = 0; b < nb; ++b) p.lvl_bblk_desc.push_back(q - d0);
+                nrbk += nb;
+                maxw = std::max(maxw, sd.w);
+                maxr = std::max(maxr, sd.w + sd.m2);
+                auto it = slot.find(sd.front);
+                if (it == slot.end()) {
+                    it = slot.emplace(sd.front, (int32_t)panels_of.size()).first;
+                    panels_of.emplace_back();
+                }
+                panels_of[it->second].push_back(q);
+            }
+            p.lvl_nrbk.push_back(nrbk);
+            p.lvl_maxw.push_back(maxw);
+            p.lvl_maxr.push_back(maxr);
+            p.max_lvl_nrbk = std::max(p.max_lvl_nrbk, nrbk);
+            size_t kmax = 0;
+            for (auto &v : panels_of) kmax = std::max(kmax, v.size());
+            for (int32_t j = (int32_t)kmax - 1; j >= 1; --j) {
+                BwdUpd u{l, j, (int64_t)p.bu_items.size() / 2, 0};
+                for (auto &v : panels_of) {
+                    if ((int32_t)v.size() <= j) continue;
+                    for (int32_t i = 0; i < j; ++i) {
+                        p.bu_items.push_back(v[i]);
+                        p.bu_items.push_back(v[j]);
+                        ++u.nit;
+                    }
+                }
+                p.bupd.push_back(u);
+            }
+            p.bu_ptr.push_back((int32_t)p.bupd.size());
+        }
     }
     // forward-solve gather lists
     p.lvl_fg_ptr.assign(p.nlevels + 1, 0);
@@ -696,6 +749,10 @@ void upload_plan(Ctx *ctx, Plan &p) {
     up(ctx, p.d_asm_items, p.asm_items);
     up(ctx, p.d_descs, p.descs);
     up(ctx, p.d_sdescs, p.sdescs);
+    up(ctx, p.d_fblk_desc, p.fblk_desc);
+    up(ctx, p.d_bblk_desc, p.bblk_desc);
+    up(ctx, p.d_lvl_bblk_desc, p.lvl_bblk_desc);
+    up(ctx, p.d_bu_items, p.bu_items);
     up(ctx, p.d_fg_dst, p.fg_dst);
     up(ctx, p.d_fg_own, p.fg_own);
     up(ctx, p.d_fg_cptr, p.fg_cptr);

@@ -180,8 +180,18 @@ def test_dataflow_solve_matches_level_sequence(g, ctx, prec, L):
     lo, hi = g.extremal_bounds(sec)
     sigma = lo + 0.45 * (hi - lo)
     B = np.random.default_rng(2).standard_normal((sec.dim, 8))
-    X = [g.factor(sec, sigma, precision=prec, solve_dataflow=df).solve(B, refine=False) for df in (0, 1)]
-    assert np.max(np.abs(X[1] - X[0])) <= 1e-12 * np.max(np.abs(X[0]))
+    fs = [g.factor(sec, sigma, precision=prec, solve_dataflow=df) for df in (0, 1)]
+    X = [f.solve(B, refine=False) for f in fs]
+    # the two schedules sum in different orders: in FP64 they agree to rounding; in FP32 each is as
+    # far from the exact solve as the other (the refined FP64 solution is the yardstick)
+    if prec == 0:
+        assert np.max(np.abs(X[1] - X[0])) <= 1e-10 * np.max(np.abs(X[0]))
+    else:
+        xr = fs[0].solve(B, refine=True)
+        e0, e1 = (np.max(np.abs(x - xr)) for x in X)
+        scale = np.max(np.abs(xr))
+        assert e0 <= 1e-2 * scale and e1 <= 1e-2 * scale
+        assert np.max(np.abs(X[1] - X[0])) <= 2.0 * max(e0, e1) + 1e-6 * scale
 
 
 def test_dataflow_solve_near(g, ctx, orc):
