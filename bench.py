@@ -37,7 +37,7 @@ EPS = [0.1, 0.5, 0.9]
 PROF_KEYS = ("factor_fp32", "schur_fp32", "schur_tc", "trisolve_fp32", "refine_spmv", "orth", "syev_krylov",
              "syev_rr", "extremal_bounds", "op_apply", "ks_restart", "ritz_h", "observables", "sector_build",
              "syev_fp32", "syev_fallback", "oa_refine", "trisolve_fp64", "factor_fp64", "syev_rr_fp64",
-             "gm_deflate", "gm_spmv", "gm_orth", "f_assemble", "f_panel", "f_build_g")
+             "gm_deflate", "gm_spmv", "gm_orth", "f_assemble", "f_panel", "f_build_g", "syev_rr_bisect")
 METRIC = "eigenpairs/s near eps (res<=1e-10||H||), L=18, mixed vs FP64; p50/p99 latency"
 
 

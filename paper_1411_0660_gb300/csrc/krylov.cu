@@ -1296,6 +1296,7 @@ RitzH::RitzH(Ctx *c, int64_t n_, int ldv, int nev_) : ctx(c), n(n_), nev(nev_) {
     M2.alloc(ctx, (size_t)ldv * ldv);
     Gw.alloc(ctx, ldv);
     Gwork.alloc(ctx, syev_work_doubles(ldv));
+    if (ldv <= EIG_SMEM_MAX_M) Bwork.alloc(ctx, syev_bisect_work(ldv));
     Ctmp.alloc(ctx, (size_t)ldv * 32);
     work.alloc(ctx, dense_tn_work(n, ldv, 32) + 64);
     gm.alloc(ctx, 1);
@@ -1356,6 +1357,25 @@ void RitzH::run(mbl_sector *sec, KrylovSchur &ks, double sigma, double hnorm, do
         // accuracy, otherwise the FP64 eigensolver runs.  The pairs' residuals on H are recomputed below.
         ProfScope ps(ctx, "syev_rr", (double)mb, st);
         const bool fp32 = ks.ldv <= EIG_SMEM_MAX_M;
+        // accept eigenvectors X (in Gs) only if the nev wanted columns are orthonormal and diagonalize
+        // G to FP64 accuracy: |e_j - X^T X e_j| <= 1e-12, |off(X^T G X) e_j| <= 1e-12 max|lambda|
+        // (leaves X^T G X in Gr3)
+        auto check_wanted = [&]() {
+            gemm_small(true, false, mb, mb, mb, 1.0, Gs.data(), mb, Gs.data(), mb, 0.0, Gr1.data(), mb, st);
+            gemm_small(false, false, mb, mb, mb, 1.0, Gsym.data(), mb, Gs.data(), mb, 0.0, Gr2.data(), mb, st);
+            gemm_small(true, false, mb, mb, mb, 1.0, Gs.data(), mb, Gr2.data(), mb, 0.0, Gr3.data(), mb, st);
+            k_oa_colnorms<<<nblk(mb, 128), 128, 0, st>>>(mb, Gr1.data(), Gr3.data(), Gr2.data());
+            MBL_LAUNCH_CHECK();
+            std::vector<double> q((size_t)2 * mb), th(mb);
+            MBL_CUDA(cudaMemcpyAsync(q.data(), Gr2.data(), q.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+            MBL_CUDA(cudaMemcpyAsync(th.data(), Gw.data(), mb * sizeof(double), cudaMemcpyDeviceToHost, st));
+            MBL_CUDA(cudaStreamSynchronize(st));
+            double amax = 0.0;
+            for (double v : th) amax = std::max(amax, std::fabs(v));
+            bool good = true;
+            for (int j : nearest_sorted(th, sigma, nev)) good = good && q[j] <= 1e-12 && q[mb + j] <= 1e-12 * amax;
+            return good;
+        };
         bool ok = false;
         if (fp32) {
             MBL_CUDA(cudaMemcpyAsync(Gsym.data(), Gs.data(), (size_t)mb * mb * sizeof(double), cudaMemcpyDeviceToDevice,
@@ -1369,21 +1389,17 @@ void RitzH::run(mbl_sector *sec, KrylovSchur &ks, double sigma, double hnorm, do
                                          cudaMemcpyDeviceToDevice, st));
                 gemm_small(false, false, mb, mb, mb, -0.5, Gr2.data(), mb, Gr1.data(), mb, 1.5, Gs.data(), mb, st);
             }
-            gemm_small(true, false, mb, mb, mb, 1.0, Gs.data(), mb, Gs.data(), mb, 0.0, Gr1.data(), mb, st);
-            gemm_small(false, false, mb, mb, mb, 1.0, Gsym.data(), mb, Gs.data(), mb, 0.0, Gr2.data(), mb, st);
-            gemm_small(true, false, mb, mb, mb, 1.0, Gs.data(), mb, Gr2.data(), mb, 0.0, Gr3.data(), mb, st);
-            k_oa_colnorms<<<nblk(mb, 128), 128, 0, st>>>(mb, Gr1.data(), Gr3.data(), Gr2.data());
-            MBL_LAUNCH_CHECK();
-            std::vector<double> q((size_t)2 * mb), th(mb);
             int info = 0;
-            MBL_CUDA(cudaMemcpyAsync(q.data(), Gr2.data(), q.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
-            MBL_CUDA(cudaMemcpyAsync(th.data(), Gw.data(), mb * sizeof(double), cudaMemcpyDeviceToHost, st));
             MBL_CUDA(cudaMemcpyAsync(&info, ginfo.data(), sizeof(int), cudaMemcpyDeviceToHost, st));
-            MBL_CUDA(cudaStreamSynchronize(st));
-            double amax = 0.0;
-            for (double v : th) amax = std::max(amax, std::fabs(v));
-            ok = info == 0;
-            for (int j : nearest_sorted(th, sigma, nev)) ok = ok && q[j] <= 1e-12 && q[mb + j] <= 1e-12 * amax;
+            ok = check_wanted() && info == 0;
+            if (!ok) {
+                // FP64 by bisection and inverse iteration, under the same check
+                ProfScope ps2(ctx, "syev_rr_bisect", (double)mb, st);
+                MBL_CUDA(cudaMemcpyAsync(Gs.data(), Gsym.data(), (size_t)mb * mb * sizeof(double),
+                                         cudaMemcpyDeviceToDevice, st));
+                syev_bisect(mb, Gs.data(), Gw.data(), Bwork.data(), st);
+                ok = check_wanted();
+            }
             if (ok) {
                 // the Ritz values are the Rayleigh quotients of the final vectors: diag(X^T G X)
                 k_copy_diag<<<nblk(mb, 128), 128, 0, st>>>(mb, Gr3.data(), Gw.data());

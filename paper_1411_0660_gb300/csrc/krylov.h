@@ -78,6 +78,7 @@ struct RitzH {
     int nev;
     unsigned nb = 0;
     DVec<double> HV, Gm, Gs, Gsym, Gr1, Gr2, Gr3, M2, Gw, Gwork, Ctmp, work, SKs, Y, HY, thd, part, nrm;
+    DVec<double> Bwork;  // bisection eigensolver scratch
     DVec<int> gm, ginfo, didx;
     DVec<int64_t> goff;
     std::vector<double> evals, resid;

@@ -229,6 +229,10 @@ void chol_qr(int64_t n, double *X, int p, double *R, double *G, double *work, in
              cudaStream_t st);
 // Batched symmetric eigensolver on device: for b in [0, batch): A_b (m_b x m_b, column-major,
 // lda_b) -> eigenvalues ascending w_b, eigenvectors (if vecs) overwrite A_b.
+// One symmetric m x m FP64 matrix (column-major, m <= 160) -> eigenvectors in place (columns
+// ascending) and eigenvalues d_w, by bisection and inverse iteration; d_work >= syev_bisect_work(m).
+size_t syev_bisect_work(int m);
+void syev_bisect(int m, double *d_A, double *d_w, double *d_work, cudaStream_t st);
 size_t syev_work_doubles(int mmax, bool vecs = true);
 // sel (optional, indexed like w): eigenvectors are computed only where sel != 0 (others zero).
 constexpr int EIG_SMEM_MAX_M = 160;  // largest order the small eigensolver keeps in shared memory
