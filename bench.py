@@ -555,8 +555,20 @@ def main():
         achieved = per_launch_work / (per_launch_ms / 1e3) / 1e12
         peak = 152 * 2 * 2 * clk * 1e6 / 1e12
         roof = {"bound": "alu", "unit": "TFLOP/s", "peak_source": "152 SM x 2 FP64 FMA/clk x 2 x 2070 MHz"}
-    roof.update({"achieved": achieved, "peak": peak, "frac": achieved / peak, "traffic": None, "kernel": dom,
+    traffic = None
+    if dom == "trisolve_fp32":
+        # DRAM bytes of one block solve from the committed ncu capture of the same kernels
+        try:
+            with open(os.path.join(ROOT, "profiles", "solve_l18_fp32_traffic.md")) as fp:
+                for ln in fp:
+                    if ln.startswith("traffic_bytes_per_solve:"):
+                        traffic = float(ln.split(":")[1])
+        except OSError:
+            traffic = None
+    roof.update({"achieved": achieved, "peak": peak, "frac": achieved / peak, "traffic": traffic, "kernel": dom,
                  "launch_ms": per_launch_ms, "work_per_launch": per_launch_work})
+    if traffic is not None:
+        roof["traffic_source"] = "profiles/solve_l18_fp32_traffic.md (ncu dram__bytes_read + write, one solve)"
 
     if rank == 0:
         lat_ms = sorted(1e3 * x for x in lat)

@@ -64,7 +64,8 @@ typedef struct mbl_opts {
     double refine_tol;    /* refinement stop: ||b - A x|| <= refine_tol (|A||x| + |b|)[1e-14]*/
     int max_refine;       /* refinement steps per application                       [20]   */
     uint64_t start_seed;  /* seed of the random start block                         [12345]*/
-    int tensor_cores;     /* FP32 fronts: Schur updates on tcgen05 (3xTF32) if nonzero [1]   */
+    int tensor_cores;     /* FP32 fronts' Schur updates: 0 CUDA cores, 1 tcgen05 3xTF32,      
+                             2 tcgen05 3xBF16 (split-BF16 operands, FP32 accumulation)   [1]   */
     int refine_mode;      /* 0: plain iterative refinement, 1: FGMRES with the factor as    */
                           /*    right preconditioner (FP64 Arnoldi per right-hand side)  [1]   */
     int gmres_restart;    /* FGMRES inner dimension before a restart (1..64)          [24]   */

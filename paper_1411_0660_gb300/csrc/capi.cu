@@ -156,9 +156,10 @@ std::shared_ptr<Plan> get_plan(mbl_sector *sec) {
     return P;
 }
 
-std::unique_ptr<Factorization> make_factorization(mbl_sector *sec, double sigma, int prec, double hnorm, bool use_tc,
+std::unique_ptr<Factorization> make_factorization(mbl_sector *sec, double sigma, int prec, double hnorm, int tc_mode,
                                                   bool dataflow) {
     if (prec != MBL_PREC_FP64 && prec != MBL_PREC_FP32) fail(MBL_ERR_INVALID, "unknown precision");
+    if (tc_mode < 0 || tc_mode > 2) fail(MBL_ERR_INVALID, "tensor_cores must be 0, 1 (3xTF32) or 2 (3xBF16)");
     auto F = std::make_unique<Factorization>();
     F->ctx = sec->ctx;
     F->sec = sec;
@@ -166,7 +167,7 @@ std::unique_ptr<Factorization> make_factorization(mbl_sector *sec, double sigma,
     F->sigma = sigma;
     F->prec = prec;
     F->tiny = (prec == MBL_PREC_FP64 ? 1e-12 : 1e-7) * hnorm;
-    F->use_tc = use_tc;
+    F->tc_mode = tc_mode;
     F->dataflow = dataflow;
     F->allocate();
     cudaStream_t st = sec->ctx->stream;
@@ -474,7 +475,7 @@ int mbl_factor(mbl_sector *sec, double sigma, const mbl_opts *opts, mbl_factoriz
     double emin, emax;
     extremal_bounds(sec, &emin, &emax);
     double hn = std::max(std::fabs(emin), std::fabs(emax));
-    auto F = make_factorization(sec, sigma, o.precision, hn, o.tensor_cores != 0, o.solve_dataflow != 0);
+    auto F = make_factorization(sec, sigma, o.precision, hn, o.tensor_cores, o.solve_dataflow != 0);
     mbl_factorization *h = new mbl_factorization();
     h->f = std::move(F);
     *out = h;

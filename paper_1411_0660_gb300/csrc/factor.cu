@@ -31,6 +31,10 @@ __device__ __forceinline__ int lower_bound_i32(const int32_t *a, int n, int x) {
     return lo;
 }
 
+// threads of the column-maximum and trsm kernels (one CTA per RB-row block): more than the block's
+// rows, so that their loads of the panel are in flight together
+constexpr int PANEL_THREADS = 256;
+
 // descriptor whose [off, off + count) range holds `b` (descs of one step are ordered by off)
 __device__ __forceinline__ int find_desc2(const PanelDesc *d, int nd, int64_t b) {
     int lo = 0, hi = nd - 1;
@@ -94,7 +98,7 @@ __global__ void __launch_bounds__(256) k_assemble(const AsmItem *items, const in
 // Largest |entry| of each panel column over the rows below the panel (current values), per step
 // descriptor: cmax[di * NB + c] (float bits, atomicMax).  Used by the pivot choice of k_panel_diag.
 template <class T>
-__global__ void __launch_bounds__(RB) k_panel_colmax(const PanelDesc *descs, int nd, const int64_t *fo,
+__global__ void __launch_bounds__(PANEL_THREADS) k_panel_colmax(const PanelDesc *descs, int nd, const int64_t *fo,
                                                      const int32_t *fsz, const T *arena, unsigned int *cmax) {
     const int di = find_desc2(descs, nd, blockIdx.x);
     const PanelDesc d = descs[di];
@@ -235,7 +239,7 @@ __global__ void __launch_bounds__(256) k_panel_diag(const PanelDesc *descs, cons
 // W21 = A21 L11^-T by forward substitution (one thread per row, no explicit inverse), then
 // L21 = W21 D^-1.  The columns of A21 are read in the panel's pivoted order.
 template <class T>
-__global__ void __launch_bounds__(RB) k_panel_trsm(const PanelDesc *descs, int nd, const int64_t *fo,
+__global__ void __launch_bounds__(PANEL_THREADS) k_panel_trsm(const PanelDesc *descs, int nd, const int64_t *fo,
                                                    const int32_t *fsz, const int32_t *sn_start, T *arena,
                                                    const T *Dg, const int32_t *piv, T *wscr,
                                                    unsigned long long *stats) {
@@ -285,7 +289,8 @@ __global__ void __launch_bounds__(RB) k_panel_trsm(const PanelDesc *descs, int n
         W[(int64_t)(r0 - k0 - w + i) + (int64_t)t * m2] = x;
         lmax = fmaxf(lmax, (float)tabs(l));
     }
-    atomicMax(reinterpret_cast<unsigned int *>(stats), __float_as_uint(lmax));
+    for (int o = 16; o > 0; o >>= 1) lmax = fmaxf(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
+    if ((tid & 31) == 0) atomicMax(reinterpret_cast<unsigned int *>(stats), __float_as_uint(lmax));
 }
 
 // Trailing update of one 64 x 64 lower tile: C[i][j] -= sum_t L21[i][t] W21[j][t]
@@ -869,17 +874,17 @@ __global__ void __launch_bounds__(256) k_bwd_step(const SolveDesc *sdescs, const
         pdl_wait();
         return;
     }
-    const int s = d.front, k0 = d.k0, w = d.w, ncs = nc[s], R = w + d.m2;
-    const int b = (int)(blockIdx.x - d.offk_l), nb = (R + RBK - 1) / RBK;
-    const int r0 = b * RBK;  // relative to k0
-    const int nr = min(RBK, R - r0), nrv = (nr + E - 1) / E;
+    const int s = d.front, k0 = d.k0, w = d.w, ncs = nc[s], R = w + d.m2, cb0 = ncs - k0;
+    const int b = (int)(blockIdx.x - d.offk_l), nb = bwd_start_blocks(R, cb0);
+    const int r0 = b == 0 ? 0 : (cb0 & ~3) + (b - 1) * RBK;  // relative to k0
+    const int nr = b == 0 ? w : min(RBK, R - r0), nrv = (nr + E - 1) / E;
     const int wc = min(RBB, w - cc);
     const int64_t zb = zo[s] + k0, ld = sg_ld(R);
     bwd_tile_issue(Gs, Gp + d.goff + (int64_t)cc * ld + r0, ld, wc, nrv);
     // thread i loads row i of v: the panel's y, zero on later panels' rows, -x on the contribution block
     static_assert(RBK == 256, "one row of v per thread");
     const int i = threadIdx.x, rr = r0 + i;
-    const int kind = i >= nr ? 0 : (rr < w ? 1 : (k0 + rr < ncs ? 0 : 3));
+    const int kind = i >= nr ? 0 : (b == 0 ? 1 : (rr < cb0 ? 0 : 3));
     const int64_t src = kind == 1 ? ((int64_t)sn_start[s] + k0 + rr) * p
                       : kind == 3 ? (int64_t)rows[rows_off[s] + k0 + rr] * p : 0;
     pdl_wait();
@@ -1003,7 +1008,7 @@ static void factor_impl(Factorization &fz, cudaStream_t st) {
                 ProfScope ps_pan(fz.ctx, "f_panel", 0.0, st);
                 MBL_CUDA(cudaMemsetAsync(cmax, 0, (size_t)stp.nd * NB * sizeof(unsigned int), st));
                 if (stp.n2 > 0) {
-                    k_panel_colmax<T><<<(unsigned)stp.n2, RB, 0, st>>>(dd, stp.nd, p.d_sn_fo.data(), p.d_sn_f.data(), arena,
+                    k_panel_colmax<T><<<(unsigned)stp.n2, PANEL_THREADS, 0, st>>>(dd, stp.nd, p.d_sn_fo.data(), p.d_sn_f.data(), arena,
                                                                        cmax);
                     MBL_LAUNCH_CHECK();
                 }
@@ -1011,7 +1016,7 @@ static void factor_impl(Factorization &fz, cudaStream_t st) {
                                                         Dg, fz.piv.data(), fz.tiny, fz.counters.data(), cmax);
                 MBL_LAUNCH_CHECK();
                 if (stp.n2 > 0) {
-                    k_panel_trsm<T><<<(unsigned)stp.n2, RB, trsm_smem<T>(), st>>>(dd, stp.nd, p.d_sn_fo.data(),
+                    k_panel_trsm<T><<<(unsigned)stp.n2, PANEL_THREADS, trsm_smem<T>(), st>>>(dd, stp.nd, p.d_sn_fo.data(),
                                                                                  p.d_sn_f.data(), p.d_sn_start.data(), arena,
                                                                                  Dg, fz.piv.data(), wscr,
                                                                                  fz.counters.data() + 3);
@@ -1022,10 +1027,10 @@ static void factor_impl(Factorization &fz, cudaStream_t st) {
                 double fl = 0.0;  // algorithmic flops: lower triangle of the trailing block, 2 per entry per k
                 for (int q = stp.d0; q < stp.d0 + stp.nd; ++q)
                     fl += (double)p.descs[q].m2 * (p.descs[q].m2 + 1) * p.descs[q].w;
-                if (sizeof(T) == 4 && fz.use_tc) {
+                if (sizeof(T) == 4 && fz.tc_mode != 0) {
                     ProfScope ps(fz.ctx, "schur_tc", fl, st);
                     launch_schur_tc(stp, dd, p, reinterpret_cast<float *>(arena), reinterpret_cast<const float *>(wscr),
-                                    fz.counters.data() + 2, st);
+                                    fz.counters.data() + 2, st, fz.tc_mode == 2);
                 } else {
                     ProfScope ps(fz.ctx, sizeof(T) == 8 ? "schur_fp64" : "schur_fp32", fl, st);
                     k_panel_update<T><<<(unsigned)stp.n3, 256, 0, st>>>(dd, stp.nd, p.d_sn_fo.data(), p.d_sn_f.data(),

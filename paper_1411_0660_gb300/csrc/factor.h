@@ -26,7 +26,7 @@ struct Factorization {
     cudaGraphExec_t graph_exec = nullptr;  // captured solve sequence for block width graph_p
     int graph_p = 0;
     long long graph_nodes = 0;
-    bool use_tc = true;  // tcgen05 Schur updates for FP32 fronts
+    int tc_mode = 1;  // FP32 fronts' Schur updates: 0 CUDA cores, 1 tcgen05 3xTF32, 2 tcgen05 3xBF16
     // launch trace of the level-by-level solve (opt-in; recaptures the solve graph when switched)
     bool trace_on = false;
     DVec<LaunchTrace> trace;
@@ -42,9 +42,9 @@ struct Factorization {
 };
 
 // tcgen05 trailing update of one panel step (FP32 fronts); err counts bounded-wait time-outs.
-size_t schur_tc_smem();
+size_t schur_tc_smem(bool bf16);
 void launch_schur_tc(const PanelStep &stp, const PanelDesc *d_descs, const Plan &p, float *arena, const float *wscr,
-                     unsigned long long *err, cudaStream_t st);
+                     unsigned long long *err, cudaStream_t st, bool bf16);
 
 // Both sweeps of a block solve as dataflow kernels (solve_df.cu), between the permutations.
 template <class T>
@@ -60,7 +60,7 @@ void factor_solve_raw(Factorization &fz, const double *B, int64_t ldb, double *X
 std::shared_ptr<Plan> get_plan(mbl_sector *sec);
 // Create, allocate and run a factorization (synchronous; fills stats).
 std::unique_ptr<Factorization> make_factorization(mbl_sector *sec, double sigma, int prec, double hnorm,
-                                                  bool use_tc = true, bool dataflow = false);
+                                                  int tc_mode = 1, bool dataflow = false);
 
 }  // namespace mbl
 

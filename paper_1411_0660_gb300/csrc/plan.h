@@ -54,7 +54,7 @@ struct SolveDesc {
     int64_t offk;                    // prefix of backward row blocks (RBK rows of [k0, f)) in the step
     int64_t moff;                    // offset (elements) of M while it is built
     int64_t goff;                    // offset (elements) of G in the packed solve factor
-    int64_t offk_l;                  // prefix of backward row blocks within the level (level-wide launch)
+    int64_t offk_l;                  // prefix of backward-start row blocks within the level (level-wide launch)
     int32_t fdesc[SUBS];             // factor descriptors of the sub-panels (-1 if absent)
 };
 
@@ -75,6 +75,14 @@ struct SolveStep {
     int32_t maxw;                    // widest panel of the step (backward column chunks = ceil(maxw / RBB))
     int64_t fblk0, bblk0;            // first entries of the step in fblk_desc / bblk_desc
 };
+
+// Row blocks of a panel in the backward start: block 0 holds the panel's own w rows; the others cover
+// the contribution block from its first row (rounded down to 16 bytes) in RBK-row blocks; the rows of
+// the front's later panels are left to the updates.  cb0 = nc - k0 (first contribution row, relative).
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+inline int bwd_start_blocks(int R, int cb0) { return cb0 >= R ? 1 : 1 + (R - (cb0 & ~3) + RBK - 1) / RBK; }
 
 // Backward sweep, level by level: one launch over every panel of the level starts each panel's
 // accumulator acc_i = G_i^T [y_i; 0; -x_cb] (its own rows and the contribution block, whose x the

@@ -3,19 +3,23 @@
 // The dense contraction of the multifrontal LDL^T (numerical-method section of arXiv:1411.0660,
 // through the factorization of H - sigma): C[i][j] -= sum_t L21[i][t] W21[j][t] on the lower
 // triangle of the trailing block, K = panel width (<= 64).  FP32 data, FP32 accumulation.  Each
-// operand x is split into two TF32 pieces x = hi + lo (hi = x rounded to TF32, lo = x - hi), and
-// three kind::tf32 MMAs accumulate hi*hi + hi*lo + lo*hi into a 128 x 128 FP32 tile in tensor
-// memory (TMEM).  One CTA of 256 threads per tile; every memory access that does not depend on
-// the MMA is issued first so that their latencies overlap:
+// operand x is split into two pieces x = hi + lo (hi = x rounded to the piece format, lo = x - hi
+// rounded too), and three MMAs accumulate hi*hi + hi*lo + lo*hi into a 128 x 128 FP32 tile in
+// tensor memory (TMEM).  Two piece formats: TF32 (kind::tf32, 8 k per MMA; about 21 significant bits
+// kept) and BF16 (kind::f16 with BF16 operands, 16 k per MMA, twice the tensor rate per operand;
+// about 16 bits kept).  One CTA of 256 threads per tile; every memory access that does not depend
+// on the MMA is issued first so that their latencies overlap:
 //   1. the raw FP32 operand tiles go to shared memory by cp.async, and each thread loads its 64
 //      entries of the C tile (row = TMEM lane, half of the columns) into registers;
-//   2. the raw tiles are split into TF32 hi/lo pieces in the canonical K-major, no-swizzle
-//      core-matrix layout (8 rows x 16 bytes per core matrix), then fenced for the tensor core;
-//   3. one thread issues 3 * (K / 8) tcgen05.mma and a tcgen05.commit to an mbarrier;
+//   2. the raw tiles are split into hi/lo pieces in the canonical K-major, no-swizzle core-matrix
+//      layout (8 rows x 16 bytes per core matrix), then fenced for the tensor core;
+//   3. one thread issues 3 MMAs per k step and a tcgen05.commit to an mbarrier;
 //   4. all threads wait on the mbarrier (bounded by %globaltimer: on expiry the CTA flags an
 //      error, skips its epilogue, frees its TMEM and returns), read the accumulator with
 //      tcgen05.ld (warps w and w + 4 share TMEM lanes 32(w mod 4).., each taking 64 columns) and
 //      store C - acc, coalesced along the rows.
+#include <cuda_bf16.h>
+
 #include "factor.h"
 
 namespace mbl {
@@ -23,27 +27,34 @@ namespace mbl {
 namespace {
 
 constexpr int TM = 128, TN = 128, TK = NB;  // tile and maximal K
-constexpr int KG = TK / 4;                   // 16-byte k groups per row
 constexpr uint32_t CORE = 128;               // bytes per core matrix
-constexpr uint32_t SBO = KG * CORE;          // next 8-row group
 constexpr uint32_t LBO = CORE;               // next k group
-constexpr uint32_t OPB = TM * TK * 4;        // bytes per operand piece (32 KB)
 constexpr uint32_t TMEM_COLS = 128;
 constexpr int THREADS = 256;
 
-// instruction descriptor of kind::tf32: D = F32, A = B = TF32, both K-major, N = 128, M = 128
-constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TN >> 3) << 17) |
-                           ((uint32_t)(TM >> 4) << 24);
+// Piece format: bytes per element, elements per 16-byte k group, k per MMA, instruction descriptor
+// (D = F32, A = B = the piece format, both K-major, N = 128, M = 128).
+template <bool BF16>
+struct Piece {
+    static constexpr int EB = BF16 ? 2 : 4;
+    static constexpr int EPG = 16 / EB;          // k values per 16-byte group
+    static constexpr int KG = TK / EPG;          // 16-byte k groups per row
+    static constexpr uint32_t SBO = KG * CORE;   // next 8-row group
+    static constexpr uint32_t OPB = TM * TK * EB;  // bytes per operand piece
+    static constexpr int KMMA = 2 * EPG;         // k per MMA (two k groups)
+    static constexpr uint32_t IDESC = (1u << 4) | ((BF16 ? 1u : 2u) << 7) | ((BF16 ? 1u : 2u) << 10) |
+                                      ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+};
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t sbo) {
     uint64_t d = 0;
     d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
     d |= (uint64_t)((LBO >> 4) & 0x3FFFu) << 16;
-    d |= (uint64_t)((SBO >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
     d |= (uint64_t)1 << 46;  // fixed 0b001 at bits 46..48; base offset 0, no swizzle
     return d;
 }
@@ -100,11 +111,41 @@ __device__ __forceinline__ void cp_async4(float *smem, const float *gmem) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
 }
 
+// hi/lo pieces of 4 (TF32) or 8 (BF16) consecutive k values of one row, packed into 16 bytes
+__device__ __forceinline__ void split_group(const float *v, uint4 &hi, uint4 &lo, bool bf16) {
+    if (!bf16) {
+        uint32_t h[4], l[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            h[e] = to_tf32(v[e]);
+            l[e] = to_tf32(v[e] - __uint_as_float(h[e]));
+        }
+        hi = make_uint4(h[0], h[1], h[2], h[3]);
+        lo = make_uint4(l[0], l[1], l[2], l[3]);
+    } else {
+        uint32_t h[4], l[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const __nv_bfloat16 h0 = __float2bfloat16_rn(v[2 * e]), h1 = __float2bfloat16_rn(v[2 * e + 1]);
+            const __nv_bfloat16 l0 = __float2bfloat16_rn(v[2 * e] - __bfloat162float(h0));
+            const __nv_bfloat16 l1 = __float2bfloat16_rn(v[2 * e + 1] - __bfloat162float(h1));
+            h[e] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+            l[e] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+        }
+        hi = make_uint4(h[0], h[1], h[2], h[3]);
+        lo = make_uint4(l[0], l[1], l[2], l[3]);
+    }
+}
+
 }  // namespace
 
+template <bool BF16>
 __global__ void __launch_bounds__(THREADS) k_schur_tc(const PanelDesc *descs, int nd, const int64_t *fo,
                                                       const int32_t *fsz, float *arena, const float *wscr,
                                                       unsigned long long *err) {
+    using PC = Piece<BF16>;
+    constexpr uint32_t OPB = PC::OPB, SBO = PC::SBO;
+    constexpr int KG = PC::KG, EPG = PC::EPG;
     extern __shared__ __align__(1024) unsigned char sm[];
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tmem_slot;
@@ -158,23 +199,23 @@ __global__ void __launch_bounds__(THREADS) k_schur_tc(const PanelDesc *descs, in
     }
     asm volatile("cp.async.wait_group 0;" ::: "memory");
     __syncthreads();
-    // 2. TF32 hi/lo pieces in the canonical layout, one 16-byte core-matrix row per unit
+    // 2. hi/lo pieces in the canonical layout, one 16-byte core-matrix row per unit
     for (int u = threadIdx.x; u < TM * KG; u += THREADS) {
         const int r = u % TM, c = u / TM;
         const uint32_t off = (uint32_t)(r >> 3) * SBO + (uint32_t)(r & 7) * 16u + (uint32_t)c * CORE;
-        uint32_t ah[4], al[4], bh[4], bl[4];
+        float va[EPG], vb[EPG];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const float va = Araw[(4 * c + e) * TM + r], vb = Braw[(4 * c + e) * TM + r];
-            ah[e] = to_tf32(va);
-            al[e] = to_tf32(va - __uint_as_float(ah[e]));
-            bh[e] = to_tf32(vb);
-            bl[e] = to_tf32(vb - __uint_as_float(bh[e]));
+        for (int e = 0; e < EPG; ++e) {
+            va[e] = Araw[(EPG * c + e) * TM + r];
+            vb[e] = Braw[(EPG * c + e) * TM + r];
         }
-        *reinterpret_cast<uint4 *>(Ahi + off) = make_uint4(ah[0], ah[1], ah[2], ah[3]);
-        *reinterpret_cast<uint4 *>(Alo + off) = make_uint4(al[0], al[1], al[2], al[3]);
-        *reinterpret_cast<uint4 *>(Bhi + off) = make_uint4(bh[0], bh[1], bh[2], bh[3]);
-        *reinterpret_cast<uint4 *>(Blo + off) = make_uint4(bl[0], bl[1], bl[2], bl[3]);
+        uint4 hi, lo;
+        split_group(va, hi, lo, BF16);
+        *reinterpret_cast<uint4 *>(Ahi + off) = hi;
+        *reinterpret_cast<uint4 *>(Alo + off) = lo;
+        split_group(vb, hi, lo, BF16);
+        *reinterpret_cast<uint4 *>(Bhi + off) = hi;
+        *reinterpret_cast<uint4 *>(Blo + off) = lo;
     }
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
@@ -184,19 +225,25 @@ __global__ void __launch_bounds__(THREADS) k_schur_tc(const PanelDesc *descs, in
 
     // 3. the MMAs
     if (threadIdx.x == 0) {
-        const int ksteps = (w + 7) / 8;
+        const int ksteps = (w + PC::KMMA - 1) / PC::KMMA;
         uint32_t acc = 0;
         for (int ks = 0; ks < ksteps; ++ks) {
-            const uint32_t koff = (uint32_t)ks * 2u * CORE;  // two k groups per MMA (K = 8 TF32)
-            const uint64_t ah = sdesc(smem_u32(Ahi) + koff), al = sdesc(smem_u32(Alo) + koff);
-            const uint64_t bh = sdesc(smem_u32(Bhi) + koff), bl = sdesc(smem_u32(Blo) + koff);
+            const uint32_t koff = (uint32_t)ks * 2u * CORE;  // two k groups per MMA
+            const uint64_t ah = sdesc(smem_u32(Ahi) + koff, SBO), al = sdesc(smem_u32(Alo) + koff, SBO);
+            const uint64_t bh = sdesc(smem_u32(Bhi) + koff, SBO), bl = sdesc(smem_u32(Blo) + koff, SBO);
             const uint64_t as[3] = {ah, ah, al}, bs[3] = {bh, bl, bh};
 #pragma unroll
             for (int u = 0; u < 3; ++u) {
-                asm volatile(
-                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                    " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-                    "l"(as[u]), "l"(bs[u]), "r"(IDESC), "r"(acc));
+                if (BF16)
+                    asm volatile(
+                        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                        "l"(as[u]), "l"(bs[u]), "r"(PC::IDESC), "r"(acc));
+                else
+                    asm volatile(
+                        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                        "l"(as[u]), "l"(bs[u]), "r"(PC::IDESC), "r"(acc));
                 acc = 1;
             }
         }
@@ -228,17 +275,26 @@ __global__ void __launch_bounds__(THREADS) k_schur_tc(const PanelDesc *descs, in
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TMEM_COLS));
 }
 
-size_t schur_tc_smem() { return 4 * (size_t)OPB + 2 * (size_t)TK * TM * sizeof(float); }
+size_t schur_tc_smem(bool bf16) {
+    return 4 * (size_t)(bf16 ? Piece<true>::OPB : Piece<false>::OPB) + 2 * (size_t)TK * TM * sizeof(float);
+}
 
 void launch_schur_tc(const PanelStep &stp, const PanelDesc *d_descs, const Plan &p, float *arena, const float *wscr,
-                     unsigned long long *err, cudaStream_t st) {
+                     unsigned long long *err, cudaStream_t st, bool bf16) {
     static std::atomic<bool> attr{false};  // per process: one device
     if (!attr) {
-        MBL_CUDA(cudaFuncSetAttribute(k_schur_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)schur_tc_smem()));
+        MBL_CUDA(cudaFuncSetAttribute(k_schur_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)schur_tc_smem(false)));
+        MBL_CUDA(cudaFuncSetAttribute(k_schur_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)schur_tc_smem(true)));
         attr = true;
     }
-    k_schur_tc<<<(unsigned)stp.n3t, THREADS, schur_tc_smem(), st>>>(d_descs, stp.nd, p.d_sn_fo.data(), p.d_sn_f.data(), arena,
-                                                               wscr, err);
+    if (bf16)
+        k_schur_tc<true><<<(unsigned)stp.n3t, THREADS, schur_tc_smem(true), st>>>(
+            d_descs, stp.nd, p.d_sn_fo.data(), p.d_sn_f.data(), arena, wscr, err);
+    else
+        k_schur_tc<false><<<(unsigned)stp.n3t, THREADS, schur_tc_smem(false), st>>>(
+            d_descs, stp.nd, p.d_sn_fo.data(), p.d_sn_f.data(), arena, wscr, err);
     MBL_LAUNCH_CHECK();
 }
 

@@ -587,7 +587,7 @@ std::shared_ptr<Plan> build_plan(int L, const std::vector<uint32_t> &states, con
             for (int32_t q = d0; q < d1; ++q) {
                 SolveDesc &sd = p.sdescs[q];
                 sd.offk_l = nrbk;
-                const int32_t nb = (sd.w + sd.m2 + RBK - 1) / RBK;
+                const int32_t nb = bwd_start_blocks(sd.w + sd.m2, p.sn_nc[sd.front] - sd.k0);
                 for (int32_t b = 0; b < nb; ++b) p.lvl_bblk_desc.push_back(q - d0);
                 nrbk += nb;
                 maxw = std::max(maxw, sd.w);

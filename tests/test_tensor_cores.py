@@ -57,3 +57,48 @@ def test_tc_solve_near(g, ctx, orc, L, h, seed, eps, nev):
     assert window_equivalent(res.evals, e.evals, sigma, nev, hn)
     for j in range(nev):
         assert np.linalg.norm(H.matvec(res.evecs[:, j]) - res.evals[j] * res.evecs[:, j]) <= EIG_TOL * hn
+
+
+@pytest.mark.parametrize("L", [12, 16])
+def test_bf16x3_factor(g, ctx, orc, L):
+    """tcgen05 with split-BF16 operands (hi*hi + hi*lo + lo*hi, FP32 accumulation): the same inertia
+    as the CUDA-core factor, an unrefined solve within the expected loss of about 5 bits against
+    3xTF32, and FP64 refinement through it to the FP64 backward-error target."""
+    sec = g.build_sector(ctx, L, 3.0, 1)
+    lo, hi = g.extremal_bounds(sec)
+    sigma = lo + 0.45 * (hi - lo)
+    f_s = g.factor(sec, sigma, precision=1, tensor_cores=0)
+    f_b = g.factor(sec, sigma, precision=1, tensor_cores=2)
+    assert f_b.stats()["negative"] == f_s.stats()["negative"]
+    B = np.random.default_rng(3).standard_normal((sec.dim, 4))
+    X = f_s.solve(B, refine=True)
+    es = np.linalg.norm(f_s.solve(B, refine=False) - X) / np.linalg.norm(X)
+    eb = np.linalg.norm(f_b.solve(B, refine=False) - X) / np.linalg.norm(X)
+    assert eb < max(2000 * es, 1e-2)
+    H = orc.csr(L, orc.fields(L, 3.0, 1))
+    Xr = f_b.solve(B, refine=True)
+    hn = max(abs(lo), abs(hi))
+    for q in range(4):
+        r = H.matvec(Xr[:, q], sigma) - B[:, q]
+        assert np.linalg.norm(r) <= 1e-13 * ((hn + abs(sigma)) * np.linalg.norm(Xr[:, q]) + np.linalg.norm(B[:, q]))
+
+
+def test_bf16x3_solve_near(g, ctx, orc):
+    L, h, seed, eps, nev = 14, 2.0, 7, 0.5, 40
+    sec = g.build_sector(ctx, L, h, seed)
+    res = g.solve_near(sec, eps, nev, precision=1, tensor_cores=2)
+    H = orc.csr(L, orc.fields(L, h, seed))
+    emin, emax = orc.extremal_bounds(H)
+    hn = max(abs(emin), abs(emax))
+    sigma = emin + eps * (emax - emin)
+    e = orc.nearest_shift_invert(H, sigma, nev + 12, hn)
+    assert res.nconv == nev
+    assert window_equivalent(res.evals, e.evals, sigma, nev, hn)
+    for j in range(nev):
+        assert np.linalg.norm(H.matvec(res.evecs[:, j]) - res.evals[j] * res.evecs[:, j]) <= EIG_TOL * hn
+
+
+def test_tensor_core_mode_is_validated(g, ctx):
+    sec = g.build_sector(ctx, 10, 1.0, 2)
+    with pytest.raises(g.MblError):
+        g.factor(sec, 0.0, precision=1, tensor_cores=3)
