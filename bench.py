@@ -395,9 +395,9 @@ def main():
     d_s1 = torch.empty(NEV, dtype=torch.float64, device="cuda")
     d_se = torch.empty(NEV, dtype=torch.float64, device="cuda")
 
-    def device_job(h, seed, eps, prec):
+    def device_job(h, seed, eps, prec, tc=1):
         sec = g.build_sector(ctx, L, h, seed)
-        nconv, sigma, st = g.solve_near_dev(sec, eps, NEV, d_ev, d_vec, d_res, precision=prec)
+        nconv, sigma, st = g.solve_near_dev(sec, eps, NEV, d_ev, d_vec, d_res, precision=prec, tensor_cores=tc)
         g.observables_dev(ctx, L, NEV, d_ev, d_vec, d_r, d_rm, d_s1, d_se)
         sec.close()
         return nconv, st
@@ -510,14 +510,32 @@ def main():
                 "mixed_over_fp64": (p_mixed / t_mixed) / max(p64 / t64, 1e-30),
                 "served_mixed_over_fp64": value / max(p64 / (t64 / 1e3), 1e-30)}
         torch.cuda.synchronize()
+        # the same subset with split-BF16 Schur updates (3xBF16 on tcgen05), the third precision mode
+        a.record()
+        pbf, evbf, bf_solves = 0, {}, 0
+        for i in sub:
+            h, seed, eps = timed_jobs[i]
+            nc, st = device_job(h, seed, eps, g.MBL_PREC_FP32, tc=2)
+            pbf += nc
+            bf_solves += st["solves"]
+            evbf[i] = d_ev.clone()
+        b.record()
+        torch.cuda.synchronize()
+        tbf = a.elapsed_time(b)
         # per result: mixed-precision eigenvalues against the FP64 path's, relative to ||H|| ~ |E| scale
+        bf_dev = 0.0
         for i in sub:
             h, seed, eps = timed_jobs[i]
             sec = g.build_sector(ctx, L, h, seed)
             lo, hi = g.extremal_bounds(sec)
             sec.close()
+            hn_i = max(abs(lo), abs(hi))
             d = (ev_mixed[i] - ev64[i]).abs().max().item()
-            job_stats[i]["max_dev_vs_fp64"] = d / max(abs(lo), abs(hi))
+            job_stats[i]["max_dev_vs_fp64"] = d / hn_i
+            bf_dev = max(bf_dev, (evbf[i] - ev64[i]).abs().max().item() / hn_i)
+        fp64["bf16x3_same_jobs"] = {"value": pbf / (tbf / 1e3), "ms_per_job": tbf / len(sub), "converged": pbf,
+                                    "solves": bf_solves, "mixed_tf32x3_solves": sum(job_stats[i]["solves"] for i in sub),
+                                    "max_dev_vs_fp64": bf_dev}
 
     # ---- end to end: the timed served region itself, on the host clock (host fields in; eigenvalues,
     # residuals, observables and eigenvectors back in host memory) ----
