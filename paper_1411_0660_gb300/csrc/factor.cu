@@ -209,10 +209,11 @@ __global__ void __launch_bounds__(256) k_panel_diag(const PanelDesc *descs, cons
         }
         __syncthreads();
         if (tid == 0) B[t][t] = dv;
-        const int m = w - t - 1;
-        for (int idx = tid; idx < m * m; idx += bd) {
-            int r = t + 1 + idx % m, c = t + 1 + idx / m;
-            if (r >= c) B[r][c] -= lcol[r] * B[c][t];
+        // trailing update of the lower triangle: lane -> rows (stride 32), warp -> columns (stride
+        // bd / 32), no index division
+        for (int c = t + 1 + wp; c < w; c += bd >> 5) {
+            const T lc = B[c][t];
+            for (int r = c + lane; r < w; r += 32) B[r][c] -= lcol[r] * lc;
         }
         __syncthreads();
     }
