@@ -274,7 +274,10 @@ def run_workload(args):
                 seeds, nev = 50, FP64 fronts, all submitted at once to a server of `--slots` streams;
     serve    -- a serving stream: Poisson arrivals (`--rate` per second, `--requests` requests) of
                 L in {14, 16, 18, 20} weighted 4:3:2:1, h ~ U[0.5, 5], seed = request id,
-                eps ~ U[0.05, 0.95], nev = 50, mixed precision; p50/p99 latency and throughput."""
+                eps ~ U[0.05, 0.95], nev = 50, mixed precision; p50/p99 latency and throughput;
+    large    -- the large sizes: L = 20, h = 3, `--seeds` seeds x eps in {0.2, 0.5, 0.8}, nev = 50, mixed
+                precision through the server; plus the symbolic analysis (fill-in, flops, device
+                footprint) of L = 18, 20 and 22, whose L = 22 fronts do not fit in one GPU."""
     import numpy as np
     import torch
 
@@ -282,7 +285,24 @@ def run_workload(args):
 
     ctx = g.Context(0)
     srv = g.Server(ctx, slots=args.slots)
-    if args.workload == "l16batch":
+    plans = None
+    if args.workload == "large":
+        dev_total = torch.cuda.get_device_properties(0).total_memory
+        plans = {}
+        for L_ in (18, 20, 22):
+            sec = g.build_sector(ctx, L_, 3.0, 0)
+            pst = g.analyse(sec, 50, 8)
+            sec.close()
+            pst["fits_one_gpu_fp32"] = pst["job_peak_bytes_fp32"] < 0.85 * dev_total
+            plans[str(L_)] = pst
+        jobs = [(20, 3.0, s, e, g.MBL_PREC_FP32) for s in range(args.seeds) for e in (0.2, 0.5, 0.8)]
+        srv.wait(srv.submit(20, 3.0, 10 ** 6, 0.5, 50))  # warm-up: kernels and graphs at L = 20
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        tickets = [srv.submit(L_, h, s, e, 50, precision=pr) for (L_, h, s, e, pr) in jobs]
+        out = [srv.wait(t) for t in tickets]
+        host_s = time.perf_counter() - t0
+    elif args.workload == "l16batch":
         jobs = [(16, h, s, e / 10.0, g.MBL_PREC_FP64) for s in range(args.seeds) for h in (1.0, 2.5, 4.0)
                 for e in range(1, 10)]
         for t in [srv.submit(16, 1.0, 10 ** 6 + k, 0.5, 50, precision=g.MBL_PREC_FP64) for k in range(args.slots)]:
@@ -326,6 +346,9 @@ def run_workload(args):
             "failed": st["failed"],
             "not_converged": [{"L": int(j[0]), "h": float(j[1]), "seed": int(j[2]), "eps": float(j[3]),
                                "nconv": r.nconv, "status": r.status} for j, r in zip(jobs, out) if r.status != 0]}
+    if plans is not None:
+        line["plans"] = plans
+        line["job_s"] = sorted(round((r.d_end_ms - r.d_start_ms) / 1e3, 2) for r in out)
     if args.workload == "serve":
         line.update({"rate_per_s": args.rate, "by_L": {str(L_): sum(1 for j in jobs if j[0] == L_) for L_ in (14, 16, 18, 20)}})
     print(json.dumps(line))
@@ -338,7 +361,7 @@ def main():
     ap.add_argument("--case", choices=["factor", "solve", "observables"], default=None,
                     help="run one factorization (and --reps solves) instead of the benchmark")
     ap.add_argument("--L", type=int, default=18)
-    ap.add_argument("--workload", choices=["l18", "l16batch", "serve"], default="l18",
+    ap.add_argument("--workload", choices=["l18", "l16batch", "serve", "large"], default="l18",
                     help="l18: the benchmark line; l16batch / serve: the batched and serving configurations")
     ap.add_argument("--seeds", type=int, default=8, help="l16batch: seeds per (h, eps)")
     ap.add_argument("--requests", type=int, default=40, help="serve: number of requests")

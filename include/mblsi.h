@@ -159,6 +159,22 @@ int mbl_factor_stats_get(const mbl_factorization *f, mbl_factor_stats *stats);
 /* x = (H - sigma)^-1 b for nrhs right-hand sides (host, n x nrhs column-major), with FP64
  * iterative refinement when `refine` is nonzero. */
 int mbl_factor_solve(mbl_factorization *f, const double *b, double *x, int nrhs, int refine);
+/* Symbolic analysis of the sector's pattern (nested-dissection ordering, supernodes, schedules;
+ * numerical-method section: the analysis phase of the direct solver), built on the host on first
+ * use for this L and cached in the context, and its predicted fill-in and device footprint.  No
+ * numeric factorization runs, so this works for sizes whose fronts would not fit in memory.
+ * job_peak_* is the serving admission estimate of one solve_near job with (nev, block). */
+typedef struct mbl_plan_stats {
+    int64_t n, nnz_l, n_supernodes, max_front, tree_levels, panel_steps, solve_steps;
+    double flops;                   /* algorithmic factorization flops */
+    double ms_analyse;              /* host time of the analysis when it was built */
+    double factor_bytes_fp32, factor_bytes_fp64;  /* entries of L and D */
+    double front_bytes_fp32, front_bytes_fp64;    /* the fronts arena (alive during the factorization) */
+    double solve_factor_bytes_fp32;               /* packed G of the solve panels (alive with the factor) */
+    double job_peak_bytes_fp32, job_peak_bytes_fp64;
+} mbl_plan_stats;
+int mbl_analyse(mbl_sector *sec, int nev, int block, mbl_plan_stats *stats);
+
 /* Launch trace of the level-by-level triangular solve, a diagnostic with no counterpart in the
  * paper.  With on != 0 every later solve of f records, for each kernel launch of its sequence, the
  * device clock (%globaltimer, ns) when the launch's first CTA started and when its last CTA

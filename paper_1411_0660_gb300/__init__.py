@@ -19,7 +19,7 @@ from dataclasses import dataclass
 import numpy as np
 
 from . import _capi
-from ._capi import MBL_PREC_FP32, MBL_PREC_FP64, FactorStats, Opts, SolveStats
+from ._capi import MBL_PREC_FP32, MBL_PREC_FP64, FactorStats, Opts, PlanStats, SolveStats
 
 __all__ = ["Context", "Sector", "Factorization", "MblError", "build_sector", "build_sector_fields",
            "extremal_bounds", "factor", "solve_near", "solve_near_dev", "observables", "observables_dev",
@@ -165,6 +165,13 @@ def extremal_bounds(sec: Sector):
     lo, hi = ctypes.c_double(), ctypes.c_double()
     _check(_lib().mbl_extremal_bounds(sec.handle, ctypes.byref(lo), ctypes.byref(hi)), sec.ctx.handle)
     return lo.value, hi.value
+
+
+def analyse(sec: Sector, nev: int = 50, block: int = 8) -> dict:
+    """Symbolic analysis of the sector's L (cached): predicted fill-in, flops and device footprint."""
+    s = PlanStats()
+    _check(_lib().mbl_analyse(sec.handle, nev, block, ctypes.byref(s)), sec.ctx.handle)
+    return {f: getattr(s, f) for f, _ in PlanStats._fields_}
 
 
 class Factorization:

@@ -36,6 +36,15 @@ class FactorStats(ctypes.Structure):
                 ("max_abs_l", c_double), ("min_abs_d", c_double)]
 
 
+class PlanStats(ctypes.Structure):
+    _fields_ = [("n", c_int64), ("nnz_l", c_int64), ("n_supernodes", c_int64), ("max_front", c_int64),
+                ("tree_levels", c_int64), ("panel_steps", c_int64), ("solve_steps", c_int64), ("flops", c_double),
+                ("ms_analyse", c_double), ("factor_bytes_fp32", c_double), ("factor_bytes_fp64", c_double),
+                ("front_bytes_fp32", c_double), ("front_bytes_fp64", c_double),
+                ("solve_factor_bytes_fp32", c_double), ("job_peak_bytes_fp32", c_double),
+                ("job_peak_bytes_fp64", c_double)]
+
+
 class SolveStats(ctypes.Structure):
     _fields_ = [("restarts", c_int), ("op_applies", c_int), ("solves", c_int), ("fp64_fallback", c_int),
                 ("krylov_dim", c_int), ("max_resid", c_double), ("ms_total", c_double), ("ms_factor", c_double)]
@@ -90,6 +99,7 @@ SIGNATURES = [
                                P(c_double), P(SolveStats)]),
     ("mbl_solve_near_dev", c_int, [c_void_p, c_double, c_int, P(Opts), c_void_p, c_void_p, c_void_p, P(c_int),
                                    P(c_double), P(SolveStats), c_void_p]),
+    ("mbl_analyse", c_int, [c_void_p, c_int, c_int, P(PlanStats)]),
     ("mbl_factor_trace", c_int, [c_void_p, c_int]),
     ("mbl_factor_trace_get", c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int, P(c_int)]),
     ("mbl_observables", c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,

@@ -502,6 +502,32 @@ int mbl_factor_stats_get(const mbl_factorization *fh, mbl_factor_stats *s) {
     return MBL_OK;
 }
 
+int mbl_analyse(mbl_sector *sec, int nev, int block, mbl_plan_stats *s) {
+    if (!sec || !s) return report(nullptr, MBL_ERR_INVALID, "NULL argument");
+    if (nev < 1 || block < 1 || block > 32) return report(sec->ctx, MBL_ERR_INVALID, "nev >= 1, block in 1..32");
+    API_TRY
+    MBL_CUDA(cudaSetDevice(sec->ctx->device));
+    std::shared_ptr<Plan> P = get_plan(sec);
+    const Plan &p = *P;
+    s->n = p.n;
+    s->nnz_l = p.nnz_l;
+    s->n_supernodes = p.ns;
+    s->max_front = p.max_front;
+    s->tree_levels = p.nlevels;
+    s->panel_steps = (int64_t)p.steps.size();
+    s->solve_steps = (int64_t)p.ssteps.size();
+    s->flops = p.flops;
+    s->ms_analyse = p.ms_analyse;
+    s->factor_bytes_fp32 = (double)(p.nnz_l + p.n) * 4.0;
+    s->factor_bytes_fp64 = (double)(p.nnz_l + p.n) * 8.0;
+    s->front_bytes_fp32 = (double)p.arena_elems * 4.0;
+    s->front_bytes_fp64 = (double)p.arena_elems * 8.0;
+    s->solve_factor_bytes_fp32 = (double)p.sg_elems * 4.0;
+    s->job_peak_bytes_fp32 = (double)job_bytes(p, nev, block, MBL_PREC_FP32);
+    s->job_peak_bytes_fp64 = (double)job_bytes(p, nev, block, MBL_PREC_FP64);
+    API_CATCH(sec->ctx)
+}
+
 int mbl_factor_trace(mbl_factorization *fh, int on) {
     if (!fh) return report(nullptr, MBL_ERR_INVALID, "NULL argument");
     Factorization &f = *fh->f;

@@ -56,6 +56,8 @@ void numeric_factor(Factorization &fz, cudaStream_t st);
 void factor_solve_raw(Factorization &fz, const double *B, int64_t ldb, double *X, int64_t ldx, int p, bool accumulate,
                       cudaStream_t st);
 
+// Upper estimate of the device bytes one solve_near job holds at its peak (serving admission).
+size_t job_bytes(const Plan &p, int nev, int block, int prec);
 // Plan of the sector's L (built from the device CSR on first use and cached in the context).
 std::shared_ptr<Plan> get_plan(mbl_sector *sec);
 // Create, allocate and run a factorization (synchronous; fills stats).

@@ -20,12 +20,6 @@
 
 namespace mbl {
 
-namespace {
-
-double now_ms(std::chrono::steady_clock::time_point t0) {
-    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-}
-
 // Upper estimate of the device bytes one job holds at its peak (plan of its L known).
 size_t job_bytes(const Plan &p, int nev, int block, int prec) {
     const double n = (double)p.n, es = prec == MBL_PREC_FP64 ? 8.0 : 4.0;
@@ -42,6 +36,12 @@ size_t job_bytes(const Plan &p, int nev, int block, int prec) {
     b += 8.0 * n * (3.0 * ldv + 2.0 * nev + 30.0 * pb);                      // Krylov, Rayleigh-Ritz, refinement
     b += 8.0 * n * 480.0;                                                    // extremal-bounds Lanczos basis
     return (size_t)(1.10 * b) + ((size_t)64 << 20);
+}
+
+namespace {
+
+double now_ms(std::chrono::steady_clock::time_point t0) {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
 }
 
 struct Job {

@@ -248,3 +248,17 @@ def test_invalid_arguments(g, ctx):
         g.solve_near(sec, 0.5, 0)
     with pytest.raises(g.MblError):
         g.solve_near(sec, 0.5, sec.dim + 1)
+
+
+def test_analyse_matches_factorization(g, ctx):
+    """The symbolic analysis alone predicts what a factorization then reports."""
+    sec = g.build_sector(ctx, 14, 2.0, 3)
+    a = g.analyse(sec, 50, 8)
+    f = g.factor(sec, 0.1, precision=1)
+    st = f.stats()
+    assert a["nnz_l"] == st["nnz_l"] and a["n"] == st["n"] and a["max_front"] == st["max_front"]
+    assert a["flops"] == st["flops"] and a["tree_levels"] == st["tree_levels"]
+    assert a["front_bytes_fp32"] == st["front_bytes"]
+    assert a["job_peak_bytes_fp64"] > a["job_peak_bytes_fp32"] > a["front_bytes_fp32"]
+    with pytest.raises(g.MblError):
+        g.analyse(sec, 0, 8)
