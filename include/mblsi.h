@@ -159,6 +159,12 @@ int mbl_factor_stats_get(const mbl_factorization *f, mbl_factor_stats *stats);
 /* x = (H - sigma)^-1 b for nrhs right-hand sides (host, n x nrhs column-major), with FP64
  * iterative refinement when `refine` is nonzero. */
 int mbl_factor_solve(mbl_factorization *f, const double *b, double *x, int nrhs, int refine);
+/* Device variant: d_b and d_x are device FP64 arrays, n x nrhs column-major (leading dimension n),
+ * owned by the caller and distinct.  The solve is enqueued on `stream` (a cudaStream_t; NULL = the
+ * context's stream) and the call returns once it has completed there.  A factorization serves one
+ * call at a time.  Unrefined solves (refine = 0) run without device allocation; MBL_ERR_TIMEOUT if
+ * a bounded dependency wait of the solve kernels expired. */
+int mbl_factor_solve_dev(mbl_factorization *f, const double *d_b, double *d_x, int nrhs, int refine, void *stream);
 /* Symbolic analysis of the sector's pattern (nested-dissection ordering, supernodes, schedules;
  * numerical-method section: the analysis phase of the direct solver), built on the host on first
  * use for this L and cached in the context, and its predicted fill-in and device footprint.  No

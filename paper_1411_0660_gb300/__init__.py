@@ -209,6 +209,13 @@ class Factorization:
                self.sec.ctx.handle)
         return X[:, 0] if np.ndim(b) == 1 else X
 
+    def solve_dev(self, d_b, d_x, nrhs: int, refine: bool = False, stream=None):
+        """Device variant of solve: d_b, d_x are float64 CUDA tensors holding n x nrhs column-major
+        blocks (nrhs contiguous vectors of length n)."""
+        s = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
+        _check(_lib().mbl_factor_solve_dev(self.handle, ctypes.c_void_p(d_b.data_ptr()), ctypes.c_void_p(d_x.data_ptr()),
+                                           nrhs, 1 if refine else 0, s), self.sec.ctx.handle)
+
     def close(self):
         if getattr(self, "handle", None):
             _lib().mbl_factor_destroy(self.handle)

@@ -94,6 +94,7 @@ SIGNATURES = [
     ("mbl_factor", c_int, [c_void_p, c_double, P(Opts), P(c_void_p)]),
     ("mbl_factor_stats_get", c_int, [c_void_p, P(FactorStats)]),
     ("mbl_factor_solve", c_int, [c_void_p, c_void_p, c_void_p, c_int, c_int]),
+    ("mbl_factor_solve_dev", c_int, [c_void_p, c_void_p, c_void_p, c_int, c_int, c_void_p]),
     ("mbl_factor_destroy", None, [c_void_p]),
     ("mbl_solve_near", c_int, [c_void_p, c_double, c_int, P(Opts), c_void_p, c_void_p, c_void_p, P(c_int),
                                P(c_double), P(SolveStats)]),

@@ -595,6 +595,40 @@ int mbl_factor_solve(mbl_factorization *fh, const double *b, double *x, int nrhs
     API_CATCH(ctx)
 }
 
+int mbl_factor_solve_dev(mbl_factorization *fh, const double *d_b, double *d_x, int nrhs, int refine, void *stream) {
+    if (!fh || !d_b || !d_x || nrhs < 1) return report(nullptr, MBL_ERR_INVALID, "bad argument");
+    Factorization &f = *fh->f;
+    Ctx *ctx = f.ctx;
+    API_TRY
+    cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : ctx->stream;
+    const int64_t n = f.plan->n;
+    if (!refine) {
+        for (int c0 = 0; c0 < nrhs; c0 += 32)
+            factor_solve_colmajor(f, d_b + (size_t)c0 * n, d_x + (size_t)c0 * n, std::min(32, nrhs - c0), st);
+    } else {
+        double emin, emax;
+        extremal_bounds(f.sec, &emin, &emax);
+        const double hn = std::max(std::fabs(emin), std::fabs(emax));
+        RefinedSolve rs{f.sec, &f, hn + std::fabs(f.sigma), 1e-15, 20};
+        rs.gmres = 1;
+        if (f.dev_b.size() < (size_t)n * 32) {
+            f.dev_b.alloc(ctx, (size_t)n * 32);
+            f.dev_x.alloc(ctx, (size_t)n * 32);
+        }
+        for (int c0 = 0; c0 < nrhs; c0 += 32) {
+            const int p = std::min(32, nrhs - c0);
+            for (int q = 0; q < p; ++q) copy_cols(n, d_b + (size_t)(c0 + q) * n, 1, 0, f.dev_b.data(), p, q, 1, st);
+            rs.apply(f.dev_b.data(), p, f.dev_x.data(), p, st);
+            for (int q = 0; q < p; ++q) copy_cols(n, f.dev_x.data(), p, q, d_x + (size_t)(c0 + q) * n, 1, 0, 1, st);
+        }
+    }
+    MBL_CUDA(cudaStreamSynchronize(st));
+    unsigned long long tmo = 0;
+    MBL_CUDA(cudaMemcpy(&tmo, f.counters.data() + 2, sizeof(tmo), cudaMemcpyDeviceToHost));
+    if (tmo != 0) fail(MBL_ERR_TIMEOUT, "a triangular-solve dependency wait timed out");
+    API_CATCH(ctx)
+}
+
 void mbl_factor_destroy(mbl_factorization *f) {
     if (!f) return;
     if (f->f && ctx_alive(f->f->ctx)) cudaStreamSynchronize(f->f->ctx->stream);

@@ -363,23 +363,26 @@ __global__ void __launch_bounds__(256) k_panel_update(const PanelDesc *descs, in
 // z_panel <- M^T (z_panel - L21^T x_below).  Own rows of a front hold pivoted-order values
 // between the two sweeps (Zs / yfw); the backward sweep leaves true-order values.
 // ------------------------------------------------------------------------------------------
+// B, X: entry (row r, right-hand side q) at r * ld + q * ldq (row-major blocks: ldq = 1;
+// column-major: ld = 1, ldq = n).
 template <class T>
-__global__ void k_perm_in(int64_t n, int p, const int32_t *perm, const double *B, int64_t ldb, T *y) {
+__global__ void k_perm_in(int64_t n, int p, const int32_t *perm, const double *B, int64_t ldb, int64_t ldbq, T *y) {
     int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= n * p) return;
     int64_t k = idx / p;
     int q = (int)(idx - k * p);
-    y[idx] = (T)B[(int64_t)perm[k] * ldb + q];
+    y[idx] = (T)B[(int64_t)perm[k] * ldb + q * ldbq];
 }
 
 template <class T>
-__global__ void k_perm_out(int64_t n, int p, const int32_t *perm, const T *x, double *X, int64_t ldx, int accumulate) {
+__global__ void k_perm_out(int64_t n, int p, const int32_t *perm, const T *x, double *X, int64_t ldx, int64_t ldxq,
+                           int accumulate) {
     int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= n * p) return;
     int64_t k = idx / p;
     int q = (int)(idx - k * p);
     double v = (double)x[idx];
-    double *dst = X + (int64_t)perm[k] * ldx + q;
+    double *dst = X + (int64_t)perm[k] * ldx + q * ldxq;
     *dst = accumulate ? *dst + v : v;
 }
 
@@ -539,7 +542,6 @@ __global__ void __launch_bounds__(256) k_fwd_step(const SolveDesc *sdescs, const
     constexpr int NH = (SPW + 255) / 256, NPF = sizeof(T) == 4 ? NH : 1;
     extern __shared__ __align__(16) unsigned char smraw[];
     T *zp = reinterpret_cast<T *>(smraw);  // SPW x PB; afterwards the 8 x PB x RBF partials
-    pdl_trigger();
     const int di = blk_desc[blockIdx.x];
     const SolveDesc d = sdescs[di];
     const int s = d.front, k0 = d.k0, w = d.w;
@@ -569,6 +571,7 @@ __global__ void __launch_bounds__(256) k_fwd_step(const SolveDesc *sdescs, const
         dg[u] = (i < nr && q < p && rr < w) ? Dg[(int64_t)sn_start[s] + k0 + rr] : T(1);
     }
     pdl_wait();
+    pdl_trigger();
     for (int idx = threadIdx.x; idx < w * PB; idx += blockDim.x) {
         int c = idx / PB, q = idx % PB;
         zp[idx] = q < p ? Z[(zb + c) * p + q] : T(0);
@@ -634,7 +637,6 @@ __global__ void __launch_bounds__(256) k_fwd_narrow(const SolveDesc *sdescs, con
                                                     const T *Dg, T *Z, T *Zs, T *yfw, int p, LaunchTrace *tr) {
     static_assert(RBF == 32, "one warp per row block");
     TraceScope trace_scope(tr);
-    pdl_trigger();
     const int lane = threadIdx.x & 31, item = blockIdx.x * 8 + (threadIdx.x >> 5);
     if (item >= nblk) {
         pdl_wait();
@@ -650,6 +652,7 @@ __global__ void __launch_bounds__(256) k_fwd_narrow(const SolveDesc *sdescs, con
     for (int c = 0; c < 32; ++c) gl[c] = (c < w && r < R) ? G[(int64_t)c * ld] : T(0);
     const T dg = r < w ? Dg[g0 + r] : T(1);
     pdl_wait();
+    pdl_trigger();
     T zr[PB], zold[PB];
 #pragma unroll
     for (int q = 0; q < PB; ++q) {
@@ -688,7 +691,6 @@ __global__ void __launch_bounds__(256) k_bwd_narrow(const SolveDesc *sdescs, int
                                                     const int64_t *rows_off, const int32_t *rows, const T *Gp,
                                                     const T *yfw, T *Zs, T *x, int p, LaunchTrace *tr) {
     TraceScope trace_scope(tr);
-    pdl_trigger();
     const int lane = threadIdx.x & 31, di = blockIdx.x * 8 + (threadIdx.x >> 5);
     if (di >= nd) {
         pdl_wait();
@@ -704,6 +706,7 @@ __global__ void __launch_bounds__(256) k_bwd_narrow(const SolveDesc *sdescs, int
     for (int j = 0; j < 32; ++j) gl[j] = (lane < w && j < R) ? G[j] : T(0);
     const int rowx = lane < R && k0 + lane >= ncs ? rw[lane] : 0;
     pdl_wait();
+    pdl_trigger();
     T acc[PB];
 #pragma unroll
     for (int q = 0; q < PB; ++q) acc[q] = T(0);
@@ -762,7 +765,6 @@ __global__ void __launch_bounds__(256) k_bwd_update(const SolveDesc *sdescs, con
     T *Gs = reinterpret_cast<T *>(smraw);    // RBB columns x bwd_ldg rows
     T *vs = Gs + RBB * bwd_ldg<T>();         // RBK x PB
     T *red = PB == 8 ? Gs : vs + RBK * PB;  // 8 warps x 8 x RBB partial sums
-    pdl_trigger();
     const SolveDesc di = sdescs[items[2 * blockIdx.x]], dj = sdescs[items[2 * blockIdx.x + 1]];
     const int cc = blockIdx.y * RBB;
     if (cc >= di.w) {
@@ -775,6 +777,7 @@ __global__ void __launch_bounds__(256) k_bwd_update(const SolveDesc *sdescs, con
     const int64_t zi = zo[s] + di.k0 + cc, zj = zo[s] + dj.k0;
     const bool fin = dj.k0 == di.k0 + di.w;
     pdl_wait();
+    pdl_trigger();
     {
         static_assert(RBK == 256, "one row of v per thread");
         const int r = threadIdx.x;
@@ -826,7 +829,6 @@ template <class T>
 __global__ void k_fwd_gather_rows(int64_t nrows, const int64_t *dst, const int64_t *own, const int64_t *cptr,
                                   const int64_t *src, const T *y, T *Z, int p, LaunchTrace *tr) {
     TraceScope trace_scope(tr);
-    pdl_trigger();
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t row = t / p;
     const int q = (int)(t - row * p);
@@ -838,6 +840,7 @@ __global__ void k_fwd_gather_rows(int64_t nrows, const int64_t *dst, const int64
         c1 = cptr[row + 1];
     }
     pdl_wait();
+    pdl_trigger();
     if (row >= nrows) return;
     T v = o >= 0 ? y[o * p + q] : T(0);
     for (int64_t c = c0; c < c1; ++c) v += Z[src[c] * p + q];
@@ -867,7 +870,6 @@ __global__ void __launch_bounds__(256) k_bwd_step(const SolveDesc *sdescs, const
     T *vs = Gs + RBB * bwd_ldg<T>();         // RBK x PB
     T *red = PB == 8 ? Gs : vs + RBK * PB;  // 8 warps x 8 x RBB partial sums
     __shared__ int s_last;
-    pdl_trigger();
     const int di = blk_desc[blockIdx.x];
     const SolveDesc d = sdescs[di];
     const int cc = blockIdx.y * RBB;
@@ -889,6 +891,7 @@ __global__ void __launch_bounds__(256) k_bwd_step(const SolveDesc *sdescs, const
     const int64_t src = kind == 1 ? ((int64_t)sn_start[s] + k0 + rr) * p
                       : kind == 3 ? (int64_t)rows[rows_off[s] + k0 + rr] * p : 0;
     pdl_wait();
+    pdl_trigger();
     {
         T *vr = vs + i * PB;
         if (kind == 0) {
@@ -1146,8 +1149,8 @@ static void solve_levels_p(Factorization &fz, int p, cudaStream_t st) {
 }
 
 template <class T>
-static void solve_impl(Factorization &fz, const double *B, int64_t ldb, double *X, int64_t ldx, int p, bool accumulate,
-                       cudaStream_t st) {
+static void solve_impl(Factorization &fz, const double *B, int64_t ldb, int64_t ldbq, double *X, int64_t ldx,
+                       int64_t ldxq, int p, bool accumulate, cudaStream_t st) {
     Plan &pl = *fz.plan;
     int64_t n = pl.n;
     fz.ensure_solve_work(p);
@@ -1157,7 +1160,7 @@ static void solve_impl(Factorization &fz, const double *B, int64_t ldb, double *
     unsigned g = (unsigned)((tot + 255) / 256);
     ProfScope ps(fz.ctx, sizeof(T) == 8 ? "trisolve_fp64" : "trisolve_fp32",
                  2.0 * (double)(pl.nnz_l + n) * sizeof(T) + 16.0 * (double)n * p, st);
-    k_perm_in<T><<<g, 256, 0, st>>>(n, p, pl.d_perm.data(), B, ldb, y);
+    k_perm_in<T><<<g, 256, 0, st>>>(n, p, pl.d_perm.data(), B, ldb, ldbq, y);
     MBL_LAUNCH_CHECK();
     // the fixed sequence of ~(levels + 4 x solve steps) launches is captured once per block width
     // and replayed as a CUDA graph
@@ -1188,15 +1191,22 @@ static void solve_impl(Factorization &fz, const double *B, int64_t ldb, double *
     }
     MBL_CUDA(cudaGraphLaunch(fz.graph_exec, st));
     g_launches.fetch_add(fz.graph_nodes);
-    k_perm_out<T><<<g, 256, 0, st>>>(n, p, pl.d_perm.data(), y, X, ldx, accumulate ? 1 : 0);
+    k_perm_out<T><<<g, 256, 0, st>>>(n, p, pl.d_perm.data(), y, X, ldx, ldxq, accumulate ? 1 : 0);
     MBL_LAUNCH_CHECK();
 }
 
 void factor_solve_raw(Factorization &fz, const double *B, int64_t ldb, double *X, int64_t ldx, int p, bool accumulate,
                       cudaStream_t st) {
     if (p < 1 || p > 32) fail(MBL_ERR_INVALID, "solve: 1 <= nrhs <= 32 per block");
-    if (fz.prec == MBL_PREC_FP64) solve_impl<double>(fz, B, ldb, X, ldx, p, accumulate, st);
-    else solve_impl<float>(fz, B, ldb, X, ldx, p, accumulate, st);
+    if (fz.prec == MBL_PREC_FP64) solve_impl<double>(fz, B, ldb, 1, X, ldx, 1, p, accumulate, st);
+    else solve_impl<float>(fz, B, ldb, 1, X, ldx, 1, p, accumulate, st);
+}
+
+void factor_solve_colmajor(Factorization &fz, const double *B, double *X, int p, cudaStream_t st) {
+    if (p < 1 || p > 32) fail(MBL_ERR_INVALID, "solve: 1 <= nrhs <= 32 per block");
+    const int64_t n = fz.plan->n;
+    if (fz.prec == MBL_PREC_FP64) solve_impl<double>(fz, B, 1, n, X, 1, n, p, false, st);
+    else solve_impl<float>(fz, B, 1, n, X, 1, n, p, false, st);
 }
 
 void Factorization::ensure_solve_work(int p) {

@@ -30,6 +30,7 @@ struct Factorization {
     // launch trace of the level-by-level solve (opt-in; recaptures the solve graph when switched)
     bool trace_on = false;
     DVec<LaunchTrace> trace;
+    DVec<double> dev_b, dev_x;  // row-major right-hand-side blocks of refined device solves (n x 32)
     std::vector<int> trace_kind;  // per traced launch: 0 forward gather, 1 forward step, 2/3 backward start/update
     int64_t perturbed = 0, negative = 0;
     double ms_factor = 0.0;
@@ -55,6 +56,8 @@ void numeric_factor(Factorization &fz, cudaStream_t st);
 // X (n x p row-major FP64, row stride ldx) (+)= (L D L^T)^-1 B, B row stride ldb; 1 <= p <= 32.
 void factor_solve_raw(Factorization &fz, const double *B, int64_t ldb, double *X, int64_t ldx, int p, bool accumulate,
                       cudaStream_t st);
+// X = (L D L^T)^-1 B for column-major n x p FP64 blocks (leading dimension n); 1 <= p <= 32.
+void factor_solve_colmajor(Factorization &fz, const double *B, double *X, int p, cudaStream_t st);
 
 // Upper estimate of the device bytes one solve_near job holds at its peak (serving admission).
 size_t job_bytes(const Plan &p, int nev, int block, int prec);
