@@ -915,22 +915,6 @@ __global__ void k_lanczos_norm_part(int64_t n, const double *w, double *part) {
     }
 }
 
-__global__ void k_lanczos_coef(int nb, const double *part, int j, const double *c1, const double *c2, double *alpha,
-                               double *beta) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    double s = 0.0;
-    for (int b = 0; b < nb; ++b) s += part[b];
-    alpha[j] = c1[j] + c2[j];
-    beta[j] = sqrt(s);
-}
-
-__global__ void k_lanczos_next(int64_t n, const double *w, const double *beta, int j, double *V, int ldv) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    double b = beta[j];
-    V[i * ldv + j + 1] = b > 0.0 ? w[i] / b : 0.0;
-}
-
 __global__ void k_normalize_first(int64_t n, double *V, int ldv, const double *part, int nb) {
     __shared__ double inv;
     if (threadIdx.x == 0) {
@@ -941,6 +925,70 @@ __global__ void k_normalize_first(int64_t n, double *V, int ldv, const double *p
     __syncthreads();
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         V[i * ldv] *= inv;
+}
+
+// Plain Lanczos steps of the extremal bounds, over LZ_BLOCKS CTAs of 256 threads with grid-stride
+// loops.  Every CTA sums the previous kernel's LZ_BLOCKS partial sums itself, in the same order, so
+// all CTAs use identical coefficients and no single-thread launch sits between the steps.
+constexpr int LZ_BLOCKS = 304;
+
+__device__ double lz_block_sum(double s) {
+    __shared__ double red[32];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    double t = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
+    return t;
+}
+
+// sum of the LZ_BLOCKS partial sums in a fixed order (a warp per CTA, then across the lanes)
+__device__ double lz_total(const double *part) {
+    __shared__ double tot;
+    if (threadIdx.x < 32) {
+        double s = 0.0;
+        for (int b = threadIdx.x; b < LZ_BLOCKS; b += 32) s += part[b];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (threadIdx.x == 0) tot = s;
+    }
+    __syncthreads();
+    return tot;
+}
+
+// dot[b] = partial sums of v^T (w - beta_{j-1} v_prev)
+__global__ void k_lz_dot(int64_t n, int j, const double *v, const double *vprev, const double *w, const double *beta,
+                         double *dot) {
+    const double b = j > 0 ? beta[j - 1] : 0.0;
+    double s = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        s += v[i] * (w[i] - b * vprev[i]);
+    s = lz_block_sum(s);
+    if (threadIdx.x == 0) dot[blockIdx.x] = s;
+}
+
+// alpha_j = sum(dot); w <- w - beta_{j-1} v_prev - alpha_j v; nrm[b] = partial sums of |w|^2
+__global__ void k_lz_update(int64_t n, int j, const double *v, const double *vprev, double *w, const double *dot,
+                            double *alpha, const double *beta, double *nrm) {
+    const double a = lz_total(dot), b = j > 0 ? beta[j - 1] : 0.0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) alpha[j] = a;
+    double s = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double x = w[i] - b * vprev[i] - a * v[i];
+        w[i] = x;
+        s += x * x;
+    }
+    s = lz_block_sum(s);
+    if (threadIdx.x == 0) nrm[blockIdx.x] = s;
+}
+
+// beta_j = sqrt(sum(nrm)); out = w / beta_j (out may be v_prev: every read of it is done)
+__global__ void k_lz_scale(int64_t n, int j, const double *w, const double *nrm, double *beta, double *out) {
+    const double b = sqrt(lz_total(nrm));
+    if (blockIdx.x == 0 && threadIdx.x == 0) beta[j] = b;
+    const double inv = b > 0.0 ? 1.0 / b : 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = w[i] * inv;
 }
 
 __device__ int tri_sturm(int m, const double *a, const double *b, double x) {
@@ -1048,42 +1096,39 @@ void extremal_bounds(mbl_sector *sec, double *emin, double *emax) {
         return;
     }
     ProfScope ps(ctx, "extremal_bounds", 0.0, st);
-    const int mmax = (int)std::min<int64_t>(n - 1, 480);
+    // Plain Lanczos (three-term recurrence, no reorthogonalization): only the extreme Ritz values
+    // are wanted, and in finite precision those still converge to the extreme eigenvalues; the lost
+    // orthogonality only adds copies of converged Ritz values (Paige's analysis of the method).
+    const int mmax = (int)std::min<int64_t>(n - 1, 1200);
     const int ldv = mmax + 1;
-    DVec<double> V, W, C1, C2, work, alpha, beta, part, scr, out;
-    V.alloc(ctx, (size_t)n * ldv);
+    DVec<double> V3, W, alpha, beta, part, scr, out;
+    V3.alloc(ctx, (size_t)2 * n);
     W.alloc(ctx, n);
-    C1.alloc(ctx, ldv);
-    C2.alloc(ctx, ldv);
-    work.alloc(ctx, dense_tn_work(n, ldv, 1) + 64);
     alpha.alloc(ctx, ldv);
     beta.alloc(ctx, ldv);
-    const int nb = 256;
-    part.alloc(ctx, nb);
+    part.alloc(ctx, 2 * (size_t)LZ_BLOCKS);
     scr.alloc(ctx, 12 * (size_t)ldv);
     out.alloc(ctx, 4);
-    k_random_block<<<nblk(n), 256, 0, st>>>(n, 1, 0xB0B5EEDull, V.data(), ldv, 0);
+    double *v = V3.data(), *vprev = V3.data() + n, *dot = part.data(), *nrm = part.data() + LZ_BLOCKS;
+    k_random_block<<<nblk(n), 256, 0, st>>>(n, 1, 0xB0B5EEDull, v, 1, 0);
     MBL_LAUNCH_CHECK();
-    // the first column is strided; normalize through a contiguous copy
-    copy_cols(n, V.data(), ldv, 0, W.data(), 1, 0, 1, st);
-    k_lanczos_norm_part<<<nb, 256, 0, st>>>(n, W.data(), part.data());
+    k_lanczos_norm_part<<<LZ_BLOCKS, 256, 0, st>>>(n, v, nrm);
     MBL_LAUNCH_CHECK();
-    k_normalize_first<<<nb, 256, 0, st>>>(n, V.data(), ldv, part.data(), nb);
+    k_normalize_first<<<LZ_BLOCKS, 256, 0, st>>>(n, v, 1, nrm, LZ_BLOCKS);
     MBL_LAUNCH_CHECK();
     double lo = 0, hi = 0;
     bool done = false;
     for (int j = 0; j < mmax && !done; ++j) {
-        launch_spmv(sec, 0.0, V.data() + j, ldv, 1, W.data(), 1, 1, 1, st);
-        dense_tn(n, V.data(), ldv, 0, j + 1, W.data(), 1, 0, 1, C1.data(), work.data(), st);
-        dense_nn_sub(n, V.data(), ldv, 0, j + 1, C1.data(), 1, W.data(), st);
-        dense_tn(n, V.data(), ldv, 0, j + 1, W.data(), 1, 0, 1, C2.data(), work.data(), st);
-        dense_nn_sub(n, V.data(), ldv, 0, j + 1, C2.data(), 1, W.data(), st);
-        k_lanczos_norm_part<<<nb, 256, 0, st>>>(n, W.data(), part.data());
+        // w = H v; alpha_j = v^T (w - beta_{j-1} v_prev); w <- w - beta_{j-1} v_prev - alpha_j v;
+        // beta_j = |w|; v_prev <- w / beta_j, then the roles of v and v_prev swap
+        launch_spmv(sec, 0.0, v, 1, 1, W.data(), 1, 1, 1, st);
+        k_lz_dot<<<LZ_BLOCKS, 256, 0, st>>>(n, j, v, vprev, W.data(), beta.data(), dot);
         MBL_LAUNCH_CHECK();
-        k_lanczos_coef<<<1, 32, 0, st>>>(nb, part.data(), j, C1.data(), C2.data(), alpha.data(), beta.data());
+        k_lz_update<<<LZ_BLOCKS, 256, 0, st>>>(n, j, v, vprev, W.data(), dot, alpha.data(), beta.data(), nrm);
         MBL_LAUNCH_CHECK();
-        k_lanczos_next<<<nblk(n), 256, 0, st>>>(n, W.data(), beta.data(), j, V.data(), ldv);
+        k_lz_scale<<<LZ_BLOCKS, 256, 0, st>>>(n, j, W.data(), nrm, beta.data(), vprev);
         MBL_LAUNCH_CHECK();
+        std::swap(v, vprev);
         const int m = j + 1;
         if ((m >= 16 && m % 8 == 0) || m == mmax) {
             k_tridiag_extremes<<<1, 64, 0, st>>>(m, alpha.data(), beta.data(), scr.data(), out.data());

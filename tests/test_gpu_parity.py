@@ -67,7 +67,7 @@ def test_spmv(g, ctx, orc):
 
 
 # ---------------------------------------------------------------- extremal bounds ----------
-@pytest.mark.parametrize("L,h,seed", [(4, 1.0, 0), (8, 2.0, 1), (10, 0.5, 2), (12, 3.0, 3), (14, 5.0, 4)])
+@pytest.mark.parametrize("L,h,seed", [(4, 1.0, 0), (8, 2.0, 1), (10, 0.5, 2), (12, 3.0, 3), (14, 5.0, 4), (16, 0.5, 5)])
 def test_extremal_bounds(g, ctx, orc, L, h, seed):
     sec = g.build_sector(ctx, L, h, seed)
     lo, hi = g.extremal_bounds(sec)
