@@ -556,60 +556,63 @@ __global__ void __launch_bounds__(EIG_THREADS) k_syev(const int *mv, const int64
 // ------------------------------------------------------------------------------------------
 size_t syev_bisect_work(int m) { return 8 * (size_t)m + 4 * (size_t)m * m + 64; }
 
-// work: d[m], e[m], e2[m], beta[m], vv[m], pp[m], Z[m x m], U[3 m x m]
-__global__ void __launch_bounds__(EIG_THREADS) k_bi_tridiag(int m, double *A, double *work) {
+// The arithmetic runs in R (FP64, or FP32 as the start of a refined decomposition); A, W and the
+// output vectors are FP64 either way.  work (R): d[m], e[m], e2[m], beta[m], vv[m], pp[m], Z[m x m],
+// U[3 m x m].
+template <class R>
+__global__ void __launch_bounds__(EIG_THREADS) k_bi_tridiag(int m, double *A, R *work) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    double *a = reinterpret_cast<double *>(smraw);
-    __shared__ double red[EIG_THREADS / 32];
-    double *d = work, *e = work + m, *e2 = work + 2 * m, *beta = work + 3 * m, *vv = work + 4 * m,
-           *pp = work + 5 * m;
-    for (int t = threadIdx.x; t < m * m; t += blockDim.x) a[t] = A[t];
+    R *a = reinterpret_cast<R *>(smraw);
+    __shared__ R red[EIG_THREADS / 32];
+    R *d = work, *e = work + m, *e2 = work + 2 * m, *beta = work + 3 * m, *vv = work + 4 * m, *pp = work + 5 * m;
+    for (int t = threadIdx.x; t < m * m; t += blockDim.x) a[t] = (R)A[t];
     __syncthreads();
-    householder_tridiag<double>(a, m, m, beta, vv, pp, red);
+    householder_tridiag<R>(a, m, m, beta, vv, pp, red);
     for (int i = threadIdx.x; i < m; i += blockDim.x) {
         d[i] = a[(size_t)i * m + i];
-        const double ev = i + 1 < m ? a[(size_t)i * m + i + 1] : 0.0;
+        const R ev = i + 1 < m ? a[(size_t)i * m + i + 1] : R(0);
         e[i] = ev;
         e2[i] = ev * ev;
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < m * m; t += blockDim.x) A[t] = a[t];  // the reflectors
+    for (int t = threadIdx.x; t < m * m; t += blockDim.x) A[t] = (double)a[t];  // the reflectors
 }
 
-// Eigenvalue j (ascending) by bisection to the resolution of FP64 on the Gershgorin interval.
-__global__ void k_bi_values(int m, const double *work, double *W) {
+// Eigenvalue j (ascending) by bisection to the resolution of R on the Gershgorin interval.
+template <class R>
+__global__ void k_bi_values(int m, const R *work, double *W) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= m) return;
-    const double *d = work, *e = work + m, *e2 = work + 2 * m;
-    double gl = d[0], gu = d[0], emax2 = 0.0;
+    const R *d = work, *e = work + m, *e2 = work + 2 * m;
+    R gl = d[0], gu = d[0], emax2 = R(0);
     for (int i = 0; i < m; ++i) {
-        const double r = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i + 1 < m ? fabs(e[i]) : 0.0);
+        const R r = (i > 0 ? fabs(e[i - 1]) : R(0)) + (i + 1 < m ? fabs(e[i]) : R(0));
         gl = fmin(gl, d[i] - r);
         gu = fmax(gu, d[i] + r);
         if (i + 1 < m) emax2 = fmax(emax2, e2[i]);
     }
-    const double tn = fmax(fabs(gl), fabs(gu));
-    gl -= 2.0 * DBL_EPSILON * tn * m + DBL_MIN;
-    gu += 2.0 * DBL_EPSILON * tn * m + DBL_MIN;
-    const double pivmin = DBL_MIN * fmax(1.0, emax2);
-    double lo = gl, hi = gu;
+    const R tn = fmax(fabs(gl), fabs(gu)), eps = Num<R>::eps(), tiny = Num<R>::tiny();
+    gl -= R(2) * eps * tn * (R)m + tiny;
+    gu += R(2) * eps * tn * (R)m + tiny;
+    const R pivmin = tiny * fmax(R(1), emax2);
+    R lo = gl, hi = gu;
     for (int it = 0; it < 200; ++it) {
-        const double mid = 0.5 * (lo + hi);
-        if (hi - lo <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + 4.0 * pivmin || mid == lo || mid == hi) break;
-        if (sturm_count<double>(m, d, e2, mid, pivmin) > j) hi = mid; else lo = mid;
+        const R mid = R(0.5) * (lo + hi);
+        if (hi - lo <= R(2) * eps * fmax(fabs(lo), fabs(hi)) + R(4) * pivmin || mid == lo || mid == hi) break;
+        if (sturm_count<R>(m, d, e2, mid, pivmin) > j) hi = mid; else lo = mid;
     }
-    W[j] = 0.5 * (lo + hi);
+    W[j] = (double)(R(0.5) * (lo + hi));
 }
 
 // One solve of (T - lambda I) y = x in place (x -> y), Gaussian elimination with partial pivoting:
 // U keeps the pivot rows (diagonal, first and second superdiagonal; a pivot below `tiny` becomes
 // +-tiny), the eliminations are applied to x as they happen, then back substitution.
-__device__ void tridiag_solve_pivoted(int m, const double *d, const double *e, double lambda, double tiny,
-                                      double *U0, double *U1, double *U2, double *x) {
-    double p0 = d[0] - lambda, p1 = m > 1 ? e[0] : 0.0, p2 = 0.0, xp = x[0];
+template <class R>
+__device__ void tridiag_solve_pivoted(int m, const R *d, const R *e, R lambda, R tiny, R *U0, R *U1, R *U2, R *x) {
+    R p0 = d[0] - lambda, p1 = m > 1 ? e[0] : R(0), p2 = R(0), xp = x[0];
     for (int i = 0; i + 1 < m; ++i) {
-        const double s = e[i], q0 = d[i + 1] - lambda, q1 = i + 2 < m ? e[i + 1] : 0.0, xq = x[i + 1];
-        double u0, u1, u2, o0, o1, o2, xu, xo;
+        const R s = e[i], q0 = d[i + 1] - lambda, q1 = i + 2 < m ? e[i + 1] : R(0), xq = x[i + 1];
+        R u0, u1, u2, o0, o1, o2, xu, xo;
         if (fabs(p0) >= fabs(s)) {
             u0 = p0; u1 = p1; u2 = p2; xu = xp;
             o0 = s; o1 = q0; o2 = q1; xo = xq;
@@ -617,18 +620,18 @@ __device__ void tridiag_solve_pivoted(int m, const double *d, const double *e, d
             u0 = s; u1 = q0; u2 = q1; xu = xq;
             o0 = p0; o1 = p1; o2 = p2; xo = xp;
         }
-        if (fabs(u0) < tiny) u0 = u0 >= 0.0 ? tiny : -tiny;
-        const double l = o0 / u0;
+        if (fabs(u0) < tiny) u0 = u0 >= R(0) ? tiny : -tiny;
+        const R l = o0 / u0;
         U0[i] = u0;
         U1[i] = u1;
         U2[i] = u2;
         x[i] = xu;
         p0 = o1 - l * u1;
         p1 = o2 - l * u2;
-        p2 = 0.0;
+        p2 = R(0);
         xp = xo - l * xu;
     }
-    if (fabs(p0) < tiny) p0 = p0 >= 0.0 ? tiny : -tiny;
+    if (fabs(p0) < tiny) p0 = p0 >= R(0) ? tiny : -tiny;
     U0[m - 1] = p0;
     x[m - 1] = xp / p0;
     if (m > 1) x[m - 2] = (x[m - 2] - U1[m - 2] * x[m - 1]) / U0[m - 2];
@@ -638,32 +641,34 @@ __device__ void tridiag_solve_pivoted(int m, const double *d, const double *e, d
 // Eigenvectors of T: thread j iterates on column j of Z (three steps from a fixed pseudo-random
 // start, normalized each time); between steps the vectors of each cluster (consecutive eigenvalues
 // closer than 1e-3 ||T||) are re-orthogonalized by the block, two classical Gram-Schmidt passes each.
-__global__ void __launch_bounds__(EIG_THREADS) k_bi_vectors(int m, const double *W, double *work) {
-    __shared__ double red[EIG_THREADS / 32];
-    __shared__ double s_h[EIG_SMEM_MAX_M];
-    const double *d = work, *e = work + m;
-    double *Z = work + 8 * m, *U = Z + (size_t)m * m;
-    double tn = 0.0;
-    for (int i = 0; i < m; ++i) tn = fmax(tn, fabs(d[i]) + (i > 0 ? fabs(e[i - 1]) : 0.0) + (i + 1 < m ? fabs(e[i]) : 0.0));
-    const double tiny = DBL_EPSILON * fmax(tn, DBL_MIN), ortol = 1e-3 * tn;
+template <class R>
+__global__ void __launch_bounds__(EIG_THREADS) k_bi_vectors(int m, const double *W, R *work) {
+    __shared__ R red[EIG_THREADS / 32];
+    __shared__ R s_h[EIG_SMEM_MAX_M];
+    const R *d = work, *e = work + m;
+    R *Z = work + 8 * m, *U = Z + (size_t)m * m;
+    R tn = R(0);
+    for (int i = 0; i < m; ++i) tn = fmax(tn, fabs(d[i]) + (i > 0 ? fabs(e[i - 1]) : R(0)) + (i + 1 < m ? fabs(e[i]) : R(0)));
+    const R tiny = Num<R>::eps() * fmax(tn, Num<R>::tiny());
+    const double ortol = 1e-3 * (double)tn;
     const int j = threadIdx.x;
-    double *z = Z + (size_t)j * m;
+    R *z = Z + (size_t)j * m;
     if (j < m) {
         uint64_t h = 0x9E3779B97F4A7C15ull * (uint64_t)(j + 1);
         for (int i = 0; i < m; ++i) {
             h ^= h >> 33;
             h *= 0xff51afd7ed558ccdull;
             h ^= h >> 33;
-            z[i] = (double)(h >> 11) * 0x1.0p-53 - 0.5;
+            z[i] = (R)((double)(h >> 11) * 0x1.0p-53 - 0.5);
         }
     }
     for (int step = 0; step < 3; ++step) {
         if (j < m) {
-            tridiag_solve_pivoted(m, d, e, W[j], tiny, U + (size_t)j * 3 * m, U + (size_t)j * 3 * m + m,
-                                  U + (size_t)j * 3 * m + 2 * m, z);
-            double nr = 0.0;
+            tridiag_solve_pivoted<R>(m, d, e, (R)W[j], tiny, U + (size_t)j * 3 * m, U + (size_t)j * 3 * m + m,
+                                     U + (size_t)j * 3 * m + 2 * m, z);
+            R nr = R(0);
             for (int i = 0; i < m; ++i) nr += z[i] * z[i];
-            nr = 1.0 / sqrt(nr);
+            nr = R(1) / sqrt(nr);
             for (int i = 0; i < m; ++i) z[i] *= nr;
         }
         __syncthreads();
@@ -673,70 +678,87 @@ __global__ void __launch_bounds__(EIG_THREADS) k_bi_vectors(int m, const double 
             int c0 = c;
             while (c0 > 0 && W[c0] - W[c0 - 1] <= ortol) --c0;
             if (c0 == c) continue;
-            double *zc = Z + (size_t)c * m;
+            R *zc = Z + (size_t)c * m;
             for (int pass = 0; pass < 2; ++pass) {
                 for (int k = c0 + (int)threadIdx.x; k < c; k += blockDim.x) {
-                    const double *zk = Z + (size_t)k * m;
-                    double sdot = 0.0;
+                    const R *zk = Z + (size_t)k * m;
+                    R sdot = R(0);
                     for (int i = 0; i < m; ++i) sdot += zk[i] * zc[i];
                     s_h[k - c0] = sdot;
                 }
                 __syncthreads();
                 for (int i = threadIdx.x; i < m; i += blockDim.x) {
-                    double v = zc[i];
+                    R v = zc[i];
                     for (int k = c0; k < c; ++k) v -= s_h[k - c0] * Z[(size_t)k * m + i];
                     zc[i] = v;
                 }
                 __syncthreads();
             }
-            double loc = 0.0;
+            R loc = R(0);
             for (int i = threadIdx.x; i < m; i += blockDim.x) loc += zc[i] * zc[i];
-            const double nr = 1.0 / sqrt(block_sum(loc, red));
+            const R nr = R(1) / sqrt(block_sum(loc, red));
             for (int i = threadIdx.x; i < m; i += blockDim.x) zc[i] *= nr;
             __syncthreads();
         }
     }
 }
 
-// z <- H_0 ... H_{m-3} z for the eigenvectors (a warp per vector), reflectors in A and beta.
-__global__ void k_bi_back(int m, const double *A, double *work) {
-    const double *beta = work + 3 * m;
-    double *Z = work + 8 * m;
+// z <- H_0 ... H_{m-3} z for the eigenvectors (a warp per vector), reflectors in A and beta; the
+// result, in FP64, to X (column-major m x m).
+template <class R>
+__global__ void k_bi_back(int m, const double *A, R *work, double *X) {
+    const R *beta = work + 3 * m;
+    R *Z = work + 8 * m;
     const int lane = threadIdx.x & 31;
     const int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (c >= m) return;
-    double *z = Z + (size_t)c * m;
+    R *z = Z + (size_t)c * m;
     for (int k = m - 3; k >= 0; --k) {
-        const double bk = beta[k];
-        if (bk == 0.0) continue;
+        const R bk = beta[k];
+        if (bk == R(0)) continue;
         const double *vk = A + (size_t)k * m + (k + 1);
         const int len = m - k - 1;
-        double sdot = 0.0;
-        for (int i = lane; i < len; i += 32) sdot += (i == 0 ? 1.0 : vk[i]) * z[k + 1 + i];
+        R sdot = R(0);
+        for (int i = lane; i < len; i += 32) sdot += (i == 0 ? R(1) : (R)vk[i]) * z[k + 1 + i];
         for (int o = 16; o > 0; o >>= 1) sdot += __shfl_xor_sync(0xffffffffu, sdot, o);
         sdot *= bk;
-        for (int i = lane; i < len; i += 32) z[k + 1 + i] -= sdot * (i == 0 ? 1.0 : vk[i]);
+        for (int i = lane; i < len; i += 32) z[k + 1 + i] -= sdot * (i == 0 ? R(1) : (R)vk[i]);
         __syncwarp();
     }
+    for (int i = lane; i < m; i += 32) X[(size_t)c * m + i] = (double)z[i];
 }
 
-void syev_bisect(int m, double *d_A, double *d_w, double *d_work, cudaStream_t st) {
+template <class R>
+static void syev_bisect_t(int m, double *d_A, double *d_w, double *d_work, cudaStream_t st) {
     if (m < 1 || m > EIG_SMEM_MAX_M) fail(MBL_ERR_INVALID, "bisection eigensolver: order must be in [1, 160]");
     static std::atomic<bool> attr{false};  // per process: one device
     if (!attr) {
-        MBL_CUDA(cudaFuncSetAttribute(k_bi_tridiag, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      EIG_SMEM_MAX_M * EIG_SMEM_MAX_M * sizeof(double)));
+        MBL_CUDA(cudaFuncSetAttribute(k_bi_tridiag<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      EIG_SMEM_MAX_M * EIG_SMEM_MAX_M * sizeof(R)));
         attr = true;
     }
-    k_bi_tridiag<<<1, EIG_THREADS, (size_t)m * m * sizeof(double), st>>>(m, d_A, d_work);
+    R *work = reinterpret_cast<R *>(d_work);
+    // the eigenvectors overwrite A only after the back-transformation has read its reflectors:
+    // they go to the U scratch first (3 m^2 entries of R hold m^2 doubles; start rounded up to 16 bytes)
+    const size_t xoff = ((8 * (size_t)m + (size_t)m * m) * sizeof(R) + 15) & ~(size_t)15;
+    double *X = reinterpret_cast<double *>(reinterpret_cast<char *>(d_work) + xoff);
+    k_bi_tridiag<R><<<1, EIG_THREADS, (size_t)m * m * sizeof(R), st>>>(m, d_A, work);
     MBL_LAUNCH_CHECK();
-    k_bi_values<<<(m + 31) / 32, 32, 0, st>>>(m, d_work, d_w);
+    k_bi_values<R><<<(m + 31) / 32, 32, 0, st>>>(m, work, d_w);
     MBL_LAUNCH_CHECK();
-    k_bi_vectors<<<1, ((m + 31) / 32) * 32, 0, st>>>(m, d_w, d_work);
+    k_bi_vectors<R><<<1, ((m + 31) / 32) * 32, 0, st>>>(m, d_w, work);
     MBL_LAUNCH_CHECK();
-    k_bi_back<<<(m + 7) / 8, 256, 0, st>>>(m, d_A, d_work);
+    k_bi_back<R><<<(m + 7) / 8, 256, 0, st>>>(m, d_A, work, X);
     MBL_LAUNCH_CHECK();
-    MBL_CUDA(cudaMemcpyAsync(d_A, d_work + 8 * (size_t)m, (size_t)m * m * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    MBL_CUDA(cudaMemcpyAsync(d_A, X, (size_t)m * m * sizeof(double), cudaMemcpyDeviceToDevice, st));
+}
+
+void syev_bisect(int m, double *d_A, double *d_w, double *d_work, cudaStream_t st) {
+    syev_bisect_t<double>(m, d_A, d_w, d_work, st);
+}
+
+void syev_bisect32(int m, double *d_A, double *d_w, double *d_work, cudaStream_t st) {
+    syev_bisect_t<float>(m, d_A, d_w, d_work, st);
 }
 
 cudaError_t syev_preload() {

@@ -233,6 +233,9 @@ void chol_qr(int64_t n, double *X, int p, double *R, double *G, double *work, in
 // ascending) and eigenvalues d_w, by bisection and inverse iteration; d_work >= syev_bisect_work(m).
 size_t syev_bisect_work(int m);
 void syev_bisect(int m, double *d_A, double *d_w, double *d_work, cudaStream_t st);
+// The same method in FP32 arithmetic (FP64 input and output; vectors to FP32 accuracy), as the start
+// of a refined decomposition; d_work >= syev_bisect_work(m) / 2 + 1.
+void syev_bisect32(int m, double *d_A, double *d_w, double *d_work, cudaStream_t st);
 size_t syev_work_doubles(int mmax, bool vecs = true);
 // sel (optional, indexed like w): eigenvectors are computed only where sel != 0 (others zero).
 constexpr int EIG_SMEM_MAX_M = 160;  // largest order the small eigensolver keeps in shared memory
