@@ -8,14 +8,17 @@ source next to this file is compiled on its own with gcc and loaded through ctyp
 What each function computes and the passage it follows:
 
 * ``fields``            Eq. 1, h_i uniform on [-h, h] (SplitMix64 stream, a stated reading)
-* ``basis``             S^z = 0 sector of even L, numerical-method section; brute force
+* ``basis``             magnetization sectors of the numerical-method section (S^z = 0 of even
+                        L; for odd L its "S^z = 1", read as n_up = (L + 1) / 2) or any n_up;
+                        brute force
 * ``csr``               Eq. 1 restricted to the sector, binary search of flipped states
 * ``syev``              dense Householder + implicit QL
 * ``extremal_bounds``   E_0, E_max of the numerical-method section
 * ``nearest``           eigenpairs closest to the target, numerical-method section
 * ``gap_ratio``         r^(n), "level statistics" paragraph
 * ``s1p``               S_1^P, "Hilbert space localization" paragraph
-* ``entanglement``      S^E = -Tr rho_A ln rho_A, "entanglement entropy" paragraph
+* ``entanglement``      S^E = -Tr rho_A ln rho_A, A = sites 0 .. floor(L/2) - 1, "entanglement
+                        entropy" paragraph
 * ``kl``                KL divergence of nearby eigenstates, "level statistics and eigenvectors
                         similarity" paragraph
 * ``sqp``               S_q^P, q != 1, "Hilbert space localization" paragraph
@@ -74,6 +77,8 @@ def lib():
         L.orc_binom.restype = ctypes.c_int64
         L.orc_basis.argtypes = [ctypes.c_int, ctypes.c_void_p]
         L.orc_basis.restype = ctypes.c_int64
+        L.orc_basis_sector.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p]
+        L.orc_basis_sector.restype = ctypes.c_int64
         L.orc_nnz.argtypes = [ctypes.c_int, _u32p, ctypes.c_int64]
         L.orc_nnz.restype = ctypes.c_int64
         L.orc_csr.argtypes = [ctypes.c_int, _f64p, ctypes.c_double, _u32p, ctypes.c_int64, _i64p, _i32p, _f64p]
@@ -124,12 +129,19 @@ def binom(n: int, k: int) -> int:
     return int(lib().orc_binom(n, k))
 
 
-def basis(L: int) -> np.ndarray:
-    n = lib().orc_basis(L, None)
+def default_nup(L: int) -> int:
+    """Up spins of the sector the numerical-method section uses at chain length L: S^z = 0
+    (L/2) for even L; for odd L its "S^z = 1" read as sum_i sigma^z_i = n_up - n_down = 1."""
+    return L // 2 if L % 2 == 0 else (L + 1) // 2
+
+
+def basis(L: int, nup: int | None = None) -> np.ndarray:
+    k = default_nup(L) if nup is None else nup
+    n = lib().orc_basis_sector(L, k, None)
     if n < 0:
-        raise ValueError(f"invalid L={L}")
+        raise ValueError(f"invalid sector L={L}, nup={k}")
     st = np.zeros(n, dtype=np.uint32)
-    lib().orc_basis(L, st.ctypes.data)
+    lib().orc_basis_sector(L, k, st.ctypes.data)
     return st
 
 
@@ -321,6 +333,7 @@ class Job:
     eps: float
     nev: int
     J: float = 1.0
+    nup: int | None = None  # up spins of the sector (None: default_nup(L))
 
 
 @dataclass
@@ -340,7 +353,7 @@ class JobResult:
 def solve_job(job: Job, method: str = "auto", hi: np.ndarray | None = None) -> JobResult:
     """The whole path for one (L, h, seed, eps, nev): fields, sector, H, E_min/E_max,
     sigma = E_min + eps (E_max - E_min), the nev eigenpairs nearest sigma, observables."""
-    st = basis(job.L)
+    st = basis(job.L, job.nup)
     if hi is None:
         hi = fields(job.L, job.h, job.seed)
     H = csr(job.L, hi, job.J, st)

@@ -59,19 +59,25 @@ static int popcount32(uint32_t s) {
 }
 
 /* ------------------------------------------------------------------------------------------
- * Basis of the S^z_tot = 0 sector (numerical-method section: S^z = 0 sector of even L).
- * Brute force: every integer below 2^L whose popcount is L/2, in ascending order.
+ * Basis of a magnetization sector (numerical-method section: the S^z = 0 sector of even L and
+ * the S^z = 1 sector of odd L).  Brute force: every integer below 2^L with nup set bits (up
+ * spins), in ascending order.  The S^z_tot = 0 sector is nup = L/2.
  * ------------------------------------------------------------------------------------------ */
-int64_t orc_basis(int L, uint32_t *states) {
-    if (L < 2 || L > 30 || (L & 1)) return -1;
+int64_t orc_basis_sector(int L, int nup, uint32_t *states) {
+    if (L < 2 || L > 30 || nup < 0 || nup > L) return -1;
     int64_t n = 0;
     uint32_t top = 1u << L;
     for (uint32_t s = 0; s < top; ++s)
-        if (popcount32(s) == L / 2) {
+        if (popcount32(s) == nup) {
             if (states) states[n] = s;
             ++n;
         }
     return n;
+}
+
+int64_t orc_basis(int L, uint32_t *states) {
+    if (L & 1) return -1;
+    return orc_basis_sector(L, L / 2, states);
 }
 
 static int64_t find_state(const uint32_t *states, int64_t n, uint32_t s) {
@@ -774,12 +780,13 @@ double orc_s1p(int64_t n, const double *y) {
 }
 
 double orc_entanglement(int L, const uint32_t *states, int64_t n, const double *y) {
-    int LA = L / 2, LB = L - L / 2;
+    /* A = sites 0 .. floor(L/2) - 1; the sector's up-spin count is that of any basis state */
+    int LA = L / 2, LB = L - L / 2, nup = n > 0 ? popcount32(states[0]) : 0;
     double nrm = dot(n, y, y), S = 0.0;
     uint32_t *as = (uint32_t *)malloc(sizeof(uint32_t) << LA);
     uint32_t *bs = (uint32_t *)malloc(sizeof(uint32_t) << LB);
     for (int nA = 0; nA <= LA; ++nA) {
-        int nB = L / 2 - nA;
+        int nB = nup - nA;
         if (nB < 0 || nB > LB) continue;
         int da = 0, db = 0;
         for (uint32_t a = 0; a < (1u << LA); ++a) if (popcount32(a) == nA) as[da++] = a;
@@ -828,7 +835,7 @@ double orc_sqp(int64_t n, const double *y, double q) {
     return log(s) / (1.0 - q);
 }
 
-/* S^z of the sites 0 .. L/2-1 of a basis state: (#up - #down) / 2 */
+/* S^z of the sites 0 .. floor(L/2)-1 of a basis state: (#up - #down) / 2 */
 static double sz_half(int L, uint32_t s) {
     int up = 0;
     for (int i = 0; i < L / 2; ++i) up += (s >> i) & 1u;

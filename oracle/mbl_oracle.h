@@ -31,8 +31,10 @@ void orc_fields(int L, double h, uint64_t seed, double *out);
 /* Binomial coefficient C(n, k) as an exact 64-bit integer (0 if k < 0 or k > n). */
 int64_t orc_binom(int n, int k);
 
-/* S^z_tot = 0 basis by brute force over all 2^L states, ascending.  Returns the count;
- * states may be NULL to only count. */
+/* Basis of the sector with nup up spins (2 <= L <= 30, 0 <= nup <= L) by brute force over all 2^L
+ * states, ascending.  Returns the count (-1 for invalid arguments); states may be NULL to only count. */
+int64_t orc_basis_sector(int L, int nup, uint32_t *states);
+/* S^z_tot = 0 basis (even L): orc_basis_sector(L, L/2, states). */
 int64_t orc_basis(int L, uint32_t *states);
 
 /* Number of stored entries of H in the sector (diagonal included, duplicates merged). */
