@@ -133,9 +133,19 @@ int mbl_ctx_synchronize(mbl_ctx *ctx);
 int mbl_build_sector(mbl_ctx *ctx, int L, double h, uint64_t seed, mbl_sector **out);
 /* Same with explicit fields h_i[L] (host) and coupling J. */
 int mbl_build_sector_fields(mbl_ctx *ctx, int L, const double *h_i, double J, mbl_sector **out);
+/* The same constructions for the magnetization sector with nup up spins (S^z_tot = nup - L/2):
+ * 2 <= L <= 22 of either parity, 0 <= nup <= L, basis = the colex enumeration of nup-subsets of the
+ * L sites (dimension C(L, nup)).  The numerical-method section uses S^z = 0 for even L
+ * (nup = L/2, what mbl_build_sector builds) and an "S^z = 1" sector for odd L = 15, 17, 19, read as
+ * nup - (L - nup) = 1, i.e. nup = (L + 1)/2.  MBL_ERR_INVALID outside these ranges. */
+int mbl_build_sector_nup(mbl_ctx *ctx, int L, int nup, double h, uint64_t seed, mbl_sector **out);
+int mbl_build_sector_fields_nup(mbl_ctx *ctx, int L, int nup, const double *h_i, double J,
+                                mbl_sector **out);
 void mbl_sector_destroy(mbl_sector *sec);
 
 int mbl_sector_info(const mbl_sector *sec, int64_t *dim, int64_t *nnz);
+/* Chain length and up-spin count of the sector (either pointer may be NULL). */
+int mbl_sector_shape(const mbl_sector *sec, int *L, int *nup);
 /* Device-to-host copies for inspection: states[dim]; rowptr[dim+1], col[nnz], val[nnz]; h_i[L]. */
 int mbl_sector_copy_basis(const mbl_sector *sec, uint32_t *states);
 int mbl_sector_copy_csr(const mbl_sector *sec, int64_t *rowptr, int32_t *col, double *val);
@@ -224,6 +234,14 @@ int mbl_observables(mbl_ctx *ctx, int L, int nev, const double *evals, const dou
 int mbl_observables_dev(mbl_ctx *ctx, int L, int nev, const double *d_evals,
                         const double *d_evecs, double *d_r, double *d_r_mean, double *d_s1p,
                         double *d_se, void *stream);
+/* The same for eigenvectors of the sector (L, nup) of mbl_build_sector_nup: A = sites
+ * 0 .. floor(L/2) - 1, B the other L - floor(L/2) sites; the Schmidt blocks are indexed by the up
+ * spins n_A of A (n_B = nup - n_A).  The entry points without nup take nup = L/2 and even L. */
+int mbl_observables_nup(mbl_ctx *ctx, int L, int nup, int nev, const double *evals,
+                        const double *evecs, double *r, double *r_mean, double *s1p, double *se);
+int mbl_observables_nup_dev(mbl_ctx *ctx, int L, int nup, int nev, const double *d_evals,
+                            const double *d_evecs, double *d_r, double *d_r_mean, double *d_s1p,
+                            double *d_se, void *stream);
 
 /* Further eigenvector observables of the characterization section and its supplement, on the
  * columns of evecs (n x nev column-major, host; ascending eigenvalues, so adjacent columns are
@@ -246,6 +264,12 @@ int mbl_observables_extra(mbl_ctx *ctx, int L, int nev, const double *evecs, dou
 int mbl_observables_extra_dev(mbl_ctx *ctx, int L, int nev, const double *d_evecs, double q,
                               double *d_kl, double *d_sqp, double *d_fluct, double *d_dynf,
                               void *stream);
+/* The same for the sector (L, nup); A = sites 0 .. floor(L/2) - 1 in fluct. */
+int mbl_observables_extra_nup(mbl_ctx *ctx, int L, int nup, int nev, const double *evecs, double q,
+                              double *kl, double *sqp, double *fluct, double *dynf);
+int mbl_observables_extra_nup_dev(mbl_ctx *ctx, int L, int nup, int nev, const double *d_evecs,
+                                  double q, double *d_kl, double *d_sqp, double *d_fluct,
+                                  double *d_dynf, void *stream);
 
 /* Half-chain entanglement entropy (the se output of mbl_observables_dev) computed without any
  * device allocation.  The paper has no counterpart: it exists for callers that cannot allocate
@@ -272,7 +296,7 @@ int mbl_entanglement_noalloc_dev(mbl_ctx *ctx, int L, int nev, const double *d_e
  * job runs the same steps as mbl_build_sector + mbl_solve_near + mbl_observables and gives the
  * same result as those calls alone.  Errors: MBL_ERR_INVALID (bad slots, server already running). */
 typedef struct mbl_request {
-    int L;            /* even, 2..22 */
+    int L;            /* 2..22 (odd L needs nup) */
     double h;         /* disorder strength, fields from the seeded stream (as mbl_build_sector) */
     uint64_t seed;
     const double *fields; /* optional h_i[L] (host, copied at submission; J = 1) instead of (h, seed) */
@@ -280,6 +304,7 @@ typedef struct mbl_request {
     int nev;
     int precision;    /* MBL_PREC_FP32 (mixed) or MBL_PREC_FP64 */
     int want_vectors; /* keep the eigenvectors for mbl_poll */
+    int nup;          /* up spins of the sector; 0 = L/2 (S^z_tot = 0, even L only) */
 } mbl_request;
 
 /* Filled by mbl_poll / mbl_wait.  The array fields are caller-owned outputs set before the call

@@ -13,6 +13,7 @@ numerical-method section, and the observables of the characterization section).
 from __future__ import annotations
 
 import ctypes
+import math
 import sys
 from dataclasses import dataclass
 
@@ -94,6 +95,9 @@ class Sector:
         n, nnz = ctypes.c_int64(), ctypes.c_int64()
         _check(_lib().mbl_sector_info(handle, ctypes.byref(n), ctypes.byref(nnz)), ctx.handle)
         self.dim, self.nnz = n.value, nnz.value
+        ln, nu = ctypes.c_int(), ctypes.c_int()
+        _check(_lib().mbl_sector_shape(handle, ctypes.byref(ln), ctypes.byref(nu)), ctx.handle)
+        self.nup = nu.value  # up spins of every basis state
 
     def basis(self) -> np.ndarray:
         out = np.zeros(self.dim, dtype=np.uint32)
@@ -147,17 +151,26 @@ def launch_count() -> int:
     return int(_lib().mbl_launch_count())
 
 
-def build_sector(ctx: Context, L: int, h: float, seed: int) -> Sector:
+def build_sector(ctx: Context, L: int, h: float, seed: int, nup: int | None = None) -> Sector:
+    """Sector with nup up spins (None: the S^z_tot = 0 sector of even L)."""
     h_ = ctypes.c_void_p()
-    _check(_lib().mbl_build_sector(ctx.handle, L, float(h), ctypes.c_uint64(seed & (2**64 - 1)), ctypes.byref(h_)),
-           ctx.handle)
+    sd = ctypes.c_uint64(seed & (2**64 - 1))
+    if nup is None:
+        rc = _lib().mbl_build_sector(ctx.handle, L, float(h), sd, ctypes.byref(h_))
+    else:
+        rc = _lib().mbl_build_sector_nup(ctx.handle, L, nup, float(h), sd, ctypes.byref(h_))
+    _check(rc, ctx.handle)
     return Sector(ctx, h_, L)
 
 
-def build_sector_fields(ctx: Context, L: int, h_i, J: float = 1.0) -> Sector:
+def build_sector_fields(ctx: Context, L: int, h_i, J: float = 1.0, nup: int | None = None) -> Sector:
     hi = np.ascontiguousarray(h_i, dtype=np.float64)
     h_ = ctypes.c_void_p()
-    _check(_lib().mbl_build_sector_fields(ctx.handle, L, _ptr(hi), float(J), ctypes.byref(h_)), ctx.handle)
+    if nup is None:
+        rc = _lib().mbl_build_sector_fields(ctx.handle, L, _ptr(hi), float(J), ctypes.byref(h_))
+    else:
+        rc = _lib().mbl_build_sector_fields_nup(ctx.handle, L, nup, _ptr(hi), float(J), ctypes.byref(h_))
+    _check(rc, ctx.handle)
     return Sector(ctx, h_, L)
 
 
@@ -275,7 +288,8 @@ def solve_near_dev(sec: Sector, eps: float, nev: int, d_evals, d_evecs, d_resid,
     return nc.value, sg.value, {f: getattr(st, f) for f, _ in SolveStats._fields_}
 
 
-def observables(ctx: Context, L: int, evals: np.ndarray, evecs: np.ndarray):
+def observables(ctx: Context, L: int, evals: np.ndarray, evecs: np.ndarray, nup: int | None = None):
+    """r, r_mean, S_1^P, S^E of eigenpairs of the sector (L, nup) (None: S^z_tot = 0, even L)."""
     ev = np.ascontiguousarray(evals, dtype=np.float64)
     V = np.asfortranarray(evecs, dtype=np.float64)
     nev = len(ev)
@@ -283,37 +297,52 @@ def observables(ctx: Context, L: int, evals: np.ndarray, evecs: np.ndarray):
     rm = np.zeros(1)
     s1p = np.zeros(nev)
     se = np.zeros(nev)
-    _check(_lib().mbl_observables(ctx.handle, L, nev, _ptr(ev), _ptr(V), _ptr(r), _ptr(rm), _ptr(s1p), _ptr(se)),
-           ctx.handle)
+    tail = (_ptr(ev), _ptr(V), _ptr(r), _ptr(rm), _ptr(s1p), _ptr(se))
+    if nup is None:
+        rc = _lib().mbl_observables(ctx.handle, L, nev, *tail)
+    else:
+        rc = _lib().mbl_observables_nup(ctx.handle, L, nup, nev, *tail)
+    _check(rc, ctx.handle)
     return r[: max(nev - 2, 0)], float(rm[0]), s1p, se
 
 
-def observables_dev(ctx: Context, L: int, nev: int, d_evals, d_evecs, d_r, d_rmean, d_s1p, d_se, stream=None):
+def observables_dev(ctx: Context, L: int, nev: int, d_evals, d_evecs, d_r, d_rmean, d_s1p, d_se, stream=None,
+                    nup: int | None = None):
     s = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
-    _check(_lib().mbl_observables_dev(ctx.handle, L, nev, ctypes.c_void_p(d_evals.data_ptr()),
-                                      ctypes.c_void_p(d_evecs.data_ptr()), ctypes.c_void_p(d_r.data_ptr()),
-                                      ctypes.c_void_p(d_rmean.data_ptr()), ctypes.c_void_p(d_s1p.data_ptr()),
-                                      ctypes.c_void_p(d_se.data_ptr()), s), ctx.handle)
+    tail = tuple(ctypes.c_void_p(t.data_ptr()) for t in (d_evals, d_evecs, d_r, d_rmean, d_s1p, d_se)) + (s,)
+    if nup is None:
+        rc = _lib().mbl_observables_dev(ctx.handle, L, nev, *tail)
+    else:
+        rc = _lib().mbl_observables_nup_dev(ctx.handle, L, nup, nev, *tail)
+    _check(rc, ctx.handle)
 
 
-def observables_extra(ctx: Context, L: int, evecs: np.ndarray, q: float = 2.0):
+def observables_extra(ctx: Context, L: int, evecs: np.ndarray, q: float = 2.0, nup: int | None = None):
     """KL of adjacent columns (nev - 1), S_q^P, bipartite fluctuation F and dynamic fraction f of
-    the columns of evecs (dim x nev, ascending eigenvalues)."""
+    the columns of evecs (dim x nev, ascending eigenvalues) of the sector (L, nup)."""
     V = np.asfortranarray(evecs, dtype=np.float64)
     nev = V.shape[1]
     kl = np.zeros(max(nev - 1, 1))
     sqp, fl, dyn = np.zeros(nev), np.zeros(nev), np.zeros(nev)
-    _check(_lib().mbl_observables_extra(ctx.handle, L, nev, _ptr(V), float(q), _ptr(kl), _ptr(sqp), _ptr(fl),
-                                        _ptr(dyn)), ctx.handle)
+    tail = (_ptr(V), float(q), _ptr(kl), _ptr(sqp), _ptr(fl), _ptr(dyn))
+    if nup is None:
+        rc = _lib().mbl_observables_extra(ctx.handle, L, nev, *tail)
+    else:
+        rc = _lib().mbl_observables_extra_nup(ctx.handle, L, nup, nev, *tail)
+    _check(rc, ctx.handle)
     return kl[: max(nev - 1, 0)], sqp, fl, dyn
 
 
-def observables_extra_dev(ctx: Context, L: int, nev: int, d_evecs, q, d_kl, d_sqp, d_fluct, d_dynf, stream=None):
+def observables_extra_dev(ctx: Context, L: int, nev: int, d_evecs, q, d_kl, d_sqp, d_fluct, d_dynf, stream=None,
+                          nup: int | None = None):
     s = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
-    _check(_lib().mbl_observables_extra_dev(ctx.handle, L, nev, ctypes.c_void_p(d_evecs.data_ptr()), float(q),
-                                            ctypes.c_void_p(d_kl.data_ptr()), ctypes.c_void_p(d_sqp.data_ptr()),
-                                            ctypes.c_void_p(d_fluct.data_ptr()), ctypes.c_void_p(d_dynf.data_ptr()),
-                                            s), ctx.handle)
+    tail = (ctypes.c_void_p(d_evecs.data_ptr()), float(q)) + tuple(
+        ctypes.c_void_p(t.data_ptr()) for t in (d_kl, d_sqp, d_fluct, d_dynf)) + (s,)
+    if nup is None:
+        rc = _lib().mbl_observables_extra_dev(ctx.handle, L, nev, *tail)
+    else:
+        rc = _lib().mbl_observables_extra_nup_dev(ctx.handle, L, nup, nev, *tail)
+    _check(rc, ctx.handle)
 
 
 def entanglement_noalloc_dev(ctx: Context, L: int, nev: int, d_evecs, d_se, stream=None):
@@ -351,11 +380,9 @@ class ServedResult:
     reserved_bytes: int
 
 
-def _dim_of(L: int) -> int:
-    n = 1
-    for i in range(1, L // 2 + 1):
-        n = n * (L // 2 + i) // i
-    return n
+def _dim_of(L: int, nup: int = 0) -> int:
+    """Dimension C(L, nup) of a sector (nup = 0: the S^z_tot = 0 sector, L/2 up spins)."""
+    return math.comb(L, nup if nup > 0 else L // 2)
 
 
 class Server:
@@ -367,23 +394,24 @@ class Server:
         _check(_lib().mbl_server_start(ctx.handle, slots, hbm_budget_bytes), ctx.handle)
 
     def submit(self, L: int, h: float, seed: int, eps: float, nev: int, precision: int = MBL_PREC_FP32,
-               want_vectors: bool = False, fields: np.ndarray | None = None) -> int:
-        """Queue a job; `fields` (h_i, length L) replaces the seeded disorder of (h, seed)."""
+               want_vectors: bool = False, fields: np.ndarray | None = None, nup: int = 0) -> int:
+        """Queue a job; `fields` (h_i, length L) replaces the seeded disorder of (h, seed); `nup`
+        selects the sector (0: S^z_tot = 0 of even L)."""
         fp = None
         if fields is not None:
             fields = np.ascontiguousarray(fields, dtype=np.float64)
             if fields.shape != (L,):
                 raise ValueError("fields must have length L")
             fp = _ptr(fields)
-        q = _capi.Request(L, float(h), seed, fp, float(eps), nev, precision, 1 if want_vectors else 0)
+        q = _capi.Request(L, float(h), seed, fp, float(eps), nev, precision, 1 if want_vectors else 0, nup)
         t = ctypes.c_uint64()
         _check(_lib().mbl_submit(self.ctx.handle, ctypes.byref(q), ctypes.byref(t)), self.ctx.handle)
-        self._req[t.value] = (L, nev, want_vectors)
+        self._req[t.value] = (L, nup, nev, want_vectors)
         return t.value
 
     def _collect(self, ticket: int, timeout_s: float | None):
-        L, nev, vec = self._req[ticket]
-        n = _dim_of(L)
+        L, nup, nev, vec = self._req[ticket]
+        n = _dim_of(L, nup)
         ev, rs, r, s1, se = (np.zeros(nev), np.zeros(nev), np.zeros(max(nev - 2, 1)), np.zeros(nev),
                              np.zeros(nev))
         V = np.zeros((n, nev), order="F") if vec else None

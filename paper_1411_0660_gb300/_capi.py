@@ -52,7 +52,7 @@ class SolveStats(ctypes.Structure):
 
 class Request(ctypes.Structure):
     _fields_ = [("L", c_int), ("h", c_double), ("seed", c_uint64), ("fields", c_void_p), ("eps", c_double),
-                ("nev", c_int), ("precision", c_int), ("want_vectors", c_int)]
+                ("nev", c_int), ("precision", c_int), ("want_vectors", c_int), ("nup", c_int)]
 
 
 class Result(ctypes.Structure):
@@ -83,6 +83,9 @@ SIGNATURES = [
     ("mbl_ctx_synchronize", c_int, [c_void_p]),
     ("mbl_build_sector", c_int, [c_void_p, c_int, c_double, c_uint64, P(c_void_p)]),
     ("mbl_build_sector_fields", c_int, [c_void_p, c_int, c_void_p, c_double, P(c_void_p)]),
+    ("mbl_build_sector_nup", c_int, [c_void_p, c_int, c_int, c_double, c_uint64, P(c_void_p)]),
+    ("mbl_build_sector_fields_nup", c_int, [c_void_p, c_int, c_int, c_void_p, c_double, P(c_void_p)]),
+    ("mbl_sector_shape", c_int, [c_void_p, P(c_int), P(c_int)]),
     ("mbl_sector_destroy", None, [c_void_p]),
     ("mbl_sector_info", c_int, [c_void_p, P(c_int64), P(c_int64)]),
     ("mbl_sector_copy_basis", c_int, [c_void_p, c_void_p]),
@@ -111,6 +114,14 @@ SIGNATURES = [
                                       c_void_p]),
     ("mbl_observables_extra_dev", c_int, [c_void_p, c_int, c_int, c_void_p, c_double, c_void_p, c_void_p,
                                           c_void_p, c_void_p, c_void_p]),
+    ("mbl_observables_nup", c_int, [c_void_p, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p,
+                                    c_void_p, c_void_p]),
+    ("mbl_observables_nup_dev", c_int, [c_void_p, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p,
+                                        c_void_p, c_void_p, c_void_p]),
+    ("mbl_observables_extra_nup", c_int, [c_void_p, c_int, c_int, c_int, c_void_p, c_double, c_void_p, c_void_p,
+                                          c_void_p, c_void_p]),
+    ("mbl_observables_extra_nup_dev", c_int, [c_void_p, c_int, c_int, c_int, c_void_p, c_double, c_void_p,
+                                              c_void_p, c_void_p, c_void_p, c_void_p]),
     ("mbl_entanglement_noalloc_dev", c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p]),
     ("mbl_server_start", c_int, [c_void_p, c_int, c_size_t]),
     ("mbl_submit", c_int, [c_void_p, P(Request), P(c_uint64)]),

@@ -140,7 +140,8 @@ std::shared_ptr<Plan> get_plan(mbl_sector *sec) {
     Ctx *ctx = sec->ctx;
     std::shared_ptr<PlanCache> cache = ctx->plans;
     std::lock_guard<std::mutex> lk(cache->mu);
-    auto it = cache->m.find(sec->L);
+    const int key = sector_key(sec->L, sec->nup);
+    auto it = cache->m.find(key);
     if (it != cache->m.end()) return it->second;
     int64_t n = sec->n;
     std::vector<uint32_t> st(n);
@@ -152,7 +153,7 @@ std::shared_ptr<Plan> get_plan(mbl_sector *sec) {
     MBL_CUDA(cudaMemcpy(col.data(), sec->col.data(), sec->nnz * sizeof(int32_t), cudaMemcpyDeviceToHost));
     auto P = build_plan(sec->L, st, rp, col);
     upload_plan(ctx, *P);
-    cache->m[sec->L] = P;
+    cache->m[key] = P;
     return P;
 }
 
@@ -344,20 +345,21 @@ int mbl_ctx_synchronize(mbl_ctx *ctx) {
     API_CATCH(ctx)
 }
 
-static int build_common(mbl_ctx *ctx, int L, const double *h_host, double J, bool from_seed, double h, uint64_t seed,
-                        mbl_sector **out) {
+static int build_common(mbl_ctx *ctx, int L, int nup, const double *h_host, double J, bool from_seed, double h,
+                        uint64_t seed, mbl_sector **out) {
     if (!ctx || !out) return report(ctx, MBL_ERR_INVALID, "NULL argument");
     *out = nullptr;
-    if (L < 2 || L > 22 || (L & 1)) return report(ctx, MBL_ERR_INVALID, "L must be even with 2 <= L <= 22");
+    if (L < 2 || L > 22) return report(ctx, MBL_ERR_INVALID, "L must satisfy 2 <= L <= 22");
+    if (nup < 0 || nup > L) return report(ctx, MBL_ERR_INVALID, "nup must satisfy 0 <= nup <= L");
     if (from_seed && !(h >= 0.0)) return report(ctx, MBL_ERR_INVALID, "h must be >= 0");
     mbl_sector *s = new mbl_sector();
     API_TRY
     MBL_CUDA(cudaSetDevice(ctx->device));
     s->ctx = ctx;
     s->L = L;
+    s->nup = nup;
     s->J = J;
-    int64_t n = 1;
-    for (int i = 1; i <= L / 2; ++i) n = n * (L / 2 + i) / i;
+    const int64_t n = host_binom(L, nup);
     s->n = n;
     ProfScope ps(ctx, "sector_build", (double)n, ctx->stream);
     s->d_hfield.alloc(ctx, 32);
@@ -380,12 +382,30 @@ static int build_common(mbl_ctx *ctx, int L, const double *h_host, double J, boo
 }
 
 int mbl_build_sector(mbl_ctx *ctx, int L, double h, uint64_t seed, mbl_sector **out) {
-    return build_common(ctx, L, nullptr, 1.0, true, h, seed, out);
+    if (L & 1) return report(ctx, MBL_ERR_INVALID, "L must be even (mbl_build_sector_nup for other sectors)");
+    return build_common(ctx, L, L / 2, nullptr, 1.0, true, h, seed, out);
 }
 
 int mbl_build_sector_fields(mbl_ctx *ctx, int L, const double *h_i, double J, mbl_sector **out) {
     if (!h_i) return report(ctx, MBL_ERR_INVALID, "h_i is NULL");
-    return build_common(ctx, L, h_i, J, false, 0.0, 0, out);
+    if (L & 1) return report(ctx, MBL_ERR_INVALID, "L must be even (mbl_build_sector_fields_nup for other sectors)");
+    return build_common(ctx, L, L / 2, h_i, J, false, 0.0, 0, out);
+}
+
+int mbl_build_sector_nup(mbl_ctx *ctx, int L, int nup, double h, uint64_t seed, mbl_sector **out) {
+    return build_common(ctx, L, nup, nullptr, 1.0, true, h, seed, out);
+}
+
+int mbl_build_sector_fields_nup(mbl_ctx *ctx, int L, int nup, const double *h_i, double J, mbl_sector **out) {
+    if (!h_i) return report(ctx, MBL_ERR_INVALID, "h_i is NULL");
+    return build_common(ctx, L, nup, h_i, J, false, 0.0, 0, out);
+}
+
+int mbl_sector_shape(const mbl_sector *sec, int *L, int *nup) {
+    if (!sec) return report(nullptr, MBL_ERR_INVALID, "sector is NULL");
+    if (L) *L = sec->L;
+    if (nup) *nup = sec->nup;
+    return MBL_OK;
 }
 
 void mbl_sector_destroy(mbl_sector *sec) {
@@ -436,7 +456,7 @@ int mbl_sector_rank(const mbl_sector *sec, const uint32_t *states, int64_t count
     ds.alloc(sec->ctx, count);
     dr.alloc(sec->ctx, count);
     MBL_CUDA(cudaMemcpy(ds.data(), states, count * sizeof(uint32_t), cudaMemcpyHostToDevice));
-    launch_rank(sec->L, ds.data(), count, dr.data(), sec->ctx->stream);
+    launch_rank(sec->L, sec->nup, ds.data(), count, dr.data(), sec->ctx->stream);
     MBL_CUDA(cudaStreamSynchronize(sec->ctx->stream));
     MBL_CUDA(cudaMemcpy(ranks, dr.data(), count * sizeof(int64_t), cudaMemcpyDeviceToHost));
     API_CATCH(sec->ctx)
@@ -682,25 +702,26 @@ int mbl_solve_near(mbl_sector *sec, double eps, int nev, const mbl_opts *opts, d
     API_CATCH(sec->ctx)
 }
 
-int mbl_observables_dev(mbl_ctx *ctx, int L, int nev, const double *d_evals, const double *d_evecs, double *d_r,
-                        double *d_r_mean, double *d_s1p, double *d_se, void *stream) {
+// Observables of nev eigenvectors of the sector (L, nup); the entry points without nup take the
+// S^z_tot = 0 sector of even L.
+static int obs_dev(mbl_ctx *ctx, int L, int nup, int nev, const double *d_evals, const double *d_evecs, double *d_r,
+                   double *d_r_mean, double *d_s1p, double *d_se, void *stream) {
     if (!ctx || !d_evals || !d_evecs || !d_s1p || !d_se || (nev > 2 && !d_r))
         return report(ctx, MBL_ERR_INVALID, "NULL argument");
-    if (L < 2 || L > 22 || (L & 1)) return report(ctx, MBL_ERR_INVALID, "L must be even with 2 <= L <= 22");
+    if (L < 2 || L > 22 || nup < 0 || nup > L) return report(ctx, MBL_ERR_INVALID, "need 2 <= L <= 22, 0 <= nup <= L");
     API_TRY
     MBL_CUDA(cudaSetDevice(ctx->device));
     cudaStream_t st = stream ? (cudaStream_t)stream : ctx->stream;
-    observables_dev(ctx, L, nev, d_evals, d_evecs, d_r, d_r_mean, d_s1p, d_se, st);
+    observables_dev(ctx, L, nup, nev, d_evals, d_evecs, d_r, d_r_mean, d_s1p, d_se, st);
     API_CATCH(ctx)
 }
 
-int mbl_observables(mbl_ctx *ctx, int L, int nev, const double *evals, const double *evecs, double *r, double *r_mean,
-                    double *s1p, double *se) {
+static int obs_host(mbl_ctx *ctx, int L, int nup, int nev, const double *evals, const double *evecs, double *r,
+                    double *r_mean, double *s1p, double *se) {
     if (!ctx || !evals || !evecs || !s1p || !se || (nev > 2 && !r)) return report(ctx, MBL_ERR_INVALID, "NULL argument");
-    if (L < 2 || L > 22 || (L & 1)) return report(ctx, MBL_ERR_INVALID, "L must be even with 2 <= L <= 22");
+    if (L < 2 || L > 22 || nup < 0 || nup > L) return report(ctx, MBL_ERR_INVALID, "need 2 <= L <= 22, 0 <= nup <= L");
     API_TRY
-    int64_t n = 1;
-    for (int i = 1; i <= L / 2; ++i) n = n * (L / 2 + i) / i;
+    const int64_t n = host_binom(L, nup);
     if (nev < 1 || nev > n) fail(MBL_ERR_INVALID, "nev must be in [1, dim]");
     DVec<double> de, dv, dr, drm, ds, dse;
     de.alloc(ctx, nev);
@@ -711,7 +732,7 @@ int mbl_observables(mbl_ctx *ctx, int L, int nev, const double *evals, const dou
     dse.alloc(ctx, nev);
     MBL_CUDA(cudaMemcpy(de.data(), evals, nev * sizeof(double), cudaMemcpyHostToDevice));
     MBL_CUDA(cudaMemcpy(dv.data(), evecs, (size_t)n * nev * sizeof(double), cudaMemcpyHostToDevice));
-    observables_dev(ctx, L, nev, de.data(), dv.data(), dr.data(), drm.data(), ds.data(), dse.data(), ctx->stream);
+    observables_dev(ctx, L, nup, nev, de.data(), dv.data(), dr.data(), drm.data(), ds.data(), dse.data(), ctx->stream);
     if (nev > 2 && r) MBL_CUDA(cudaMemcpy(r, dr.data(), (nev - 2) * sizeof(double), cudaMemcpyDeviceToHost));
     if (r_mean) MBL_CUDA(cudaMemcpy(r_mean, drm.data(), sizeof(double), cudaMemcpyDeviceToHost));
     MBL_CUDA(cudaMemcpy(s1p, ds.data(), nev * sizeof(double), cudaMemcpyDeviceToHost));
@@ -719,26 +740,25 @@ int mbl_observables(mbl_ctx *ctx, int L, int nev, const double *evals, const dou
     API_CATCH(ctx)
 }
 
-int mbl_observables_extra_dev(mbl_ctx *ctx, int L, int nev, const double *d_evecs, double q, double *d_kl,
-                              double *d_sqp, double *d_fluct, double *d_dynf, void *stream) {
+static int obs_extra_dev(mbl_ctx *ctx, int L, int nup, int nev, const double *d_evecs, double q, double *d_kl,
+                         double *d_sqp, double *d_fluct, double *d_dynf, void *stream) {
     if (!ctx || !d_evecs || !d_sqp || !d_fluct || !d_dynf || (nev > 1 && !d_kl))
         return report(ctx, MBL_ERR_INVALID, "NULL argument");
-    if (L < 2 || L > 22 || (L & 1)) return report(ctx, MBL_ERR_INVALID, "L must be even with 2 <= L <= 22");
+    if (L < 2 || L > 22 || nup < 0 || nup > L) return report(ctx, MBL_ERR_INVALID, "need 2 <= L <= 22, 0 <= nup <= L");
     API_TRY
     MBL_CUDA(cudaSetDevice(ctx->device));
     cudaStream_t st = stream ? (cudaStream_t)stream : ctx->stream;
-    observables_extra_dev(ctx, L, nev, d_evecs, q, d_kl, d_sqp, d_fluct, d_dynf, st);
+    observables_extra_dev(ctx, L, nup, nev, d_evecs, q, d_kl, d_sqp, d_fluct, d_dynf, st);
     API_CATCH(ctx)
 }
 
-int mbl_observables_extra(mbl_ctx *ctx, int L, int nev, const double *evecs, double q, double *kl, double *sqp,
+static int obs_extra_host(mbl_ctx *ctx, int L, int nup, int nev, const double *evecs, double q, double *kl, double *sqp,
                           double *fluct, double *dynf) {
     if (!ctx || !evecs || !sqp || !fluct || !dynf || (nev > 1 && !kl))
         return report(ctx, MBL_ERR_INVALID, "NULL argument");
-    if (L < 2 || L > 22 || (L & 1)) return report(ctx, MBL_ERR_INVALID, "L must be even with 2 <= L <= 22");
+    if (L < 2 || L > 22 || nup < 0 || nup > L) return report(ctx, MBL_ERR_INVALID, "need 2 <= L <= 22, 0 <= nup <= L");
     API_TRY
-    int64_t n = 1;
-    for (int i = 1; i <= L / 2; ++i) n = n * (L / 2 + i) / i;
+    const int64_t n = host_binom(L, nup);
     if (nev < 1 || nev > n) fail(MBL_ERR_INVALID, "nev must be in [1, dim]");
     DVec<double> dv, dk, dq, df, dd;
     dv.alloc(ctx, (size_t)n * nev);
@@ -747,13 +767,60 @@ int mbl_observables_extra(mbl_ctx *ctx, int L, int nev, const double *evecs, dou
     df.alloc(ctx, nev);
     dd.alloc(ctx, nev);
     MBL_CUDA(cudaMemcpy(dv.data(), evecs, (size_t)n * nev * sizeof(double), cudaMemcpyHostToDevice));
-    observables_extra_dev(ctx, L, nev, dv.data(), q, dk.data(), dq.data(), df.data(), dd.data(), ctx->stream);
+    observables_extra_dev(ctx, L, nup, nev, dv.data(), q, dk.data(), dq.data(), df.data(), dd.data(), ctx->stream);
     MBL_CUDA(cudaStreamSynchronize(ctx->stream));
     if (nev > 1) MBL_CUDA(cudaMemcpy(kl, dk.data(), (nev - 1) * sizeof(double), cudaMemcpyDeviceToHost));
     MBL_CUDA(cudaMemcpy(sqp, dq.data(), nev * sizeof(double), cudaMemcpyDeviceToHost));
     MBL_CUDA(cudaMemcpy(fluct, df.data(), nev * sizeof(double), cudaMemcpyDeviceToHost));
     MBL_CUDA(cudaMemcpy(dynf, dd.data(), nev * sizeof(double), cudaMemcpyDeviceToHost));
     API_CATCH(ctx)
+}
+
+#define MBL_EVEN_L(ctx, L) \
+    if ((L) & 1) return report(ctx, MBL_ERR_INVALID, "L must be even (the _nup entry points take other sectors)")
+
+int mbl_observables_dev(mbl_ctx *ctx, int L, int nev, const double *d_evals, const double *d_evecs, double *d_r,
+                        double *d_r_mean, double *d_s1p, double *d_se, void *stream) {
+    MBL_EVEN_L(ctx, L);
+    return obs_dev(ctx, L, L / 2, nev, d_evals, d_evecs, d_r, d_r_mean, d_s1p, d_se, stream);
+}
+
+int mbl_observables_nup_dev(mbl_ctx *ctx, int L, int nup, int nev, const double *d_evals, const double *d_evecs,
+                            double *d_r, double *d_r_mean, double *d_s1p, double *d_se, void *stream) {
+    return obs_dev(ctx, L, nup, nev, d_evals, d_evecs, d_r, d_r_mean, d_s1p, d_se, stream);
+}
+
+int mbl_observables(mbl_ctx *ctx, int L, int nev, const double *evals, const double *evecs, double *r, double *r_mean,
+                    double *s1p, double *se) {
+    MBL_EVEN_L(ctx, L);
+    return obs_host(ctx, L, L / 2, nev, evals, evecs, r, r_mean, s1p, se);
+}
+
+int mbl_observables_nup(mbl_ctx *ctx, int L, int nup, int nev, const double *evals, const double *evecs, double *r,
+                        double *r_mean, double *s1p, double *se) {
+    return obs_host(ctx, L, nup, nev, evals, evecs, r, r_mean, s1p, se);
+}
+
+int mbl_observables_extra_dev(mbl_ctx *ctx, int L, int nev, const double *d_evecs, double q, double *d_kl,
+                              double *d_sqp, double *d_fluct, double *d_dynf, void *stream) {
+    MBL_EVEN_L(ctx, L);
+    return obs_extra_dev(ctx, L, L / 2, nev, d_evecs, q, d_kl, d_sqp, d_fluct, d_dynf, stream);
+}
+
+int mbl_observables_extra_nup_dev(mbl_ctx *ctx, int L, int nup, int nev, const double *d_evecs, double q,
+                                  double *d_kl, double *d_sqp, double *d_fluct, double *d_dynf, void *stream) {
+    return obs_extra_dev(ctx, L, nup, nev, d_evecs, q, d_kl, d_sqp, d_fluct, d_dynf, stream);
+}
+
+int mbl_observables_extra(mbl_ctx *ctx, int L, int nev, const double *evecs, double q, double *kl, double *sqp,
+                          double *fluct, double *dynf) {
+    MBL_EVEN_L(ctx, L);
+    return obs_extra_host(ctx, L, L / 2, nev, evecs, q, kl, sqp, fluct, dynf);
+}
+
+int mbl_observables_extra_nup(mbl_ctx *ctx, int L, int nup, int nev, const double *evecs, double q, double *kl,
+                              double *sqp, double *fluct, double *dynf) {
+    return obs_extra_host(ctx, L, nup, nev, evecs, q, kl, sqp, fluct, dynf);
 }
 
 }  // extern "C"

@@ -137,6 +137,17 @@ struct EntTables;  // entanglement block tables, observables.cu
 
 // Symbolic analyses by L.  Shared by a context and its serving workers; `mu` serializes lookups
 // and the (one-off) builds.
+// C(n, k) on the host (0 outside 0 <= k <= n)
+inline int64_t host_binom(int n, int k) {
+    if (k < 0 || k > n) return 0;
+    int64_t r = 1;
+    for (int i = 1; i <= k; ++i) r = r * (n - k + i) / i;
+    return r;
+}
+
+// Cache key of a sector (chain length L <= 32, nup up spins)
+inline int sector_key(int L, int nup) { return L * 64 + nup; }
+
 struct PlanCache {
     std::mutex mu;
     std::map<int, std::shared_ptr<Plan>> m;
@@ -150,7 +161,7 @@ struct Ctx {
     cudaStream_t stream = nullptr;
     std::string last_error;
     std::shared_ptr<PlanCache> plans = std::make_shared<PlanCache>();  // per L; shared with serving workers
-    std::map<int, std::shared_ptr<EntTables>> ent;  // per L
+    std::map<int, std::shared_ptr<EntTables>> ent;  // per sector (sector_key)
     int sm_count = 0;
     bool prof = false;
     std::map<std::string, ProfAcc> profile;
@@ -179,6 +190,7 @@ struct mbl_ctx : public mbl::Ctx {};
 struct mbl_sector {
     mbl::Ctx *ctx = nullptr;
     int L = 0;
+    int nup = 0;  // up spins of every basis state (S^z_tot = nup - L/2)
     int64_t n = 0, nnz = 0;
     double J = 1.0;
     double hfield[32] = {0};
@@ -198,7 +210,8 @@ namespace mbl {
 void upload_binomials();
 void launch_fields(int L, double h, uint64_t seed, double *d_out, cudaStream_t st);
 void build_sector_device(mbl_sector *sec, cudaStream_t st);
-void launch_rank(int L, const uint32_t *d_states, int64_t count, int64_t *d_ranks, cudaStream_t st);
+// rank of each state among the L-bit words with nup set bits (-1 if it is not one of them)
+void launch_rank(int L, int nup, const uint32_t *d_states, int64_t count, int64_t *d_ranks, cudaStream_t st);
 // y[i*ys_r + q*ys_c] = sum_j A_ij x[j*xs_r + q*xs_c] - shift x[i*xs_r + q*xs_c]   (FP64)
 void launch_spmv(const mbl_sector *sec, double shift, const double *x, int64_t xs_r, int64_t xs_c,
                  double *y, int64_t ys_r, int64_t ys_c, int p, cudaStream_t st);

@@ -102,13 +102,6 @@ __global__ void k_entropy_sum(int nev, int nblk, const int32_t *dA, const int64_
     se[j] = S;
 }
 
-static int64_t host_binom(int n, int k) {
-    if (k < 0 || k > n) return 0;
-    int64_t r = 1;
-    for (int i = 1; i <= k; ++i) r = r * (n - k + i) / i;
-    return r;
-}
-
 static int64_t host_rank(uint32_t s) {
     int64_t r = 0;
     int t = 0;
@@ -121,7 +114,7 @@ static int64_t host_rank(uint32_t s) {
     return r;
 }
 
-// Per basis state: m_A = S^z of sites 0 .. L/2-1 and M = sum_j S^z_j e^{2 pi i j / L}.
+// Per basis state: m_A = S^z of sites 0 .. floor(L/2)-1 and M = sum_j S^z_j e^{2 pi i j / L}.
 __global__ void k_state_tables(int64_t n, int L, const uint32_t *states, double *mA, double *Mre, double *Mim) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -139,15 +132,17 @@ __global__ void k_state_tables(int64_t n, int L, const uint32_t *states, double 
     Mim[i] = mi;
 }
 
-EntTables &ent_tables(Ctx *ctx, int L) {
-    auto it = ctx->ent.find(L);
+EntTables &ent_tables(Ctx *ctx, int L, int nup) {
+    const int key = sector_key(L, nup);
+    auto it = ctx->ent.find(key);
     if (it != ctx->ent.end()) return *it->second;
     auto T = std::make_shared<EntTables>();
+    // A = sites 0 .. floor(L/2) - 1 (the low bits), B = the rest
     int LA = L / 2, LB = L - L / 2;
     std::vector<int32_t> idx, da, db;
     std::vector<int64_t> boff;
     for (int nA = 0; nA <= LA; ++nA) {
-        int nB = L / 2 - nA;
+        int nB = nup - nA;
         if (nB < 0 || nB > LB) continue;
         std::vector<uint32_t> as, bs;
         for (uint32_t a = 0; a < (1u << LA); ++a) if (__builtin_popcount(a) == nA) as.push_back(a);
@@ -160,9 +155,9 @@ EntTables &ent_tables(Ctx *ctx, int L) {
     }
     {
         std::vector<uint32_t> st;
-        st.reserve((size_t)host_binom(L, L / 2));
+        st.reserve((size_t)host_binom(L, nup));
         for (uint32_t s = 0; s < (1u << L); ++s)
-            if (__builtin_popcount(s) == L / 2) st.push_back(s);
+            if (__builtin_popcount(s) == nup) st.push_back(s);
         T->d_states.alloc(ctx, st.size());
         MBL_CUDA(cudaMemcpy(T->d_states.data(), st.data(), st.size() * 4, cudaMemcpyHostToDevice));
         T->d_mA.alloc(ctx, st.size());
@@ -186,7 +181,7 @@ EntTables &ent_tables(Ctx *ctx, int L) {
     MBL_CUDA(cudaMemcpy(T->d_dA.data(), da.data(), da.size() * 4, cudaMemcpyHostToDevice));
     MBL_CUDA(cudaMemcpy(T->d_dB.data(), db.data(), db.size() * 4, cudaMemcpyHostToDevice));
     EntTables &ref = *T;
-    ctx->ent[L] = T;
+    ctx->ent[key] = T;
     return ref;
 }
 
@@ -296,13 +291,13 @@ __global__ void k_kl_fin(int npair, int nch, const double *part, const double *n
     kl[j] = f ? INFINITY : t / nrm2[j] + log(nrm2[j + 1]) - log(nrm2[j]);
 }
 
-void observables_extra_dev(Ctx *ctx, int L, int nev, const double *d_evecs, double q, double *d_kl, double *d_sqp,
-                           double *d_fluct, double *d_dynf, cudaStream_t st) {
+void observables_extra_dev(Ctx *ctx, int L, int nup, int nev, const double *d_evecs, double q, double *d_kl,
+                           double *d_sqp, double *d_fluct, double *d_dynf, cudaStream_t st) {
     ProfScope ps_all(ctx, "observables", (double)nev, st);
-    const int64_t n = host_binom(L, L / 2);
+    const int64_t n = host_binom(L, nup);
     if (nev < 1 || nev > n) fail(MBL_ERR_INVALID, "observables: nev must be in [1, dim]");
     if (!(q > 0.0) || q == 1.0 || !std::isfinite(q)) fail(MBL_ERR_INVALID, "observables: q must be positive and not 1");
-    EntTables &E = ent_tables(ctx, L);
+    EntTables &E = ent_tables(ctx, L, nup);
     // about two CTAs per SM over all vectors, chunks of at least 2048 rows
     const int nch = (int)std::max<int64_t>(1, std::min<int64_t>((2 * ctx->sm_count + nev - 1) / nev, n / 2048));
     const size_t need_part = (size_t)nev * nch * OBS_NS, need_nrm = (size_t)nev;
@@ -329,10 +324,10 @@ void observables_extra_dev(Ctx *ctx, int L, int nev, const double *d_evecs, doub
     }
 }
 
-void observables_dev(Ctx *ctx, int L, int nev, const double *d_evals, const double *d_evecs, double *d_r,
+void observables_dev(Ctx *ctx, int L, int nup, int nev, const double *d_evals, const double *d_evecs, double *d_r,
                      double *d_rmean, double *d_s1p, double *d_se, cudaStream_t st) {
     ProfScope ps_all(ctx, "observables", (double)nev, st);
-    int64_t n = host_binom(L, L / 2);
+    int64_t n = host_binom(L, nup);
     if (nev < 1 || nev > n) fail(MBL_ERR_INVALID, "observables: nev must be in [1, dim]");
     if (nev > 2 || d_rmean) {
         k_gap_ratio<<<1, 32, 0, st>>>(nev, d_evals, d_r, d_rmean);
@@ -342,7 +337,7 @@ void observables_dev(Ctx *ctx, int L, int nev, const double *d_evals, const doub
     nrm2.alloc(ctx, nev);
     k_s1p<<<nev, 256, 0, st>>>(n, d_evecs, d_s1p, nrm2.data());
     MBL_LAUNCH_CHECK();
-    EntTables &E = ent_tables(ctx, L);
+    EntTables &E = ent_tables(ctx, L, nup);
     int nb = E.nblk;
     int64_t batch = (int64_t)nev * nb;
     std::vector<int> hm(batch);

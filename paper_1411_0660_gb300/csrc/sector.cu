@@ -1,8 +1,9 @@
 // sector.cu -- disorder fields, combinadic basis, CSR Hamiltonian and FP64 SpMV on the device.
 //
-// Eq. 1 of arXiv:1411.0660 restricted to the S^z_tot = 0 sector (numerical-method section).
+// Eq. 1 of arXiv:1411.0660 restricted to a magnetization sector (numerical-method section: the
+// S^z = 0 sector of even L, the S^z = 1 sector of odd L; here any number nup of up spins).
 // All of it is integer bit manipulation plus a fixed-order FP64 diagonal, so the result is
-// bit-exact: the basis is the colex enumeration of L/2-subsets (the combinatorial number
+// bit-exact: the basis is the colex enumeration of nup-subsets (the combinatorial number
 // system), the column of a flipped state is its combinadic rank, and the diagonal is summed in
 // a fixed order with explicitly rounded multiplies and adds (no FMA contraction).
 #include "mbl_internal.h"
@@ -70,16 +71,16 @@ __device__ __forceinline__ uint32_t combinadic_unrank(int L, int K, int64_t r) {
     return s;
 }
 
-__global__ void k_unrank(int L, int64_t n, uint32_t *states) {
+__global__ void k_unrank(int L, int nup, int64_t n, uint32_t *states) {
     int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < n) states[k] = combinadic_unrank(L, L / 2, k);
+    if (k < n) states[k] = combinadic_unrank(L, nup, k);
 }
 
-__global__ void k_rank(int L, const uint32_t *in, int64_t count, int64_t *out) {
+__global__ void k_rank(int L, int nup, const uint32_t *in, int64_t count, int64_t *out) {
     int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= count) return;
     uint32_t s = in[k];
-    bool ok = (L >= 32 || (s >> L) == 0) && __popc(s) == L / 2;
+    bool ok = (L >= 32 || (s >> L) == 0) && __popc(s) == nup;
     out[k] = ok ? combinadic_rank(s) : -1;
 }
 
@@ -212,7 +213,7 @@ void build_sector_device(mbl_sector *sec, cudaStream_t st) {
     sec->rowptr.alloc(ctx, n + 1);
     int thr = 256;
     int64_t g = (n + thr - 1) / thr;
-    k_unrank<<<(unsigned)g, thr, 0, st>>>(sec->L, n, sec->states.data());
+    k_unrank<<<(unsigned)g, thr, 0, st>>>(sec->L, sec->nup, n, sec->states.data());
     MBL_LAUNCH_CHECK();
     DVec<int32_t> counts;
     counts.alloc(ctx, n);
@@ -238,9 +239,9 @@ void build_sector_device(mbl_sector *sec, cudaStream_t st) {
     MBL_CUDA(cudaStreamSynchronize(st));
 }
 
-void launch_rank(int L, const uint32_t *d_states, int64_t count, int64_t *d_ranks, cudaStream_t st) {
+void launch_rank(int L, int nup, const uint32_t *d_states, int64_t count, int64_t *d_ranks, cudaStream_t st) {
     if (count <= 0) return;
-    k_rank<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(L, d_states, count, d_ranks);
+    k_rank<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(L, nup, d_states, count, d_ranks);
     MBL_LAUNCH_CHECK();
 }
 

@@ -86,8 +86,9 @@ void Server::run(Job &J, mbl_ctx *w) {
     mbl_sector *sec = nullptr;
     bool held = false;
     try {
-        int rc = J.fields.empty() ? mbl_build_sector(w, q.L, q.h, q.seed, &sec)
-                                  : mbl_build_sector_fields(w, q.L, J.fields.data(), 1.0, &sec);
+        const int nup = q.nup > 0 ? q.nup : q.L / 2;
+        int rc = J.fields.empty() ? mbl_build_sector_nup(w, q.L, nup, q.h, q.seed, &sec)
+                                  : mbl_build_sector_fields_nup(w, q.L, nup, J.fields.data(), 1.0, &sec);
         if (rc != MBL_OK) fail(rc, mbl_last_error(w));
         std::shared_ptr<Plan> plan = get_plan(sec);
         mbl_opts o;
@@ -131,7 +132,7 @@ void Server::run(Job &J, mbl_ctx *w) {
         J.status = rc;
         if (rc != MBL_OK) J.err = mbl_last_error(w);
         double *d_r = dobs.data(), *d_rm = d_r + nev, *d_s1 = d_rm + 1, *d_se = d_s1 + nev;
-        int rc2 = mbl_observables_dev(w, q.L, nev, de.data(), dv.data(), d_r, d_rm, d_s1, d_se, nullptr);
+        int rc2 = mbl_observables_nup_dev(w, q.L, nup, nev, de.data(), dv.data(), d_r, d_rm, d_s1, d_se, nullptr);
         if (rc2 != MBL_OK) fail(rc2, mbl_last_error(w));
         MBL_CUDA(cudaEventRecord(ev.b, w->stream));
         MBL_CUDA(cudaStreamSynchronize(w->stream));
@@ -297,7 +298,9 @@ int mbl_submit(mbl_ctx *ctx, const mbl_request *req, uint64_t *ticket) {
     if (!ctx || !req || !ticket) return MBL_ERR_INVALID;
     Server *s = ctx->server;
     if (!s) return srv_report(ctx, MBL_ERR_INVALID, "no server: call mbl_server_start first");
-    if (req->L < 2 || req->L > 22 || (req->L & 1)) return srv_report(ctx, MBL_ERR_INVALID, "L must be even, 2..22");
+    if (req->L < 2 || req->L > 22) return srv_report(ctx, MBL_ERR_INVALID, "L must be in 2..22");
+    if (req->nup < 0 || req->nup > req->L || (req->nup == 0 && (req->L & 1)))
+        return srv_report(ctx, MBL_ERR_INVALID, "nup must be in 1..L (or 0 for the S^z = 0 sector of even L)");
     if (!(req->eps >= 0.0 && req->eps <= 1.0)) return srv_report(ctx, MBL_ERR_INVALID, "eps must be in [0, 1]");
     if (req->h < 0.0 || req->nev < 1) return srv_report(ctx, MBL_ERR_INVALID, "h >= 0 and nev >= 1 required");
     if (req->precision != MBL_PREC_FP32 && req->precision != MBL_PREC_FP64)
