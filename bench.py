@@ -277,7 +277,10 @@ def run_workload(args):
                 eps ~ U[0.05, 0.95], nev = 50, mixed precision; p50/p99 latency and throughput;
     large    -- the large sizes: L = 20, h = 3, `--seeds` seeds x eps in {0.2, 0.5, 0.8}, nev = 50, mixed
                 precision through the server; plus the symbolic analysis (fill-in, flops, device
-                footprint) of L = 18, 20 and 22, whose L = 22 fronts do not fit in one GPU."""
+                footprint) of L = 18, 20 and 22, whose L = 22 fronts do not fit in one GPU;
+    odd      -- the odd-L sector of the numerical-method section at its largest size: L = 19 with
+                10 up spins (its "S^z = 1", dimension 92 378), h in {1, 3, 5} x `--seeds` seeds x
+                eps in {0.2, 0.5, 0.8}, nev = 50, mixed precision through the server."""
     import numpy as np
     import torch
 
@@ -300,6 +303,15 @@ def run_workload(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         tickets = [srv.submit(L_, h, s, e, 50, precision=pr) for (L_, h, s, e, pr) in jobs]
+        out = [srv.wait(t) for t in tickets]
+        host_s = time.perf_counter() - t0
+    elif args.workload == "odd":
+        jobs = [(19, h, s, e, g.MBL_PREC_FP32) for s in range(args.seeds) for h in (1.0, 3.0, 5.0)
+                for e in (0.2, 0.5, 0.8)]
+        srv.wait(srv.submit(19, 3.0, 10 ** 6, 0.5, 50, nup=10))  # warm-up: plan, kernels, graphs
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        tickets = [srv.submit(L_, h, s, e, 50, precision=pr, nup=10) for (L_, h, s, e, pr) in jobs]
         out = [srv.wait(t) for t in tickets]
         host_s = time.perf_counter() - t0
     elif args.workload == "l16batch":
@@ -348,6 +360,7 @@ def run_workload(args):
                                "nconv": r.nconv, "status": r.status} for j, r in zip(jobs, out) if r.status != 0]}
     if plans is not None:
         line["plans"] = plans
+    if args.workload in ("large", "odd"):
         line["job_s"] = sorted(round((r.d_end_ms - r.d_start_ms) / 1e3, 2) for r in out)
     if args.workload == "serve":
         line.update({"rate_per_s": args.rate, "by_L": {str(L_): sum(1 for j in jobs if j[0] == L_) for L_ in (14, 16, 18, 20)}})
@@ -361,7 +374,7 @@ def main():
     ap.add_argument("--case", choices=["factor", "solve", "observables"], default=None,
                     help="run one factorization (and --reps solves) instead of the benchmark")
     ap.add_argument("--L", type=int, default=18)
-    ap.add_argument("--workload", choices=["l18", "l16batch", "serve", "large"], default="l18",
+    ap.add_argument("--workload", choices=["l18", "l16batch", "serve", "large", "odd"], default="l18",
                     help="l18: the benchmark line; l16batch / serve: the batched and serving configurations")
     ap.add_argument("--seeds", type=int, default=8, help="l16batch: seeds per (h, eps)")
     ap.add_argument("--requests", type=int, default=40, help="serve: number of requests")
