@@ -212,16 +212,31 @@ __global__ void k_zero(double *x, int64_t cnt) {
     if (t < cnt) x[t] = 0.0;
 }
 
-// R = B - (H - sigma) Y for p columns; per-CTA partial sums of |R_q|^2, |Y_q|^2, |B_q|^2
-__global__ void k_refine_resid(int64_t n, const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col,
-                               const double *__restrict__ val, double sigma, const double *__restrict__ B, int ldb,
-                               const double *__restrict__ Y, double *__restrict__ R, int p, double *part) {
-    __shared__ double acc[3 * 32];
-    for (int t = threadIdx.x; t < 3 * 32; t += blockDim.x) acc[t] = 0.0;
-    __syncthreads();
-    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+// Per-CTA sums over the entries t of a CTA of 256 threads with t mod p = q, in index order: the same
+// bits on every run (the decisions that read these norms must not depend on warp scheduling).
+// v: K arrays of 256 values in shared memory; out[k * p + q].
+template <int K>
+__device__ void cta_column_sums(const double (*v)[256], int p, int64_t t0, double *out) {
+    const int base = (int)(t0 % p);
+    for (int u = threadIdx.x; u < K * p; u += blockDim.x) {
+        const int k = u / p, q = u - k * p;
+        double sum = 0.0;
+        for (int j = (q - base + p) % p; j < 256; j += p) sum += v[k][j];
+        out[u] = sum;
+    }
+}
+
+// R = B - (H - sigma) Y for p columns; per-CTA partial sums of |R_q|^2, |Y_q|^2, |B_q|^2.  256 threads.
+__global__ void __launch_bounds__(256) k_refine_resid(int64_t n, const int64_t *__restrict__ rowptr,
+                                                      const int32_t *__restrict__ col, const double *__restrict__ val,
+                                                      double sigma, const double *__restrict__ B, int ldb,
+                                                      const double *__restrict__ Y, double *__restrict__ R, int p,
+                                                      double *part) {
+    __shared__ double v[3][256];
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x, t = t0 + threadIdx.x;
     int64_t i = t / p;
     int q = (int)(t - i * p);
+    double rr = 0.0, yy = 0.0, bb = 0.0;
     if (i < n) {
         double s = 0.0;
         for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) s = fma(val[e], Y[(int64_t)col[e] * p + q], s);
@@ -229,15 +244,15 @@ __global__ void k_refine_resid(int64_t n, const int64_t *__restrict__ rowptr, co
         double b = B[i * ldb + q];
         double r = b - (s - sigma * y);
         R[i * p + q] = r;
-        atomicAdd(&acc[q], r * r);
-        atomicAdd(&acc[32 + q], y * y);
-        atomicAdd(&acc[64 + q], b * b);
+        rr = r * r;
+        yy = y * y;
+        bb = b * b;
     }
+    v[0][threadIdx.x] = rr;
+    v[1][threadIdx.x] = yy;
+    v[2][threadIdx.x] = bb;
     __syncthreads();
-    for (int u = threadIdx.x; u < 3 * p; u += blockDim.x) {
-        int which = u / p, qq = u % p;
-        part[(size_t)blockIdx.x * 3 * p + u] = acc[which * 32 + qq];
-    }
+    cta_column_sums<3>(v, p, t0, part + (size_t)blockIdx.x * 3 * p);
 }
 
 // out[u] = sum_b part[b * w + u], u < w: one warp per output, lanes over the partial blocks (all
@@ -253,22 +268,25 @@ __global__ void k_reduce_parts(int nb, int w, const double *part, double *out) {
 }
 static unsigned reduce_grid(int w) { return (unsigned)((w + 7) / 8); }
 
-// per-CTA partial sums of |X_q|^2 and |Y_q - theta_q X_q|^2 for m columns (row-major, ld m)
-__global__ void k_pair_resid(int64_t n, int m, const double *X, const double *HX, const double *theta, double *part) {
-    extern __shared__ double acc2[];
-    for (int t = threadIdx.x; t < 2 * m; t += blockDim.x) acc2[t] = 0.0;
-    __syncthreads();
-    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+// per-CTA partial sums of |X_q|^2 and |Y_q - theta_q X_q|^2 for m columns (row-major, ld m), in a
+// fixed order (cta_column_sums).  256 threads.
+__global__ void __launch_bounds__(256) k_pair_resid(int64_t n, int m, const double *X, const double *HX,
+                                                    const double *theta, double *part) {
+    __shared__ double v[2][256];
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x, t = t0 + threadIdx.x;
     int64_t i = t / m;
     int q = (int)(t - i * m);
+    double xx = 0.0, rr = 0.0;
     if (i < n) {
         double x = X[i * m + q];
         double r = HX[i * m + q] - theta[q] * x;
-        atomicAdd(&acc2[q], x * x);
-        atomicAdd(&acc2[m + q], r * r);
+        xx = x * x;
+        rr = r * r;
     }
+    v[0][threadIdx.x] = xx;
+    v[1][threadIdx.x] = rr;
     __syncthreads();
-    for (int u = threadIdx.x; u < 2 * m; u += blockDim.x) part[(size_t)blockIdx.x * 2 * m + u] = acc2[u];
+    cta_column_sums<2>(v, m, t0, part + (size_t)blockIdx.x * 2 * m);
 }
 
 __global__ void k_scale_cols_to_cm(int64_t n, int m, const double *Y, const double *nrm2, double *out_cm) {
@@ -1114,6 +1132,10 @@ void extremal_bounds(mbl_sector *sec, double *emin, double *emax) {
     scr.alloc(ctx, 12 * (size_t)ldv);
     out.alloc(ctx, 4);
     double *v = V3.data(), *vprev = V3.data() + n, *dot = part.data(), *nrm = part.data() + LZ_BLOCKS;
+    // v_prev enters the first step multiplied by beta_{-1} = 0: it must hold numbers (0 * NaN is NaN,
+    // and pool memory keeps whatever it held before)
+    k_zero<<<nblk(2 * n), 256, 0, st>>>(V3.data(), 2 * n);
+    MBL_LAUNCH_CHECK();
     k_random_block<<<nblk(n), 256, 0, st>>>(n, 1, 0xB0B5EEDull, v, 1, 0);
     MBL_LAUNCH_CHECK();
     k_lanczos_norm_part<<<LZ_BLOCKS, 256, 0, st>>>(n, v, nrm);
@@ -1208,7 +1230,7 @@ void solve_near(mbl_sector *sec, double eps, int nev, const mbl_opts &o, double 
         unsigned nb = nblk(n * nev);
         part.alloc(ctx, (size_t)nb * 2 * nev);
         nrm.alloc(ctx, 2 * nev);
-        k_pair_resid<<<nb, 256, 2 * nev * sizeof(double), st>>>(n, nev, Yr.data(), HY.data(), th.data(), part.data());
+        k_pair_resid<<<nb, 256, 0, st>>>(n, nev, Yr.data(), HY.data(), th.data(), part.data());
         MBL_LAUNCH_CHECK();
         k_reduce_parts<<<reduce_grid(2 * nev), 256, 0, st>>>((int)nb, 2 * nev, part.data(), nrm.data());
         MBL_LAUNCH_CHECK();
@@ -1488,7 +1510,7 @@ void RitzH::run(mbl_sector *sec, KrylovSchur &ks, double sigma, double hnorm, do
     launch_spmv(sec, 0.0, Y.data(), nev, 1, HY.data(), nev, 1, nev, st);
     for (int j = 0; j < nev; ++j) evals[j] = gth[idx[j]];
     MBL_CUDA(cudaMemcpyAsync(thd.data(), evals.data(), nev * sizeof(double), cudaMemcpyHostToDevice, st));
-    k_pair_resid<<<nb, 256, 2 * nev * sizeof(double), st>>>(n, nev, Y.data(), HY.data(), thd.data(), part.data());
+    k_pair_resid<<<nb, 256, 0, st>>>(n, nev, Y.data(), HY.data(), thd.data(), part.data());
     MBL_LAUNCH_CHECK();
     k_reduce_parts<<<reduce_grid(2 * nev), 256, 0, st>>>((int)nb, 2 * nev, part.data(), nrm.data());
     MBL_LAUNCH_CHECK();

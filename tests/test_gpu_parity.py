@@ -137,6 +137,37 @@ def test_factor_solve_dev_matches_host(g, ctx, orc, prec):
     sec.close()
 
 
+def test_bounds_factor_and_solves_are_bit_reproducible(g, ctx):
+    """The extremal bounds, the factorization (every Schur-update mode) and the unrefined and
+    refined block solves give the same bits when repeated: none of their reductions depends on
+    the order in which CTAs or warps run."""
+    L, h, seed = 14, 5.0, 23
+    b = []
+    for _ in range(2):
+        sec = g.build_sector(ctx, L, h, seed)
+        b.append(g.extremal_bounds(sec))
+        sec.close()
+    assert b[0] == b[1]
+    sec = g.build_sector(ctx, L, h, seed)
+    lo, hi = b[0]
+    sigma = lo + 0.1 * (hi - lo)
+    B = np.random.default_rng(4).standard_normal((sec.dim, 8))
+    for kw in (dict(precision=1, tensor_cores=1), dict(precision=1, tensor_cores=0), dict(precision=0)):
+        xs = []
+        for _ in range(2):
+            f = g.factor(sec, sigma, **kw)
+            xs.append(f.solve(B, refine=False))
+            xs.append(f.solve(B, refine=False))
+            f.close()
+        for x in xs[1:]:
+            assert np.array_equal(x.view(np.uint64), xs[0].view(np.uint64))
+    f = g.factor(sec, sigma, precision=1)
+    xr = [f.solve(B, refine=True) for _ in range(2)]
+    assert np.array_equal(xr[0].view(np.uint64), xr[1].view(np.uint64))
+    f.close()
+    sec.close()
+
+
 # ---------------------------------------------------------------- eigenpairs + observables ---
 def _reference(orc, H, L, eps, nev):
     """Oracle spectrum around sigma: the full dense spectrum up to L = 12, else the nev + 12
