@@ -486,6 +486,11 @@ __global__ void __launch_bounds__(EIG_THREADS) k_syev(const int *mv, const int64
                 if (lo >= m - 1) s_done = 1;
             }
             __syncthreads();
+            // every thread takes the exit decision here, between the barriers: thread 0 rewrites
+            // s_done (and s_lo, s_hi) as soon as it has passed the barrier below, so a thread
+            // reading s_done after that barrier could see the next sweep's value, leave the loop
+            // one sweep early and reach the barriers after the loop out of step with the block
+            const bool done = s_done != 0;
             if (s_hi >= 0) {
                 int lo = s_lo, hi = s_hi;
                 // Z is column-major (column k contiguous): thread r walks its row down the sweep,
@@ -502,7 +507,7 @@ __global__ void __launch_bounds__(EIG_THREADS) k_syev(const int *mv, const int64
                 }
             }
             __syncthreads();
-            if (s_done) break;
+            if (done) break;
         }
         if (threadIdx.x == 0) {
             // selection sort of the eigenvalues; the permutation is kept in cs
