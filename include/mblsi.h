@@ -4,10 +4,12 @@
  *
  * Model (Eq. 1, field written as +h_i, periodic chain, J = 1 unless given):
  *     H = J sum_{i=0}^{L-1} S_i . S_{(i+1) mod L} + sum_i h_i S^z_i ,   h_i uniform on [-h, h]
- * restricted to the S^z_tot = 0 sector of even L (numerical-method section).  Site i is bit i
- * of a uint32 state, a set bit is spin up; the basis is every state with L/2 set bits in
- * ascending integer order (= the combinatorial number system, rank(s) = sum_t C(p_t, t+1) over
- * the set-bit positions p_0 < p_1 < ...).
+ * restricted to a magnetization sector (numerical-method section: S^z_tot = 0 for even L, the
+ * "S^z = 1" sector for odd L).  Site i is bit i of a uint32 state, a set bit is spin up; the basis
+ * of the sector with nup up spins is every state with nup set bits in ascending integer order
+ * (= the combinatorial number system, rank(s) = sum_t C(p_t, t+1) over the set-bit positions
+ * p_0 < p_1 < ...).  Entry points without "nup" in their name take nup = L/2 and even L; the
+ * *_nup entry points take any 0 <= nup <= L and either parity of L.
  *
  * Energy target (numerical-method section, read with E_min at eps = 0):
  *     sigma = E_min + eps (E_max - E_min),   ||H|| := max(|E_min|, |E_max|)
@@ -37,7 +39,7 @@ extern "C" {
 #endif
 
 #define MBL_OK 0
-#define MBL_ERR_INVALID 1       /* bad argument: L odd, L < 2, L > 22, nev outside [1, n] ... */
+#define MBL_ERR_INVALID 1       /* bad argument: L < 2, L > 22, odd L without nup, nev outside [1, n] ... */
 #define MBL_ERR_OOM 2           /* the HBM budget of the context cannot hold the request */
 #define MBL_ERR_SINGULAR 3      /* factorization broke down even with FP64 fronts */
 #define MBL_ERR_NOT_CONVERGED 4 /* eigenpairs below tolerance not reached; partial results out */
