@@ -53,3 +53,25 @@ def test_no_gpu_calls_needed_to_load(libpath):
     lib = _capi.load()
     assert b"sm_103a" in lib.mbl_version()
     assert lib.mbl_status_string(4) == b"not converged"
+
+
+def _prototypes():
+    """name -> number of parameters of every function prototype in include/mblsi.h."""
+    txt = open(os.path.join(ROOT, "include", "mblsi.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    out = {}
+    for m in re.finditer(r"\b(mbl_[a-z0-9_]+)\s*\(([^;{]*?)\)\s*;", txt):
+        params = m.group(2).strip()
+        out[m.group(1)] = 0 if params in ("", "void") else params.count(",") + 1
+    return out
+
+
+def test_binding_parameter_counts_match_the_header():
+    """Each ctypes signature has as many parameters as its C prototype (a missing or extra
+    argument would otherwise only surface as a wrong value on the GPU)."""
+    from paper_1411_0660_gb300 import _capi
+
+    proto = _prototypes()
+    bad = [(n, len(args), proto[n]) for n, _, args in _capi.SIGNATURES if n in proto and len(args) != proto[n]]
+    assert not bad, bad
+    assert len(proto) >= 20
