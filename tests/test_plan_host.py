@@ -32,7 +32,7 @@ def checker(tmp_path_factory):
     return exe
 
 
-@pytest.mark.parametrize("L,nup", [(2, 1), (8, 4), (10, 5), (11, 5), (12, 3), (13, 7), (14, 7), (15, 8), (16, 8),
+@pytest.mark.parametrize("L,nup", [(2, 1), (8, 4), (10, 5), (11, 5), (12, 3), (13, 7), (14, 7), (15, 8), (16, 8), (17, 9), (18, 9),
                                    (12, 1), (9, 0)])
 def test_plan_invariants(checker, L, nup):
     r = subprocess.run([checker, str(L), str(nup)], capture_output=True, text=True, timeout=120)
