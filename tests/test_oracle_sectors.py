@@ -117,3 +117,19 @@ def test_fluct_odd_chain_closed_forms(orc, L, nup):
     y = np.zeros(len(st))
     y[0] = y[j] = 1 / math.sqrt(2)
     assert abs(orc.fluct(L, y, st) - 0.25) < 1e-15
+
+
+@pytest.mark.parametrize("L,nup", [(7, 4), (9, 5), (8, 3)])
+def test_dynf_general_sector_limits(orc, L, nup):
+    """f = 1 - |<M>|^2 / <M^+ M>, M = sum_j S^z_j e^{2 pi i j / L}: a basis state has a definite M
+    (f = 0); the uniform vector of the sector is translation invariant, so <M> = 0 (f = 1)."""
+    st = orc.basis(L, nup)
+    for k in (0, len(st) // 2, len(st) - 1):
+        e = np.zeros(len(st))
+        e[k] = 1.0
+        s = int(st[k])
+        M = sum((0.5 if (s >> j) & 1 else -0.5) * np.exp(2j * math.pi * j / L) for j in range(L))
+        if abs(M) > 1e-12:
+            assert abs(orc.dynf(L, e, st)) < 1e-14
+    u = np.ones(len(st)) / math.sqrt(len(st))
+    assert abs(orc.dynf(L, u, st) - 1.0) < 1e-14
