@@ -730,11 +730,30 @@ int orc_nearest_shift_invert(int64_t n, const int64_t *rowptr, const int32_t *co
         }
     double *th = (double *)malloc((size_t)m * sizeof(double));
     int rc = orc_syev(m, G, th, 1);
+    /* The result is the nev eigenpairs nearest sigma.  Plain Rayleigh-Ritz on H can also give
+     * spurious interior Ritz values (mixtures of directions on both sides of sigma) whose pairs are
+     * not eigenpairs, so the Ritz values are taken in order of distance to sigma (ties: the lower)
+     * and a pair is kept only if its own residual ||H y - theta y|| is at most 1e-8 ||H|| (a
+     * converged pair is near 1e-13 ||H||, a spurious one many orders larger). */
+    int *order = (int *)malloc((size_t)m * sizeof(int));
     int *idx = (int *)malloc((size_t)nev * sizeof(int));
-    nearest_indices(m, th, sigma, nev, idx);
-    for (int t = 0; t < nev; ++t) {
-        const double *s = G + (size_t)idx[t] * m;
-        double *y = evecs + (size_t)t * N;
+    double *ys = (double *)malloc(N * (size_t)nev * sizeof(double));
+    double *rs = (double *)malloc((size_t)nev * sizeof(double));
+    for (int i = 0; i < m; ++i) order[i] = i;
+    for (int a = 1; a < m; ++a) {
+        int x = order[a], b = a - 1;
+        while (b >= 0) {
+            double dx_ = fabs(th[x] - sigma), db_ = fabs(th[order[b]] - sigma);
+            if (db_ < dx_ || (db_ == dx_ && th[order[b]] <= th[x])) break;
+            order[b + 1] = order[b];
+            --b;
+        }
+        order[b + 1] = x;
+    }
+    int kept = 0;
+    for (int t = 0; t < m && kept < nev; ++t) {
+        const double *s = G + (size_t)order[t] * m;
+        double *y = ys + (size_t)kept * N;
         for (int64_t i = 0; i < n; ++i) y[i] = 0.0;
         for (int a = 0; a < m; ++a) {
             const double *va = V + (size_t)a * N;
@@ -742,10 +761,29 @@ int orc_nearest_shift_invert(int64_t n, const int64_t *rowptr, const int32_t *co
         }
         double yn = sqrt(dot(n, y, y));
         for (int64_t i = 0; i < n; ++i) y[i] /= yn;
-        evals[t] = th[idx[t]];
-        orc_spmv(n, rowptr, col, val, evals[t], y, r);
-        resid[t] = sqrt(dot(n, r, r));
+        orc_spmv(n, rowptr, col, val, th[order[t]], y, r);
+        double res = sqrt(dot(n, r, r));
+        if (res > 1e-8 * hnorm) continue;
+        idx[kept] = order[t];
+        rs[kept] = res;
+        ++kept;
     }
+    /* ascending order of the kept eigenvalues */
+    for (int t = 0; t < kept; ++t) {
+        int best = t;
+        for (int u = t + 1; u < kept; ++u)
+            if (th[idx[u]] < th[idx[best]]) best = u;
+        evals[t] = th[idx[best]];
+        resid[t] = rs[best];
+        memcpy(evecs + (size_t)t * N, ys + (size_t)best * N, N * sizeof(double));
+        if (best != t) {
+            int ti = idx[t]; idx[t] = idx[best]; idx[best] = ti;
+            double tr = rs[t]; rs[t] = rs[best]; rs[best] = tr;
+            memcpy(ys + (size_t)best * N, ys + (size_t)t * N, N * sizeof(double));
+        }
+    }
+    free(order); free(ys); free(rs);
+    if (kept < nev) converged = 0;
     free(idx); free(th); free(G); free(HV);
     free(V); free(w); free(r); free(dx); free(al); free(be); free(nu); free(zl);
     orc_ldlt_free(f);

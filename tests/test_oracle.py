@@ -245,6 +245,23 @@ def test_shift_invert_matches_dense(orc, L, h, eps):
     assert np.abs(d.r - s.r).max() < 1e-9
 
 
+def test_shift_invert_keeps_no_spurious_ritz_value(orc):
+    """Regression: plain Rayleigh-Ritz on H in a shift-invert Krylov space can yield an interior Ritz
+    value that is not an eigenvalue (here -2.8254779 at L = 14, h = 1.5, seed 61, eps = 0.32 with 32
+    pairs asked).  The window must equal the library eigensolver's 32 nearest eigenvalues."""
+    L, h, seed, eps, nev = 14, 1.5, 61, 0.32, 32
+    H = orc.csr(L, orc.fields(L, h, seed))
+    w = np.linalg.eigvalsh(H.dense())
+    sigma = w[0] + eps * (w[-1] - w[0])
+    hn = max(abs(w[0]), abs(w[-1]))
+    s = orc.nearest_shift_invert(H, sigma, nev, hn)
+    d = np.abs(w - sigma)
+    want = np.sort(w[np.lexsort((w, d))[:nev]])
+    assert np.abs(np.sort(s.evals) - want).max() < 1e-12 * hn
+    assert s.resid.max() < 1e-12 * hn
+    assert np.all(np.diff(s.evals) >= 0)
+
+
 # ---------------------------------------------------------------- observables ----------------
 def test_gap_ratio_hand_example(orc):
     r, rm = orc.gap_ratio(np.array([0.0, 1.0, 3.0, 4.0, 4.5]))
