@@ -96,14 +96,15 @@ def test_sector_solve_near_and_observables(g, ctx, orc, L, nup, h, seed, eps, ne
     assert res.nconv == nev
     assert window_equivalent(res.evals, spectrum, sigma, nev, hn)
     Y = res.evecs
-    for j in range(nev):
-        assert np.linalg.norm(H.matvec(Y[:, j]) - res.evals[j] * Y[:, j]) <= EIG_TOL * hn
+    res_o = np.array([np.linalg.norm(H.matvec(Y[:, j]) - res.evals[j] * Y[:, j]) for j in range(nev)])
+    assert np.all(res_o <= EIG_TOL * hn)
     assert np.abs(Y.T @ Y - np.eye(nev)).max() < 1e-10
     r_g, rm_g, s1_g, se_g = g.observables(ctx, L, res.evals, Y, nup=nup)
     r_o, rm_o = orc.gap_ratio(res.evals)
     assert np.allclose(r_g, r_o, atol=1e-12, equal_nan=True)
     kl_g, sq_g, fl_g, df_g = g.observables_extra(ctx, L, Y, 2.0, nup=nup)
-    mask = well_conditioned(spectrum, res.evals, res.resid)
+    # the vectors compared are chosen by the oracle's residuals, not the GPU's own report
+    mask = well_conditioned(spectrum, res.evals, res_o)
     for j in np.nonzero(mask)[0]:
         y = Y[:, j]
         assert abs(s1_g[j] - orc.s1p(y)) <= OBS_TOL
