@@ -12,6 +12,8 @@
 //   3. back-transformation by the stored reflectors, one warp per vector.
 #include <cfloat>
 
+#include <mutex>
+
 #include "mbl_internal.h"
 
 namespace mbl {
@@ -766,24 +768,40 @@ void syev_bisect32(int m, double *d_A, double *d_w, double *d_work, cudaStream_t
     syev_bisect_t<float>(m, d_A, d_w, d_work, st);
 }
 
-cudaError_t syev_preload() {
+namespace {
+// Shared-memory attributes of the batched eigensolver, set once per device (function attributes
+// are per device).  Setting them also loads both kernels, which otherwise load lazily on first
+// launch and take device memory then.
+std::mutex g_syev_mu;
+bool g_syev_ready[64] = {};
+
+cudaError_t syev_prepare_current_device() {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(g_syev_mu);
+    if (dev >= 0 && dev < 64 && g_syev_ready[dev]) return cudaSuccess;
     cudaFuncAttributes fa;
-    return cudaFuncGetAttributes(&fa, k_syev<double>);
+    e = cudaFuncSetAttribute(k_syev<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             EIG_SMEM_MAX_M * EIG_SMEM_MAX_M * sizeof(double));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_syev<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 EIG_SMEM_MAX_M * EIG_SMEM_MAX_M * sizeof(float));
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_syev<double>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_syev<float>);
+    if (e == cudaSuccess && dev >= 0 && dev < 64) g_syev_ready[dev] = true;
+    return e;
 }
+}  // namespace
+
+cudaError_t syev_preload() { return syev_prepare_current_device(); }
 
 void syev_batched(int batch, const int *d_m, const int64_t *d_aoff, const int64_t *d_woff, double *d_A,
                   double *d_w, int vecs, const int *d_sel, int mmax, double *d_work, int *d_info, cudaStream_t st,
                   bool fp32) {
     (void)d_sel;
     if (batch <= 0) return;
-    static std::atomic<bool> attr{false};  // per process: one device
-    if (!attr) {
-        MBL_CUDA(cudaFuncSetAttribute(k_syev<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      EIG_SMEM_MAX_M * EIG_SMEM_MAX_M * sizeof(double)));
-        MBL_CUDA(cudaFuncSetAttribute(k_syev<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      EIG_SMEM_MAX_M * EIG_SMEM_MAX_M * sizeof(float)));
-        attr = true;
-    }
+    MBL_CUDA(syev_prepare_current_device());
     if (fp32) {
         if (mmax > EIG_SMEM_MAX_M) fail(MBL_ERR_INVALID, "FP32 small eigensolver limited to order 160");
         k_syev<float><<<batch, EIG_THREADS, (size_t)mmax * mmax * sizeof(float), st>>>(

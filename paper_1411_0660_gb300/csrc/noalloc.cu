@@ -128,19 +128,23 @@ __global__ void __launch_bounds__(256) k_na_gram(int h, int64_t n, const double 
     }
 }
 
-__global__ void k_na_entropy(int h, int nev, const int64_t *woff, const double *lam, double *se) {
+// S_E of each vector from its blocks' Schmidt weights; NaN where the eigensolver flagged a block
+// as not converged (info != 0), so that a wrong entropy is never returned silently.
+__global__ void k_na_entropy(int h, int nev, const int64_t *woff, const double *lam, const int *info, double *se) {
     __shared__ int64_t B[17][9];
     fill_binom(B);
     __syncthreads();
     const int nb = h + 1;
     for (int j = threadIdx.x; j < nev; j += blockDim.x) {
         double S = 0.0;
+        bool bad = false;
         for (int q = 0; q < nb; ++q) {
+            bad = bad || info[(int64_t)j * nb + q] != 0;
             const double *l = lam + woff[(int64_t)j * nb + q];
             for (int i = 0; i < (int)B[h][q]; ++i)
                 if (l[i] > 1e-15) S -= l[i] * log(l[i]);
         }
-        se[j] = S;
+        se[j] = bad ? nan("") : S;
     }
 }
 
@@ -215,7 +219,7 @@ void entanglement_noalloc(Ctx *ctx, int L, int nev, const double *d_evecs, doubl
     k_na_gram<<<(unsigned)batch, 256, 0, st>>>(h, n, d_evecs, goff, G);
     MBL_LAUNCH_CHECK();
     syev_batched((int)batch, m, goff, woff, G, lam, 0, nullptr, mmax, work, info, st);
-    k_na_entropy<<<1, 64, 0, st>>>(h, nev, woff, lam, d_se);
+    k_na_entropy<<<1, 64, 0, st>>>(h, nev, woff, lam, info, d_se);
     MBL_LAUNCH_CHECK();
 }
 

@@ -13,6 +13,7 @@
 // one batched eigenvalue launch.
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 
 #include "observables.h"
 
@@ -90,16 +91,21 @@ __global__ void k_gram(int64_t n, int nblk, const double *Y, const double *nrm2,
     }
 }
 
-__global__ void k_entropy_sum(int nev, int nblk, const int32_t *dA, const int64_t *woff, const double *lam, double *se) {
+// S_E of vector j from the Schmidt weights of its nblk blocks; NaN if the eigensolver reported a
+// block it did not converge (info != 0), so that a wrong value is never returned silently.
+__global__ void k_entropy_sum(int nev, int nblk, const int32_t *dA, const int64_t *woff, const double *lam,
+                              const int *info, double *se) {
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= nev) return;
     double S = 0.0;
+    bool bad = false;
     for (int q = 0; q < nblk; ++q) {
+        bad = bad || info[(int64_t)j * nblk + q] != 0;
         const double *l = lam + woff[(int64_t)j * nblk + q];
         for (int i = 0; i < dA[q]; ++i)
             if (l[i] > 1e-15) S -= l[i] * log(l[i]);
     }
-    se[j] = S;
+    se[j] = bad ? nan("") : S;
 }
 
 static int64_t host_rank(uint32_t s) {
@@ -366,17 +372,23 @@ void observables_dev(Ctx *ctx, int L, int nup, int nev, const double *d_evals, c
     MBL_CUDA(cudaMemcpyAsync(dm.data(), hm.data(), batch * sizeof(int), cudaMemcpyHostToDevice, st));
     MBL_CUDA(cudaMemcpyAsync(dgo.data(), hg.data(), batch * sizeof(int64_t), cudaMemcpyHostToDevice, st));
     MBL_CUDA(cudaMemcpyAsync(dwo.data(), hw.data(), batch * sizeof(int64_t), cudaMemcpyHostToDevice, st));
-    static std::atomic<bool> attr{false};  // per process: one device
-    if (!attr) {
-        MBL_CUDA(cudaFuncSetAttribute(k_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, 12288 * 8));
-        attr = true;
+    {
+        // function attributes are per device: set once on each device that runs this
+        static std::mutex mu;
+        static bool ready[64] = {};
+        std::lock_guard<std::mutex> lk(mu);
+        if (ctx->device < 0 || ctx->device >= 64 || !ready[ctx->device]) {
+            MBL_CUDA(cudaFuncSetAttribute(k_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, 12288 * 8));
+            if (ctx->device >= 0 && ctx->device < 64) ready[ctx->device] = true;
+        }
     }
     k_gram<<<(unsigned)batch, 256, 12288 * 8, st>>>(n, nb, d_evecs, nrm2.data(), E.d_idx.data(), E.d_boff.data(),
                                                     E.d_dA.data(), E.d_dB.data(), dgo.data(), G.data());
     MBL_LAUNCH_CHECK();
     syev_batched((int)batch, dm.data(), dgo.data(), dwo.data(), G.data(), lam.data(), 0, nullptr, E.dAmax,
                  work.data(), info.data(), st);
-    k_entropy_sum<<<(nev + 63) / 64, 64, 0, st>>>(nev, nb, E.d_dA.data(), dwo.data(), lam.data(), d_se);
+    k_entropy_sum<<<(nev + 63) / 64, 64, 0, st>>>(nev, nb, E.d_dA.data(), dwo.data(), lam.data(), info.data(),
+                                                   d_se);
     MBL_LAUNCH_CHECK();
     MBL_CUDA(cudaStreamSynchronize(st));
 }
