@@ -7,13 +7,17 @@ job's fields, extremal bounds, numeric factorization (FP32 fronts on tcgen05, FP
 block shift-invert Lanczos, Rayleigh-Ritz on H, observables.  The timed region runs all K steps'
 jobs in the served form (continuous batching on `--slots` worker streams with HBM admission): the
 value is the converged eigenpairs (residual <= 1e-10 ||H||) over the device span of those jobs
-(CUDA events).  The same jobs then run one after another on one stream for the kernel profile and
-the roofline, and a subset runs on the plain FP64 path for the mixed-versus-FP64 comparison.  The
-symbolic analysis of the L = 18 pattern is setup (built once in warm-up, excluded).
+(CUDA events).  After it, on the first `--compare-jobs` jobs and the same server: `--repeats`
+served mixed runs (the spread of the value) and one served FP64 run (mixed versus FP64 in the same
+form); then the same jobs one after another on one stream for the kernel profile and the roofline,
+and every `--fp64-stride`-th of them on the FP64 and split-BF16 paths one after another.  The
+symbolic analysis of the L = 18 pattern is setup (built once in warm-up, excluded).  One compact
+JSON line goes to stdout; the per-job records and the full profile go to `--detail`.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--batch B] [--slots S] [--impl reference]
     python bench.py --case {factor,solve} [--L L] [--reps R] [--precision fp32|fp64]   (profiler cases)
     python bench.py --case observables [--L L] [--reps R]   (the eigenvector observables on nev = 50 vectors)
+    python bench.py --workload {l16batch,serve,large,odd}   (the other configurations)
 """
 from __future__ import annotations
 
@@ -39,6 +43,11 @@ PROF_KEYS = ("factor_fp32", "schur_fp32", "schur_tc", "trisolve_fp32", "refine_s
              "syev_fp32", "syev_fallback", "oa_refine", "trisolve_fp64", "factor_fp64", "syev_rr_fp64",
              "gm_deflate", "gm_spmv", "gm_orth", "f_assemble", "f_panel", "f_build_g", "syev_rr_bisect")
 METRIC = "eigenpairs/s near eps (res<=1e-10||H||), L=18, mixed vs FP64; p50/p99 latency"
+WORKLOAD = ("L=18 shift-invert, dim 48620, nev=50, h in {0.5,1,2,3,4,5}, eps in {0.1,0.5,0.9}, "
+            "seeds 1000+k")
+# job-time classes of the compact line (device ms per job of the sequential profiled pass)
+BREAKDOWN = ("factor_fp32", "schur_tc", "f_panel", "f_build_g", "trisolve_fp32", "gm_deflate", "gm_orth",
+             "gm_spmv", "orth", "syev_krylov", "syev_rr", "ritz_h", "extremal_bounds", "observables")
 
 
 def jobs_for_step(step: int, batch: int, rank: int = 0, world: int = 1):
@@ -99,10 +108,29 @@ def measured_peaks():
 
 
 # --------------------------------------------------------------------------------------------
+def oracle_l18_scale():
+    """Ratio (mean oracle seconds per L = 16 job) / (mean per L = 18 job) of the stored oracle runs in
+    tests/golden (same oracle, one core each, jobs of the L = 18 workload's shape): an L = 18 oracle job
+    takes about half an hour, so the L = 18 rate is the timed L = 16 rate times this ratio."""
+    t = {}
+    for L_ in (16, 18):
+        with open(os.path.join(ROOT, "tests", "golden", f"oracle_L{L_}.json")) as f:
+            js = json.load(f)["jobs"]
+        t[L_] = sum(j["oracle_seconds"] for j in js) / len(js)
+    return t[16] / t[18], t[16], t[18]
+
+
+def _oracle_pool_rate(pool, jobs):
+    t0 = time.perf_counter()
+    res = pool.map(_oracle_job, jobs)
+    return sum(res), time.perf_counter() - t0
+
+
 def run_reference(args):
-    """The oracle as it stands on the host cores: a bounded sample of the same L=18 jobs is out of
-    reach (about an hour per job), so each step runs the oracle on L=16 jobs of the same shape and
-    reports their eigenpairs/s, labelled as such."""
+    """The oracle as it stands on the host cores.  Each timed step runs one L = 16 job of the L = 18
+    workload's shape per core (a bounded sample: an L = 18 oracle job takes about half an hour); the
+    reported value is that rate carried to L = 18 by the stored oracle timings (oracle_l18_scale),
+    labelled as extrapolated, with the measured L = 16 rate beside it."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
@@ -118,21 +146,25 @@ def run_reference(args):
             # warm-up steps only start the workers (imports, oracle library load): one L=12 job each
             Ls = 16 if s >= args.warmup else 12
             jobs = [(Ls, h, seed, eps, NEV if Ls == 16 else 20) for (h, seed, eps) in jobs_for_step(s, per_step)]
-            t0 = time.perf_counter()
-            res = pool.map(_oracle_job, jobs)
-            dt = time.perf_counter() - t0
+            p, dt = _oracle_pool_rate(pool, jobs)
             if s >= args.warmup:
                 t_steps.append(dt)
-                pairs += sum(res)
+                pairs += p
     tot = sum(t_steps)
-    v = pairs / tot
+    v16 = pairs / tot
+    scale, t16, t18 = oracle_l18_scale()
+    v = v16 * scale
+    cpu = {"value": v, "unit": "eigenpairs/s", "cores": cores, "kind": "oracle",
+           "sample": f"{per_step * args.steps} oracle shift-invert jobs at L=16 (one per core, nev=50) timed: "
+                     f"{v16:.3f} eigenpairs/s; carried to L=18 by the stored oracle seconds per job "
+                     f"(L=16 {t16:.1f} s, L=18 {t18:.0f} s, ratio {scale:.4f}): extrapolated",
+           "value_l16_measured": v16, "extrapolated": True}
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "eigenpairs/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "oracle sample: L=16 jobs shaped like the L=18 workload (h in {0.5..5}, "
-                                   "eps in {0.1,0.5,0.9}, nev=50)", "L": 16, "nev": NEV, "jobs_per_step": per_step},
-            "cpu_baseline": {"value": v, "unit": "eigenpairs/s", "cores": cores, "kind": "oracle",
-                             "sample": f"{per_step * args.steps} oracle shift-invert jobs at L=16 (one per core)"},
+            "config": {"workload": WORKLOAD, "L": L, "nev": NEV, "jobs_per_step": per_step,
+                       "sample_L": 16, "extrapolated_to_L": 18},
+            "cpu_baseline": cpu,
             "e2e": {"value": v, "unit": "eigenpairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -147,30 +179,89 @@ def _oracle_job(job):
     return int((r.resid <= 1e-10 * hn).sum())
 
 
-def cpu_baseline_sample(seconds: float = 20.0):
-    """Oracle on the host cores for a bounded time: L=16 jobs of the workload's shape."""
+def cpu_baseline_sample():
+    """Oracle on the host cores: one L = 16 job of the workload's shape per core (about 20-35 s),
+    carried to L = 18 by the stored oracle timings and labelled as extrapolated."""
     import multiprocessing as mp
 
     cores = os.cpu_count() or 1
     ctx = mp.get_context("spawn")
     jobs = [(16, h, seed, eps, NEV) for (h, seed, eps) in jobs_for_step(0, cores)]
-    t0 = time.perf_counter()
     with ctx.Pool(cores) as pool:
-        res = pool.map(_oracle_job, jobs)
-    dt = time.perf_counter() - t0
-    return {"value": sum(res) / dt, "unit": "eigenpairs/s", "cores": cores, "kind": "oracle",
-            "sample": f"{len(jobs)} oracle shift-invert jobs at L=16 (nev=50, one per core) in {dt:.1f} s; "
-                      f"an L=18 oracle job takes about an hour on one core"}
+        p, dt = _oracle_pool_rate(pool, jobs)
+    v16 = p / dt
+    scale, t16, t18 = oracle_l18_scale()
+    return {"value": v16 * scale, "unit": "eigenpairs/s", "cores": cores, "kind": "oracle",
+            "sample": f"{len(jobs)} oracle shift-invert jobs at L=16 (nev=50, one per core) in {dt:.1f} s = "
+                      f"{v16:.3f} eigenpairs/s; carried to L=18 by the stored oracle seconds per job "
+                      f"(L=16 {t16:.1f} s, L=18 {t18:.0f} s): extrapolated",
+            "value_l16_measured": v16, "extrapolated": True}
 
 
 # --------------------------------------------------------------------------------------------
+def run_batch_case(args):
+    """Profiler case of the batched solve: --batch factorizations of L-site sectors (h = 3, seeds 5, 6,
+    ..., eps = 0.5), then --reps unrefined block solves of all of them in shared launches (8
+    right-hand sides each), inside an NVTX range "solve".  Prints the CUDA-event time per batched
+    solve and the achieved algorithmic bandwidth."""
+    import numpy as np
+    import torch
+
+    import paper_1411_0660_gb300 as g
+
+    ctx = g.Context(0)
+    K = args.batch
+    secs, facts = [], []
+    for k in range(K):
+        sec = g.build_sector(ctx, args.L, 3.0, 5 + k)
+        lo, hi = g.extremal_bounds(sec)
+        secs.append(sec)
+        facts.append(g.factor(sec, lo + 0.5 * (hi - lo), precision=g.MBL_PREC_FP32))
+    n, p = secs[0].dim, 8
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(7)
+    d_b = [torch.randn(n * p, dtype=torch.float64, device="cuda", generator=gen) for _ in range(K)]
+    d_x = [torch.zeros_like(b) for b in d_b]
+    for _ in range(2):
+        g.factor_solve_batch_dev(facts, d_b, d_x, p)
+    st = facts[0].stats()
+    nvtx = getattr(torch.cuda, "nvtx", None)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if nvtx is not None:
+        nvtx.range_push("solve")
+    e0.record()
+    for _ in range(args.reps):
+        g.factor_solve_batch_dev(facts, d_b, d_x, p)
+    e1.record()
+    torch.cuda.synchronize()
+    if nvtx is not None:
+        nvtx.range_pop()
+    ms = e0.elapsed_time(e1) / args.reps
+    algo = K * (2.0 * (st["nnz_l"] + n) * 4 + 16.0 * n * p)
+    peak = (measured_peaks() or {}).get("hbm_gbs")
+    gbs = algo / (ms * 1e-3) / 1e9
+    print(json.dumps({"case": "solve_batch", "L": args.L, "jobs": K, "reps": args.reps, "ms_per_batched_solve": ms,
+                      "ms_per_solve": ms / K, "algorithmic_bytes": algo, "achieved_gbs": gbs,
+                      "frac_of_measured_hbm": gbs / peak if peak else None}))
+    for f in facts:
+        f.close()
+    for s_ in secs:
+        s_.close()
+    ctx.close()
+    return 0
+
+
 def run_case(args):
     """A single-operation case for profilers: one L-site sector (h = 3, seed 5), one factorization of
-    H - sigma at eps = 0.5, then --reps unrefined block solves with 8 right-hand sides."""
+    H - sigma at eps = 0.5, then --reps unrefined block solves with 8 right-hand sides (with
+    --batch K > 1: the batched solve of K factorizations, run_batch_case)."""
     import numpy as np
 
     import paper_1411_0660_gb300 as g
 
+    if args.case == "solve" and args.batch > 1 and args.batch_case:
+        return run_batch_case(args)
     ctx = g.Context(0)
     sec = g.build_sector(ctx, args.L, 3.0, 5)
     lo, hi = g.extremal_bounds(sec)
@@ -369,6 +460,28 @@ def run_workload(args):
     return 0
 
 
+def served_run(srv, jobs, fields, precision=None, want_vectors=False):
+    """Submit every job at once to the server and wait for all: converged pairs, the device span
+    (first job start to last job end, CUDA events), the host wall time and per-job latencies."""
+    import paper_1411_0660_gb300 as g
+
+    prec = g.MBL_PREC_FP32 if precision is None else precision
+    t0 = time.perf_counter()
+    tickets = [srv.submit(L, h, seed, eps, NEV, precision=prec, want_vectors=want_vectors, fields=hf)
+               for (h, seed, eps), hf in zip(jobs, fields)]
+    out = [srv.wait(t) for t in tickets]
+    host_s = time.perf_counter() - t0
+    span_ms = max(r.d_end_ms for r in out) - min(r.d_start_ms for r in out)
+    pairs = sum(r.nconv for r in out)
+    return {"pairs": pairs, "span_ms": span_ms, "host_s": host_s, "value": pairs / (span_ms / 1e3),
+            "lat_ms": sorted(r.t_end_ms - r.t_submit_ms for r in out), "results": out}
+
+
+def _pct(xs, q):
+    xs = sorted(xs)
+    return xs[min(len(xs) - 1, int(q * len(xs)))]
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--case", choices=["factor", "solve", "observables"], default=None,
@@ -390,9 +503,20 @@ def main():
     ap.add_argument("--batch", type=int, default=6)
     ap.add_argument("--slots", type=int, default=8, help="concurrent jobs (worker streams) in the timed region")
     ap.add_argument("--impl", default="gb300")
-    ap.add_argument("--fp64-stride", type=int, default=3)
+    ap.add_argument("--compare-jobs", type=int, default=18,
+                    help="jobs of the comparison arms (served FP64 vs served mixed, repeats, profiled pass)")
+    ap.add_argument("--repeats", type=int, default=3, help="served mixed runs of the comparison jobs (spread)")
+    ap.add_argument("--fp64-stride", type=int, default=3,
+                    help="sequential FP64 and split-BF16 passes on every stride-th comparison job (0: skip)")
+    ap.add_argument("--detail", default="/tmp/bench_detail.json",
+                    help="file for the per-job records and the full kernel-class profile")
+    ap.add_argument("--clocks-csv", default="/tmp/clocks_bench.csv",
+                    help="nvidia-smi samples taken during the timed region")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch-jobs", type=int, default=16, help="served form: jobs per batched solve launch (1: off)")
+    ap.add_argument("--batch-window-us", type=float, default=300.0, help="served form: batcher collection window")
     args = ap.parse_args()
+    args.batch_case = args.case == "solve" and "--batch" in sys.argv
     if args.case == "observables":
         return run_observables_case(args)
     if args.case:
@@ -422,7 +546,7 @@ def main():
 
         dist.init_process_group("nccl")
     ctx = g.Context(local)
-    n = 48620
+    n = math.comb(L, L // 2)
     d_ev = torch.empty(NEV, dtype=torch.float64, device="cuda")
     d_vec = torch.empty(n * NEV, dtype=torch.float64, device="cuda")
     d_res = torch.empty(NEV, dtype=torch.float64, device="cuda")
@@ -447,62 +571,80 @@ def main():
         dist.barrier()
 
     timed_jobs = [j for s in range(args.steps) for j in jobs_for_step(args.warmup + s, args.batch, rank, world)]
-    clocks = ClockSampler(os.path.join(ROOT, "gpurun_out", "clocks_bench.csv") if os.path.isdir(
-        os.path.join(ROOT, "gpurun_out")) else "/tmp/clocks_bench.csv")
+    clocks = ClockSampler(args.clocks_csv)
     nvtx = getattr(torch.cuda, "nvtx", None)
 
-    # ---- timed region: the served (continuously batched) form, all K steps' jobs in flight ----
-    # Jobs run on `slots` worker streams as HBM allows; the span is measured on the device with the
-    # jobs' CUDA events (first start to last end, relative to one reference event).
     # the jobs' inputs: their disorder realizations h_i (host arrays, prepared untimed)
     host_fields = []
     for (h, seed, eps) in timed_jobs:
         sec0 = g.build_sector(ctx, L, h, seed)
         host_fields.append(np.ascontiguousarray(sec0.fields()))
         sec0.close()
-    srv = g.Server(ctx, slots=args.slots)
+    srv = g.Server(ctx, slots=args.slots, batch_jobs=args.batch_jobs, batch_window_us=args.batch_window_us)
     for t in [srv.submit(L, h, seed, eps, NEV) for (h, seed, eps) in jobs_for_step(0, args.slots, rank, world)]:
         srv.wait(t)  # worker warm-up: kernels loaded, graphs captured once per worker
+    for t in [srv.submit(L, h, seed, eps, NEV, precision=g.MBL_PREC_FP64)
+              for (h, seed, eps) in jobs_for_step(1, 2, rank, world)]:
+        srv.wait(t)  # FP64 kernels and graphs too (used by the comparison arm after the timed region)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
+
+    # ---- timed region: the served (continuously batched) form, all K steps' jobs in flight ----
+    # Jobs run on `slots` worker streams as HBM allows; the span is measured on the device with the
+    # jobs' CUDA events (first start to last end).  The host wall time of the same region, with the
+    # fields copied in and eigenpairs, vectors and observables copied back per job, is the e2e number.
     l0 = g.launch_count()
+    b0 = srv.stats()
     with clocks:
         torch.cuda.synchronize()
         if nvtx is not None:
             nvtx.range_push("timed")
-        t_host0 = time.perf_counter()
-        tickets = [srv.submit(L, h, seed, eps, NEV, want_vectors=True, fields=hf)
-                   for (h, seed, eps), hf in zip(timed_jobs, host_fields)]
-        served = [srv.wait(t) for t in tickets]
+        main_run = served_run(srv, timed_jobs, host_fields, want_vectors=True)
         torch.cuda.synchronize()
-        t_host = time.perf_counter() - t_host0
         if nvtx is not None:
             nvtx.range_pop()
     launches = g.launch_count() - l0
     srv_stats = srv.stats()
-    srv.stop()
-    ms = max(r.d_end_ms for r in served) - min(r.d_start_ms for r in served)
-    pairs = sum(r.nconv for r in served)
-    lat = [(r.t_end_ms - r.t_submit_ms) / 1e3 for r in served]
+    # the batched solves of the timed region (CUDA events around each batch on the batcher's stream)
+    served_solve = {k: srv_stats[k] - b0[k] for k in ("solve_batches", "batched_solves", "batch_ms", "batch_bytes")}
+    ms = main_run["span_ms"]
+    pairs = main_run["pairs"]
+    t_host = main_run["host_s"]
     tmax = ms
     if dist:
-        t = torch.tensor([ms, pairs], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t[:1], op=dist.ReduceOp.MAX)
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
         tt = torch.tensor([float(pairs)], dtype=torch.float64, device="cuda")
         dist.all_reduce(tt, op=dist.ReduceOp.SUM)
         tmax, pairs = float(t[0]), int(tt[0])
     value = pairs / (tmax / 1e3)
+    served_res = main_run.pop("results")
 
-    # ---- the same jobs one after another on one stream (profiled): kernel breakdown, roofline ----
+    # ---- comparison arms on the first `compare_jobs` jobs, same server (same slots) ----
+    cmp_idx = list(range(min(args.compare_jobs, len(timed_jobs))))
+    cmp_jobs = [timed_jobs[i] for i in cmp_idx]
+    cmp_fields = [host_fields[i] for i in cmp_idx]
+    reps = []
+    for _ in range(max(1, args.repeats)):
+        r = served_run(srv, cmp_jobs, cmp_fields)
+        r.pop("results")
+        reps.append(r)
+    s64 = served_run(srv, cmp_jobs, cmp_fields, precision=g.MBL_PREC_FP64)
+    s64_res = s64.pop("results")
+    srv.stop()
+    rep_vals = [r["value"] for r in reps]
+    served_mixed_cmp = statistics.median(rep_vals)
+
+    # ---- the comparison jobs one after another on one stream (profiled): kernel breakdown, roofline ----
     ctx.set_profiling(True)
-    job_ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(timed_jobs) + 1)]
+    job_ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(cmp_jobs) + 1)]
     job_pairs, job_stats = [], []
-    ev_mixed = torch.empty((len(timed_jobs), NEV), dtype=torch.float64, device="cuda")
+    ev_mixed = torch.empty((len(cmp_jobs), NEV), dtype=torch.float64, device="cuda")
     torch.cuda.synchronize()
     if nvtx is not None:
         nvtx.range_push("sequential")
-    for i, (h, seed, eps) in enumerate(timed_jobs):
+    for i, (h, seed, eps) in enumerate(cmp_jobs):
         job_ev[i].record()
         nc, st = device_job(h, seed, eps, g.MBL_PREC_FP32)
         job_pairs.append(nc)
@@ -512,76 +654,60 @@ def main():
     torch.cuda.synchronize()
     if nvtx is not None:
         nvtx.range_pop()
-    job_ms = [job_ev[i].elapsed_time(job_ev[i + 1]) for i in range(len(timed_jobs))]
+    job_ms = [job_ev[i].elapsed_time(job_ev[i + 1]) for i in range(len(cmp_jobs))]
     prof = {k: ctx.profile(k) for k in PROF_KEYS}
     ctx.set_profiling(False)
-    sequential = {"value": sum(job_pairs) / (sum(job_ms) / 1e3), "unit": "eigenpairs/s",
-                  "ms_per_job": sum(job_ms) / len(job_ms)}
+    seq_mixed = sum(job_pairs) / (sum(job_ms) / 1e3)
 
-    # ---- the plain FP64 GPU path on a subset of the same jobs (every third one: all h and eps) ----
-    sub = list(range(0, len(timed_jobs), max(1, args.fp64_stride)))
-    fp64 = None
-    if args.fp64_stride > 0 and sub:
-        ctx.set_profiling(True)
-        torch.cuda.synchronize()
+    # mixed against FP64 eigenvalues, per job (served FP64 results), relative to ||H||
+    dev_vs_fp64 = []
+    for i, (h, seed, eps) in enumerate(cmp_jobs):
+        sec = g.build_sector(ctx, L, h, seed)
+        lo, hi = g.extremal_bounds(sec)
+        sec.close()
+        hn_i = max(abs(lo), abs(hi))
+        d = float(np.abs(ev_mixed[i].cpu().numpy() - s64_res[i].evals).max()) / hn_i
+        job_stats[i]["max_dev_vs_fp64"] = d
+        dev_vs_fp64.append(d)
+
+    # ---- sequential FP64 and split-BF16 on every stride-th comparison job ----
+    seq = None
+    sub = list(range(0, len(cmp_jobs), args.fp64_stride)) if args.fp64_stride > 0 else []
+    if sub:
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
         a.record()
         p64 = 0
-        ev64 = {}
         for i in sub:
-            h, seed, eps = timed_jobs[i]
-            nc, st = device_job(h, seed, eps, g.MBL_PREC_FP64)
+            nc, st = device_job(*cmp_jobs[i], g.MBL_PREC_FP64)
             p64 += nc
-            ev64[i] = d_ev.clone()
         b.record()
         torch.cuda.synchronize()
         t64 = a.elapsed_time(b)
-        f64 = ctx.profile("factor_fp64")
-        ctx.set_profiling(False)
-        t_mixed = sum(job_ms[i] for i in sub)
-        p_mixed = sum(job_pairs[i] for i in sub)
-        fp64 = {"value": p64 / (t64 / 1e3), "unit": "eigenpairs/s", "jobs": len(sub),
-                "ms_per_job": t64 / len(sub), "factor_ms_per_job": f64["ms"] / max(1, f64["launches"]),
-                "mixed_same_jobs": {"value": p_mixed / (t_mixed / 1e3), "ms_per_job": t_mixed / len(sub)},
-                "mixed_over_fp64": (p_mixed / t_mixed) / max(p64 / t64, 1e-30),
-                "served_mixed_over_fp64": value / max(p64 / (t64 / 1e3), 1e-30)}
-        torch.cuda.synchronize()
-        # the same subset with split-BF16 Schur updates (3xBF16 on tcgen05), the third precision mode
         a.record()
-        pbf, evbf, bf_solves = 0, {}, 0
+        pbf, bf_solves, bf_dev = 0, 0, 0.0
         for i in sub:
-            h, seed, eps = timed_jobs[i]
-            nc, st = device_job(h, seed, eps, g.MBL_PREC_FP32, tc=2)
+            nc, st = device_job(*cmp_jobs[i], g.MBL_PREC_FP32, tc=2)
             pbf += nc
             bf_solves += st["solves"]
-            evbf[i] = d_ev.clone()
+            bf_dev = max(bf_dev, float(np.abs(d_ev.cpu().numpy() - s64_res[i].evals).max()))
         b.record()
         torch.cuda.synchronize()
         tbf = a.elapsed_time(b)
-        # per result: mixed-precision eigenvalues against the FP64 path's, relative to ||H|| ~ |E| scale
-        bf_dev = 0.0
-        for i in sub:
-            h, seed, eps = timed_jobs[i]
-            sec = g.build_sector(ctx, L, h, seed)
-            lo, hi = g.extremal_bounds(sec)
-            sec.close()
-            hn_i = max(abs(lo), abs(hi))
-            d = (ev_mixed[i] - ev64[i]).abs().max().item()
-            job_stats[i]["max_dev_vs_fp64"] = d / hn_i
-            bf_dev = max(bf_dev, (evbf[i] - ev64[i]).abs().max().item() / hn_i)
-        fp64["bf16x3_same_jobs"] = {"value": pbf / (tbf / 1e3), "ms_per_job": tbf / len(sub), "converged": pbf,
-                                    "solves": bf_solves, "mixed_tf32x3_solves": sum(job_stats[i]["solves"] for i in sub),
-                                    "max_dev_vs_fp64": bf_dev}
+        t_mixed = sum(job_ms[i] for i in sub)
+        p_mixed = sum(job_pairs[i] for i in sub)
+        seq = {"jobs": len(sub), "mixed": p_mixed / (t_mixed / 1e3), "fp64": p64 / (t64 / 1e3),
+               "bf16x3": pbf / (tbf / 1e3), "mixed_over_fp64": (p_mixed / t_mixed) / max(p64 / t64, 1e-30),
+               "ms_per_job": {"mixed": t_mixed / len(sub), "fp64": t64 / len(sub), "bf16x3": tbf / len(sub)},
+               "solves": {"tf32x3": sum(job_stats[i]["solves"] for i in sub), "bf16x3": bf_solves}}
 
-    # ---- end to end: the timed served region itself, on the host clock (host fields in; eigenvalues,
-    # residuals, observables and eigenvectors back in host memory) ----
-    n_dim = math.comb(L, L // 2)
+    # ---- end to end: the timed served region itself, on the host clock ----
     h2d_job = L * 8
-    d2h_job = 8 * (NEV * 4 + (NEV - 2) + n_dim * NEV)
+    d2h_job = 8 * (NEV * 4 + (NEV - 2) + n * NEV)
+    # host wall of the timed served region: fields h_i in per job; eigenvalues, residuals,
+    # observables and eigenvectors back to host memory
     e2e = {"value": pairs / t_host, "unit": "eigenpairs/s", "h2d_bytes_per_step": h2d_job * args.batch,
-           "d2h_bytes_per_step": d2h_job * args.batch,
-           "note": "host wall time of the timed served region; inputs h_i copied from host memory per job, "
-                   "eigenvalues, residuals, observables and eigenvectors copied back"}
+           "d2h_bytes_per_step": d2h_job * args.batch}
 
     # ---- roofline of the dominant kernel class ----
     peaks = measured_peaks()
@@ -593,14 +719,13 @@ def main():
     if dom in ("trisolve_fp32", "refine_spmv"):
         achieved = per_launch_work / (per_launch_ms / 1e3) / 1e9
         peak = peaks["hbm_gbs"] if peaks else 6800.0
-        roof = {"bound": "hbm", "unit": "GB/s", "peak_source": "measured copy" if peaks else "fallback"}
+        roof = {"bound": "hbm", "unit": "GB/s", "peak_source": "of measured copy" if peaks else "of fallback"}
     elif dom == "schur_tc":
-        # 3xTF32 on tcgen05: algorithmic flops counted once; TF32 dense peak = measured BF16 x 1.1/2.25
         achieved = per_launch_work / (per_launch_ms / 1e3) / 1e12
         bf = (peaks or {}).get("bf16_tflops", 1900.0)
         peak = bf * 1.1 / 2.25
         roof = {"bound": "tensor", "unit": "TFLOP/s",
-                "peak_source": "measured BF16 x nominal TF32/BF16 ratio (1.1/2.25)" if peaks else "fallback"}
+                "peak_source": "of measured BF16 x nominal TF32/BF16 (1.1/2.25)" if peaks else "of fallback"}
     elif dom == "schur_fp32":
         achieved = per_launch_work / (per_launch_ms / 1e3) / 1e12
         peak = 152 * 128 * 2 * clk * 1e6 / 1e12
@@ -621,41 +746,70 @@ def main():
             traffic = None
     roof.update({"achieved": achieved, "peak": peak, "frac": achieved / peak, "traffic": traffic, "kernel": dom,
                  "launch_ms": per_launch_ms, "work_per_launch": per_launch_work})
-    if traffic is not None:
-        roof["traffic_source"] = "profiles/solve_l18_fp32_traffic.md (ncu dram__bytes_read + write, one solve)"
+    roof_seq = {"kernel": dom, "achieved": achieved, "frac": achieved / peak, "launch_ms": per_launch_ms}
+    if served_solve["solve_batches"] > 0 and dom == "trisolve_fp32":
+        # the served form's solves: one launch of the batched sequence per batch of jobs, timed with
+        # CUDA events on the batcher's stream inside the timed region
+        nb = served_solve["solve_batches"]
+        kmean = served_solve["batched_solves"] / nb
+        per_launch_ms = served_solve["batch_ms"] / nb
+        per_launch_work = served_solve["batch_bytes"] / nb
+        achieved = per_launch_work / (per_launch_ms / 1e3) / 1e9
+        traffic = None
+        try:
+            with open(os.path.join(ROOT, "profiles", "solve_l18_fp32_batch_traffic.md")) as fp:
+                for ln in fp:
+                    if ln.startswith("traffic_bytes_per_solve:"):
+                        traffic = float(ln.split(":")[1]) * kmean
+        except OSError:
+            traffic = None
+        roof = {"bound": "hbm", "unit": "GB/s", "peak_source": roof["peak_source"], "achieved": achieved,
+                "peak": peak, "frac": achieved / peak, "traffic": traffic,
+                "kernel": "trisolve_fp32 batched (served, timed region)", "launch_ms": per_launch_ms,
+                "work_per_launch": per_launch_work, "jobs_per_launch": kmean, "launches": nb,
+                "sequential": roof_seq}
 
     if rank == 0:
-        lat_ms = sorted(1e3 * x for x in lat)
+        nj = len(cmp_jobs)
         line = {
             "metric": METRIC, "value": value, "unit": "eigenpairs/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": tmax / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32 fronts + f64 refinement", "data": "synthetic",
-            "config": {"workload": "L=18 shift-invert: dim 48620, nev=50, h in {0.5,1,2,3,4,5}, eps in "
-                                   "{0.1,0.5,0.9}, seeds 1000+k; served on worker streams", "L": L, "nev": NEV,
-                       "jobs_per_step": args.batch, "slots": args.slots,
-                       "parallelism": f"replicas x{world}", "l2": "working set (factor ~0.5 GB, fronts ~3 GB) "
-                                                                  "far above the 129 MB L2"},
+            "config": {"workload": WORKLOAD + f"; served on {args.slots} worker streams", "L": L, "nev": NEV,
+                       "jobs_per_step": args.batch, "slots": args.slots, "parallelism": f"replicas x{world}",
+                       "l2": "inputs > L2 (factor 0.5 GB/job)"},
             "gpu_launches": launches,
             "clocks": clocks.summary(local),
-            "latency_ms": {"p50": lat_ms[len(lat_ms) // 2], "p99": lat_ms[min(len(lat_ms) - 1,
-                                                                              int(0.99 * len(lat_ms)))],
-                           "note": "submission to completion; all timed jobs submitted at once"},
-            "served": {"slots": args.slots, "host_s": t_host, "peak_reserved_gb": srv_stats["peak_reserved_bytes"] / 1e9,
-                       "budget_gb": srv_stats["budget_bytes"] / 1e9},
-            "sequential": sequential,
-            "fp64_path": fp64,
-            "per_job": [{"h": j[0], "seed": j[1], "eps": j[2], "nconv": job_pairs[i], "ms": round(job_ms[i], 1),
-                         "max_resid_rel": job_stats[i]["max_resid"], "restarts": job_stats[i]["restarts"],
-                         "solves": job_stats[i]["solves"], "fp64_fallback": job_stats[i]["fp64_fallback"],
-                         **({"max_dev_vs_fp64": job_stats[i]["max_dev_vs_fp64"]}
-                            if "max_dev_vs_fp64" in job_stats[i] else {})}
-                        for i, j in enumerate(timed_jobs)],
+            "latency_ms": {"p50": _pct(main_run["lat_ms"], 0.5), "p99": _pct(main_run["lat_ms"], 0.99)},
+            "jobs": {"n": len(served_res), "converged": sum(r.nconv for r in served_res),
+                     "requested": NEV * len(served_res), "min_nconv": min(r.nconv for r in served_res),
+                     "max_resid_over_H": max(float(s["max_resid"]) for s in job_stats),
+                     "fp64_fallbacks": sum(int(s["fp64_fallback"]) for s in job_stats)},
+            "repeats": {"n": len(rep_vals), "jobs": nj, "values": [round(v, 2) for v in rep_vals],
+                        "spread": (max(rep_vals) - min(rep_vals)) / statistics.median(rep_vals)},
+            "mixed_vs_fp64": {"jobs": nj, "served_mixed": served_mixed_cmp, "served_fp64": s64["value"],
+                              "served_ratio": served_mixed_cmp / max(s64["value"], 1e-30),
+                              "fp64_converged": s64["pairs"], "max_eval_dev_over_H": max(dev_vs_fp64),
+                              "sequential": seq},
+            "ms_per_job": {k: round(prof[k]["ms"] / nj, 2) for k in BREAKDOWN},
+            "sequential_mixed": {"value": seq_mixed, "ms_per_job": sum(job_ms) / nj,
+                                 "solves_per_job": sum(s["solves"] for s in job_stats) / nj},
+            "served": {"host_s": t_host, "peak_reserved_gb": srv_stats["peak_reserved_bytes"] / 1e9},
             "roofline": roof,
-            "profile": prof,
             "e2e": e2e,
             "cpu_baseline": cpu,
+            "detail": args.detail,
         }
-        print(json.dumps(line))
+        detail = {"per_job": [{"h": j[0], "seed": j[1], "eps": j[2], "nconv": job_pairs[i], "ms": job_ms[i],
+                               **{k: v for k, v in job_stats[i].items()}} for i, j in enumerate(cmp_jobs)],
+                  "served_latency_ms": main_run["lat_ms"], "profile": prof, "line": line}
+        try:
+            with open(args.detail, "w") as fo:
+                json.dump(detail, fo)
+        except OSError:
+            line["detail"] = None
+        sys.stdout.flush()
+        print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
     return 0

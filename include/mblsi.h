@@ -74,6 +74,9 @@ typedef struct mbl_opts {
     int solve_dataflow;   /* 1: solves as one persistent dataflow kernel per sweep; 0: one */
                           /*    graph-captured launch per level gather and solve panel  [0]    */
     int deflate;          /* FGMRES preconditioner deflated by the kept Ritz vectors    [1]    */
+    double wait_limit_s;  /* limit of each bounded dependency wait of the dataflow solves, */
+                          /*    seconds in [0, 60]; 0 = 1 s.  An expired wait stops the   */
+                          /*    waiting CTA and the call returns MBL_ERR_TIMEOUT        [0]    */
 } mbl_opts;
 
 typedef struct mbl_factor_stats {
@@ -177,6 +180,16 @@ int mbl_factor_solve(mbl_factorization *f, const double *b, double *x, int nrhs,
  * call at a time.  Unrefined solves (refine = 0) run without device allocation; MBL_ERR_TIMEOUT if
  * a bounded dependency wait of the solve kernels expired. */
 int mbl_factor_solve_dev(mbl_factorization *f, const double *d_b, double *d_x, int nrhs, int refine, void *stream);
+/* Unrefined solves of K factorizations at once: d_x[k] = (L_k D_k L_k^T)^-1 d_b[k] for k < K, each
+ * an n x nrhs column-major device block (leading dimension n), owned by the caller.  All K
+ * factorizations must come from sectors of the same (L, nup) -- one symbolic plan -- and the same
+ * precision, each at most once, none made with solve_dataflow.  The jobs share every launch of the
+ * solve sequence (the same kernels on each factorization's own buffers), so each result is
+ * bit-identical to mbl_factor_solve_dev(refine = 0) of its factorization alone.  Enqueued on
+ * `stream` (NULL = the first factorization's context stream); returns once complete.  1 <= K <= 64.
+ * Not in the paper: the batching pattern for many small jobs of one sector size. */
+int mbl_factor_solve_batch_dev(mbl_factorization *const *fs, int K, const double *const *d_b,
+                               double *const *d_x, int nrhs, void *stream);
 /* Symbolic analysis of the sector's pattern (nested-dissection ordering, supernodes, schedules;
  * numerical-method section: the analysis phase of the direct solver), built on the host on first
  * use for this L and cached in the context, and its predicted fill-in and device footprint.  No
@@ -330,7 +343,23 @@ typedef struct mbl_server_stats {
     int64_t submitted, completed, failed;
     int running, queued, slots;
     size_t budget_bytes, reserved_bytes, peak_reserved_bytes;
+    int64_t solve_batches;   /* batched triangular-solve launches (see mbl_server_batching) */
+    int64_t batched_solves;  /* block solves they held */
+    double batch_ms;         /* their device time (CUDA events on the batcher's stream) */
+    double batch_bytes;      /* their algorithmic bytes: per block solve the factor read by both
+                                sweeps plus the right-hand sides, 2 (nnz_L + n) w + 16 n p */
 } mbl_server_stats;
+
+/* Continuous batching of the workers' triangular solves (set before mbl_server_start; defaults
+ * max_jobs = 16, window_us = 300).  Jobs of one sector size share a symbolic plan, so their block
+ * solves are one launch sequence on different buffers: a worker's solve is handed to a batcher
+ * thread, which launches the sequence once for up to max_jobs workers' solves of the same (plan,
+ * precision, block width) -- every launch covers all of them -- as soon as every worker inside a
+ * solve phase of that group has one waiting, or the oldest has waited window_us microseconds.
+ * Results are the same as unbatched solves (the same kernels on each job's own buffers).
+ * max_jobs = 1 turns batching off.  Not in the paper: a serving pattern for many small jobs.
+ * MBL_ERR_INVALID while a server runs or for max_jobs outside [1, 64], window_us outside [0, 1e6]. */
+int mbl_server_batching(mbl_ctx *ctx, int max_jobs, double window_us);
 
 int mbl_server_start(mbl_ctx *ctx, int slots, size_t budget_bytes);
 /* Queue a request; *ticket identifies it.  MBL_ERR_INVALID for bad arguments or no server. */

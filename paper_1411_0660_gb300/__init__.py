@@ -24,7 +24,7 @@ from ._capi import MBL_PREC_FP32, MBL_PREC_FP64, FactorStats, Opts, PlanStats, S
 
 __all__ = ["Context", "Sector", "Factorization", "MblError", "build_sector", "build_sector_fields",
            "extremal_bounds", "factor", "solve_near", "solve_near_dev", "observables", "observables_dev",
-           "default_opts", "launch_count", "entanglement_noalloc_dev", "Server", "ServedResult", "MBL_PREC_FP32", "MBL_PREC_FP64"]
+           "default_opts", "launch_count", "factor_solve_batch_dev", "entanglement_noalloc_dev", "Server", "ServedResult", "MBL_PREC_FP32", "MBL_PREC_FP64"]
 
 
 class MblError(RuntimeError):
@@ -245,6 +245,17 @@ class Factorization:
             pass
 
 
+def factor_solve_batch_dev(facts, d_bs, d_xs, nrhs: int, stream=None):
+    """Unrefined solves of several factorizations of one sector shape in shared launches:
+    d_xs[k] = (L D L^T)_k^-1 d_bs[k] (torch float64 CUDA tensors, n x nrhs column-major)."""
+    K = len(facts)
+    fa = (ctypes.c_void_p * K)(*[f.handle.value for f in facts])
+    ba = (ctypes.c_void_p * K)(*[t.data_ptr() for t in d_bs])
+    xa = (ctypes.c_void_p * K)(*[t.data_ptr() for t in d_xs])
+    s = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
+    _check(_lib().mbl_factor_solve_batch_dev(fa, K, ba, xa, nrhs, s), facts[0].sec.ctx.handle)
+
+
 def factor(sec: Sector, sigma: float, opts: Opts | None = None, **kw) -> Factorization:
     o = opts if opts is not None else default_opts(**kw)
     h = ctypes.c_void_p()
@@ -388,9 +399,13 @@ def _dim_of(L: int, nup: int = 0) -> int:
 class Server:
     """Worker threads of a context serving (L, h, seed, eps, nev) requests as memory allows."""
 
-    def __init__(self, ctx: Context, slots: int = 4, hbm_budget_bytes: int = 0):
+    def __init__(self, ctx: Context, slots: int = 4, hbm_budget_bytes: int = 0, batch_jobs: int = 16,
+                 batch_window_us: float = 300.0):
+        """`batch_jobs` > 1 batches the workers' triangular solves of one sector size into shared
+        launches (at most that many jobs per launch, waiting up to `batch_window_us`); 1 turns it off."""
         self.ctx = ctx
         self._req = {}
+        _check(_lib().mbl_server_batching(ctx.handle, batch_jobs, float(batch_window_us)), ctx.handle)
         _check(_lib().mbl_server_start(ctx.handle, slots, hbm_budget_bytes), ctx.handle)
 
     def submit(self, L: int, h: float, seed: int, eps: float, nev: int, precision: int = MBL_PREC_FP32,

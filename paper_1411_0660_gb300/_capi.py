@@ -26,7 +26,8 @@ class Opts(ctypes.Structure):
     _fields_ = [("precision", c_int), ("block", c_int), ("ncv", c_int), ("max_restarts", c_int),
                 ("tol", c_double), ("target_tol", c_double), ("refine_tol", c_double), ("max_refine", c_int),
                 ("start_seed", c_uint64), ("tensor_cores", c_int), ("refine_mode", c_int),
-                ("gmres_restart", c_int), ("solve_dataflow", c_int), ("deflate", c_int)]
+                ("gmres_restart", c_int), ("solve_dataflow", c_int), ("deflate", c_int),
+                ("wait_limit_s", c_double)]
 
 
 class FactorStats(ctypes.Structure):
@@ -66,7 +67,8 @@ class Result(ctypes.Structure):
 class ServerStats(ctypes.Structure):
     _fields_ = [("submitted", c_int64), ("completed", c_int64), ("failed", c_int64), ("running", c_int),
                 ("queued", c_int), ("slots", c_int), ("budget_bytes", c_size_t), ("reserved_bytes", c_size_t),
-                ("peak_reserved_bytes", c_size_t)]
+                ("peak_reserved_bytes", c_size_t), ("solve_batches", c_int64), ("batched_solves", c_int64),
+                ("batch_ms", c_double), ("batch_bytes", c_double)]
 
 
 # (name, restype, argtypes); every entry point of include/mblsi.h
@@ -124,6 +126,8 @@ SIGNATURES = [
                                               c_void_p, c_void_p, c_void_p, c_void_p]),
     ("mbl_entanglement_noalloc_dev", c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p]),
     ("mbl_server_start", c_int, [c_void_p, c_int, c_size_t]),
+    ("mbl_server_batching", c_int, [c_void_p, c_int, c_double]),
+    ("mbl_factor_solve_batch_dev", c_int, [c_void_p, c_int, c_void_p, c_void_p, c_int, c_void_p]),
     ("mbl_submit", c_int, [c_void_p, P(Request), P(c_uint64)]),
     ("mbl_poll", c_int, [c_void_p, c_uint64, P(Result)]),
     ("mbl_wait", c_int, [c_void_p, c_uint64, c_double, P(Result)]),

@@ -157,8 +157,14 @@ std::shared_ptr<Plan> get_plan(mbl_sector *sec) {
     return P;
 }
 
+uint64_t wait_limit_ns(double seconds) {
+    if (!(seconds >= 0.0) || seconds > 60.0) fail(MBL_ERR_INVALID, "wait_limit_s must be in [0, 60]");
+    if (seconds == 0.0) return 1000000000ull;
+    return std::max<uint64_t>(1, (uint64_t)(seconds * 1e9));
+}
+
 std::unique_ptr<Factorization> make_factorization(mbl_sector *sec, double sigma, int prec, double hnorm, int tc_mode,
-                                                  bool dataflow) {
+                                                  bool dataflow, uint64_t wait_ns) {
     if (prec != MBL_PREC_FP64 && prec != MBL_PREC_FP32) fail(MBL_ERR_INVALID, "unknown precision");
     if (tc_mode < 0 || tc_mode > 2) fail(MBL_ERR_INVALID, "tensor_cores must be 0, 1 (3xTF32) or 2 (3xBF16)");
     auto F = std::make_unique<Factorization>();
@@ -170,6 +176,7 @@ std::unique_ptr<Factorization> make_factorization(mbl_sector *sec, double sigma,
     F->tiny = (prec == MBL_PREC_FP64 ? 1e-12 : 1e-7) * hnorm;
     F->tc_mode = tc_mode;
     F->dataflow = dataflow;
+    F->wait_ns = wait_ns;
     F->allocate();
     cudaStream_t st = sec->ctx->stream;
     cudaEvent_t e0, e1;
@@ -243,6 +250,7 @@ void mbl_opts_default(mbl_opts *o) {
     o->gmres_restart = 24;
     o->solve_dataflow = 0;
     o->deflate = 1;
+    o->wait_limit_s = 0.0;
 }
 
 const char *mbl_version(void) { return "mblsi 0.1 (sm_103a)"; }
@@ -495,7 +503,8 @@ int mbl_factor(mbl_sector *sec, double sigma, const mbl_opts *opts, mbl_factoriz
     double emin, emax;
     extremal_bounds(sec, &emin, &emax);
     double hn = std::max(std::fabs(emin), std::fabs(emax));
-    auto F = make_factorization(sec, sigma, o.precision, hn, o.tensor_cores, o.solve_dataflow != 0);
+    auto F = make_factorization(sec, sigma, o.precision, hn, o.tensor_cores, o.solve_dataflow != 0,
+                                wait_limit_ns(o.wait_limit_s));
     mbl_factorization *h = new mbl_factorization();
     h->f = std::move(F);
     *out = h;
@@ -610,7 +619,10 @@ int mbl_factor_solve(mbl_factorization *fh, const double *b, double *x, int nrhs
     MBL_CUDA(cudaStreamSynchronize(st));
     unsigned long long tmo = 0;
     MBL_CUDA(cudaMemcpy(&tmo, f.counters.data() + 2, sizeof(tmo), cudaMemcpyDeviceToHost));
-    if (tmo != 0) fail(MBL_ERR_TIMEOUT, "a triangular-solve dependency wait timed out");
+    if (tmo != 0) {
+        reset_solve_counters(f, st);
+        fail(MBL_ERR_TIMEOUT, "a triangular-solve dependency wait timed out");
+    }
     MBL_CUDA(cudaMemcpy(x, cm.data(), (size_t)n * nrhs * sizeof(double), cudaMemcpyDeviceToHost));
     API_CATCH(ctx)
 }
@@ -645,7 +657,52 @@ int mbl_factor_solve_dev(mbl_factorization *fh, const double *d_b, double *d_x, 
     MBL_CUDA(cudaStreamSynchronize(st));
     unsigned long long tmo = 0;
     MBL_CUDA(cudaMemcpy(&tmo, f.counters.data() + 2, sizeof(tmo), cudaMemcpyDeviceToHost));
-    if (tmo != 0) fail(MBL_ERR_TIMEOUT, "a triangular-solve dependency wait timed out");
+    if (tmo != 0) {
+        reset_solve_counters(f, st);
+        fail(MBL_ERR_TIMEOUT, "a triangular-solve dependency wait timed out");
+    }
+    API_CATCH(ctx)
+}
+
+int mbl_factor_solve_batch_dev(mbl_factorization *const *fs, int K, const double *const *d_b, double *const *d_x,
+                               int nrhs, void *stream) {
+    if (!fs || !d_b || !d_x || K < 1 || K > 64 || nrhs < 1) return report(nullptr, MBL_ERR_INVALID, "bad argument");
+    for (int k = 0; k < K; ++k)
+        if (!fs[k] || !fs[k]->f || !d_b[k] || !d_x[k]) return report(nullptr, MBL_ERR_INVALID, "NULL entry");
+    Factorization &f0 = *fs[0]->f;
+    Ctx *ctx = f0.ctx;
+    API_TRY
+    for (int k = 0; k < K; ++k) {
+        const Factorization &f = *fs[k]->f;
+        if (f.plan.get() != f0.plan.get() || f.prec != f0.prec)
+            fail(MBL_ERR_INVALID, "batched solve: every factorization needs the same sector shape and precision");
+        if (f.dataflow) fail(MBL_ERR_INVALID, "batched solve: dataflow factorizations are not batched");
+        for (int j = 0; j < k; ++j)
+            if (fs[j]->f.get() == &f) fail(MBL_ERR_INVALID, "batched solve: a factorization appears twice");
+    }
+    cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : ctx->stream;
+    const int64_t n = f0.plan->n;
+    const size_t es = f0.prec == MBL_PREC_FP64 ? sizeof(SolveBufs<double>) : sizeof(SolveBufs<float>);
+    std::vector<char> htab(es * K);
+    std::vector<SolveIO> hio(K);
+    DevMem dtab, dio;
+    dtab.alloc(ctx, es * K);
+    dio.alloc(ctx, sizeof(SolveIO) * K);
+    for (int c0 = 0; c0 < nrhs; c0 += 32) {
+        const int p = std::min(32, nrhs - c0);
+        for (int k = 0; k < K; ++k) {
+            Factorization &f = *fs[k]->f;
+            f.ensure_solve_work(p);
+            if (f.prec == MBL_PREC_FP64) reinterpret_cast<SolveBufs<double> *>(htab.data())[k] = solve_bufs<double>(f);
+            else reinterpret_cast<SolveBufs<float> *>(htab.data())[k] = solve_bufs<float>(f);
+            hio[k] = SolveIO{d_b[k] + (size_t)c0 * n, d_x[k] + (size_t)c0 * n, 1, 1, n, n, 0, 0};
+        }
+        // pageable sources: the copies complete before the calls return, so the tables can change
+        MBL_CUDA(cudaMemcpyAsync(dtab.p, htab.data(), es * K, cudaMemcpyHostToDevice, st));
+        MBL_CUDA(cudaMemcpyAsync(dio.p, hio.data(), sizeof(SolveIO) * K, cudaMemcpyHostToDevice, st));
+        enqueue_batched_solve(*f0.plan, f0.prec, dtab.p, static_cast<const SolveIO *>(dio.p), (unsigned)K, p, st);
+        MBL_CUDA(cudaStreamSynchronize(st));
+    }
     API_CATCH(ctx)
 }
 

@@ -536,9 +536,11 @@ __global__ void __launch_bounds__(256) k_apply_m(const SolveDesc *sdescs, int nd
 // (FP32: both halves; FP64: the first).
 template <class T, int PB>
 __global__ void __launch_bounds__(256) k_fwd_step(const SolveDesc *sdescs, const int32_t *blk_desc, const int64_t *zo,
-                                                  const int32_t *sn_start, const T *Gp, const T *Dg, T *Z, T *Zs,
-                                                  T *yfw, int p, LaunchTrace *tr) {
+                                                  const int32_t *sn_start, const SolveBufs<T> *jb, int p,
+                                                  LaunchTrace *tr) {
     TraceScope trace_scope(tr);
+    const T *Gp = jb[blockIdx.z].G, *Dg = jb[blockIdx.z].D;
+    T *Z = jb[blockIdx.z].Z, *Zs = jb[blockIdx.z].Zs, *yfw = jb[blockIdx.z].yfw;
     constexpr int NH = (SPW + 255) / 256, NPF = sizeof(T) == 4 ? NH : 1;
     extern __shared__ __align__(16) unsigned char smraw[];
     T *zp = reinterpret_cast<T *>(smraw);  // SPW x PB; afterwards the 8 x PB x RBF partials
@@ -633,10 +635,12 @@ __global__ void __launch_bounds__(256) k_fwd_step(const SolveDesc *sdescs, const
 // the previous step.
 template <class T, int PB>
 __global__ void __launch_bounds__(256) k_fwd_narrow(const SolveDesc *sdescs, const int32_t *blk_desc, int nblk,
-                                                    const int64_t *zo, const int32_t *sn_start, const T *Gp,
-                                                    const T *Dg, T *Z, T *Zs, T *yfw, int p, LaunchTrace *tr) {
+                                                    const int64_t *zo, const int32_t *sn_start,
+                                                    const SolveBufs<T> *jb, int p, LaunchTrace *tr) {
     static_assert(RBF == 32, "one warp per row block");
     TraceScope trace_scope(tr);
+    const T *Gp = jb[blockIdx.z].G, *Dg = jb[blockIdx.z].D;
+    T *Z = jb[blockIdx.z].Z, *Zs = jb[blockIdx.z].Zs, *yfw = jb[blockIdx.z].yfw;
     const int lane = threadIdx.x & 31, item = blockIdx.x * 8 + (threadIdx.x >> 5);
     if (item >= nblk) {
         pdl_wait();
@@ -688,9 +692,11 @@ __global__ void __launch_bounds__(256) k_fwd_narrow(const SolveDesc *sdescs, con
 template <class T, int PB>
 __global__ void __launch_bounds__(256) k_bwd_narrow(const SolveDesc *sdescs, int nd, const int64_t *zo,
                                                     const int32_t *nc, const int32_t *sn_start,
-                                                    const int64_t *rows_off, const int32_t *rows, const T *Gp,
-                                                    const T *yfw, T *Zs, T *x, int p, LaunchTrace *tr) {
+                                                    const int64_t *rows_off, const int32_t *rows,
+                                                    const SolveBufs<T> *jb, int p, LaunchTrace *tr) {
     TraceScope trace_scope(tr);
+    const T *Gp = jb[blockIdx.z].G, *yfw = jb[blockIdx.z].yfw;
+    T *Zs = jb[blockIdx.z].Zs, *x = jb[blockIdx.z].y;
     const int lane = threadIdx.x & 31, di = blockIdx.x * 8 + (threadIdx.x >> 5);
     if (di >= nd) {
         pdl_wait();
@@ -757,9 +763,11 @@ __global__ void __launch_bounds__(256) k_bwd_narrow(const SolveDesc *sdescs, int
 // writer per launch, so the updates are deterministic.
 template <class T, int PB>
 __global__ void __launch_bounds__(256) k_bwd_update(const SolveDesc *sdescs, const int32_t *items, const int64_t *zo,
-                                                    const int32_t *sn_start, const T *Gp, T *Zs, T *x, int p,
+                                                    const int32_t *sn_start, const SolveBufs<T> *jb, int p,
                                                     LaunchTrace *tr) {
     TraceScope trace_scope(tr);
+    const T *Gp = jb[blockIdx.z].G;
+    T *Zs = jb[blockIdx.z].Zs, *x = jb[blockIdx.z].y;
     constexpr int E = 16 / sizeof(T);
     extern __shared__ __align__(16) unsigned char smraw[];
     T *Gs = reinterpret_cast<T *>(smraw);    // RBB columns x bwd_ldg rows
@@ -827,8 +835,10 @@ __global__ void k_trace_reset(LaunchTrace *tr, int n) {
 // contributions in tree order; one thread per (row, right-hand side).
 template <class T>
 __global__ void k_fwd_gather_rows(int64_t nrows, const int64_t *dst, const int64_t *own, const int64_t *cptr,
-                                  const int64_t *src, const T *y, T *Z, int p, LaunchTrace *tr) {
+                                  const int64_t *src, const SolveBufs<T> *jb, int p, LaunchTrace *tr) {
     TraceScope trace_scope(tr);
+    const T *y = jb[blockIdx.z].y;
+    T *Z = jb[blockIdx.z].Z;
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t row = t / p;
     const int q = (int)(t - row * p);
@@ -860,10 +870,12 @@ __global__ void k_fwd_gather_rows(int64_t nrows, const int64_t *dst, const int64
 template <class T, int PB>
 __global__ void __launch_bounds__(256) k_bwd_step(const SolveDesc *sdescs, const int32_t *blk_desc, const int64_t *zo,
                                                   const int32_t *nc, const int32_t *sn_start,
-                                                  const int64_t *rows_off, const int32_t *rows, const T *Gp,
-                                                  const T *yfw, T *Zs, T *P, unsigned int *cnt, T *x, int p,
-                                                  LaunchTrace *tr) {
+                                                  const int64_t *rows_off, const int32_t *rows,
+                                                  const SolveBufs<T> *jb, int64_t cnt_off, int p, LaunchTrace *tr) {
     TraceScope trace_scope(tr);
+    const T *Gp = jb[blockIdx.z].G, *yfw = jb[blockIdx.z].yfw;
+    T *Zs = jb[blockIdx.z].Zs, *P = jb[blockIdx.z].P, *x = jb[blockIdx.z].y;
+    unsigned int *cnt = jb[blockIdx.z].cnt + cnt_off;
     constexpr int E = 16 / sizeof(T);
     extern __shared__ __align__(16) unsigned char smraw[];
     T *Gs = reinterpret_cast<T *>(smraw);    // RBB columns x bwd_ldg rows
@@ -1068,20 +1080,64 @@ void numeric_factor(Factorization &fz, cudaStream_t st) {
     else factor_impl<float>(fz, st);
 }
 
-// The level x panel sequence between the permutations, on the factorization's internal buffers.
+// The level x panel sequence between the permutations for K jobs of one plan (grid z = job):
+// jb[k] holds job k's buffers.  trb (optional) receives one launch record per launch.
 template <class T, int PB>
-static void solve_levels(Factorization &fz, int p, cudaStream_t st) {
-    Plan &pl = *fz.plan;
-    const T *Gp = static_cast<const T *>(fz.gpk.m.p);
-    T *Dg = static_cast<T *>(fz.D.m.p);
-    T *Z = static_cast<T *>(fz.zwork.m.p);
-    T *Zs = static_cast<T *>(fz.zsolved.m.p);
-    T *y = static_cast<T *>(fz.ywork.m.p);
-    T *yfw = static_cast<T *>(fz.yfw.m.p);
-    T *P = static_cast<T *>(fz.pwork.m.p);
-    unsigned int *cnt = fz.scnt.data();
+static void solve_levels(const Plan &pl, const SolveBufs<T> *jb, unsigned K, int p, LaunchTrace *trb,
+                         std::vector<int> *kinds, cudaStream_t st) {
     const size_t fsm = fwd_step_smem<T, PB>(), bsm = bwd_step_smem<T, PB>();
-    // launch trace: one record per launch below, reset at the start of every solve
+    int it = 0;
+    auto next_tr = [&](int kind) -> LaunchTrace * {
+        if (!trb) return nullptr;
+        if (kinds) kinds->push_back(kind);
+        return trb + it++;
+    };
+    for (int l = 0; l < pl.nlevels; ++l) {
+        {
+            const int64_t f0 = pl.lvl_fg_ptr[l], nrows = pl.lvl_fg_ptr[l + 1] - f0;
+            launch_pdl(k_fwd_gather_rows<T>, dim3((unsigned)((nrows * p + 255) / 256), 1, K), dim3(256), 0, st, nrows,
+                       pl.d_fg_dst.data() + f0, pl.d_fg_own.data() + f0, pl.d_fg_cptr.data() + f0,
+                       (const int64_t *)pl.d_fg_src.data(), jb, p, next_tr(0));
+        }
+        for (int si = pl.lvl_sstep_ptr[l]; si < pl.lvl_sstep_ptr[l + 1]; ++si) {
+            const SolveStep &ss = pl.ssteps[si];
+            const SolveDesc *sd = pl.d_sdescs.data() + ss.d0;
+            if (ss.maxw <= 32) {
+                launch_pdl(k_fwd_narrow<T, PB>, dim3((unsigned)((ss.nrb + 7) / 8), 1, K), dim3(256), 0, st, sd,
+                           (const int32_t *)pl.d_fblk_desc.data() + ss.fblk0, (int)ss.nrb, pl.d_sn_zo.data(),
+                           pl.d_sn_start.data(), jb, p, next_tr(1));
+                continue;
+            }
+            launch_pdl(k_fwd_step<T, PB>, dim3((unsigned)ss.nrb, 1, K), dim3(256), fsm, st, sd,
+                       (const int32_t *)pl.d_fblk_desc.data() + ss.fblk0, pl.d_sn_zo.data(), pl.d_sn_start.data(),
+                       jb, p, next_tr(1));
+        }
+    }
+    for (int l = pl.nlevels - 1; l >= 0; --l) {
+        const SolveDesc *sdl = pl.d_sdescs.data() + pl.lvl_d0[l];
+        if (pl.lvl_maxw[l] <= 32 && pl.lvl_maxr[l] <= 512) {  // single narrow, short panels: a warp each
+            launch_pdl(k_bwd_narrow<T, PB>, dim3((unsigned)((pl.lvl_nd[l] + 7) / 8), 1, K), dim3(256), 0, st, sdl,
+                       pl.lvl_nd[l], pl.d_sn_zo.data(), pl.d_sn_nc.data(), pl.d_sn_start.data(),
+                       pl.d_sn_rows_off.data(), pl.d_rows.data(), jb, p, next_tr(2));
+        } else {
+            launch_pdl(k_bwd_step<T, PB>, dim3((unsigned)pl.lvl_nrbk[l], (pl.lvl_maxw[l] + RBB - 1) / RBB, K),
+                       dim3(256), bsm, st, sdl, (const int32_t *)pl.d_lvl_bblk_desc.data() + pl.lvl_bblk0[l],
+                       pl.d_sn_zo.data(), pl.d_sn_nc.data(), pl.d_sn_start.data(), pl.d_sn_rows_off.data(),
+                       pl.d_rows.data(), jb, (int64_t)pl.lvl_d0[l] * SUBS, p, next_tr(2));
+        }
+        for (int u = pl.bu_ptr[l]; u < pl.bu_ptr[l + 1]; ++u) {
+            const BwdUpd &bu = pl.bupd[u];
+            launch_pdl(k_bwd_update<T, PB>, dim3((unsigned)bu.nit, SUBS, K), dim3(256), bsm, st,
+                       (const SolveDesc *)pl.d_sdescs.data(), (const int32_t *)pl.d_bu_items.data() + 2 * bu.it0,
+                       pl.d_sn_zo.data(), pl.d_sn_start.data(), jb, p, next_tr(3));
+        }
+    }
+}
+
+// The sequence on one factorization's own buffers, with its optional launch trace.
+template <class T, int PB>
+static void solve_levels_fz(Factorization &fz, int p, cudaStream_t st) {
+    Plan &pl = *fz.plan;
     const int ntr = 2 * pl.nlevels + (int)pl.ssteps.size() + (int)pl.bupd.size();
     LaunchTrace *trb = nullptr;
     if (fz.trace_on && fz.trace.size() >= (size_t)ntr) {  // allocated when tracing is switched on
@@ -1090,62 +1146,62 @@ static void solve_levels(Factorization &fz, int p, cudaStream_t st) {
         MBL_LAUNCH_CHECK();
         fz.trace_kind.clear();
     }
-    int it = 0;
-    auto next_tr = [&](int kind) -> LaunchTrace * {
-        if (!trb) return nullptr;
-        fz.trace_kind.push_back(kind);
-        return trb + it++;
-    };
-    for (int l = 0; l < pl.nlevels; ++l) {
-        {
-            const int64_t f0 = pl.lvl_fg_ptr[l], nrows = pl.lvl_fg_ptr[l + 1] - f0;
-            launch_pdl(k_fwd_gather_rows<T>, dim3((unsigned)((nrows * p + 255) / 256)), dim3(256), 0, st, nrows,
-                       pl.d_fg_dst.data() + f0, pl.d_fg_own.data() + f0, pl.d_fg_cptr.data() + f0,
-                       (const int64_t *)pl.d_fg_src.data(), (const T *)y, Z, p, next_tr(0));
-        }
-        for (int si = pl.lvl_sstep_ptr[l]; si < pl.lvl_sstep_ptr[l + 1]; ++si) {
-            const SolveStep &ss = pl.ssteps[si];
-            const SolveDesc *sd = pl.d_sdescs.data() + ss.d0;
-            if (ss.maxw <= 32) {
-                launch_pdl(k_fwd_narrow<T, PB>, dim3((unsigned)((ss.nrb + 7) / 8)), dim3(256), 0, st, sd,
-                           (const int32_t *)pl.d_fblk_desc.data() + ss.fblk0, (int)ss.nrb, pl.d_sn_zo.data(),
-                           pl.d_sn_start.data(), Gp, (const T *)Dg, Z, Zs, yfw, p, next_tr(1));
-                continue;
-            }
-            launch_pdl(k_fwd_step<T, PB>, dim3((unsigned)ss.nrb), dim3(256), fsm, st, sd,
-                       (const int32_t *)pl.d_fblk_desc.data() + ss.fblk0,
-                       pl.d_sn_zo.data(), pl.d_sn_start.data(), Gp, (const T *)Dg, Z, Zs, yfw, p, next_tr(1));
-        }
-    }
-    for (int l = pl.nlevels - 1; l >= 0; --l) {
-        const SolveDesc *sdl = pl.d_sdescs.data() + pl.lvl_d0[l];
-        if (pl.lvl_maxw[l] <= 32 && pl.lvl_maxr[l] <= 512) {  // single narrow, short panels: a warp each
-            launch_pdl(k_bwd_narrow<T, PB>, dim3((unsigned)((pl.lvl_nd[l] + 7) / 8)), dim3(256), 0, st, sdl,
-                       pl.lvl_nd[l], pl.d_sn_zo.data(), pl.d_sn_nc.data(), pl.d_sn_start.data(),
-                       pl.d_sn_rows_off.data(), pl.d_rows.data(), Gp, (const T *)yfw, Zs, y, p, next_tr(2));
-        } else {
-            launch_pdl(k_bwd_step<T, PB>, dim3((unsigned)pl.lvl_nrbk[l], (pl.lvl_maxw[l] + RBB - 1) / RBB), dim3(256),
-                       bsm, st, sdl, (const int32_t *)pl.d_lvl_bblk_desc.data() + pl.lvl_bblk0[l],
-                       pl.d_sn_zo.data(), pl.d_sn_nc.data(), pl.d_sn_start.data(), pl.d_sn_rows_off.data(),
-                       pl.d_rows.data(), Gp, (const T *)yfw, Zs, P, cnt + (size_t)pl.lvl_d0[l] * SUBS, y, p,
-                       next_tr(2));
-        }
-        for (int u = pl.bu_ptr[l]; u < pl.bu_ptr[l + 1]; ++u) {
-            const BwdUpd &bu = pl.bupd[u];
-            launch_pdl(k_bwd_update<T, PB>, dim3((unsigned)bu.nit, SUBS), dim3(256), bsm, st,
-                       (const SolveDesc *)pl.d_sdescs.data(), (const int32_t *)pl.d_bu_items.data() + 2 * bu.it0,
-                       pl.d_sn_zo.data(), pl.d_sn_start.data(), Gp, Zs, y, p, next_tr(3));
-        }
-    }
+    solve_levels<T, PB>(pl, reinterpret_cast<const SolveBufs<T> *>(fz.dbufs.m.p), 1u, p, trb, &fz.trace_kind, st);
 }
 
 template <class T>
 static void solve_levels_p(Factorization &fz, int p, cudaStream_t st) {
     switch (rhs_pad(p)) {
-        case 8: solve_levels<T, 8>(fz, p, st); break;
-        case 16: solve_levels<T, 16>(fz, p, st); break;
-        default: solve_levels<T, 32>(fz, p, st); break;
+        case 8: solve_levels_fz<T, 8>(fz, p, st); break;
+        case 16: solve_levels_fz<T, 16>(fz, p, st); break;
+        default: solve_levels_fz<T, 32>(fz, p, st); break;
     }
+}
+
+// Batched solves: per job k, rows of its right-hand-side block B_k are permuted into its y, the
+// level sequence runs over all K jobs (grid z), and the result goes back to X_k.
+template <class T>
+__global__ void k_perm_in_b(int64_t n, int p, const int32_t *perm, const SolveIO *io, const SolveBufs<T> *jb) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n * p) return;
+    const int64_t k = idx / p;
+    const int q = (int)(idx - k * p);
+    const SolveIO &o = io[blockIdx.z];
+    jb[blockIdx.z].y[idx] = (T)o.B[(int64_t)perm[k] * o.ldb + q * o.ldbq];
+}
+
+template <class T>
+__global__ void k_perm_out_b(int64_t n, int p, const int32_t *perm, const SolveIO *io, const SolveBufs<T> *jb) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n * p) return;
+    const int64_t k = idx / p;
+    const int q = (int)(idx - k * p);
+    const SolveIO &o = io[blockIdx.z];
+    const double v = (double)jb[blockIdx.z].y[idx];
+    double *dst = o.X + (int64_t)perm[k] * o.ldx + q * o.ldxq;
+    *dst = o.accumulate ? *dst + v : v;
+}
+
+template <class T>
+static void enqueue_batched_t(const Plan &pl, const void *tab, const SolveIO *io, unsigned K, int p, cudaStream_t st) {
+    const SolveBufs<T> *jb = static_cast<const SolveBufs<T> *>(tab);
+    const unsigned g = (unsigned)((pl.n * p + 255) / 256);
+    k_perm_in_b<T><<<dim3(g, 1, K), 256, 0, st>>>(pl.n, p, pl.d_perm.data(), io, jb);
+    MBL_LAUNCH_CHECK();
+    switch (rhs_pad(p)) {
+        case 8: solve_levels<T, 8>(pl, jb, K, p, nullptr, nullptr, st); break;
+        case 16: solve_levels<T, 16>(pl, jb, K, p, nullptr, nullptr, st); break;
+        default: solve_levels<T, 32>(pl, jb, K, p, nullptr, nullptr, st); break;
+    }
+    k_perm_out_b<T><<<dim3(g, 1, K), 256, 0, st>>>(pl.n, p, pl.d_perm.data(), io, jb);
+    MBL_LAUNCH_CHECK();
+}
+
+void enqueue_batched_solve(const Plan &pl, int prec, const void *tab, const SolveIO *io, unsigned K, int p,
+                           cudaStream_t st) {
+    if (p < 1 || p > 32 || K < 1 || K > 65535) fail(MBL_ERR_INVALID, "batched solve: bad block width or job count");
+    if (prec == MBL_PREC_FP64) enqueue_batched_t<double>(pl, tab, io, K, p, st);
+    else enqueue_batched_t<float>(pl, tab, io, K, p, st);
 }
 
 template <class T>
@@ -1198,6 +1254,11 @@ static void solve_impl(Factorization &fz, const double *B, int64_t ldb, int64_t 
 void factor_solve_raw(Factorization &fz, const double *B, int64_t ldb, double *X, int64_t ldx, int p, bool accumulate,
                       cudaStream_t st) {
     if (p < 1 || p > 32) fail(MBL_ERR_INVALID, "solve: 1 <= nrhs <= 32 per block");
+    if (fz.ctx->batcher && !fz.dataflow && !fz.trace_on) {
+        // a serving worker: the solve joins the other workers' solves of the same plan in one launch
+        batched_solve(fz.ctx->batcher, fz, B, ldb, X, ldx, p, accumulate, st);
+        return;
+    }
     if (fz.prec == MBL_PREC_FP64) solve_impl<double>(fz, B, ldb, 1, X, ldx, 1, p, accumulate, st);
     else solve_impl<float>(fz, B, ldb, 1, X, ldx, 1, p, accumulate, st);
 }
@@ -1207,6 +1268,30 @@ void factor_solve_colmajor(Factorization &fz, const double *B, double *X, int p,
     const int64_t n = fz.plan->n;
     if (fz.prec == MBL_PREC_FP64) solve_impl<double>(fz, B, 1, n, X, 1, n, p, false, st);
     else solve_impl<float>(fz, B, 1, n, X, 1, n, p, false, st);
+}
+
+template <class T>
+SolveBufs<T> solve_bufs(const Factorization &fz) {
+    SolveBufs<T> b;
+    b.G = static_cast<const T *>(fz.gpk.m.p);
+    b.D = static_cast<const T *>(fz.D.m.p);
+    b.Z = static_cast<T *>(fz.zwork.m.p);
+    b.Zs = static_cast<T *>(fz.zsolved.m.p);
+    b.y = static_cast<T *>(fz.ywork.m.p);
+    b.yfw = static_cast<T *>(fz.yfw.m.p);
+    b.P = static_cast<T *>(fz.pwork.m.p);
+    b.cnt = fz.scnt.data();
+    return b;
+}
+template SolveBufs<float> solve_bufs<float>(const Factorization &);
+template SolveBufs<double> solve_bufs<double>(const Factorization &);
+
+template <class T>
+static void write_bufs(Factorization &fz) {
+    const SolveBufs<T> b = solve_bufs<T>(fz);
+    if (fz.dbufs.size() < sizeof(b)) fz.dbufs.alloc(fz.ctx, sizeof(b));
+    MBL_CUDA(cudaMemcpyAsync(fz.dbufs.data(), &b, sizeof(b), cudaMemcpyHostToDevice, fz.ctx->stream));
+    MBL_CUDA(cudaStreamSynchronize(fz.ctx->stream));
 }
 
 void Factorization::ensure_solve_work(int p) {
@@ -1220,6 +1305,14 @@ void Factorization::ensure_solve_work(int p) {
     pwork.alloc(ctx, (size_t)std::max<int64_t>(std::max<int64_t>(pl.max_lvl_nrbk * SUBS, pl.df_pslots), 1) * RBB *
                          rhs_pad(p) * es);
     work_p = p;
+    // the device table the level-sequence kernels read (the solve graph is recaptured with it)
+    if (prec == MBL_PREC_FP64) write_bufs<double>(*this);
+    else write_bufs<float>(*this);
+    if (graph_exec) {
+        cudaGraphExecDestroy(graph_exec);
+        graph_exec = nullptr;
+        graph_p = 0;
+    }
 }
 
 void Factorization::allocate() {
@@ -1236,6 +1329,12 @@ void Factorization::allocate() {
     scnt.alloc(ctx, std::max<size_t>(pl.sdescs.size() * SUBS, 1));
     dfcnt.alloc(ctx, (size_t)4 * pl.ns + 2);
     MBL_CUDA(cudaMemset(scnt.data(), 0, std::max<size_t>(pl.sdescs.size() * SUBS, 1) * sizeof(unsigned int)));
+}
+
+void reset_solve_counters(Factorization &fz, cudaStream_t st) {
+    MBL_CUDA(cudaMemsetAsync(fz.counters.data() + 2, 0, sizeof(unsigned long long), st));
+    MBL_CUDA(cudaMemsetAsync(fz.scnt.data(), 0, fz.scnt.size() * sizeof(unsigned int), st));
+    MBL_CUDA(cudaStreamSynchronize(st));
 }
 
 void Factorization::release_scratch() {

@@ -5,6 +5,19 @@
 
 namespace mbl {
 
+// Buffers of one factorization's level-sequence triangular solve as the solve kernels read them.
+// A launch takes a table of these, one per job (blockIdx.z), so that several factorizations of
+// one plan (same pattern, same launch sequence) are solved by one launch sequence.
+template <class T>
+struct SolveBufs {
+    const T *G;          // packed solve factor
+    const T *D;          // pivots
+    T *Z, *Zs;           // front work rows: gathered, solved
+    T *y, *yfw;          // permuted right-hand side / solution; forward result
+    T *P;                // backward partial sums
+    unsigned int *cnt;   // backward arrival counters (per solve descriptor and column chunk)
+};
+
 struct Factorization {
     Ctx *ctx = nullptr;
     mbl_sector *sec = nullptr;
@@ -18,6 +31,7 @@ struct Factorization {
     DVec<unsigned int> scnt;  // per (solve panel, column chunk) arrival counters of the backward step
     DVec<int32_t> dfcnt;      // dataflow solve: per-front completion counters (4 ns) and two tickets
     bool dataflow = false;    // solves as one persistent kernel per sweep (else level-by-level launches)
+    uint64_t wait_ns = 1000000000ull;  // limit of each bounded dependency wait of the dataflow solve
     // [0] perturbed pivots, [1] negative pivots, [2] wait time-outs, [3] max |l| (float bits, low
     // word), [4] min |d| (float bits, low word)
     DVec<unsigned long long> counters;
@@ -31,6 +45,7 @@ struct Factorization {
     bool trace_on = false;
     DVec<LaunchTrace> trace;
     DVec<double> dev_b, dev_x;  // row-major right-hand-side blocks of refined device solves (n x 32)
+    DVec<char> dbufs;           // device SolveBufs<T> of this factorization (one entry)
     std::vector<int> trace_kind;  // per traced launch: 0 forward gather, 1 forward step, 2/3 backward start/update
     int64_t perturbed = 0, negative = 0;
     double ms_factor = 0.0;
@@ -41,6 +56,40 @@ struct Factorization {
     void release_scratch();
     void ensure_solve_work(int p);
 };
+
+// Right-hand side and result of one job of a batched solve (row-major FP64 blocks, row strides).
+struct SolveIO {
+    const double *B;
+    double *X;
+    int64_t ldb, ldx;    // row strides
+    int64_t ldbq, ldxq;  // right-hand-side (column) strides
+    int accumulate;      // X += solution instead of X = solution
+    int pad;
+};
+
+// Enqueue the solve of K jobs of one plan and precision: tab holds K SolveBufs<T> (T by prec), io
+// K SolveIO, both on the device; p right-hand sides per job.  Capturable in a CUDA graph.
+void enqueue_batched_solve(const Plan &pl, int prec, const void *tab, const SolveIO *io, unsigned K, int p,
+                           cudaStream_t st);
+
+struct SolveBatcher;
+// A serving worker's solve through the context's batcher (batch.cu): enqueued on st after the
+// work already there; returns once the batch holding it is launched.
+void batched_solve(SolveBatcher *b, Factorization &fz, const double *B, int64_t ldb, double *X, int64_t ldx, int p,
+                   bool accumulate, cudaStream_t st);
+// Workers inside a solve phase of (plan, precision, p): the batcher waits for all of them before
+// it launches, up to its window.
+void batcher_enter(SolveBatcher *b, const Plan *pl, int prec, int p);
+void batcher_leave(SolveBatcher *b, const Plan *pl, int prec, int p);
+// A batcher with its own thread, stream and context on `device`; batches of at most max_jobs.
+SolveBatcher *batcher_create(int device, int max_jobs, double window_us);
+void batcher_destroy(SolveBatcher *b);  // after every worker using it has stopped
+// Launched batches, solves in them, their device time (CUDA events) and algorithmic bytes.
+void batcher_stats(SolveBatcher *b, int64_t *batches, int64_t *solves, double *ms, double *bytes);
+
+// The SolveBufs of a factorization (its solve work allocated).
+template <class T>
+SolveBufs<T> solve_bufs(const Factorization &fz);
 
 // tcgen05 trailing update of one panel step (FP32 fronts); err counts bounded-wait time-outs.
 size_t schur_tc_smem(bool bf16);
@@ -65,7 +114,13 @@ size_t job_bytes(const Plan &p, int nev, int block, int prec);
 std::shared_ptr<Plan> get_plan(mbl_sector *sec);
 // Create, allocate and run a factorization (synchronous; fills stats).
 std::unique_ptr<Factorization> make_factorization(mbl_sector *sec, double sigma, int prec, double hnorm,
-                                                  int tc_mode = 1, bool dataflow = false);
+                                                  int tc_mode = 1, bool dataflow = false,
+                                                  uint64_t wait_ns = 1000000000ull);
+// Wait-limit option (seconds, 0 = the 1 s default) in nanoseconds.
+uint64_t wait_limit_ns(double seconds);
+// After a solve reported expired waits: clear the time-out count and the per-chunk arrival counters
+// that the stopped CTAs may have left behind, so that the factorization serves later solves.
+void reset_solve_counters(Factorization &fz, cudaStream_t st);
 
 }  // namespace mbl
 

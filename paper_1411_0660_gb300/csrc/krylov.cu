@@ -1267,7 +1267,8 @@ void solve_near(mbl_sector *sec, double eps, int nev, const mbl_opts &o, double 
     if (std::fabs(sigma - emax) <= guard) sigma_f = emax + nudge;
     auto tf0 = std::chrono::steady_clock::now();
     std::unique_ptr<Factorization> fz =
-        make_factorization(sec, sigma_f, o.precision, hnorm, o.tensor_cores, o.solve_dataflow != 0);
+        make_factorization(sec, sigma_f, o.precision, hnorm, o.tensor_cores, o.solve_dataflow != 0,
+                           wait_limit_ns(o.wait_limit_s));
     S.ms_factor = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tf0).count();
     RefinedSolve op{sec, fz.get(), hnorm + std::fabs(sigma_f), o.refine_tol, o.max_refine};
     op.gmres = o.refine_mode;
@@ -1284,17 +1285,40 @@ void solve_near(mbl_sector *sec, double eps, int nev, const mbl_opts &o, double 
     double screen = 1e-6;
     int restarts = 0, nc = 0;
     double mxres = INFINITY, prev_rr = INFINITY;
+    int nudges = 0;  // moves of the factorization shift off an eigenvalue
+    // a serving worker announces its solve phases to the solve batcher, which then waits for its
+    // solves before launching a batch of the same plan
+    struct BatchPhase {
+        SolveBatcher *b;
+        const Plan *pl = nullptr;
+        int prec = 0, p = 0;
+        void enter(const Factorization &f, int p_) {
+            if (!b || f.dataflow || pl) return;
+            pl = f.plan.get();
+            prec = f.prec;
+            p = p_;
+            batcher_enter(b, pl, prec, p);
+        }
+        void leave() {
+            if (pl) batcher_leave(b, pl, prec, p);
+            pl = nullptr;
+        }
+        ~BatchPhase() { leave(); }
+    } phase{ctx->batcher};
     for (;; ++restarts) {
+        phase.enter(*fz, p);
         while (!ks.full()) {
             ks.expand(opfn, st);
             if (op.stalled && fz->prec == MBL_PREC_FP32) {
+                phase.leave();
                 // refinement stalled near the shift: refactor with FP64 fronts.  The Krylov-Schur
                 // relation built so far holds only to the accuracy of the stalled solves, and thick
                 // restarts would carry that error along for good: start the iteration again.
                 auto tf1 = std::chrono::steady_clock::now();
                 op.fz = nullptr;
                 fz.reset();  // free the FP32 fronts first: the two factors never coexist in HBM
-                fz = make_factorization(sec, sigma_f, MBL_PREC_FP64, hnorm, 1, o.solve_dataflow != 0);
+                fz = make_factorization(sec, sigma_f, MBL_PREC_FP64, hnorm, 1, o.solve_dataflow != 0,
+                                        wait_limit_ns(o.wait_limit_s));
                 S.ms_factor += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tf1).count();
                 op.fz = fz.get();
                 op.stalled = false;
@@ -1303,10 +1327,46 @@ void solve_near(mbl_sector *sec, double eps, int nev, const mbl_opts &o, double 
                 ks.start(o.start_seed, st);
                 screen = 1e-6;
                 prev_rr = INFINITY;
+                phase.enter(*fz, p);
             }
         }
+        phase.leave();
         ks.ritz(st, th, rn);
         int mm = (int)th.size();
+        if (nudges < 3) {
+            // A shift within 1e-4 of the mean level spacing of an eigenvalue (a target exactly on
+            // one) makes that Ritz value of (H - sigma)^-1 dominate every solve: the refinement's
+            // backward-error bound scales with |x|, which that one component then sets, and the
+            // other components, the ones the iteration still needs, stay accurate to a few digits
+            // only.  Factor a tenth of a spacing away from that eigenvalue (an ordinary distance) and
+            // start again; the window is still chosen by distance to sigma, and the basis keeps more
+            // than nev Ritz pairs around the shift.  A shift that lands on another level moves again.
+            const double spacing = (emax - emin) / (double)n;
+            double tmax = 0.0, tnear = 0.0;
+            for (double t : th)
+                if (std::fabs(t) > tmax) tmax = std::fabs(t), tnear = t;
+            if (tmax * spacing > 1e4) {
+                const double lam = sigma_f + 1.0 / tnear;  // the eigenvalue the shift sits on
+                const double side = (sigma_f >= lam ? 1.0 : -1.0) * (nudges == 1 ? -1.0 : 1.0);
+                sigma_f = lam + side * (0.1 + 0.05 * nudges) * spacing;
+                ++nudges;
+                const int prec_now = fz->prec;
+                op.fz = nullptr;
+                fz.reset();
+                auto tf1 = std::chrono::steady_clock::now();
+                fz = make_factorization(sec, sigma_f, prec_now, hnorm, o.tensor_cores, o.solve_dataflow != 0,
+                                        wait_limit_ns(o.wait_limit_s));
+                S.ms_factor += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tf1).count();
+                op.fz = fz.get();
+                op.anorm = hnorm + std::fabs(sigma_f);
+                op.stalled = false;
+                op.clear_deflation();
+                ks.start(o.start_seed, st);
+                screen = 1e-6;
+                prev_rr = INFINITY;
+                continue;
+            }
+        }
         std::vector<int> order(mm);
         std::iota(order.begin(), order.end(), 0);
         std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return std::fabs(th[a]) > std::fabs(th[b]); });
@@ -1338,7 +1398,10 @@ void solve_near(mbl_sector *sec, double eps, int nev, const mbl_opts &o, double 
         unsigned long long tmo = 0;  // bounded waits of the dataflow solves that expired
         MBL_CUDA(cudaMemcpyAsync(&tmo, fz->counters.data() + 2, sizeof(tmo), cudaMemcpyDeviceToHost, st));
         MBL_CUDA(cudaStreamSynchronize(st));
-        if (tmo != 0) fail(MBL_ERR_TIMEOUT, "a triangular-solve dependency wait timed out");
+        if (tmo != 0) {
+            reset_solve_counters(*fz, st);
+            fail(MBL_ERR_TIMEOUT, "a triangular-solve dependency wait timed out");
+        }
     }
     MBL_CUDA(cudaMemcpyAsync(d_evals, rr.evals.data(), nev * sizeof(double), cudaMemcpyHostToDevice, st));
     MBL_CUDA(cudaMemcpyAsync(d_resid, rr.resid.data(), nev * sizeof(double), cudaMemcpyHostToDevice, st));

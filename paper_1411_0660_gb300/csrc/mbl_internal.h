@@ -167,6 +167,9 @@ struct Ctx {
     std::map<std::string, ProfAcc> profile;
     std::vector<cudaEvent_t> event_pool;
     struct Server *server = nullptr;  // serving workers (server.cu), if started
+    struct SolveBatcher *batcher = nullptr;  // a serving worker's solve batcher (batch.cu), shared
+    int batch_max_jobs = 16;                 // server option: jobs per batched solve (1 = no batching)
+    double batch_window_us = 300.0;          // server option: longest wait for the other workers
     cudaEvent_t take_event();
     void resolve_profile();
 };
@@ -257,7 +260,8 @@ constexpr int EIG_SMEM_MAX_M = 160;  // largest order the small eigensolver keep
 void syev_batched(int batch, const int *d_m, const int64_t *d_aoff, const int64_t *d_woff, double *d_A,
                   double *d_w, int vecs, const int *d_sel, int mmax, double *d_work, int *d_info,
                   cudaStream_t st, bool fp32 = false);
-// load the FP64 small-eigensolver kernel now (kernels otherwise load lazily on first launch)
+// set the small eigensolver's shared-memory attributes on the current device and load its FP32 and
+// FP64 kernels now (kernels otherwise load lazily on first launch, taking device memory then)
 cudaError_t syev_preload();
 // C = alpha op(A) op(B) + beta C for small column-major FP64 matrices
 void gemm_small(bool ta, bool tb, int M, int N, int K, double alpha, const double *A, int lda, const double *B,

@@ -76,6 +76,7 @@ struct Server {
     bool stop = false;
     std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
     cudaEvent_t ref = nullptr;  // recorded at start on the parent stream: origin of the device times
+    SolveBatcher *batcher = nullptr;  // shared by the workers (none if batching is off)
 
     void worker(int i);
     void run(Job &J, mbl_ctx *w);
@@ -214,6 +215,7 @@ void server_shutdown(Ctx *ctx) {
     s->cv_work.notify_all();
     s->cv_mem.notify_all();
     for (auto &th : s->threads) th.join();
+    batcher_destroy(s->batcher);
     for (mbl_ctx *w : s->wctx) mbl_ctx_destroy(w);
     if (s->ref) cudaEventDestroy(s->ref);
     ctx->server = nullptr;
@@ -279,6 +281,10 @@ int mbl_server_start(mbl_ctx *ctx, int slots, size_t budget_bytes) {
             }
             w->plans = ctx->plans;
             s->wctx.push_back(w);
+        }
+        if (ctx->batch_max_jobs > 1 && slots > 1) {
+            s->batcher = batcher_create(ctx->device, ctx->batch_max_jobs, ctx->batch_window_us);
+            for (mbl_ctx *w : s->wctx) w->batcher = s->batcher;
         }
         MBL_CUDA(cudaEventCreate(&s->ref));
         MBL_CUDA(cudaEventRecord(s->ref, ctx->stream));
@@ -372,6 +378,25 @@ int mbl_server_stats_get(mbl_ctx *ctx, mbl_server_stats *out) {
     out->budget_bytes = s->budget;
     out->reserved_bytes = s->reserved;
     out->peak_reserved_bytes = s->peak_reserved;
+    out->solve_batches = out->batched_solves = 0;
+    out->batch_ms = out->batch_bytes = 0.0;
+    if (s->batcher) {
+        try {
+            batcher_stats(s->batcher, &out->solve_batches, &out->batched_solves, &out->batch_ms, &out->batch_bytes);
+        } catch (const Error &e) {
+            return srv_report(ctx, e.code, e.msg);
+        }
+    }
+    return MBL_OK;
+}
+
+int mbl_server_batching(mbl_ctx *ctx, int max_jobs, double window_us) {
+    if (!ctx) return MBL_ERR_INVALID;
+    if (ctx->server) return srv_report(ctx, MBL_ERR_INVALID, "set batching before mbl_server_start");
+    if (max_jobs < 1 || max_jobs > 64 || !(window_us >= 0.0 && window_us <= 1e6))
+        return srv_report(ctx, MBL_ERR_INVALID, "max_jobs in [1, 64], window_us in [0, 1e6]");
+    ctx->batch_max_jobs = max_jobs;
+    ctx->batch_window_us = window_us;
     return MBL_OK;
 }
 

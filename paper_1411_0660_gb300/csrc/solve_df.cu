@@ -23,8 +23,6 @@ namespace mbl {
 
 namespace {
 
-constexpr uint64_t DF_WAIT_NS = 1000000000ull;  // 1 s per wait
-
 struct DfArgs {
     const SolveItem *items;
     int nitems;
@@ -40,6 +38,7 @@ struct DfArgs {
     unsigned int *ticket;
     unsigned int *arrive;  // per (descriptor, column chunk)
     unsigned long long *err;
+    uint64_t wait_ns;  // limit of each wait (Factorization::wait_ns)
 };
 
 __device__ __forceinline__ uint64_t df_clock() {
@@ -54,12 +53,12 @@ __device__ __forceinline__ int ld_acquire(const int32_t *p) {
     return v;
 }
 
-// thread 0: wait until *c >= v (bounded)
-__device__ bool df_wait(const int32_t *c, int v, unsigned long long *err) {
+// thread 0: wait until *c >= v, for at most wait_ns nanoseconds
+__device__ bool df_wait(const int32_t *c, int v, unsigned long long *err, uint64_t wait_ns) {
     if (ld_acquire(c) >= v) return true;
     const uint64_t t0 = df_clock();
     while (ld_acquire(c) < v) {
-        if (df_clock() - t0 > DF_WAIT_NS) {
+        if (df_clock() - t0 > wait_ns) {
             atomicAdd(err, 1ull);
             return false;
         }
@@ -96,7 +95,7 @@ __global__ void __launch_bounds__(256) k_df_fwd(DfArgs A, const T *Gp, const T *
                 bool ok = true;
                 for (int c = A.ch_ptr[s]; ok && c < A.ch_ptr[s + 1]; ++c) {
                     const int ch = A.ch_list[c];
-                    ok = df_wait(A.fcnt + ch, A.ftotal[ch], A.err);
+                    ok = df_wait(A.fcnt + ch, A.ftotal[ch], A.err, A.wait_ns);
                 }
                 s_ok = ok;
             }
@@ -133,7 +132,9 @@ __global__ void __launch_bounds__(256) k_df_fwd(DfArgs A, const T *Gp, const T *
                 for (int c = 0; c < 32; ++c) lv[h][c] = g[(int64_t)(c0 + c) * ld];
             }
         }
-        if (tid == 0) s_ok = df_wait(A.gcnt + s, A.gchunks[s], A.err) && df_wait(A.fcnt + s, A.fprefix[qd], A.err);
+        if (tid == 0)
+            s_ok = df_wait(A.gcnt + s, A.gchunks[s], A.err, A.wait_ns) &&
+                   df_wait(A.fcnt + s, A.fprefix[qd], A.err, A.wait_ns);
         __syncthreads();
         if (!s_ok) return;
         for (int idx = tid; idx < w * PB; idx += blockDim.x) {
@@ -208,7 +209,7 @@ __global__ void __launch_bounds__(256) k_df_bwd(DfArgs A, const T *Gp, const T *
             // ---- backward gather: forward result of the fully summed rows, ancestors' x below
             if (tid == 0) {
                 const int pa = A.parent[s];
-                s_ok = pa < 0 || df_wait(A.bcnt + pa, A.btotal[pa], A.err);
+                s_ok = pa < 0 || df_wait(A.bcnt + pa, A.btotal[pa], A.err, A.wait_ns);
             }
             __syncthreads();
             if (!s_ok) return;
@@ -234,7 +235,9 @@ __global__ void __launch_bounds__(256) k_df_bwd(DfArgs A, const T *Gp, const T *
         const int wc = min(RBB, w - cc);
         const int64_t zb = A.zo[s] + k0, ld = sg_ld(R);
         bwd_tile_issue(Gs, Gp + d.goff + (int64_t)cc * ld + r0, ld, wc, nrv);  // read-only: copy before waiting
-        if (tid == 0) s_ok = df_wait(A.bgcnt + s, A.gchunks[s], A.err) && df_wait(A.bcnt + s, A.bprefix[qd], A.err);
+        if (tid == 0)
+            s_ok = df_wait(A.bgcnt + s, A.gchunks[s], A.err, A.wait_ns) &&
+                   df_wait(A.bcnt + s, A.bprefix[qd], A.err, A.wait_ns);
         __syncthreads();
         if (!s_ok) {
             cp_async_commit_wait();
@@ -344,6 +347,7 @@ void df_sweeps(Factorization &fz, int p, cudaStream_t st) {
     A.bcnt = cnt + 3 * ns;
     A.arrive = fz.scnt.data();
     A.err = fz.counters.data() + 2;
+    A.wait_ns = fz.wait_ns;
     const T *Gp = static_cast<const T *>(fz.gpk.m.p);
     const T *Dg = static_cast<const T *>(fz.D.m.p);
     T *Z = static_cast<T *>(fz.zwork.m.p);

@@ -1,0 +1,144 @@
+"""Failure paths of the GPU library, made to happen on purpose without faulting the GPU (needs a GB300).
+
+* A refinement stall: plain iterative refinement limited to one step cannot bring an FP32-factor
+  solve to the FP64 backward-error target, so the first application stalls and the shift-invert
+  driver must refactor with FP64 fronts (fp64_fallback = 1) and still return the oracle's window.
+* A shift exactly on an eigenvalue: with J = 0 the Hamiltonian is diagonal and its eigenvalues are
+  the diagonal entries (the oracle's CSR holds them bit for bit).  The factorization of H - sigma
+  with sigma equal to one of them meets an exactly zero pivot; it must perturb it (static pivoting)
+  rather than produce NaN, and solve_near with the target on that eigenvalue must return the
+  diagonal entries nearest sigma, or MBL_ERR_SINGULAR, never NaN.
+* An expired bounded wait: the dataflow triangular solve waits on per-front completion counters
+  with a time limit; a limit of one nanosecond makes waits run out, the call must report
+  MBL_ERR_TIMEOUT, and the context must keep working afterwards.
+"""
+import numpy as np
+import pytest
+
+from parity import EIG_TOL, window_equivalent
+
+pytestmark = pytest.mark.gpu
+
+MBL_ERR_SINGULAR = 3
+MBL_ERR_TIMEOUT = 5
+
+
+@pytest.fixture(scope="module")
+def g():
+    import paper_1411_0660_gb300 as g
+
+    return g
+
+
+@pytest.fixture(scope="module")
+def ctx(g):
+    c = g.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.mark.parametrize("L,h,seed,eps,nev", [(14, 0.5, 40, 0.5, 30), (12, 3.0, 41, 0.3, 20)])
+def test_forced_refinement_stall_falls_back_to_fp64(g, ctx, orc, L, h, seed, eps, nev):
+    sec = g.build_sector(ctx, L, h, seed)
+    res = g.solve_near(sec, eps, nev, precision=g.MBL_PREC_FP32, refine_mode=0, max_refine=1)
+    sec.close()
+    assert res.stats["fp64_fallback"] == 1
+    assert np.all(np.isfinite(res.evals)) and np.all(np.isfinite(res.evecs)) and np.all(np.isfinite(res.resid))
+    assert res.nconv == nev
+    H = orc.csr(L, orc.fields(L, h, seed))
+    emin, emax = orc.extremal_bounds(H)
+    hn = max(abs(emin), abs(emax))
+    sigma = emin + eps * (emax - emin)
+    assert abs(res.sigma - sigma) <= 1e-12 * hn
+    spectrum = orc.nearest_shift_invert(H, sigma, nev + 12, hn).evals
+    assert window_equivalent(res.evals, spectrum, sigma, nev, hn)
+    for j in range(nev):
+        y = res.evecs[:, j]
+        assert np.linalg.norm(H.matvec(y) - res.evals[j] * y) <= EIG_TOL * hn
+
+
+def _j0_sector(g, ctx, orc, L, seed):
+    hi = orc.fields(L, 2.0, seed)
+    sec = g.build_sector_fields(ctx, L, hi, 0.0)
+    H = orc.csr(L, hi, 0.0)
+    rp, col = H.rowptr, H.col
+    diag = np.array([H.val[rp[k] + np.nonzero(col[rp[k]:rp[k + 1]] == k)[0][0]] for k in range(H.n)])
+    return sec, H, diag
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_factor_with_shift_on_an_eigenvalue_has_no_nan(g, ctx, orc, prec):
+    L = 12
+    sec, H, diag = _j0_sector(g, ctx, orc, L, 42)
+    d = np.sort(diag)
+    sigma = float(d[len(d) // 2])  # exactly a diagonal entry: an exactly zero pivot
+    f = g.factor(sec, sigma, precision=prec)
+    st = f.stats()
+    assert st["perturbed"] >= 1
+    B = np.random.default_rng(7).standard_normal((sec.dim, 4))
+    X = f.solve(B, refine=False)
+    assert np.all(np.isfinite(X))
+    # every other component is the exact diagonal solve b_i / (d_i - sigma) to the fronts' precision
+    hn = np.max(np.abs(diag))
+    off = np.abs(diag - sigma) > 1e-5 * hn  # well clear of the perturbation threshold of either precision
+    want = B[off] / (diag[off] - sigma)[:, None]
+    rel = 1e-12 if prec == 0 else 1e-5
+    assert np.max(np.abs(X[off] - want) / np.maximum(np.abs(want), 1e-300)) <= rel
+    f.close()
+    sec.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_solve_near_with_target_on_an_eigenvalue(g, ctx, orc, prec):
+    L, nev = 12, 20
+    sec, H, diag = _j0_sector(g, ctx, orc, L, 43)
+    d = np.sort(diag)
+    emin, emax = d[0], d[-1]
+    hn = max(abs(emin), abs(emax))
+    target = d[len(d) // 3]
+    eps = (target - emin) / (emax - emin)
+    try:
+        res = g.solve_near(sec, eps, nev, precision=prec)
+    except g.MblError as e:
+        assert e.code == MBL_ERR_SINGULAR
+        return
+    finally:
+        sec.close()
+    assert np.all(np.isfinite(res.evals)) and np.all(np.isfinite(res.evecs)) and np.all(np.isfinite(res.resid))
+    assert abs(res.sigma - target) <= 1e-12 * hn  # the target sits on the eigenvalue to the bounds' accuracy
+    assert res.nconv == nev
+    assert window_equivalent(res.evals, d, res.sigma, nev, hn)
+    for j in range(nev):
+        y = res.evecs[:, j]
+        assert np.linalg.norm(H.matvec(y) - res.evals[j] * y) <= EIG_TOL * hn
+
+
+def test_dataflow_wait_expiry_reports_timeout(g, ctx, orc):
+    L, h, seed = 14, 2.0, 44
+    sec = g.build_sector(ctx, L, h, seed)
+    lo, hi = g.extremal_bounds(sec)
+    sigma = lo + 0.5 * (hi - lo)
+    B = np.random.default_rng(8).standard_normal((sec.dim, 8))
+    f = g.factor(sec, sigma, precision=g.MBL_PREC_FP32, solve_dataflow=1, wait_limit_s=1e-9)
+    codes = []
+    for _ in range(3):
+        try:
+            f.solve(B, refine=False)
+            codes.append(0)
+        except g.MblError as e:
+            codes.append(e.code)
+            break
+    f.close()
+    assert codes[-1] == MBL_ERR_TIMEOUT, codes
+    # the context still works: a factorization with the default limit solves correctly
+    f2 = g.factor(sec, sigma, precision=g.MBL_PREC_FP32, solve_dataflow=1)
+    X = f2.solve(B, refine=True)
+    H = orc.csr(L, orc.fields(L, h, seed))
+    hn = max(abs(lo), abs(hi))
+    for q in range(8):
+        r = H.matvec(X[:, q], sigma) - B[:, q]
+        assert np.linalg.norm(r) <= 1e-13 * ((hn + abs(sigma)) * np.linalg.norm(X[:, q]) + np.linalg.norm(B[:, q]))
+    f2.close()
+    with pytest.raises(g.MblError):
+        g.factor(sec, sigma, precision=g.MBL_PREC_FP32, solve_dataflow=1, wait_limit_s=-1.0)
+    sec.close()
