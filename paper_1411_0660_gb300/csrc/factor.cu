@@ -13,6 +13,8 @@
 // Pivoting permutes only the variables of the current panel; the rows of earlier panel
 // columns keep their order and the solves apply each panel's permutation when they reach it.
 #include <cfloat>
+#include <map>
+#include <mutex>
 
 #include "factor.h"
 #include "solve_tile.cuh"
@@ -529,103 +531,114 @@ __global__ void __launch_bounds__(256) k_apply_m(const SolveDesc *sdescs, int nd
     }
 }
 
-// Forward solve step, RBF rows of [k0, f) per CTA: with z = Z[panel] (PB >= p, zero-padded),
-// rows of the panel get Zs = M z and rows below get Z -= (L21 M) z.  Warp j takes columns
-// [32 j, 32 j + 32) of each 256-column half of the panel; the eight partial sums meet in shared
-// memory.  The CTA's rows of G are streamed into registers before waiting for the previous step
-// (FP32: both halves; FP64: the first).
+// Forward solve step over the row blocks (RBF rows of [k0, f)) of every panel of the step and of
+// every job of the launch: a block of job j's panel with z = Z[panel] (PB >= p, zero-padded) gives
+// Zs = M z on the panel's own rows and Z -= (L21 M) z on the rows below.  CTAs walk the (job, row
+// block) items with a grid stride (the grid is the resident capacity, so there is no tail wave).
+// Per item the RBF x w tile of G is copied to shared memory with 16-byte cp.async (issued before the
+// wait on the previous step for the first item, since G is read-only); warp j then takes columns
+// [32 j, 32 j + 32) and lane i row i, and the eight partial sums meet in shared memory in a fixed
+// order (results do not depend on which CTA takes an item).
+template <class T>
+__host__ __device__ constexpr size_t fwd_gtile_bytes() { return sizeof(T) * (size_t)SPW * RBF; }
+
+template <class T>
+__device__ __forceinline__ void fwd_tile_issue(T *Gs, const T *G, int64_t ld, int w, int rows_avail) {
+    // 16-byte pieces: column c, rows [4 v, 4 v + 4) of the tile; rows past the padded column end are
+    // not copied (their lanes are discarded)
+    constexpr int E = 16 / sizeof(T), PPC = RBF / E;
+    for (int u = threadIdx.x; u < w * PPC; u += blockDim.x) {
+        const int c = u / PPC, v = u - c * PPC;
+        if (v * E < rows_avail) cp_async16(Gs + c * RBF + v * E, G + (int64_t)c * ld + v * E);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
 template <class T, int PB>
-__global__ void __launch_bounds__(256) k_fwd_step(const SolveDesc *sdescs, const int32_t *blk_desc, const int64_t *zo,
-                                                  const int32_t *sn_start, const SolveBufs<T> *jb, int p,
-                                                  LaunchTrace *tr) {
+__global__ void __launch_bounds__(256, PB <= 8 ? 4 : 2)
+    k_fwd_step(const SolveDesc *sdescs, const int32_t *blk_desc, int nrb, int K, const int64_t *zo,
+               const int32_t *sn_start, const SolveBufs<T> *jb, int p, LaunchTrace *tr) {
+    static_assert(SPW == 256 && RBF == 32, "eight warps of 32 columns, a lane per row");
     TraceScope trace_scope(tr);
-    const T *Gp = jb[blockIdx.z].G, *Dg = jb[blockIdx.z].D;
-    T *Z = jb[blockIdx.z].Z, *Zs = jb[blockIdx.z].Zs, *yfw = jb[blockIdx.z].yfw;
-    constexpr int NH = (SPW + 255) / 256, NPF = sizeof(T) == 4 ? NH : 1;
     extern __shared__ __align__(16) unsigned char smraw[];
-    T *zp = reinterpret_cast<T *>(smraw);  // SPW x PB; afterwards the 8 x PB x RBF partials
-    const int di = blk_desc[blockIdx.x];
-    const SolveDesc d = sdescs[di];
-    const int s = d.front, k0 = d.k0, w = d.w;
-    const int r0 = (int)(blockIdx.x - d.off) * RBF;  // relative to k0
-    const int nr = min(RBF, w + d.m2 - r0);
-    const int64_t zb = zo[s] + k0, ld = sg_ld(w + d.m2);
+    T *Gs = reinterpret_cast<T *>(smraw);                         // SPW columns x RBF rows
+    T *zp = reinterpret_cast<T *>(smraw + fwd_gtile_bytes<T>());  // SPW x PB
+    T *red = Gs;                                                  // 8 x PB x RBF partials, after the products
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-    const T *g = Gp + d.goff + r0 + lane;
-    T lv[NPF][32];
+    const int nit = nrb * K;
+    bool waited = false;
+    for (int it = blockIdx.x; it < nit; it += gridDim.x) {
+        const int job = it / nrb, b = it - job * nrb;
+        const SolveBufs<T> J = jb[job];
+        const int di = blk_desc[b];
+        const SolveDesc d = sdescs[di];
+        const int s = d.front, k0 = d.k0, w = d.w, R = w + d.m2;
+        const int r0 = (b - (int)d.off) * RBF;  // relative to k0
+        const int nr = min(RBF, R - r0);
+        const int64_t zb = zo[s] + k0, ld = sg_ld(R);
+        fwd_tile_issue(Gs, J.G + d.goff + r0, ld, w, (int)(ld - r0));
+        // this thread's outputs o = threadIdx.x + 256 u (row i = o % RBF, right-hand side q = o / RBF)
+        constexpr int NO = RBF * PB / 256;
+        static_assert(NO * 256 == RBF * PB, "outputs per thread");
+        T dg[NO], zold[NO];
 #pragma unroll
-    for (int h = 0; h < NPF; ++h) {
-        const int c0 = h * 256 + wp * 32;
-        if (lane < nr && c0 + 32 <= w) {
-#pragma unroll
-            for (int c = 0; c < 32; ++c) lv[h][c] = g[(int64_t)(c0 + c) * ld];
+        for (int u = 0; u < NO; ++u) {
+            const int o = threadIdx.x + 256 * u, i = o % RBF, q = o / RBF, rr = r0 + i;
+            dg[u] = (i < nr && q < p && rr < w) ? J.D[(int64_t)sn_start[s] + k0 + rr] : T(1);
         }
-    }
-    // this thread's outputs o = threadIdx.x + 256 u (row i = o % RBF, right-hand side q = o / RBF):
-    // the pivots of panel rows are static (read before waiting); the rows below are read together
-    // with the panel's z, so that only one round trip follows the wait
-    constexpr int NO = RBF * PB / 256;
-    static_assert(NO * 256 == RBF * PB, "outputs per thread");
-    T dg[NO], zold[NO];
+        if (!waited) {
+            pdl_wait();
+            pdl_trigger();
+            waited = true;
+        }
+        for (int idx = threadIdx.x; idx < w * PB; idx += blockDim.x) {
+            const int c = idx / PB, q = idx % PB;
+            zp[idx] = q < p ? J.Z[(zb + c) * p + q] : T(0);
+        }
 #pragma unroll
-    for (int u = 0; u < NO; ++u) {
-        const int o = threadIdx.x + 256 * u, i = o % RBF, q = o / RBF, rr = r0 + i;
-        dg[u] = (i < nr && q < p && rr < w) ? Dg[(int64_t)sn_start[s] + k0 + rr] : T(1);
-    }
-    pdl_wait();
-    pdl_trigger();
-    for (int idx = threadIdx.x; idx < w * PB; idx += blockDim.x) {
-        int c = idx / PB, q = idx % PB;
-        zp[idx] = q < p ? Z[(zb + c) * p + q] : T(0);
-    }
+        for (int u = 0; u < NO; ++u) {
+            const int o = threadIdx.x + 256 * u, i = o % RBF, q = o / RBF, rr = r0 + i;
+            zold[u] = (i < nr && q < p && rr >= w) ? J.Z[(zb + rr) * p + q] : T(0);
+        }
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        __syncthreads();
+        T acc[PB];
 #pragma unroll
-    for (int u = 0; u < NO; ++u) {
-        const int o = threadIdx.x + 256 * u, i = o % RBF, q = o / RBF, rr = r0 + i;
-        zold[u] = (i < nr && q < p && rr >= w) ? Z[(zb + rr) * p + q] : T(0);
-    }
-    __syncthreads();
-    T acc[PB];
+        for (int q = 0; q < PB; ++q) acc[q] = T(0);
+        {
+            const int c0 = wp * 32, c1 = min(w, c0 + 32);
+            if (lane < nr) {
+                for (int c = c0; c < c1; ++c) {
+                    const T l = Gs[c * RBF + lane];
 #pragma unroll
-    for (int q = 0; q < PB; ++q) acc[q] = T(0);
-#pragma unroll
-    for (int h = 0; h < NH; ++h) {
-        const int c0 = h * 256 + wp * 32, c1 = min(w, c0 + 32);
-        if (lane >= nr || c0 >= c1) continue;
-        if (h < NPF && c1 - c0 == 32) {
-#pragma unroll
-            for (int c = 0; c < 32; ++c)
-#pragma unroll
-                for (int q = 0; q < PB; ++q) acc[q] += lv[h < NPF ? h : 0][c] * zp[(c0 + c) * PB + q];
-        } else {
-            for (int c = c0; c < c1; ++c) {
-                const T l = g[(int64_t)c * ld];
-#pragma unroll
-                for (int q = 0; q < PB; ++q) acc[q] += l * zp[c * PB + q];
+                    for (int q = 0; q < PB; ++q) acc[q] += l * zp[c * PB + q];
+                }
             }
         }
-    }
-    __syncthreads();
-    T *red = zp;
+        __syncthreads();
 #pragma unroll
-    for (int q = 0; q < PB; ++q) red[(wp * PB + q) * RBF + lane] = acc[q];
-    __syncthreads();
+        for (int q = 0; q < PB; ++q) red[(wp * PB + q) * RBF + lane] = acc[q];
+        __syncthreads();
 #pragma unroll
-    for (int u = 0; u < NO; ++u) {
-        const int o = threadIdx.x + 256 * u, i = o % RBF, q = o / RBF;
-        if (i >= nr || q >= p) continue;
-        T v = T(0);
+        for (int u = 0; u < NO; ++u) {
+            const int o = threadIdx.x + 256 * u, i = o % RBF, q = o / RBF;
+            if (i >= nr || q >= p) continue;
+            T v = T(0);
 #pragma unroll
-        for (int j = 0; j < 8; ++j) v += red[(j * PB + q) * RBF + i];
-        const int rr = r0 + i;
-        if (rr < w) {
-            // a panel row is final here: also its diagonal-scaled value for the backward sweep
-            const int64_t gr = (int64_t)sn_start[s] + k0 + rr;
-            Zs[(zb + rr) * p + q] = v;
-            yfw[gr * p + q] = v / dg[u];
-        } else {
-            Z[(zb + rr) * p + q] = zold[u] - v;
+            for (int j = 0; j < 8; ++j) v += red[(j * PB + q) * RBF + i];
+            const int rr = r0 + i;
+            if (rr < w) {
+                // a panel row is final here: also its diagonal-scaled value for the backward sweep
+                const int64_t gr = (int64_t)sn_start[s] + k0 + rr;
+                J.Zs[(zb + rr) * p + q] = v;
+                J.yfw[gr * p + q] = v / dg[u];
+            } else {
+                J.Z[(zb + rr) * p + q] = zold[u] - v;
+            }
         }
+        __syncthreads();  // Gs, zp and red are reused by the next item
     }
+    if (!waited) pdl_wait();
 }
 
 // Narrow steps (every panel of the step at most 32 columns wide, e.g. the leaves of the tree): one
@@ -963,7 +976,7 @@ static size_t trsm_smem() { return sizeof(T) * (size_t)2 * NB * (NB + 1); }
 template <class T>
 static size_t apply_m_smem() { return sizeof(T) * ((size_t)RBB * 33 + (size_t)32 * 257); }
 template <class T, int PB>
-static size_t fwd_step_smem() { return sizeof(T) * (size_t)SPW * PB; }
+static size_t fwd_step_smem() { return fwd_gtile_bytes<T>() + sizeof(T) * (size_t)SPW * PB; }
 template <class T, int PB>
 static size_t bwd_step_smem() { return bwd_tile_smem<T, PB>(); }
 static int rhs_pad(int p) { return p <= 8 ? 8 : (p <= 16 ? 16 : 32); }
@@ -976,6 +989,26 @@ static void set_step_attrs() {
                                   (int)bwd_step_smem<T, PB>()));
     MBL_CUDA(cudaFuncSetAttribute(k_bwd_update<T, PB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)bwd_step_smem<T, PB>()));
+}
+
+// CTAs of 256 threads of `kern` (dynamic shared memory smem) that the device holds at once: the grid
+// of the grid-stride solve kernels.  Cached per device and kernel.
+template <class K>
+static int64_t resident_grid(K *kern, size_t smem) {
+    static std::mutex mu;
+    static std::map<std::pair<int, const void *>, int64_t> cache;
+    int dev = 0;
+    MBL_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(mu);
+    auto key = std::make_pair(dev, reinterpret_cast<const void *>(kern));
+    auto itc = cache.find(key);
+    if (itc != cache.end()) return itc->second;
+    int occ = 0, sms = 0;
+    MBL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 256, smem));
+    MBL_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int64_t g = (int64_t)std::max(1, occ) * sms;
+    cache[key] = g;
+    return g;
 }
 
 template <class T>
@@ -1086,6 +1119,7 @@ template <class T, int PB>
 static void solve_levels(const Plan &pl, const SolveBufs<T> *jb, unsigned K, int p, LaunchTrace *trb,
                          std::vector<int> *kinds, cudaStream_t st) {
     const size_t fsm = fwd_step_smem<T, PB>(), bsm = bwd_step_smem<T, PB>();
+    const int64_t fwd_cap = resident_grid(k_fwd_step<T, PB>, fsm);
     int it = 0;
     auto next_tr = [&](int kind) -> LaunchTrace * {
         if (!trb) return nullptr;
@@ -1108,9 +1142,10 @@ static void solve_levels(const Plan &pl, const SolveBufs<T> *jb, unsigned K, int
                            pl.d_sn_start.data(), jb, p, next_tr(1));
                 continue;
             }
-            launch_pdl(k_fwd_step<T, PB>, dim3((unsigned)ss.nrb, 1, K), dim3(256), fsm, st, sd,
-                       (const int32_t *)pl.d_fblk_desc.data() + ss.fblk0, pl.d_sn_zo.data(), pl.d_sn_start.data(),
-                       jb, p, next_tr(1));
+            const int64_t items = ss.nrb * (int64_t)K;
+            launch_pdl(k_fwd_step<T, PB>, dim3((unsigned)std::min<int64_t>(items, fwd_cap)), dim3(256), fsm, st, sd,
+                       (const int32_t *)pl.d_fblk_desc.data() + ss.fblk0, (int)ss.nrb, (int)K, pl.d_sn_zo.data(),
+                       pl.d_sn_start.data(), jb, p, next_tr(1));
         }
     }
     for (int l = pl.nlevels - 1; l >= 0; --l) {
