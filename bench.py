@@ -17,7 +17,7 @@ JSON line goes to stdout; the per-job records and the full profile go to `--deta
     python bench.py [--gpus N] [--steps K] [--warmup W] [--batch B] [--slots S] [--impl reference]
     python bench.py --case {factor,solve} [--L L] [--reps R] [--precision fp32|fp64]   (profiler cases)
     python bench.py --case observables [--L L] [--reps R]   (the eigenvector observables on nev = 50 vectors)
-    python bench.py --workload {l16batch,serve,large,odd}   (the other configurations)
+    python bench.py --workload {l16batch,serve,large,odd,l22}   (the other configurations)
 """
 from __future__ import annotations
 
@@ -359,6 +359,42 @@ def run_observables_case(args):
     return 0
 
 
+def run_l22(args):
+    """The largest sector of the paper's campaign: L = 22 (dimension 705 432), h = 3, seed `--seeds`
+    jobs from 0, eps = 0.5, nev = 50, FP32 fronts in the memory-lean arena with FP64 refinement, one
+    job after another on the direct path.  Prints the analysis (fill-in, flops, whole and lean arena,
+    job peak), and per job the wall time, factorization time, solves and convergence."""
+    import torch
+
+    import paper_1411_0660_gb300 as g
+
+    ctx = g.Context(0)
+    out = {"workload": "l22", "L": 22, "n": math.comb(22, 11), "jobs": []}
+    for seed in range(args.seeds):
+        sec = g.build_sector(ctx, 22, 3.0, seed)
+        if seed == 0:
+            t0 = time.perf_counter()
+            a = g.analyse(sec, NEV, 8)
+            a["host_s"] = time.perf_counter() - t0
+            out["plan"] = {k: a[k] for k in ("nnz_l", "flops", "max_front", "tree_levels", "front_bytes_fp32",
+                                             "front_peak_bytes_fp32", "solve_factor_bytes_fp32",
+                                             "job_peak_bytes_fp32", "ms_analyse", "host_s")}
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        t0 = time.perf_counter()
+        res = g.solve_near(sec, 0.5, NEV, allow_partial=True)
+        dt = time.perf_counter() - t0
+        lo, hi = g.extremal_bounds(sec)
+        hn = max(abs(lo), abs(hi))
+        sec.close()
+        out["jobs"].append({"seed": seed, "s": dt, "nconv": res.nconv, "max_resid_over_H": float(res.resid.max() / hn),
+                            "sigma": res.sigma, "stats": res.stats, "free_gb_before": free0 / 1e9})
+    out["eigenpairs_per_s"] = sum(j["nconv"] for j in out["jobs"]) / sum(j["s"] for j in out["jobs"])
+    print(json.dumps(out))
+    ctx.close()
+    return 0
+
+
 def run_workload(args):
     """Other configurations of the workload table, each printing its own JSON line:
     l16batch -- batched small sizes: L = 16, h in {1, 2.5, 4} x eps in {0.1, ..., 0.9} x `--seeds`
@@ -387,7 +423,7 @@ def run_workload(args):
             sec = g.build_sector(ctx, L_, 3.0, 0)
             pst = g.analyse(sec, 50, 8)
             sec.close()
-            pst["fits_one_gpu_fp32"] = pst["job_peak_bytes_fp32"] < 0.85 * dev_total
+            pst["fits_one_gpu_fp32"] = pst["job_peak_bytes_fp32"] < dev_total - 4e9
             plans[str(L_)] = pst
         jobs = [(20, 3.0, s, e, g.MBL_PREC_FP32) for s in range(args.seeds) for e in (0.2, 0.5, 0.8)]
         srv.wait(srv.submit(20, 3.0, 10 ** 6, 0.5, 50))  # warm-up: kernels and graphs at L = 20
@@ -487,7 +523,7 @@ def main():
     ap.add_argument("--case", choices=["factor", "solve", "observables"], default=None,
                     help="run one factorization (and --reps solves) instead of the benchmark")
     ap.add_argument("--L", type=int, default=18)
-    ap.add_argument("--workload", choices=["l18", "l16batch", "serve", "large", "odd"], default="l18",
+    ap.add_argument("--workload", choices=["l18", "l16batch", "serve", "large", "odd", "l22"], default="l18",
                     help="l18: the benchmark line; l16batch / serve: the batched and serving configurations")
     ap.add_argument("--seeds", type=int, default=8, help="l16batch: seeds per (h, eps)")
     ap.add_argument("--requests", type=int, default=40, help="serve: number of requests")
@@ -521,6 +557,8 @@ def main():
         return run_observables_case(args)
     if args.case:
         return run_case(args)
+    if args.workload == "l22":
+        return run_l22(args)
     if args.workload != "l18":
         return run_workload(args)
     if args.impl == "reference":

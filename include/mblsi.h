@@ -77,6 +77,13 @@ typedef struct mbl_opts {
     double wait_limit_s;  /* limit of each bounded dependency wait of the dataflow solves, */
                           /*    seconds in [0, 60]; 0 = 1 s.  An expired wait stops the   */
                           /*    waiting CTA and the call returns MBL_ERR_TIMEOUT        [0]    */
+    int arena_mode;       /* fronts arena: 0 automatic (memory-lean when the whole arena  */
+                          /*    would exceed 8 GiB), 1 memory-lean, 2 whole arena       [0]    */
+                          /*    Memory-lean: the arena is a reserved virtual range whose */
+                          /*    regions (fronts of one tree level with one parent level) */
+                          /*    are backed by device memory from their level's assembly */
+                          /*    until their parents' assembly; a front's factor columns  */
+                          /*    are released once copied to the solve factor.            */
 } mbl_opts;
 
 typedef struct mbl_factor_stats {
@@ -203,6 +210,8 @@ typedef struct mbl_plan_stats {
     double front_bytes_fp32, front_bytes_fp64;    /* the fronts arena (alive during the factorization) */
     double solve_factor_bytes_fp32;               /* packed G of the solve panels (alive with the factor) */
     double job_peak_bytes_fp32, job_peak_bytes_fp64;
+    double front_peak_bytes_fp32, front_peak_bytes_fp64;  /* the fronts arena at its peak in the automatic
+                                                             arena mode (see mbl_opts.arena_mode) */
 } mbl_plan_stats;
 int mbl_analyse(mbl_sector *sec, int nev, int block, mbl_plan_stats *stats);
 

@@ -27,7 +27,7 @@ class Opts(ctypes.Structure):
                 ("tol", c_double), ("target_tol", c_double), ("refine_tol", c_double), ("max_refine", c_int),
                 ("start_seed", c_uint64), ("tensor_cores", c_int), ("refine_mode", c_int),
                 ("gmres_restart", c_int), ("solve_dataflow", c_int), ("deflate", c_int),
-                ("wait_limit_s", c_double)]
+                ("wait_limit_s", c_double), ("arena_mode", c_int)]
 
 
 class FactorStats(ctypes.Structure):
@@ -43,7 +43,8 @@ class PlanStats(ctypes.Structure):
                 ("ms_analyse", c_double), ("factor_bytes_fp32", c_double), ("factor_bytes_fp64", c_double),
                 ("front_bytes_fp32", c_double), ("front_bytes_fp64", c_double),
                 ("solve_factor_bytes_fp32", c_double), ("job_peak_bytes_fp32", c_double),
-                ("job_peak_bytes_fp64", c_double)]
+                ("job_peak_bytes_fp64", c_double), ("front_peak_bytes_fp32", c_double),
+                ("front_peak_bytes_fp64", c_double)]
 
 
 class SolveStats(ctypes.Structure):

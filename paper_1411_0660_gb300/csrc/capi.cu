@@ -164,7 +164,8 @@ uint64_t wait_limit_ns(double seconds) {
 }
 
 std::unique_ptr<Factorization> make_factorization(mbl_sector *sec, double sigma, int prec, double hnorm, int tc_mode,
-                                                  bool dataflow, uint64_t wait_ns) {
+                                                  bool dataflow, uint64_t wait_ns, int arena_mode) {
+    if (arena_mode < ARENA_AUTO || arena_mode > ARENA_FULL) fail(MBL_ERR_INVALID, "arena_mode must be 0, 1 or 2");
     if (prec != MBL_PREC_FP64 && prec != MBL_PREC_FP32) fail(MBL_ERR_INVALID, "unknown precision");
     if (tc_mode < 0 || tc_mode > 2) fail(MBL_ERR_INVALID, "tensor_cores must be 0, 1 (3xTF32) or 2 (3xBF16)");
     auto F = std::make_unique<Factorization>();
@@ -177,7 +178,7 @@ std::unique_ptr<Factorization> make_factorization(mbl_sector *sec, double sigma,
     F->tc_mode = tc_mode;
     F->dataflow = dataflow;
     F->wait_ns = wait_ns;
-    F->allocate();
+    F->allocate(arena_is_lean(*F->plan, prec, arena_mode));
     cudaStream_t st = sec->ctx->stream;
     cudaEvent_t e0, e1;
     MBL_CUDA(cudaEventCreate(&e0));
@@ -251,6 +252,7 @@ void mbl_opts_default(mbl_opts *o) {
     o->solve_dataflow = 0;
     o->deflate = 1;
     o->wait_limit_s = 0.0;
+    o->arena_mode = 0;
 }
 
 const char *mbl_version(void) { return "mblsi 0.1 (sm_103a)"; }
@@ -504,7 +506,7 @@ int mbl_factor(mbl_sector *sec, double sigma, const mbl_opts *opts, mbl_factoriz
     extremal_bounds(sec, &emin, &emax);
     double hn = std::max(std::fabs(emin), std::fabs(emax));
     auto F = make_factorization(sec, sigma, o.precision, hn, o.tensor_cores, o.solve_dataflow != 0,
-                                wait_limit_ns(o.wait_limit_s));
+                                wait_limit_ns(o.wait_limit_s), o.arena_mode);
     mbl_factorization *h = new mbl_factorization();
     h->f = std::move(F);
     *out = h;
@@ -524,7 +526,7 @@ int mbl_factor_stats_get(const mbl_factorization *fh, mbl_factor_stats *s) {
     s->negative = f.negative;
     s->flops = p.flops;
     s->factor_bytes = (double)(p.nnz_l + p.n) * f.elem_size();
-    s->front_bytes = (double)p.arena_elems * f.elem_size();
+    s->front_bytes = f.lean_used ? (double)p.lean_peak_elems * f.elem_size() : (double)p.arena_elems * f.elem_size();
     s->ms_factor = f.ms_factor;
     s->max_abs_l = f.max_l;
     s->min_abs_d = f.min_d;
@@ -552,6 +554,8 @@ int mbl_analyse(mbl_sector *sec, int nev, int block, mbl_plan_stats *s) {
     s->front_bytes_fp32 = (double)p.arena_elems * 4.0;
     s->front_bytes_fp64 = (double)p.arena_elems * 8.0;
     s->solve_factor_bytes_fp32 = (double)p.sg_elems * 4.0;
+    s->front_peak_bytes_fp32 = arena_peak_bytes(p, MBL_PREC_FP32, ARENA_AUTO);
+    s->front_peak_bytes_fp64 = arena_peak_bytes(p, MBL_PREC_FP64, ARENA_AUTO);
     s->job_peak_bytes_fp32 = (double)job_bytes(p, nev, block, MBL_PREC_FP32);
     s->job_peak_bytes_fp64 = (double)job_bytes(p, nev, block, MBL_PREC_FP64);
     API_CATCH(sec->ctx)

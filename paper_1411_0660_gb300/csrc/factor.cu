@@ -12,6 +12,8 @@
 //   update     A22 -= L21 W21^T on the lower triangle, 64 x 64 tiles in parallel.
 // Pivoting permutes only the variables of the current panel; the rows of earlier panel
 // columns keep their order and the solves apply each panel's permutation when they reach it.
+#include <cuda.h>
+
 #include <cfloat>
 #include <map>
 #include <mutex>
@@ -20,6 +22,145 @@
 #include "solve_tile.cuh"
 
 namespace mbl {
+
+// The driver's virtual-memory calls, resolved through the runtime at first use (the library does
+// not link the driver library itself, so it still loads where no driver is installed).
+struct VmmApi {
+    decltype(&::cuGetErrorString) error_string = nullptr;
+    decltype(&::cuMemGetAllocationGranularity) granularity = nullptr;
+    decltype(&::cuMemAddressReserve) reserve = nullptr;
+    decltype(&::cuMemAddressFree) address_free = nullptr;
+    decltype(&::cuMemCreate) create = nullptr;
+    decltype(&::cuMemMap) map = nullptr;
+    decltype(&::cuMemSetAccess) set_access = nullptr;
+    decltype(&::cuMemUnmap) unmap = nullptr;
+    decltype(&::cuMemRelease) release = nullptr;
+};
+
+static const VmmApi &vmm() {
+    static const VmmApi api = [] {
+        VmmApi a;
+        auto get = [](const char *name, void **fn) {
+            cudaDriverEntryPointQueryResult q;
+            if (cudaGetDriverEntryPointByVersion(name, fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+                q != cudaDriverEntryPointSuccess)
+                *fn = nullptr;
+        };
+        get("cuGetErrorString", reinterpret_cast<void **>(&a.error_string));
+        get("cuMemGetAllocationGranularity", reinterpret_cast<void **>(&a.granularity));
+        get("cuMemAddressReserve", reinterpret_cast<void **>(&a.reserve));
+        get("cuMemAddressFree", reinterpret_cast<void **>(&a.address_free));
+        get("cuMemCreate", reinterpret_cast<void **>(&a.create));
+        get("cuMemMap", reinterpret_cast<void **>(&a.map));
+        get("cuMemSetAccess", reinterpret_cast<void **>(&a.set_access));
+        get("cuMemUnmap", reinterpret_cast<void **>(&a.unmap));
+        get("cuMemRelease", reinterpret_cast<void **>(&a.release));
+        (void)cudaGetLastError();
+        return a;
+    }();
+    if (!api.granularity || !api.reserve || !api.address_free || !api.create || !api.map || !api.set_access ||
+        !api.unmap || !api.release)
+        fail(MBL_ERR_CUDA, "memory-lean arena: the driver's virtual-memory entry points are unavailable");
+    return api;
+}
+
+#define MBL_CU(x)                                                                                            \
+    do {                                                                                                     \
+        CUresult r_ = (x);                                                                                   \
+        if (r_ != CUDA_SUCCESS) {                                                                            \
+            const char *m_ = nullptr;                                                                        \
+            if (vmm().error_string) vmm().error_string(r_, &m_);                                             \
+            ::mbl::fail(r_ == CUDA_ERROR_OUT_OF_MEMORY ? MBL_ERR_OOM : MBL_ERR_CUDA,                        \
+                        std::string(#x) + " -> " + (m_ ? m_ : "?"));                                         \
+        }                                                                                                    \
+    } while (0)
+
+// Physical backing of the memory-lean fronts arena: the whole arena is one reserved virtual range
+// (so that every kernel addresses a front as arena + fo[s], as with the ordinary arena), and each
+// region of the plan is backed chunk by chunk (LEAN_CHUNK elements) only while its fronts are live.
+struct LeanArena {
+    CUdeviceptr base = 0;
+    size_t bytes = 0, es = 4;
+    Ctx *ctx = nullptr;
+    CUmemAllocationProp prop{};
+    std::vector<std::vector<CUmemGenericAllocationHandle>> h;  // per region and chunk (0: not backed)
+
+    void reserve(Ctx *c, const Plan &p, size_t es_) {
+        ctx = c;
+        es = es_;
+        prop.type = CU_MEM_ALLOCATION_TYPE_PINNED;
+        prop.location.type = CU_MEM_LOCATION_TYPE_DEVICE;
+        prop.location.id = c->device;
+        size_t gran = 0;
+        MBL_CU(vmm().granularity(&gran, &prop, CU_MEM_ALLOC_GRANULARITY_MINIMUM));
+        if (gran == 0 || ((size_t)ARENA_ALIGN * es) % gran != 0)
+            fail(MBL_ERR_CUDA, "memory-lean arena: allocation granularity does not divide the region alignment");
+        bytes = (size_t)p.arena_elems * es;
+        MBL_CU(vmm().reserve(&base, bytes, (size_t)ARENA_ALIGN * es, 0, 0));
+        h.assign(p.regions.size(), {});
+        for (size_t r = 0; r < p.regions.size(); ++r)
+            h[r].assign((size_t)((p.regions[r].fo1 - p.regions[r].fo0 + LEAN_CHUNK - 1) / LEAN_CHUNK), 0);
+    }
+    // byte offset and length of chunk c of region r (the last one rounded up to ARENA_ALIGN elements)
+    void chunk(const Plan &p, size_t r, size_t c, size_t &off, size_t &len) const {
+        const ArenaRegion &g = p.regions[r];
+        const int64_t a0 = g.fo0 + (int64_t)c * LEAN_CHUNK, a1 = std::min(g.fo1, a0 + LEAN_CHUNK);
+        off = (size_t)a0 * es;
+        len = (size_t)((a1 - a0 + ARENA_ALIGN - 1) / ARENA_ALIGN * ARENA_ALIGN) * es;
+    }
+    void map_region(const Plan &p, size_t r) {
+        CUmemAccessDesc acc{};
+        acc.location = prop.location;
+        acc.flags = CU_MEM_ACCESS_FLAGS_PROT_READWRITE;
+        for (size_t c = 0; c < h[r].size(); ++c) {
+            if (h[r][c]) continue;
+            size_t off, len;
+            chunk(p, r, c, off, len);
+            if (ctx->budget && ctx->in_use + len > ctx->budget)
+                fail(MBL_ERR_OOM, "memory-lean arena: chunk exceeds the context budget");
+            CUmemGenericAllocationHandle hd = 0;
+            MBL_CU(vmm().create(&hd, len, &prop, 0));
+            CUresult e = vmm().map(base + off, len, 0, hd, 0);
+            if (e == CUDA_SUCCESS) e = vmm().set_access(base + off, len, &acc, 1);
+            if (e != CUDA_SUCCESS) {
+                vmm().unmap(base + off, len);
+                vmm().release(hd);
+                MBL_CU(e);
+            }
+            h[r][c] = hd;
+            ctx->in_use += len;
+            ctx->peak = std::max(ctx->peak, ctx->in_use);
+        }
+    }
+    // the caller has synchronized every stream that used the chunk
+    void unmap_chunk(const Plan &p, size_t r, size_t c) {
+        if (!h[r][c]) return;
+        size_t off, len;
+        chunk(p, r, c, off, len);
+        MBL_CU(vmm().unmap(base + off, len));
+        MBL_CU(vmm().release(h[r][c]));
+        h[r][c] = 0;
+        ctx->in_use -= len;
+    }
+    void unmap_region(const Plan &p, size_t r) {
+        for (size_t c = 0; c < h[r].size(); ++c) unmap_chunk(p, r, c);
+    }
+    // (no CUDA error escapes: also run from destructors)
+    void release_all(const Plan *p) {
+        for (size_t r = 0; r < h.size(); ++r)
+            for (size_t c = 0; c < h[r].size(); ++c)
+                if (h[r][c]) {
+                    size_t off = 0, len = 0;
+                    if (p) chunk(*p, r, c, off, len);
+                    if (p) vmm().unmap(base + off, len);
+                    vmm().release(h[r][c]);
+                    h[r][c] = 0;
+                    if (ctx && ctx_alive(ctx)) ctx->in_use -= len;
+                }
+        if (base) vmm().address_free(base, bytes);
+        base = 0;
+    }
+};
 
 template <class T>
 __device__ __forceinline__ T tabs(T x) { return x < T(0) ? -x : x; }
@@ -1027,9 +1168,28 @@ template <class T>
 static void factor_impl(Factorization &fz, cudaStream_t st) {
     Plan &p = *fz.plan;
     mbl_sector *sec = fz.sec;
-    T *arena = static_cast<T *>(fz.arena.m.p);
+    LeanArena *lean = fz.lean.get();
+    T *arena = lean ? reinterpret_cast<T *>(lean->base) : static_cast<T *>(fz.arena.m.p);
     T *Dg = static_cast<T *>(fz.D.m.p);
     T *wscr = static_cast<T *>(fz.wscr.m.p);
+    T *Gp = static_cast<T *>(fz.gpk.m.p);
+    MBL_CUDA(cudaMemsetAsync(Gp, 0, (size_t)p.sg_elems * sizeof(T), st));  // padding rows of G stay zero
+    // G = [M; L21 M] of the solve panels of level l (the panels' M blocks first)
+    auto build_g_level = [&](int l) {
+        if (p.lvl_nd[l] <= 0) return;
+        ProfScope ps_g(fz.ctx, "f_build_g", 0.0, st);
+        k_build_m<T><<<dim3((unsigned)p.lvl_nd[l], SPW / 32), 256, build_m_smem<T>(), st>>>(
+            p.d_sdescs.data() + p.lvl_d0[l], p.d_sn_fo.data(), p.d_sn_f.data(), p.d_sn_start.data(), arena,
+            fz.piv.data(), static_cast<T *>(fz.M.m.p));
+        MBL_LAUNCH_CHECK();
+        for (int si = p.lvl_sstep_ptr[l]; si < p.lvl_sstep_ptr[l + 1]; ++si) {
+            const SolveStep &ss = p.ssteps[si];
+            k_apply_m<T><<<dim3((unsigned)ss.nrbb, (SPW + 255) / 256), 256, apply_m_smem<T>(), st>>>(
+                p.d_sdescs.data() + ss.d0, ss.nd, p.d_sn_fo.data(), p.d_sn_f.data(), arena,
+                static_cast<const T *>(fz.M.m.p), Gp);
+            MBL_LAUNCH_CHECK();
+        }
+    };
     static std::atomic<bool> attr{false};  // per process: one device
     if (!attr) {
         MBL_CUDA(cudaFuncSetAttribute(k_panel_trsm<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)trsm_smem<T>()));
@@ -1040,6 +1200,9 @@ static void factor_impl(Factorization &fz, cudaStream_t st) {
     MBL_CUDA(cudaMemsetAsync(fz.counters.data() + 4, 0x7f, sizeof(unsigned int), st));  // min |d| starts huge
     for (int l = 0; l < p.nlevels; ++l) {
         int na = p.asm_ptr[l + 1] - p.asm_ptr[l];
+        if (lean)
+            for (size_t r = 0; r < p.regions.size(); ++r)
+                if (p.regions[r].level == l) lean->map_region(p, r);
         {
             ProfScope ps_asm(fz.ctx, "f_assemble", 0.0, st);
             k_assemble<T><<<na, 256, 0, st>>>(p.d_asm_items.data() + p.asm_ptr[l], p.d_sn_fo.data(), p.d_sn_f.data(),
@@ -1048,6 +1211,11 @@ static void factor_impl(Factorization &fz, cudaStream_t st) {
                                               p.d_amap_ptr.data(), p.d_amap_src.data(), p.d_amap_row.data(),
                                               sec->val.data(), fz.sigma, arena);
             MBL_LAUNCH_CHECK();
+        }
+        if (lean) {  // contribution blocks last read by this assembly
+            MBL_CUDA(cudaStreamSynchronize(st));
+            for (size_t r = 0; r < p.regions.size(); ++r)
+                if (p.regions[r].level < l && p.regions[r].release == l) lean->unmap_region(p, r);
         }
         for (int si = p.lvl_step_ptr[l]; si < p.lvl_step_ptr[l + 1]; ++si) {
             const PanelStep &stp = p.steps[si];
@@ -1088,7 +1256,16 @@ static void factor_impl(Factorization &fz, cudaStream_t st) {
                 }
             }
         }
+        if (lean) {  // the level's factor columns move to G; then they, and its root fronts, can go
+            build_g_level(l);
+            MBL_CUDA(cudaStreamSynchronize(st));
+            for (int64_t i = p.lean_prefix_ptr[l]; i < p.lean_prefix_ptr[l + 1]; ++i)
+                lean->unmap_chunk(p, (size_t)p.lean_prefix[i].first, (size_t)p.lean_prefix[i].second);
+            for (size_t r = 0; r < p.regions.size(); ++r)
+                if (p.regions[r].level == l && p.regions[r].release == l) lean->unmap_region(p, r);
+        }
     }
+    if (lean) return;
     // block operators of the solve panels, then G = [M; L21 M] of each panel into the packed solve factor
     if (!p.sdescs.empty()) {
         ProfScope ps_g(fz.ctx, "f_build_g", 0.0, st);
@@ -1097,8 +1274,6 @@ static void factor_impl(Factorization &fz, cudaStream_t st) {
                                                            p.d_sn_start.data(), arena, fz.piv.data(),
                                                            static_cast<T *>(fz.M.m.p));
         MBL_LAUNCH_CHECK();
-        T *Gp = static_cast<T *>(fz.gpk.m.p);
-        MBL_CUDA(cudaMemsetAsync(Gp, 0, (size_t)p.sg_elems * sizeof(T), st));  // padding rows stay zero
         for (const SolveStep &ss : p.ssteps) {
             k_apply_m<T><<<dim3((unsigned)ss.nrbb, (SPW + 255) / 256), 256, apply_m_smem<T>(), st>>>(p.d_sdescs.data() + ss.d0, ss.nd,
                                                                            p.d_sn_fo.data(), p.d_sn_f.data(), arena,
@@ -1350,10 +1525,28 @@ void Factorization::ensure_solve_work(int p) {
     }
 }
 
-void Factorization::allocate() {
+bool arena_is_lean(const Plan &p, int prec, int mode) {
+    if (mode == ARENA_LEAN) return true;
+    if (mode == ARENA_FULL) return false;
+    const double es = prec == MBL_PREC_FP64 ? 8.0 : 4.0;
+    return (double)p.arena_elems * es > 8.0 * (double)(1ull << 30);
+}
+
+double arena_peak_bytes(const Plan &p, int prec, int mode) {
+    const double es = prec == MBL_PREC_FP64 ? 8.0 : 4.0;
+    return (arena_is_lean(p, prec, mode) ? (double)p.lean_peak_elems : (double)p.arena_elems) * es;
+}
+
+void Factorization::allocate(bool lean_arena) {
     Plan &pl = *plan;
     size_t es = elem_size();
-    arena.alloc(ctx, (size_t)pl.arena_elems * es);
+    lean_used = lean_arena;
+    if (lean_arena) {
+        lean = std::make_unique<LeanArena>();
+        lean->reserve(ctx, pl, es);
+    } else {
+        arena.alloc(ctx, (size_t)pl.arena_elems * es);
+    }
     D.alloc(ctx, (size_t)pl.n * es);
     piv.alloc(ctx, pl.n);
     counters.alloc(ctx, 5);
@@ -1377,10 +1570,21 @@ void Factorization::release_scratch() {
     cmax.release();
     M.release();      // folded into G = [M; L21 M]
     arena.release();  // the solves read only the packed G and D
+    if (lean) {
+        MBL_CUDA(cudaStreamSynchronize(ctx->stream));
+        lean->release_all(plan.get());
+        lean.reset();
+    }
 }
+
+Factorization::Factorization() = default;
 
 Factorization::~Factorization() {
     if (graph_exec) cudaGraphExecDestroy(graph_exec);
+    if (lean) {
+        if (ctx_alive(ctx)) cudaStreamSynchronize(ctx->stream);
+        lean->release_all(plan.get());
+    }
 }
 
 }  // namespace mbl

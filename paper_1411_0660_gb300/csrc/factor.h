@@ -18,6 +18,15 @@ struct SolveBufs {
     unsigned int *cnt;   // backward arrival counters (per solve descriptor and column chunk)
 };
 
+struct LeanArena;  // physical backing of the memory-lean fronts arena (factor.cu)
+
+// Fronts arena modes: the whole arena allocated at once, or the memory-lean arena (regions backed
+// only while their fronts are live).  Automatic: lean when the whole arena would exceed 8 GiB.
+constexpr int ARENA_AUTO = 0, ARENA_LEAN = 1, ARENA_FULL = 2;
+bool arena_is_lean(const Plan &p, int prec, int mode);
+// Device bytes of the fronts arena at its peak in that mode.
+double arena_peak_bytes(const Plan &p, int prec, int mode);
+
 struct Factorization {
     Ctx *ctx = nullptr;
     mbl_sector *sec = nullptr;
@@ -31,6 +40,8 @@ struct Factorization {
     DVec<unsigned int> scnt;  // per (solve panel, column chunk) arrival counters of the backward step
     DVec<int32_t> dfcnt;      // dataflow solve: per-front completion counters (4 ns) and two tickets
     bool dataflow = false;    // solves as one persistent kernel per sweep (else level-by-level launches)
+    std::unique_ptr<LeanArena> lean;  // set: the fronts live in the memory-lean arena, not `arena`
+    bool lean_used = false;           // the factorization ran in the memory-lean arena
     uint64_t wait_ns = 1000000000ull;  // limit of each bounded dependency wait of the dataflow solve
     // [0] perturbed pivots, [1] negative pivots, [2] wait time-outs, [3] max |l| (float bits, low
     // word), [4] min |d| (float bits, low word)
@@ -51,8 +62,9 @@ struct Factorization {
     double ms_factor = 0.0;
 
     size_t elem_size() const { return prec == MBL_PREC_FP64 ? sizeof(double) : sizeof(float); }
+    Factorization();  // out of line: LeanArena is complete only in factor.cu
     ~Factorization();
-    void allocate();
+    void allocate(bool lean_arena = false);
     void release_scratch();
     void ensure_solve_work(int p);
 };
@@ -115,7 +127,7 @@ std::shared_ptr<Plan> get_plan(mbl_sector *sec);
 // Create, allocate and run a factorization (synchronous; fills stats).
 std::unique_ptr<Factorization> make_factorization(mbl_sector *sec, double sigma, int prec, double hnorm,
                                                   int tc_mode = 1, bool dataflow = false,
-                                                  uint64_t wait_ns = 1000000000ull);
+                                                  uint64_t wait_ns = 1000000000ull, int arena_mode = ARENA_AUTO);
 // Wait-limit option (seconds, 0 = the 1 s default) in nanoseconds.
 uint64_t wait_limit_ns(double seconds);
 // After a solve reported expired waits: clear the time-out count and the per-chunk arrival counters

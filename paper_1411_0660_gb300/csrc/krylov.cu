@@ -1268,7 +1268,7 @@ void solve_near(mbl_sector *sec, double eps, int nev, const mbl_opts &o, double 
     auto tf0 = std::chrono::steady_clock::now();
     std::unique_ptr<Factorization> fz =
         make_factorization(sec, sigma_f, o.precision, hnorm, o.tensor_cores, o.solve_dataflow != 0,
-                           wait_limit_ns(o.wait_limit_s));
+                           wait_limit_ns(o.wait_limit_s), o.arena_mode);
     S.ms_factor = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tf0).count();
     RefinedSolve op{sec, fz.get(), hnorm + std::fabs(sigma_f), o.refine_tol, o.max_refine};
     op.gmres = o.refine_mode;
@@ -1318,7 +1318,7 @@ void solve_near(mbl_sector *sec, double eps, int nev, const mbl_opts &o, double 
                 op.fz = nullptr;
                 fz.reset();  // free the FP32 fronts first: the two factors never coexist in HBM
                 fz = make_factorization(sec, sigma_f, MBL_PREC_FP64, hnorm, 1, o.solve_dataflow != 0,
-                                        wait_limit_ns(o.wait_limit_s));
+                                        wait_limit_ns(o.wait_limit_s), o.arena_mode);
                 S.ms_factor += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tf1).count();
                 op.fz = fz.get();
                 op.stalled = false;
@@ -1355,7 +1355,7 @@ void solve_near(mbl_sector *sec, double eps, int nev, const mbl_opts &o, double 
                 fz.reset();
                 auto tf1 = std::chrono::steady_clock::now();
                 fz = make_factorization(sec, sigma_f, prec_now, hnorm, o.tensor_cores, o.solve_dataflow != 0,
-                                        wait_limit_ns(o.wait_limit_s));
+                                        wait_limit_ns(o.wait_limit_s), o.arena_mode);
                 S.ms_factor += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tf1).count();
                 op.fz = fz.get();
                 op.anorm = hnorm + std::fabs(sigma_f);

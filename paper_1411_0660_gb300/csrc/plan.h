@@ -7,6 +7,8 @@
 // batched numeric factorization and the triangular solves replay.
 #pragma once
 
+#include <utility>
+
 #include "mbl_internal.h"
 
 namespace mbl {
@@ -17,6 +19,8 @@ constexpr int TB = 64;  // tile edge of the trailing (Schur) update
 constexpr int ACOLS = 32;  // columns per assembly work item
 constexpr int SPW = 256;   // width of a solve panel (4 factor panels): one dense block operator M each
 constexpr int SUBS = SPW / NB;
+constexpr int64_t ARENA_ALIGN = (int64_t)1 << 19;  // elements: 2 MiB in FP32, 4 MiB in FP64
+constexpr int64_t LEAN_CHUNK = (int64_t)1 << 23;   // elements per physical chunk of the memory-lean arena
 
 // One active front in one (level, panel) step.
 struct PanelDesc {
@@ -103,6 +107,13 @@ struct SolveItem {
     int32_t front, a, b;
 };
 
+// Fronts [fo0, fo1) of one level whose contribution blocks are last read by the assembly of level
+// `release` (their parents' level; the level itself for roots).
+struct ArenaRegion {
+    int32_t level, release;
+    int64_t fo0, fo1;
+};
+
 struct AsmItem {     // assembly work item: columns [c0, c0 + ACOLS) of a front
     int32_t front, c0;
 };
@@ -121,6 +132,14 @@ struct Plan {
     std::vector<int64_t> amap_src;            // CSR position
     std::vector<int32_t> amap_row;            // local row in the front
     std::vector<int32_t> lvl_ptr, lvl_fronts;  // fronts by level
+    // the fronts arena as regions of fronts sharing (level, release level), ordered by both; each
+    // starts on an ARENA_ALIGN boundary.  lean_peak_elems is the most the regions hold at one time
+    // when each is mapped from its level's assembly to its release.
+    std::vector<ArenaRegion> regions;
+    int64_t lean_peak_elems = 0;
+    // (region, chunk) pairs lying wholly in one front's fully summed columns, by level (ptr nlevels + 1)
+    std::vector<int64_t> lean_prefix_ptr;
+    std::vector<std::pair<int32_t, int32_t>> lean_prefix;
     std::vector<int32_t> asm_ptr;             // assembly items by level
     std::vector<AsmItem> asm_items;
     std::vector<PanelStep> steps;

@@ -20,22 +20,29 @@
 
 namespace mbl {
 
-// Upper estimate of the device bytes one job holds at its peak (plan of its L known).
+// Upper estimate of the device bytes one job holds at its peak (plan of its L known).  A job runs in
+// phases: extremal bounds (a Lanczos basis), the numeric factorization (fronts arena at its peak in
+// the automatic arena mode, the packed solve factor, the panel operators), then the Krylov iteration
+// (solve factor, solve work, Krylov basis, Rayleigh-Ritz and refinement work).  A refactorization
+// (shift moved off an eigenvalue, FP64 fallback) runs with the Krylov buffers alive, so they count
+// in the factorization phase too.  The sector and the outputs are held throughout.
 size_t job_bytes(const Plan &p, int nev, int block, int prec) {
     const double n = (double)p.n, es = prec == MBL_PREC_FP64 ? 8.0 : 4.0;
     const int pb = std::max(1, std::min(32, block));
     const double pad = pb <= 8 ? 8 : (pb <= 16 ? 16 : 32);
     const double ldv = 2.0 * nev + 3.0 * pb;
-    double b = 0.0;
-    b += 20.0 * n + 12.0 * (double)p.nnzA;                                   // sector
-    b += (double)p.arena_elems * es + n * (es + 4.0);                        // fronts, D, pivots
-    b += (double)std::max<int64_t>(p.wscratch_elems, 1) * es + (double)p.m_elems * es;
-    b += (double)p.sg_elems * es;                                            // packed solve factor
-    b += 2.0 * (double)p.zwork_elems * pb * es + 2.0 * n * pb * es;         // solve work
-    b += (double)std::max(p.max_sstep_nrbk, p.max_lvl_nrbk) * SUBS * RBB * pad * es;
-    b += 8.0 * n * (3.0 * ldv + 2.0 * nev + 30.0 * pb);                      // Krylov, Rayleigh-Ritz, refinement
-    b += 8.0 * n * 480.0;                                                    // extremal-bounds Lanczos basis
-    return (size_t)(1.10 * b) + ((size_t)64 << 20);
+    const double held = 20.0 * n + 12.0 * (double)p.nnzA      // sector
+                        + 8.0 * n * nev + 64.0 * nev;         // outputs
+    const double factor_keep = (double)p.sg_elems * es + n * (es + 4.0);  // packed solve factor, D, pivots
+    const double krylov = 8.0 * n * (3.0 * ldv + 2.0 * nev + 30.0 * pb)  // Krylov, Rayleigh-Ritz, refinement
+                          + 2.0 * (double)p.zwork_elems * pb * es + 2.0 * n * pb * es  // solve work
+                          + (double)std::max(p.max_sstep_nrbk, p.max_lvl_nrbk) * SUBS * RBB * pad * es;
+    const double bounds = 8.0 * n * 480.0;  // extremal-bounds Lanczos basis
+    const double factor = arena_peak_bytes(p, prec, ARENA_AUTO) + factor_keep +
+                          (double)std::max<int64_t>(p.wscratch_elems, 1) * es + (double)p.m_elems * es + krylov;
+    const double solve = factor_keep + krylov;
+    const double peak = held + std::max(bounds, std::max(factor, solve));
+    return (size_t)(1.05 * peak) + ((size_t)128 << 20);
 }
 
 namespace {

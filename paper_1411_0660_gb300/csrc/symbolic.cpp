@@ -448,14 +448,105 @@ std::shared_ptr<Plan> build_plan(int L, const std::vector<uint32_t> &states, con
         std::vector<int32_t> fill(p.lvl_ptr.begin(), p.lvl_ptr.end() - 1);
         for (int32_t s = 0; s < ns; ++s) p.lvl_fronts[fill[p.sn_level[s]]++] = s;
     }
+    // Fronts are grouped by (level, release level), the release level of a front being its parent's
+    // level -- the assembly that reads its contribution block last -- or its own for a root.  Each
+    // group is one region of the arena starting on an ARENA_ALIGN boundary, so that the memory-lean
+    // factorization can back each region with its own physical memory: mapped before its level
+    // assembles, released right after its release level's assembly (a root's after its own level's
+    // solve-factor build).  Regions are ordered by level, then release level.
     p.sn_fo.assign(ns + 1, 0);
     p.sn_zo.assign(ns + 1, 0);
-    for (int32_t s = 0; s < ns; ++s) {
-        int64_t f = p.sn_f[s];
-        p.sn_fo[s + 1] = p.sn_fo[s] + f * f;
-        p.sn_zo[s + 1] = p.sn_zo[s] + f;
+    for (int32_t s = 0; s < ns; ++s) p.sn_zo[s + 1] = p.sn_zo[s] + p.sn_f[s];
+    p.regions.clear();
+    {
+        int64_t cur = 0;
+        for (int l = 0; l < p.nlevels; ++l) {
+            std::vector<std::pair<int32_t, int32_t>> fr;  // (release level, front)
+            for (int32_t q = p.lvl_ptr[l]; q < p.lvl_ptr[l + 1]; ++q) {
+                const int32_t s = p.lvl_fronts[q];
+                fr.push_back({p.sn_parent[s] < 0 ? l : p.sn_level[p.sn_parent[s]], s});
+            }
+            std::stable_sort(fr.begin(), fr.end(),
+                             [](const std::pair<int32_t, int32_t> &x, const std::pair<int32_t, int32_t> &y) {
+                                 return x.first < y.first;
+                             });
+            for (size_t i = 0; i < fr.size(); ++i) {
+                if (i == 0 || fr[i].first != fr[i - 1].first) {
+                    cur = (cur + ARENA_ALIGN - 1) / ARENA_ALIGN * ARENA_ALIGN;
+                    p.regions.push_back(ArenaRegion{l, fr[i].first, cur, cur});
+                }
+                const int32_t s = fr[i].second;
+                p.sn_fo[s] = cur;
+                cur += (int64_t)p.sn_f[s] * p.sn_f[s];
+                p.regions.back().fo1 = cur;
+            }
+        }
+        p.arena_elems = (cur + ARENA_ALIGN - 1) / ARENA_ALIGN * ARENA_ALIGN;
+        p.sn_fo[ns] = p.arena_elems;
     }
-    p.arena_elems = p.sn_fo[ns];
+    // Peak of the memory-lean arena.  Each region is mapped as chunks of LEAN_CHUNK elements (the last
+    // one rounded up to ARENA_ALIGN) when its level assembles; a region whose release level is later is
+    // released right after that level's assembly; once a level's panels and solve-factor build are done,
+    // the chunks lying wholly inside one of its fronts' fully summed columns [fo, fo + nc f) (the
+    // factor, now copied to the solve factor) and its root regions are released too.  The peak is
+    // taken after each assembly and after each level's panels, the two points where nothing has been
+    // released yet since the last mapping.
+    {
+        auto chunk_sz = [](int64_t a0, int64_t a1) {
+            return (std::min(a1, a0 + LEAN_CHUNK) - a0 + ARENA_ALIGN - 1) / ARENA_ALIGN * ARENA_ALIGN;
+        };
+        std::vector<std::vector<char>> gone(p.regions.size());
+        for (size_t r = 0; r < p.regions.size(); ++r)
+            gone[r].assign((size_t)((p.regions[r].fo1 - p.regions[r].fo0 + LEAN_CHUNK - 1) / LEAN_CHUNK), 0);
+        auto release_region = [&](size_t r, int64_t &mapped) {
+            const ArenaRegion &g = p.regions[r];
+            for (size_t c = 0; c < gone[r].size(); ++c)
+                if (!gone[r][c]) {
+                    gone[r][c] = 1;
+                    mapped -= chunk_sz(g.fo0 + (int64_t)c * LEAN_CHUNK, g.fo1);
+                }
+        };
+        // chunks wholly inside a front's fully summed columns, by level: released after its build
+        p.lean_prefix_ptr.assign(p.nlevels + 1, 0);
+        p.lean_prefix.clear();
+        for (int l = 0; l < p.nlevels; ++l) {
+            for (size_t r = 0; r < p.regions.size(); ++r) {
+                const ArenaRegion &g = p.regions[r];
+                if (g.level != l || g.release == l) continue;
+                for (size_t c = 0; c < gone[r].size(); ++c) {
+                    const int64_t a0 = g.fo0 + (int64_t)c * LEAN_CHUNK, a1 = std::min(g.fo1, a0 + LEAN_CHUNK);
+                    for (int32_t q = p.lvl_ptr[l]; q < p.lvl_ptr[l + 1]; ++q) {
+                        const int32_t s = p.lvl_fronts[q];
+                        if (p.sn_fo[s] <= a0 && a1 <= p.sn_fo[s] + (int64_t)p.sn_nc[s] * p.sn_f[s]) {
+                            p.lean_prefix.push_back({(int32_t)r, (int32_t)c});
+                            break;
+                        }
+                    }
+                }
+            }
+            p.lean_prefix_ptr[l + 1] = (int64_t)p.lean_prefix.size();
+        }
+        int64_t mapped = 0, peak = 0;
+        for (int l = 0; l < p.nlevels; ++l) {
+            for (const ArenaRegion &g : p.regions)
+                if (g.level == l)
+                    for (int64_t a0 = g.fo0; a0 < g.fo1; a0 += LEAN_CHUNK) mapped += chunk_sz(a0, g.fo1);
+            peak = std::max(peak, mapped);  // the assembly of level l
+            for (size_t r = 0; r < p.regions.size(); ++r)
+                if (p.regions[r].level < l && p.regions[r].release == l) release_region(r, mapped);
+            peak = std::max(peak, mapped);  // its panels and solve-factor build
+            for (int64_t i = p.lean_prefix_ptr[l]; i < p.lean_prefix_ptr[l + 1]; ++i) {
+                const int32_t r = p.lean_prefix[i].first, c = p.lean_prefix[i].second;
+                if (!gone[r][c]) {
+                    gone[r][c] = 1;
+                    mapped -= chunk_sz(p.regions[r].fo0 + (int64_t)c * LEAN_CHUNK, p.regions[r].fo1);
+                }
+            }
+            for (size_t r = 0; r < p.regions.size(); ++r)
+                if (p.regions[r].level == l && p.regions[r].release == l) release_region(r, mapped);
+        }
+        p.lean_peak_elems = peak;
+    }
     p.zwork_elems = p.sn_zo[ns];
     p.max_front = 0;
     p.nnz_l = 0;

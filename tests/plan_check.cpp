@@ -205,7 +205,37 @@ int main(int argc, char **argv) {
         for (int s = 0; s < p.ns; ++s)
             if (bc[s] != p.df_btotal[s] || bgc[s] != p.df_gchunks[s]) return bad("backward totals", s, bc[s]);
     }
-    std::printf("ok L=%d nup=%d n=%ld supernodes=%d levels=%d nnz_l=%ld solve_panels=%zu\n", L, nup, (long)n, p.ns,
-                p.nlevels, (long)p.nnz_l, p.sdescs.size());
+    // fronts arena: aligned, disjoint regions ordered by (level, release); every front inside the
+    // region of its level and its parent's level; the lean peak does not exceed the whole arena
+    {
+        std::map<std::pair<int, int>, int> reg;
+        for (size_t i = 0; i < p.regions.size(); ++i) {
+            const ArenaRegion &r = p.regions[i];
+            if (r.fo0 % ARENA_ALIGN) return bad("region alignment", (long)i);
+            if (r.fo1 < r.fo0 || r.fo1 > p.arena_elems) return bad("region bounds", (long)i);
+            if (i && (p.regions[i - 1].fo1 > r.fo0)) return bad("regions overlap", (long)i);
+            if (i && std::make_pair(p.regions[i - 1].level, p.regions[i - 1].release) >= std::make_pair(r.level, r.release))
+                return bad("region order", (long)i);
+            if (r.release < r.level || r.release >= p.nlevels) return bad("release level", (long)i);
+            reg[{r.level, r.release}] = (int)i;
+        }
+        std::vector<std::pair<int64_t, int64_t>> iv;
+        for (int32_t s = 0; s < p.ns; ++s) {
+            const int l = p.sn_level[s], rl = p.sn_parent[s] < 0 ? l : p.sn_level[p.sn_parent[s]];
+            auto it = reg.find({l, rl});
+            if (it == reg.end()) return bad("front without region", s);
+            const ArenaRegion &r = p.regions[it->second];
+            const int64_t f = p.sn_f[s];
+            if (p.sn_fo[s] < r.fo0 || p.sn_fo[s] + f * f > r.fo1) return bad("front outside its region", s);
+            iv.push_back({p.sn_fo[s], p.sn_fo[s] + f * f});
+        }
+        std::sort(iv.begin(), iv.end());
+        for (size_t i = 1; i < iv.size(); ++i)
+            if (iv[i].first < iv[i - 1].second) return bad("fronts overlap", (long)i);
+    }
+    if (p.lean_peak_elems <= 0 || p.lean_peak_elems > p.arena_elems) return bad("lean peak", p.lean_peak_elems);
+    std::printf("ok L=%d nup=%d n=%ld supernodes=%d levels=%d nnz_l=%ld solve_panels=%zu arena=%ld lean_peak=%ld\n",
+                L, nup, (long)n, p.ns, p.nlevels, (long)p.nnz_l, p.sdescs.size(), (long)p.arena_elems,
+                (long)p.lean_peak_elems);
     return 0;
 }
