@@ -17,7 +17,7 @@ JSON line goes to stdout; the per-job records and the full profile go to `--deta
     python bench.py [--gpus N] [--steps K] [--warmup W] [--batch B] [--slots S] [--impl reference]
     python bench.py --case {factor,solve} [--L L] [--reps R] [--precision fp32|fp64]   (profiler cases)
     python bench.py --case observables [--L L] [--reps R]   (the eigenvector observables on nev = 50 vectors)
-    python bench.py --workload {l16batch,serve,large,odd,l22}   (the other configurations)
+    python bench.py --workload {l16batch,serve,large,odd,l22,campaign}   (the other configurations)
 """
 from __future__ import annotations
 
@@ -382,14 +382,46 @@ def run_l22(args):
         torch.cuda.synchronize()
         free0 = torch.cuda.mem_get_info()[0]
         t0 = time.perf_counter()
-        res = g.solve_near(sec, 0.5, NEV, allow_partial=True)
+        try:
+            res = g.solve_near(sec, 0.5, NEV, allow_partial=True)
+        except g.MblError as e:
+            out["jobs"].append({"seed": seed, "error": str(e), "s": time.perf_counter() - t0})
+            sec.close()
+            continue
         dt = time.perf_counter() - t0
         lo, hi = g.extremal_bounds(sec)
         hn = max(abs(lo), abs(hi))
         sec.close()
         out["jobs"].append({"seed": seed, "s": dt, "nconv": res.nconv, "max_resid_over_H": float(res.resid.max() / hn),
                             "sigma": res.sigma, "stats": res.stats, "free_gb_before": free0 / 1e9})
-    out["eigenpairs_per_s"] = sum(j["nconv"] for j in out["jobs"]) / sum(j["s"] for j in out["jobs"])
+    out["eigenpairs_per_s"] = sum(j.get("nconv", 0) for j in out["jobs"]) / sum(j["s"] for j in out["jobs"])
+    print(json.dumps(out))
+    ctx.close()
+    return 0
+
+
+def run_campaign_workload(args):
+    """Disorder-averaging campaign: L in {12, 14, 16}, h in {1, 2, 2.5, 3, 3.5, 4, 4.5, 5, 6}, `--seeds`
+    realizations each, eps = 0.5, nev = 20, through the server; the gap ratio binned per realization,
+    mean and standard error per (L, h), the collapse g[(h - h_c) L^(1/nu)] (cubic, w = 0.8) and a
+    bootstrap of it, and the weak / strong disorder means against the GOE / Poisson values."""
+    import paper_1411_0660_gb300 as g
+    from paper_1411_0660_gb300 import campaign as cp
+
+    ctx = g.Context(0)
+    Ls, hs = [12, 14, 16], [1.0, 2.0, 2.5, 3.0, 3.5, 4.0, 4.5, 5.0, 6.0]
+    data = cp.run_campaign(ctx, Ls, hs, range(args.seeds), eps=0.5, nev=20, observable="r", slots=args.slots)
+    L, h, Q, dQ = cp.points(data)
+    table = {f"L{int(a)}_h{b}": [round(q, 4), round(e, 4)] for a, b, q, e in zip(L, h, Q, dQ)}
+    fit = cp.collapse_fit(L, h, Q, dQ, w=0.8, L_min=12, hc_range=(2.0, 5.5), nu_range=(0.3, 2.5))
+    boot = cp.bootstrap_fit(data, samples=40, seed=1, w=0.8, L_min=12, hc_range=(2.0, 5.5), nu_range=(0.3, 2.5))
+    out = {"workload": "campaign", "observable": "r", "eps": 0.5, "nev": 20, "seeds": args.seeds,
+           "jobs": data["jobs"], "converged": data["converged"], "requested": data["requested"],
+           "seconds": data["seconds"], "eigenpairs_per_s": data["converged"] / data["seconds"],
+           "r_mean_stderr": table, "collapse": {"hc": fit["hc"], "nu": fit["nu"], "chi2_per_dof": fit["chi2_per_dof"],
+                                                "points": fit["points"], "hc_std": boot["hc_std"],
+                                                "nu_std": boot["nu_std"], "bootstrap_fits": boot["fits"]},
+           "paper": {"r_goe": 0.5307, "r_poisson": 2 * math.log(2) - 1, "hc_eps05": 3.72, "nu_eps05": 0.91}}
     print(json.dumps(out))
     ctx.close()
     return 0
@@ -523,7 +555,8 @@ def main():
     ap.add_argument("--case", choices=["factor", "solve", "observables"], default=None,
                     help="run one factorization (and --reps solves) instead of the benchmark")
     ap.add_argument("--L", type=int, default=18)
-    ap.add_argument("--workload", choices=["l18", "l16batch", "serve", "large", "odd", "l22"], default="l18",
+    ap.add_argument("--workload", choices=["l18", "l16batch", "serve", "large", "odd", "l22", "campaign"],
+                    default="l18",
                     help="l18: the benchmark line; l16batch / serve: the batched and serving configurations")
     ap.add_argument("--seeds", type=int, default=8, help="l16batch: seeds per (h, eps)")
     ap.add_argument("--requests", type=int, default=40, help="serve: number of requests")
@@ -559,6 +592,8 @@ def main():
         return run_case(args)
     if args.workload == "l22":
         return run_l22(args)
+    if args.workload == "campaign":
+        return run_campaign_workload(args)
     if args.workload != "l18":
         return run_workload(args)
     if args.impl == "reference":
