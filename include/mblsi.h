@@ -84,6 +84,8 @@ typedef struct mbl_opts {
                           /*    are backed by device memory from their level's assembly */
                           /*    until their parents' assembly; a front's factor columns  */
                           /*    are released once copied to the solve factor.            */
+    double pivot_tiny;    /* static pivoting: a pivot below pivot_tiny ||H|| is replaced by  */
+                          /*    +-pivot_tiny ||H||; 0 = 1e-7 (FP32 fronts), 1e-12 (FP64)  [0]    */
 } mbl_opts;
 
 typedef struct mbl_factor_stats {
@@ -100,6 +102,13 @@ typedef struct mbl_factor_stats {
     double ms_factor;       /* device time of the numeric factorization */
     double max_abs_l;       /* largest |L_ij| (element growth of the pivoting) */
     double min_abs_d;       /* smallest |D_jj| */
+    /* Autotuned tile shape of the FP32 fronts' trailing update by size class c of the panel step's
+     * largest trailing block (64 2^c <= m2 < 64 2^(c+1); class 0 also smaller, class 7 also larger),
+     * measured once per sector shape and tensor-core mode on a synthetic front of the class:
+     * 1 = tcgen05 128 x 128 tiles, 0 = CUDA-core 64 x 64 tiles, -1 = not tuned (FP64 fronts or CUDA
+     * cores requested); the two timings in microseconds (0 where the class has no panel step). */
+    int tune_choice[8];
+    float tune_us_tc[8], tune_us_cc[8];
 } mbl_factor_stats;
 
 typedef struct mbl_solve_stats {
@@ -111,6 +120,13 @@ typedef struct mbl_solve_stats {
     double max_resid;       /* max ||H y - theta y|| / ||H|| of the returned pairs */
     double ms_total;        /* wall time of solve_near */
     double ms_factor;       /* of which numeric factorization */
+    int shift_moves;        /* times the factorization shift moved off an eigenvalue (target on one) */
+    int refine_escalations; /* stalls answered with a longer FGMRES instead of FP64 fronts (which would
+                               not fit in device memory) */
+    int factor_reused;      /* serving: the factorization came from the server's cache of live factors */
+    double static_pivot;    /* static pivoting threshold used, relative to ||H|| (0: the precision's
+                               default); sqrt(eps_FP32) for FP32 fronts where an FP64 refactorization
+                               could not fit in device memory */
 } mbl_solve_stats;
 
 void mbl_opts_default(mbl_opts *opts);
@@ -346,6 +362,7 @@ typedef struct mbl_result {
     double d_start_ms, d_end_ms;
     size_t reserved_bytes;
     double *evals, *resid, *r, *s1p, *se, *evecs;
+    int factor_reused;  /* the job's factorization came from the server's cache of live factors */
 } mbl_result;
 
 typedef struct mbl_server_stats {
@@ -357,7 +374,18 @@ typedef struct mbl_server_stats {
     double batch_ms;         /* their device time (CUDA events on the batcher's stream) */
     double batch_bytes;      /* their algorithmic bytes: per block solve the factor read by both
                                 sweeps plus the right-hand sides, 2 (nnz_L + n) w + 16 n p */
+    int64_t cache_hits;      /* requests served with a cached live factorization */
+    size_t cache_bytes;      /* device bytes the cache holds now */
 } mbl_server_stats;
+
+/* Residency of live factorizations (set before mbl_server_start; default fraction 0.25, 0 = off).
+ * A finished job's sector and factorization stay on the device, up to `fraction` of the server
+ * budget, most recently used kept first; a later request with the same sector shape, fields (or
+ * (h, seed)), eps and precision takes them and skips the sector build, the extremal bounds and the
+ * factorization.  Cached bytes count against the budget: admission evicts the least recently used
+ * entries before it makes a request wait.  Not in the paper: a serving pattern for repeated targets.
+ * MBL_ERR_INVALID while a server runs or for fraction outside [0, 0.9]. */
+int mbl_server_cache(mbl_ctx *ctx, double fraction);
 
 /* Continuous batching of the workers' triangular solves (set before mbl_server_start; defaults
  * max_jobs = 16, window_us = 300).  Jobs of one sector size share a symbolic plan, so their block

@@ -194,7 +194,11 @@ class Factorization:
     def stats(self) -> dict:
         s = FactorStats()
         _check(_lib().mbl_factor_stats_get(self.handle, ctypes.byref(s)), self.sec.ctx.handle)
-        return {f: getattr(s, f) for f, _ in FactorStats._fields_}
+        out = {}
+        for f, _ in FactorStats._fields_:
+            v = getattr(s, f)
+            out[f] = list(v) if isinstance(v, ctypes.Array) else v
+        return out
 
     def set_trace(self, on: bool = True):
         """Record per-launch start/end device clocks of later solves (diagnostic)."""
@@ -389,6 +393,7 @@ class ServedResult:
     d_start_ms: float
     d_end_ms: float
     reserved_bytes: int
+    factor_reused: int = 0
 
 
 def _dim_of(L: int, nup: int = 0) -> int:
@@ -400,12 +405,14 @@ class Server:
     """Worker threads of a context serving (L, h, seed, eps, nev) requests as memory allows."""
 
     def __init__(self, ctx: Context, slots: int = 4, hbm_budget_bytes: int = 0, batch_jobs: int = 16,
-                 batch_window_us: float = 300.0):
+                 batch_window_us: float = 300.0, cache_fraction: float = 0.25):
         """`batch_jobs` > 1 batches the workers' triangular solves of one sector size into shared
-        launches (at most that many jobs per launch, waiting up to `batch_window_us`); 1 turns it off."""
+        launches (at most that many jobs per launch, waiting up to `batch_window_us`); 1 turns it off.
+        `cache_fraction` of the budget keeps finished jobs' live factorizations for repeated requests."""
         self.ctx = ctx
         self._req = {}
         _check(_lib().mbl_server_batching(ctx.handle, batch_jobs, float(batch_window_us)), ctx.handle)
+        _check(_lib().mbl_server_cache(ctx.handle, float(cache_fraction)), ctx.handle)
         _check(_lib().mbl_server_start(ctx.handle, slots, hbm_budget_bytes), ctx.handle)
 
     def submit(self, L: int, h: float, seed: int, eps: float, nev: int, precision: int = MBL_PREC_FP32,
@@ -444,7 +451,7 @@ class Server:
             _check(rc, self.ctx.handle)
         return ServedResult(rc, out.nconv, out.L, out.dim, out.sigma, ev, rs, r[: max(nev - 2, 0)], out.r_mean, s1,
                             se, V, out.t_submit_ms, out.t_admit_ms, out.t_end_ms, out.d_start_ms, out.d_end_ms,
-                            out.reserved_bytes)
+                            out.reserved_bytes, out.factor_reused)
 
     def poll(self, ticket: int):
         """The result if finished, else None (non-blocking)."""

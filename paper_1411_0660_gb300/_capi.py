@@ -27,14 +27,15 @@ class Opts(ctypes.Structure):
                 ("tol", c_double), ("target_tol", c_double), ("refine_tol", c_double), ("max_refine", c_int),
                 ("start_seed", c_uint64), ("tensor_cores", c_int), ("refine_mode", c_int),
                 ("gmres_restart", c_int), ("solve_dataflow", c_int), ("deflate", c_int),
-                ("wait_limit_s", c_double), ("arena_mode", c_int)]
+                ("wait_limit_s", c_double), ("arena_mode", c_int), ("pivot_tiny", c_double)]
 
 
 class FactorStats(ctypes.Structure):
     _fields_ = [("n", c_int64), ("nnz_l", c_int64), ("n_supernodes", c_int64), ("max_front", c_int64),
                 ("tree_levels", c_int64), ("perturbed", c_int64), ("negative", c_int64), ("flops", c_double),
                 ("factor_bytes", c_double), ("front_bytes", c_double), ("ms_factor", c_double),
-                ("max_abs_l", c_double), ("min_abs_d", c_double)]
+                ("max_abs_l", c_double), ("min_abs_d", c_double), ("tune_choice", c_int * 8),
+                ("tune_us_tc", ctypes.c_float * 8), ("tune_us_cc", ctypes.c_float * 8)]
 
 
 class PlanStats(ctypes.Structure):
@@ -49,7 +50,9 @@ class PlanStats(ctypes.Structure):
 
 class SolveStats(ctypes.Structure):
     _fields_ = [("restarts", c_int), ("op_applies", c_int), ("solves", c_int), ("fp64_fallback", c_int),
-                ("krylov_dim", c_int), ("max_resid", c_double), ("ms_total", c_double), ("ms_factor", c_double)]
+                ("krylov_dim", c_int), ("max_resid", c_double), ("ms_total", c_double), ("ms_factor", c_double),
+                ("shift_moves", c_int), ("refine_escalations", c_int), ("factor_reused", c_int),
+                ("static_pivot", c_double)]
 
 
 class Request(ctypes.Structure):
@@ -62,14 +65,16 @@ class Result(ctypes.Structure):
                 ("sigma", c_double), ("r_mean", c_double), ("t_submit_ms", c_double), ("t_admit_ms", c_double),
                 ("t_end_ms", c_double), ("d_start_ms", c_double), ("d_end_ms", c_double),
                 ("reserved_bytes", c_size_t), ("evals", c_void_p), ("resid", c_void_p),
-                ("r", c_void_p), ("s1p", c_void_p), ("se", c_void_p), ("evecs", c_void_p)]
+                ("r", c_void_p), ("s1p", c_void_p), ("se", c_void_p), ("evecs", c_void_p),
+                ("factor_reused", c_int)]
 
 
 class ServerStats(ctypes.Structure):
     _fields_ = [("submitted", c_int64), ("completed", c_int64), ("failed", c_int64), ("running", c_int),
                 ("queued", c_int), ("slots", c_int), ("budget_bytes", c_size_t), ("reserved_bytes", c_size_t),
                 ("peak_reserved_bytes", c_size_t), ("solve_batches", c_int64), ("batched_solves", c_int64),
-                ("batch_ms", c_double), ("batch_bytes", c_double)]
+                ("batch_ms", c_double), ("batch_bytes", c_double), ("cache_hits", c_int64),
+                ("cache_bytes", c_size_t)]
 
 
 # (name, restype, argtypes); every entry point of include/mblsi.h
@@ -128,6 +133,7 @@ SIGNATURES = [
     ("mbl_entanglement_noalloc_dev", c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p]),
     ("mbl_server_start", c_int, [c_void_p, c_int, c_size_t]),
     ("mbl_server_batching", c_int, [c_void_p, c_int, c_double]),
+    ("mbl_server_cache", c_int, [c_void_p, c_double]),
     ("mbl_factor_solve_batch_dev", c_int, [c_void_p, c_int, c_void_p, c_void_p, c_int, c_void_p]),
     ("mbl_submit", c_int, [c_void_p, P(Request), P(c_uint64)]),
     ("mbl_poll", c_int, [c_void_p, c_uint64, P(Result)]),

@@ -20,6 +20,7 @@
 
 #include "factor.h"
 #include "solve_tile.cuh"
+#include "tc_pieces.cuh"
 
 namespace mbl {
 
@@ -386,7 +387,8 @@ template <class T>
 __global__ void __launch_bounds__(PANEL_THREADS) k_panel_trsm(const PanelDesc *descs, int nd, const int64_t *fo,
                                                    const int32_t *fsz, const int32_t *sn_start, T *arena,
                                                    const T *Dg, const int32_t *piv, T *wscr,
-                                                   unsigned long long *stats) {
+                                                   unsigned long long *stats, void *pieces, int64_t prow,
+                                                   int pmode) {
     extern __shared__ __align__(16) unsigned char smraw[];
     T(*Lb)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(smraw);                      // L11
     T(*As)[NB + 1] = reinterpret_cast<T(*)[NB + 1]>(smraw + sizeof(T) * NB * (NB + 1));
@@ -432,6 +434,26 @@ __global__ void __launch_bounds__(PANEL_THREADS) k_panel_trsm(const PanelDesc *d
         F[(int64_t)(k0 + t) * f + r0 + i] = l;
         W[(int64_t)(r0 - k0 - w + i) + (int64_t)t * m2] = x;
         lmax = fmaxf(lmax, (float)tabs(l));
+    }
+    if (sizeof(T) == 4 && pmode) {
+        // tensor-core operand pieces of this block's rows of L21 and W21 (pieces 0/1 and 2/3), row-major
+        // with NB per row, zero past the panel width; rows start at the descriptor's woff / NB
+        const int64_t rb = d.woff / NB + (r0 - k0 - w);
+        for (int idx = tid; idx < nr * NB; idx += blockDim.x) {
+            const int i = idx / NB, t = idx - i * NB;
+            const float xv = t < w ? (float)As[i][t] : 0.f;
+            const float lv = t < w ? (float)(As[i][t] * Dinv[t]) : 0.f;
+            const int64_t e = (rb + i) * NB + t;
+            if (pmode == 1) {
+                uint32_t *P = static_cast<uint32_t *>(pieces);
+                split_tf32(lv, P[e], P[prow * NB + e]);
+                split_tf32(xv, P[2 * prow * NB + e], P[3 * prow * NB + e]);
+            } else {
+                uint16_t *P = static_cast<uint16_t *>(pieces);
+                split_bf16(lv, P[e], P[prow * NB + e]);
+                split_bf16(xv, P[2 * prow * NB + e], P[3 * prow * NB + e]);
+            }
+        }
     }
     for (int o = 16; o > 0; o >>= 1) lmax = fmaxf(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
     if ((tid & 31) == 0) atomicMax(reinterpret_cast<unsigned int *>(stats), __float_as_uint(lmax));
@@ -1236,7 +1258,10 @@ static void factor_impl(Factorization &fz, cudaStream_t st) {
                     k_panel_trsm<T><<<(unsigned)stp.n2, PANEL_THREADS, trsm_smem<T>(), st>>>(dd, stp.nd, p.d_sn_fo.data(),
                                                                                  p.d_sn_f.data(), p.d_sn_start.data(), arena,
                                                                                  Dg, fz.piv.data(), wscr,
-                                                                                 fz.counters.data() + 3);
+                                                                                 fz.counters.data() + 3,
+                                                                                 fz.tma ? fz.pieces.m.p : nullptr,
+                                                                                 fz.prow,
+                                                                                 fz.tma && sizeof(T) == 4 ? fz.tc_mode : 0);
                     MBL_LAUNCH_CHECK();
                 }
             }
@@ -1244,10 +1269,19 @@ static void factor_impl(Factorization &fz, cudaStream_t st) {
                 double fl = 0.0;  // algorithmic flops: lower triangle of the trailing block, 2 per entry per k
                 for (int q = stp.d0; q < stp.d0 + stp.nd; ++q)
                     fl += (double)p.descs[q].m2 * (p.descs[q].m2 + 1) * p.descs[q].w;
-                if (sizeof(T) == 4 && fz.tc_mode != 0) {
+                // the autotuned tile shape of this step's size class (tensor cores unless the tuning found the
+                // CUDA-core tiles faster for it)
+                const bool tc = sizeof(T) == 4 && fz.tc_mode != 0 &&
+                                (!p.tuned[fz.tc_mode] || p.tune_tc[fz.tc_mode][p.step_class[si]]);
+                if (tc) {
                     ProfScope ps(fz.ctx, "schur_tc", fl, st);
-                    launch_schur_tc(stp, dd, p, reinterpret_cast<float *>(arena), reinterpret_cast<const float *>(wscr),
-                                    fz.counters.data() + 2, st, fz.tc_mode == 2);
+                    if (fz.tma)
+                        launch_schur_tma(stp, dd, p.d_sn_fo.data(), p.d_sn_f.data(), reinterpret_cast<float *>(arena),
+                                         fz.tmap, fz.counters.data() + 2, st, fz.tc_mode == 2);
+                    else
+                        launch_schur_tc(stp, dd, p, reinterpret_cast<float *>(arena),
+                                        reinterpret_cast<const float *>(wscr), fz.counters.data() + 2, st,
+                                        fz.tc_mode == 2);
                 } else {
                     ProfScope ps(fz.ctx, sizeof(T) == 8 ? "schur_fp64" : "schur_fp32", fl, st);
                     k_panel_update<T><<<(unsigned)stp.n3, 256, 0, st>>>(dd, stp.nd, p.d_sn_fo.data(), p.d_sn_f.data(),
@@ -1281,6 +1315,93 @@ static void factor_impl(Factorization &fz, cudaStream_t st) {
             MBL_LAUNCH_CHECK();
         }
     }
+}
+
+__global__ void k_fill_hash(float *x, int64_t n, uint32_t seed) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t h = (uint32_t)i * 2654435761u ^ seed;
+    h ^= h >> 15;
+    h *= 2246822519u;
+    h ^= h >> 13;
+    x[i] = (float)(h & 0xFFFFFF) * (1.0f / 16777216.0f) - 0.5f;
+}
+
+void tune_schur(Factorization &fz, cudaStream_t st) {
+    Plan &p = *fz.plan;
+    const int mode = fz.tc_mode;
+    if (fz.prec != MBL_PREC_FP32 || mode < 1 || mode > 2 || !fz.tma) return;
+    std::lock_guard<std::mutex> lk(p.tune_mu);
+    if (p.tuned[mode]) return;
+    bool present[TUNE_CLASSES] = {};
+    for (int32_t c : p.step_class) present[c] = true;
+    unsigned long long *err = fz.counters.data() + 2;
+    for (int c = 0; c < TUNE_CLASSES; ++c) {
+        p.tune_tc[mode][c] = 1;
+        p.tune_us[mode][c][0] = p.tune_us[mode][c][1] = 0.f;
+        if (!present[c]) continue;
+        // a synthetic front whose one 64-column panel leaves a trailing block in the middle of the class
+        const int m2 = (int)(64.0 * (double)(1 << c) * 1.41), f = m2 + NB;
+        DVec<float> F, W;
+        DVec<char> pc;
+        DVec<PanelDesc> dd;
+        DVec<int64_t> fo;
+        DVec<int32_t> fsz;
+        F.alloc(fz.ctx, (size_t)f * f);
+        W.alloc(fz.ctx, (size_t)m2 * NB);
+        pc.alloc(fz.ctx, (size_t)4 * m2 * NB * (mode == 2 ? 2 : 4));
+        dd.alloc(fz.ctx, 1);
+        fo.alloc(fz.ctx, 1);
+        fsz.alloc(fz.ctx, 1);
+        k_fill_hash<<<(unsigned)(((int64_t)f * f + 255) / 256), 256, 0, st>>>(F.data(), (int64_t)f * f, 1u + c);
+        MBL_LAUNCH_CHECK();
+        k_fill_hash<<<(unsigned)(((int64_t)m2 * NB + 255) / 256), 256, 0, st>>>(W.data(), (int64_t)m2 * NB, 7u + c);
+        MBL_LAUNCH_CHECK();
+        MBL_CUDA(cudaMemsetAsync(pc.data(), 0, pc.size(), st));
+        const PanelDesc d{0, 0, NB, m2, 0, 0, 0, 0};
+        const int64_t z = 0;
+        MBL_CUDA(cudaMemcpyAsync(dd.data(), &d, sizeof(d), cudaMemcpyHostToDevice, st));
+        MBL_CUDA(cudaMemcpyAsync(fo.data(), &z, sizeof(z), cudaMemcpyHostToDevice, st));
+        MBL_CUDA(cudaMemcpyAsync(fsz.data(), &f, sizeof(int), cudaMemcpyHostToDevice, st));
+        alignas(64) unsigned char map[128];
+        if (!encode_pieces_map(map, pc.data(), m2, mode == 2)) continue;
+        PanelStep stp{};
+        stp.nd = 1;
+        const int64_t T64 = (m2 + TB - 1) / TB, T128 = (m2 + 127) / 128;
+        stp.n3 = T64 * (T64 + 1) / 2;
+        stp.n3t = T128 * (T128 + 1) / 2;
+        cudaEvent_t e[3];
+        for (auto &x : e) MBL_CUDA(cudaEventCreate(&x));
+        float us[2] = {0.f, 0.f};
+        for (int v = 0; v < 2; ++v) {
+            auto run = [&] {
+                if (v == 0)
+                    launch_schur_tma(stp, dd.data(), fo.data(), fsz.data(), F.data(), map, err, st, mode == 2);
+                else {
+                    k_panel_update<float><<<(unsigned)stp.n3, 256, 0, st>>>(dd.data(), 1, fo.data(), fsz.data(),
+                                                                            F.data(), W.data());
+                    MBL_LAUNCH_CHECK();
+                }
+            };
+            run();  // warm-up (and the kernel load)
+            MBL_CUDA(cudaEventRecord(e[0], st));
+            for (int r = 0; r < 3; ++r) run();
+            MBL_CUDA(cudaEventRecord(e[1], st));
+            MBL_CUDA(cudaEventSynchronize(e[1]));
+            float ms = 0.f;
+            MBL_CUDA(cudaEventElapsedTime(&ms, e[0], e[1]));
+            us[v] = 1000.f * ms / 3.f;
+        }
+        for (auto &x : e) cudaEventDestroy(x);
+        p.tune_us[mode][c][0] = us[0];
+        p.tune_us[mode][c][1] = us[1];
+        p.tune_tc[mode][c] = us[0] <= us[1] ? 1 : 0;
+    }
+    // the synthetic updates counted no real time-outs: clear the counter the factorization reads
+    MBL_CUDA(cudaMemsetAsync(err, 0, sizeof(unsigned long long), st));
+    MBL_CUDA(cudaStreamSynchronize(st));
+    if (fz.lean) trim_device_pool(fz.ctx->device);  // the synthetic fronts' memory back to the device
+    p.tuned[mode] = true;
 }
 
 void numeric_factor(Factorization &fz, cudaStream_t st) {
@@ -1542,6 +1663,10 @@ void Factorization::allocate(bool lean_arena) {
     size_t es = elem_size();
     lean_used = lean_arena;
     if (lean_arena) {
+        // the lean arena's chunks come from the device, not the stream-ordered pool: hand the pool's
+        // cached free blocks back first
+        MBL_CUDA(cudaStreamSynchronize(ctx->stream));
+        trim_device_pool(ctx->device);
         lean = std::make_unique<LeanArena>();
         lean->reserve(ctx, pl, es);
     } else {
@@ -1556,6 +1681,15 @@ void Factorization::allocate(bool lean_arena) {
     gpk.alloc(ctx, (size_t)std::max<int64_t>(pl.sg_elems, 1) * es);
     scnt.alloc(ctx, std::max<size_t>(pl.sdescs.size() * SUBS, 1));
     dfcnt.alloc(ctx, (size_t)4 * pl.ns + 2);
+    tma = false;
+    if (prec == MBL_PREC_FP32 && tc_mode != 0 && pl.wscratch_elems > 0) {
+        // operand pieces of the TMA-fed Schur update: 4 arrays of prow rows x NB pieces
+        prow = pl.wscratch_elems / NB;
+        const size_t eb = tc_mode == 2 ? 2 : 4;
+        pieces.alloc(ctx, (size_t)4 * prow * NB * eb);
+        tma = encode_pieces_map(tmap, pieces.m.p, prow, tc_mode == 2);
+        if (!tma) pieces.release();
+    }
     MBL_CUDA(cudaMemset(scnt.data(), 0, std::max<size_t>(pl.sdescs.size() * SUBS, 1) * sizeof(unsigned int)));
 }
 
@@ -1567,6 +1701,7 @@ void reset_solve_counters(Factorization &fz, cudaStream_t st) {
 
 void Factorization::release_scratch() {
     wscr.release();
+    pieces.release();
     cmax.release();
     M.release();      // folded into G = [M; L21 M]
     arena.release();  // the solves read only the packed G and D
@@ -1578,6 +1713,15 @@ void Factorization::release_scratch() {
 }
 
 Factorization::Factorization() = default;
+
+size_t Factorization::held_bytes() const {
+    size_t b = 0;
+    for (const DevMem *m : {&arena.m, &D.m, &wscr.m, &cmax.m, &M.m, &zwork.m, &zsolved.m, &ywork.m, &yfw.m, &pwork.m,
+                            &gpk.m, &piv.m, &scnt.m, &dfcnt.m, &counters.m, &trace.m, &dev_b.m, &dev_x.m, &dbufs.m,
+                            &pieces.m})
+        b += m->bytes;
+    return b;
+}
 
 Factorization::~Factorization() {
     if (graph_exec) cudaGraphExecDestroy(graph_exec);

@@ -24,6 +24,7 @@ struct LeanArena;  // physical backing of the memory-lean fronts arena (factor.c
 // only while their fronts are live).  Automatic: lean when the whole arena would exceed 8 GiB.
 constexpr int ARENA_AUTO = 0, ARENA_LEAN = 1, ARENA_FULL = 2;
 bool arena_is_lean(const Plan &p, int prec, int mode);
+void trim_device_pool(int device);  // release the stream-ordered pool's cached free blocks (capi.cu)
 // Device bytes of the fronts arena at its peak in that mode.
 double arena_peak_bytes(const Plan &p, int prec, int mode);
 
@@ -52,6 +53,10 @@ struct Factorization {
     int graph_p = 0;
     long long graph_nodes = 0;
     int tc_mode = 1;  // FP32 fronts' Schur updates: 0 CUDA cores, 1 tcgen05 3xTF32, 2 tcgen05 3xBF16
+    DVec<char> pieces;                    // tensor-core operand pieces of the step's L21 and W21
+    int64_t prow = 0;                     // rows of each piece array
+    alignas(64) unsigned char tmap[128];  // tensor map over the pieces (TMA-fed Schur update)
+    bool tma = false;                     // the pieces and their tensor map are ready
     // launch trace of the level-by-level solve (opt-in; recaptures the solve graph when switched)
     bool trace_on = false;
     DVec<LaunchTrace> trace;
@@ -63,6 +68,7 @@ struct Factorization {
 
     size_t elem_size() const { return prec == MBL_PREC_FP64 ? sizeof(double) : sizeof(float); }
     Factorization();  // out of line: LeanArena is complete only in factor.cu
+    size_t held_bytes() const;  // device bytes it holds now (all its buffers)
     ~Factorization();
     void allocate(bool lean_arena = false);
     void release_scratch();
@@ -103,8 +109,18 @@ void batcher_stats(SolveBatcher *b, int64_t *batches, int64_t *solves, double *m
 template <class T>
 SolveBufs<T> solve_bufs(const Factorization &fz);
 
-// tcgen05 trailing update of one panel step (FP32 fronts); err counts bounded-wait time-outs.
+// tcgen05 trailing update of one panel step (FP32 fronts); err counts bounded-wait time-outs.  The
+// TMA-fed form reads the operand pieces the panel's trsm wrote (tensor map from encode_pieces_map over
+// 4 x prow x NB pieces); the other form splits the raw operands itself.
 size_t schur_tc_smem(bool bf16);
+bool encode_pieces_map(void *map, void *pieces, int64_t prow, bool bf16);
+void launch_schur_tma(const PanelStep &stp, const PanelDesc *d_descs, const int64_t *fo, const int32_t *fsz,
+                      float *arena, const void *map, unsigned long long *err, cudaStream_t st, bool bf16);
+// Autotuning of the FP32 fronts' trailing update (once per plan and tensor-core mode): for every size
+// class of trailing block that the plan's panel steps have, time one update of a synthetic front of
+// that class with tcgen05 128 x 128 tiles (TMA-fed) and with CUDA-core 64 x 64 tiles, and keep the
+// faster in the plan.
+void tune_schur(Factorization &fz, cudaStream_t st);
 void launch_schur_tc(const PanelStep &stp, const PanelDesc *d_descs, const Plan &p, float *arena, const float *wscr,
                      unsigned long long *err, cudaStream_t st, bool bf16);
 
@@ -127,7 +143,8 @@ std::shared_ptr<Plan> get_plan(mbl_sector *sec);
 // Create, allocate and run a factorization (synchronous; fills stats).
 std::unique_ptr<Factorization> make_factorization(mbl_sector *sec, double sigma, int prec, double hnorm,
                                                   int tc_mode = 1, bool dataflow = false,
-                                                  uint64_t wait_ns = 1000000000ull, int arena_mode = ARENA_AUTO);
+                                                  uint64_t wait_ns = 1000000000ull, int arena_mode = ARENA_AUTO,
+                                                  double pivot_tiny = 0.0);
 // Wait-limit option (seconds, 0 = the 1 s default) in nanoseconds.
 uint64_t wait_limit_ns(double seconds);
 // After a solve reported expired waits: clear the time-out count and the per-chunk arrival counters

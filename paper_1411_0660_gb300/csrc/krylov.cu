@@ -837,7 +837,7 @@ void RefinedSolve::apply_fgmres(const double *X, int ldx, double *Y, int p, cuda
         MBL_LAUNCH_CHECK();
     };
     double prev = INFINITY;
-    for (int outer = 0; outer < 4; ++outer) {
+    for (int outer = 0; outer < max_outer; ++outer) {
         std::vector<double> rn, lim;
         double worst = residual(X, ldx, Y, p, st, &rn, &lim);
         if (worst <= 1.0) return;
@@ -1190,8 +1190,41 @@ static std::vector<int> nearest_sorted(const std::vector<double> &th, double sig
     return idx;
 }
 
+// Whether an FP64 factorization of the plan could be held at all: its fronts arena at its peak, its
+// solve factor and panel scratch against the device's total memory (less a margin for the rest of the
+// job) and the context budget.
+static bool fp64_fits_plan(const Plan &p, int arena_mode, const Ctx *ctx) {
+    const double need = arena_peak_bytes(p, MBL_PREC_FP64, arena_mode) + 8.0 * (double)p.sg_elems +
+                        12.0 * (double)p.n + 8.0 * (double)(p.m_elems + p.wscratch_elems);
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return true;
+    }
+    if (ctx->budget && need > (double)ctx->budget) return false;
+    return need < 0.9 * (double)tot;
+}
+
+// Whether an FP64 refactorization fits in device memory once the FP32 factor fz is freed: the FP64
+// fronts arena at its peak, the FP64 solve factor and panel scratch against the free memory plus what
+// fz releases, and the context budget.
+static bool fp64_fits(const Factorization &fz, int arena_mode) {
+    const Plan &p = *fz.plan;
+    const double need = arena_peak_bytes(p, MBL_PREC_FP64, arena_mode) + 8.0 * (double)p.sg_elems +
+                        12.0 * (double)p.n + 8.0 * (double)(p.m_elems + p.wscratch_elems);
+    const double freed = 4.0 * (double)p.sg_elems + 8.0 * (double)p.n;
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return true;
+    }
+    if (fz.ctx->budget && (double)fz.ctx->in_use - freed + need > (double)fz.ctx->budget) return false;
+    return need < 0.95 * ((double)fr + freed);
+}
+
 void solve_near(mbl_sector *sec, double eps, int nev, const mbl_opts &o, double *d_evals, double *d_evecs,
-                double *d_resid, int *nconv, double *sigma_used, mbl_solve_stats *stats, cudaStream_t st) {
+                double *d_resid, int *nconv, double *sigma_used, mbl_solve_stats *stats, cudaStream_t st,
+                std::unique_ptr<Factorization> *keep) {
     auto t0 = std::chrono::steady_clock::now();
     Ctx *ctx = sec->ctx;
     int64_t n = sec->n;
@@ -1266,9 +1299,29 @@ void solve_near(mbl_sector *sec, double eps, int nev, const mbl_opts &o, double 
     if (std::fabs(sigma - emin) <= guard) sigma_f = emin - nudge;
     if (std::fabs(sigma - emax) <= guard) sigma_f = emax + nudge;
     auto tf0 = std::chrono::steady_clock::now();
-    std::unique_ptr<Factorization> fz =
-        make_factorization(sec, sigma_f, o.precision, hnorm, o.tensor_cores, o.solve_dataflow != 0,
-                           wait_limit_ns(o.wait_limit_s), o.arena_mode);
+    // Static pivoting threshold of FP32 fronts.  By default 1e-7 ||H||: few pivots are perturbed and the
+    // FP64 refactorization backs up a stalled refinement.  Where that refactorization could not fit in
+    // device memory (the largest sectors), the FP32 factor must stand on its own: use the static
+    // pivoting threshold sqrt(eps_FP32) ||H|| (perturbing more pivots bounds the element growth, and a
+    // stable factor of a slightly perturbed matrix is a far better FGMRES preconditioner than an
+    // unstable one; at L = 22 the growth falls from 5.5e5 to 4.4e3 and the refinement converges).
+    double tiny_rel = o.pivot_tiny;
+    if (o.precision == MBL_PREC_FP32 && tiny_rel == 0.0 && !fp64_fits_plan(*get_plan(sec), o.arena_mode, ctx))
+        tiny_rel = std::sqrt((double)FLT_EPSILON / 2.0);
+    S.static_pivot = tiny_rel;
+    std::unique_ptr<Factorization> fz;
+    if (keep && *keep && (*keep)->sec == sec && !(*keep)->trace_on &&
+        ((*keep)->prec == o.precision || (*keep)->prec == MBL_PREC_FP64) &&
+        (*keep)->tc_mode == o.tensor_cores && (*keep)->dataflow == (o.solve_dataflow != 0)) {
+        // a live factorization of this very request (serving residency): its shift is the one the
+        // earlier run settled on (moved off an eigenvalue, or FP64 after a refinement stall)
+        fz = std::move(*keep);
+        sigma_f = fz->sigma;
+        S.factor_reused = 1;
+    } else {
+        fz = make_factorization(sec, sigma_f, o.precision, hnorm, o.tensor_cores, o.solve_dataflow != 0,
+                                wait_limit_ns(o.wait_limit_s), o.arena_mode, tiny_rel);
+    }
     S.ms_factor = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tf0).count();
     RefinedSolve op{sec, fz.get(), hnorm + std::fabs(sigma_f), o.refine_tol, o.max_refine};
     op.gmres = o.refine_mode;
@@ -1309,6 +1362,14 @@ void solve_near(mbl_sector *sec, double eps, int nev, const mbl_opts &o, double 
         phase.enter(*fz, p);
         while (!ks.full()) {
             ks.expand(opfn, st);
+            if (op.stalled && fz->prec == MBL_PREC_FP32 && !fp64_fits(*fz, o.arena_mode)) {
+                // FP64 fronts would not fit beside what the job holds (the largest sectors): keep the FP32
+                // factor and give the refinement more room instead (longer and more FGMRES cycles)
+                op.stalled = false;
+                op.kmax = 64;
+                op.max_outer = 16;
+                S.refine_escalations += 1;
+            }
             if (op.stalled && fz->prec == MBL_PREC_FP32) {
                 phase.leave();
                 // refinement stalled near the shift: refactor with FP64 fronts.  The Krylov-Schur
@@ -1350,12 +1411,14 @@ void solve_near(mbl_sector *sec, double eps, int nev, const mbl_opts &o, double 
                 const double side = (sigma_f >= lam ? 1.0 : -1.0) * (nudges == 1 ? -1.0 : 1.0);
                 sigma_f = lam + side * (0.1 + 0.05 * nudges) * spacing;
                 ++nudges;
+                S.shift_moves = nudges;
                 const int prec_now = fz->prec;
                 op.fz = nullptr;
                 fz.reset();
                 auto tf1 = std::chrono::steady_clock::now();
                 fz = make_factorization(sec, sigma_f, prec_now, hnorm, o.tensor_cores, o.solve_dataflow != 0,
-                                        wait_limit_ns(o.wait_limit_s), o.arena_mode);
+                                        wait_limit_ns(o.wait_limit_s), o.arena_mode,
+                                        prec_now == MBL_PREC_FP32 ? tiny_rel : 0.0);
                 S.ms_factor += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tf1).count();
                 op.fz = fz.get();
                 op.anorm = hnorm + std::fabs(sigma_f);
@@ -1407,6 +1470,7 @@ void solve_near(mbl_sector *sec, double eps, int nev, const mbl_opts &o, double 
     MBL_CUDA(cudaMemcpyAsync(d_resid, rr.resid.data(), nev * sizeof(double), cudaMemcpyHostToDevice, st));
     MBL_CUDA(cudaStreamSynchronize(st));
     *nconv = nc;
+    if (keep) *keep = std::move(fz);
     S.restarts = restarts;
     S.op_applies = op.applies;
     S.solves = op.solves;

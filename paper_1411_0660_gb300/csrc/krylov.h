@@ -46,6 +46,7 @@ struct RefinedSolve {
     double last_rel = 0.0;
     int gmres = 1;     // 1: FGMRES refinement (factor as right preconditioner); 0: plain refinement
     int kmax = 24;     // FGMRES inner dimension
+    int max_outer = 4; // FGMRES restarts per application before a stall is declared
     DVec<double> R, part, norms, GV, GZ, GW, Gh, Gy, Gdots;
     // Deflation of the preconditioner (FGMRES mode): with U (n x kd, row stride ldu) approximate
     // eigenvectors nearest sigma and A = H - sigma, the preconditioner is
@@ -91,7 +92,10 @@ struct RitzH {
 };
 
 void extremal_bounds(mbl_sector *sec, double *emin, double *emax);
+// keep (optional): a live factorization of this request to use instead of factoring (if it matches
+// the sector and options), and where the job's factorization is left for reuse afterwards.
 void solve_near(mbl_sector *sec, double eps, int nev, const mbl_opts &o, double *d_evals, double *d_evecs,
-                double *d_resid, int *nconv, double *sigma_used, mbl_solve_stats *stats, cudaStream_t st);
+                double *d_resid, int *nconv, double *sigma_used, mbl_solve_stats *stats, cudaStream_t st,
+                std::unique_ptr<Factorization> *keep = nullptr);
 
 }  // namespace mbl

@@ -170,6 +170,7 @@ struct Ctx {
     struct SolveBatcher *batcher = nullptr;  // a serving worker's solve batcher (batch.cu), shared
     int batch_max_jobs = 16;                 // server option: jobs per batched solve (1 = no batching)
     double batch_window_us = 300.0;          // server option: longest wait for the other workers
+    double cache_fraction = 0.25;            // server option: budget share of the live-factor cache
     cudaEvent_t take_event();
     void resolve_profile();
 };

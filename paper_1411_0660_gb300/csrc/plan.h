@@ -118,8 +118,26 @@ struct AsmItem {     // assembly work item: columns [c0, c0 + ACOLS) of a front
     int32_t front, c0;
 };
 
+// Size classes of a panel step's largest trailing block m2 for the Schur-update autotuning:
+// class c holds 64 2^c <= m2 < 64 2^(c+1) (class 0 also everything smaller, the last class everything
+// larger).
+constexpr int TUNE_CLASSES = 8;
+inline int tune_class(int64_t m2) {
+    int c = 0;
+    while (c + 1 < TUNE_CLASSES && m2 >= ((int64_t)64 << (c + 1))) ++c;
+    return c;
+}
+
 struct Plan {
     int L = 0;
+    // Schur-update autotuning by tensor-core mode (1: 3xTF32, 2: 3xBF16) and size class: 1 = tcgen05
+    // tiles, 0 = CUDA-core tiles; the timings (microseconds per update of the class's synthetic front,
+    // tensor then CUDA cores, 0 where the class has no step) are kept for reporting.
+    std::mutex tune_mu;
+    bool tuned[3] = {};
+    int8_t tune_tc[3][TUNE_CLASSES] = {};
+    float tune_us[3][TUNE_CLASSES][2] = {};
+    std::vector<int32_t> step_class;  // per panel step: class of its largest trailing block
     int64_t n = 0, nnzA = 0;
     std::vector<int32_t> perm, iperm;  // new -> old, old -> new
     int32_t ns = 0;

@@ -18,6 +18,8 @@
 //      error, skips its epilogue, frees its TMEM and returns), read the accumulator with
 //      tcgen05.ld (warps w and w + 4 share TMEM lanes 32(w mod 4).., each taking 64 columns) and
 //      store C - acc, coalesced along the rows.
+#include <cuda.h>
+#include <mutex>
 #include <cuda_bf16.h>
 
 #include "factor.h"
@@ -275,8 +277,210 @@ __global__ void __launch_bounds__(THREADS) k_schur_tc(const PanelDesc *descs, in
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TMEM_COLS));
 }
 
+// ---------------------------------------------------------------------------------------------
+// TMA-fed form.  The panel's trsm has written the hi/lo pieces of L21 (pieces 0, 1) and W21 (2, 3)
+// row-major, NB pieces per row, rows at the descriptor's woff / NB.  A 4-D tensor map views them as
+// (16-byte k group elements, rows, k groups, pieces) with strides (row = NB pieces, k group = 16 bytes,
+// piece = the array), so that one cp.async.bulk.tensor per operand (box: a k group x 128 rows x every
+// k group x 2 pieces) lands the two pieces of a 128-row tile in the canonical K-major, no-swizzle
+// core-matrix layout the MMA reads: k groups 128 x 16 = 2048 bytes apart (LBO), 8-row groups 128 bytes
+// apart (SBO).  One thread arms an mbarrier with the expected bytes and issues both copies; meanwhile
+// every thread loads its part of C into registers; the MMAs follow as in k_schur_tc.
+template <bool BF16>
+struct TmaPiece {
+    static constexpr int EB = BF16 ? 2 : 4;
+    static constexpr int EPG = 16 / EB;              // elements per 16-byte k group
+    static constexpr int KG = NB / EPG;              // k groups per row
+    static constexpr uint32_t OPB = 128u * NB * EB;  // bytes per piece of a 128-row tile
+    static constexpr uint32_t LBO_T = 128u * 16u;    // next k group
+    static constexpr uint32_t SBO_T = 128u;          // next 8-row group
+    static constexpr int KMMA = 2 * EPG;
+};
+
+__device__ __forceinline__ uint64_t sdesc2(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;  // fixed 0b001 at bits 46..48; base offset 0, no swizzle
+    return d;
+}
+
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const void *tmap, int c0, int c1, int c2, int c3,
+                                            uint32_t mbar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+        "[%6];\n" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(tmap)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(mbar)
+        : "memory");
+}
+
+template <bool BF16>
+__global__ void __launch_bounds__(THREADS) k_schur_tma(const __grid_constant__ CUtensorMap pieces,
+                                                       const PanelDesc *descs, int nd, const int64_t *fo,
+                                                       const int32_t *fsz, float *arena, unsigned long long *err) {
+    using PC = TmaPiece<BF16>;
+    constexpr uint32_t OPB = PC::OPB;
+    extern __shared__ __align__(1024) unsigned char sm[];
+    __shared__ __align__(8) uint64_t mbar_ld, mbar_mma;
+    __shared__ uint32_t tmem_slot;
+    unsigned char *Apc = sm, *Bpc = sm + 2 * OPB;  // [piece][k group][row][16 bytes]
+
+    const int di = find_desc3t(descs, nd, blockIdx.x);
+    const PanelDesc d = descs[di];
+    const int s = d.front, f = fsz[s], k0 = d.k0, w = d.w;
+    const int64_t t = (int64_t)blockIdx.x - d.off3t;
+    int bi = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+    while ((int64_t)(bi + 1) * (bi + 2) / 2 <= t) ++bi;
+    while ((int64_t)bi * (bi + 1) / 2 > t) --bi;
+    const int bj = (int)(t - (int64_t)bi * (bi + 1) / 2);
+    const int base = k0 + w;
+    const int i0 = base + bi * TM, j0 = base + bj * TN;
+    float *F = arena + fo[s];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int quarter = warp & 3, half = warp >> 2;
+    const int row0 = (int)(d.woff / NB);
+
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&mbar_ld)));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&mbar_mma)));
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(&mbar_ld)),
+                     "r"(4u * OPB)
+                     : "memory");
+        tma_load_4d(smem_u32(Apc), &pieces, 0, row0 + bi * TM, 0, 0, smem_u32(&mbar_ld));
+        tma_load_4d(smem_u32(Bpc), &pieces, 0, row0 + bj * TN, 0, 2, smem_u32(&mbar_ld));
+    }
+    // this thread's part of C: row gi, columns j0 + 64 half + c (lower triangle only)
+    const int gi = i0 + quarter * 32 + lane;
+    float cv[64];
+#pragma unroll
+    for (int c = 0; c < 64; ++c) {
+        const int gj = j0 + 64 * half + c;
+        cv[c] = (gi < f && gj < f && gi >= gj) ? F[(int64_t)gj * f + gi] : 0.0f;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+    // operands landed (bounded wait); then one thread issues the MMAs
+    bool ok = mbar_wait(smem_u32(&mbar_ld), 0, 2000000000ull);
+    if (threadIdx.x == 0 && ok) {
+        const int ksteps = (w + PC::KMMA - 1) / PC::KMMA;
+        uint32_t acc = 0;
+        for (int ks = 0; ks < ksteps; ++ks) {
+            const uint32_t koff = (uint32_t)ks * 2u * PC::LBO_T;  // two k groups per MMA
+            const uint64_t ah = sdesc2(smem_u32(Apc) + koff, PC::LBO_T, PC::SBO_T);
+            const uint64_t al = sdesc2(smem_u32(Apc) + OPB + koff, PC::LBO_T, PC::SBO_T);
+            const uint64_t bh = sdesc2(smem_u32(Bpc) + koff, PC::LBO_T, PC::SBO_T);
+            const uint64_t bl = sdesc2(smem_u32(Bpc) + OPB + koff, PC::LBO_T, PC::SBO_T);
+            const uint64_t as[3] = {ah, ah, al}, bs[3] = {bh, bl, bh};
+#pragma unroll
+            for (int u = 0; u < 3; ++u) {
+                if (BF16)
+                    asm volatile(
+                        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                        "l"(as[u]), "l"(bs[u]), "r"(Piece<true>::IDESC), "r"(acc));
+                else
+                    asm volatile(
+                        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                        "l"(as[u]), "l"(bs[u]), "r"(Piece<false>::IDESC), "r"(acc));
+                acc = 1;
+            }
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                         smem_u32(&mbar_mma))
+                     : "memory");
+    }
+    if (ok) ok = mbar_wait(smem_u32(&mbar_mma), 0, 2000000000ull);
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    if (!ok) {
+        // a wait expired: flag it, give the copies and MMAs in flight a second bounded wait, skip the
+        // epilogue
+        if (lane == 0) atomicAdd(err, 1ull);
+        mbar_wait(smem_u32(&mbar_ld), 0, 2000000000ull);
+        if (threadIdx.x == 0) mbar_wait(smem_u32(&mbar_mma), 0, 2000000000ull);
+    } else {
+#pragma unroll
+        for (int jc = 0; jc < 64; jc += 32) {
+            uint32_t r[32];
+            tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(64 * half + jc), r);
+#pragma unroll
+            for (int c = 0; c < 32; ++c) {
+                const int gj = j0 + 64 * half + jc + c;
+                if (gi < f && gj < f && gi >= gj) F[(int64_t)gj * f + gi] = cv[jc + c] - __uint_as_float(r[c]);
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TMEM_COLS));
+}
+
 size_t schur_tc_smem(bool bf16) {
     return 4 * (size_t)(bf16 ? Piece<true>::OPB : Piece<false>::OPB) + 2 * (size_t)TK * TM * sizeof(float);
+}
+
+size_t schur_tma_smem(bool bf16) { return 4 * (size_t)(bf16 ? TmaPiece<true>::OPB : TmaPiece<false>::OPB); }
+
+bool encode_pieces_map(void *map, void *pieces, int64_t prow, bool bf16) {
+    using Encode = decltype(&::cuTensorMapEncodeTiled);
+    static Encode enc = [] {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            fn = nullptr;
+        (void)cudaGetLastError();
+        return reinterpret_cast<Encode>(fn);
+    }();
+    if (!enc || !pieces || prow < 1) return false;
+    const int eb = bf16 ? 2 : 4, epg = 16 / eb;
+    cuuint64_t dims[4] = {(cuuint64_t)epg, (cuuint64_t)prow, (cuuint64_t)(NB / epg), 4};
+    cuuint64_t strides[3] = {(cuuint64_t)NB * eb, 16, (cuuint64_t)prow * NB * eb};
+    cuuint32_t box[4] = {(cuuint32_t)epg, (cuuint32_t)TM, (cuuint32_t)(NB / epg), 2};
+    cuuint32_t estr[4] = {1, 1, 1, 1};
+    const CUresult r = enc(static_cast<CUtensorMap *>(map),
+                           bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, pieces,
+                           dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+void launch_schur_tma(const PanelStep &stp, const PanelDesc *d_descs, const int64_t *fo, const int32_t *fsz,
+                      float *arena, const void *map, unsigned long long *err, cudaStream_t st, bool bf16) {
+    static std::mutex mu;
+    static bool ready[64] = {};
+    int dev = 0;
+    MBL_CUDA(cudaGetDevice(&dev));
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (dev < 0 || dev >= 64 || !ready[dev]) {
+            MBL_CUDA(cudaFuncSetAttribute(k_schur_tma<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)schur_tma_smem(false)));
+            MBL_CUDA(cudaFuncSetAttribute(k_schur_tma<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)schur_tma_smem(true)));
+            if (dev >= 0 && dev < 64) ready[dev] = true;
+        }
+    }
+    const CUtensorMap &m = *static_cast<const CUtensorMap *>(map);
+    if (bf16)
+        k_schur_tma<true><<<(unsigned)stp.n3t, THREADS, schur_tma_smem(true), st>>>(m, d_descs, stp.nd, fo, fsz, arena,
+                                                                                     err);
+    else
+        k_schur_tma<false><<<(unsigned)stp.n3t, THREADS, schur_tma_smem(false), st>>>(m, d_descs, stp.nd, fo, fsz,
+                                                                                       arena, err);
+    MBL_LAUNCH_CHECK();
 }
 
 void launch_schur_tc(const PanelStep &stp, const PanelDesc *d_descs, const Plan &p, float *arena, const float *wscr,

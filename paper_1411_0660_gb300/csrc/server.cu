@@ -11,7 +11,9 @@
 // result is the one it would have alone.
 #include <chrono>
 #include <condition_variable>
+#include <cstring>
 #include <deque>
+#include <list>
 #include <thread>
 
 #include "factor.h"
@@ -39,7 +41,8 @@ size_t job_bytes(const Plan &p, int nev, int block, int prec) {
                           + (double)std::max(p.max_sstep_nrbk, p.max_lvl_nrbk) * SUBS * RBB * pad * es;
     const double bounds = 8.0 * n * 480.0;  // extremal-bounds Lanczos basis
     const double factor = arena_peak_bytes(p, prec, ARENA_AUTO) + factor_keep +
-                          (double)std::max<int64_t>(p.wscratch_elems, 1) * es + (double)p.m_elems * es + krylov;
+                          (double)std::max<int64_t>(p.wscratch_elems, 1) * 5.0 * es + (double)p.m_elems * es +
+                          krylov;  // W21 scratch and the four operand-piece arrays
     const double solve = factor_keep + krylov;
     const double peak = held + std::max(bounds, std::max(factor, solve));
     return (size_t)(1.05 * peak) + ((size_t)128 << 20);
@@ -56,6 +59,7 @@ struct Job {
     std::vector<double> fields;  // explicit disorder (copied at submission), empty = from (h, seed)
     int state = 0;  // 0 queued, 1 running, 2 done
     int status = MBL_OK;
+    int factor_reused = 0;
     std::string err;
     int nconv = 0;
     int64_t dim = 0;
@@ -67,6 +71,17 @@ struct Job {
 };
 
 }  // namespace
+
+// A finished job's sector and live factorization, kept for a later identical request (serving
+// residency): same sector shape and fields, target and precision.
+struct CacheEntry {
+    int L = 0, nup = 0, prec = 0;
+    double eps = 0.0;
+    std::vector<double> fields;
+    mbl_sector *sec = nullptr;
+    std::unique_ptr<Factorization> fz;
+    size_t bytes = 0;
+};
 
 struct Server {
     Ctx *parent = nullptr;
@@ -84,20 +99,61 @@ struct Server {
     std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
     cudaEvent_t ref = nullptr;  // recorded at start on the parent stream: origin of the device times
     SolveBatcher *batcher = nullptr;  // shared by the workers (none if batching is off)
+    // live factorizations, most recently used first; their bytes count against the budget
+    std::list<std::unique_ptr<CacheEntry>> cache;
+    size_t cache_bytes = 0, cache_limit = 0;
+    int64_t cache_hits = 0;
+    void evict_one();  // mu held
 
     void worker(int i);
     void run(Job &J, mbl_ctx *w);
 };
 
+void Server::evict_one() {
+    std::unique_ptr<CacheEntry> e = std::move(cache.back());
+    cache.pop_back();
+    cache_bytes -= e->bytes;
+    e->fz.reset();
+    mbl_sector_destroy(e->sec);
+}
+
 void Server::run(Job &J, mbl_ctx *w) {
     const mbl_request &q = J.req;
     mbl_sector *sec = nullptr;
     bool held = false;
+    std::unique_ptr<Factorization> keep;
     try {
         const int nup = q.nup > 0 ? q.nup : q.L / 2;
         int rc = J.fields.empty() ? mbl_build_sector_nup(w, q.L, nup, q.h, q.seed, &sec)
                                   : mbl_build_sector_fields_nup(w, q.L, nup, J.fields.data(), 1.0, &sec);
         if (rc != MBL_OK) fail(rc, mbl_last_error(w));
+        if (cache_limit) {
+            // a live factorization of the same request: take it (with its sector) out of the cache
+            std::unique_ptr<CacheEntry> hit;
+            {
+                std::lock_guard<std::mutex> lk(mu);
+                for (auto it = cache.begin(); it != cache.end(); ++it) {
+                    const CacheEntry &e = **it;
+                    if (e.L == q.L && e.nup == nup && e.prec == q.precision && e.eps == q.eps &&
+                        std::memcmp(e.fields.data(), sec->hfield, sizeof(double) * q.L) == 0) {
+                        hit = std::move(*it);
+                        cache.erase(it);
+                        cache_bytes -= hit->bytes;
+                        ++cache_hits;
+                        break;
+                    }
+                }
+            }
+            if (hit) {
+                mbl_sector_destroy(sec);
+                sec = hit->sec;
+                keep = std::move(hit->fz);
+                // the entry was made by another worker: from here on its work runs on this worker's
+                // stream (that worker synchronized its stream when the job ended)
+                sec->ctx = w;
+                keep->ctx = w;
+            }
+        }
         std::shared_ptr<Plan> plan = get_plan(sec);
         mbl_opts o;
         mbl_opts_default(&o);
@@ -106,7 +162,14 @@ void Server::run(Job &J, mbl_ctx *w) {
         {
             std::unique_lock<std::mutex> lk(mu);
             if (est > budget) fail(MBL_ERR_OOM, "request needs more HBM than the server budget");
-            cv_mem.wait(lk, [&] { return stop || reserved + est <= budget; });
+            for (;;) {  // admit when the job fits beside the running ones, evicting cached factors first
+                if (stop || reserved + est + cache_bytes <= budget) break;
+                if (!cache.empty()) {
+                    evict_one();
+                    continue;
+                }
+                cv_mem.wait(lk);
+            }
             if (stop) fail(MBL_ERR_INVALID, "server stopped");
             reserved += est;
             peak_reserved = std::max(peak_reserved, reserved);
@@ -134,11 +197,13 @@ void Server::run(Job &J, mbl_ctx *w) {
         dobs.alloc(w, (size_t)3 * nev + 1);
         int nconv = 0;
         double sigma = 0.0;
-        rc = mbl_solve_near_dev(sec, q.eps, nev, &o, de.data(), dv.data(), dr.data(), &nconv, &sigma, nullptr,
-                                nullptr);
-        if (rc != MBL_OK && rc != MBL_ERR_NOT_CONVERGED) fail(rc, mbl_last_error(w));
+        mbl_solve_stats sst{};
+        solve_near(sec, q.eps, nev, o, de.data(), dv.data(), dr.data(), &nconv, &sigma, &sst, w->stream,
+                   cache_limit ? &keep : nullptr);
+        J.factor_reused = sst.factor_reused;
+        rc = nconv < nev ? MBL_ERR_NOT_CONVERGED : MBL_OK;
         J.status = rc;
-        if (rc != MBL_OK) J.err = mbl_last_error(w);
+        if (rc != MBL_OK) J.err = "only " + std::to_string(nconv) + " of " + std::to_string(nev) + " eigenpairs reached the tolerance";
         double *d_r = dobs.data(), *d_rm = d_r + nev, *d_s1 = d_rm + 1, *d_se = d_s1 + nev;
         int rc2 = mbl_observables_nup_dev(w, q.L, nup, nev, de.data(), dv.data(), d_r, d_rm, d_s1, d_se, nullptr);
         if (rc2 != MBL_OK) fail(rc2, mbl_last_error(w));
@@ -175,6 +240,26 @@ void Server::run(Job &J, mbl_ctx *w) {
         J.status = MBL_ERR_CUDA;
         J.err = e.what();
     }
+    // keep the sector and its live factorization for an identical request, within the cache limit
+    if (sec && keep && cache_limit && J.status == MBL_OK && cudaStreamSynchronize(w->stream) == cudaSuccess) {
+        auto e = std::make_unique<CacheEntry>();
+        e->L = q.L;
+        e->nup = q.nup > 0 ? q.nup : q.L / 2;
+        e->prec = q.precision;
+        e->eps = q.eps;
+        e->fields.assign(sec->hfield, sec->hfield + q.L);
+        e->bytes = keep->held_bytes() + (size_t)(20 * sec->n + 12 * sec->nnz);
+        if (e->bytes <= cache_limit) {
+            e->sec = sec;
+            e->fz = std::move(keep);
+            sec = nullptr;
+            std::lock_guard<std::mutex> lk(mu);
+            cache_bytes += e->bytes;
+            cache.push_front(std::move(e));
+            while (cache_bytes > cache_limit) evict_one();
+        }
+    }
+    keep.reset();
     if (sec) mbl_sector_destroy(sec);
     {
         std::lock_guard<std::mutex> lk(mu);
@@ -222,6 +307,10 @@ void server_shutdown(Ctx *ctx) {
     s->cv_work.notify_all();
     s->cv_mem.notify_all();
     for (auto &th : s->threads) th.join();
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        while (!s->cache.empty()) s->evict_one();
+    }
     batcher_destroy(s->batcher);
     for (mbl_ctx *w : s->wctx) mbl_ctx_destroy(w);
     if (s->ref) cudaEventDestroy(s->ref);
@@ -254,6 +343,7 @@ void fill_result(const Job &J, mbl_result *out) {
     out->d_start_ms = J.d_start;
     out->d_end_ms = J.d_end;
     out->reserved_bytes = J.reserved;
+    out->factor_reused = J.factor_reused;
     auto put = [](double *dst, const std::vector<double> &v) {
         if (dst && !v.empty()) std::copy(v.begin(), v.end(), dst);
     };
@@ -289,6 +379,7 @@ int mbl_server_start(mbl_ctx *ctx, int slots, size_t budget_bytes) {
             w->plans = ctx->plans;
             s->wctx.push_back(w);
         }
+        s->cache_limit = ctx->cache_fraction > 0.0 ? (size_t)(ctx->cache_fraction * (double)s->budget) : 0;
         if (ctx->batch_max_jobs > 1 && slots > 1) {
             s->batcher = batcher_create(ctx->device, ctx->batch_max_jobs, ctx->batch_window_us);
             for (mbl_ctx *w : s->wctx) w->batcher = s->batcher;
@@ -385,6 +476,8 @@ int mbl_server_stats_get(mbl_ctx *ctx, mbl_server_stats *out) {
     out->budget_bytes = s->budget;
     out->reserved_bytes = s->reserved;
     out->peak_reserved_bytes = s->peak_reserved;
+    out->cache_hits = s->cache_hits;
+    out->cache_bytes = s->cache_bytes;
     out->solve_batches = out->batched_solves = 0;
     out->batch_ms = out->batch_bytes = 0.0;
     if (s->batcher) {
@@ -394,6 +487,14 @@ int mbl_server_stats_get(mbl_ctx *ctx, mbl_server_stats *out) {
             return srv_report(ctx, e.code, e.msg);
         }
     }
+    return MBL_OK;
+}
+
+int mbl_server_cache(mbl_ctx *ctx, double fraction) {
+    if (!ctx) return MBL_ERR_INVALID;
+    if (ctx->server) return srv_report(ctx, MBL_ERR_INVALID, "set the cache before mbl_server_start");
+    if (!(fraction >= 0.0 && fraction <= 0.9)) return srv_report(ctx, MBL_ERR_INVALID, "fraction in [0, 0.9]");
+    ctx->cache_fraction = fraction;
     return MBL_OK;
 }
 

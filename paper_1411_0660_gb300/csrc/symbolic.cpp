@@ -618,6 +618,11 @@ std::shared_ptr<Plan> build_plan(int L, const std::vector<uint32_t> &states, con
                 p.descs.push_back(d);
             }
             stp.nd = (int32_t)p.descs.size() - stp.d0;
+            {
+                int64_t mx = 0;
+                for (int32_t q = stp.d0; q < stp.d0 + stp.nd; ++q) mx = std::max<int64_t>(mx, p.descs[q].m2);
+                p.step_class.push_back(tune_class(mx));
+            }
             p.max_desc_per_step = std::max<int64_t>(p.max_desc_per_step, stp.nd);
             p.max_step_n2 = std::max<int64_t>(p.max_step_n2, stp.n2);
             p.wscratch_elems = std::max(p.wscratch_elems, stp.wsize);

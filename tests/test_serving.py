@@ -111,3 +111,32 @@ def test_oversized_request_and_bad_arguments(g, ctx):
         srv.submit(12, 1.0, 0, 1.5, 10)
     assert e.value.code == 1
     srv.stop()
+
+
+def test_repeated_request_reuses_the_live_factor(g, ctx, orc):
+    """Serving residency: a request identical to a finished one takes its sector and factorization
+    from the cache (no new factorization) and returns the same eigenpairs; a cache of size zero never
+    reuses; the oracle confirms the reused result."""
+    L, h, seed, eps, nev = 14, 2.0, 80, 0.4, 20
+    srv = g.Server(ctx, slots=2, cache_fraction=0.25)
+    a = srv.wait(srv.submit(L, h, seed, eps, nev, want_vectors=True), 300.0)
+    b = srv.wait(srv.submit(L, h, seed, eps, nev, want_vectors=True), 300.0)
+    c = srv.wait(srv.submit(L, h, seed + 1, eps, nev), 300.0)  # another realization: no reuse
+    st = srv.stats()
+    srv.stop()
+    assert a.status == 0 and b.status == 0 and c.status == 0
+    assert a.factor_reused == 0 and b.factor_reused == 1 and c.factor_reused == 0
+    assert st["cache_hits"] == 1
+    H = orc.csr(L, orc.fields(L, h, seed))
+    emin, emax = orc.extremal_bounds(H)
+    hn = max(abs(emin), abs(emax))
+    assert np.max(np.abs(a.evals - b.evals)) <= EIG_TOL * hn
+    for j in range(nev):
+        y = b.evecs[:, j]
+        assert np.linalg.norm(H.matvec(y) - b.evals[j] * y) <= EIG_TOL * hn
+    srv0 = g.Server(ctx, slots=1, cache_fraction=0.0)
+    x = srv0.wait(srv0.submit(L, h, seed, eps, nev), 300.0)
+    y = srv0.wait(srv0.submit(L, h, seed, eps, nev), 300.0)
+    st0 = srv0.stats()
+    srv0.stop()
+    assert x.factor_reused == 0 and y.factor_reused == 0 and st0["cache_hits"] == 0

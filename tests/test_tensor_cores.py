@@ -102,3 +102,25 @@ def test_tensor_core_mode_is_validated(g, ctx):
     sec = g.build_sector(ctx, 10, 1.0, 2)
     with pytest.raises(g.MblError):
         g.factor(sec, 0.0, precision=1, tensor_cores=3)
+
+
+def test_schur_tile_autotuning_recorded(g, ctx):
+    """The FP32 fronts' trailing update is autotuned per size class of trailing block (tcgen05 128 x 128
+    tiles against CUDA-core 64 x 64 tiles, timed on a synthetic front of the class): every class the
+    plan's panel steps have gets a choice and two timings; FP32 fronts on CUDA cores are not tuned."""
+    sec = g.build_sector(ctx, 16, 2.0, 90)
+    lo, hi = g.extremal_bounds(sec)
+    f = g.factor(sec, lo + 0.5 * (hi - lo), precision=1, tensor_cores=1)
+    st = f.stats()
+    f.close()
+    tuned = [c for c in range(8) if st["tune_choice"][c] >= 0]
+    assert tuned == list(range(8))
+    present = [c for c in range(8) if st["tune_us_tc"][c] > 0]
+    assert present, st
+    for c in present:
+        assert st["tune_us_cc"][c] > 0 and st["tune_choice"][c] in (0, 1)
+        assert st["tune_choice"][c] == (1 if st["tune_us_tc"][c] <= st["tune_us_cc"][c] else 0)
+    f0 = g.factor(sec, lo + 0.5 * (hi - lo), precision=1, tensor_cores=0)
+    assert all(c == -1 for c in f0.stats()["tune_choice"])
+    f0.close()
+    sec.close()
