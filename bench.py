@@ -584,6 +584,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch-jobs", type=int, default=16, help="served form: jobs per batched solve launch (1: off)")
     ap.add_argument("--batch-window-us", type=float, default=300.0, help="served form: batcher collection window")
+    ap.add_argument("--batch-lanes", type=int, default=2, help="served form: streams of batched solves")
     args = ap.parse_args()
     args.batch_case = args.case == "solve" and "--batch" in sys.argv
     if args.case == "observables":
@@ -653,7 +654,8 @@ def main():
         sec0 = g.build_sector(ctx, L, h, seed)
         host_fields.append(np.ascontiguousarray(sec0.fields()))
         sec0.close()
-    srv = g.Server(ctx, slots=args.slots, batch_jobs=args.batch_jobs, batch_window_us=args.batch_window_us)
+    srv = g.Server(ctx, slots=args.slots, batch_jobs=args.batch_jobs, batch_window_us=args.batch_window_us,
+                   batch_lanes=args.batch_lanes)
     for t in [srv.submit(L, h, seed, eps, NEV) for (h, seed, eps) in jobs_for_step(0, args.slots, rank, world)]:
         srv.wait(t)  # worker warm-up: kernels loaded, graphs captured once per worker
     for t in [srv.submit(L, h, seed, eps, NEV, precision=g.MBL_PREC_FP64)

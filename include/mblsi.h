@@ -388,15 +388,17 @@ typedef struct mbl_server_stats {
 int mbl_server_cache(mbl_ctx *ctx, double fraction);
 
 /* Continuous batching of the workers' triangular solves (set before mbl_server_start; defaults
- * max_jobs = 16, window_us = 300).  Jobs of one sector size share a symbolic plan, so their block
- * solves are one launch sequence on different buffers: a worker's solve is handed to a batcher
- * thread, which launches the sequence once for up to max_jobs workers' solves of the same (plan,
- * precision, block width) -- every launch covers all of them -- as soon as every worker inside a
- * solve phase of that group has one waiting, or the oldest has waited window_us microseconds.
- * Results are the same as unbatched solves (the same kernels on each job's own buffers).
- * max_jobs = 1 turns batching off.  Not in the paper: a serving pattern for many small jobs.
- * MBL_ERR_INVALID while a server runs or for max_jobs outside [1, 64], window_us outside [0, 1e6]. */
-int mbl_server_batching(mbl_ctx *ctx, int max_jobs, double window_us);
+ * max_jobs = 16, window_us = 300, lanes = 2).  Jobs of one sector size share a symbolic plan, so
+ * their block solves are one launch sequence on different buffers: a worker's solve is handed to a
+ * batcher thread, which launches the sequence once for up to max_jobs workers' solves of the same
+ * (plan, precision, block width) -- every launch covers all of them -- on one of `lanes` streams:
+ * as soon as every worker inside a solve phase of that group has one waiting, or, while a lane is
+ * idle, when the oldest has waited window_us microseconds.  While every lane is busy, requests
+ * gather until one completes.  Results are the same as unbatched solves (the same kernels on each
+ * job's own buffers).  max_jobs = 1 turns batching off.  Not in the paper: a serving pattern for
+ * many small jobs.  MBL_ERR_INVALID while a server runs or for max_jobs outside [1, 64], window_us
+ * outside [0, 1e6], lanes outside [1, 8]. */
+int mbl_server_batching(mbl_ctx *ctx, int max_jobs, double window_us, int lanes);
 
 int mbl_server_start(mbl_ctx *ctx, int slots, size_t budget_bytes);
 /* Queue a request; *ticket identifies it.  MBL_ERR_INVALID for bad arguments or no server. */

@@ -405,13 +405,15 @@ class Server:
     """Worker threads of a context serving (L, h, seed, eps, nev) requests as memory allows."""
 
     def __init__(self, ctx: Context, slots: int = 4, hbm_budget_bytes: int = 0, batch_jobs: int = 16,
-                 batch_window_us: float = 300.0, cache_fraction: float = 0.25):
+                 batch_window_us: float = 300.0, cache_fraction: float = 0.25, batch_lanes: int = 2):
         """`batch_jobs` > 1 batches the workers' triangular solves of one sector size into shared
-        launches (at most that many jobs per launch, waiting up to `batch_window_us`); 1 turns it off.
-        `cache_fraction` of the budget keeps finished jobs' live factorizations for repeated requests."""
+        launches (at most that many jobs per launch, waiting up to `batch_window_us` while one of the
+        `batch_lanes` streams is idle); 1 turns it off.  `cache_fraction` of the budget keeps finished
+        jobs' live factorizations for repeated requests."""
         self.ctx = ctx
         self._req = {}
-        _check(_lib().mbl_server_batching(ctx.handle, batch_jobs, float(batch_window_us)), ctx.handle)
+        _check(_lib().mbl_server_batching(ctx.handle, batch_jobs, float(batch_window_us), int(batch_lanes)),
+               ctx.handle)
         _check(_lib().mbl_server_cache(ctx.handle, float(cache_fraction)), ctx.handle)
         _check(_lib().mbl_server_start(ctx.handle, slots, hbm_budget_bytes), ctx.handle)
 

@@ -132,7 +132,7 @@ SIGNATURES = [
                                               c_void_p, c_void_p, c_void_p, c_void_p]),
     ("mbl_entanglement_noalloc_dev", c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p]),
     ("mbl_server_start", c_int, [c_void_p, c_int, c_size_t]),
-    ("mbl_server_batching", c_int, [c_void_p, c_int, c_double]),
+    ("mbl_server_batching", c_int, [c_void_p, c_int, c_double, c_int]),
     ("mbl_server_cache", c_int, [c_void_p, c_double]),
     ("mbl_factor_solve_batch_dev", c_int, [c_void_p, c_int, c_void_p, c_void_p, c_int, c_void_p]),
     ("mbl_submit", c_int, [c_void_p, P(Request), P(c_uint64)]),

@@ -25,6 +25,18 @@ bool ctx_alive(const Ctx *c) {
     return c && live_ctx().count(c) != 0;
 }
 
+void smem_limit(const void *fn, size_t bytes) {
+    static std::mutex mu;
+    static std::map<std::pair<const void *, int>, size_t> *done = new std::map<std::pair<const void *, int>, size_t>();
+    int dev = 0;
+    MBL_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(mu);
+    size_t &have = (*done)[{fn, dev}];
+    if (have >= bytes) return;
+    MBL_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    have = bytes;
+}
+
 cudaEvent_t Ctx::take_event() {
     if (!event_pool.empty()) {
         cudaEvent_t e = event_pool.back();

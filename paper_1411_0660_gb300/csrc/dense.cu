@@ -92,11 +92,7 @@ static void dense_tn_t(int64_t n, const TV *V, int ldv, int c0, int k, const dou
     if (rows_per < 1) rows_per = 1;
     int nch = (int)((n + rows_per - 1) / rows_per);
     size_t smem = (size_t)TN_ROWS * (k + p) * sizeof(TV);
-    static std::atomic<bool> attr{false};  // per process: one device
-    if (!attr) {
-        MBL_CUDA(cudaFuncSetAttribute(k_tn_partial<TV>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-        attr = true;
-    }
+    smem_limit((const void *)k_tn_partial<TV>, 200 * 1024);
     k_tn_partial<TV><<<nch, threads, smem, st>>>(n, V, ldv, c0, k, X, ldx, x0, p, work, rows_per);
     MBL_LAUNCH_CHECK();
     k_tn_reduce<<<(unsigned)((k * p + 7) / 8), 256, 0, st>>>(nch, k * p, work, C);
@@ -738,12 +734,7 @@ __global__ void k_bi_back(int m, const double *A, R *work, double *X) {
 template <class R>
 static void syev_bisect_t(int m, double *d_A, double *d_w, double *d_work, cudaStream_t st) {
     if (m < 1 || m > EIG_SMEM_MAX_M) fail(MBL_ERR_INVALID, "bisection eigensolver: order must be in [1, 160]");
-    static std::atomic<bool> attr{false};  // per process: one device
-    if (!attr) {
-        MBL_CUDA(cudaFuncSetAttribute(k_bi_tridiag<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      EIG_SMEM_MAX_M * EIG_SMEM_MAX_M * sizeof(R)));
-        attr = true;
-    }
+    smem_limit((const void *)k_bi_tridiag<R>, EIG_SMEM_MAX_M * EIG_SMEM_MAX_M * sizeof(R));
     R *work = reinterpret_cast<R *>(d_work);
     // the eigenvectors overwrite A only after the back-transformation has read its reflectors:
     // they go to the U scratch first (3 m^2 entries of R hold m^2 doubles; start rounded up to 16 bytes)

@@ -165,6 +165,9 @@ struct LeanArena {
 
 template <class T>
 __device__ __forceinline__ T tabs(T x) { return x < T(0) ? -x : x; }
+// c - a b, rounded once
+__device__ __forceinline__ float fnms(float a, float b, float c) { return __fmaf_rn(-a, b, c); }
+__device__ __forceinline__ double fnms(double a, double b, double c) { return __fma_rn(-a, b, c); }
 
 __device__ __forceinline__ int lower_bound_i32(const int32_t *a, int n, int x) {
     int lo = 0, hi = n;
@@ -261,26 +264,37 @@ __global__ void __launch_bounds__(PANEL_THREADS) k_panel_colmax(const PanelDesc 
     }
 }
 
+// LDL^T of a panel's w x w diagonal block with symmetric 1x1 pivoting, 128 threads.  The block is
+// kept whole (both triangles) in shared memory so that every candidate pivot's off-diagonal entries
+// lie in its own row.  A pair of threads owns row t + 1 + i of the trailing block during the update
+// of step t (the two threads take alternate columns) and the same index as candidate t + 1 + i in the
+// pivot choice of step t + 1, so the largest off-diagonal magnitude that the choice needs falls out
+// of the update.  Both mirror entries of the update subtract u_a l_b with one rounding (a the larger
+// index, u the unscaled pivot column, l = u / d), so the block stays exactly symmetric.
 template <class T>
-__global__ void __launch_bounds__(256) k_panel_diag(const PanelDesc *descs, const int64_t *fo, const int32_t *fsz,
+__global__ void __launch_bounds__(128) k_panel_diag(const PanelDesc *descs, const int64_t *fo, const int32_t *fsz,
                                                     const int32_t *sn_start, T *arena, T *Dg, int32_t *piv,
                                                     double tiny, unsigned long long *counters,
                                                     const unsigned int *cmax) {
     __shared__ T B[NB][NB + 1];
-    __shared__ T lcol[NB];
+    __shared__ T ucol[NB], lcol[NB], dvec[NB];
     __shared__ int perm[NB];
     __shared__ float cm[NB];
-    __shared__ float s_sc[2], s_dd[2];
-    __shared__ int s_jj[2];
+    __shared__ unsigned int s_k1[4], s_k2[4];
+    __shared__ int s_jj[4];
     __shared__ unsigned int s_npert, s_nneg;
-    static_assert(NB == 64, "the pivot search runs on two warps, one thread per candidate");
+    static_assert(NB == 64, "two threads per row of a 64-wide block on 128 threads");
     const PanelDesc d = descs[blockIdx.x];
     const int s = d.front, f = fsz[s], k0 = d.k0, w = d.w;
     T *F = arena + fo[s];
-    const int tid = threadIdx.x, bd = blockDim.x, lane = tid & 31, wp = tid >> 5;
-    for (int idx = tid; idx < w * w; idx += bd) {
-        int r = idx % w, c = idx / w;
-        B[r][c] = (r >= c) ? F[(int64_t)(k0 + c) * f + k0 + r] : T(0);
+    const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5, pi = tid >> 1, h = tid & 1;
+    for (int idx = tid; idx < w * w; idx += 128) {
+        const int r = idx % w, c = idx / w;
+        if (r >= c) {
+            const T v = F[(int64_t)(k0 + c) * f + k0 + r];
+            B[r][c] = v;
+            B[c][r] = v;
+        }
     }
     if (tid < w) {
         perm[tid] = tid;
@@ -288,96 +302,130 @@ __global__ void __launch_bounds__(256) k_panel_diag(const PanelDesc *descs, cons
     }
     if (tid == 0) s_npert = s_nneg = 0u;
     __syncthreads();
+    // off-diagonal magnitude of candidate pi's row over the whole block (step 0)
+    float om = 0.f;
+    if (pi < w) {
+        for (int c = h; c < w; c += 2)
+            if (c != pi) om = fmaxf(om, (float)tabs(B[pi][c]));
+    }
+    om = fmaxf(om, __shfl_xor_sync(0xffffffffu, om, 1));
     for (int t = 0; t < w; ++t) {
         // pivot: the candidate whose diagonal is largest relative to the rest of its column (inside the
-        // block and, from before this panel, in the rows below), which bounds the multipliers.  Thread
-        // j of the first two warps scores candidate j; order: largest score, then largest |d|, then the
-        // smallest index.
-        if (wp < 2) {
-            float sc = -1.f, dj = -1.f;
-            int jj = w;
-            const int j = tid;
-            if (j >= t && j < w) {
-                float om = cm[perm[j]];
-                for (int i = t; i < j; ++i) om = fmaxf(om, (float)tabs(B[j][i]));
-                for (int i = j + 1; i < w; ++i) om = fmaxf(om, (float)tabs(B[i][j]));
-                dj = (float)tabs(B[j][j]);
-                sc = om > 0.f ? dj / om : 3.0e38f;
-                jj = j;
+        // block and, from before this panel, in the rows below), which bounds the multipliers; order:
+        // largest score, then largest |d|, then the smallest index.  Scores and |d| are non-negative
+        // floats, so their bit patterns order like their values: a warp's choice is three redux.sync
+        // steps (score, then |d| among the best scores, then the smallest index).
+        {
+            const int j = t + pi;
+            const bool valid = j < w;
+            unsigned int k1 = 0u, k2 = 0u;
+            if (valid) {
+                const float o = fmaxf(om, cm[perm[j]]);
+                const float dj = (float)tabs(B[j][j]);
+                const float sc = o > 0.f ? dj / o : 3.0e38f;
+                k1 = __float_as_uint(sc) + 1u;  // 0 marks a lane without a candidate
+                k2 = __float_as_uint(dj);
             }
-            for (int o = 16; o > 0; o >>= 1) {
-                const float osc = __shfl_xor_sync(0xffffffffu, sc, o), odj = __shfl_xor_sync(0xffffffffu, dj, o);
-                const int ojj = __shfl_xor_sync(0xffffffffu, jj, o);
-                if (ojj < w && (osc > sc || (osc == sc && (odj > dj || (odj == dj && ojj < jj))))) {
-                    sc = osc;
-                    dj = odj;
-                    jj = ojj;
-                }
-            }
+            const unsigned int m1 = __reduce_max_sync(0xffffffffu, k1);
+            const unsigned int m2 = __reduce_max_sync(0xffffffffu, k1 == m1 ? k2 : 0u);
+            const unsigned int jm =
+                __reduce_min_sync(0xffffffffu, (valid && k1 == m1 && k2 == m2) ? (unsigned int)j : (unsigned int)w);
             if (lane == 0) {
-                s_sc[wp] = sc;
-                s_dd[wp] = dj;
-                s_jj[wp] = jj;
+                s_k1[wp] = m1;
+                s_k2[wp] = m2;
+                s_jj[wp] = (int)jm;
             }
         }
         __syncthreads();
         int j = s_jj[0];
         {
-            const int oj = s_jj[1];
-            if (oj < w && (j >= w || s_sc[1] > s_sc[0] || (s_sc[1] == s_sc[0] && s_dd[1] > s_dd[0]))) j = oj;
-            if (j >= w) j = t;
+            // the warps hold candidates in increasing order: a later warp wins only if strictly better
+            unsigned int b1 = s_k1[0], b2 = s_k2[0];
+#pragma unroll
+            for (int v = 1; v < 4; ++v) {
+                const unsigned int k1 = s_k1[v], k2 = s_k2[v];
+                if (k1 > b1 || (k1 == b1 && k2 > b2)) {
+                    b1 = k1;
+                    b2 = k2;
+                    j = s_jj[v];
+                }
+            }
+            if (b1 == 0u || j >= w) j = t;
         }
         if (j != t) {
-            for (int c = tid; c < t; c += bd) { T x = B[t][c]; B[t][c] = B[j][c]; B[j][c] = x; }
-            for (int c = t + 1 + tid; c < j; c += bd) { T x = B[c][t]; B[c][t] = B[j][c]; B[j][c] = x; }
-            for (int r = j + 1 + tid; r < w; r += bd) { T x = B[r][t]; B[r][t] = B[r][j]; B[r][j] = x; }
+            // symmetric exchange of indices t and j: rows over every column (the computed L rows
+            // included), then columns over the trailing rows
+            if (tid < w) {
+                const T x = B[t][tid];
+                B[t][tid] = B[j][tid];
+                B[j][tid] = x;
+            }
             if (tid == 0) {
-                T x = B[t][t]; B[t][t] = B[j][j]; B[j][j] = x;
-                int pp = perm[t]; perm[t] = perm[j]; perm[j] = pp;
+                const int pp = perm[t];
+                perm[t] = perm[j];
+                perm[j] = pp;
+            }
+            __syncthreads();
+            if (tid >= t && tid < w) {
+                const T x = B[tid][t];
+                B[tid][t] = B[tid][j];
+                B[tid][j] = x;
             }
         }
         __syncthreads();
-        // the pivot (a tiny one replaced by +-tiny, statically), then the column: lcol keeps the
-        // unscaled entries, the column itself becomes L's
+        // the pivot (a tiny one replaced by +-tiny, statically); the column: u keeps the unscaled
+        // entries, the column itself becomes L's
+        // (B[t][t] itself is left as it is: D goes to dvec)
         T dv = B[t][t];
         const bool pert = !(tabs(dv) >= (T)tiny);
         if (pert) dv = (dv >= T(0)) ? (T)tiny : (T)(-tiny);
+        const int r = t + 1 + pi;
+        const bool own = r < w;
+        T ur = (own && h == 0) ? B[r][t] : T(0);
+        ur = __shfl_sync(0xffffffffu, ur, lane & ~1);  // the pair's second thread never reads B[r][t]
+        const T lr = own ? ur / dv : T(0);
+        if (own && h == 0) {
+            B[r][t] = lr;
+            ucol[r] = ur;
+            lcol[r] = lr;
+        }
         if (tid == 0) {
+            dvec[t] = dv;
             s_npert += pert ? 1u : 0u;
             s_nneg += dv < T(0) ? 1u : 0u;
         }
-        for (int r = t + 1 + tid; r < w; r += bd) {
-            const T u = B[r][t];
-            lcol[r] = u;
-            B[r][t] = u / dv;
-        }
         __syncthreads();
-        if (tid == 0) B[t][t] = dv;
-        // trailing update of the lower triangle: lane -> rows (stride 32), warp -> columns (stride
-        // bd / 32), no index division
-        for (int c = t + 1 + wp; c < w; c += bd >> 5) {
-            const T lc = B[c][t];
-            for (int r = c + lane; r < w; r += 32) B[r][c] -= lcol[r] * lc;
+        // trailing update of row r over the columns of this thread, both triangles.  The next step's
+        // choice reads only the thread's own row, so no barrier closes the step.
+        om = 0.f;
+        if (own) {
+#pragma unroll 4
+            for (int c = t + 1 + h; c < w; c += 2) {
+                const T v = c <= r ? fnms(ur, lcol[c], B[r][c]) : fnms(ucol[c], lr, B[r][c]);
+                B[r][c] = v;
+                if (c != r) om = fmaxf(om, (float)tabs(v));
+            }
         }
-        __syncthreads();
+        om = fmaxf(om, __shfl_xor_sync(0xffffffffu, om, 1));
     }
+    __syncthreads();
     if (tid == 0) {
         if (s_npert) atomicAdd(&counters[0], (unsigned long long)s_npert);
         if (s_nneg) atomicAdd(&counters[1], (unsigned long long)s_nneg);
     }
     // write L11 (strictly lower), D on the diagonal, pivots
-    for (int idx = tid; idx < w * w; idx += bd) {
-        int r = idx % w, c = idx / w;
-        if (r >= c) F[(int64_t)(k0 + c) * f + k0 + r] = B[r][c];
+    for (int idx = tid; idx < w * w; idx += 128) {
+        const int r = idx % w, c = idx / w;
+        if (r >= c) F[(int64_t)(k0 + c) * f + k0 + r] = r == c ? dvec[r] : B[r][c];
     }
     const int64_t g0 = (int64_t)sn_start[s] + k0;
     if (tid < w) {
-        Dg[g0 + tid] = B[tid][tid];
+        Dg[g0 + tid] = dvec[tid];
         piv[g0 + tid] = k0 + perm[tid];
         float lmax = 0.f;
         for (int r = tid + 1; r < w; ++r) lmax = fmaxf(lmax, (float)tabs(B[r][tid]));
         atomicMax(reinterpret_cast<unsigned int *>(counters + 3), __float_as_uint(lmax));
-        atomicMin(reinterpret_cast<unsigned int *>(counters + 4), __float_as_uint((float)tabs(B[tid][tid])));
+        atomicMin(reinterpret_cast<unsigned int *>(counters + 4), __float_as_uint((float)tabs(dvec[tid])));
     }
 }
 
@@ -1146,12 +1194,9 @@ static int rhs_pad(int p) { return p <= 8 ? 8 : (p <= 16 ? 16 : 32); }
 
 template <class T, int PB>
 static void set_step_attrs() {
-    MBL_CUDA(cudaFuncSetAttribute(k_fwd_step<T, PB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)fwd_step_smem<T, PB>()));
-    MBL_CUDA(cudaFuncSetAttribute(k_bwd_step<T, PB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)bwd_step_smem<T, PB>()));
-    MBL_CUDA(cudaFuncSetAttribute(k_bwd_update<T, PB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)bwd_step_smem<T, PB>()));
+    smem_limit((const void *)k_fwd_step<T, PB>, fwd_step_smem<T, PB>());
+    smem_limit((const void *)k_bwd_step<T, PB>, bwd_step_smem<T, PB>());
+    smem_limit((const void *)k_bwd_update<T, PB>, bwd_step_smem<T, PB>());
 }
 
 // CTAs of 256 threads of `kern` (dynamic shared memory smem) that the device holds at once: the grid
@@ -1176,14 +1221,11 @@ static int64_t resident_grid(K *kern, size_t smem) {
 
 template <class T>
 static void set_solve_attrs() {
-    static std::atomic<bool> done{false};
-    if (done) return;
-    MBL_CUDA(cudaFuncSetAttribute(k_build_m<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)build_m_smem<T>()));
-    MBL_CUDA(cudaFuncSetAttribute(k_apply_m<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)apply_m_smem<T>()));
+    smem_limit((const void *)k_build_m<T>, build_m_smem<T>());
+    smem_limit((const void *)k_apply_m<T>, apply_m_smem<T>());
     set_step_attrs<T, 8>();
     set_step_attrs<T, 16>();
     set_step_attrs<T, 32>();
-    done = true;
 }
 
 template <class T>
@@ -1212,11 +1254,7 @@ static void factor_impl(Factorization &fz, cudaStream_t st) {
             MBL_LAUNCH_CHECK();
         }
     };
-    static std::atomic<bool> attr{false};  // per process: one device
-    if (!attr) {
-        MBL_CUDA(cudaFuncSetAttribute(k_panel_trsm<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)trsm_smem<T>()));
-        attr = true;
-    }
+    smem_limit((const void *)k_panel_trsm<T>, trsm_smem<T>());
     set_solve_attrs<T>();
     MBL_CUDA(cudaMemsetAsync(fz.counters.data(), 0, 5 * sizeof(unsigned long long), st));
     MBL_CUDA(cudaMemsetAsync(fz.counters.data() + 4, 0x7f, sizeof(unsigned int), st));  // min |d| starts huge
@@ -1251,7 +1289,7 @@ static void factor_impl(Factorization &fz, cudaStream_t st) {
                                                                        cmax);
                     MBL_LAUNCH_CHECK();
                 }
-                k_panel_diag<T><<<stp.nd, 256, 0, st>>>(dd, p.d_sn_fo.data(), p.d_sn_f.data(), p.d_sn_start.data(), arena,
+                k_panel_diag<T><<<stp.nd, 128, 0, st>>>(dd, p.d_sn_fo.data(), p.d_sn_f.data(), p.d_sn_start.data(), arena,
                                                         Dg, fz.piv.data(), fz.tiny, fz.counters.data(), cmax);
                 MBL_LAUNCH_CHECK();
                 if (stp.n2 > 0) {

@@ -99,8 +99,9 @@ void batched_solve(SolveBatcher *b, Factorization &fz, const double *B, int64_t 
 // it launches, up to its window.
 void batcher_enter(SolveBatcher *b, const Plan *pl, int prec, int p);
 void batcher_leave(SolveBatcher *b, const Plan *pl, int prec, int p);
-// A batcher with its own thread, stream and context on `device`; batches of at most max_jobs.
-SolveBatcher *batcher_create(int device, int max_jobs, double window_us);
+// A batcher with its own thread, `lanes` streams and context on `device`; batches of at most
+// max_jobs.
+SolveBatcher *batcher_create(int device, int max_jobs, double window_us, int lanes);
 void batcher_destroy(SolveBatcher *b);  // after every worker using it has stopped
 // Launched batches, solves in them, their device time (CUDA events) and algorithmic bytes.
 void batcher_stats(SolveBatcher *b, int64_t *batches, int64_t *solves, double *ms, double *bytes);

@@ -37,12 +37,21 @@ __global__ void k_random_block(int64_t n, int p, uint64_t seed, double *X, int l
     X[i * ldx + x0 + q] = (double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0;
 }
 
-// T(row, col) at T[col * ldt + row].  Column block [j, j+p) against rows [0, m): C1 + C2.
+// T(row, col) at T[col * ldt + row].  Column block [j, j+p) against rows [0, m): C1 + C2, mirrored
+// into row block [j, j+p).  Within the diagonal block the two computed entries (a, q) and (j + q,
+// a - j) are equal only up to rounding; one thread writes both mirror entries with their mean, so no
+// entry is written twice with different values (which one landed would depend on warp scheduling).
 __global__ void k_write_T_block(double *T, int ldt, int m, int j, int p, const double *C1, const double *C2) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= m * p) return;
     int a = t / p, q = t % p;
     double v = C1[t] + C2[t];
+    if (a >= j && a < j + p) {
+        const int qa = a - j;
+        if (qa < q) return;  // written by the thread of the mirror entry
+        const int u = (j + q) * p + qa;
+        if (qa > q) v = 0.5 * (v + (C1[u] + C2[u]));
+    }
     T[(size_t)(j + q) * ldt + a] = v;
     T[(size_t)a * ldt + (j + q)] = v;
 }
@@ -774,11 +783,7 @@ void RefinedSolve::set_deflation(const double *U_, int ldu_, int k, cudaStream_t
     // A U, then E = U^T A U (k x k, row-major) and its inverse
     launch_spmv(sec, fz->sigma, U_, ldu_, 1, AU.data(), k, 1, k, st);
     dense_tn(n, U_, ldu_, 0, k, AU.data(), k, 0, k, Einv.data(), Dwork.data(), st);
-    static std::atomic<bool> attr{false};  // per process: one device
-    if (!attr) {
-        MBL_CUDA(cudaFuncSetAttribute(k_small_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, 90 * 90 * 8));
-        attr = true;
-    }
+    smem_limit((const void *)k_small_inverse, 90 * 90 * 8);
     k_small_inverse<<<1, 512, (size_t)k * k * sizeof(double), st>>>(k, Einv.data(), Dflag.data());
     MBL_LAUNCH_CHECK();
     int ok = 0;

@@ -90,6 +90,10 @@ void launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cuda
 struct Ctx;
 bool ctx_alive(const Ctx *c);
 
+// Raise kernel fn's dynamic shared-memory limit to `bytes` on the current device, once per
+// (kernel, device): function attributes are per device.
+void smem_limit(const void *fn, size_t bytes);
+
 // Device allocation accounted against the context budget (admission control).
 struct DevMem {
     void *p = nullptr;
@@ -170,6 +174,7 @@ struct Ctx {
     struct SolveBatcher *batcher = nullptr;  // a serving worker's solve batcher (batch.cu), shared
     int batch_max_jobs = 16;                 // server option: jobs per batched solve (1 = no batching)
     double batch_window_us = 300.0;          // server option: longest wait for the other workers
+    int batch_lanes = 2;                     // server option: streams of batched solves
     double cache_fraction = 0.25;            // server option: budget share of the live-factor cache
     cudaEvent_t take_event();
     void resolve_profile();

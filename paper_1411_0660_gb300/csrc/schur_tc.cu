@@ -485,14 +485,8 @@ void launch_schur_tma(const PanelStep &stp, const PanelDesc *d_descs, const int6
 
 void launch_schur_tc(const PanelStep &stp, const PanelDesc *d_descs, const Plan &p, float *arena, const float *wscr,
                      unsigned long long *err, cudaStream_t st, bool bf16) {
-    static std::atomic<bool> attr{false};  // per process: one device
-    if (!attr) {
-        MBL_CUDA(cudaFuncSetAttribute(k_schur_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)schur_tc_smem(false)));
-        MBL_CUDA(cudaFuncSetAttribute(k_schur_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)schur_tc_smem(true)));
-        attr = true;
-    }
+    smem_limit((const void *)k_schur_tc<false>, schur_tc_smem(false));
+    smem_limit((const void *)k_schur_tc<true>, schur_tc_smem(true));
     if (bf16)
         k_schur_tc<true><<<(unsigned)stp.n3t, THREADS, schur_tc_smem(true), st>>>(
             d_descs, stp.nd, p.d_sn_fo.data(), p.d_sn_f.data(), arena, wscr, err);

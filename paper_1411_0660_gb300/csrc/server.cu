@@ -381,7 +381,7 @@ int mbl_server_start(mbl_ctx *ctx, int slots, size_t budget_bytes) {
         }
         s->cache_limit = ctx->cache_fraction > 0.0 ? (size_t)(ctx->cache_fraction * (double)s->budget) : 0;
         if (ctx->batch_max_jobs > 1 && slots > 1) {
-            s->batcher = batcher_create(ctx->device, ctx->batch_max_jobs, ctx->batch_window_us);
+            s->batcher = batcher_create(ctx->device, ctx->batch_max_jobs, ctx->batch_window_us, ctx->batch_lanes);
             for (mbl_ctx *w : s->wctx) w->batcher = s->batcher;
         }
         MBL_CUDA(cudaEventCreate(&s->ref));
@@ -498,13 +498,14 @@ int mbl_server_cache(mbl_ctx *ctx, double fraction) {
     return MBL_OK;
 }
 
-int mbl_server_batching(mbl_ctx *ctx, int max_jobs, double window_us) {
+int mbl_server_batching(mbl_ctx *ctx, int max_jobs, double window_us, int lanes) {
     if (!ctx) return MBL_ERR_INVALID;
     if (ctx->server) return srv_report(ctx, MBL_ERR_INVALID, "set batching before mbl_server_start");
-    if (max_jobs < 1 || max_jobs > 64 || !(window_us >= 0.0 && window_us <= 1e6))
-        return srv_report(ctx, MBL_ERR_INVALID, "max_jobs in [1, 64], window_us in [0, 1e6]");
+    if (max_jobs < 1 || max_jobs > 64 || !(window_us >= 0.0 && window_us <= 1e6) || lanes < 1 || lanes > 8)
+        return srv_report(ctx, MBL_ERR_INVALID, "max_jobs in [1, 64], window_us in [0, 1e6], lanes in [1, 8]");
     ctx->batch_max_jobs = max_jobs;
     ctx->batch_window_us = window_us;
+    ctx->batch_lanes = lanes;
     return MBL_OK;
 }
 

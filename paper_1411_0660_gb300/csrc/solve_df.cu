@@ -301,20 +301,15 @@ size_t df_bwd_smem() { return bwd_tile_smem<T, PB>(); }
 template <class T, int PB>
 void df_sweeps(Factorization &fz, int p, cudaStream_t st) {
     Plan &pl = *fz.plan;
-    static std::atomic<bool> attr{false};  // per process: one device
-    static int grid_f = 0, grid_b = 0;
-    if (!attr) {
-        MBL_CUDA(cudaFuncSetAttribute(k_df_fwd<T, PB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)df_fwd_smem<T, PB>()));
-        MBL_CUDA(cudaFuncSetAttribute(k_df_bwd<T, PB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)df_bwd_smem<T, PB>()));
-        int of = 0, ob = 0;
-        MBL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&of, k_df_fwd<T, PB>, 256, df_fwd_smem<T, PB>()));
-        MBL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ob, k_df_bwd<T, PB>, 256, df_bwd_smem<T, PB>()));
-        grid_f = std::max(1, of) * fz.ctx->sm_count;
-        grid_b = std::max(1, ob) * fz.ctx->sm_count;
-        attr = true;
-    }
+    // the persistent sweeps wait on one another's CTAs: every CTA must be resident, so the grid is the
+    // occupancy of this device times its SM count
+    smem_limit((const void *)k_df_fwd<T, PB>, df_fwd_smem<T, PB>());
+    smem_limit((const void *)k_df_bwd<T, PB>, df_bwd_smem<T, PB>());
+    int of = 0, ob = 0;
+    MBL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&of, k_df_fwd<T, PB>, 256, df_fwd_smem<T, PB>()));
+    MBL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ob, k_df_bwd<T, PB>, 256, df_bwd_smem<T, PB>()));
+    const int grid_f = std::max(1, of) * fz.ctx->sm_count;
+    const int grid_b = std::max(1, ob) * fz.ctx->sm_count;
     const int ns = pl.ns;
     int32_t *cnt = fz.dfcnt.data();
     MBL_CUDA(cudaMemsetAsync(cnt, 0, ((size_t)4 * ns + 2) * sizeof(int32_t), st));

@@ -168,6 +168,25 @@ def test_bounds_factor_and_solves_are_bit_reproducible(g, ctx):
     sec.close()
 
 
+@pytest.mark.parametrize("L,h,seed,eps,prec", [(14, 1.0, 3, 0.5, 1), (14, 1.0, 3, 0.5, 0), (16, 5.0, 1023, 0.1, 1)])
+def test_solve_near_is_bit_reproducible(g, ctx, L, h, seed, eps, prec):
+    """Two whole shift-invert runs on the same sector, and a third on a freshly built copy of it,
+    return the same bits: eigenvalues, eigenvectors and residuals, and the same solve count.  Every
+    reduction of the Krylov layer (block Gram-Schmidt, the projected matrix, the small eigensolves,
+    the refinement's norms) sums in an order that does not depend on how CTAs or warps are scheduled."""
+    sec = g.build_sector(ctx, L, h, seed)
+    rs = [g.solve_near(sec, eps, 30, precision=prec) for _ in range(2)]
+    sec.close()
+    sec = g.build_sector(ctx, L, h, seed)
+    rs.append(g.solve_near(sec, eps, 30, precision=prec))
+    sec.close()
+    for r in rs[1:]:
+        assert r.stats["solves"] == rs[0].stats["solves"]
+        assert np.array_equal(r.evals.view(np.uint64), rs[0].evals.view(np.uint64))
+        assert np.array_equal(r.evecs.view(np.uint64), rs[0].evecs.view(np.uint64))
+        assert np.array_equal(r.resid.view(np.uint64), rs[0].resid.view(np.uint64))
+
+
 # ---------------------------------------------------------------- eigenpairs + observables ---
 def _reference(orc, H, L, eps, nev):
     """Oracle spectrum around sigma: the full dense spectrum up to L = 12, else the nev + 12
