@@ -585,6 +585,10 @@ def main():
     ap.add_argument("--batch-jobs", type=int, default=16, help="served form: jobs per batched solve launch (1: off)")
     ap.add_argument("--batch-window-us", type=float, default=300.0, help="served form: batcher collection window")
     ap.add_argument("--batch-lanes", type=int, default=2, help="served form: streams of batched solves")
+    ap.add_argument("--cache-fraction", type=float, default=0.0,
+                    help="served form: share of HBM keeping finished jobs' factorizations (0: off; the "
+                         "workload's realizations are all distinct, and the comparison arms rerun the "
+                         "same jobs, which a cache would answer from stored factorizations)")
     args = ap.parse_args()
     args.batch_case = args.case == "solve" and "--batch" in sys.argv
     if args.case == "observables":
@@ -655,7 +659,7 @@ def main():
         host_fields.append(np.ascontiguousarray(sec0.fields()))
         sec0.close()
     srv = g.Server(ctx, slots=args.slots, batch_jobs=args.batch_jobs, batch_window_us=args.batch_window_us,
-                   batch_lanes=args.batch_lanes)
+                   batch_lanes=args.batch_lanes, cache_fraction=args.cache_fraction)
     for t in [srv.submit(L, h, seed, eps, NEV) for (h, seed, eps) in jobs_for_step(0, args.slots, rank, world)]:
         srv.wait(t)  # worker warm-up: kernels loaded, graphs captured once per worker
     for t in [srv.submit(L, h, seed, eps, NEV, precision=g.MBL_PREC_FP64)

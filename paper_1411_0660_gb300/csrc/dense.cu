@@ -226,6 +226,7 @@ void chol_qr(int64_t n, double *X, int p, double *R, double *G, double *work, in
 // ------------------------------------------------------------------------------------------
 constexpr int EIG_THREADS = 512;
 constexpr int EIG_QL_MAX = 512;  // tridiagonal order kept in shared memory during the QL sweeps
+constexpr size_t EIG_SMEM_BYTES = 204800;  // dynamic shared memory of the batched eigensolver
 
 size_t syev_work_doubles(int mmax, bool vecs) {
     // d, e, beta, v, p, e^2 (8m with slack) [+ Z (m*m) + sort scratch (m*m) with eigenvectors]
@@ -366,7 +367,7 @@ __device__ void householder_tridiag(R *a, int lda, int m, R *beta, R *vv, R *pp,
 template <class R>
 __global__ void __launch_bounds__(EIG_THREADS) k_syev(const int *mv, const int64_t *aoff, const int64_t *woff,
                                                       double *Aall, double *Wall, int vecs, double *workall,
-                                                      size_t wstride, int *info, int smem_m) {
+                                                      size_t wstride, int *info, int smem_m, int zsm) {
     extern __shared__ __align__(16) unsigned char smraw[];
     R *sm = reinterpret_cast<R *>(smraw);
     __shared__ R red[EIG_THREADS / 32];
@@ -378,8 +379,10 @@ __global__ void __launch_bounds__(EIG_THREADS) k_syev(const int *mv, const int64
     R *work = reinterpret_cast<R *>(workall + (size_t)b * wstride);
     R *d = work, *e = work + m, *beta = work + 2 * m, *vv = work + 3 * m, *pp = work + 4 * m;
     R *e2 = work + 5 * m;
-    R *Z = work + 8 * m;                 // m x m
-    R *scr = Z + (size_t)m * m;          // m x m scratch
+    const bool in_smem = m <= smem_m;  // the launch's dynamic shared memory holds smem_m^2 entries
+    // the eigenvectors: in shared memory behind the matrix when the launch holds two of them (the
+    // QL rotations update Z one dependent row element after another), else in the work array
+    R *Z = (in_smem && zsm) ? sm + (size_t)smem_m * smem_m : work + 8 * m;
     if (threadIdx.x == 0 && info) info[b] = 0;
     if (m <= 0) return;
     if (m == 1) {
@@ -389,7 +392,6 @@ __global__ void __launch_bounds__(EIG_THREADS) k_syev(const int *mv, const int64
         }
         return;
     }
-    const bool in_smem = m <= smem_m;  // the launch's dynamic shared memory holds smem_m^2 entries
     R *a;
     if (in_smem) {
         a = sm;
@@ -441,11 +443,11 @@ __global__ void __launch_bounds__(EIG_THREADS) k_syev(const int *mv, const int64
         return;
     }
     // ---- 3. implicit QL on (d, e) accumulating Z (column-major m x m, starts as identity) ----
+    // the sweeps run on one thread as a chain of dependent updates of d, e and the rotation list:
+    // keep those in shared memory (global memory would put an L2 round trip in every link)
+    __shared__ R q_d[EIG_QL_MAX], q_e[EIG_QL_MAX], q_cs[EIG_QL_MAX], q_sn[EIG_QL_MAX];
+    R *cs = pp, *sn = vv;  // reuse the Householder scratch for the sweep's rotations
     {
-        // the sweeps run on one thread as a chain of dependent updates of d, e and the rotation list:
-        // keep those in shared memory (global memory would put an L2 round trip in every link)
-        __shared__ R q_d[EIG_QL_MAX], q_e[EIG_QL_MAX], q_cs[EIG_QL_MAX], q_sn[EIG_QL_MAX];
-        R *cs = pp, *sn = vv;  // reuse the Householder scratch for the sweep's rotations
         if (m <= EIG_QL_MAX) {
             for (int i = threadIdx.x; i < m; i += blockDim.x) {
                 q_d[i] = d[i];
@@ -520,13 +522,8 @@ __global__ void __launch_bounds__(EIG_THREADS) k_syev(const int *mv, const int64
         }
         __syncthreads();
         for (int j = threadIdx.x; j < m; j += blockDim.x) W[j] = (double)d[j];
-        for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
-            int c = t / m, r = t % m;
-            scr[t] = Z[(size_t)(int)cs[c] * m + r];
-        }
-        __syncthreads();
-        for (int t = threadIdx.x; t < m * m; t += blockDim.x) Z[t] = scr[t];
-        __syncthreads();
+        // the columns of Z are put in ascending order at the write-out (the back-transformation acts
+        // on each column alone)
     }
     // ---- 4. back-transformation y = H_0 ... H_{m-3} z, one warp per vector ----
     int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -546,7 +543,10 @@ __global__ void __launch_bounds__(EIG_THREADS) k_syev(const int *mv, const int64
         }
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < m * m; t += blockDim.x) Ag[t] = (double)Z[t];
+    for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
+        const int c = t / m, r = t - c * m;
+        Ag[t] = (double)Z[(size_t)(int)cs[c] * m + r];
+    }
 }
 
 // ------------------------------------------------------------------------------------------
@@ -773,11 +773,9 @@ cudaError_t syev_prepare_current_device() {
     std::lock_guard<std::mutex> lk(g_syev_mu);
     if (dev >= 0 && dev < 64 && g_syev_ready[dev]) return cudaSuccess;
     cudaFuncAttributes fa;
-    e = cudaFuncSetAttribute(k_syev<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             EIG_SMEM_MAX_M * EIG_SMEM_MAX_M * sizeof(double));
+    e = cudaFuncSetAttribute(k_syev<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EIG_SMEM_BYTES);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_syev<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 EIG_SMEM_MAX_M * EIG_SMEM_MAX_M * sizeof(float));
+        e = cudaFuncSetAttribute(k_syev<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EIG_SMEM_BYTES);
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_syev<double>);
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_syev<float>);
     if (e == cudaSuccess && dev >= 0 && dev < 64) g_syev_ready[dev] = true;
@@ -793,15 +791,20 @@ void syev_batched(int batch, const int *d_m, const int64_t *d_aoff, const int64_
     (void)d_sel;
     if (batch <= 0) return;
     MBL_CUDA(syev_prepare_current_device());
+    // the matrix in shared memory up to order 160; the eigenvectors beside it when both fit
+    const size_t mm = (size_t)mmax * mmax;
     if (fp32) {
         if (mmax > EIG_SMEM_MAX_M) fail(MBL_ERR_INVALID, "FP32 small eigensolver limited to order 160");
-        k_syev<float><<<batch, EIG_THREADS, (size_t)mmax * mmax * sizeof(float), st>>>(
-            d_m, d_aoff, d_woff, d_A, d_w, vecs, d_work, syev_work_doubles(mmax, vecs != 0), d_info, mmax);
+        const int zsm = vecs && 2 * mm * sizeof(float) <= EIG_SMEM_BYTES;
+        k_syev<float><<<batch, EIG_THREADS, (zsm ? 2 : 1) * mm * sizeof(float), st>>>(
+            d_m, d_aoff, d_woff, d_A, d_w, vecs, d_work, syev_work_doubles(mmax, vecs != 0), d_info, mmax, zsm);
     } else {
-        size_t smem = mmax <= EIG_SMEM_MAX_M ? (size_t)mmax * mmax * sizeof(double) : 0;
+        const bool sm = mmax <= EIG_SMEM_MAX_M;
+        const int zsm = sm && vecs && 2 * mm * sizeof(double) <= EIG_SMEM_BYTES;
+        const size_t smem = sm ? (zsm ? 2 : 1) * mm * sizeof(double) : 0;
         k_syev<double><<<batch, EIG_THREADS, smem, st>>>(d_m, d_aoff, d_woff, d_A, d_w, vecs, d_work,
                                                          syev_work_doubles(mmax, vecs != 0), d_info,
-                                                         mmax <= EIG_SMEM_MAX_M ? mmax : 0);
+                                                         sm ? mmax : 0, zsm);
     }
     MBL_LAUNCH_CHECK();
 }

@@ -333,9 +333,19 @@ static unsigned nblk(int64_t tot, int thr = 256) { return (unsigned)((tot + thr 
 // ------------------------------------------------------------------------------------------
 // Krylov-Schur engine
 // ------------------------------------------------------------------------------------------
+// dst[:, d0:d0+m] (FP32, row stride ldd) = src[:, s0:s0+m] (row stride lds)
+__global__ void k_cols_f32(int64_t n, const double *src, int lds, int s0, float *dst, int ldd, int d0, int m) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n * m) return;
+    const int64_t i = t / m;
+    const int j = (int)(t - i * m);
+    dst[i * ldd + d0 + j] = (float)src[i * lds + s0 + j];
+}
+
 KrylovSchur::KrylovSchur(Ctx *c, int64_t n_, int p_, int ncv_) : ctx(c), n(n_), p(p_), ncv(ncv_) {
     ldv = ncv + p;
     V.alloc(ctx, (size_t)n * ldv);
+    V32.alloc(ctx, (size_t)n * ldv);
     V2.alloc(ctx, (size_t)n * ldv);
     W.alloc(ctx, (size_t)n * p);
     T.alloc(ctx, (size_t)ldv * ldv);
@@ -398,6 +408,8 @@ void KrylovSchur::start(uint64_t seed, cudaStream_t st) {
         if (attempt == 3) fail(MBL_ERR_INVALID, "Krylov start block is rank deficient");
     }
     copy_cols(n, W.data(), p, 0, V.data(), ldv, 0, p, st);
+    k_cols_f32<<<nblk(n * p), 256, 0, st>>>(n, W.data(), p, 0, V32.data(), ldv, 0, p);
+    MBL_LAUNCH_CHECK();
     m = p;
 }
 
@@ -406,7 +418,11 @@ void KrylovSchur::expand(const OpFn &op, cudaStream_t st) {
     op(V.data() + j, ldv, W.data(), st);
     double *Vd = V.data();
     ProfScope ps(ctx, "orth", 8.0 * (double)n * m * p, st);
-    dense_tn(n, Vd, ldv, 0, m, W.data(), p, 0, p, C1.data(), work.data(), st);
+    // classical Gram-Schmidt twice.  The first pass's coefficients C1 = V^T W come from the FP32 copy
+    // of V in FP32 arithmetic (they only have to make the second pass's input nearly orthogonal);
+    // the subtraction W -= V C1 is FP64 on the FP64 basis, so that W = V (C1 + C2) + W' holds to FP64
+    // rounding whatever C1's error (the Krylov-Schur relation rests on it); the second pass is FP64
+    dense_tn32(n, V32.data(), ldv, 0, m, W.data(), p, 0, p, C1.data(), work.data(), st);
     dense_nn_sub(n, Vd, ldv, 0, m, C1.data(), p, W.data(), st);
     dense_tn(n, Vd, ldv, 0, m, W.data(), p, 0, p, C2.data(), work.data(), st);
     dense_nn_sub(n, Vd, ldv, 0, m, C2.data(), p, W.data(), st);
@@ -429,6 +445,8 @@ void KrylovSchur::expand(const OpFn &op, cudaStream_t st) {
         MBL_LAUNCH_CHECK();
     }
     copy_cols(n, W.data(), p, 0, V.data(), ldv, m, p, st);
+    k_cols_f32<<<nblk(n * p), 256, 0, st>>>(n, W.data(), p, 0, V32.data(), ldv, m, p);
+    MBL_LAUNCH_CHECK();
     m += p;
 }
 
@@ -503,6 +521,8 @@ void KrylovSchur::restart(const std::vector<int> &keep_idx, cudaStream_t st) {
     dense_nn(n, V.data(), ldv, mm, Y, k, V2.data(), ldv, 0, st);
     copy_cols(n, V.data(), ldv, mm, V2.data(), ldv, k, p, st);
     std::swap(V, V2);
+    k_cols_f32<<<nblk(n * (k + p)), 256, 0, st>>>(n, V.data(), ldv, 0, V32.data(), ldv, 0, k + p);
+    MBL_LAUNCH_CHECK();
     k_zero<<<nblk((int64_t)ldv * ldv), 256, 0, st>>>(T.data(), (int64_t)ldv * ldv);
     MBL_LAUNCH_CHECK();
     k_restart_T<<<nblk((int64_t)(k + p) * (k + p)), 256, 0, st>>>(T.data(), ldv, k, p, Gk, Bk.data());
@@ -1161,7 +1181,9 @@ void extremal_bounds(mbl_sector *sec, double *emin, double *emax) {
         MBL_LAUNCH_CHECK();
         std::swap(v, vprev);
         const int m = j + 1;
-        if ((m >= 16 && m % 8 == 0) || m == mmax) {
+        // convergence checks every 16 steps from m = 32: a check costs a bisection of T on one CTA,
+        // several times the Lanczos steps it could save
+        if ((m >= 32 && m % 16 == 0) || m == mmax) {
             k_tridiag_extremes<<<1, 64, 0, st>>>(m, alpha.data(), beta.data(), scr.data(), out.data());
             MBL_LAUNCH_CHECK();
             double h[4], bj;

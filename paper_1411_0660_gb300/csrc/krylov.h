@@ -18,6 +18,7 @@ struct KrylovSchur {
     int p, ncv, ldv;
     int m = 0;  // basis columns; the first m - p have been expanded
     DVec<double> V, V2, W, T, C1, C2, R1, R2, Rm, G, work, eigA, eigW, eigWork, res, SK, NS1, NS2, NS3, Ts, Bk;
+    DVec<float> V32;  // FP32 copy of V for the first Gram-Schmidt pass
     DVec<int> flag, eigInfo, eigM, keep;
     DVec<int64_t> eigOff;
 
