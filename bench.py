@@ -436,7 +436,7 @@ def run_workload(args):
                 eps ~ U[0.05, 0.95], nev = 50, mixed precision; p50/p99 latency and throughput;
     large    -- the large sizes: L = 20, h = 3, `--seeds` seeds x eps in {0.2, 0.5, 0.8}, nev = 50, mixed
                 precision through the server; plus the symbolic analysis (fill-in, flops, device
-                footprint) of L = 18, 20 and 22, whose L = 22 fronts do not fit in one GPU;
+                footprint) of L = 18, 20 and 22 (at L = 22 only the memory-lean fronts arena fits);
     odd      -- the odd-L sector of the numerical-method section at its largest size: L = 19 with
                 10 up spins (its "S^z = 1", dimension 92 378), h in {1, 3, 5} x `--seeds` seeds x
                 eps in {0.2, 0.5, 0.8}, nev = 50, mixed precision through the server."""
