@@ -371,7 +371,7 @@ __global__ void __launch_bounds__(EIG_THREADS) k_syev(const int *mv, const int64
     extern __shared__ __align__(16) unsigned char smraw[];
     R *sm = reinterpret_cast<R *>(smraw);
     __shared__ R red[EIG_THREADS / 32];
-    __shared__ R s_gl, s_gu, s_pivmin;
+    __shared__ R s_gl, s_gu, s_pivmin, s_atol;
     int b = blockIdx.x;
     int m = mv[b];
     double *Ag = Aall + aoff[b];
@@ -427,14 +427,18 @@ __global__ void __launch_bounds__(EIG_THREADS) k_syev(const int *mv, const int64
             s_gl = gl;
             s_gu = gu;
             s_pivmin = Num<R>::tiny() * fmax(R(1), emax2);
+            s_atol = R(2) * Num<R>::eps() * tn;
         }
         __syncthreads();
+        // every eigenvalue to an absolute accuracy of 2 eps ||T|| (LAPACK's choice of ABSTOL for
+        // eigenvalues to full accuracy relative to the norm): an eigenvalue near zero -- most of an
+        // entanglement spectrum -- is not bisected on to its own relative precision
         for (int j = threadIdx.x; j < m; j += blockDim.x) {
             R lo = s_gl, hi = s_gu;
             for (int it = 0; it < 200; ++it) {
                 R mid = R(0.5) * (lo + hi);
-                if (hi - lo <= R(2) * Num<R>::eps() * fmax(fabs(lo), fabs(hi)) + R(4) * s_pivmin || mid == lo ||
-                    mid == hi)
+                if (hi - lo <= R(2) * Num<R>::eps() * fmax(fabs(lo), fabs(hi)) + R(4) * s_pivmin || hi - lo <= s_atol ||
+                    mid == lo || mid == hi)
                     break;
                 if (sturm_count(m, d, e2, mid, s_pivmin) > j) hi = mid; else lo = mid;
             }
@@ -597,11 +601,13 @@ __global__ void k_bi_values(int m, const R *work, double *W) {
     const R tn = fmax(fabs(gl), fabs(gu)), eps = Num<R>::eps(), tiny = Num<R>::tiny();
     gl -= R(2) * eps * tn * (R)m + tiny;
     gu += R(2) * eps * tn * (R)m + tiny;
-    const R pivmin = tiny * fmax(R(1), emax2);
+    const R pivmin = tiny * fmax(R(1), emax2), atol = R(2) * eps * tn;  // absolute accuracy 2 eps ||T||
     R lo = gl, hi = gu;
     for (int it = 0; it < 200; ++it) {
         const R mid = R(0.5) * (lo + hi);
-        if (hi - lo <= R(2) * eps * fmax(fabs(lo), fabs(hi)) + R(4) * pivmin || mid == lo || mid == hi) break;
+        if (hi - lo <= R(2) * eps * fmax(fabs(lo), fabs(hi)) + R(4) * pivmin || hi - lo <= atol || mid == lo ||
+            mid == hi)
+            break;
         if (sturm_count<R>(m, d, e2, mid, pivmin) > j) hi = mid; else lo = mid;
     }
     W[j] = (double)(R(0.5) * (lo + hi));
