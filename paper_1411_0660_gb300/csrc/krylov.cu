@@ -1422,18 +1422,21 @@ void solve_near(mbl_sector *sec, double eps, int nev, const mbl_opts &o, double 
         ks.ritz(st, th, rn);
         int mm = (int)th.size();
         if (nudges < 3) {
-            // A shift within 1e-4 of the mean level spacing of an eigenvalue (a target exactly on
-            // one) makes that Ritz value of (H - sigma)^-1 dominate every solve: the refinement's
-            // backward-error bound scales with |x|, which that one component then sets, and the
-            // other components, the ones the iteration still needs, stay accurate to a few digits
-            // only.  Factor a tenth of a spacing away from that eigenvalue (an ordinary distance) and
-            // start again; the window is still chosen by distance to sigma, and the basis keeps more
-            // than nev Ritz pairs around the shift.  A shift that lands on another level moves again.
+            // A shift within 1e-2 of the mean level spacing s of an eigenvalue (a target exactly on
+            // one, or by chance close to one) makes that Ritz value of (H - sigma)^-1 dominate every
+            // solve: the refinement's backward-error bound scales with |x|, which that one component
+            // then sets, so the other components, the ones the iteration still needs, are accurate
+            // only to about refine_tol * s / distance relative to ||H||.  At 1e-4 s that floor is
+            // 1e-10 ||H||, the acceptance bound itself (an L = 16 job at 2.8e-4 s stalled there for
+            // 60 restarts with 39 of 50 pairs); at 1e-2 s it is 1e-12.  Factor a tenth of a spacing
+            // away from that eigenvalue (an ordinary distance) and start again; the window is still
+            // chosen by distance to sigma, and the basis keeps more than nev Ritz pairs around the
+            // shift.  A shift that lands on another level moves again.
             const double spacing = (emax - emin) / (double)n;
             double tmax = 0.0, tnear = 0.0;
             for (double t : th)
                 if (std::fabs(t) > tmax) tmax = std::fabs(t), tnear = t;
-            if (tmax * spacing > 1e4) {
+            if (tmax * spacing > 1e2) {
                 const double lam = sigma_f + 1.0 / tnear;  // the eigenvalue the shift sits on
                 const double side = (sigma_f >= lam ? 1.0 : -1.0) * (nudges == 1 ? -1.0 : 1.0);
                 sigma_f = lam + side * (0.1 + 0.05 * nudges) * spacing;
