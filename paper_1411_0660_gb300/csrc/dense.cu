@@ -279,13 +279,25 @@ __device__ int sturm_count(int m, const R *d, const R *e2, R x, R pivmin) {
 // One implicit QL sweep on the unreduced block lo..hi of (d, e), recording the rotations:
 // T <- J^T T J with J = [[c, s], [-s, c]] in planes (hi-1, hi), ..., (lo, lo+1); the first rotation
 // zeroes the upper entry of the last column of T - mu I, the others chase the bulge upward.
+//
+// The sweep is one dependent chain, so the entries it carries from one rotation to the next (the
+// updated d[k + 1] and e[k], and the chased pair x, z) stay in registers: each rotation loads only the
+// entries it meets for the first time, d[k] and e[k - 1], one rotation ahead, and stores each final
+// value once.  The arithmetic, and so every result, is the same as with d and e updated in place.
 template <class R>
 __device__ void ql_sweep_record(int lo, int hi, R *d, R *e, R *cs, R *sn) {
     R delta = R(0.5) * (d[lo + 1] - d[lo]);
     R b = e[lo];
     R mu = d[lo] - b * b / (delta + copysign(hypot(delta, b), delta));
-    R x = d[hi] - mu, z = e[hi - 1];
+    R dk1 = d[hi];      // d[k + 1] as the sweep has left it
+    R ek = e[hi - 1];   // e[k] as the sweep has left it
+    R x = dk1 - mu, z = ek;
+    R a = d[hi - 1];                          // d[k], not touched yet
+    R em = hi - 1 > lo ? e[hi - 2] : R(0);    // e[k - 1], not touched yet
     for (int k = hi - 1; k >= lo; --k) {
+        // the entries the next rotation meets first
+        const R a_next = k > lo ? d[k - 1] : R(0);
+        const R em_next = k - 1 > lo ? e[k - 2] : R(0);
         R r = hypot(x, z);
         R c = R(1), s = R(0);
         if (r != R(0)) {
@@ -294,19 +306,26 @@ __device__ void ql_sweep_record(int lo, int hi, R *d, R *e, R *cs, R *sn) {
             s = z * ir;
         }
         if (k < hi - 1) e[k + 1] = r;
-        R a = d[k], bb = e[k], dd = d[k + 1];
-        d[k] = a * c * c - R(2) * bb * c * s + dd * s * s;
+        const R bb = ek, dd = dk1;
+        const R dk = a * c * c - R(2) * bb * c * s + dd * s * s;
         d[k + 1] = a * s * s + R(2) * bb * c * s + dd * c * c;
-        e[k] = (a - dd) * c * s + bb * (c * c - s * s);
+        const R ekn = (a - dd) * c * s + bb * (c * c - s * s);
         if (k > lo) {
-            R bulge = s * e[k - 1];
-            e[k - 1] = c * e[k - 1];
-            x = e[k];
+            const R bulge = s * em;
+            ek = c * em;  // e[k - 1] after this rotation: the next rotation's e[k]
+            x = ekn;
             z = bulge;
+            e[k] = ekn;   // final unless the next rotation overwrites it with its r
+        } else {
+            e[k] = ekn;
         }
+        dk1 = dk;  // the next rotation's d[k + 1]
+        a = a_next;
+        em = em_next;
         cs[k] = c;
         sn[k] = s;
     }
+    d[lo] = dk1;
 }
 
 // Householder reduction of the symmetric m x m matrix a (column-major, lower triangle used, leading
@@ -499,13 +518,21 @@ __global__ void __launch_bounds__(EIG_THREADS) k_syev(const int *mv, const int64
                 int lo = s_lo, hi = s_hi;
                 // Z is column-major (column k contiguous): thread r walks its row down the sweep,
                 // carrying the rotated entry of column k + 1; accesses coalesce across threads
+                // (the next rotation's inputs are loaded before this one's store, which the compiler
+                // could not otherwise move ahead of it: Z and the rotation list might alias)
                 for (int r = threadIdx.x; r < m; r += blockDim.x) {
                     R a1 = Z[(size_t)hi * m + r];
+                    R a0 = Z[(size_t)(hi - 1) * m + r];
+                    R c = cs[hi - 1], sv = sn[hi - 1];
                     for (int k = hi - 1; k >= lo; --k) {
-                        const R c = cs[k], sv = sn[k];
-                        const R a0 = Z[(size_t)k * m + r];
+                        const bool more = k > lo;
+                        const R a0n = more ? Z[(size_t)(k - 1) * m + r] : R(0);
+                        const R cn = more ? cs[k - 1] : R(0), svn = more ? sn[k - 1] : R(0);
                         Z[(size_t)(k + 1) * m + r] = sv * a0 + c * a1;
                         a1 = c * a0 - sv * a1;
+                        a0 = a0n;
+                        c = cn;
+                        sv = svn;
                     }
                     Z[(size_t)lo * m + r] = a1;
                 }
