@@ -786,6 +786,87 @@ __global__ void k_cols_to_f32(int64_t n, const double *src, int lds, int k, floa
     dst[t] = (float)src[i * lds + (t - i * k)];
 }
 
+// ---- deflation products: tall-skinny products with the FP32 copies U32, AU32 (n x kd, kd <= 90) ----
+constexpr int DEFL_ROWS = 256;  // rows per CTA of k_defl_tn
+
+// part[b][a][q] = sum over the block's rows r of U[r][a] V[r][q] (FP32 arithmetic, V converted): thread
+// a of the CTA owns column a of U (coalesced row reads), the block's rows of V are staged in shared
+// memory and read as broadcasts.
+template <int PB>
+__global__ void __launch_bounds__(128) k_defl_tn(int64_t n, int kd, int p, const float *__restrict__ U,
+                                                const double *__restrict__ V, double *__restrict__ part) {
+    __shared__ float sv[DEFL_ROWS * PB];
+    const int64_t r0 = (int64_t)blockIdx.x * DEFL_ROWS;
+    const int nr = (int)min((int64_t)DEFL_ROWS, n - r0);
+    for (int e = threadIdx.x; e < nr * PB; e += blockDim.x) {
+        const int r = e / PB, q = e - r * PB;
+        sv[e] = q < p ? (float)V[(r0 + r) * p + q] : 0.f;
+    }
+    __syncthreads();
+    const int a = threadIdx.x;
+    if (a >= kd) return;
+    float acc[PB];
+#pragma unroll
+    for (int q = 0; q < PB; ++q) acc[q] = 0.f;
+    const float *u = U + r0 * kd + a;
+    for (int r = 0; r < nr; ++r) {
+        const float ur = u[(int64_t)r * kd];
+#pragma unroll
+        for (int q = 0; q < PB; ++q) acc[q] = fmaf(ur, sv[r * PB + q], acc[q]);
+    }
+    double *out = part + ((size_t)blockIdx.x * kd + a) * p;
+#pragma unroll
+    for (int q = 0; q < PB; ++q)
+        if (q < p) out[q] = (double)acc[q];
+}
+
+// c = Einv C (kd x p, row-major) with C = sum over the nb blocks of part, in block order; one CTA.
+__global__ void __launch_bounds__(1024) k_defl_coef(int nb, int kd, int p, const double *__restrict__ part,
+                                                    const double *__restrict__ Einv, double *__restrict__ c) {
+    __shared__ double sc[90 * 32];
+    const int kp = kd * p;
+    for (int o = threadIdx.x; o < kp; o += blockDim.x) {
+        double s = 0.0;
+        for (int b = 0; b < nb; ++b) s += part[(size_t)b * kp + o];
+        sc[o] = s;
+    }
+    __syncthreads();
+    for (int o = threadIdx.x; o < kp; o += blockDim.x) {
+        const int a = o / p, q = o - a * p;
+        double s = 0.0;
+        for (int k = 0; k < kd; ++k) s = fma(Einv[(size_t)a * kd + k], sc[k * p + q], s);
+        c[o] = s;
+    }
+}
+
+// Xout[r][q] = Xin[r][q] + sign * sum_a U[r][a] c[a][q] (the sum in FP32): a thread per row, c staged
+// in shared memory.  Xin may be Xout.
+template <int PB>
+__global__ void __launch_bounds__(128) k_defl_apply(int64_t n, int kd, int p, const float *__restrict__ U,
+                                                   const double *__restrict__ c, const double *Xin, double *Xout,
+                                                   double sign) {
+    __shared__ float scf[90 * PB];
+    for (int e = threadIdx.x; e < kd * PB; e += blockDim.x) {
+        const int a = e / PB, q = e - a * PB;
+        scf[e] = q < p ? (float)c[a * p + q] : 0.f;
+    }
+    __syncthreads();
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    float acc[PB];
+#pragma unroll
+    for (int q = 0; q < PB; ++q) acc[q] = 0.f;
+    const float *u = U + r * kd;
+    for (int a = 0; a < kd; ++a) {
+        const float ua = u[a];
+#pragma unroll
+        for (int q = 0; q < PB; ++q) acc[q] = fmaf(ua, scf[a * PB + q], acc[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < PB; ++q)
+        if (q < p) Xout[r * p + q] = Xin[r * p + q] + sign * (double)acc[q];
+}
+
 void RefinedSolve::set_deflation(const double *U_, int ldu_, int k, cudaStream_t st) {
     kd = 0;
     if (k <= 0) return;
@@ -794,9 +875,11 @@ void RefinedSolve::set_deflation(const double *U_, int ldu_, int k, cudaStream_t
     Ctx *ctx = sec->ctx;
     if (AU.size() < (size_t)n * k) AU.alloc(ctx, (size_t)n * k);
     if (Einv.size() < (size_t)k * k) Einv.alloc(ctx, (size_t)k * k);
-    if (Dc0.size() < (size_t)k * 32) Dc0.alloc(ctx, (size_t)k * 32);
     if (Dc1.size() < (size_t)k * 32) Dc1.alloc(ctx, (size_t)k * 32);
-    if (Dwork.size() < dense_tn_work(n, k, std::max(k, 32)) + 64) Dwork.alloc(ctx, dense_tn_work(n, k, std::max(k, 32)) + 64);
+    // Dwork: E's partial sums (dense_tn), then the deflation products' per-block partial sums
+    const size_t dwork = std::max(dense_tn_work(n, k, std::max(k, 32)),
+                                  (size_t)((n + DEFL_ROWS - 1) / DEFL_ROWS) * (size_t)k * 32) + 64;
+    if (Dwork.size() < dwork) Dwork.alloc(ctx, dwork);
     if (Dflag.size() < 1) Dflag.alloc(ctx, 1);
     if (U32.size() < (size_t)n * k) U32.alloc(ctx, (size_t)n * k);
     if (AU32.size() < (size_t)n * k) AU32.alloc(ctx, (size_t)n * k);
@@ -824,18 +907,30 @@ void RefinedSolve::precondition(const double *V, double *Z, int p, cudaStream_t 
     }
     const int64_t n = sec->n;
     if (Dt.size() < (size_t)n * p) Dt.alloc(sec->ctx, (size_t)n * p);
+    const unsigned nbd = (unsigned)((n + DEFL_ROWS - 1) / DEFL_ROWS);
+    const int pb = p <= 8 ? 8 : (p <= 16 ? 16 : 32);
+    auto apply = [&](const float *Uf, const double *Xin, double *Xout, double sign) {
+        const unsigned g = nblk(n, 128);
+        if (pb == 8) k_defl_apply<8><<<g, 128, 0, st>>>(n, kd, p, Uf, Dc1.data(), Xin, Xout, sign);
+        else if (pb == 16) k_defl_apply<16><<<g, 128, 0, st>>>(n, kd, p, Uf, Dc1.data(), Xin, Xout, sign);
+        else k_defl_apply<32><<<g, 128, 0, st>>>(n, kd, p, Uf, Dc1.data(), Xin, Xout, sign);
+        MBL_LAUNCH_CHECK();
+    };
     {
         ProfScope ps(sec->ctx, "gm_deflate", 0.0, st);
         // c = E^-1 U^T v  (kd x p, row-major)
-        dense_tn32(n, U32.data(), kd, 0, kd, V, p, 0, p, Dc0.data(), Dwork.data(), st);
-        gemm_small(false, false, p, kd, kd, 1.0, Dc0.data(), p, Einv.data(), kd, 0.0, Dc1.data(), p, st);
+        if (pb == 8) k_defl_tn<8><<<nbd, 128, 0, st>>>(n, kd, p, U32.data(), V, Dwork.data());
+        else if (pb == 16) k_defl_tn<16><<<nbd, 128, 0, st>>>(n, kd, p, U32.data(), V, Dwork.data());
+        else k_defl_tn<32><<<nbd, 128, 0, st>>>(n, kd, p, U32.data(), V, Dwork.data());
+        MBL_LAUNCH_CHECK();
+        k_defl_coef<<<1, 1024, 0, st>>>((int)nbd, kd, p, Dwork.data(), Einv.data(), Dc1.data());
+        MBL_LAUNCH_CHECK();
         // z = M^-1 (v - A U c) + U c
-        dense_nn_sub32(n, AU32.data(), kd, 0, kd, Dc1.data(), p, V, Dt.data(), st);
+        apply(AU32.data(), V, Dt.data(), -1.0);
     }
     factor_solve_raw(*fz, Dt.data(), p, Z, p, p, false, st);
     ProfScope ps(sec->ctx, "gm_deflate", 0.0, st);
-    gemm_small(false, false, p, kd, kd, -1.0, Dc0.data(), p, Einv.data(), kd, 0.0, Dc1.data(), p, st);
-    dense_nn_sub32(n, U32.data(), kd, 0, kd, Dc1.data(), p, Z, Z, st);
+    apply(U32.data(), Z, Z, 1.0);
 }
 
 void RefinedSolve::apply_fgmres(const double *X, int ldx, double *Y, int p, cudaStream_t st) {
