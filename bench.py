@@ -108,16 +108,16 @@ def measured_peaks():
 
 
 # --------------------------------------------------------------------------------------------
-def oracle_l18_scale():
-    """Ratio (mean oracle seconds per L = 16 job) / (mean per L = 18 job) of the stored oracle runs in
+def oracle_l18_scale(Ls: int = 16):
+    """Ratio (mean oracle seconds per L = Ls job) / (mean per L = 18 job) of the stored oracle runs in
     tests/golden (same oracle, one core each, jobs of the L = 18 workload's shape): an L = 18 oracle job
-    takes about half an hour, so the L = 18 rate is the timed L = 16 rate times this ratio."""
+    takes about half an hour, so the L = 18 rate is the timed L = Ls rate times this ratio."""
     t = {}
-    for L_ in (16, 18):
+    for L_ in (Ls, 18):
         with open(os.path.join(ROOT, "tests", "golden", f"oracle_L{L_}.json")) as f:
             js = json.load(f)["jobs"]
         t[L_] = sum(j["oracle_seconds"] for j in js) / len(js)
-    return t[16] / t[18], t[16], t[18]
+    return t[Ls] / t[18], t[Ls], t[18]
 
 
 def _oracle_pool_rate(pool, jobs):
@@ -127,10 +127,12 @@ def _oracle_pool_rate(pool, jobs):
 
 
 def run_reference(args):
-    """The oracle as it stands on the host cores.  Each timed step runs one L = 16 job of the L = 18
-    workload's shape per core (a bounded sample: an L = 18 oracle job takes about half an hour); the
-    reported value is that rate carried to L = 18 by the stored oracle timings (oracle_l18_scale),
-    labelled as extrapolated, with the measured L = 16 rate beside it."""
+    """The oracle as it stands on the host cores.  Each timed step runs one job of the L = 18 workload's
+    shape per core at a smaller size (a bounded sample: an L = 18 oracle job takes about half an hour):
+    L = 16 (about 30 s a step) for up to 5 steps, L = 14 (about 1.5 s) for more, so that the whole run
+    ends within a few minutes.  The reported value is that rate carried to L = 18 by the stored oracle
+    timings of the same shapes (oracle_l18_scale), labelled as extrapolated, with the measured rate
+    beside it."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
@@ -141,29 +143,30 @@ def run_reference(args):
     per_step = max(1, cores)
     t_steps = []
     pairs = 0
+    Lsample = 16 if args.steps <= 5 else 14
     with ctx.Pool(cores) as pool:
         for s in range(args.warmup + args.steps):
             # warm-up steps only start the workers (imports, oracle library load): one L=12 job each
-            Ls = 16 if s >= args.warmup else 12
-            jobs = [(Ls, h, seed, eps, NEV if Ls == 16 else 20) for (h, seed, eps) in jobs_for_step(s, per_step)]
+            Ls = Lsample if s >= args.warmup else 12
+            jobs = [(Ls, h, seed, eps, NEV if Ls == Lsample else 20) for (h, seed, eps) in jobs_for_step(s, per_step)]
             p, dt = _oracle_pool_rate(pool, jobs)
             if s >= args.warmup:
                 t_steps.append(dt)
                 pairs += p
     tot = sum(t_steps)
     v16 = pairs / tot
-    scale, t16, t18 = oracle_l18_scale()
+    scale, t16, t18 = oracle_l18_scale(Lsample)
     v = v16 * scale
     cpu = {"value": v, "unit": "eigenpairs/s", "cores": cores, "kind": "oracle",
-           "sample": f"{per_step * args.steps} oracle shift-invert jobs at L=16 (one per core, nev=50) timed: "
-                     f"{v16:.3f} eigenpairs/s; carried to L=18 by the stored oracle seconds per job "
-                     f"(L=16 {t16:.1f} s, L=18 {t18:.0f} s, ratio {scale:.4f}): extrapolated",
-           "value_l16_measured": v16, "extrapolated": True}
+           "sample": f"{per_step * args.steps} oracle shift-invert jobs at L={Lsample} (one per core, nev=50) "
+                     f"timed: {v16:.3f} eigenpairs/s; carried to L=18 by the stored oracle seconds per job "
+                     f"(L={Lsample} {t16:.1f} s, L=18 {t18:.0f} s, ratio {scale:.5f}): extrapolated",
+           f"value_l{Lsample}_measured": v16, "extrapolated": True}
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "eigenpairs/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "L": L, "nev": NEV, "jobs_per_step": per_step,
-                       "sample_L": 16, "extrapolated_to_L": 18},
+                       "sample_L": Lsample, "extrapolated_to_L": 18},
             "cpu_baseline": cpu,
             "e2e": {"value": v, "unit": "eigenpairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))

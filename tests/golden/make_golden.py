@@ -1,9 +1,10 @@
-"""Write oracle results for sizes the oracle cannot redo inside a test (L = 16, 18).
+"""Write oracle results for sizes the oracle cannot redo inside a test (L = 14, 16, 18).
 
 Calls only the CPU oracle (oracle/); nothing here comes from the GPU path.  Each job is
 (L, h, seed, eps, nev); the file keeps E_min, E_max, sigma, the nev eigenvalues nearest sigma,
 their residuals, the gap ratios and S_1^P / S^E of each eigenvector.  Run:
 
+    python tests/golden/make_golden.py L14        # 9 jobs, seconds
     python tests/golden/make_golden.py L16        # 9 jobs, minutes
     python tests/golden/make_golden.py L18        # 3 jobs, about an hour each on one core
 """
@@ -17,6 +18,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
 
 SETS = {
+    # the same shape at L=14 (the reference arm's per-step sample when many steps are asked for)
+    "L14": [(14, h, 0, eps, 50) for h in (1.0, 2.5, 4.0) for eps in (0.1, 0.5, 0.9)],
     # the batched L=16 workload shape: h in {1, 2.5, 4}, eps in {0.1, 0.5, 0.9}, nev = 50
     "L16": [(16, h, 0, eps, 50) for h in (1.0, 2.5, 4.0) for eps in (0.1, 0.5, 0.9)],
     # the L=18 workload shape: h in {0.5, 3, 5}, eps in {0.1, 0.5, 0.9}, nev = 50

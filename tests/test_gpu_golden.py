@@ -1,9 +1,10 @@
 """GPU path versus stored oracle results at the workload sizes (needs a GB300).
 
-tests/golden/oracle_L16.json and oracle_L18.json were written by tests/golden/make_golden.py from
+tests/golden/oracle_L14.json, oracle_L16.json and oracle_L18.json were written by
+tests/golden/make_golden.py from
 the CPU oracle alone (minimum-degree LDL^T shift-invert Lanczos, Rayleigh-Ritz on H).  The GPU
 runs the same jobs in the configuration the benchmark times (FP32 fronts with FP64 refinement,
-block 8) and, at L=18, also with FP64 fronts.  Tolerances as in parity.py: sigma and eigenvalues
+block 8) and, at L = 14 and 18, also with FP64 fronts.  Tolerances as in parity.py: sigma and eigenvalues
 within 1e-10 ||H||, the same window (edge ties accepted), residuals <= 1e-10 ||H||, gap ratios
 within 1e-8 and entropies within 1e-8 for eigenvectors that are well conditioned by the oracle's
 recomputed residuals.  At L = 18 the further observables (KL, S_2^P, F, f) of the solved vectors
@@ -27,7 +28,8 @@ def _jobs(name):
         return json.load(f)["jobs"]
 
 
-CASES = [(j, 1) for j in _jobs("L16")] + [(j, p) for j in _jobs("L18") for p in (1, 0)]
+CASES = ([(j, p) for j in _jobs("L14") for p in (1, 0)] + [(j, 1) for j in _jobs("L16")] +
+         [(j, p) for j in _jobs("L18") for p in (1, 0)])
 
 
 @pytest.fixture(scope="module")
