@@ -50,6 +50,18 @@ BREAKDOWN = ("factor_fp32", "schur_tc", "f_panel", "f_build_g", "trisolve_fp32",
              "gm_spmv", "orth", "syev_krylov", "syev_rr", "ritz_h", "extremal_bounds", "observables")
 
 
+def reduce_over_ranks(ms: float, pairs: int, dist, device: str = "cuda"):
+    """Whole-job figures of a multi-rank run: the slowest rank's span (MAX) and the converged pairs of
+    all ranks (SUM), through torch.distributed collectives on `device`."""
+    import torch
+
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    tt = torch.tensor([float(pairs)], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.SUM)
+    return float(t[0]), int(tt[0])
+
+
 def jobs_for_step(step: int, batch: int, rank: int = 0, world: int = 1):
     out = []
     for b in range(batch):
@@ -695,11 +707,7 @@ def main():
     t_host = main_run["host_s"]
     tmax = ms
     if dist:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tt = torch.tensor([float(pairs)], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.SUM)
-        tmax, pairs = float(t[0]), int(tt[0])
+        tmax, pairs = reduce_over_ranks(ms, pairs, dist, "cuda")
     value = pairs / (tmax / 1e3)
     served_res = main_run.pop("results")
 
