@@ -75,7 +75,8 @@ def collapse_fit(L, h, Q, dQ, w: float = 0.8, L_min: float = 0, hc_range=(1.0, 6
                  deg: int = 3):
     """Best (h_c, nu) of the ansatz Q = g[(h - h_c) L^(1/nu)], g a polynomial of degree `deg` fitted in
     the window |h - h_c| <= w over the sizes L >= L_min, by minimizing the weighted misfit per degree
-    of freedom: a grid over (h_c, nu), then two finer grids around the best point."""
+    of freedom: a grid over (h_c, nu) in the given ranges, then two finer grids around the best point
+    (within the ranges; a best point on a range's edge means the data do not fix that parameter)."""
     L, h, Q, dQ = (np.asarray(a, dtype=np.float64) for a in (L, h, Q, dQ))
     keep = (L >= L_min) & np.isfinite(Q) & np.isfinite(dQ) & (dQ > 0)
     L, h, Q, dQ = L[keep], h[keep], Q[keep], dQ[keep]
@@ -96,8 +97,9 @@ def collapse_fit(L, h, Q, dQ, w: float = 0.8, L_min: float = 0, hc_range=(1.0, 6
                     best = (s, float(hc), float(nu))
         if best[1] is None:
             break
-        hc_lo, hc_hi = best[1] - 5 * hstep, best[1] + 5 * hstep
-        nu_lo, nu_hi = max(0.05, best[2] - 5 * nstep), best[2] + 5 * nstep
+        # finer grids around the best point, within the given ranges
+        hc_lo, hc_hi = max(hc_range[0], best[1] - 5 * hstep), min(hc_range[1], best[1] + 5 * hstep)
+        nu_lo, nu_hi = max(nu_range[0], best[2] - 5 * nstep), min(nu_range[1], best[2] + 5 * nstep)
     if best[1] is None:
         raise ValueError("collapse_fit: too few points in the window")
     c2, npts, coef = _chi2(best[1], best[2], L, h, Q, dQ, w, deg)
