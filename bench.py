@@ -194,6 +194,18 @@ def _oracle_job(job):
     return int((r.resid <= 1e-10 * hn).sum())
 
 
+def _round_floats(x, sig: int = 6):
+    """The line's floats to `sig` significant digits (the line stays under about 3 KB; the detail file
+    keeps full precision)."""
+    if isinstance(x, float):
+        return float(f"{x:.{sig}g}") if math.isfinite(x) else x
+    if isinstance(x, dict):
+        return {k: _round_floats(v, sig) for k, v in x.items()}
+    if isinstance(x, list):
+        return [_round_floats(v, sig) for v in x]
+    return x
+
+
 def cpu_baseline_sample():
     """Oracle on the host cores: one L = 16 job of the workload's shape per core (about 20-35 s),
     carried to L = 18 by the stored oracle timings and labelled as extrapolated."""
@@ -701,7 +713,8 @@ def main():
     launches = g.launch_count() - l0
     srv_stats = srv.stats()
     # the batched solves of the timed region (CUDA events around each batch on the batcher's stream)
-    served_solve = {k: srv_stats[k] - b0[k] for k in ("solve_batches", "batched_solves", "batch_ms", "batch_bytes")}
+    served_solve = {k: srv_stats[k] - b0[k]
+                    for k in ("solve_batches", "batched_solves", "batch_ms", "batch_bytes", "batch_busy_ms")}
     ms = main_run["span_ms"]
     pairs = main_run["pairs"]
     t_host = main_run["host_s"]
@@ -858,6 +871,11 @@ def main():
                 "kernel": "trisolve_fp32 batched (served, timed region)", "launch_ms": per_launch_ms,
                 "work_per_launch": per_launch_work, "jobs_per_launch": kmean, "launches": nb,
                 "sequential": roof_seq}
+        if served_solve["batch_busy_ms"] > 0:
+            # all batches' bytes over the time during which at least one was executing: the lanes'
+            # batches overlap, so this is the class's aggregate rate, where `achieved` is per launch
+            agg = served_solve["batch_bytes"] / (served_solve["batch_busy_ms"] / 1e3) / 1e9
+            roof["aggregate"] = {"achieved": agg, "frac": agg / peak, "busy_ms": served_solve["batch_busy_ms"]}
 
     if rank == 0:
         nj = len(cmp_jobs)
@@ -899,7 +917,7 @@ def main():
         except OSError:
             line["detail"] = None
         sys.stdout.flush()
-        print(json.dumps(line), flush=True)
+        print(json.dumps(_round_floats(line)), flush=True)
     if dist:
         dist.destroy_process_group()
     return 0

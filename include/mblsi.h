@@ -376,6 +376,9 @@ typedef struct mbl_server_stats {
                                 sweeps plus the right-hand sides, 2 (nnz_L + n) w + 16 n p */
     int64_t cache_hits;      /* requests served with a cached live factorization */
     size_t cache_bytes;      /* device bytes the cache holds now */
+    double batch_busy_ms;    /* time during which at least one batch was executing (the union of the
+                                batches' intervals; batches on different lanes overlap, so batch_ms
+                                can exceed it) */
 } mbl_server_stats;
 
 /* Residency of live factorizations (set before mbl_server_start; default fraction 0.25, 0 = off).

@@ -74,7 +74,7 @@ class ServerStats(ctypes.Structure):
                 ("queued", c_int), ("slots", c_int), ("budget_bytes", c_size_t), ("reserved_bytes", c_size_t),
                 ("peak_reserved_bytes", c_size_t), ("solve_batches", c_int64), ("batched_solves", c_int64),
                 ("batch_ms", c_double), ("batch_bytes", c_double), ("cache_hits", c_int64),
-                ("cache_bytes", c_size_t)]
+                ("cache_bytes", c_size_t), ("batch_busy_ms", c_double)]
 
 
 # (name, restype, argtypes); every entry point of include/mblsi.h

@@ -98,6 +98,12 @@ struct SolveBatcher {
     double ms = 0.0, bytes = 0.0;
     std::vector<Timing> timing;
     std::vector<cudaEvent_t> ev_pool;
+    // the union of the batches' intervals: start and end of each resolved batch relative to the first
+    // batch of the current window (wref, its start event), merged when the window closes
+    cudaEvent_t wref = nullptr;
+    std::vector<std::pair<float, float>> ivals;
+    double busy_ms = 0.0;
+    void close_window();
 
     Group &group(const Plan *pl, int prec, int p) {
         auto &g = groups[std::make_tuple(pl, prec, p)];
@@ -136,11 +142,32 @@ void SolveBatcher::resolve(bool wait) {
         MBL_CUDA(cudaEventElapsedTime(&m, t.e0, t.e1));
         ms += m;
         bytes += t.bytes;
-        ev_pool.push_back(t.e0);
+        float a = 0.f;
+        if (!wref) wref = t.e0;  // kept (not returned to the pool) until the window closes
+        else MBL_CUDA(cudaEventElapsedTime(&a, wref, t.e0));
+        ivals.emplace_back(a, a + m);
+        if (t.e0 != wref) ev_pool.push_back(t.e0);
         ev_pool.push_back(t.e1);
     }
     (void)cudaGetLastError();  // a cudaEventQuery of unfinished work reports cudaErrorNotReady
     timing.erase(timing.begin(), timing.begin() + (ptrdiff_t)k);
+}
+
+void SolveBatcher::close_window() {
+    std::sort(ivals.begin(), ivals.end());
+    double end = -1e300;
+    for (const auto &iv : ivals) {
+        if (iv.first > end) {
+            busy_ms += iv.second - iv.first;
+            end = iv.second;
+        } else if (iv.second > end) {
+            busy_ms += iv.second - end;
+            end = iv.second;
+        }
+    }
+    ivals.clear();
+    if (wref) ev_pool.push_back(wref);
+    wref = nullptr;
 }
 
 // The graph of the batched launch sequence for k jobs on lane `li` (tables at the lane's tab / io).
@@ -379,6 +406,7 @@ void batcher_destroy(SolveBatcher *b) {
     for (cudaStream_t s : b->streams) cudaStreamSynchronize(s);  // the completion callbacks too
     try {
         b->resolve(true);
+        b->close_window();
     } catch (...) {
     }
     for (cudaEvent_t e : b->ev_pool) cudaEventDestroy(e);
@@ -399,13 +427,15 @@ void batcher_destroy(SolveBatcher *b) {
     delete b;
 }
 
-void batcher_stats(SolveBatcher *b, int64_t *batches, int64_t *solves, double *ms, double *bytes) {
+void batcher_stats(SolveBatcher *b, int64_t *batches, int64_t *solves, double *ms, double *bytes, double *busy_ms) {
     std::lock_guard<std::mutex> lk(b->tmu);
     b->resolve(true);
+    b->close_window();
     *batches = b->batches;
     *solves = b->solves;
     *ms = b->ms;
     *bytes = b->bytes;
+    *busy_ms = b->busy_ms;
 }
 
 }  // namespace mbl

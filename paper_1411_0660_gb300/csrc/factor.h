@@ -104,7 +104,7 @@ void batcher_leave(SolveBatcher *b, const Plan *pl, int prec, int p);
 SolveBatcher *batcher_create(int device, int max_jobs, double window_us, int lanes);
 void batcher_destroy(SolveBatcher *b);  // after every worker using it has stopped
 // Launched batches, solves in them, their device time (CUDA events) and algorithmic bytes.
-void batcher_stats(SolveBatcher *b, int64_t *batches, int64_t *solves, double *ms, double *bytes);
+void batcher_stats(SolveBatcher *b, int64_t *batches, int64_t *solves, double *ms, double *bytes, double *busy_ms);
 
 // The SolveBufs of a factorization (its solve work allocated).
 template <class T>

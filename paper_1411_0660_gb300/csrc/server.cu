@@ -479,10 +479,11 @@ int mbl_server_stats_get(mbl_ctx *ctx, mbl_server_stats *out) {
     out->cache_hits = s->cache_hits;
     out->cache_bytes = s->cache_bytes;
     out->solve_batches = out->batched_solves = 0;
-    out->batch_ms = out->batch_bytes = 0.0;
+    out->batch_ms = out->batch_bytes = out->batch_busy_ms = 0.0;
     if (s->batcher) {
         try {
-            batcher_stats(s->batcher, &out->solve_batches, &out->batched_solves, &out->batch_ms, &out->batch_bytes);
+            batcher_stats(s->batcher, &out->solve_batches, &out->batched_solves, &out->batch_ms, &out->batch_bytes,
+                          &out->batch_busy_ms);
         } catch (const Error &e) {
             return srv_report(ctx, e.code, e.msg);
         }
