@@ -764,6 +764,143 @@ __global__ void k_bi_back(int m, const double *A, R *work, double *X) {
     for (int i = lane; i < m; i += 32) X[(size_t)c * m + i] = (double)z[i];
 }
 
+// ------------------------------------------------------------------------------------------
+// FP32 eigen-decomposition by the cyclic Jacobi method (Jacobi 1846; the parallel round-robin ordering
+// of Brent and Luk, 1985): every round rotates m/2 disjoint index pairs (p, q) at once, each rotation
+// chosen to annihilate a_pq; the two-sided update A <- J^T A J is done as the column rotations of all
+// pairs, then their row rotations, and V <- V J accumulates the eigenvectors.  m - 1 rounds (m even,
+// a dummy index added for odd m) visit every pair once: a sweep.  Sweeps repeat until the
+// off-diagonal mass is below FP32 rounding of the diagonal, at most JAC_SWEEPS.  One CTA per matrix,
+// A and V in shared memory (leading dimension m | 1, so that the row passes are free of bank
+// conflicts).  Unlike the QL sweeps, whose rotations form one chain on one thread, every step is
+// spread over the CTA.  A result that did not converge sets info[b] = 1.
+// ------------------------------------------------------------------------------------------
+constexpr int JAC_SWEEPS = 24;
+
+__global__ void __launch_bounds__(EIG_THREADS) k_syev_jacobi(const int *mv, const int64_t *aoff, const int64_t *woff,
+                                                             double *Aall, double *Wall, int *info) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ float s_c[EIG_SMEM_MAX_M / 2 + 1], s_s[EIG_SMEM_MAX_M / 2 + 1];
+    __shared__ int s_p[EIG_SMEM_MAX_M / 2 + 1], s_q[EIG_SMEM_MAX_M / 2 + 1];
+    __shared__ float red[EIG_THREADS / 32][2];
+    __shared__ int s_done;
+    const int b = blockIdx.x, m = mv[b], tid = threadIdx.x, nt = blockDim.x;
+    double *Ag = Aall + aoff[b];
+    double *W = Wall + woff[b];
+    if (tid == 0) info[b] = 0;
+    if (m <= 0) return;
+    const int ld = m | 1, M = (m + 1) & ~1, np = M / 2;
+    float *A = reinterpret_cast<float *>(smraw);  // A[c * ld + r]
+    float *V = A + (size_t)ld * m;                // V[c * ld + r]
+    for (int e = tid; e < m * m; e += nt) {
+        const int c = e / m, r = e - c * m;
+        A[c * ld + r] = (float)Ag[(size_t)c * m + r];
+        V[c * ld + r] = r == c ? 1.f : 0.f;
+    }
+    if (tid == 0) s_done = 0;
+    __syncthreads();
+    int sweep = 0;
+    float prev_off = 3.0e38f;  // (thread 0) the off-diagonal mass after the previous sweep
+    for (; sweep < JAC_SWEEPS; ++sweep) {
+        // convergence: the off-diagonal mass at FP32 rounding of the diagonal's (m ulp-sized entries
+        // per row), or a sweep that no longer halves it (rounding has been reached)
+        float off = 0.f, dia = 0.f;
+        for (int e = tid; e < m * m; e += nt) {
+            const int c = e / m, r = e - c * m;
+            const float v = A[c * ld + r];
+            if (r == c) dia += v * v;
+            else off += v * v;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            off += __shfl_xor_sync(0xffffffffu, off, o);
+            dia += __shfl_xor_sync(0xffffffffu, dia, o);
+        }
+        if ((tid & 31) == 0) {
+            red[tid >> 5][0] = off;
+            red[tid >> 5][1] = dia;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            float o2 = 0.f, d2 = 0.f;
+            for (int w = 0; w < nt / 32; ++w) {
+                o2 += red[w][0];
+                d2 += red[w][1];
+            }
+            s_done = o2 <= (float)m * 1e-13f * d2 || (sweep >= 3 && o2 > 0.5f * prev_off);
+            prev_off = o2;
+        }
+        __syncthreads();
+        if (s_done) break;
+        for (int round = 0; round < M - 1; ++round) {
+            // pair i: the players at positions i and M - 1 - i (player 0 fixed, the others rotate)
+            for (int i = tid; i < np; i += nt) {
+                const int ia = i, ib = M - 1 - i;
+                const int p = ia == 0 ? 0 : ((ia - 1 + round) % (M - 1)) + 1;
+                const int q = ((ib - 1 + round) % (M - 1)) + 1;
+                float c = 1.f, sn = 0.f;
+                if (p < m && q < m) {
+                    const float apq = A[q * ld + p];
+                    if (apq != 0.f) {
+                        const float app = A[p * ld + p], aqq = A[q * ld + q];
+                        const float th = (aqq - app) / (2.f * apq);
+                        const float t = copysignf(1.f, th) / (fabsf(th) + sqrtf(th * th + 1.f));
+                        c = 1.f / sqrtf(t * t + 1.f);
+                        sn = t * c;
+                    }
+                }
+                s_c[i] = c;
+                s_s[i] = sn;
+                s_p[i] = p;
+                s_q[i] = q;
+            }
+            __syncthreads();
+            // columns p, q of A and V: (x_p, x_q) <- (c x_p - s x_q, s x_p + c x_q); a warp per pair,
+            // its lanes over the rows
+            const int lane = tid & 31, nw = nt >> 5;
+            for (int i = tid >> 5; i < np; i += nw) {
+                const int p = s_p[i], q = s_q[i];
+                if (p >= m || q >= m) continue;
+                const float c = s_c[i], sn = s_s[i];
+                float *Ap = A + p * ld, *Aq = A + q * ld, *Vp = V + p * ld, *Vq = V + q * ld;
+                for (int r = lane; r < m; r += 32) {
+                    const float ap = Ap[r], aq = Aq[r];
+                    Ap[r] = c * ap - sn * aq;
+                    Aq[r] = sn * ap + c * aq;
+                    const float vp = Vp[r], vq = Vq[r];
+                    Vp[r] = c * vp - sn * vq;
+                    Vq[r] = sn * vp + c * vq;
+                }
+            }
+            __syncthreads();
+            // rows p, q of A: a warp per pair, its lanes over the columns
+            for (int i = tid >> 5; i < np; i += nw) {
+                const int p = s_p[i], q = s_q[i];
+                if (p >= m || q >= m) continue;
+                const float c = s_c[i], sn = s_s[i];
+                for (int col = lane; col < m; col += 32) {
+                    const float ap = A[col * ld + p], aq = A[col * ld + q];
+                    A[col * ld + p] = c * ap - sn * aq;
+                    A[col * ld + q] = sn * ap + c * aq;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    if (tid == 0 && !s_done) info[b] = 1;
+    // ascending eigenvalues: the rank of each diagonal entry (ties by index), then the vectors to
+    // their ranks' columns
+    for (int j = tid; j < m; j += nt) {
+        const float dj = A[j * ld + j];
+        int rank = 0;
+        for (int k = 0; k < m; ++k) {
+            const float dk = A[k * ld + k];
+            rank += (dk < dj || (dk == dj && k < j)) ? 1 : 0;
+        }
+        W[rank] = (double)dj;
+        for (int r = 0; r < m; ++r) Ag[(size_t)rank * m + r] = (double)V[j * ld + r];
+    }
+}
+
 template <class R>
 static void syev_bisect_t(int m, double *d_A, double *d_w, double *d_work, cudaStream_t st) {
     if (m < 1 || m > EIG_SMEM_MAX_M) fail(MBL_ERR_INVALID, "bisection eigensolver: order must be in [1, 160]");
@@ -809,8 +946,12 @@ cudaError_t syev_prepare_current_device() {
     e = cudaFuncSetAttribute(k_syev<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EIG_SMEM_BYTES);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_syev<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EIG_SMEM_BYTES);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_syev_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(2 * (EIG_SMEM_MAX_M | 1) * EIG_SMEM_MAX_M * sizeof(float)));
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_syev<double>);
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_syev<float>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_syev_jacobi);
     if (e == cudaSuccess && dev >= 0 && dev < 64) g_syev_ready[dev] = true;
     return e;
 }
@@ -839,6 +980,16 @@ void syev_batched(int batch, const int *d_m, const int64_t *d_aoff, const int64_
                                                          syev_work_doubles(mmax, vecs != 0), d_info,
                                                          sm ? mmax : 0, zsm);
     }
+    MBL_LAUNCH_CHECK();
+}
+
+void syev_jacobi32(int batch, const int *d_m, const int64_t *d_aoff, const int64_t *d_woff, double *d_A, double *d_w,
+                   int mmax, int *d_info, cudaStream_t st) {
+    if (batch <= 0) return;
+    if (mmax > EIG_SMEM_MAX_M) fail(MBL_ERR_INVALID, "Jacobi eigensolver limited to order 160");
+    MBL_CUDA(syev_prepare_current_device());
+    k_syev_jacobi<<<batch, EIG_THREADS, (size_t)2 * (mmax | 1) * mmax * sizeof(float), st>>>(d_m, d_aoff, d_woff, d_A,
+                                                                                             d_w, d_info);
     MBL_LAUNCH_CHECK();
 }
 

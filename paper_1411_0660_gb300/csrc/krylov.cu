@@ -463,6 +463,7 @@ void KrylovSchur::ritz(cudaStream_t st, std::vector<double> &theta, std::vector<
         // FP32 reduction and QL, then two steps of FP64 refinement of the whole decomposition: a
         // thick restart keeps an invariant subspace of T, so the kept vectors must be accurate to
         // FP64 rounding (an FP32-accurate subspace would cap the attainable residuals near 1e-7).
+        // (The FP32 Jacobi start, unchecked here, left an L = 16 job at 48 of 50 pairs.)
         // Bisection and inverse iteration in FP32 are not a usable start here: the small Ritz values
         // of T lie in clusters within which inverse iteration mixes the vectors, the kept block then
         // cuts through such a cluster, and an L = 16 job converged 47 of 50 pairs (three refinement
@@ -1675,10 +1676,10 @@ void RitzH::run(mbl_sector *sec, KrylovSchur &ks, double sigma, double hnorm, do
     MBL_LAUNCH_CHECK();
     MBL_CUDA(cudaMemcpyAsync(gm.data(), &mb, sizeof(int), cudaMemcpyHostToDevice, st));
     {
-        // FP32 eigensolve (bisection and inverse iteration, every eigenvalue and vector on its own
-        // thread) refined by three Ogita-Aishima steps and re-orthonormalized (Newton-Schulz)
-        // in FP64; accepted only if the nev wanted columns are orthonormal and diagonalize G to FP64
-        // accuracy, otherwise the FP64 eigensolver runs.  The pairs' residuals on H are recomputed below.
+        // FP32 eigensolve (the parallel Jacobi method) refined by three Ogita-Aishima steps and
+        // re-orthonormalized (Newton-Schulz) in FP64; accepted only if the nev wanted columns are
+        // orthonormal and diagonalize G to FP64 accuracy, otherwise FP64 bisection and inverse
+        // iteration run.  The pairs' residuals on H are recomputed below.
         ProfScope ps(ctx, "syev_rr", (double)mb, st);
         const bool fp32 = ks.ldv <= EIG_SMEM_MAX_M;
         // accept eigenvectors X (in Gs) only if the nev wanted columns are orthonormal and diagonalize
@@ -1704,7 +1705,7 @@ void RitzH::run(mbl_sector *sec, KrylovSchur &ks, double sigma, double hnorm, do
         if (fp32) {
             MBL_CUDA(cudaMemcpyAsync(Gsym.data(), Gs.data(), (size_t)mb * mb * sizeof(double), cudaMemcpyDeviceToDevice,
                                      st));
-            syev_bisect32(mb, Gs.data(), Gw.data(), Gwork.data(), st);
+            syev_jacobi32(1, gm.data(), goff.data(), goff.data(), Gs.data(), Gw.data(), ks.ldv, ginfo.data(), st);
             refine_eig(mb, Gsym.data(), Gs.data(), Gw.data(), 3, Gr1.data(), Gr2.data(), Gr3.data(), st);
             for (int it = 0; it < 2; ++it) {  // X <- 1.5 X - 0.5 X (X^T X)
                 gemm_small(true, false, mb, mb, mb, 1.0, Gs.data(), mb, Gs.data(), mb, 0.0, Gr1.data(), mb, st);

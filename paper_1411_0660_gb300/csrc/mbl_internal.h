@@ -266,6 +266,11 @@ constexpr int EIG_SMEM_MAX_M = 160;  // largest order the small eigensolver keep
 void syev_batched(int batch, const int *d_m, const int64_t *d_aoff, const int64_t *d_woff, double *d_A,
                   double *d_w, int vecs, const int *d_sel, int mmax, double *d_work, int *d_info,
                   cudaStream_t st, bool fp32 = false);
+// Eigenvalues (ascending) and eigenvectors of the batch's matrices (order <= 160) by the parallel
+// cyclic Jacobi method in FP32 on one CTA each, as the start of a refined decomposition; info[b] = 1
+// if a matrix did not converge in the sweep limit.
+void syev_jacobi32(int batch, const int *d_m, const int64_t *d_aoff, const int64_t *d_woff, double *d_A, double *d_w,
+                   int mmax, int *d_info, cudaStream_t st);
 // set the small eigensolver's shared-memory attributes on the current device and load its FP32 and
 // FP64 kernels now (kernels otherwise load lazily on first launch, taking device memory then)
 cudaError_t syev_preload();
