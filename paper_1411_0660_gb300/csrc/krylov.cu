@@ -821,23 +821,16 @@ __global__ void __launch_bounds__(128) k_defl_tn(int64_t n, int kd, int p, const
         if (q < p) out[q] = (double)acc[q];
 }
 
-// c = Einv C (kd x p, row-major) with C = sum over the nb blocks of part, in block order; one CTA.
-__global__ void __launch_bounds__(1024) k_defl_coef(int nb, int kd, int p, const double *__restrict__ part,
-                                                    const double *__restrict__ Einv, double *__restrict__ c) {
-    __shared__ double sc[90 * 32];
-    const int kp = kd * p;
-    for (int o = threadIdx.x; o < kp; o += blockDim.x) {
-        double s = 0.0;
-        for (int b = 0; b < nb; ++b) s += part[(size_t)b * kp + o];
-        sc[o] = s;
-    }
-    __syncthreads();
-    for (int o = threadIdx.x; o < kp; o += blockDim.x) {
-        const int a = o / p, q = o - a * p;
-        double s = 0.0;
-        for (int k = 0; k < kd; ++k) s = fma(Einv[(size_t)a * kd + k], sc[k * p + q], s);
-        c[o] = s;
-    }
+// c = Einv C (kd x p, row-major; C = U^T v, reduced from the block sums by k_reduce_parts): a thread
+// per output.
+__global__ void k_defl_coef(int kd, int p, const double *__restrict__ C, const double *__restrict__ Einv,
+                            double *__restrict__ c) {
+    const int o = blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= kd * p) return;
+    const int a = o / p, q = o - a * p;
+    double s = 0.0;
+    for (int k = 0; k < kd; ++k) s = fma(Einv[(size_t)a * kd + k], C[k * p + q], s);
+    c[o] = s;
 }
 
 // Xout[r][q] = Xin[r][q] + sign * sum_a U[r][a] c[a][q] (the sum in FP32): a thread per row, c staged
@@ -876,6 +869,7 @@ void RefinedSolve::set_deflation(const double *U_, int ldu_, int k, cudaStream_t
     Ctx *ctx = sec->ctx;
     if (AU.size() < (size_t)n * k) AU.alloc(ctx, (size_t)n * k);
     if (Einv.size() < (size_t)k * k) Einv.alloc(ctx, (size_t)k * k);
+    if (Dc0.size() < (size_t)k * 32) Dc0.alloc(ctx, (size_t)k * 32);
     if (Dc1.size() < (size_t)k * 32) Dc1.alloc(ctx, (size_t)k * 32);
     // Dwork: E's partial sums (dense_tn), then the deflation products' per-block partial sums
     const size_t dwork = std::max(dense_tn_work(n, k, std::max(k, 32)),
@@ -924,7 +918,9 @@ void RefinedSolve::precondition(const double *V, double *Z, int p, cudaStream_t 
         else if (pb == 16) k_defl_tn<16><<<nbd, 128, 0, st>>>(n, kd, p, U32.data(), V, Dwork.data());
         else k_defl_tn<32><<<nbd, 128, 0, st>>>(n, kd, p, U32.data(), V, Dwork.data());
         MBL_LAUNCH_CHECK();
-        k_defl_coef<<<1, 1024, 0, st>>>((int)nbd, kd, p, Dwork.data(), Einv.data(), Dc1.data());
+        k_reduce_parts<<<reduce_grid(kd * p), 256, 0, st>>>((int)nbd, kd * p, Dwork.data(), Dc0.data());
+        MBL_LAUNCH_CHECK();
+        k_defl_coef<<<(unsigned)((kd * p + 127) / 128), 128, 0, st>>>(kd, p, Dc0.data(), Einv.data(), Dc1.data());
         MBL_LAUNCH_CHECK();
         // z = M^-1 (v - A U c) + U c
         apply(AU32.data(), V, Dt.data(), -1.0);

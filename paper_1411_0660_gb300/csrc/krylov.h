@@ -56,7 +56,7 @@ struct RefinedSolve {
     // (U^T A U)^-1 is formed in FP64; U and A U are kept as FP32 copies (n x kd), since the
     // preconditioner needs them only to FP32 accuracy and FP64 products would cost ~20x more.
     int kd = 0;
-    DVec<double> AU, Einv, Dc1, Dt, Dwork;
+    DVec<double> AU, Einv, Dc0, Dc1, Dt, Dwork;
     DVec<float> U32, AU32;
     DVec<int> Dflag;
     void apply(const double *X, int ldx, double *Y, int p, cudaStream_t st);
