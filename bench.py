@@ -112,6 +112,36 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
+_ORDERING = {"band": 0, "cover": 1}
+_ordering = 0
+
+
+def _context(device):
+    """A library context whose symbolic analyses use the ordering chosen on the command line."""
+    ctx = g.Context(device)
+    ctx.set_ordering(_ordering)
+    return ctx
+
+
+def profiled_traffic(name, algorithmic_bytes):
+    """DRAM bytes per solve from a committed ncu summary under profiles/, or None when that capture
+    was taken on a different factorization (its algorithmic bytes per solve are not this run's within
+    1%: another ordering or sector), or when the summary is missing."""
+    traffic = alg = None
+    try:
+        with open(os.path.join(ROOT, "profiles", name)) as fp:
+            for ln in fp:
+                if ln.startswith("traffic_bytes_per_solve:"):
+                    traffic = float(ln.split(":")[1])
+                elif ln.startswith("algorithmic_bytes_per_solve:"):
+                    alg = float(ln.split(":")[1])
+    except OSError:
+        return None
+    if traffic is None or alg is None or abs(alg - algorithmic_bytes) > 0.01 * algorithmic_bytes:
+        return None
+    return traffic
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -236,7 +266,7 @@ def run_batch_case(args):
 
     import paper_1411_0660_gb300 as g
 
-    ctx = g.Context(0)
+    ctx = _context(0)
     K = args.batch
     secs, facts = [], []
     for k in range(K):
@@ -289,7 +319,7 @@ def run_case(args):
 
     if args.case == "solve" and args.batch > 1 and args.batch_case:
         return run_batch_case(args)
-    ctx = g.Context(0)
+    ctx = _context(0)
     sec = g.build_sector(ctx, args.L, 3.0, 5)
     lo, hi = g.extremal_bounds(sec)
     prec = g.MBL_PREC_FP64 if args.precision == "fp64" else g.MBL_PREC_FP32
@@ -349,7 +379,7 @@ def run_observables_case(args):
 
     import paper_1411_0660_gb300 as g
 
-    ctx = g.Context(0)
+    ctx = _context(0)
     n, nev = math.comb(args.L, args.L // 2), NEV
     dev = torch.device("cuda:0")
     gen = torch.Generator(device=dev)
@@ -395,7 +425,7 @@ def run_l22(args):
 
     import paper_1411_0660_gb300 as g
 
-    ctx = g.Context(0)
+    ctx = _context(0)
     out = {"workload": "l22", "L": 22, "n": math.comb(22, 11), "jobs": []}
     for seed in range(args.seeds):
         sec = g.build_sector(ctx, 22, 3.0, seed)
@@ -435,7 +465,7 @@ def run_campaign_workload(args):
     import paper_1411_0660_gb300 as g
     from paper_1411_0660_gb300 import campaign as cp
 
-    ctx = g.Context(0)
+    ctx = _context(0)
     Ls, hs = [12, 14, 16], [1.0, 2.0, 2.5, 3.0, 3.5, 4.0, 4.5, 5.0, 6.0]
     data = cp.run_campaign(ctx, Ls, hs, range(args.seeds), eps=0.5, nev=20, observable="r", slots=args.slots)
     L, h, Q, dQ = cp.points(data)
@@ -472,7 +502,7 @@ def run_workload(args):
 
     import paper_1411_0660_gb300 as g
 
-    ctx = g.Context(0)
+    ctx = _context(0)
     srv = g.Server(ctx, slots=args.slots)
     plans = None
     if args.workload == "large":
@@ -612,11 +642,15 @@ def main():
     ap.add_argument("--batch-jobs", type=int, default=16, help="served form: jobs per batched solve launch (1: off)")
     ap.add_argument("--batch-window-us", type=float, default=300.0, help="served form: batcher collection window")
     ap.add_argument("--batch-lanes", type=int, default=2, help="served form: streams of batched solves")
+    ap.add_argument("--ordering", choices=sorted(_ORDERING), default="band",
+                    help="fill-reducing ordering of the symbolic analysis")
     ap.add_argument("--cache-fraction", type=float, default=0.0,
                     help="served form: share of HBM keeping finished jobs' factorizations (0: off; the "
                          "workload's realizations are all distinct, and the comparison arms rerun the "
                          "same jobs, which a cache would answer from stored factorizations)")
     args = ap.parse_args()
+    global _ordering
+    _ordering = _ORDERING[args.ordering]
     args.batch_case = args.case == "solve" and "--batch" in sys.argv
     if args.case == "observables":
         return run_observables_case(args)
@@ -650,7 +684,7 @@ def main():
         import torch.distributed as dist
 
         dist.init_process_group("nccl")
-    ctx = g.Context(local)
+    ctx = _context(local)
     n = math.comb(L, L // 2)
     d_ev = torch.empty(NEV, dtype=torch.float64, device="cuda")
     d_vec = torch.empty(n * NEV, dtype=torch.float64, device="cuda")
@@ -840,13 +874,7 @@ def main():
     traffic = None
     if dom == "trisolve_fp32":
         # DRAM bytes of one block solve from the committed ncu capture of the same kernels
-        try:
-            with open(os.path.join(ROOT, "profiles", "solve_l18_fp32_traffic.md")) as fp:
-                for ln in fp:
-                    if ln.startswith("traffic_bytes_per_solve:"):
-                        traffic = float(ln.split(":")[1])
-        except OSError:
-            traffic = None
+        traffic = profiled_traffic("solve_l18_fp32_traffic.md", per_launch_work)
     roof.update({"achieved": achieved, "peak": peak, "frac": achieved / peak, "traffic": traffic, "kernel": dom,
                  "launch_ms": per_launch_ms, "work_per_launch": per_launch_work})
     roof_seq = {"kernel": dom, "achieved": achieved, "frac": achieved / peak, "launch_ms": per_launch_ms}
@@ -858,14 +886,8 @@ def main():
         per_launch_ms = served_solve["batch_ms"] / nb
         per_launch_work = served_solve["batch_bytes"] / nb
         achieved = per_launch_work / (per_launch_ms / 1e3) / 1e9
-        traffic = None
-        try:
-            with open(os.path.join(ROOT, "profiles", "solve_l18_fp32_batch_traffic.md")) as fp:
-                for ln in fp:
-                    if ln.startswith("traffic_bytes_per_solve:"):
-                        traffic = float(ln.split(":")[1]) * kmean
-        except OSError:
-            traffic = None
+        traffic = profiled_traffic("solve_l18_fp32_batch_traffic.md", per_launch_work / kmean)
+        traffic = traffic * kmean if traffic is not None else None
         roof = {"bound": "hbm", "unit": "GB/s", "peak_source": roof["peak_source"], "achieved": achieved,
                 "peak": peak, "frac": achieved / peak, "traffic": traffic,
                 "kernel": "trisolve_fp32 batched (served, timed region)", "launch_ms": per_launch_ms,
@@ -885,7 +907,7 @@ def main():
             "vs_baseline": None, "dtype": "f32 fronts + f64 refinement", "data": "synthetic",
             "config": {"workload": WORKLOAD + f"; served on {args.slots} worker streams", "L": L, "nev": NEV,
                        "jobs_per_step": args.batch, "slots": args.slots, "parallelism": f"replicas x{world}",
-                       "l2": "inputs > L2 (factor 0.5 GB/job)"},
+                       "l2": "inputs > L2 (factor > 0.3 GB/job)", "ordering": args.ordering},
             "gpu_launches": launches,
             "clocks": clocks.summary(local),
             "latency_ms": {"p50": _pct(main_run["lat_ms"], 0.5), "p99": _pct(main_run["lat_ms"], 0.99)},

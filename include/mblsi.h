@@ -51,6 +51,13 @@ extern "C" {
 #define MBL_PREC_FP64 0   /* FP64 fronts and FP64 triangular solves */
 #define MBL_PREC_FP32 1   /* FP32 fronts and solves, FP64 iterative refinement */
 
+/* Fill-reducing orderings of the symbolic analysis (nested dissection along the Fourier modes of
+ * the magnetization profile; see mbl_ctx_set_ordering). */
+#define MBL_ORDER_BAND 0  /* separators = bands of one mode, chosen from the two numbered depth, depth + 1 */
+#define MBL_ORDER_COVER 1 /* all modes k <= L/2 searched, separators refined to a minimum vertex cover:
+                             less fill and fewer flops, but more single-column supernodes, so less
+                             pivot freedom and a less accurate unrefined factor */
+
 typedef struct mbl_ctx mbl_ctx;
 typedef struct mbl_sector mbl_sector;
 typedef struct mbl_factorization mbl_factorization;
@@ -230,6 +237,13 @@ typedef struct mbl_plan_stats {
                                                              arena mode (see mbl_opts.arena_mode) */
 } mbl_plan_stats;
 int mbl_analyse(mbl_sector *sec, int nev, int block, mbl_plan_stats *stats);
+/* Ordering used by the symbolic analyses built from now on in this context and in the serving
+ * workers that share its plans (MBL_ORDER_*, default MBL_ORDER_BAND).  Plans are cached per
+ * (L, nup, ordering), so plans and factorizations made before the call are unaffected.  Any
+ * ordering gives the same factorization in exact arithmetic; they differ in fill-in, flops and
+ * front sizes (mbl_analyse).  MBL_ERR_INVALID for an unknown value.  Not in the paper, whose
+ * direct solver (the MUMPS package) chooses its own ordering. */
+int mbl_ctx_set_ordering(mbl_ctx *ctx, int ordering);
 
 /* Launch trace of the level-by-level triangular solve, a diagnostic with no counterpart in the
  * paper.  With on != 0 every later solve of f records, for each kernel launch of its sequence, the

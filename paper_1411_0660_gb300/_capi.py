@@ -20,6 +20,8 @@ MBL_ERR_CUDA = 6
 MBL_PENDING = 7
 MBL_PREC_FP64 = 0
 MBL_PREC_FP32 = 1
+MBL_ORDER_BAND = 0
+MBL_ORDER_COVER = 1
 
 
 class Opts(ctypes.Structure):
@@ -85,6 +87,7 @@ SIGNATURES = [
     ("mbl_status_string", ctypes.c_char_p, [c_int]),
     ("mbl_launch_count", ctypes.c_longlong, []),
     ("mbl_ctx_set_profiling", c_int, [c_void_p, c_int]),
+    ("mbl_ctx_set_ordering", c_int, [c_void_p, c_int]),
     ("mbl_ctx_profile_get", c_int, [c_void_p, ctypes.c_char_p, P(c_int64), P(c_double), P(c_double)]),
     ("mbl_ctx_create", c_int, [c_int, c_size_t, P(c_void_p)]),
     ("mbl_ctx_destroy", None, [c_void_p]),

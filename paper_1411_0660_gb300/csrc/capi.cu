@@ -152,7 +152,8 @@ std::shared_ptr<Plan> get_plan(mbl_sector *sec) {
     Ctx *ctx = sec->ctx;
     std::shared_ptr<PlanCache> cache = ctx->plans;
     std::lock_guard<std::mutex> lk(cache->mu);
-    const int key = sector_key(sec->L, sec->nup);
+    const int ordering = cache->ordering;
+    const int key = plan_key(sec->L, sec->nup, ordering);
     auto it = cache->m.find(key);
     if (it != cache->m.end()) return it->second;
     int64_t n = sec->n;
@@ -163,7 +164,7 @@ std::shared_ptr<Plan> get_plan(mbl_sector *sec) {
     MBL_CUDA(cudaMemcpy(st.data(), sec->states.data(), n * sizeof(uint32_t), cudaMemcpyDeviceToHost));
     MBL_CUDA(cudaMemcpy(rp.data(), sec->rowptr.data(), (n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost));
     MBL_CUDA(cudaMemcpy(col.data(), sec->col.data(), sec->nnz * sizeof(int32_t), cudaMemcpyDeviceToHost));
-    auto P = build_plan(sec->L, st, rp, col);
+    auto P = build_plan(sec->L, st, rp, col, ordering);
     upload_plan(ctx, *P);
     cache->m[key] = P;
     return P;
@@ -326,6 +327,15 @@ int mbl_ctx_set_profiling(mbl_ctx *ctx, int on) {
     ctx->resolve_profile();
     ctx->profile.clear();
     ctx->prof = on != 0;
+    API_CATCH(ctx)
+}
+
+int mbl_ctx_set_ordering(mbl_ctx *ctx, int ordering) {
+    if (!ctx) return report(nullptr, MBL_ERR_INVALID, "ctx is NULL");
+    if (ordering != MBL_ORDER_COVER && ordering != MBL_ORDER_BAND) return report(ctx, MBL_ERR_INVALID, "unknown ordering");
+    API_TRY
+    std::lock_guard<std::mutex> lk(ctx->plans->mu);
+    ctx->plans->ordering = ordering;
     API_CATCH(ctx)
 }
 

@@ -154,8 +154,10 @@ inline int sector_key(int L, int nup) { return L * 64 + nup; }
 
 struct PlanCache {
     std::mutex mu;
-    std::map<int, std::shared_ptr<Plan>> m;
+    std::map<int, std::shared_ptr<Plan>> m;  // key: plan_key(L, nup, ordering)
+    int ordering = MBL_ORDER_BAND;           // for plans built from now on
 };
+inline int plan_key(int L, int nup, int ordering) { return sector_key(L, nup) * 4 + ordering; }
 
 struct Ctx {
     int device = 0;

@@ -216,9 +216,10 @@ struct Plan {
     bool on_device = false;
 };
 
-// Build the plan for the pattern of a sector (host arrays: states, rowptr, col of the CSR).
+// Build the plan for the pattern of a sector (host arrays: states, rowptr, col of the CSR) with
+// the fill-reducing ordering MBL_ORDER_BAND or MBL_ORDER_COVER.
 std::shared_ptr<Plan> build_plan(int L, const std::vector<uint32_t> &states, const std::vector<int64_t> &rowptr,
-                                 const std::vector<int32_t> &col);
+                                 const std::vector<int32_t> &col, int ordering = MBL_ORDER_BAND);
 void upload_plan(Ctx *ctx, Plan &p);
 
 }  // namespace mbl

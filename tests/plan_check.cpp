@@ -5,7 +5,7 @@
 // structural invariants that the numeric factorization and the solves rely on.  Prints "ok ..." and
 // exits 0, or prints the first violated invariant and exits 1.
 //
-// Usage: plan_check L nup
+// Usage: plan_check L nup [ordering]   (ordering: MBL_ORDER_BAND = 0 (default), MBL_ORDER_COVER = 1)
 #include <algorithm>
 #include <cstdio>
 #include <cstdlib>
@@ -42,8 +42,9 @@ static int popcount32(uint32_t s) {
 }
 
 int main(int argc, char **argv) {
-    if (argc != 3) return bad("usage: plan_check L nup");
+    if (argc != 3 && argc != 4) return bad("usage: plan_check L nup [ordering]");
     const int L = std::atoi(argv[1]), nup = std::atoi(argv[2]);
+    const int ordering = argc == 4 ? std::atoi(argv[3]) : MBL_ORDER_BAND;
     std::vector<uint32_t> st;
     for (uint32_t s = 0; s < (1u << L); ++s)
         if (popcount32(s) == nup) st.push_back(s);
@@ -64,7 +65,12 @@ int main(int argc, char **argv) {
         col.insert(col.end(), c.begin(), c.end());
         rp[k + 1] = (int64_t)col.size();
     }
-    auto P = build_plan(L, st, rp, col);
+    std::shared_ptr<Plan> P;
+    try {
+        P = build_plan(L, st, rp, col, ordering);
+    } catch (const Error &e) {
+        return bad(e.msg.c_str(), e.code);
+    }
     const Plan &p = *P;
 
     // 1. the ordering is a permutation with its inverse
@@ -234,8 +240,9 @@ int main(int argc, char **argv) {
             if (iv[i].first < iv[i - 1].second) return bad("fronts overlap", (long)i);
     }
     if (p.lean_peak_elems <= 0 || p.lean_peak_elems > p.arena_elems) return bad("lean peak", p.lean_peak_elems);
-    std::printf("ok L=%d nup=%d n=%ld supernodes=%d levels=%d nnz_l=%ld solve_panels=%zu arena=%ld lean_peak=%ld\n",
+    std::printf("ok L=%d nup=%d n=%ld supernodes=%d levels=%d nnz_l=%ld solve_panels=%zu arena=%ld lean_peak=%ld "
+                "flops=%.6e max_front=%d\n",
                 L, nup, (long)n, p.ns, p.nlevels, (long)p.nnz_l, p.sdescs.size(), (long)p.arena_elems,
-                (long)p.lean_peak_elems);
+                (long)p.lean_peak_elems, p.flops, (int)p.max_front);
     return 0;
 }

@@ -6,7 +6,9 @@ columns; front row lists whose contribution rows belong to ancestors and nest in
 rows; an L structure that holds the pattern of P A P^T; nnz(L); solve panels that tile every
 front's fully summed block with consistent offsets into the packed solve factor; solve steps that
 cover every panel once; a forward gather that writes every front row once; and dataflow item
-lists whose dependencies are met in list order."""
+lists whose dependencies are met in list order.  Both fill-reducing orderings are checked, and the
+optional one (cover-refined separators over all modes) is checked to need less fill and fewer flops
+than the default band separators."""
 import os
 import subprocess
 
@@ -34,6 +36,29 @@ def checker(tmp_path_factory):
 
 @pytest.mark.parametrize("L,nup", [(2, 1), (8, 4), (10, 5), (11, 5), (12, 3), (13, 7), (14, 7), (15, 8), (16, 8), (17, 9), (18, 9),
                                    (12, 1), (9, 0)])
-def test_plan_invariants(checker, L, nup):
-    r = subprocess.run([checker, str(L), str(nup)], capture_output=True, text=True, timeout=120)
+@pytest.mark.parametrize("ordering", [0, 1])
+def test_plan_invariants(checker, L, nup, ordering):
+    r = subprocess.run([checker, str(L), str(nup), str(ordering)], capture_output=True, text=True, timeout=120)
     assert r.returncode == 0 and r.stdout.startswith("ok"), r.stdout + r.stderr
+
+
+def _stats(checker, L, nup, ordering):
+    r = subprocess.run([checker, str(L), str(nup), str(ordering)], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0 and r.stdout.startswith("ok"), r.stdout + r.stderr
+    return {k: float(v) for k, v in (t.split("=") for t in r.stdout.split()[1:])}
+
+
+@pytest.mark.parametrize("L,nup", [(14, 7), (16, 8), (18, 9), (17, 9)])
+def test_cover_ordering_reduces_fill(checker, L, nup):
+    """A minimum cover of the edges crossing a threshold inside a band is never larger than the band,
+    and the cover ordering also searches every mode: fill-in and flops shrink, the largest front
+    does not grow by more than a few percent."""
+    band, cover = _stats(checker, L, nup, 0), _stats(checker, L, nup, 1)
+    assert cover["nnz_l"] < 0.9 * band["nnz_l"], (cover, band)
+    assert cover["flops"] < 0.85 * band["flops"], (cover, band)
+    assert cover["max_front"] <= 1.05 * band["max_front"], (cover, band)
+
+
+def test_unknown_ordering_is_rejected(checker):
+    r = subprocess.run([checker, "8", "4", "7"], capture_output=True, text=True, timeout=60)
+    assert r.returncode != 0
