@@ -112,7 +112,7 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
-_ORDERING = {"band": 0, "cover": 1}
+_ORDERING = {"band": 0, "cover": 1, "modes": 2}
 _ordering = 0
 
 

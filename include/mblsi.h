@@ -55,8 +55,9 @@ extern "C" {
  * the magnetization profile; see mbl_ctx_set_ordering). */
 #define MBL_ORDER_BAND 0  /* separators = bands of one mode, chosen from the two numbered depth, depth + 1 */
 #define MBL_ORDER_COVER 1 /* all modes k <= L/2 searched, separators refined to a minimum vertex cover:
-                             less fill and fewer flops, but more single-column supernodes, so less
-                             pivot freedom and a less accurate unrefined factor */
+                             the least fill and flops, but more single-column supernodes and a
+                             heavier tail of element growth in the unrefined factor */
+#define MBL_ORDER_MODES 2 /* all modes k <= L/2 searched, the band separator of the best one */
 
 typedef struct mbl_ctx mbl_ctx;
 typedef struct mbl_sector mbl_sector;

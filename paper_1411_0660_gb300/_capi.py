@@ -22,6 +22,7 @@ MBL_PREC_FP64 = 0
 MBL_PREC_FP32 = 1
 MBL_ORDER_BAND = 0
 MBL_ORDER_COVER = 1
+MBL_ORDER_MODES = 2
 
 
 class Opts(ctypes.Structure):

@@ -5,7 +5,7 @@
 // structural invariants that the numeric factorization and the solves rely on.  Prints "ok ..." and
 // exits 0, or prints the first violated invariant and exits 1.
 //
-// Usage: plan_check L nup [ordering]   (ordering: MBL_ORDER_BAND = 0 (default), MBL_ORDER_COVER = 1)
+// Usage: plan_check L nup [ordering]   (MBL_ORDER_BAND = 0 (default), MBL_ORDER_COVER = 1, MBL_ORDER_MODES = 2)
 #include <algorithm>
 #include <cstdio>
 #include <cstdlib>

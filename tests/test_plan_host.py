@@ -6,9 +6,9 @@ columns; front row lists whose contribution rows belong to ancestors and nest in
 rows; an L structure that holds the pattern of P A P^T; nnz(L); solve panels that tile every
 front's fully summed block with consistent offsets into the packed solve factor; solve steps that
 cover every panel once; a forward gather that writes every front row once; and dataflow item
-lists whose dependencies are met in list order.  Both fill-reducing orderings are checked, and the
-optional one (cover-refined separators over all modes) is checked to need less fill and fewer flops
-than the default band separators."""
+lists whose dependencies are met in list order.  All three fill-reducing orderings are checked, and
+the two optional ones (band or cover-refined separators over all modes) are checked to need less
+fill and fewer flops than the default band separators of a fixed mode sequence."""
 import os
 import subprocess
 
@@ -36,7 +36,7 @@ def checker(tmp_path_factory):
 
 @pytest.mark.parametrize("L,nup", [(2, 1), (8, 4), (10, 5), (11, 5), (12, 3), (13, 7), (14, 7), (15, 8), (16, 8), (17, 9), (18, 9),
                                    (12, 1), (9, 0)])
-@pytest.mark.parametrize("ordering", [0, 1])
+@pytest.mark.parametrize("ordering", [0, 1, 2])
 def test_plan_invariants(checker, L, nup, ordering):
     r = subprocess.run([checker, str(L), str(nup), str(ordering)], capture_output=True, text=True, timeout=120)
     assert r.returncode == 0 and r.stdout.startswith("ok"), r.stdout + r.stderr
@@ -53,10 +53,12 @@ def test_cover_ordering_reduces_fill(checker, L, nup):
     """A minimum cover of the edges crossing a threshold inside a band is never larger than the band,
     and the cover ordering also searches every mode: fill-in and flops shrink, the largest front
     does not grow by more than a few percent."""
-    band, cover = _stats(checker, L, nup, 0), _stats(checker, L, nup, 1)
+    band, cover, modes = (_stats(checker, L, nup, o) for o in (0, 1, 2))
     assert cover["nnz_l"] < 0.9 * band["nnz_l"], (cover, band)
     assert cover["flops"] < 0.85 * band["flops"], (cover, band)
     assert cover["max_front"] <= 1.05 * band["max_front"], (cover, band)
+    # the cover refines the best band among the same modes: never more fill than that band alone
+    assert cover["nnz_l"] <= modes["nnz_l"] <= band["nnz_l"], (cover, modes, band)
 
 
 def test_unknown_ordering_is_rejected(checker):
