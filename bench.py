@@ -112,8 +112,8 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
-_ORDERING = {"band": 0, "cover": 1, "modes": 2}
-_ordering = 0
+_ORDERING = {"band": 0, "cover": 1, "modes": 2, "auto": 3}
+_ordering = 3
 
 
 def _context(device):
@@ -642,7 +642,7 @@ def main():
     ap.add_argument("--batch-jobs", type=int, default=16, help="served form: jobs per batched solve launch (1: off)")
     ap.add_argument("--batch-window-us", type=float, default=300.0, help="served form: batcher collection window")
     ap.add_argument("--batch-lanes", type=int, default=2, help="served form: streams of batched solves")
-    ap.add_argument("--ordering", choices=sorted(_ORDERING), default="band",
+    ap.add_argument("--ordering", choices=sorted(_ORDERING), default="auto",
                     help="fill-reducing ordering of the symbolic analysis")
     ap.add_argument("--cache-fraction", type=float, default=0.0,
                     help="served form: share of HBM keeping finished jobs' factorizations (0: off; the "
@@ -715,10 +715,14 @@ def main():
 
     # the jobs' inputs: their disorder realizations h_i (host arrays, prepared untimed)
     host_fields = []
+    plan = None
     for (h, seed, eps) in timed_jobs:
         sec0 = g.build_sector(ctx, L, h, seed)
         host_fields.append(np.ascontiguousarray(sec0.fields()))
+        if plan is None:  # the plan the served jobs use (built by the warm-up already)
+            plan = g.analyse(sec0, NEV, 8)
         sec0.close()
+    ordering_used = {v: k for k, v in _ORDERING.items()}[int(plan["ordering"])]
     srv = g.Server(ctx, slots=args.slots, batch_jobs=args.batch_jobs, batch_window_us=args.batch_window_us,
                    batch_lanes=args.batch_lanes, cache_fraction=args.cache_fraction)
     for t in [srv.submit(L, h, seed, eps, NEV) for (h, seed, eps) in jobs_for_step(0, args.slots, rank, world)]:
@@ -907,7 +911,7 @@ def main():
             "vs_baseline": None, "dtype": "f32 fronts + f64 refinement", "data": "synthetic",
             "config": {"workload": WORKLOAD + f"; served on {args.slots} worker streams", "L": L, "nev": NEV,
                        "jobs_per_step": args.batch, "slots": args.slots, "parallelism": f"replicas x{world}",
-                       "l2": "inputs > L2 (factor > 0.3 GB/job)", "ordering": args.ordering},
+                       "l2": "inputs > L2 (factor > 0.3 GB/job)", "ordering": f"{args.ordering} ({ordering_used}, nnz(L) = {int(plan['nnz_l'])})"},
             "gpu_launches": launches,
             "clocks": clocks.summary(local),
             "latency_ms": {"p50": _pct(main_run["lat_ms"], 0.5), "p99": _pct(main_run["lat_ms"], 0.99)},

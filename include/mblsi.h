@@ -58,6 +58,9 @@ extern "C" {
                              the least fill and flops, but more single-column supernodes and a
                              heavier tail of element growth in the unrefined factor */
 #define MBL_ORDER_MODES 2 /* all modes k <= L/2 searched, the band separator of the best one */
+#define MBL_ORDER_AUTO 3  /* MBL_ORDER_MODES for sectors of dimension >= 40000 (L >= 18 at half filling),
+                             where its smaller factor pays; MBL_ORDER_BAND below, where the
+                             factorization is bound by the per-level launch chain */
 
 typedef struct mbl_ctx mbl_ctx;
 typedef struct mbl_sector mbl_sector;
@@ -236,10 +239,11 @@ typedef struct mbl_plan_stats {
     double job_peak_bytes_fp32, job_peak_bytes_fp64;
     double front_peak_bytes_fp32, front_peak_bytes_fp64;  /* the fronts arena at its peak in the automatic
                                                              arena mode (see mbl_opts.arena_mode) */
+    int64_t ordering;               /* the MBL_ORDER_* the plan was built with (MBL_ORDER_AUTO resolved) */
 } mbl_plan_stats;
 int mbl_analyse(mbl_sector *sec, int nev, int block, mbl_plan_stats *stats);
 /* Ordering used by the symbolic analyses built from now on in this context and in the serving
- * workers that share its plans (MBL_ORDER_*, default MBL_ORDER_BAND).  Plans are cached per
+ * workers that share its plans (MBL_ORDER_*, default MBL_ORDER_AUTO).  Plans are cached per
  * (L, nup, ordering), so plans and factorizations made before the call are unaffected.  Any
  * ordering gives the same factorization in exact arithmetic; they differ in fill-in, flops and
  * front sizes (mbl_analyse).  MBL_ERR_INVALID for an unknown value.  Not in the paper, whose

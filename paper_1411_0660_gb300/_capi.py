@@ -23,6 +23,7 @@ MBL_PREC_FP32 = 1
 MBL_ORDER_BAND = 0
 MBL_ORDER_COVER = 1
 MBL_ORDER_MODES = 2
+MBL_ORDER_AUTO = 3
 
 
 class Opts(ctypes.Structure):
@@ -48,7 +49,7 @@ class PlanStats(ctypes.Structure):
                 ("front_bytes_fp32", c_double), ("front_bytes_fp64", c_double),
                 ("solve_factor_bytes_fp32", c_double), ("job_peak_bytes_fp32", c_double),
                 ("job_peak_bytes_fp64", c_double), ("front_peak_bytes_fp32", c_double),
-                ("front_peak_bytes_fp64", c_double)]
+                ("front_peak_bytes_fp64", c_double), ("ordering", c_int64)]
 
 
 class SolveStats(ctypes.Structure):

@@ -152,7 +152,7 @@ std::shared_ptr<Plan> get_plan(mbl_sector *sec) {
     Ctx *ctx = sec->ctx;
     std::shared_ptr<PlanCache> cache = ctx->plans;
     std::lock_guard<std::mutex> lk(cache->mu);
-    const int ordering = cache->ordering;
+    const int ordering = resolve_ordering(cache->ordering, sec->n);
     const int key = plan_key(sec->L, sec->nup, ordering);
     auto it = cache->m.find(key);
     if (it != cache->m.end()) return it->second;
@@ -332,7 +332,8 @@ int mbl_ctx_set_profiling(mbl_ctx *ctx, int on) {
 
 int mbl_ctx_set_ordering(mbl_ctx *ctx, int ordering) {
     if (!ctx) return report(nullptr, MBL_ERR_INVALID, "ctx is NULL");
-    if (ordering != MBL_ORDER_BAND && ordering != MBL_ORDER_COVER && ordering != MBL_ORDER_MODES)
+    if (ordering != MBL_ORDER_BAND && ordering != MBL_ORDER_COVER && ordering != MBL_ORDER_MODES &&
+        ordering != MBL_ORDER_AUTO)
         return report(ctx, MBL_ERR_INVALID, "unknown ordering");
     API_TRY
     std::lock_guard<std::mutex> lk(ctx->plans->mu);
@@ -588,6 +589,7 @@ int mbl_analyse(mbl_sector *sec, int nev, int block, mbl_plan_stats *s) {
     s->solve_factor_bytes_fp32 = (double)p.sg_elems * 4.0;
     s->front_peak_bytes_fp32 = arena_peak_bytes(p, MBL_PREC_FP32, ARENA_AUTO);
     s->front_peak_bytes_fp64 = arena_peak_bytes(p, MBL_PREC_FP64, ARENA_AUTO);
+    s->ordering = p.ordering;
     s->job_peak_bytes_fp32 = (double)job_bytes(p, nev, block, MBL_PREC_FP32);
     s->job_peak_bytes_fp64 = (double)job_bytes(p, nev, block, MBL_PREC_FP64);
     API_CATCH(sec->ctx)

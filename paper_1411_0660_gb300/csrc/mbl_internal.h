@@ -155,9 +155,14 @@ inline int sector_key(int L, int nup) { return L * 64 + nup; }
 struct PlanCache {
     std::mutex mu;
     std::map<int, std::shared_ptr<Plan>> m;  // key: plan_key(L, nup, ordering)
-    int ordering = MBL_ORDER_BAND;           // for plans built from now on
+    int ordering = MBL_ORDER_AUTO;           // for plans built from now on
 };
 inline int plan_key(int L, int nup, int ordering) { return sector_key(L, nup) * 4 + ordering; }
+// The ordering MBL_ORDER_AUTO stands for, for a sector of dimension n.
+inline int resolve_ordering(int ordering, int64_t n) {
+    if (ordering != MBL_ORDER_AUTO) return ordering;
+    return n >= 40000 ? MBL_ORDER_MODES : MBL_ORDER_BAND;
+}
 
 struct Ctx {
     int device = 0;

@@ -200,6 +200,7 @@ struct Plan {
     double flops = 0.0;
     int32_t max_front = 0, nlevels = 0;
     double ms_analyse = 0.0;
+    int ordering = MBL_ORDER_BAND;  // the separator rule the ordering used
 
     // device mirror
     DVec<int32_t> d_perm, d_iperm, d_sn_start, d_sn_nc, d_sn_f, d_rows, d_relind, d_ch_ptr, d_ch_list, d_amap_row;
@@ -217,9 +218,9 @@ struct Plan {
 };
 
 // Build the plan for the pattern of a sector (host arrays: states, rowptr, col of the CSR) with
-// the fill-reducing ordering MBL_ORDER_BAND or MBL_ORDER_COVER.
+// the fill-reducing ordering MBL_ORDER_* (MBL_ORDER_AUTO resolved by the sector dimension).
 std::shared_ptr<Plan> build_plan(int L, const std::vector<uint32_t> &states, const std::vector<int64_t> &rowptr,
-                                 const std::vector<int32_t> &col, int ordering = MBL_ORDER_BAND);
+                                 const std::vector<int32_t> &col, int ordering = MBL_ORDER_AUTO);
 void upload_plan(Ctx *ctx, Plan &p);
 
 }  // namespace mbl

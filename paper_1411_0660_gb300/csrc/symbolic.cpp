@@ -10,12 +10,14 @@
 // f_k in a band [m, m + D_k) separate {f_k < m} from {f_k >= m + D_k}.  (On this graph the f_k are
 // exact eigenvectors of the graph Laplacian, with eigenvalue 2 - 2 cos(2 pi k / L): k = 1 is the
 // spectral-bisection direction of the whole sector.)  Two separator rules:
-//   MBL_ORDER_BAND (default): the band itself, with the mode chosen from the two numbered depth and
+//   MBL_ORDER_BAND: the band itself, with the mode chosen from the two numbered depth and
 //     depth + 1.
 //   MBL_ORDER_MODES: every mode k <= L/2 is tried, and the band of least cost near the median
 //     (cost |S| + 0.3 ||V1| - |V2||) over all of them is taken.  A subgraph already split along one
 //     mode can then be split along an orthogonal one (the band rule re-splits a depth-1 subgraph
 //     along the sine mode that depth 0 used).  At L = 18: 27% less fill, 43% fewer flops.
+//   MBL_ORDER_AUTO (default): MODES for sectors of dimension >= 40000, BAND below (at L = 16 the
+//     saving is small and the factorization is bound by its per-level launch chain).
 //   MBL_ORDER_COVER: every mode k <= L/2 is ranked by its best band near the median
 //     (cost |S| + 0.3 ||V1| - |V2||); for the three best, the separator is the minimum vertex
 //     cover of the edges crossing the band's midpoint (Koenig's theorem on a maximum bipartite
@@ -23,7 +25,7 @@
 //     searching all modes lets a subgraph already split along one mode be split along an
 //     orthogonal one.  At L = 18 this needs 40% less fill and 58% fewer flops, but the covers
 //     leave about twice as many single-column supernodes, whose pivots in-panel pivoting cannot
-//     choose, and the unrefined factor is markedly less accurate; it is therefore not the default.
+//     choose, and its unrefined factor has a heavier tail of element growth.
 // The separator is then thinned (a separator vertex with no neighbour on one side moves to the
 // other side), and the two halves are dissected recursively.  Subgraphs of at most LEAF vertices
 // are ordered by minimum degree.
@@ -345,12 +347,15 @@ struct ND {
 
 std::shared_ptr<Plan> build_plan(int L, const std::vector<uint32_t> &states, const std::vector<int64_t> &rowptr,
                                  const std::vector<int32_t> &col, int ordering) {
-    if (ordering != MBL_ORDER_BAND && ordering != MBL_ORDER_COVER && ordering != MBL_ORDER_MODES)
+    if (ordering != MBL_ORDER_BAND && ordering != MBL_ORDER_COVER && ordering != MBL_ORDER_MODES &&
+        ordering != MBL_ORDER_AUTO)
         fail(MBL_ERR_INVALID, "unknown ordering");
+    ordering = resolve_ordering(ordering, (int64_t)states.size());
     auto t0 = std::chrono::steady_clock::now();
     auto P = std::make_shared<Plan>();
     Plan &p = *P;
     int64_t n = (int64_t)states.size();
+    p.ordering = ordering;
     p.L = L;
     p.n = n;
     p.nnzA = rowptr[n];

@@ -5,7 +5,8 @@
 // structural invariants that the numeric factorization and the solves rely on.  Prints "ok ..." and
 // exits 0, or prints the first violated invariant and exits 1.
 //
-// Usage: plan_check L nup [ordering]   (MBL_ORDER_BAND = 0 (default), MBL_ORDER_COVER = 1, MBL_ORDER_MODES = 2)
+// Usage: plan_check L nup [ordering]   (MBL_ORDER_BAND = 0, MBL_ORDER_COVER = 1, MBL_ORDER_MODES = 2,
+//                                      MBL_ORDER_AUTO = 3 (default))
 #include <algorithm>
 #include <cstdio>
 #include <cstdlib>
@@ -44,7 +45,7 @@ static int popcount32(uint32_t s) {
 int main(int argc, char **argv) {
     if (argc != 3 && argc != 4) return bad("usage: plan_check L nup [ordering]");
     const int L = std::atoi(argv[1]), nup = std::atoi(argv[2]);
-    const int ordering = argc == 4 ? std::atoi(argv[3]) : MBL_ORDER_BAND;
+    const int ordering = argc == 4 ? std::atoi(argv[3]) : MBL_ORDER_AUTO;
     std::vector<uint32_t> st;
     for (uint32_t s = 0; s < (1u << L); ++s)
         if (popcount32(s) == nup) st.push_back(s);
@@ -241,8 +242,8 @@ int main(int argc, char **argv) {
     }
     if (p.lean_peak_elems <= 0 || p.lean_peak_elems > p.arena_elems) return bad("lean peak", p.lean_peak_elems);
     std::printf("ok L=%d nup=%d n=%ld supernodes=%d levels=%d nnz_l=%ld solve_panels=%zu arena=%ld lean_peak=%ld "
-                "flops=%.6e max_front=%d\n",
+                "flops=%.6e max_front=%d ordering=%d\n",
                 L, nup, (long)n, p.ns, p.nlevels, (long)p.nnz_l, p.sdescs.size(), (long)p.arena_elems,
-                (long)p.lean_peak_elems, p.flops, (int)p.max_front);
+                (long)p.lean_peak_elems, p.flops, (int)p.max_front, p.ordering);
     return 0;
 }

@@ -61,6 +61,15 @@ def test_cover_ordering_reduces_fill(checker, L, nup):
     assert cover["nnz_l"] <= modes["nnz_l"] <= band["nnz_l"], (cover, modes, band)
 
 
+@pytest.mark.parametrize("L,nup,resolved", [(16, 8, 0), (17, 9, 0), (18, 9, 2), (18, 4, 0)])
+def test_auto_ordering_by_sector_dimension(checker, L, nup, resolved):
+    """The default picks the modes ordering for sectors of dimension >= 40000 and the band ordering
+    below, and builds exactly the plan that ordering builds."""
+    auto, explicit = _stats(checker, L, nup, 3), _stats(checker, L, nup, resolved)
+    assert auto["ordering"] == resolved
+    assert auto == explicit
+
+
 def test_unknown_ordering_is_rejected(checker):
     r = subprocess.run([checker, "8", "4", "7"], capture_output=True, text=True, timeout=60)
     assert r.returncode != 0
