@@ -226,7 +226,7 @@ int mbl_factor_solve_batch_dev(mbl_factorization *const *fs, int K, const double
                                double *const *d_x, int nrhs, void *stream);
 /* Symbolic analysis of the sector's pattern (nested-dissection ordering, supernodes, schedules;
  * numerical-method section: the analysis phase of the direct solver), built on the host on first
- * use for this L and cached in the context, and its predicted fill-in and device footprint.  No
+ * use for this (L, nup, ordering) and cached in the context, and its predicted fill-in and device footprint.  No
  * numeric factorization runs, so this works for sizes whose fronts would not fit in memory.
  * job_peak_* is the serving admission estimate of one solve_near job with (nev, block). */
 typedef struct mbl_plan_stats {
