@@ -229,6 +229,15 @@ struct ND {
         return c;
     }
 
+    // part[] of the band [m, m + D) of one mode: 1 below it (V1), 3 inside (S), 2 above (V2).
+    void assign_band(const std::vector<int32_t> &V, int mode, double m) {
+        const double Dm = D[mode];
+        for (int32_t v : V) {
+            const double f = fval(mode, states[v]);
+            part[v] = f < m - 1e-12 ? 1 : (f < m + Dm - 1e-12 ? 3 : 2);
+        }
+    }
+
     // Split V into part[] = 1 (V1), 2 (V2), 3 (S).  Returns false if no mode splits V.
     bool split_band(const std::vector<int32_t> &V, int depth) {
         double best_cost = 1e300, best_m = 0.0;
@@ -240,11 +249,7 @@ struct ND {
             if (cost < best_cost) { best_cost = cost; best_m = m; best_mode = mode; }
         }
         if (best_mode < 0) return false;
-        const double Dm = D[best_mode];
-        for (int32_t v : V) {
-            const double fv = fval(best_mode, states[v]);
-            part[v] = fv < best_m - 1e-12 ? 1 : (fv < best_m + Dm - 1e-12 ? 3 : 2);
-        }
+        assign_band(V, best_mode, best_m);
         return true;
     }
 
@@ -263,12 +268,7 @@ struct ND {
         if (rank.empty()) return false;
         std::sort(rank.begin(), rank.end());
         if (!cover) {
-            const int mode = rank[0].second;
-            const double m = mstart[mode];
-            for (int32_t v : V) {
-                const double f = fval(mode, states[v]);
-                part[v] = f < m - 1e-12 ? 1 : (f < m + D[mode] - 1e-12 ? 3 : 2);
-            }
+            assign_band(V, rank[0].second, mstart[rank[0].second]);
             return true;
         }
         for (int a = 0; a < N; ++a) pos_in[V[a]] = a;
@@ -289,12 +289,7 @@ struct ND {
         }
         for (int a = 0; a < N; ++a) pos_in[V[a]] = -1;
         if (best >= 1e300) {  // every cover emptied a side: the band of the best mode
-            const int mode = rank[0].second;
-            const double m = mstart[mode];
-            for (int32_t v : V) {
-                const double f = fval(mode, states[v]);
-                part[v] = f < m - 1e-12 ? 1 : (f < m + D[mode] - 1e-12 ? 3 : 2);
-            }
+            assign_band(V, rank[0].second, mstart[rank[0].second]);
             return true;
         }
         for (int a = 0; a < N; ++a) part[V[a]] = best_cov[a] ? 3 : (best_fv[a] < best_t ? 1 : 2);
