@@ -112,7 +112,7 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
-_ORDERING = {"band": 0, "cover": 1, "modes": 2, "auto": 3}
+_ORDERING = {"band": 0, "cover": 1, "modes": 2, "auto": 3, "hybrid": 4}
 _ordering = 3
 
 

@@ -61,6 +61,8 @@ extern "C" {
 #define MBL_ORDER_AUTO 3  /* MBL_ORDER_MODES for sectors of dimension >= 40000 (L >= 18 at half filling),
                              where its smaller factor pays; MBL_ORDER_BAND below, where the
                              factorization is bound by the per-level launch chain */
+#define MBL_ORDER_HYBRID 4 /* MBL_ORDER_COVER on subgraphs of >= 2000 vertices, MBL_ORDER_MODES on smaller
+                              ones: nearly the cover's fill without its single-column leaves */
 
 typedef struct mbl_ctx mbl_ctx;
 typedef struct mbl_sector mbl_sector;

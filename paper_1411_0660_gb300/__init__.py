@@ -20,12 +20,13 @@ from dataclasses import dataclass
 import numpy as np
 
 from . import _capi
-from ._capi import MBL_ORDER_AUTO, MBL_ORDER_BAND, MBL_ORDER_COVER, MBL_ORDER_MODES, MBL_PREC_FP32, MBL_PREC_FP64, FactorStats, Opts, PlanStats, SolveStats
+from ._capi import (MBL_ORDER_AUTO, MBL_ORDER_BAND, MBL_ORDER_COVER, MBL_ORDER_HYBRID, MBL_ORDER_MODES,
+                    MBL_PREC_FP32, MBL_PREC_FP64, FactorStats, Opts, PlanStats, SolveStats)
 
 __all__ = ["Context", "Sector", "Factorization", "MblError", "build_sector", "build_sector_fields",
            "extremal_bounds", "factor", "solve_near", "solve_near_dev", "observables", "observables_dev",
            "default_opts", "launch_count", "factor_solve_batch_dev", "entanglement_noalloc_dev", "Server", "ServedResult", "MBL_PREC_FP32", "MBL_PREC_FP64",
-           "MBL_ORDER_AUTO", "MBL_ORDER_BAND", "MBL_ORDER_COVER", "MBL_ORDER_MODES"]
+           "MBL_ORDER_AUTO", "MBL_ORDER_BAND", "MBL_ORDER_COVER", "MBL_ORDER_MODES", "MBL_ORDER_HYBRID"]
 
 
 class MblError(RuntimeError):
@@ -67,7 +68,7 @@ class Context:
 
     def set_ordering(self, ordering: int):
         """Ordering of the symbolic analyses built from now on: MBL_ORDER_AUTO (the default),
-        MBL_ORDER_BAND, MBL_ORDER_MODES or MBL_ORDER_COVER."""
+        MBL_ORDER_BAND, MBL_ORDER_MODES, MBL_ORDER_COVER or MBL_ORDER_HYBRID."""
         _check(_lib().mbl_ctx_set_ordering(self.handle, int(ordering)), self.handle)
 
     def profile(self, name: str) -> dict:

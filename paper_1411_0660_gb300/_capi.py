@@ -24,6 +24,7 @@ MBL_ORDER_BAND = 0
 MBL_ORDER_COVER = 1
 MBL_ORDER_MODES = 2
 MBL_ORDER_AUTO = 3
+MBL_ORDER_HYBRID = 4
 
 
 class Opts(ctypes.Structure):

@@ -332,9 +332,7 @@ int mbl_ctx_set_profiling(mbl_ctx *ctx, int on) {
 
 int mbl_ctx_set_ordering(mbl_ctx *ctx, int ordering) {
     if (!ctx) return report(nullptr, MBL_ERR_INVALID, "ctx is NULL");
-    if (ordering != MBL_ORDER_BAND && ordering != MBL_ORDER_COVER && ordering != MBL_ORDER_MODES &&
-        ordering != MBL_ORDER_AUTO)
-        return report(ctx, MBL_ERR_INVALID, "unknown ordering");
+    if (ordering < MBL_ORDER_BAND || ordering > MBL_ORDER_HYBRID) return report(ctx, MBL_ERR_INVALID, "unknown ordering");
     API_TRY
     std::lock_guard<std::mutex> lk(ctx->plans->mu);
     ctx->plans->ordering = ordering;

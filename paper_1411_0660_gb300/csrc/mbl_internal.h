@@ -157,7 +157,7 @@ struct PlanCache {
     std::map<int, std::shared_ptr<Plan>> m;  // key: plan_key(L, nup, ordering)
     int ordering = MBL_ORDER_AUTO;           // for plans built from now on
 };
-inline int plan_key(int L, int nup, int ordering) { return sector_key(L, nup) * 4 + ordering; }
+inline int plan_key(int L, int nup, int ordering) { return sector_key(L, nup) * 8 + ordering; }
 // The ordering MBL_ORDER_AUTO stands for, for a sector of dimension n.
 inline int resolve_ordering(int ordering, int64_t n) {
     if (ordering != MBL_ORDER_AUTO) return ordering;

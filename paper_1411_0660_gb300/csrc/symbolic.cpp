@@ -18,6 +18,8 @@
 //     along the sine mode that depth 0 used).  At L = 18: 27% less fill, 43% fewer flops.
 //   MBL_ORDER_AUTO (default): MODES for sectors of dimension >= 40000, BAND below (at L = 16 the
 //     saving is small and the factorization is bound by its per-level launch chain).
+//   MBL_ORDER_HYBRID: COVER on subgraphs of at least HYBRID_COVER_MIN vertices, where the
+//     separators set the fill, MODES below, where the covers would leave single-column leaves.
 //   MBL_ORDER_COVER: every mode k <= L/2 is ranked by its best band near the median
 //     (cost |S| + 0.3 ||V1| - |V2||); for the three best, the separator is the minimum vertex
 //     cover of the edges crossing the band's midpoint (Koenig's theorem on a maximum bipartite
@@ -46,6 +48,7 @@ namespace mbl {
 namespace {
 
 constexpr int LEAF = 64;
+constexpr int HYBRID_COVER_MIN = 2000;  // MBL_ORDER_HYBRID: cover separators on subgraphs this large
 
 struct Graph {
     int64_t n;
@@ -302,7 +305,8 @@ struct ND {
             return;
         }
         const int N = (int)V.size();
-        const bool ok = ordering == MBL_ORDER_BAND ? split_band(V, depth) : split_modes(V, ordering == MBL_ORDER_COVER);
+        const bool cover = ordering == MBL_ORDER_COVER || (ordering == MBL_ORDER_HYBRID && N >= HYBRID_COVER_MIN);
+        const bool ok = ordering == MBL_ORDER_BAND ? split_band(V, depth) : split_modes(V, cover);
         if (!ok) {  // cannot split (degenerate values): minimum degree in chunks
             std::vector<int32_t> chunk;
             for (int a = 0; a < N; ++a) {
@@ -342,9 +346,7 @@ struct ND {
 
 std::shared_ptr<Plan> build_plan(int L, const std::vector<uint32_t> &states, const std::vector<int64_t> &rowptr,
                                  const std::vector<int32_t> &col, int ordering) {
-    if (ordering != MBL_ORDER_BAND && ordering != MBL_ORDER_COVER && ordering != MBL_ORDER_MODES &&
-        ordering != MBL_ORDER_AUTO)
-        fail(MBL_ERR_INVALID, "unknown ordering");
+    if (ordering < MBL_ORDER_BAND || ordering > MBL_ORDER_HYBRID) fail(MBL_ERR_INVALID, "unknown ordering");
     ordering = resolve_ordering(ordering, (int64_t)states.size());
     auto t0 = std::chrono::steady_clock::now();
     auto P = std::make_shared<Plan>();

@@ -6,7 +6,7 @@
 // exits 0, or prints the first violated invariant and exits 1.
 //
 // Usage: plan_check L nup [ordering]   (MBL_ORDER_BAND = 0, MBL_ORDER_COVER = 1, MBL_ORDER_MODES = 2,
-//                                      MBL_ORDER_AUTO = 3 (default))
+//                                      MBL_ORDER_AUTO = 3 (default), MBL_ORDER_HYBRID = 4)
 #include <algorithm>
 #include <cstdio>
 #include <cstdlib>

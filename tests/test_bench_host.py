@@ -32,4 +32,5 @@ def test_orderings_named_like_the_library():
     from paper_1411_0660_gb300 import _capi
 
     assert bench._ORDERING == {"band": _capi.MBL_ORDER_BAND, "cover": _capi.MBL_ORDER_COVER,
-                               "modes": _capi.MBL_ORDER_MODES, "auto": _capi.MBL_ORDER_AUTO}
+                               "modes": _capi.MBL_ORDER_MODES, "auto": _capi.MBL_ORDER_AUTO,
+                               "hybrid": _capi.MBL_ORDER_HYBRID}

@@ -36,7 +36,7 @@ def checker(tmp_path_factory):
 
 @pytest.mark.parametrize("L,nup", [(2, 1), (8, 4), (10, 5), (11, 5), (12, 3), (13, 7), (14, 7), (15, 8), (16, 8), (17, 9), (18, 9),
                                    (12, 1), (9, 0)])
-@pytest.mark.parametrize("ordering", [0, 1, 2])
+@pytest.mark.parametrize("ordering", [0, 1, 2, 4])
 def test_plan_invariants(checker, L, nup, ordering):
     r = subprocess.run([checker, str(L), str(nup), str(ordering)], capture_output=True, text=True, timeout=120)
     assert r.returncode == 0 and r.stdout.startswith("ok"), r.stdout + r.stderr
@@ -53,12 +53,15 @@ def test_cover_ordering_reduces_fill(checker, L, nup):
     """A minimum cover of the edges crossing a threshold inside a band is never larger than the band,
     and the cover ordering also searches every mode: fill-in and flops shrink, the largest front
     does not grow by more than a few percent."""
-    band, cover, modes = (_stats(checker, L, nup, o) for o in (0, 1, 2))
+    band, cover, modes, hybrid = (_stats(checker, L, nup, o) for o in (0, 1, 2, 4))
     assert cover["nnz_l"] < 0.9 * band["nnz_l"], (cover, band)
     assert cover["flops"] < 0.85 * band["flops"], (cover, band)
     assert cover["max_front"] <= 1.05 * band["max_front"], (cover, band)
     # the cover refines the best band among the same modes: never more fill than that band alone
     assert cover["nnz_l"] <= modes["nnz_l"] <= band["nnz_l"], (cover, modes, band)
+    # the hybrid takes covers only where subgraphs are large: between the two, and fewer supernodes
+    assert cover["nnz_l"] <= hybrid["nnz_l"] <= modes["nnz_l"], (cover, hybrid, modes)
+    assert hybrid["supernodes"] <= cover["supernodes"], (hybrid, cover)
 
 
 @pytest.mark.parametrize("L,nup,resolved", [(16, 8, 0), (17, 9, 0), (18, 9, 2), (18, 4, 0)])
