@@ -32,7 +32,7 @@
 // other side), and the two halves are dissected recursively.  Subgraphs of at most LEAF vertices
 // are ordered by minimum degree.
 //
-// Symbolic factorization.  Elimination tree (Liu), postorder, column counts from row subtrees,
+// Symbolic factorization.  Elimination tree (Liu), postorder, column counts (Gilbert, Ng and Peyton),
 // fundamental supernodes, relaxed amalgamation, and supernodal row structures by merging the
 // children's update rows.
 #include <algorithm>
@@ -449,20 +449,59 @@ std::shared_ptr<Plan> build_plan(int L, const std::vector<uint32_t> &states, con
     lower_lists(p.perm, p.iperm, lp, li);
     etree(lp, li, parent);
 
-    // ---- 3. column counts (strictly lower) by row subtrees ----
+    // ---- 3. column counts (strictly lower), Gilbert, Ng and Peyton (1994) ----
+    // Column j of L holds row i > j exactly when j lies in the row subtree T_i (the union of the
+    // tree paths from each k < i with A(i, k) != 0 up to i).  With the columns in postorder,
+    // colcount(j) = 1 + #{i > j : j in T_i} is the sum over the subtree of j of
+    //   delta(d) = [d a leaf of the tree] - #children(d)
+    //            + #{i : d a leaf of T_i} - #{i : d the lowest common ancestor of two leaves of
+    //              T_i adjacent in postorder},
+    // which takes O(nnz(A)) work plus near-constant-time ancestor queries, instead of one step per
+    // entry of L.  d is a leaf of T_i iff no earlier neighbour k of row i lies in d's subtree,
+    // i.e. the last neighbour seen is before first(d), the first descendant of d; the common
+    // ancestor of the previous leaf and d is the root of the previous leaf's set in a union-find
+    // whose completed nodes point at their parents (Tarjan's offline ancestors).
     std::vector<int64_t> cc(n, 0);
     {
-        std::vector<int32_t> mark(n, -1);
-        for (int64_t i = 0; i < n; ++i) {
-            mark[i] = (int32_t)i;
-            for (int64_t e = lp[i]; e < lp[i + 1]; ++e) {
-                int32_t r = li[e];
-                while (mark[r] != i) {
-                    cc[r]++;
-                    mark[r] = (int32_t)i;
-                    r = parent[r];
-                }
+        std::vector<int64_t> up(n + 1, 0);  // upper pattern: rows i > j of column j, ascending
+        for (int64_t i = 0; i < n; ++i)
+            for (int64_t e = lp[i]; e < lp[i + 1]; ++e) up[li[e] + 1]++;
+        for (int64_t j = 0; j < n; ++j) up[j + 1] += up[j];
+        std::vector<int32_t> ui(up[n]);
+        {
+            std::vector<int64_t> fill(up.begin(), up.end() - 1);
+            for (int64_t i = 0; i < n; ++i)
+                for (int64_t e = lp[i]; e < lp[i + 1]; ++e) ui[fill[li[e]]++] = (int32_t)i;
+        }
+        std::vector<int32_t> first(n, -1), last(n, -1), prevleaf(n, -1), anc(n);
+        std::vector<int64_t> delta(n, 0);
+        for (int64_t k = 0; k < n; ++k)
+            for (int64_t j = k; j != -1 && first[j] == -1; j = parent[j]) first[j] = (int32_t)k;
+        std::iota(anc.begin(), anc.end(), 0);
+        auto find = [&](int32_t x) {  // root of x's set, with path halving
+            while (anc[x] != x) {
+                anc[x] = anc[anc[x]];
+                x = anc[x];
             }
+            return x;
+        };
+        for (int64_t j = 0; j < n; ++j) {
+            if (first[j] == j) delta[j] += 1;      // a leaf of the elimination tree
+            if (parent[j] >= 0) delta[parent[j]] -= 1;
+            for (int64_t e = up[j]; e < up[j + 1]; ++e) {
+                const int32_t i = ui[e];
+                if (last[i] < first[j]) {           // j is a leaf of T_i
+                    delta[j] += 1;
+                    if (prevleaf[i] >= 0) delta[find(prevleaf[i])] -= 1;
+                    prevleaf[i] = (int32_t)j;
+                }
+                last[i] = (int32_t)j;
+            }
+            if (parent[j] >= 0) anc[j] = parent[j];
+        }
+        for (int64_t j = 0; j < n; ++j) {
+            if (parent[j] >= 0) delta[parent[j]] += delta[j];
+            cc[j] = delta[j] - 1;
         }
     }
     std::vector<int32_t> nchild(n, 0);
