@@ -17,7 +17,7 @@ LIB = os.path.join(OUT_DIR, "libmblsi.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVFLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
            "-I" + INCLUDE, "-I" + CSRC] + ARCH
-CXXFLAGS = ["-std=c++17", "-O2", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
+CXXFLAGS = ["-std=c++17", "-O2", "-fPIC", "-pthread", "-I" + INCLUDE, "-I" + CSRC]
 
 
 def _nvcc() -> str:
@@ -69,7 +69,7 @@ def build(force: bool = False) -> str:
         objs = list(ex.map(lambda s: _compile(s, hm, force), srcs))
     if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs):
         tmp = LIB + f".{os.getpid()}.tmp"
-        cmd = [_nvcc(), "-shared"] + ARCH + ["-o", tmp] + objs
+        cmd = [_nvcc(), "-shared"] + ARCH + ["-o", tmp] + objs + ["-lpthread"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed: {' '.join(cmd)}\n{r.stdout}\n{r.stderr}")

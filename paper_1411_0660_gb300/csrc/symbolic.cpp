@@ -40,6 +40,7 @@
 #include <chrono>
 #include <cmath>
 #include <numeric>
+#include <thread>
 
 #include "plan.h"
 
@@ -263,11 +264,22 @@ struct ND {
         const int N = (int)V.size();
         const int nmodes = 2 * (L / 2);
         std::vector<std::pair<double, int>> rank;
-        std::vector<double> mstart(nmodes, 0.0);
-        for (int mode = 0; mode < nmodes; ++mode) {
-            const double cost = best_band(V, mode, mstart[mode]);
-            if (cost < 1e300) rank.push_back({cost, mode});
+        std::vector<double> mstart(nmodes, 0.0), cost(nmodes, 1e300);
+        // the modes are independent (best_band only reads): large subgraphs spread them over threads
+        auto some_modes = [&](int m0, int step) {
+            for (int mode = m0; mode < nmodes; mode += step) cost[mode] = best_band(V, mode, mstart[mode]);
+        };
+        const int nt = N >= 1024 ? std::min<int>(nmodes, std::max(1, (int)std::thread::hardware_concurrency())) : 1;
+        if (nt > 1) {
+            std::vector<std::thread> pool;
+            for (int t = 1; t < nt; ++t) pool.emplace_back(some_modes, t, nt);
+            some_modes(0, nt);
+            for (std::thread &th : pool) th.join();
+        } else {
+            some_modes(0, 1);
         }
+        for (int mode = 0; mode < nmodes; ++mode)
+            if (cost[mode] < 1e300) rank.push_back({cost[mode], mode});
         if (rank.empty()) return false;
         std::sort(rank.begin(), rank.end());
         if (!cover) {

@@ -27,7 +27,7 @@ def checker(tmp_path_factory):
     if not os.path.isdir(libdir):
         libdir = os.path.join(os.path.dirname(inc), "lib")
     exe = str(tmp_path_factory.mktemp("plan") / "plan_check")
-    cmd = ["g++", "-O2", "-std=c++17", "-I" + inc, "-I" + os.path.join(ROOT, "include"), "-I" + CSRC,
+    cmd = ["g++", "-O2", "-std=c++17", "-pthread", "-I" + inc, "-I" + os.path.join(ROOT, "include"), "-I" + CSRC,
            os.path.join(ROOT, "tests", "plan_check.cpp"), os.path.join(CSRC, "symbolic.cpp"), "-o", exe,
            "-L" + libdir, "-lcudart", "-Wl,-rpath," + libdir]
     subprocess.run(cmd, check=True, capture_output=True)
