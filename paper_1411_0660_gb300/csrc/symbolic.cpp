@@ -40,6 +40,8 @@
 #include <chrono>
 #include <cmath>
 #include <numeric>
+#include <exception>
+#include <system_error>
 #include <thread>
 
 #include "plan.h"
@@ -265,19 +267,29 @@ struct ND {
         const int nmodes = 2 * (L / 2);
         std::vector<std::pair<double, int>> rank;
         std::vector<double> mstart(nmodes, 0.0), cost(nmodes, 1e300);
-        // the modes are independent (best_band only reads): large subgraphs spread them over threads
-        auto some_modes = [&](int m0, int step) {
-            for (int mode = m0; mode < nmodes; mode += step) cost[mode] = best_band(V, mode, mstart[mode]);
-        };
+        // the modes are independent (best_band only reads): large subgraphs spread them over threads.
+        // A thread that cannot be started leaves its stride to the calling thread; an exception in
+        // a worker (host memory) is carried back and rethrown after every worker has joined.
         const int nt = N >= 1024 ? std::min<int>(nmodes, std::max(1, (int)std::thread::hardware_concurrency())) : 1;
-        if (nt > 1) {
-            std::vector<std::thread> pool;
-            for (int t = 1; t < nt; ++t) pool.emplace_back(some_modes, t, nt);
-            some_modes(0, nt);
-            for (std::thread &th : pool) th.join();
-        } else {
-            some_modes(0, 1);
+        std::vector<std::exception_ptr> err(nt);
+        auto some_modes = [&](int m0) {
+            try {
+                for (int mode = m0; mode < nmodes; mode += nt) cost[mode] = best_band(V, mode, mstart[mode]);
+            } catch (...) {
+                err[m0] = std::current_exception();
+            }
+        };
+        std::vector<std::thread> pool;
+        int started = 1;
+        try {
+            for (; started < nt; ++started) pool.emplace_back(some_modes, started);
+        } catch (const std::system_error &) {
         }
+        some_modes(0);
+        for (int t = started; t < nt; ++t) some_modes(t);
+        for (std::thread &th : pool) th.join();
+        for (const std::exception_ptr &e : err)
+            if (e) std::rethrow_exception(e);
         for (int mode = 0; mode < nmodes; ++mode)
             if (cost[mode] < 1e300) rank.push_back({cost[mode], mode});
         if (rank.empty()) return false;
