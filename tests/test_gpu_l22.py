@@ -1,8 +1,10 @@
 """The largest sector of the paper's campaign, L = 22 (dimension 705 432), on one GPU (needs a GB300).
 
-With whole-square fronts the factorization would need 444 GB of fronts at once; the memory-lean arena
+With the band ordering's plan, whole-square fronts would need 444 GB at once; the memory-lean arena
 needs about 156 GB at its peak, so one FP32 job (fronts, the 80 GB solve factor, Krylov basis) fits
-one GB300: the admission estimate is about 255 GB of the 298 GB, the measured peak about 180 GB.  One job (h = 3, seed 0, eps = 0.5, nev = 50) must return 50 eigenpairs whose residuals,
+one GB300: the admission estimate is about 255 GB of the 298 GB, the measured peak about 180 GB.
+The default ordering builds the smaller modes plan at this size (fronts' peak about 110 GB, solve
+factor about 54 GB).  One job (h = 3, seed 0, eps = 0.5, nev = 50) must return 50 eigenpairs whose residuals,
 recomputed with the oracle's CSR Hamiltonian, are within 1e-10 ||H||, with the shift placed by the
 oracle's extremal bounds.  The oracle's dense and shift-invert eigensolvers do not reach this size,
 so the window itself is checked by its defining property on the GPU's pairs: orthonormal vectors of
