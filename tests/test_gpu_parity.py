@@ -231,6 +231,25 @@ def _check_job(g, ctx, orc, L, h, seed, eps, nev, prec, block=8, **kw):
     return res, spectrum, hn
 
 
+@pytest.mark.parametrize("ordering", ["BAND", "MODES", "COVER", "HYBRID"])
+def test_every_ordering_matches_the_oracle(g, orc, ordering):
+    """Every fill-reducing ordering factors the same matrix (in exact arithmetic a symmetric
+    permutation of one LDL^T), so each must give the oracle's eigenpairs: L = 14, h = 2.5, seed 3,
+    eps = 0.5, 20 pairs, FP32 fronts.  A context of its own, so the shared one keeps the default."""
+    code = getattr(g, f"MBL_ORDER_{ordering}")
+    c = g.Context(0)
+    try:
+        c.set_ordering(code)
+        sec = g.build_sector(c, 14, 2.5, 3)
+        assert g.analyse(sec, 20, 8)["ordering"] == code
+        sec.close()
+        _check_job(g, c, orc, 14, 2.5, 3, 0.5, 20, 1)
+        with pytest.raises(g.MblError):
+            c.set_ordering(7)
+    finally:
+        c.close()
+
+
 @pytest.mark.parametrize("prec", [0, 1])
 def test_config_L12_h2_seed0(g, ctx, orc, prec):
     """Headline small case: L=12, h=2.0, seed 0, eps=0.5, nev=20 (FP64 and FP32 fronts)."""
